@@ -1,0 +1,123 @@
+"""Pins for the oracle's randomized SVD (Section 2.1, Section 2.2)."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import rsvd as R
+from oracle.linalg import apply, householder_qr
+from synth import prescribed_dense, spectrum_geometric
+from tests.metrics import max_principal_angle
+
+
+def test_exact_when_sketch_spans_the_range():
+    """A of exact rank 25 and r = 30 >= 25: the randomized SVD is exact."""
+    m, n, k, p = 300, 120, 20, 10
+    s = np.concatenate([spectrum_geometric(25, 0.8), np.zeros(0)])
+    A, U0, V0 = prescribed_dense(m, n, s, seed=11)
+    for q in (0, 1, 2):
+        U, S, V = R.rsvd(A, k, p, q, seed=21)
+        assert np.max(np.abs(S - s[:k]) / s[:k]) < 1e-12
+        assert max_principal_angle(U, U0[:, :k]) < 1e-10
+        assert max_principal_angle(V, V0[:, :k]) < 1e-10
+        # the factors reproduce the rank-k truncation of A
+        Ak = (U0[:, :k] * s[:k]) @ V0[:, :k].T
+        assert np.linalg.norm((U * S) @ V.T - Ak) < 1e-12 * np.linalg.norm(Ak)
+
+
+def test_exact_when_r_equals_min_dimension():
+    m, n = 80, 40
+    s = spectrum_geometric(40, 0.9)
+    A, U0, V0 = prescribed_dense(m, n, s, seed=3)
+    U, S, V = R.rsvd(A, 30, 10, 0, seed=4)
+    assert np.max(np.abs(S - s[:30]) / s[:30]) < 1e-12
+
+
+def _hmt_factor(k, p, m, n, q):
+    return (1 + 11 * math.sqrt(k + p) * math.sqrt(min(m, n))) ** (1.0 / (2 * q + 1))
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_hmt_error_bound_over_seeds(q):
+    """||A - Q Q^T A||_2 <= [1 + 11 sqrt(k+p) sqrt(min(m,n))]^(1/(2q+1)) sigma_{k+1}
+    (Halko, Martinsson & Tropp 2011, Eq. (1.9) and its power-scheme form in
+    Section 10.4), which holds with probability >= 1 - 6 p^-p."""
+    m, n, k, p = 400, 200, 20, 10
+    s = 1.0 / np.arange(1, n + 1)
+    A, _, _ = prescribed_dense(m, n, s, seed=5)
+    for seed in range(10):
+        Q = R.range_finder(A, k + p, q, seed)
+        err = np.linalg.norm(A - Q @ (Q.T @ A), 2)
+        assert err <= _hmt_factor(k, p, m, n, q) * s[k]
+        assert err >= s[k + p] * (1 - 1e-12)  # no rank-r projector beats sigma_{r+1}
+
+
+def test_power_iterations_shrink_the_error():
+    m, n, k, p = 500, 300, 20, 5
+    s = 1.0 / np.sqrt(np.arange(1, n + 1))
+    A, _, _ = prescribed_dense(m, n, s, seed=6)
+    errs = []
+    for q in (0, 1, 2):
+        Q = R.range_finder(A, k + p, q, seed=7)
+        errs.append(np.linalg.norm(A - Q @ (Q.T @ A), 2))
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_interlacing_and_rayleigh_ritz():
+    """sigma_i(Q^T A) <= sigma_i(A); the small SVD equals a library SVD of Q^T A."""
+    m, n, k, p, q = 300, 150, 10, 5, 1
+    s = spectrum_geometric(150, 0.97)
+    A, _, _ = prescribed_dense(m, n, s, seed=8)
+    U, S, V = R.rsvd(A, k, p, q, seed=9)
+    assert np.all(S <= s[:k] * (1 + 1e-12))
+    Q = R.range_finder(A, k + p, q, seed=9)
+    ref = np.linalg.svd(Q.T @ A, compute_uv=False)[:k]
+    assert np.allclose(S, ref, rtol=1e-12)
+    # U = Q U_B: U lies in span(Q); U and V are orthonormal and U^T A V = diag(S)
+    assert np.linalg.norm(U - Q @ (Q.T @ U)) < 1e-12
+    assert np.linalg.norm(U.T @ U - np.eye(k)) < 1e-12
+    assert np.linalg.norm(V.T @ V - np.eye(k)) < 1e-12
+    assert np.allclose(U.T @ A @ V, np.diag(S), atol=1e-12)
+
+
+def test_small_svd_of_bt_reconstructs_b():
+    rng = np.random.default_rng(12)
+    Bt = rng.standard_normal((90, 12)) * np.logspace(0, -4, 12)
+    UB, sig, V = R.small_svd_of_bt(Bt)
+    assert np.linalg.norm(V @ np.diag(sig) @ UB.T - Bt) < 1e-13 * np.linalg.norm(Bt)
+    assert np.allclose(sig, np.linalg.svd(Bt, compute_uv=False), rtol=1e-12)
+
+
+def test_full_svd_matches_library():
+    rng = np.random.default_rng(13)
+    for shape in [(9, 4), (4, 9), (6, 6)]:
+        A = rng.standard_normal(shape)
+        U, S, V = R.full_svd(A)
+        assert np.allclose(S, np.linalg.svd(A, compute_uv=False), rtol=1e-13)
+        assert np.linalg.norm((U * S) @ V.T - A) < 1e-13 * np.linalg.norm(A)
+
+
+def test_signs_are_normalised():
+    m, n = 60, 30
+    A, _, _ = prescribed_dense(m, n, spectrum_geometric(30, 0.7), seed=14)
+    U, S, V = R.rsvd(A, 5, 5, 1, seed=15)
+    idx = np.argmax(np.abs(U), axis=0)
+    assert np.all(U[idx, np.arange(5)] > 0)
+
+
+def test_argument_checks():
+    A = np.zeros((10, 5))
+    with pytest.raises(ValueError):
+        R.rsvd(A, 4, 2, 0, seed=1)  # k + p > min(m, n)
+    with pytest.raises(ValueError):
+        R.rsvd(A, 0, 2, 0, seed=1)
+
+
+def test_fp32_input_is_widened_exactly():
+    rng = np.random.default_rng(16)
+    A32 = rng.standard_normal((50, 20)).astype(np.float32)
+    X = rng.standard_normal((20, 3))
+    assert np.array_equal(apply(A32, X), A32.astype(np.float64) @ X)
+    Q, _ = householder_qr(apply(A32, X))
+    assert Q.shape == (50, 3)

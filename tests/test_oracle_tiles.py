@@ -1,0 +1,71 @@
+"""Pins for the oracle's block-cyclic tile map and CSR tiles (brute force)."""
+
+import numpy as np
+import pytest
+
+from oracle import tiles as T
+
+
+@pytest.mark.parametrize("m,n,mb,nb,S", [(10, 7, 3, 2, 2), (100000, 20000, 4096, 4096, 2),
+                                         (1, 1, 5, 5, 3), (8, 8, 8, 8, 1), (0, 5, 2, 2, 2)])
+def test_tile_map_partitions_the_matrix(m, n, mb, nb, S):
+    tiles = T.tile_map(m, n, mb, nb, S)
+    Tm, Tn = -(-m // mb), -(-n // nb)
+    assert len(tiles) == Tm * Tn
+    assert [t[0] for t in tiles] == list(range(len(tiles)))
+    if m * n <= 10000:
+        cover = np.zeros((m, n), dtype=np.int64)
+        for t, I, J, r0, r1, c0, c1, slot in tiles:
+            cover[r0:r1, c0:c1] += 1
+            assert slot == t % S and t == I * Tn + J
+        assert np.all(cover == 1)
+    else:
+        area = sum((r1 - r0) * (c1 - c0) for _, _, _, r0, r1, c0, c1, _ in tiles)
+        assert area == m * n
+
+
+def test_c2_tile_edges():
+    tiles = T.tile_map(100000, 20000, 4096, 4096, 2)
+    assert len(tiles) == 25 * 5
+    last = tiles[-1]
+    assert last[3:7] == (24 * 4096, 100000, 4 * 4096, 20000)
+    assert 100000 - 24 * 4096 == 1696 and 20000 - 4 * 4096 == 3616
+
+
+def _random_csr(m, n, density, seed):
+    rng = np.random.default_rng(seed)
+    D = (rng.random((m, n)) < density) * rng.integers(1, 9, size=(m, n)).astype(np.float32)
+    rp = [0]
+    ci = []
+    v = []
+    for i in range(m):
+        nz = np.nonzero(D[i])[0]
+        ci += list(nz)
+        v += list(D[i, nz])
+        rp.append(len(ci))
+    return D, np.array(rp), np.array(ci), np.array(v, dtype=np.float32)
+
+
+def test_csr_tiles_match_dense_slices():
+    D, rp, ci, v = _random_csr(23, 17, 0.2, 1)
+    for (_, _, _, r0, r1, c0, c1, _) in T.tile_map(23, 17, 5, 6, 2):
+        lrp, lci, lv = T.csr_tile(rp, ci, v, r0, r1, c0, c1)
+        sub = np.zeros((r1 - r0, c1 - c0), dtype=np.float32)
+        for i in range(r1 - r0):
+            for e in range(lrp[i], lrp[i + 1]):
+                sub[i, lci[e]] = lv[e]
+        assert np.array_equal(sub, D[r0:r1, c0:c1])
+    total = sum(T.csr_tile(rp, ci, v, r0, r1, c0, c1)[0][-1]
+                for (_, _, _, r0, r1, c0, c1, _) in T.tile_map(23, 17, 5, 6, 2))
+    assert total == len(v)
+
+
+def test_csr_transpose_is_exact():
+    D, rp, ci, v = _random_csr(19, 11, 0.3, 2)
+    trp, tci, tv = T.csr_transpose(19, 11, rp, ci, v)
+    Dt = np.zeros((11, 19), dtype=np.float32)
+    for j in range(11):
+        assert np.all(np.diff(tci[trp[j]:trp[j + 1]]) > 0)
+        for e in range(trp[j], trp[j + 1]):
+            Dt[j, tci[e]] = tv[e]
+    assert np.array_equal(Dt, D.T)
