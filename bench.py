@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the randomized SVD on one (or N independent) GB300.
+
+Workload: dense FP32 A, 100000 x 20000 (8 GB), A = U diag(s) V^T with
+s_i = |1/i + 1e-4 g_i|, rank k = 100, oversampling p = 20, q = 2 power
+iterations, 4096 x 4096 block-cyclic tiles.  One step = one full randomized
+SVD (Gaussian test matrix, 2q+2 A-passes, CholeskyQR2 after each, small SVD,
+lift) with A already resident in HBM.  A (8 GB) is larger than L2 (129 MB),
+so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  Options:
+  --gpus N --steps K --warmup W    replicas on N GPUs (torchrun), K timed steps
+  --impl reference                 time the FP64 CPU oracle on a bounded sample
+  --prec bf16|fp32|bf16x3          precision of the headline path
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "dense_fp32_100000x20000"
+METRIC = "rsvd_throughput_dense_fp32_100000x20000_k100_p20_q2"
+UNIT = "rSVD/s"
+ORACLE_SAMPLE_ROWS = 10000
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop x SM clock.  The clock is the
+# median SM clock sampled under load in the same run (max 2070 MHz).
+def _fp32_peak_tflops(sm_mhz: float) -> float:
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 20 ms during a region."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "20",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.1)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                sm.append(float(parts[2]))
+                mx = float(parts[3])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[6:10]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _spectrum(n, noise_seed):
+    from synth import spectrum_harmonic_noisy
+    return spectrum_harmonic_noisy(n, 1e-4, noise_seed)
+
+
+def _build_A(device):
+    import torch
+    from synth import WORKLOADS, prescribed_dense_torch
+    w = WORKLOADS[WORKLOAD]
+    s = _spectrum(w.n, w.noise_seed)
+    A = prescribed_dense_torch(w.m, w.n, s, w.data_seed, device=device)
+    torch.cuda.synchronize()
+    return w, A
+
+
+def _traffic_for(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this build."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+    except OSError:
+        return None
+    ent = data.get(kernel_key)
+    if not ent:
+        return None
+    from paper_1907_06470_gb300 import build as b
+    if ent.get("source_digest") != b._digest():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def oracle_sample_seconds(A_rows_f32: np.ndarray, w) -> float:
+    """Wall time of the FP64 CPU oracle on the first rows of A (same n, k, p, q, seed)."""
+    from oracle import rsvd as OR
+    t0 = time.perf_counter()
+    OR.rsvd(A_rows_f32, w.k, w.p, w.q, w.seed, "f32")
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import torch
+    device = torch.device("cuda", local) if torch.cuda.is_available() else None
+    if device is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no CUDA device to build the synthetic matrix"}))
+        return 0
+    w, A = _build_A(device)
+    sample = A[:ORACLE_SAMPLE_ROWS].cpu().numpy()
+    del A
+    torch.cuda.empty_cache()
+    scale = w.m / ORACLE_SAMPLE_ROWS
+    for _ in range(args.warmup):
+        oracle_sample_seconds(sample, w)
+    times = [oracle_sample_seconds(sample, w) for _ in range(args.steps)]
+    t_step = sum(times) / len(times) * scale
+    value = 1.0 / t_step
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": w.m, "n": w.n, "k": w.k, "p": w.p, "q": w.q, "tile": w.tile},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {ORACLE_SAMPLE_ROWS} of {w.m} rows, full n, k, p, q; "
+                                   f"time scaled by m/{ORACLE_SAMPLE_ROWS} = {scale:g}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import paper_1907_06470_gb300 as g
+    g.load()
+
+    w, A = _build_A(device)
+    m, n, k, p, q = w.m, w.n, w.k, w.p, w.q
+    prec = args.prec
+
+    plan = g.Plan(m, n, k, p, q, w.seed, prec=prec, mb=w.tile, nb=w.tile)
+    plan.set_profiling(True)
+    U = torch.empty(m, k, device=device)
+    S = torch.empty(k, device=device)
+    V = torch.empty(n, k, device=device)
+    for _ in range(args.warmup):
+        plan.run(A, U, S, V)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    stage_sum = {}
+    sampler = ClockSampler(local)
+    sampler.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = g.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.run(A, U, S, V)
+        for key, val in plan.stage_ms().items():
+            stage_sum[key] = stage_sum.get(key, 0.0) + val
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    launches = g.kernel_launches() - launches0
+    clocks = sampler.stop()
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = ws * args.steps / (elapsed_ms / 1e3)
+    S_head = S.double().cpu().numpy()
+
+    # --- roofline of the dominant kernel: the A-pass ---------------------------
+    peaks, peak_kind = _peaks()
+    apass_calls = stage_sum.get("apass_calls", 0)
+    apass_ms = stage_sum.get("apass_fwd", 0.0) + stage_sum.get("apass_trans", 0.0)
+    avg_apass_s = apass_ms / max(apass_calls, 1) / 1e3
+    bytes_per_pass = m * n * 4 + (m + n) * (k + p) * 4
+    flops_per_pass = 2.0 * m * n * (k + p)
+    if prec == "fp32":
+        achieved = flops_per_pass / avg_apass_s / 1e12
+        peak = _fp32_peak_tflops(clocks["sm_mhz"] or 2070.0)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load",
+                "traffic": _traffic_for("simt_gemm_kernel"), "kernel": "simt_gemm_kernel (A-pass)"}
+    else:
+        achieved = bytes_per_pass / avg_apass_s / 1e9
+        peak = float(peaks["hbm_gbs"])
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"hbm_gbs ({peak_kind})",
+                "traffic": _traffic_for("tc_apass_kernel"), "kernel": "tc_apass_kernel (A-pass)",
+                "tflops": flops_per_pass / avg_apass_s / 1e12}
+    roof["algorithmic_bytes_per_launch"] = bytes_per_pass
+    roof["avg_launch_ms"] = avg_apass_s * 1e3
+
+    # --- plain FP32 path for comparison (not part of the timed region) ----------
+    extra = {}
+    if prec != "fp32" and not args.no_compare:
+        p32 = g.Plan(m, n, k, p, q, w.seed, prec="fp32", mb=w.tile, nb=w.tile)
+        U2, S2, V2 = p32.run(A)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(2):
+            p32.run(A, U2, S2, V2)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = f0.elapsed_time(f1) / 2
+        S32 = S2.double().cpu().numpy()
+        extra["fp32_path"] = {"ms_per_step": ms32, "speedup_of_headline": ms32 / ms_per_step,
+                              "sigma_rel_diff_headline_vs_fp32": float(np.max(np.abs(S_head - S32) / S32))}
+        p32.close()
+        del U2, V2
+
+    # --- end to end through the public API with host buffers ----------------------
+    e2e = None
+    if not args.no_e2e:
+        A_host = torch.empty(m, n, dtype=torch.float32, pin_memory=True)
+        A_host.copy_(A)
+        Uh = torch.empty(m, k, pin_memory=True)
+        Sh = torch.empty(k, pin_memory=True)
+        Vh = torch.empty(n, k, pin_memory=True)
+        plan_h = g.Plan(m, n, k, p, q, w.seed, prec=prec, mb=w.tile, nb=w.tile)
+        del A
+        torch.cuda.empty_cache()
+        Ud, Sd, Vd = plan_h.run(A_host)
+        torch.cuda.synchronize()
+        steps_e2e = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(steps_e2e):
+            plan_h.run(A_host, Ud, Sd, Vd)
+            Uh.copy_(Ud, non_blocking=True)
+            Sh.copy_(Sd, non_blocking=True)
+            Vh.copy_(Vd, non_blocking=True)
+            torch.cuda.synchronize()
+        t_e2e = (time.perf_counter() - t0) / steps_e2e
+        e2e = {"value": ws / t_e2e, "unit": UNIT, "h2d_bytes_per_step": m * n * 4,
+               "d2h_bytes_per_step": (m * k + k + n * k) * 4, "ms_per_step": t_e2e * 1e3}
+        plan_h.close()
+        del A_host
+
+    # --- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) -----------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        # rebuild only the sample rows' source: A was freed for the e2e copy
+        _, A2 = _build_A(device)
+        sample = A2[:ORACLE_SAMPLE_ROWS].cpu().numpy()
+        del A2
+        t = oracle_sample_seconds(sample, w) * (m / ORACLE_SAMPLE_ROWS)
+        cpu = {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"first {ORACLE_SAMPLE_ROWS} of {m} rows, full n={n}, k, p, q; time x {m / ORACLE_SAMPLE_ROWS:g}"}
+
+    if rank == 0:
+        stages = {kk: vv / args.steps for kk, vv in stage_sum.items() if kk != "apass_calls"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"bf16": "bf16", "bf16x3": "bf16x3",
+                                                                  "fp32": "f32"}[prec],
+            "data": "synthetic: A = U diag(s) V^T, U and V from QR of seeded Gaussians, s_i = |1/i + 1e-4 g_i|",
+            "config": {"workload": WORKLOAD, "m": m, "n": n, "k": k, "p": p, "q": q, "tile": w.tile,
+                       "prec": prec, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (A is 8 GB)"},
+            "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
+            "cpu_baseline": cpu, "stages_ms_per_step": stages,
+            "apass_calls_per_step": apass_calls / args.steps,
+        }
+        line.update(extra)
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["bf16", "fp32", "bf16x3"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,237 @@
+/*
+ * rsvd.h - C ABI of the GB300 randomized-SVD library (librsvd_gb300.so).
+ *
+ * The library computes the rank-k randomized SVD of Halko, Martinsson & Tropp
+ * as described in Demchik, Bacak, Bordag, "Out-of-core singular value
+ * decomposition" (arXiv:1907.06470), Section 2.1 (steps 1-7) with the power
+ * scheme of Section 2.2 (Eq. (2), evaluated right to left as in Eq. (3)),
+ * over the block-wise / block-cyclic matrix partition of Section 2.3 and
+ * Section 3.1.  Every step runs in CUDA kernels on one GB300 (sm_103a).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an rsvd_status; nothing aborts and nothing prints.
+ *     rsvd_last_error() returns a per-thread text detail of the last failure.
+ *   - Matrices are row-major.  "device" pointers are CUDA global memory of the
+ *     current device; "host" pointers are ordinary (preferably pinned) memory.
+ *   - The caller owns every buffer it passes; the library never frees them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that return a device status (rsvd_run, rsvd_orth, rsvd_small_svd,
+ *     rsvd_full) synchronise `stream` once before returning; the others only
+ *     enqueue work.
+ */
+#ifndef RSVD_GB300_H
+#define RSVD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RSVD_OK = 0,
+  RSVD_ERR_INVALID_ARG = 1,   /* an argument breaks a documented rule */
+  RSVD_ERR_OOM = 2,           /* cudaMalloc / host allocation failed */
+  RSVD_ERR_CAP_TOO_SMALL = 3, /* mem_cap below the planner's minimum */
+  RSVD_ERR_CUDA = 4,          /* a CUDA runtime/driver call failed */
+  RSVD_ERR_NOT_SPD = 5,       /* Cholesky breakdown: Gram matrix not positive definite */
+  RSVD_ERR_NO_CONVERGE = 6,   /* Jacobi sweep limit reached */
+  RSVD_ERR_TIMEOUT = 7,       /* a device-side wait exceeded its spin limit */
+  RSVD_ERR_UNSUPPORTED = 8    /* valid request this build does not implement */
+} rsvd_status;
+
+/* Arithmetic of the A-passes (the products with A of Section 2.1 steps 2 and 5
+ * and of Eq. (3)).  FP64: everything FP64.  FP32: FP32 FMA products.  BF16:
+ * A and the panel rounded to bfloat16, products on the tensor cores with FP32
+ * accumulation; the final pass B^T = A^T Q is recomputed in split-BF16
+ * (hi+lo, three products, about FP32 accuracy) when opts.refine != 0.
+ * BF16X3: every A-pass in split-BF16. */
+typedef enum {
+  RSVD_PREC_FP64 = 0,
+  RSVD_PREC_FP32 = 1,
+  RSVD_PREC_BF16 = 2,
+  RSVD_PREC_BF16X3 = 3
+} rsvd_prec;
+
+typedef enum { RSVD_F64 = 0, RSVD_F32 = 1, RSVD_BF16 = 2 } rsvd_dtype;
+typedef enum { RSVD_DENSE = 0, RSVD_CSR = 1 } rsvd_kind;
+typedef enum { RSVD_ON_DEVICE = 0, RSVD_ON_HOST = 1 } rsvd_location;
+
+/* Options of rsvd_plan; a NULL pointer selects the defaults given here. */
+typedef struct {
+  int32_t prec;      /* rsvd_prec; default FP64 for FP64 plans, FP32 otherwise */
+  int32_t refine;    /* BF16 only: split-BF16 recompute of B^T (default 1) */
+  int64_t mb, nb;    /* block-cyclic tile edges (Section 3.1); 0 = planner choice */
+  int32_t n_slots;   /* block-cyclic slots = copy/compute buffer pairs (default 2) */
+  int32_t dtype;     /* rsvd_dtype of A and of the outputs: F64 or F32 (default F32) */
+} rsvd_opts;
+
+/* Descriptor of the input matrix A (m x n). */
+typedef struct {
+  int32_t kind;      /* rsvd_kind: DENSE row-major, or CSR */
+  int32_t dtype;     /* rsvd_dtype of the values: F64 or F32 (CSR: F32) */
+  int32_t location;  /* rsvd_location of the data */
+  int32_t reserved;
+  int64_t m, n;
+  const void* data;  /* DENSE: element (i,j) at data[i*ld + j] */
+  int64_t ld;        /* DENSE: leading dimension in elements, >= n */
+  const int32_t* rowptr;  /* CSR: m+1 offsets */
+  const int32_t* colidx;  /* CSR: nnz column indices, ascending inside each row */
+  const float* val;       /* CSR: nnz values */
+  int64_t nnz;
+} rsvd_matrix;
+
+/* One tile of the block-cyclic map (Section 3.1): rows [row0,row1) x cols [col0,col1). */
+typedef struct {
+  int64_t t, I, J, row0, row1, col0, col1, slot;
+} rsvd_tile;
+
+typedef struct rsvd_plan_s* rsvd_plan_t;
+
+/* Planner summary, filled by rsvd_plan_info. */
+typedef struct {
+  int64_t m, n;
+  int32_t k, p, q, r;        /* r = k + p */
+  int32_t prec, dtype;
+  int64_t mb, nb;            /* tile edges in use */
+  int64_t tiles_m, tiles_n;  /* tile grid */
+  int32_t n_slots;
+  int32_t resident;          /* 1: A is used from device memory during rsvd_run */
+  size_t workspace_bytes;    /* device memory owned by the plan */
+  size_t min_cap_bytes;      /* smallest mem_cap this problem can be planned in */
+  uint64_t seed;
+} rsvd_plan_info_t;
+
+/* ---- Section 2.1 / 2.2: plan and run -------------------------------------- */
+
+/* Plan a rank-k randomized SVD of an m x n matrix with oversampling p
+ * (r = k + p columns in the sketch, Section 2.1 step 1) and q power
+ * iterations (Section 2.2).  `seed` selects the Gaussian stream of the test
+ * matrix (see rsvd_gaussian).  Device workspace is allocated here and owned by
+ * the plan; `mem_cap_bytes` bounds it together with any device copy of A
+ * (0 = no cap: run in core when A fits, the paper's default in Section 3.5).
+ * Rules: 1 <= k, 0 <= p, k + p <= min(m, n), k + p <= 256, 0 <= q <= 64.
+ * Errors: INVALID_ARG, CAP_TOO_SMALL (see rsvd_plan_min_cap), OOM, CUDA.
+ * On success *out receives a plan that must be released with rsvd_destroy. */
+rsvd_status rsvd_plan(int64_t m, int64_t n, int k, int p, int q, uint64_t seed,
+                      size_t mem_cap_bytes, const rsvd_opts* opts, rsvd_plan_t* out);
+
+/* Smallest mem_cap_bytes that rsvd_plan accepts for these arguments (host only). */
+rsvd_status rsvd_plan_min_cap(int64_t m, int64_t n, int k, int p, const rsvd_opts* opts,
+                              size_t* out_bytes);
+
+rsvd_status rsvd_plan_info(rsvd_plan_t plan, rsvd_plan_info_t* out);
+
+/* Run the planned randomized SVD on A (Section 2.1 steps 1-7 with Eq. (3)).
+ * A: dense (device or pinned host) with dtype equal to the plan's dtype.
+ * Outputs (device, plan dtype): U m x k row-major, S k values descending,
+ * V n x k row-major, so that A ~ U diag(S) V^T.  Each pair (u_i, v_i) is signed
+ * so that the largest-magnitude entry of u_i is positive.  Synchronises
+ * `stream`.  Errors: INVALID_ARG (shape/dtype mismatch), NOT_SPD, NO_CONVERGE,
+ * TIMEOUT, CUDA.  The plan stays valid after an error. */
+rsvd_status rsvd_run(rsvd_plan_t plan, const rsvd_matrix* A, void* U, void* S, void* V,
+                     void* stream);
+
+/* Exact thin SVD of a small dense device matrix (Section 3: the library's
+ * non-approximate path), t = min(m, n) <= 256 and m*n <= 2^24: U m x t, S t,
+ * V n x t, same dtype as A, signs as in rsvd_run.  FP64 one-sided Jacobi on
+ * the columns of A (m >= n) or of A^T (m < n).  Allocates and frees its own
+ * device workspace.  Synchronises `stream`. */
+rsvd_status rsvd_full(const rsvd_matrix* A, void* U, void* S, void* V, void* stream);
+
+void rsvd_destroy(rsvd_plan_t plan);
+
+/* ---- Tracing (Section 4.1 stage breakdown) ----------------------------------- */
+
+/* Stages of rsvd_run, after the paper's list of processing stages in
+ * Section 4.1 ("Preparation of O", "O*A^T", "Orthogonalization", "A^T*Q_r",
+ * "SVD0 Preparation" + "SVD0", "Postprocessing") plus the host-to-device copy of a
+ * host-resident A. */
+typedef enum {
+  RSVD_STAGE_GAUSSIAN = 0,    /* test matrix O */
+  RSVD_STAGE_APASS_FWD = 1,   /* products A X */
+  RSVD_STAGE_APASS_TRANS = 2, /* products A^T X, including B^T = A^T Q */
+  RSVD_STAGE_ORTH = 3,        /* CholeskyQR2 of the range-finder panels */
+  RSVD_STAGE_SMALL_SVD = 4,   /* QR of B^T + one-sided Jacobi */
+  RSVD_STAGE_LIFT = 5,        /* U = Q U_B, V = Q_b W, signs */
+  RSVD_STAGE_H2D = 6,         /* copy of a host-resident A */
+  RSVD_STAGE_TOTAL = 7,       /* whole rsvd_run on the device */
+  RSVD_STAGE_COUNT = 8
+} rsvd_stage;
+
+/* Enable (1) or disable (0) stage timing: rsvd_run then records CUDA events
+ * around each stage on its stream.  Host only; cheap when disabled. */
+rsvd_status rsvd_plan_set_profiling(rsvd_plan_t plan, int32_t enable);
+
+/* Times (ms, summed per stage) of the last profiled rsvd_run: `ms` receives
+ * RSVD_STAGE_COUNT values; *apass_calls (may be NULL) the number of A-passes. */
+rsvd_status rsvd_plan_stage_ms(rsvd_plan_t plan, double* ms, int32_t* apass_calls);
+
+/* Number of CUDA kernels this library has launched in this process so far. */
+unsigned long long rsvd_kernel_launches(void);
+
+const char* rsvd_status_str(rsvd_status status);
+const char* rsvd_last_error(void);
+
+/* ---- Individual steps (used by the parity tests) -------------------------- */
+
+/* Section 2.1 step 1: entries of the n x r Gaussian matrix O.  Entry (i, j) is
+ * element e = i*r + j of one stream: Philox4x32-10 (Salmon et al., SC'11) with
+ * key (seed mod 2^32, seed >> 32) and counter (g mod 2^32, g >> 32, 0, 0),
+ * g = e >> 1, gives words x0..x3; N1 = ((x0<<32)|x1) >> 11, N2 = ((x2<<32)|x3) >> 11;
+ * u1 = (N1+1)*2^-53; theta = 2 pi (2 N2 + 1) 2^-54; the value is
+ * sqrt(-2 ln u1) * (e even ? cos theta : sin theta), computed in FP64 with
+ * the library's own ln/sin/cos and rounded once (nearest-even) to out_dtype.
+ * layout 0: out[i*ld + j] (ld >= r); layout 1 (transposed): out[j*ld + i]
+ * (ld >= n).  out_dtype: F64, F32 or BF16.  Device output; enqueues only. */
+rsvd_status rsvd_gaussian(uint64_t seed, int64_t n, int64_t r, int32_t out_dtype,
+                          int32_t layout, void* out, int64_t ld, void* stream);
+
+/* Block-cyclic tile map of Section 3.1 (host only): tile t = I*Tn + J covers
+ * rows [I*mb, min(m,(I+1)*mb)) x cols [J*nb, min(n,(J+1)*nb)) and goes to slot
+ * t mod n_slots.  Writes at most `cap` tiles to `out` (may be NULL when cap is
+ * 0) and the total count to *count. */
+rsvd_status rsvd_tile_map(int64_t m, int64_t n, int64_t mb, int64_t nb, int32_t n_slots,
+                          rsvd_tile* out, int64_t cap, int64_t* count);
+
+/* One A-pass (Section 2.1 steps 2 and 5, Eq. (3)): Y = A X (trans = 0) or
+ * Y = A^T X (trans = 1), block-wise over the tile grid (mb, nb) of Section 2.3,
+ * with the partial products of each tile row/column added in a fixed order.
+ * A: dense device matrix (F64 or F32).  X: K x r row-major of A's dtype (K = n
+ * for trans = 0, m for trans = 1), leading dimension ldx.  Y: M x r row-major
+ * of A's dtype, leading dimension ldy.  prec: FP64 (A F64), FP32, BF16 or
+ * BF16X3 (A F32).  r <= 256.  Needs `ws_bytes` >= rsvd_apass_workspace(...).
+ * Enqueues only. */
+size_t rsvd_apass_workspace(int64_t m, int64_t n, int32_t r, int32_t trans, int32_t prec,
+                            int64_t mb, int64_t nb);
+rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_t r,
+                       const void* X, int64_t ldx, void* Y, int64_t ldy, int64_t mb, int64_t nb,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* Section 2.1 steps 3-4: orthonormal basis of the columns of a device panel
+ * Y (M x r row-major, F64 or F32, leading dimension ldy) by CholeskyQR2:
+ * G = Y^T Y accumulated in FP64, G = R1^T R1 (FP64 Cholesky), Q1 = Y R1^-1,
+ * repeated once on Q1.  Writes Q (M x r, same dtype, leading dimension ldq, may
+ * not alias Y) and, when R is not NULL, the FP64 upper-triangular r x r factor
+ * R = R2 R1 (row-major) with Y = Q R.  r <= 256, M >= r.  Needs `ws_bytes` >=
+ * rsvd_orth_workspace(M, r).  Errors: NOT_SPD.  Synchronises `stream`. */
+size_t rsvd_orth_workspace(int64_t M, int32_t r);
+rsvd_status rsvd_orth(int32_t dtype, int64_t M, int32_t r, const void* Y, int64_t ldy,
+                      void* Q, int64_t ldq, double* R, void* ws, size_t ws_bytes, void* stream);
+
+/* Section 2.1 step 6 core: one-sided Jacobi SVD (Hestenes; stopping test of
+ * Demmel & Veselic) of a device FP64 square matrix, given column-major as Mc
+ * (column c at Mc + c*r, r <= 256): Mc W = U diag(sigma).  Outputs (device,
+ * FP64): sigma (r, descending), U and W as r x r row-major with the columns
+ * ordered like sigma.  Needs `ws_bytes` >= rsvd_small_svd_workspace(r).
+ * Errors: NO_CONVERGE, TIMEOUT.  Synchronises `stream`. */
+size_t rsvd_small_svd_workspace(int32_t r);
+rsvd_status rsvd_small_svd(int32_t r, const double* Mc, double* sigma, double* U, double* W,
+                           void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSVD_GB300_H */

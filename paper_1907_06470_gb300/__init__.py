@@ -1,0 +1,232 @@
+"""GB300-native randomized SVD (Demchik, Bacak, Bordag, arXiv:1907.06470).
+
+Thin PyTorch binding over librsvd_gb300.so: torch provides device memory and
+the current stream; every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library cannot be built or loaded
+on a GPU machine, these functions raise.
+
+Main entry points
+-----------------
+rsvd(A, k, p, q, seed, ...)   rank-k randomized SVD (Section 2.1, Section 2.2)
+Plan                          reusable plan + workspace for repeated runs
+full_svd(A)                   exact SVD of a small matrix
+gaussian / tile_map / apass / orth / small_svd
+                              the individual steps (Section 2.1 steps 1-6,
+                              Section 3.1 tile map)
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _lib
+from ._lib import RsvdError, load  # noqa: F401
+
+__all__ = ["rsvd", "Plan", "full_svd", "gaussian", "tile_map", "apass", "orth", "small_svd",
+           "RsvdError", "load"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr():
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return _lib.DTYPE["f64"]
+    if t.dtype == torch.float32:
+        return _lib.DTYPE["f32"]
+    raise TypeError(f"A must be float32 or float64, got {t.dtype}")
+
+
+def _dense_desc(A) -> _lib.RsvdMatrix:
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a 2-D tensor with unit column stride (row-major)")
+    d = _lib.RsvdMatrix()
+    d.kind = _lib.DENSE
+    d.dtype = _dtype_code(A)
+    d.location = _lib.ON_DEVICE if A.is_cuda else _lib.ON_HOST
+    d.m, d.n = A.shape
+    d.data = A.data_ptr()
+    d.ld = A.stride(0)
+    return d
+
+
+def _check(st):
+    _lib.check(st)
+
+
+class Plan:
+    """A planned rank-k randomized SVD (rsvd_plan); owns its device workspace."""
+
+    def __init__(self, m, n, k, p=10, q=2, seed=0, mem_cap=0, prec=None, dtype="f32",
+                 mb=0, nb=0, refine=True, n_slots=2):
+        lib = load()
+        if prec is None:
+            prec = "fp64" if dtype == "f64" else "fp32"
+        o = _lib.RsvdOpts()
+        o.prec = _lib.PREC[prec]
+        o.refine = 1 if refine else 0
+        o.mb, o.nb = mb, nb
+        o.n_slots = n_slots
+        o.dtype = _lib.DTYPE[dtype]
+        h = C.c_void_p()
+        _check(lib.rsvd_plan(m, n, k, p, q, seed, mem_cap, C.byref(o), C.byref(h)))
+        self._h = h
+        self.m, self.n, self.k, self.p, self.q, self.seed = m, n, k, p, q, seed
+        self.dtype = dtype
+        self.prec = prec
+
+    def info(self) -> dict:
+        i = _lib.RsvdPlanInfo()
+        _check(load().rsvd_plan_info(self._h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def run(self, A, U=None, S=None, V=None):
+        """Factor A (device tensor, or pinned host tensor); returns (U, S, V) on the device."""
+        torch = _torch()
+        tdt = torch.float64 if self.dtype == "f64" else torch.float32
+        dev = A.device if A.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        if U is None:
+            U = torch.empty(self.m, self.k, dtype=tdt, device=dev)
+        if S is None:
+            S = torch.empty(self.k, dtype=tdt, device=dev)
+        if V is None:
+            V = torch.empty(self.n, self.k, dtype=tdt, device=dev)
+        d = _dense_desc(A)
+        _check(load().rsvd_run(self._h, C.byref(d), C.c_void_p(U.data_ptr()), C.c_void_p(S.data_ptr()),
+                               C.c_void_p(V.data_ptr()), _stream_ptr()))
+        return U, S, V
+
+    def set_profiling(self, on=True):
+        _check(load().rsvd_plan_set_profiling(self._h, 1 if on else 0))
+
+    def stage_ms(self) -> dict:
+        """Per-stage device times (ms) of the last profiled run, plus the A-pass count."""
+        arr = (C.c_double * len(_lib.STAGES))()
+        calls = C.c_int32()
+        _check(load().rsvd_plan_stage_ms(self._h, arr, C.byref(calls)))
+        out = {name: arr[i] for i, name in enumerate(_lib.STAGES)}
+        out["apass_calls"] = calls.value
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rsvd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rsvd(A, k, p=10, q=2, seed=0, mem_cap=0, prec=None, mb=0, nb=0, refine=True):
+    """Rank-k randomized SVD of a dense float32/float64 matrix (CUDA or pinned host tensor)."""
+    torch = _torch()
+    dtype = "f64" if A.dtype == torch.float64 else "f32"
+    plan = Plan(A.shape[0], A.shape[1], k, p, q, seed, mem_cap, prec, dtype, mb, nb, refine)
+    try:
+        return plan.run(A)
+    finally:
+        plan.close()
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(load().rsvd_kernel_launches())
+
+
+def full_svd(A):
+    """Exact thin SVD (U, S, V) of a small dense CUDA matrix, min(m, n) <= 256."""
+    torch = _torch()
+    m, n = A.shape
+    t = min(m, n)
+    U = torch.empty(m, t, dtype=A.dtype, device=A.device)
+    S = torch.empty(t, dtype=A.dtype, device=A.device)
+    V = torch.empty(n, t, dtype=A.dtype, device=A.device)
+    d = _dense_desc(A)
+    _check(load().rsvd_full(C.byref(d), C.c_void_p(U.data_ptr()), C.c_void_p(S.data_ptr()),
+                            C.c_void_p(V.data_ptr()), _stream_ptr()))
+    return U, S, V
+
+
+def gaussian(n, r, seed, dtype="f32", layout=0, out=None, device="cuda"):
+    """The n x r Gaussian test matrix (layout 0) or its transpose (layout 1)."""
+    torch = _torch()
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    if out is None:
+        out = torch.empty((n, r) if layout == 0 else (r, n), dtype=tdt, device=device)
+    ld = out.stride(0)
+    _check(load().rsvd_gaussian(seed, n, r, _lib.DTYPE[dtype], layout, C.c_void_p(out.data_ptr()), ld,
+                                _stream_ptr()))
+    return out
+
+
+def tile_map(m, n, mb, nb, n_slots=2):
+    """Block-cyclic tile map as a list of (t, I, J, row0, row1, col0, col1, slot)."""
+    lib = load()
+    cnt = C.c_int64()
+    _check(lib.rsvd_tile_map(m, n, mb, nb, n_slots, None, 0, C.byref(cnt)))
+    arr = (_lib.RsvdTile * max(cnt.value, 1))()
+    _check(lib.rsvd_tile_map(m, n, mb, nb, n_slots, arr, cnt.value, C.byref(cnt)))
+    return [(x.t, x.I, x.J, x.row0, x.row1, x.col0, x.col1, x.slot) for x in arr[:cnt.value]]
+
+
+def apass(A, X, trans=False, prec=None, mb=0, nb=0, out=None):
+    """One A-pass: A @ X (trans=False) or A.T @ X (trans=True), on the library's kernels."""
+    torch = _torch()
+    if prec is None:
+        prec = "fp64" if A.dtype == torch.float64 else "fp32"
+    m, n = A.shape
+    r = X.shape[1]
+    M = n if trans else m
+    if out is None:
+        out = torch.empty(M, r, dtype=A.dtype, device=A.device)
+    lib = load()
+    wsb = lib.rsvd_apass_workspace(m, n, r, int(trans), _lib.PREC[prec], mb, nb)
+    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=A.device)
+    d = _dense_desc(A)
+    _check(lib.rsvd_apass(C.byref(d), int(trans), _lib.PREC[prec], r, C.c_void_p(X.data_ptr()), X.stride(0),
+                          C.c_void_p(out.data_ptr()), out.stride(0), mb, nb, C.c_void_p(ws.data_ptr()), wsb,
+                          _stream_ptr()))
+    return out
+
+
+def orth(Y, want_R=False):
+    """CholeskyQR2 of a device panel: returns Q (and the FP64 factor R when asked)."""
+    torch = _torch()
+    M, r = Y.shape
+    Q = torch.empty_like(Y)
+    R = torch.empty(r, r, dtype=torch.float64, device=Y.device) if want_R else None
+    lib = load()
+    wsb = lib.rsvd_orth_workspace(M, r)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=Y.device)
+    _check(lib.rsvd_orth(_dtype_code(Y), M, r, C.c_void_p(Y.data_ptr()), Y.stride(0), C.c_void_p(Q.data_ptr()),
+                         Q.stride(0), C.c_void_p(R.data_ptr() if R is not None else None),
+                         C.c_void_p(ws.data_ptr()), wsb, _stream_ptr()))
+    return (Q, R) if want_R else Q
+
+
+def small_svd(Mc):
+    """One-sided Jacobi SVD of a square FP64 device matrix given column-major (i.e. pass M^T row-major)."""
+    torch = _torch()
+    r = Mc.shape[0]
+    sigma = torch.empty(r, dtype=torch.float64, device=Mc.device)
+    U = torch.empty(r, r, dtype=torch.float64, device=Mc.device)
+    W = torch.empty(r, r, dtype=torch.float64, device=Mc.device)
+    lib = load()
+    wsb = lib.rsvd_small_svd_workspace(r)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=Mc.device)
+    Mc = Mc.contiguous()
+    _check(lib.rsvd_small_svd(r, C.c_void_p(Mc.data_ptr()), C.c_void_p(sigma.data_ptr()),
+                              C.c_void_p(U.data_ptr()), C.c_void_p(W.data_ptr()), C.c_void_p(ws.data_ptr()),
+                              wsb, _stream_ptr()))
+    return sigma, U, W

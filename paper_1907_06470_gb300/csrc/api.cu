@@ -1,0 +1,601 @@
+// C ABI: planner (Section 3.4 / 3.5), the randomized SVD driver (Section 2.1
+// steps 1-7 with the power scheme of Section 2.2), the exact small SVD, and
+// the per-step entry points.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rsvd {
+
+// ---- errors -------------------------------------------------------------------
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
+}
+
+cudaError_t after_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+rsvd_status fail(rsvd_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+rsvd_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+  return e == cudaErrorMemoryAllocation ? RSVD_ERR_OOM : RSVD_ERR_CUDA;
+}
+
+rsvd_status status_from_device(int code) {
+  switch (code) {
+    case DEV_OK: return RSVD_OK;
+    case DEV_NOT_SPD: return fail(RSVD_ERR_NOT_SPD, "Cholesky breakdown: Gram matrix not positive definite");
+    case DEV_NO_CONVERGE: return fail(RSVD_ERR_NO_CONVERGE, "one-sided Jacobi reached its sweep limit");
+    case DEV_TIMEOUT: return fail(RSVD_ERR_TIMEOUT, "a device-side wait exceeded its spin limit");
+    default: return fail(RSVD_ERR_INVALID_ARG, "device reported an invalid argument");
+  }
+}
+
+rsvd_status read_device_status(const int* d_status, cudaStream_t stream) {
+  int h = 0;
+  RSVD_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  RSVD_CUDA(cudaStreamSynchronize(stream));
+  return status_from_device(h);
+}
+
+// ---- A-pass dispatch -----------------------------------------------------------
+
+namespace {
+
+// Chunking of the reduction dimension follows the tile map: the forward pass
+// (K = n) is split at tile columns, the transposed pass (K = m) at tile rows.
+struct PassShape {
+  int64_t M, K, kchunk;
+  int nsplit;
+};
+
+PassShape pass_shape(int64_t m, int64_t n, int trans, int64_t mb, int64_t nb) {
+  PassShape s;
+  s.M = trans ? n : m;
+  s.K = trans ? m : n;
+  s.kchunk = trans ? mb : nb;
+  if (s.kchunk <= 0 || s.kchunk > s.K) s.kchunk = s.K;
+  s.kchunk = round_up(s.kchunk, 8);
+  s.nsplit = (int)cdiv(s.K, s.kchunk);
+  if (s.nsplit < 1) s.nsplit = 1;
+  return s;
+}
+
+size_t elem_size(int dtype) { return dtype == RSVD_F64 ? 8 : (dtype == RSVD_BF16 ? 2 : 4); }
+
+}  // namespace
+
+size_t apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t mb, int64_t nb) {
+  const PassShape s = pass_shape(m, n, trans, mb, nb);
+  const size_t esz = prec == RSVD_PREC_FP64 ? 8 : 4;
+  if (prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3)
+    return tc_apass_ws_bytes(m, n, r, trans, prec, mb, nb);
+  return s.nsplit > 1 ? (size_t)s.nsplit * s.M * r * esz + 256 : 256;
+}
+
+rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const void* X, int64_t ldx,
+                        void* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws, size_t ws_bytes,
+                        cudaStream_t stream) {
+  if (A.kind != RSVD_DENSE || A.location != RSVD_ON_DEVICE)
+    return fail(RSVD_ERR_INVALID_ARG, "apass: A must be a dense device matrix");
+  if (ws_bytes < apass_ws_bytes(A.m, A.n, r, trans, prec, mb, nb))
+    return fail(RSVD_ERR_INVALID_ARG, "apass: workspace too small");
+  const PassShape s = pass_shape(A.m, A.n, trans, mb, nb);
+  if (prec == RSVD_PREC_FP64) {
+    if (A.dtype != RSVD_F64) return fail(RSVD_ERR_INVALID_ARG, "apass: FP64 precision needs FP64 A");
+    return simt_gemm<double>(s.M, r, s.K, static_cast<const double*>(A.data), A.ld, trans != 0,
+                             static_cast<const double*>(X), ldx, static_cast<double*>(Y), ldy, false,
+                             s.nsplit, s.kchunk, static_cast<double*>(ws), stream);
+  }
+  if (A.dtype != RSVD_F32) return fail(RSVD_ERR_INVALID_ARG, "apass: FP32/BF16 precision needs FP32 A");
+  if (prec == RSVD_PREC_FP32) {
+    return simt_gemm<float>(s.M, r, s.K, static_cast<const float*>(A.data), A.ld, trans != 0,
+                            static_cast<const float*>(X), ldx, static_cast<float*>(Y), ldy, false,
+                            s.nsplit, s.kchunk, static_cast<float*>(ws), stream);
+  }
+  return tc_apass_from_f32(A, trans, prec, r, static_cast<const float*>(X), ldx,
+                           static_cast<float*>(Y), ldy, mb, nb, ws, ws_bytes, stream);
+}
+
+}  // namespace rsvd
+
+using namespace rsvd;
+
+// ---- plan -----------------------------------------------------------------------
+
+namespace {
+
+// CUDA-event spans around the stages of one rsvd_run.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<std::pair<int, int>> spans;  // (stage, index of the start event)
+  size_t used = 0;
+  double ms[RSVD_STAGE_COUNT] = {};
+  int apass_calls = 0;
+
+  rsvd_status reserve(size_t pairs) {
+    while (ev.size() < 2 * pairs) {
+      cudaEvent_t e;
+      RSVD_CUDA(cudaEventCreate(&e));
+      ev.push_back(e);
+    }
+    return RSVD_OK;
+  }
+  void begin() { used = 0; spans.clear(); apass_calls = 0; }
+  int start(int stage, cudaStream_t s) {
+    if (!on || used + 2 > ev.size()) return -1;
+    cudaEventRecord(ev[used], s);
+    spans.push_back({stage, (int)used});
+    used += 2;
+    return (int)used - 2;
+  }
+  void stop(int idx, cudaStream_t s) {
+    if (idx >= 0) cudaEventRecord(ev[idx + 1], s);
+  }
+  void collect() {
+    for (double& x : ms) x = 0.0;
+    for (auto& sp : spans) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[sp.second], ev[sp.second + 1]) == cudaSuccess) ms[sp.first] += t;
+    }
+  }
+  ~Profiler() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+struct Span {
+  Profiler& p;
+  cudaStream_t s;
+  int idx;
+  Span(Profiler& p_, int stage, cudaStream_t s_) : p(p_), s(s_), idx(p_.start(stage, s_)) {}
+  ~Span() { p.stop(idx, s); }
+};
+
+}  // namespace
+
+struct rsvd_plan_s {
+  int64_t m = 0, n = 0;
+  int k = 0, p = 0, q = 0, r = 0, ldr = 0;
+  uint64_t seed = 0;
+  int prec = RSVD_PREC_FP32, dtype = RSVD_F32, refine = 1, n_slots = 2;
+  int64_t mb = 0, nb = 0;
+  size_t mem_cap = 0, ws_bytes = 0, a_copy_bytes = 0;
+  void* ws = nullptr;
+  // carved device buffers
+  void* X = nullptr;    // n x ldr  (test matrix / Z panel)
+  void* Y = nullptr;    // m x ldr
+  void* Qm = nullptr;   // m x ldr
+  void* Bt = nullptr;   // n x ldr
+  void* Qb = nullptr;   // n x ldr
+  void* apass_ws = nullptr;
+  size_t apass_ws_bytes = 0;
+  OrthWs orth;
+  JacobiWs jac;
+  double* R = nullptr;      // r x r
+  double* sigma = nullptr;  // r
+  double* UR = nullptr;     // r x r
+  double* WR = nullptr;     // r x r
+  void* URk = nullptr;      // r x k in dtype
+  void* WRk = nullptr;      // r x k in dtype
+  void* sign_scratch = nullptr;
+  size_t sign_scratch_bytes = 0;
+  int* status = nullptr;
+  void* Adev = nullptr;     // device copy of a host-resident A
+  Profiler prof;
+};
+
+namespace {
+
+rsvd_status check_args(int64_t m, int64_t n, int k, int p, int q, const rsvd_opts* o) {
+  if (m <= 0 || n <= 0 || k < 1 || p < 0 || q < 0 || q > 64)
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: need m, n >= 1, k >= 1, p >= 0, 0 <= q <= 64");
+  const int64_t r = (int64_t)k + p;
+  if (r > m || r > n) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: k + p must not exceed min(m, n)");
+  if (r > 256) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: k + p must not exceed 256");
+  if (o) {
+    if (o->dtype != RSVD_F32 && o->dtype != RSVD_F64)
+      return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: dtype must be F32 or F64");
+    if (o->prec < RSVD_PREC_FP64 || o->prec > RSVD_PREC_BF16X3)
+      return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: unknown precision");
+    if ((o->prec == RSVD_PREC_FP64) != (o->dtype == RSVD_F64))
+      return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: FP64 precision goes with FP64 data and only with it");
+    if (o->mb < 0 || o->nb < 0 || o->n_slots < 0)
+      return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: negative tile edge or slot count");
+  }
+  return RSVD_OK;
+}
+
+void apply_opts(rsvd_plan_s* P, const rsvd_opts* o) {
+  if (o) {
+    P->dtype = o->dtype;
+    P->prec = o->prec;
+    P->refine = o->refine;
+    P->mb = o->mb;
+    P->nb = o->nb;
+    P->n_slots = o->n_slots > 0 ? o->n_slots : 2;
+  }
+  if (P->mb <= 0) P->mb = P->m;  // in core: one block row unless asked otherwise
+  if (P->nb <= 0) P->nb = P->n;
+  if (P->mb > P->m) P->mb = P->m;
+  if (P->nb > P->n) P->nb = P->n;
+}
+
+// Carve (or, with base == nullptr, size) the plan's workspace.
+size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
+  Carver c(base, base ? cap : ~size_t(0) / 2);
+  const size_t esz = elem_size(P->dtype);
+  const int64_t mx = P->m > P->n ? P->m : P->n;
+  P->X = c.take<char>((size_t)P->n * P->ldr * esz);
+  P->Y = c.take<char>((size_t)P->m * P->ldr * esz);
+  P->Qm = c.take<char>((size_t)P->m * P->ldr * esz);
+  P->Bt = c.take<char>((size_t)P->n * P->ldr * esz);
+  P->Qb = c.take<char>((size_t)P->n * P->ldr * esz);
+  const size_t a0 = apass_ws_bytes(P->m, P->n, P->r, 0, P->prec, P->mb, P->nb);
+  const size_t a1 = apass_ws_bytes(P->m, P->n, P->r, 1, P->prec, P->mb, P->nb);
+  size_t a2 = 0;
+  if (P->prec == RSVD_PREC_BF16 && P->refine)
+    a2 = apass_ws_bytes(P->m, P->n, P->r, 1, RSVD_PREC_BF16X3, P->mb, P->nb);
+  P->apass_ws_bytes = a0 > a1 ? a0 : a1;
+  if (a2 > P->apass_ws_bytes) P->apass_ws_bytes = a2;
+  P->apass_ws = c.take<char>(P->apass_ws_bytes);
+  P->orth = orth_ws_carve(c, mx, P->r, P->dtype);
+  P->jac = jacobi_ws_carve(c, P->r, P->r);
+  P->R = c.take<double>((size_t)P->r * P->r);
+  P->sigma = c.take<double>((size_t)P->r);
+  P->UR = c.take<double>((size_t)P->r * P->r);
+  P->WR = c.take<double>((size_t)P->r * P->r);
+  P->URk = c.take<char>((size_t)P->r * P->k * esz);
+  P->WRk = c.take<char>((size_t)P->r * P->k * esz);
+  P->sign_scratch_bytes = sign_scratch_bytes(P->m, P->k);
+  P->sign_scratch = c.take<char>(P->sign_scratch_bytes);
+  P->status = c.take<int>(4);
+  if (base) {
+    P->orth.status = P->status;
+    P->jac.status = P->status;
+  }
+  return c.used + 256;
+}
+
+template <typename T>
+rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cudaStream_t st) {
+  const int64_t m = P->m, n = P->n;
+  const int r = P->r, k = P->k, ldr = P->ldr;
+  T* X = static_cast<T*>(P->X);
+  T* Y = static_cast<T*>(P->Y);
+  T* Q = static_cast<T*>(P->Qm);
+  T* Bt = static_cast<T*>(P->Bt);
+  T* Qb = static_cast<T*>(P->Qb);
+  const int prec = P->prec;
+  const int final_prec = (prec == RSVD_PREC_BF16 && P->refine) ? RSVD_PREC_BF16X3 : prec;
+  Profiler& pf = P->prof;
+  auto apass = [&](int trans, int pr, const T* Xin, T* Yout) -> rsvd_status {
+    Span sp(pf, trans ? RSVD_STAGE_APASS_TRANS : RSVD_STAGE_APASS_FWD, st);
+    ++pf.apass_calls;
+    return apass_dense(A, trans, pr, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes, st);
+  };
+  auto orth = [&](int64_t M, const T* Yin, T* Qout) -> rsvd_status {
+    Span sp(pf, RSVD_STAGE_ORTH, st);
+    return orth_panel<T>(M, r, Yin, ldr, Qout, ldr, nullptr, P->orth, st);
+  };
+  {
+    Span total(pf, RSVD_STAGE_TOTAL, st);
+    RSVD_CUDA(cudaMemsetAsync(P->status, 0, sizeof(int), st));
+    {  // step 1: Gaussian test matrix (n x r)
+      Span sp(pf, RSVD_STAGE_GAUSSIAN, st);
+      RSVD_TRY(launch_gaussian(P->seed, n, r, P->dtype, 0, X, ldr, st));
+    }
+    // step 2 and steps 3-4: Y = A O, Q = orth(Y)
+    RSVD_TRY(apass(0, prec, X, Y));
+    RSVD_TRY(orth(m, Y, Q));
+    // Eq. (3), right to left: q times Z = orth(A^T Q), Q = orth(A Z)
+    for (int it = 0; it < P->q; ++it) {
+      RSVD_TRY(apass(1, prec, Q, Bt));
+      RSVD_TRY(orth(n, Bt, X));
+      RSVD_TRY(apass(0, prec, X, Y));
+      RSVD_TRY(orth(m, Y, Q));
+    }
+    // step 5: B^T = A^T Q
+    RSVD_TRY(apass(1, final_prec, Q, Bt));
+    {  // step 6: B^T = Q_b R, R^T = U_R diag(sigma) W^T  =>  B = U_R diag(sigma) (Q_b W)^T
+      Span sp(pf, RSVD_STAGE_SMALL_SVD, st);
+      RSVD_TRY(orth_panel<T>(n, r, Bt, ldr, Qb, ldr, P->R, P->orth, st));
+      RSVD_TRY(jacobi_svd(r, r, P->R, P->sigma, P->UR, P->WR, P->jac, st));
+    }
+    {  // step 7: U = Q U_R[:, :k], V = Q_b W[:, :k]
+      Span sp(pf, RSVD_STAGE_LIFT, st);
+      T* URk = static_cast<T*>(P->URk);
+      T* WRk = static_cast<T*>(P->WRk);
+      RSVD_TRY((convert_matrix<double, T>(r, k, P->UR, r, URk, k, st)));
+      RSVD_TRY((convert_matrix<double, T>(r, k, P->WR, r, WRk, k, st)));
+      RSVD_TRY(simt_gemm<T>(m, k, r, Q, ldr, false, URk, k, U, k, false, 1, r, nullptr, st));
+      RSVD_TRY(simt_gemm<T>(n, k, r, Qb, ldr, false, WRk, k, V, k, false, 1, r, nullptr, st));
+      RSVD_TRY((convert_matrix<double, T>(1, k, P->sigma, k, S, k, st)));
+      RSVD_TRY(normalise_signs<T>(m, n, k, U, k, V, k, P->sign_scratch, P->sign_scratch_bytes, st));
+    }
+  }
+  const rsvd_status res = read_device_status(P->status, st);
+  if (pf.on) pf.collect();
+  return res;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rsvd_status_str(rsvd_status s) {
+  switch (s) {
+    case RSVD_OK: return "RSVD_OK";
+    case RSVD_ERR_INVALID_ARG: return "RSVD_ERR_INVALID_ARG";
+    case RSVD_ERR_OOM: return "RSVD_ERR_OOM";
+    case RSVD_ERR_CAP_TOO_SMALL: return "RSVD_ERR_CAP_TOO_SMALL";
+    case RSVD_ERR_CUDA: return "RSVD_ERR_CUDA";
+    case RSVD_ERR_NOT_SPD: return "RSVD_ERR_NOT_SPD";
+    case RSVD_ERR_NO_CONVERGE: return "RSVD_ERR_NO_CONVERGE";
+    case RSVD_ERR_TIMEOUT: return "RSVD_ERR_TIMEOUT";
+    case RSVD_ERR_UNSUPPORTED: return "RSVD_ERR_UNSUPPORTED";
+  }
+  return "RSVD_ERR_UNKNOWN";
+}
+
+const char* rsvd_last_error(void) { return g_last_error.c_str(); }
+
+rsvd_status rsvd_tile_map(int64_t m, int64_t n, int64_t mb, int64_t nb, int32_t n_slots, rsvd_tile* out,
+                          int64_t cap, int64_t* count) {
+  if (m < 0 || n < 0 || mb <= 0 || nb <= 0 || n_slots <= 0 || cap < 0 || !count)
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_tile_map: bad arguments");
+  const int64_t Tm = cdiv(m, mb), Tn = cdiv(n, nb);
+  *count = Tm * Tn;
+  if (cap > 0 && !out) return fail(RSVD_ERR_INVALID_ARG, "rsvd_tile_map: out is NULL");
+  int64_t t = 0;
+  for (int64_t I = 0; I < Tm && t < cap; ++I)
+    for (int64_t J = 0; J < Tn && t < cap; ++J, ++t) {
+      rsvd_tile& x = out[t];
+      x.t = t; x.I = I; x.J = J;
+      x.row0 = I * mb; x.row1 = (I + 1) * mb < m ? (I + 1) * mb : m;
+      x.col0 = J * nb; x.col1 = (J + 1) * nb < n ? (J + 1) * nb : n;
+      x.slot = t % n_slots;
+    }
+  return RSVD_OK;
+}
+
+size_t rsvd_apass_workspace(int64_t m, int64_t n, int32_t r, int32_t trans, int32_t prec, int64_t mb,
+                            int64_t nb) {
+  return apass_ws_bytes(m, n, r, trans, prec, mb, nb);
+}
+
+rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_t r, const void* X,
+                       int64_t ldx, void* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws,
+                       size_t ws_bytes, void* stream) {
+  if (!A || !X || !Y || r < 1 || r > 256 || (trans != 0 && trans != 1) || ldx < r || ldy < r)
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: bad arguments");
+  if (A->kind == RSVD_DENSE && A->ld < A->n) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: ld < n");
+  return apass_dense(*A, trans, prec, r, X, ldx, Y, ldy, mb, nb, ws, ws_bytes, as_stream(stream));
+}
+
+size_t rsvd_orth_workspace(int64_t M, int32_t r) { return orth_ws_bytes(M, r, RSVD_F64) + 1024; }
+
+rsvd_status rsvd_orth(int32_t dtype, int64_t M, int32_t r, const void* Y, int64_t ldy, void* Q,
+                      int64_t ldq, double* R, void* ws, size_t ws_bytes, void* stream) {
+  if (r < 1 || r > 256 || M < r || ldy < r || ldq < r || !Y || !Q || (dtype != RSVD_F32 && dtype != RSVD_F64))
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_orth: bad arguments");
+  if (ws_bytes < rsvd_orth_workspace(M, r)) return fail(RSVD_ERR_INVALID_ARG, "rsvd_orth: workspace too small");
+  Carver c(ws, ws_bytes);
+  OrthWs w = orth_ws_carve(c, M, r, dtype);
+  if (c.overflow) return fail(RSVD_ERR_INVALID_ARG, "rsvd_orth: workspace too small");
+  cudaStream_t st = as_stream(stream);
+  RSVD_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+  if (dtype == RSVD_F64) {
+    RSVD_TRY(orth_panel<double>(M, r, static_cast<const double*>(Y), ldy, static_cast<double*>(Q), ldq, R, w, st));
+  } else {
+    RSVD_TRY(orth_panel<float>(M, r, static_cast<const float*>(Y), ldy, static_cast<float*>(Q), ldq, R, w, st));
+  }
+  return read_device_status(w.status, st);
+}
+
+size_t rsvd_small_svd_workspace(int32_t r) { return jacobi_ws_bytes(r, r) + 512; }
+
+rsvd_status rsvd_small_svd(int32_t r, const double* Mc, double* sigma, double* U, double* W, void* ws,
+                           size_t ws_bytes, void* stream) {
+  if (r < 1 || r > 256 || !Mc || !sigma || !U || !W)
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_small_svd: bad arguments");
+  if (ws_bytes < rsvd_small_svd_workspace(r)) return fail(RSVD_ERR_INVALID_ARG, "rsvd_small_svd: workspace too small");
+  Carver c(ws, ws_bytes);
+  JacobiWs w = jacobi_ws_carve(c, r, r);
+  cudaStream_t st = as_stream(stream);
+  RSVD_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+  RSVD_TRY(jacobi_svd(r, r, Mc, sigma, U, W, w, st));
+  return read_device_status(w.status, st);
+}
+
+rsvd_status rsvd_plan_min_cap(int64_t m, int64_t n, int k, int p, const rsvd_opts* opts, size_t* out_bytes) {
+  RSVD_TRY(check_args(m, n, k, p, 0, opts));
+  if (!out_bytes) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_min_cap: out is NULL");
+  rsvd_plan_s P;
+  P.m = m; P.n = n; P.k = k; P.p = p; P.r = k + p; P.ldr = (int)round_up(P.r, 4);
+  apply_opts(&P, opts);
+  *out_bytes = layout(&P, nullptr, 0);
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_plan(int64_t m, int64_t n, int k, int p, int q, uint64_t seed, size_t mem_cap_bytes,
+                      const rsvd_opts* opts, rsvd_plan_t* out) {
+  if (!out) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: out is NULL");
+  *out = nullptr;
+  RSVD_TRY(check_args(m, n, k, p, q, opts));
+  rsvd_plan_s* P = new (std::nothrow) rsvd_plan_s();
+  if (!P) return fail(RSVD_ERR_OOM, "rsvd_plan: host allocation failed");
+  P->m = m; P->n = n; P->k = k; P->p = p; P->q = q; P->r = k + p; P->seed = seed;
+  P->ldr = (int)round_up(P->r, 4);
+  apply_opts(P, opts);
+  P->mem_cap = mem_cap_bytes;
+  P->ws_bytes = layout(P, nullptr, 0);
+  if (mem_cap_bytes && P->ws_bytes > mem_cap_bytes) {
+    delete P;
+    return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_plan: mem_cap below the workspace this plan needs");
+  }
+  cudaError_t e = cudaMalloc(&P->ws, P->ws_bytes);
+  if (e != cudaSuccess) {
+    delete P;
+    return cuda_fail(e, "rsvd_plan: cudaMalloc(workspace)");
+  }
+  layout(P, P->ws, P->ws_bytes);
+  *out = P;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_info(rsvd_plan_t P, rsvd_plan_info_t* o) {
+  if (!P || !o) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_info: NULL argument");
+  std::memset(o, 0, sizeof(*o));
+  o->m = P->m; o->n = P->n; o->k = P->k; o->p = P->p; o->q = P->q; o->r = P->r;
+  o->prec = P->prec; o->dtype = P->dtype; o->mb = P->mb; o->nb = P->nb;
+  o->tiles_m = cdiv(P->m, P->mb); o->tiles_n = cdiv(P->n, P->nb); o->n_slots = P->n_slots;
+  o->resident = 1; o->workspace_bytes = P->ws_bytes; o->min_cap_bytes = P->ws_bytes; o->seed = P->seed;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void* V, void* stream) {
+  if (!P || !A || !U || !S || !V) return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: NULL argument");
+  if (A->m != P->m || A->n != P->n || A->dtype != P->dtype)
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: A does not match the plan (shape or dtype)");
+  if (A->kind != RSVD_DENSE) return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: CSR input is not available in this build");
+  if (A->ld < A->n || !A->data) return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: bad dense descriptor");
+  cudaStream_t st = as_stream(stream);
+  rsvd_matrix Ad = *A;
+  P->prof.begin();
+  if (A->location == RSVD_ON_HOST) {
+    // Automatic in-core switch (Section 3.5): a host matrix that fits under the
+    // cap is copied to the device once and processed in core.
+    const size_t bytes = (size_t)A->m * A->n * elem_size(A->dtype);
+    if (P->mem_cap && P->ws_bytes + bytes > P->mem_cap)
+      return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: host matrix larger than mem_cap needs streaming");
+    if (P->a_copy_bytes < bytes) {
+      if (P->Adev) cudaFree(P->Adev);
+      P->Adev = nullptr;
+      P->a_copy_bytes = 0;
+      RSVD_CUDA(cudaMalloc(&P->Adev, bytes));
+      P->a_copy_bytes = bytes;
+    }
+    const size_t row = (size_t)A->n * elem_size(A->dtype);
+    Span sp(P->prof, RSVD_STAGE_H2D, st);
+    RSVD_CUDA(cudaMemcpy2DAsync(P->Adev, row, A->data, (size_t)A->ld * elem_size(A->dtype), row, A->m,
+                                cudaMemcpyHostToDevice, st));
+    Ad.data = P->Adev;
+    Ad.ld = A->n;
+    Ad.location = RSVD_ON_DEVICE;
+  }
+  if (P->dtype == RSVD_F64)
+    return run_typed<double>(P, Ad, static_cast<double*>(U), static_cast<double*>(S), static_cast<double*>(V), st);
+  return run_typed<float>(P, Ad, static_cast<float*>(U), static_cast<float*>(S), static_cast<float*>(V), st);
+}
+
+rsvd_status rsvd_plan_set_profiling(rsvd_plan_t P, int32_t enable) {
+  if (!P) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_set_profiling: NULL plan");
+  if (enable) RSVD_TRY(P->prof.reserve(16 + 4 * ((size_t)P->q + 1)));
+  P->prof.on = enable != 0;
+  return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_stage_ms(rsvd_plan_t P, double* ms, int32_t* apass_calls) {
+  if (!P || !ms) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_stage_ms: NULL argument");
+  for (int i = 0; i < RSVD_STAGE_COUNT; ++i) ms[i] = P->prof.ms[i];
+  if (apass_calls) *apass_calls = P->prof.apass_calls;
+  return RSVD_OK;
+}
+
+unsigned long long rsvd_kernel_launches(void) { return g_launches.load(); }
+
+void rsvd_destroy(rsvd_plan_t P) {
+  if (!P) return;
+  if (P->ws) cudaFree(P->ws);
+  if (P->Adev) cudaFree(P->Adev);
+  delete P;
+}
+
+rsvd_status rsvd_full(const rsvd_matrix* A, void* U, void* S, void* V, void* stream) {
+  if (!A || !U || !S || !V || A->kind != RSVD_DENSE || A->location != RSVD_ON_DEVICE || !A->data)
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_full: need a dense device matrix and outputs");
+  const int64_t m = A->m, n = A->n, t = m < n ? m : n;
+  if (m < 1 || n < 1 || t > 256 || A->ld < n || (A->dtype != RSVD_F64 && A->dtype != RSVD_F32))
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_full: need min(m, n) <= 256, ld >= n, F32 or F64");
+  if (m * n > ((int64_t)1 << 24)) return fail(RSVD_ERR_INVALID_ARG, "rsvd_full: more than 2^24 entries");
+  cudaStream_t st = as_stream(stream);
+  // One-sided Jacobi on the columns of A (m >= n) or of A^T (m < n), in FP64.
+  //   m >= n: A W = U diag(s)   -> U = Uo, V = W
+  //   m <  n: A^T W = V diag(s) -> V = Uo, U = W
+  const int64_t rows = m >= n ? m : n, cols = t;
+  const size_t jb = jacobi_ws_bytes(rows, (int)cols);
+  const size_t sb = sign_scratch_bytes(m, (int)t);
+  Sizer sz;
+  sz.take<double>((size_t)rows * cols);
+  sz.take<double>((size_t)cols);
+  sz.take<double>((size_t)rows * cols);
+  sz.take<double>((size_t)cols * cols);
+  sz.take<char>(jb);
+  sz.take<char>(sb);
+  const size_t total = sz.used + 1024;
+  void* ws = nullptr;
+  RSVD_CUDA(cudaMalloc(&ws, total));
+  Carver c(ws, total);
+  double* Mc = c.take<double>((size_t)rows * cols);
+  double* sig = c.take<double>((size_t)cols);
+  double* Uo = c.take<double>((size_t)rows * cols);
+  double* Wo = c.take<double>((size_t)cols * cols);
+  char* jbase = c.take<char>(jb);
+  void* sc = c.take<char>(sb);
+  Carver jc(jbase, jb);
+  JacobiWs jw = jacobi_ws_carve(jc, rows, (int)cols);
+  rsvd_status s = RSVD_OK;
+  const int64_t s_row = m >= n ? A->ld : 1;   // Mc[c*rows + i] = A at i*s_row + c*s_col
+  const int64_t s_col = m >= n ? 1 : A->ld;
+  if (cudaMemsetAsync(jw.status, 0, sizeof(int), st) != cudaSuccess) s = fail(RSVD_ERR_CUDA, "rsvd_full: memset");
+  if (s == RSVD_OK) {
+    s = A->dtype == RSVD_F64
+            ? gather_colmajor_f64<double>(rows, cols, static_cast<const double*>(A->data), s_row, s_col, Mc, st)
+            : gather_colmajor_f64<float>(rows, cols, static_cast<const float*>(A->data), s_row, s_col, Mc, st);
+  }
+  if (s == RSVD_OK) s = jacobi_svd((int)rows, (int)cols, Mc, sig, Uo, Wo, jw, st);
+  const double* Usrc = m >= n ? Uo : Wo;
+  const double* Vsrc = m >= n ? Wo : Uo;
+  if (s == RSVD_OK) {
+    if (A->dtype == RSVD_F64) {
+      double* Ud = static_cast<double*>(U);
+      double* Vd = static_cast<double*>(V);
+      s = convert_matrix<double, double>(m, t, Usrc, t, Ud, t, st);
+      if (s == RSVD_OK) s = convert_matrix<double, double>(n, t, Vsrc, t, Vd, t, st);
+      if (s == RSVD_OK) s = convert_matrix<double, double>(1, t, sig, t, static_cast<double*>(S), t, st);
+      if (s == RSVD_OK) s = normalise_signs<double>(m, n, (int)t, Ud, t, Vd, t, sc, sb, st);
+    } else {
+      float* Uf = static_cast<float*>(U);
+      float* Vf = static_cast<float*>(V);
+      s = convert_matrix<double, float>(m, t, Usrc, t, Uf, t, st);
+      if (s == RSVD_OK) s = convert_matrix<double, float>(n, t, Vsrc, t, Vf, t, st);
+      if (s == RSVD_OK) s = convert_matrix<double, float>(1, t, sig, t, static_cast<float*>(S), t, st);
+      if (s == RSVD_OK) s = normalise_signs<float>(m, n, (int)t, Uf, t, Vf, t, sc, sb, st);
+    }
+  }
+  if (s == RSVD_OK) s = read_device_status(jw.status, st);
+  cudaStreamSynchronize(st);
+  cudaFree(ws);
+  return s;
+}
+
+}  // extern "C"

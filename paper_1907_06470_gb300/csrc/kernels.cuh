@@ -1,0 +1,89 @@
+// Internal launchers shared by the translation units of the library.
+#pragma once
+
+#include "common.cuh"
+
+namespace rsvd {
+
+// gaussian.cu -- Section 2.1 step 1.
+rsvd_status launch_gaussian(uint64_t seed, int64_t n, int64_t r, int dtype, int layout, void* out,
+                            int64_t ld, cudaStream_t stream);
+
+// Replace column k of the M x r panel Q (k with dead[k] != 0) by a random
+// vector of unit expected norm: entries stream(seed, k*M + i) / sqrt(M).
+rsvd_status fill_dead_columns(int64_t M, int r, const int* dead, void* Q, int64_t ldq, int dtype,
+                              uint64_t seed, cudaStream_t stream);
+constexpr uint64_t kDeadFillSeed = 0x6A09E667F3BCC909ULL;
+
+// gemm_simt.cu -- C (+)= op(A) B, K split into nsplit chunks of kchunk with
+// partials (M*N each) in `partial`, added in chunk order.
+template <typename T>
+rsvd_status simt_gemm(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, bool transA,
+                      const T* B, int64_t ldb, T* C, int64_t ldc, bool accumulate, int nsplit,
+                      int64_t kchunk, T* partial, cudaStream_t stream);
+
+// orth.cu -- CholeskyQR2 pieces.
+struct OrthWs {
+  double* G = nullptr;        // r x r Gram (FP64)
+  double* L1 = nullptr;       // r x r Cholesky factors (lower, FP64)
+  double* L2 = nullptr;
+  double* Rinv = nullptr;     // r x r upper inverse (FP64)
+  int* dead1 = nullptr;       // deflated pivots of the two sweeps (r each)
+  int* dead2 = nullptr;
+  void* Rinv_t = nullptr;     // the same in the panel dtype
+  double* gram_partial = nullptr;
+  int64_t gram_chunks = 0;
+  void* tmp = nullptr;        // M x r panel (first-sweep result)
+  int64_t ld_tmp = 0;
+  int* status = nullptr;      // device status word
+};
+size_t orth_ws_bytes(int64_t M, int r, int dtype);
+OrthWs orth_ws_carve(Carver& c, int64_t M, int r, int dtype);
+
+template <typename T>
+rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t ldq, double* R,
+                       const OrthWs& ws, cudaStream_t stream);
+
+// jacobi.cu -- Section 2.1 step 6 core.
+struct JacobiWs {
+  double* M = nullptr;        // rows x r working columns (column-major)
+  double* W = nullptr;        // r x r accumulated rotations (column-major)
+  unsigned* barrier = nullptr;  // grid barrier words (count, generation)
+  int* rotated = nullptr;     // one flag per sweep
+  int* sweeps = nullptr;      // sweeps used
+  int* status = nullptr;
+};
+constexpr int kJacobiMaxSweeps = 64;
+size_t jacobi_ws_bytes(int64_t rows, int r);
+JacobiWs jacobi_ws_carve(Carver& c, int64_t rows, int r);
+// Mc column-major rows x r; outputs sigma (r), U (rows x r) and W (r x r)
+// row-major with columns ordered like sigma (descending).
+rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double* U, double* W,
+                       const JacobiWs& ws, cudaStream_t stream);
+
+// lift.cu -- conversions, sign normalisation.
+template <typename Tin, typename Tout>
+rsvd_status convert_matrix(int64_t rows, int64_t cols, const Tin* in, int64_t ldi, Tout* out,
+                           int64_t ldo, cudaStream_t stream);
+template <typename T>
+rsvd_status normalise_signs(int64_t m, int64_t n, int k, T* U, int64_t ldu, T* V, int64_t ldv,
+                            void* scratch, size_t scratch_bytes, cudaStream_t stream);
+size_t sign_scratch_bytes(int64_t m, int k);
+// out[c*rows + i] = (double) A[i*s_row + c*s_col]  (column-major FP64 gather)
+template <typename T>
+rsvd_status gather_colmajor_f64(int64_t rows, int64_t cols, const T* A, int64_t s_row, int64_t s_col,
+                                double* out, cudaStream_t stream);
+
+// api.cu -- A-pass dispatch.
+size_t apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t mb, int64_t nb);
+rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const void* X, int64_t ldx,
+                        void* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws, size_t ws_bytes,
+                        cudaStream_t stream);
+
+// gemm_tc.cu -- tensor-core (tcgen05) A-passes on FP32 A with in-kernel BF16 conversion.
+size_t tc_apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t mb, int64_t nb);
+rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X,
+                              int64_t ldx, float* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws,
+                              size_t ws_bytes, cudaStream_t stream);
+
+}  // namespace rsvd

@@ -1,0 +1,77 @@
+"""Host-side checks of the C ABI: the library loads, exports every declared
+symbol, and its host-only logic (tile map, argument checks, planner sizes)
+matches the oracle.  No GPU compute is called here."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from oracle import tiles as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    with open(os.path.join(ROOT, "include", "rsvd.h")) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:rsvd_status|size_t|void|const char\*|unsigned long long)\s+(rsvd_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert "rsvd_plan" in names and "rsvd_run" in names and len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header():
+    from paper_1907_06470_gb300 import _lib
+    assert sorted(_lib.SIGNATURES) == _declared_functions()
+
+
+@pytest.mark.parametrize("m,n,mb,nb,S", [(10, 7, 3, 2, 2), (100000, 20000, 4096, 4096, 2),
+                                         (600000, 100000, 8192, 8192, 3), (1, 1, 5, 5, 1), (0, 4, 2, 2, 2)])
+def test_tile_map_is_bit_exact_with_oracle(m, n, mb, nb, S):
+    import paper_1907_06470_gb300 as g
+    assert g.tile_map(m, n, mb, nb, S) == T.tile_map(m, n, mb, nb, S)
+
+
+def test_tile_map_rejects_bad_arguments(lib):
+    cnt = C.c_int64()
+    assert lib.rsvd_tile_map(10, 10, 0, 2, 1, None, 0, C.byref(cnt)) == 1
+    assert lib.rsvd_tile_map(10, 10, 2, 2, 0, None, 0, C.byref(cnt)) == 1
+    assert b"rsvd_tile_map" in lib.rsvd_last_error()
+
+
+def test_plan_argument_rules_checked_before_any_device_call(lib):
+    from paper_1907_06470_gb300 import _lib
+    h = C.c_void_p()
+    # k + p > min(m, n)
+    assert lib.rsvd_plan(100, 20, 15, 10, 2, 1, 0, None, C.byref(h)) == 1
+    # k + p > 256
+    assert lib.rsvd_plan(10000, 10000, 250, 10, 2, 1, 0, None, C.byref(h)) == 1
+    # FP64 precision with FP32 data
+    o = _lib.RsvdOpts(prec=0, refine=1, mb=0, nb=0, n_slots=2, dtype=1)
+    assert lib.rsvd_plan(100, 50, 5, 5, 1, 1, 0, C.byref(o), C.byref(h)) == 1
+    assert h.value is None
+
+
+def test_min_cap_grows_with_the_problem(lib):
+    from paper_1907_06470_gb300 import _lib
+    out = C.c_size_t()
+    o = _lib.RsvdOpts(prec=1, refine=1, mb=4096, nb=4096, n_slots=2, dtype=1)
+    assert lib.rsvd_plan_min_cap(100000, 20000, 100, 20, C.byref(o), C.byref(out)) == 0
+    big = out.value
+    assert lib.rsvd_plan_min_cap(10000, 2000, 100, 20, C.byref(o), C.byref(out)) == 0
+    assert out.value < big
+    # the panels alone: 2 m-panels + 3 n-panels of r=120 FP32 columns
+    assert big >= (2 * 100000 + 3 * 20000) * 120 * 4
+
+
+def test_status_strings(lib):
+    for code, name in {0: b"RSVD_OK", 5: b"RSVD_ERR_NOT_SPD", 7: b"RSVD_ERR_TIMEOUT"}.items():
+        assert lib.rsvd_status_str(code) == name
