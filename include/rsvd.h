@@ -201,8 +201,10 @@ rsvd_status rsvd_tile_map(int64_t m, int64_t n, int64_t mb, int64_t nb, int32_t 
  * A: dense device matrix (F64 or F32).  X: K x r row-major of A's dtype (K = n
  * for trans = 0, m for trans = 1), leading dimension ldx.  Y: M x r row-major
  * of A's dtype, leading dimension ldy.  prec: FP64 (A F64), FP32, BF16 or
- * BF16X3 (A F32).  r <= 256.  Needs `ws_bytes` >= rsvd_apass_workspace(...).
- * Enqueues only. */
+ * BF16X3 (A F32; A 16-byte aligned with ld % 4 == 0; BF16X3 needs r <= 192).
+ * r <= 256.  Needs `ws_bytes` >= rsvd_apass_workspace(...).  FP64/FP32 enqueue
+ * only; BF16/BF16X3 synchronise `stream` and return TIMEOUT if a wait of the
+ * tensor-core pipeline expired. */
 size_t rsvd_apass_workspace(int64_t m, int64_t n, int32_t r, int32_t trans, int32_t prec,
                             int64_t mb, int64_t nb);
 rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_t r,

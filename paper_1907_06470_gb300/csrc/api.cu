@@ -92,7 +92,7 @@ size_t apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t 
 
 rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const void* X, int64_t ldx,
                         void* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws, size_t ws_bytes,
-                        cudaStream_t stream) {
+                        int* status, cudaStream_t stream) {
   if (A.kind != RSVD_DENSE || A.location != RSVD_ON_DEVICE)
     return fail(RSVD_ERR_INVALID_ARG, "apass: A must be a dense device matrix");
   if (ws_bytes < apass_ws_bytes(A.m, A.n, r, trans, prec, mb, nb))
@@ -110,8 +110,10 @@ rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const 
                             static_cast<const float*>(X), ldx, static_cast<float*>(Y), ldy, false,
                             s.nsplit, s.kchunk, static_cast<float*>(ws), stream);
   }
+  if (prec != RSVD_PREC_BF16 && prec != RSVD_PREC_BF16X3)
+    return fail(RSVD_ERR_INVALID_ARG, "apass: unknown precision");
   return tc_apass_from_f32(A, trans, prec, r, static_cast<const float*>(X), ldx,
-                           static_cast<float*>(Y), ldy, mb, nb, ws, ws_bytes, stream);
+                           static_cast<float*>(Y), ldy, mb, nb, ws, ws_bytes, status, stream);
 }
 
 }  // namespace rsvd
@@ -290,7 +292,8 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   auto apass = [&](int trans, int pr, const T* Xin, T* Yout) -> rsvd_status {
     Span sp(pf, trans ? RSVD_STAGE_APASS_TRANS : RSVD_STAGE_APASS_FWD, st);
     ++pf.apass_calls;
-    return apass_dense(A, trans, pr, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes, st);
+    return apass_dense(A, trans, pr, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes,
+                       P->status, st);
   };
   auto orth = [&](int64_t M, const T* Yin, T* Qout) -> rsvd_status {
     Span sp(pf, RSVD_STAGE_ORTH, st);
@@ -301,7 +304,8 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     RSVD_CUDA(cudaMemsetAsync(P->status, 0, sizeof(int), st));
     {  // step 1: Gaussian test matrix (n x r)
       Span sp(pf, RSVD_STAGE_GAUSSIAN, st);
-      RSVD_TRY(launch_gaussian(P->seed, n, r, P->dtype, 0, X, ldr, st));
+      const bool bf16_panel = prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3;
+      RSVD_TRY(launch_gaussian(P->seed, n, r, bf16_panel ? kF32HoldingBf16 : P->dtype, 0, X, ldr, st));
     }
     // step 2 and steps 3-4: Y = A O, Q = orth(Y)
     RSVD_TRY(apass(0, prec, X, Y));
@@ -379,7 +383,7 @@ rsvd_status rsvd_tile_map(int64_t m, int64_t n, int64_t mb, int64_t nb, int32_t 
 
 size_t rsvd_apass_workspace(int64_t m, int64_t n, int32_t r, int32_t trans, int32_t prec, int64_t mb,
                             int64_t nb) {
-  return apass_ws_bytes(m, n, r, trans, prec, mb, nb);
+  return apass_ws_bytes(m, n, r, trans, prec, mb, nb) + 512;
 }
 
 rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_t r, const void* X,
@@ -388,7 +392,18 @@ rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_
   if (!A || !X || !Y || r < 1 || r > 256 || (trans != 0 && trans != 1) || ldx < r || ldy < r)
     return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: bad arguments");
   if (A->kind == RSVD_DENSE && A->ld < A->n) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: ld < n");
-  return apass_dense(*A, trans, prec, r, X, ldx, Y, ldy, mb, nb, ws, ws_bytes, as_stream(stream));
+  if (prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3) {
+    // The tensor-core pipeline reports an expired wait through a device word:
+    // this call synchronises the stream and returns it.
+    const size_t need = apass_ws_bytes(A->m, A->n, r, trans, prec, mb, nb);
+    if (ws_bytes < need + 512) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: workspace too small");
+    int* st_word = reinterpret_cast<int*>(static_cast<char*>(ws) + ((need + 255) & ~size_t(255)));
+    cudaStream_t st = as_stream(stream);
+    RSVD_CUDA(cudaMemsetAsync(st_word, 0, sizeof(int), st));
+    RSVD_TRY(apass_dense(*A, trans, prec, r, X, ldx, Y, ldy, mb, nb, ws, need, st_word, st));
+    return read_device_status(st_word, st);
+  }
+  return apass_dense(*A, trans, prec, r, X, ldx, Y, ldy, mb, nb, ws, ws_bytes, nullptr, as_stream(stream));
 }
 
 size_t rsvd_orth_workspace(int64_t M, int32_t r) { return orth_ws_bytes(M, r, RSVD_F64) + 1024; }

@@ -124,6 +124,9 @@ __device__ __forceinline__ void store_value(void* out, int64_t idx, double v) {
     static_cast<double*>(out)[idx] = v;
   } else if constexpr (kDtype == RSVD_F32) {
     static_cast<float*>(out)[idx] = __double2float_rn(v);
+  } else if constexpr (kDtype == kF32HoldingBf16) {
+    // rounded once to bfloat16, stored exactly in an FP32 container
+    static_cast<uint32_t*>(out)[idx] = (uint32_t)f64_to_bf16_bits(v) << 16;
   } else {
     static_cast<uint16_t*>(out)[idx] = f64_to_bf16_bits(v);
   }
@@ -224,6 +227,9 @@ rsvd_status launch_gaussian(uint64_t seed, int64_t n, int64_t r, int dtype, int 
       break;
     case RSVD_BF16:
       gaussian_kernel<RSVD_BF16><<<(int)blocks, threads, 0, stream>>>(seed, n, r, layout, out, ld);
+      break;
+    case kF32HoldingBf16:
+      gaussian_kernel<kF32HoldingBf16><<<(int)blocks, threads, 0, stream>>>(seed, n, r, layout, out, ld);
       break;
     default:
       return fail(RSVD_ERR_INVALID_ARG, "gaussian: dtype must be F64, F32 or BF16");

@@ -191,6 +191,23 @@ rsvd_status simt_gemm(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, 
   return RSVD_OK;
 }
 
+template <typename T>
+rsvd_status reduce_partials(int64_t M, int64_t N, int nsplit, const T* P, int64_t ldp, int64_t pstride, T* out,
+                            int64_t ldo, bool accumulate, cudaStream_t stream) {
+  if (M * N == 0) return RSVD_OK;
+  int64_t blocks = cdiv(M * N, 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  reduce_partials_kernel<T><<<(int)blocks, 256, 0, stream>>>(M, N, nsplit, P, ldp, pstride, out, ldo,
+                                                              accumulate ? 1 : 0);
+  RSVD_CUDA(after_launch());
+  return RSVD_OK;
+}
+
+template rsvd_status reduce_partials<float>(int64_t, int64_t, int, const float*, int64_t, int64_t, float*,
+                                            int64_t, bool, cudaStream_t);
+template rsvd_status reduce_partials<double>(int64_t, int64_t, int, const double*, int64_t, int64_t, double*,
+                                             int64_t, bool, cudaStream_t);
+
 template rsvd_status simt_gemm<float>(int64_t, int64_t, int64_t, const float*, int64_t, bool,
                                       const float*, int64_t, float*, int64_t, bool, int, int64_t,
                                       float*, cudaStream_t);

@@ -1,14 +1,510 @@
-// Tensor-core A-passes (placeholder until the tcgen05 kernel lands).
+// Tensor-core A-passes (Section 2.1 steps 2 and 5, Eq. (3)) on FP32 A with
+// BF16 operands and FP32 accumulation in TMEM (tcgen05, sm_103a).
+//
+//   C[M x N] = Ahat[M x K] * X[K x N],   Ahat = A (forward) or A^T (transposed)
+//
+// A stays FP32 in HBM and is read exactly once per pass.  Each CTA is a
+// persistent, warp-specialised pipeline:
+//   warp 0     TMA producer: FP32 tile of A (64 x 128 or 128 x 64) and the
+//              BF16 panel tile (64 x N, 128-byte swizzle) per K step of 64
+//   warp 1     TMEM allocator and single-thread tcgen05.mma issuer
+//   warps 2-5  converters: round the FP32 tile to BF16 (and the residual to a
+//              second BF16 "lo" tile in split mode), transposing it for A^T,
+//              into the K-major 128-byte-swizzled operand layout
+//   warps 6-9  epilogue: tcgen05.ld of the FP32 accumulator, stores to C
+// Two TMEM accumulators let the epilogue of one 128-row tile overlap the MMAs
+// of the next.  The reduction dimension may be split across CTAs for load
+// balance; the partial products are then added in split order by a second
+// kernel, so the result does not depend on scheduling.
+//
+// Split mode (BF16X3): A = A_hi + A_lo and X = X_hi + X_lo, each part BF16,
+// C = A_hi X_hi + A_hi X_lo + A_lo X_hi, about 16 significant bits per operand.
+//
+// Every wait is bounded (about one second of global time); a wait that expires
+// records DEV_TIMEOUT, every role stops issuing work, and the CTA frees its
+// TMEM before returning.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc_ptx.cuh"
 
 namespace rsvd {
+namespace {
 
-size_t tc_apass_ws_bytes(int64_t, int64_t, int, int, int, int64_t, int64_t) { return 256; }
+constexpr int BM = 128;            // output rows per tile (MMA M)
+constexpr int BK = 64;             // K per step: one 128-byte BF16 row
+constexpr int A32_BYTES = BM * BK * 4;
+constexpr int A16_BYTES = BM * BK * 2;
+constexpr int SOP = 2;             // operand (BF16) ring depth
+constexpr int THREADS = 320;
+constexpr uint64_t kWaitNs = 1000000000ull;
 
-rsvd_status tc_apass_from_f32(const rsvd_matrix&, int, int, int, const float*, int64_t, float*, int64_t,
-                              int64_t, int64_t, void*, size_t, cudaStream_t) {
-  return fail(RSVD_ERR_UNSUPPORTED, "tensor-core A-pass not built yet");
+struct TcArgs {
+  int64_t M;            // output rows
+  int N;                // output columns written (r)
+  int NP;               // MMA N: r rounded up to 16
+  int acc_stride;       // TMEM column offset of the second accumulator
+  int tmem_cols;        // TMEM columns allocated
+  int64_t mtiles;
+  int64_t ksteps;       // total K steps
+  int64_t ksteps_per_split;
+  int nsplit;
+  float* C;
+  int64_t ldc;
+  int64_t c_split_stride;
+  int* status;
+};
+
+template <bool SPLIT>
+struct Layout {
+  static constexpr int S32 = SPLIT ? 2 : 3;
+  static constexpr int PARTS = SPLIT ? 2 : 1;
+  __host__ __device__ static size_t a16_off(int s, int part) { return ((size_t)s * PARTS + part) * A16_BYTES; }
+  __host__ __device__ static size_t b16_base() { return (size_t)SOP * PARTS * A16_BYTES; }
+  __host__ __device__ static size_t b16_off(int NP, int s, int part) {
+    return b16_base() + ((size_t)s * PARTS + part) * (size_t)NP * 128;
+  }
+  __host__ __device__ static size_t a32_off(int NP, int s) {
+    return b16_base() + (size_t)SOP * PARTS * NP * 128 + (size_t)s * A32_BYTES;
+  }
+  __host__ __device__ static size_t bar_off(int NP) { return a32_off(NP, S32); }
+  // barriers: full32, empty32 (S32 each), fullA, fullB, emptyOp (SOP each),
+  // accFull, accEmpty (2 each), then the TMEM address word
+  __host__ __device__ static size_t total(int NP) {
+    return bar_off(NP) + (size_t)(2 * S32 + 3 * SOP + 4) * 8 + 16 + 1024;
+  }
+};
+
+__device__ __forceinline__ void flag_timeout(int* status) { dev_set_status(status, DEV_TIMEOUT); }
+
+template <bool TRANS, bool SPLIT>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                const __grid_constant__ CUtensorMap mapBlo, const TcArgs a) {
+  using L = Layout<SPLIT>;
+  constexpr int S32 = L::S32;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int NP = a.NP;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::bar_off(NP));
+  uint64_t* full32 = bars;
+  uint64_t* empty32 = full32 + S32;
+  uint64_t* fullA = empty32 + S32;
+  uint64_t* fullB = fullA + SOP;
+  uint64_t* emptyOp = fullB + SOP;
+  uint64_t* accFull = emptyOp + SOP;
+  uint64_t* accEmpty = accFull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accEmpty + 2);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const volatile int* vstatus = a.status;
+  volatile int* vabort = &s_abort;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S32; ++i) { ptx::mbar_init(&full32[i], 1); ptx::mbar_init(&empty32[i], 4); }
+    for (int i = 0; i < SOP; ++i) {
+      ptx::mbar_init(&fullA[i], 4);
+      ptx::mbar_init(&fullB[i], 1);
+      ptx::mbar_init(&emptyOp[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) { ptx::mbar_init(&accFull[i], 1); ptx::mbar_init(&accEmpty[i], 4); }
+    ptx::fence_mbar_init();
+    s_abort = 0;
+  }
+  if (warp == 0 && lane == 0) {
+    ptx::prefetch_tensormap(&mapA);
+    ptx::prefetch_tensormap(&mapB);
+    if (SPLIT) ptx::prefetch_tensormap(&mapBlo);
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int64_t units = a.mtiles * a.nsplit;
+  const uint32_t b_bytes = (uint32_t)NP * 128u;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int64_t it = 0;
+      for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
+        const int64_t z = u / a.mtiles, mt = u % a.mtiles;
+        const int64_t k0 = z * a.ksteps_per_split;
+        const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
+        for (int64_t ks = k0; ks < k1; ++ks, ++it) {
+          const int s32 = (int)(it % S32);
+          const uint32_t ph32 = (uint32_t)((it / S32) & 1);
+          if (!ptx::mbar_wait(&empty32[s32], ph32 ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
+          ptx::mbar_arrive_expect_tx(&full32[s32], A32_BYTES);
+          void* dstA = smem + L::a32_off(NP, s32);
+          if (TRANS) ptx::tma_load_2d(dstA, &mapA, &full32[s32], (int32_t)(mt * BM), (int32_t)(ks * BK));
+          else ptx::tma_load_2d(dstA, &mapA, &full32[s32], (int32_t)(ks * BK), (int32_t)(mt * BM));
+          const int sop = (int)(it % SOP);
+          const uint32_t phop = (uint32_t)((it / SOP) & 1);
+          if (!ptx::mbar_wait(&emptyOp[sop], phop ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
+          ptx::mbar_arrive_expect_tx(&fullB[sop], b_bytes * L::PARTS);
+          ptx::tma_load_2d(smem + L::b16_off(NP, sop, 0), &mapB, &fullB[sop], (int32_t)(ks * BK), 0);
+          if (SPLIT) ptx::tma_load_2d(smem + L::b16_off(NP, sop, 1), &mapBlo, &fullB[sop], (int32_t)(ks * BK), 0);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = ptx::idesc_bf16_f32(BM, (uint32_t)NP);
+      int64_t it = 0, ua = 0;
+      for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x, ++ua) {
+        const int64_t z = u / a.mtiles;
+        const int64_t k0 = z * a.ksteps_per_split;
+        const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
+        const int acc = (int)(ua & 1);
+        const uint32_t pha = (uint32_t)((ua >> 1) & 1);
+        if (!ptx::mbar_wait(&accEmpty[acc], pha ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
+        ptx::tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * a.acc_stride);
+        uint32_t accumulate = 0;
+        bool ok = true;
+        for (int64_t ks = k0; ks < k1; ++ks, ++it) {
+          const int sop = (int)(it % SOP);
+          const uint32_t phop = (uint32_t)((it / SOP) & 1);
+          if (!ptx::mbar_wait(&fullA[sop], phop, vstatus, kWaitNs) ||
+              !ptx::mbar_wait(&fullB[sop], phop, vstatus, kWaitNs)) {
+            flag_timeout(a.status); s_abort = 1; ok = false; break;
+          }
+          ptx::tc_fence_after();
+          const uint64_t ad = ptx::smem_desc_sw128(smem + L::a16_off(sop, 0));
+          const uint64_t bd = ptx::smem_desc_sw128(smem + L::b16_off(NP, sop, 0));
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            // advance 16 BF16 (32 bytes) along K inside the swizzled row
+            ptx::mma_bf16(d_tmem, ad + 2 * kk, bd + 2 * kk, idesc, accumulate);
+            accumulate = 1;
+            if (SPLIT) {
+              const uint64_t adl = ptx::smem_desc_sw128(smem + L::a16_off(sop, 1));
+              const uint64_t bdl = ptx::smem_desc_sw128(smem + L::b16_off(NP, sop, 1));
+              ptx::mma_bf16(d_tmem, ad + 2 * kk, bdl + 2 * kk, idesc, 1);
+              ptx::mma_bf16(d_tmem, adl + 2 * kk, bd + 2 * kk, idesc, 1);
+            }
+          }
+          ptx::mma_commit(&emptyOp[sop]);
+        }
+        if (!ok) break;
+        ptx::mma_commit(&accFull[acc]);
+      }
+    }
+  } else if (warp < 6) {
+    // ---------------- converters ----------------
+    const int cw = warp - 2;
+    int64_t it = 0;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+      const int64_t z = u / a.mtiles;
+      const int64_t k0 = z * a.ksteps_per_split;
+      const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
+      bool ok = true;
+      for (int64_t ks = k0; ks < k1; ++ks, ++it) {
+        const int s32 = (int)(it % S32);
+        const uint32_t ph32 = (uint32_t)((it / S32) & 1);
+        const int sop = (int)(it % SOP);
+        const uint32_t phop = (uint32_t)((it / SOP) & 1);
+        bool w = ptx::mbar_wait(&full32[s32], ph32, vstatus, kWaitNs) &&
+                 ptx::mbar_wait(&emptyOp[sop], phop ^ 1, vstatus, kWaitNs);
+        if (!__all_sync(0xffffffffu, w)) { if (lane == 0) flag_timeout(a.status); ok = false; break; }
+        const float* src = reinterpret_cast<const float*>(smem + L::a32_off(NP, s32));
+        uint8_t* hi = smem + L::a16_off(sop, 0);
+        uint8_t* lo = smem + L::a16_off(sop, SPLIT ? 1 : 0);
+        if (!TRANS) {
+          // src[i][k], 128 rows of 64 floats: lane converts k = 2*lane, 2*lane+1 of row i
+#pragma unroll 4
+          for (int rr = 0; rr < 32; ++rr) {
+            const int i = cw * 32 + rr;
+            const float2 v = reinterpret_cast<const float2*>(src + i * BK)[lane];
+            const __nv_bfloat162 h = __float22bfloat162_rn(v);
+            const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)lane >> 2) ^ ((uint32_t)i & 7u)) << 4) +
+                                 (((uint32_t)lane & 3u) << 2);
+            *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
+            if (SPLIT) {
+              const float2 hf = __bfloat1622float2(h);
+              const __nv_bfloat162 l = __float22bfloat162_rn(make_float2(v.x - hf.x, v.y - hf.y));
+              *reinterpret_cast<__nv_bfloat162*>(lo + off) = l;
+            }
+          }
+        } else {
+          // src[k][i], 64 rows of 128 floats: lane owns output row i, 8 K values per chunk
+          const int i = cw * 32 + lane;
+#pragma unroll 2
+          for (int c = 0; c < BK / 8; ++c) {
+            float v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = src[(c * 8 + t) * BM + i];
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const __nv_bfloat162 h = __float22bfloat162_rn(make_float2(v[2 * t], v[2 * t + 1]));
+              hw[t] = *reinterpret_cast<const uint32_t*>(&h);
+              if (SPLIT) {
+                const float2 hf = __bfloat1622float2(h);
+                const __nv_bfloat162 l =
+                    __float22bfloat162_rn(make_float2(v[2 * t] - hf.x, v[2 * t + 1] - hf.y));
+                lw[t] = *reinterpret_cast<const uint32_t*>(&l);
+              }
+            }
+            const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)c) ^ ((uint32_t)i & 7u)) << 4);
+            *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            if (SPLIT) *reinterpret_cast<uint4*>(lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          }
+        }
+        ptx::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          ptx::mbar_arrive(&fullA[sop]);
+          ptx::mbar_arrive(&empty32[s32]);
+        }
+      }
+      if (!ok) break;
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    int64_t ua = 0;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++ua) {
+      const int64_t z = u / a.mtiles, mt = u % a.mtiles;
+      const int acc = (int)(ua & 1);
+      const uint32_t pha = (uint32_t)((ua >> 1) & 1);
+      const bool w = ptx::mbar_wait(&accFull[acc], pha, vstatus, kWaitNs);
+      if (!__all_sync(0xffffffffu, w)) { if (lane == 0) flag_timeout(a.status); break; }
+      ptx::tc_fence_after();
+      const int64_t row = mt * BM + q * 32 + lane;
+      float* crow = a.C + z * a.c_split_stride + row * a.ldc;
+      for (int c0 = 0; c0 < NP; c0 += 32) {
+        uint32_t v[32];
+        ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * a.acc_stride + c0), v);
+        ptx::tmem_ld_wait();
+        if (row < a.M) {
+          const int nv = min(32, a.N - c0);
+          if (nv == 32 && (a.ldc & 3) == 0) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(crow + c0 + j) =
+                  make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
+                              __uint_as_float(v[j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < nv) crow[c0 + j] = __uint_as_float(v[j]);
+          }
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&accEmpty[acc]);
+    }
+  }
+
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem_base, (uint32_t)a.tmem_cols);
+  }
+}
+
+// Xt[j][k] = bf16(X[k][j]) for j < r, 0 for r <= j < NP (and the residual
+// into Xlo): the K-major panel operand of the MMA.
+__global__ void panel_to_bf16_kernel(int64_t K, int r, int NP, const float* __restrict__ X, int64_t ldx,
+                                     __nv_bfloat16* __restrict__ Xhi, __nv_bfloat16* __restrict__ Xlo,
+                                     int64_t ldb) {
+  __shared__ float tile[32][33];
+  const int64_t k0 = (int64_t)blockIdx.x * 32;
+  const int j0 = blockIdx.y * 32;
+  for (int t = threadIdx.y; t < 32; t += blockDim.y) {
+    const int64_t k = k0 + t;
+    const int j = j0 + threadIdx.x;
+    tile[t][threadIdx.x] = (k < K && j < r) ? X[k * ldx + j] : 0.f;
+  }
+  __syncthreads();
+  for (int t = threadIdx.y; t < 32; t += blockDim.y) {
+    const int j = j0 + t;
+    const int64_t k = k0 + threadIdx.x;
+    if (j < NP && k < K) {
+      const float v = tile[threadIdx.x][t];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      Xhi[(int64_t)j * ldb + k] = h;
+      if (Xlo) Xlo[(int64_t)j * ldb + k] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+  }
+}
+
+// ---- host side ----------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+rsvd_status encode_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
+                      uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle sw) {
+  auto fn = encode_fn();
+  if (!fn) return fail(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(RSVD_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+  return RSVD_OK;
+}
+
+struct TcShape {
+  int64_t M, K, mtiles, ksteps, ksteps_per_split, ldb;
+  int NP, nsplit;
+};
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
+}
+
+// Split of the K range chosen for balance over the SMs: minimise
+// ceil(units / SMs) * steps_per_unit plus the cost of the partial sums.
+TcShape tc_shape(int64_t m, int64_t n, int r, int trans) {
+  TcShape s;
+  s.M = trans ? n : m;
+  s.K = trans ? m : n;
+  s.NP = (int)round_up(r, 16);
+  s.mtiles = cdiv(s.M, BM);
+  s.ksteps = cdiv(s.K, BK);
+  s.ldb = round_up(s.K, 8);
+  const int64_t sms = num_sms();
+  double best = 1e300;
+  int bestS = 1;
+  for (int S = 1; S <= 64 && S <= s.ksteps; ++S) {
+    const int64_t per = cdiv(s.ksteps, S);
+    const int64_t used = cdiv(s.ksteps, per);
+    const double rounds = (double)cdiv(s.mtiles * used, sms);
+    const double partial = used > 1 ? (double)used * s.M * r * 8.0 / ((double)A32_BYTES * sms) : 0.0;
+    const double cost = rounds * per + partial;
+    if (cost < best - 1e-9) { best = cost; bestS = (int)used; }
+  }
+  s.ksteps_per_split = cdiv(s.ksteps, bestS);
+  s.nsplit = (int)cdiv(s.ksteps, s.ksteps_per_split);
+  return s;
+}
+
+}  // namespace
+
+size_t tc_apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t, int64_t) {
+  const TcShape s = tc_shape(m, n, r, trans);
+  const bool split = prec == RSVD_PREC_BF16X3;
+  Sizer z;
+  z.take<__nv_bfloat16>((size_t)s.NP * s.ldb);
+  if (split) z.take<__nv_bfloat16>((size_t)s.NP * s.ldb);
+  if (s.nsplit > 1) z.take<float>((size_t)s.nsplit * round_up(s.M * r, 4));
+  z.take<int>(4);
+  return z.used + 256;
+}
+
+rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X, int64_t ldx,
+                              float* Y, int64_t ldy, int64_t, int64_t, void* ws, size_t ws_bytes,
+                              int* status, cudaStream_t stream) {
+  const bool split = prec == RSVD_PREC_BF16X3;
+  if (r < 1 || r > 256) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: r must be in [1, 256]");
+  if (A.ld % 4 != 0 || (reinterpret_cast<uintptr_t>(A.data) & 15) != 0)
+    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: A needs a 16-byte aligned base and ld % 4 == 0");
+  const TcShape s = tc_shape(A.m, A.n, r, trans);
+  if (split && s.NP > 192) return fail(RSVD_ERR_UNSUPPORTED, "split-BF16 A-pass supports k + p <= 192");
+  Carver c(ws, ws_bytes);
+  auto* Xhi = c.take<__nv_bfloat16>((size_t)s.NP * s.ldb);
+  __nv_bfloat16* Xlo = split ? c.take<__nv_bfloat16>((size_t)s.NP * s.ldb) : nullptr;
+  const int64_t slab = round_up(s.M * r, 4);
+  float* partial = s.nsplit > 1 ? c.take<float>((size_t)s.nsplit * slab) : nullptr;
+  int* own_status = c.take<int>(4);
+  if (c.overflow) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: workspace too small");
+  if (!status) {
+    status = own_status;
+    RSVD_CUDA(cudaMemsetAsync(status, 0, sizeof(int), stream));
+  }
+
+  {  // panel -> BF16 (hi, lo), K-major
+    dim3 grid((unsigned)cdiv(s.K, 32), (unsigned)cdiv(s.NP, 32));
+    panel_to_bf16_kernel<<<grid, dim3(32, 8), 0, stream>>>(s.K, r, s.NP, X, ldx, Xhi, Xlo, s.ldb);
+    RSVD_CUDA(after_launch());
+  }
+  CUtensorMap mapA, mapB, mapBlo;
+  if (trans)
+    RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A.data, (uint64_t)A.n, (uint64_t)A.m,
+                       (uint64_t)A.ld * 4, BM, BK, CU_TENSOR_MAP_SWIZZLE_NONE));
+  else
+    RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A.data, (uint64_t)A.n, (uint64_t)A.m,
+                       (uint64_t)A.ld * 4, BK, BM, CU_TENSOR_MAP_SWIZZLE_NONE));
+  RSVD_TRY(encode_2d(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Xhi, (uint64_t)s.K, (uint64_t)s.NP,
+                     (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP, CU_TENSOR_MAP_SWIZZLE_128B));
+  if (split)
+    RSVD_TRY(encode_2d(&mapBlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Xlo, (uint64_t)s.K, (uint64_t)s.NP,
+                       (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP, CU_TENSOR_MAP_SWIZZLE_128B));
+  else
+    mapBlo = mapB;
+
+  TcArgs ta;
+  ta.M = s.M;
+  ta.N = r;
+  ta.NP = s.NP;
+  ta.acc_stride = (int)round_up(s.NP, 32);
+  int cols = 32;
+  while (cols < 2 * ta.acc_stride) cols *= 2;
+  ta.tmem_cols = cols;
+  ta.mtiles = s.mtiles;
+  ta.ksteps = s.ksteps;
+  ta.ksteps_per_split = s.ksteps_per_split;
+  ta.nsplit = s.nsplit;
+  ta.C = s.nsplit > 1 ? partial : Y;
+  ta.ldc = s.nsplit > 1 ? r : ldy;
+  ta.c_split_stride = s.nsplit > 1 ? slab : 0;
+  ta.status = status;
+
+  const int64_t units = s.mtiles * s.nsplit;
+  const int grid = (int)(units < num_sms() ? units : num_sms());
+  const size_t smem = split ? Layout<true>::total(s.NP) : Layout<false>::total(s.NP);
+  if (smem > 232448) return fail(RSVD_ERR_UNSUPPORTED, "tensor-core A-pass: shared memory plan too large");
+  auto launch = [&](auto kern) -> rsvd_status {
+    RSVD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, THREADS, smem, stream>>>(mapA, mapB, mapBlo, ta);
+    RSVD_CUDA(after_launch());
+    return RSVD_OK;
+  };
+  if (trans) {
+    RSVD_TRY(split ? launch(tc_apass_kernel<true, true>) : launch(tc_apass_kernel<true, false>));
+  } else {
+    RSVD_TRY(split ? launch(tc_apass_kernel<false, true>) : launch(tc_apass_kernel<false, false>));
+  }
+  if (s.nsplit > 1) RSVD_TRY(reduce_partials<float>(s.M, r, s.nsplit, partial, r, slab, Y, ldy, false, stream));
+  return RSVD_OK;
 }
 
 }  // namespace rsvd

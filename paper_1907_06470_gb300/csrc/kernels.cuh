@@ -5,7 +5,10 @@
 
 namespace rsvd {
 
-// gaussian.cu -- Section 2.1 step 1.
+// gaussian.cu -- Section 2.1 step 1.  Besides the public dtypes, kF32HoldingBf16
+// writes the values rounded once to bfloat16 into an FP32 buffer (the test
+// matrix of the BF16 path, whose A-pass converts its panel to BF16 exactly).
+constexpr int kF32HoldingBf16 = 3;
 rsvd_status launch_gaussian(uint64_t seed, int64_t n, int64_t r, int dtype, int layout, void* out,
                             int64_t ld, cudaStream_t stream);
 
@@ -21,6 +24,11 @@ template <typename T>
 rsvd_status simt_gemm(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, bool transA,
                       const T* B, int64_t ldb, T* C, int64_t ldc, bool accumulate, int nsplit,
                       int64_t kchunk, T* partial, cudaStream_t stream);
+
+// out[i, j] (+)= sum_z P[z*pstride + i*ldp + j], z in increasing order.
+template <typename T>
+rsvd_status reduce_partials(int64_t M, int64_t N, int nsplit, const T* P, int64_t ldp, int64_t pstride, T* out,
+                            int64_t ldo, bool accumulate, cudaStream_t stream);
 
 // orth.cu -- CholeskyQR2 pieces.
 struct OrthWs {
@@ -78,12 +86,14 @@ rsvd_status gather_colmajor_f64(int64_t rows, int64_t cols, const T* A, int64_t 
 size_t apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t mb, int64_t nb);
 rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const void* X, int64_t ldx,
                         void* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws, size_t ws_bytes,
-                        cudaStream_t stream);
+                        int* status, cudaStream_t stream);
 
 // gemm_tc.cu -- tensor-core (tcgen05) A-passes on FP32 A with in-kernel BF16 conversion.
 size_t tc_apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t mb, int64_t nb);
+// `status` (may be NULL: a workspace word is used) receives DEV_TIMEOUT if a
+// pipeline wait expires.
 rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X,
                               int64_t ldx, float* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws,
-                              size_t ws_bytes, cudaStream_t stream);
+                              size_t ws_bytes, int* status, cudaStream_t stream);
 
 }  // namespace rsvd

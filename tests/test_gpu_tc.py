@@ -1,0 +1,112 @@
+"""Tensor-core (tcgen05) A-passes: exactness on small integers, accuracy of the
+BF16 and split-BF16 modes against FP64 products, split-K balance, and the
+BF16 randomized SVD against the oracle."""
+
+import numpy as np
+import pytest
+
+from oracle import linalg as OL
+from oracle import rsvd as OR
+from synth import prescribed_dense, spectrum_harmonic_noisy
+from tests.metrics import max_principal_angle, sigma_rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1907_06470_gb300 as g
+    g.load()
+    return g
+
+
+def _bf16(x):
+    return torch.as_tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+# row strides are multiples of 4 floats (the TMA rule the library enforces)
+SHAPES = [(300, 200, 17), (128, 64, 1), (513, 388, 120), (1000, 132, 128), (257, 1000, 200), (640, 320, 256),
+          (129, 68, 30)]
+
+
+@pytest.mark.parametrize("m,n,r", SHAPES)
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_tc_apass_exact_on_small_integers(g, m, n, r, trans, prec):
+    if prec == "bf16x3" and r > 192:
+        pytest.skip("split mode supports r <= 192")
+    rng = np.random.default_rng(m * 7 + n * 3 + r)
+    A = rng.integers(-4, 5, size=(m, n)).astype(np.float32)
+    K = m if trans else n
+    X = rng.integers(-4, 5, size=(K, r)).astype(np.float32)
+    got = g.apass(torch.as_tensor(A, device="cuda"), torch.as_tensor(X, device="cuda"), trans, prec).cpu().numpy()
+    ref = OL.apply(A, X, trans=trans).astype(np.float32)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("trans", [False, True])
+def test_tc_apass_bf16_error_model(g, trans):
+    """BF16 mode = exact product of the BF16-rounded operands, accumulated in FP32."""
+    m, n, r = 2000, 1500, 120
+    rng = np.random.default_rng(1 + trans)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    K = m if trans else n
+    X = rng.standard_normal((K, r)).astype(np.float32)
+    got = g.apass(torch.as_tensor(A, device="cuda"), torch.as_tensor(X, device="cuda"), trans, "bf16").cpu().numpy()
+    Ab, Xb = _bf16(A), _bf16(X)
+    ref = OL.apply(Ab, Xb, trans=trans)
+    bound = (K + 2) * 2.0 ** -24 * OL.apply(np.abs(Ab), np.abs(Xb), trans=trans)
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("trans", [False, True])
+def test_tc_apass_split_mode_is_near_fp32(g, trans):
+    m, n, r = 1500, 1100, 64
+    rng = np.random.default_rng(5 + trans)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    K = m if trans else n
+    X = rng.standard_normal((K, r)).astype(np.float32)
+    got = g.apass(torch.as_tensor(A, device="cuda"), torch.as_tensor(X, device="cuda"), trans, "bf16x3").cpu().numpy()
+    ref = OL.apply(A, X, trans=trans)
+    scale = OL.apply(np.abs(A), np.abs(X), trans=trans)
+    rel = np.max(np.abs(got - ref) / scale)
+    assert rel < 2.0 ** -14  # BF16 alone sits near 2^-9
+    bf = g.apass(torch.as_tensor(A, device="cuda"), torch.as_tensor(X, device="cuda"), trans, "bf16").cpu().numpy()
+    assert rel < np.max(np.abs(bf - ref) / scale) / 30
+
+
+def test_tc_apass_split_k_matches_unsplit_reference(g):
+    """Long K with few output tiles forces the K range to be split over CTAs."""
+    m, n, r = 60000, 256, 32
+    rng = np.random.default_rng(9)
+    A = rng.integers(-2, 3, size=(m, n)).astype(np.float32)
+    Y = rng.integers(-2, 3, size=(m, r)).astype(np.float32)
+    got = g.apass(torch.as_tensor(A, device="cuda"), torch.as_tensor(Y, device="cuda"), True, "bf16").cpu().numpy()
+    assert np.array_equal(got, OL.apply(A, Y, trans=True).astype(np.float32))
+
+
+def test_tc_apass_rejects_misaligned_rows(g):
+    A = torch.zeros(64, 67, device="cuda")
+    X = torch.zeros(67, 8, device="cuda")
+    with pytest.raises(g.RsvdError):
+        g.apass(A, X, False, "bf16")
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_bf16_rsvd_against_oracle(g, prec):
+    """BF16 path (reported, not pinned to FP32 tolerances): errors against the
+    FP64 oracle run with the same BF16-rounded test matrix."""
+    m, n, k, p, q, seed = 8000, 4000, 100, 20, 2, 2002
+    s = spectrum_harmonic_noisy(n, 1e-4, 3002)
+    A, _, _ = prescribed_dense(m, n, s, 1002, dtype=np.float32)
+    U, S, V = (t.cpu().numpy().astype(np.float64) for t in
+               g.rsvd(torch.as_tensor(A, device="cuda"), k, p, q, seed, prec=prec))
+    Uo, So, Vo = OR.rsvd(A, k, p, q, seed, "bf16")
+    es, eu, ev = sigma_rel_err(S, So), max_principal_angle(U, Uo), max_principal_angle(V, Vo)
+    print(f"{prec}: sigma rel err {es:.2e}, U angle {eu:.2e}, V angle {ev:.2e}")
+    if prec == "bf16x3":
+        assert es <= 1e-4 and eu <= 1e-2
+    else:
+        assert es <= 1e-2
