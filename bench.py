@@ -335,6 +335,41 @@ def run_ours(args):
     return 0
 
 
+def run_apass_only(args):
+    """Forward and transposed A-passes alone on a random FP32 matrix (a small,
+    quick target for kernel profiling and tuning)."""
+    import torch
+    import paper_1907_06470_gb300 as g
+    g.load()
+    m, n, r = args.m, args.n, args.r
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1234)
+    A = torch.randn(m, n, generator=gen, device="cuda")
+    X = torch.randn(n, r, generator=gen, device="cuda")
+    Yt = torch.randn(m, r, generator=gen, device="cuda")
+    Y = torch.empty(m, r, device="cuda")
+    Z = torch.empty(n, r, device="cuda")
+    for _ in range(args.warmup):
+        g.apass(A, X, False, args.prec, out=Y)
+        g.apass(A, Yt, True, args.prec, out=Z)
+    torch.cuda.synchronize()
+    out = {}
+    for name, (src, dst, tr) in {"forward": (X, Y, False), "transposed": (Yt, Z, True)}.items():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            g.apass(A, src, tr, args.prec, out=dst)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        nbytes = m * n * 4 + (m + n) * r * 4
+        out[name] = {"ms": ms, "GB/s": nbytes / ms / 1e6, "TFLOP/s": 2.0 * m * n * r / ms / 1e9}
+    print(json.dumps({"mode": "apass", "m": m, "n": n, "r": r, "prec": args.prec, "steps": args.steps,
+                      "note": "each call includes the panel conversion and a stream sync", **out}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,7 +380,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--mode", default="rsvd", choices=["rsvd", "apass"])
+    ap.add_argument("--m", type=int, default=25000)
+    ap.add_argument("--n", type=int, default=20000)
+    ap.add_argument("--r", type=int, default=120)
     args = ap.parse_args()
+    if args.mode == "apass":
+        return run_apass_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
