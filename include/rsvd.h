@@ -232,6 +232,29 @@ size_t rsvd_small_svd_workspace(int32_t r);
 rsvd_status rsvd_small_svd(int32_t r, const double* Mc, double* sigma, double* U, double* W,
                            void* ws, size_t ws_bytes, void* stream);
 
+/* ---- Variant without allocation (no counterpart in the paper) --------------- */
+
+/* Largest r accepted by rsvd_small_svd_noalloc. */
+#define RSVD_NOALLOC_MAX_R 256
+
+/* rsvd_small_svd for callers that cannot allocate device memory -- for example
+ * code whose device memory is entirely reserved by a framework's memory pool,
+ * or latency-sensitive code that must not let cudaMalloc/cudaFree synchronise
+ * the device -- and therefore cannot provide the workspace rsvd_small_svd
+ * takes.  Same arguments and results as rsvd_small_svd, minus the workspace;
+ * it calls no allocation routine.  Its scratch is one static device array of
+ * about 1 MiB (two RSVD_NOALLOC_MAX_R^2 FP64 matrices plus a few words) that
+ * every GPU loading this library keeps until the process exits.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call uses the same
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and return wrong results; serialise them.  The words that must
+ * start at zero are cleared by each call.  Errors: INVALID_ARG for r outside
+ * [1, RSVD_NOALLOC_MAX_R] (checked on the host before any GPU work),
+ * NO_CONVERGE, TIMEOUT, CUDA.  Synchronises `stream`. */
+rsvd_status rsvd_small_svd_noalloc(int32_t r, const double* Mc, double* sigma, double* U, double* W,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ from . import _lib
 from ._lib import RsvdError, load  # noqa: F401
 
 __all__ = ["rsvd", "Plan", "full_svd", "gaussian", "tile_map", "apass", "orth", "small_svd",
-           "RsvdError", "load"]
+           "small_svd_noalloc", "RsvdError", "load"]
 
 
 def _torch():
@@ -229,4 +229,21 @@ def small_svd(Mc):
     _check(lib.rsvd_small_svd(r, C.c_void_p(Mc.data_ptr()), C.c_void_p(sigma.data_ptr()),
                               C.c_void_p(U.data_ptr()), C.c_void_p(W.data_ptr()), C.c_void_p(ws.data_ptr()),
                               wsb, _stream_ptr()))
+    return sigma, U, W
+
+
+def small_svd_noalloc(Mc, sigma=None, U=None, W=None):
+    """small_svd without a workspace: for callers that cannot allocate device
+    memory (the library uses its own static scratch; calls must not overlap on
+    the GPU).  Outputs may be passed in preallocated."""
+    torch = _torch()
+    r = Mc.shape[0]
+    if sigma is None:
+        sigma = torch.empty(r, dtype=torch.float64, device=Mc.device)
+    if U is None:
+        U = torch.empty(r, r, dtype=torch.float64, device=Mc.device)
+    if W is None:
+        W = torch.empty(r, r, dtype=torch.float64, device=Mc.device)
+    _check(load().rsvd_small_svd_noalloc(r, C.c_void_p(Mc.data_ptr()), C.c_void_p(sigma.data_ptr()),
+                                         C.c_void_p(U.data_ptr()), C.c_void_p(W.data_ptr()), _stream_ptr()))
     return sigma, U, W

@@ -67,7 +67,9 @@ SIGNATURES = {
     "rsvd_orth": (c_i32, [c_i32, c_i64, c_i32, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_size, c_vp]),
     "rsvd_small_svd_workspace": (c_size, [c_i32]),
     "rsvd_small_svd": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
+    "rsvd_small_svd_noalloc": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
 }
+NOALLOC_MAX_R = 256
 
 _lock = threading.Lock()
 _lib = None
