@@ -192,6 +192,34 @@ rsvd_status simt_gemm(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, 
 }
 
 template <typename T>
+rsvd_status simt_gemm_partials(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, bool transA,
+                               const T* B, int64_t ldb, int nsplit, int64_t kchunk, T* partial,
+                               cudaStream_t stream) {
+  if (M <= 0 || N <= 0) return RSVD_OK;
+  if (nsplit < 1 || kchunk % 4 != 0 || !partial)
+    return fail(RSVD_ERR_INVALID_ARG, "simt_gemm_partials: bad split");
+  const bool vec = (lda % 4 == 0) && (ldb % 4 == 0) && aligned16(A) && aligned16(B);
+  dim3 grid((unsigned)cdiv(M, BM), (unsigned)cdiv(N, BN), (unsigned)nsplit);
+  if (grid.y > 65535 || grid.z > 65535) return fail(RSVD_ERR_INVALID_ARG, "simt_gemm_partials: grid too large");
+#define RSVD_LAUNCH(TR, VE)                                                                      \
+  simt_gemm_kernel<T, TR, VE><<<grid, THREADS, 0, stream>>>(M, N, K, A, lda, B, ldb, partial, N, \
+                                                            M * N, kchunk, 0)
+  if (transA) {
+    if (vec) RSVD_LAUNCH(true, true); else RSVD_LAUNCH(true, false);
+  } else {
+    if (vec) RSVD_LAUNCH(false, true); else RSVD_LAUNCH(false, false);
+  }
+#undef RSVD_LAUNCH
+  RSVD_CUDA(after_launch());
+  return RSVD_OK;
+}
+
+template rsvd_status simt_gemm_partials<float>(int64_t, int64_t, int64_t, const float*, int64_t, bool, const float*,
+                                               int64_t, int, int64_t, float*, cudaStream_t);
+template rsvd_status simt_gemm_partials<double>(int64_t, int64_t, int64_t, const double*, int64_t, bool,
+                                                const double*, int64_t, int, int64_t, double*, cudaStream_t);
+
+template <typename T>
 rsvd_status reduce_partials(int64_t M, int64_t N, int nsplit, const T* P, int64_t ldp, int64_t pstride, T* out,
                             int64_t ldo, bool accumulate, cudaStream_t stream) {
   if (M * N == 0) return RSVD_OK;

@@ -54,15 +54,23 @@ struct TcArgs {
   int64_t ksteps;       // total K steps
   int64_t ksteps_per_split;
   int nsplit;
+  int s32;              // FP32 staging ring depth
   float* C;
   int64_t ldc;
   int64_t c_split_stride;
   int* status;
 };
 
+#ifndef RSVD_TC_MAX_S32
+#define RSVD_TC_MAX_S32 4
+#endif
+constexpr int kMaxS32 = RSVD_TC_MAX_S32;  // deepest FP32 staging ring
+
+// Shared-memory plan: BF16 operand slots (A then panel), then the FP32 staging
+// ring of depth S32 (a runtime choice: as deep as the 227 KB allow), then the
+// barriers and the TMEM address word.
 template <bool SPLIT>
 struct Layout {
-  static constexpr int S32 = SPLIT ? 2 : 3;
   static constexpr int PARTS = SPLIT ? 2 : 1;
   __host__ __device__ static size_t a16_off(int s, int part) { return ((size_t)s * PARTS + part) * A16_BYTES; }
   __host__ __device__ static size_t b16_base() { return (size_t)SOP * PARTS * A16_BYTES; }
@@ -72,11 +80,11 @@ struct Layout {
   __host__ __device__ static size_t a32_off(int NP, int s) {
     return b16_base() + (size_t)SOP * PARTS * NP * 128 + (size_t)s * A32_BYTES;
   }
-  __host__ __device__ static size_t bar_off(int NP) { return a32_off(NP, S32); }
-  // barriers: full32, empty32 (S32 each), fullA, fullB, emptyOp (SOP each),
+  __host__ __device__ static size_t bar_off(int NP, int S32) { return a32_off(NP, S32); }
+  // barriers: full32, empty32 (kMaxS32 each), fullA, fullB, emptyOp (SOP each),
   // accFull, accEmpty (2 each), then the TMEM address word
-  __host__ __device__ static size_t total(int NP) {
-    return bar_off(NP) + (size_t)(2 * S32 + 3 * SOP + 4) * 8 + 16 + 1024;
+  __host__ __device__ static size_t total(int NP, int S32) {
+    return bar_off(NP, S32) + (size_t)(2 * kMaxS32 + 3 * SOP + 4) * 8 + 16 + 1024;
   }
 };
 
@@ -87,14 +95,14 @@ __global__ void __launch_bounds__(THREADS, 1)
 tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const __grid_constant__ CUtensorMap mapBlo, const TcArgs a) {
   using L = Layout<SPLIT>;
-  constexpr int S32 = L::S32;
+  const int S32 = a.s32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int NP = a.NP;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::bar_off(NP));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::bar_off(NP, S32));
   uint64_t* full32 = bars;
-  uint64_t* empty32 = full32 + S32;
-  uint64_t* fullA = empty32 + S32;
+  uint64_t* empty32 = full32 + kMaxS32;
+  uint64_t* fullA = empty32 + kMaxS32;
   uint64_t* fullB = fullA + SOP;
   uint64_t* emptyOp = fullB + SOP;
   uint64_t* accFull = emptyOp + SOP;
@@ -217,8 +225,8 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         const uint32_t ph32 = (uint32_t)((it / S32) & 1);
         const int sop = (int)(it % SOP);
         const uint32_t phop = (uint32_t)((it / SOP) & 1);
-        bool w = ptx::mbar_wait(&full32[s32], ph32, vstatus, kWaitNs) &&
-                 ptx::mbar_wait(&emptyOp[sop], phop ^ 1, vstatus, kWaitNs);
+        const bool w = ptx::mbar_wait(&full32[s32], ph32, vstatus, kWaitNs) &&
+                       ptx::mbar_wait(&emptyOp[sop], phop ^ 1, vstatus, kWaitNs);
         if (!__all_sync(0xffffffffu, w)) { if (lane == 0) flag_timeout(a.status); ok = false; break; }
         const float* src = reinterpret_cast<const float*>(smem + L::a32_off(NP, s32));
         uint8_t* hi = smem + L::a16_off(sop, 0);
@@ -490,8 +498,13 @@ rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, 
 
   const int64_t units = s.mtiles * s.nsplit;
   const int grid = (int)(units < num_sms() ? units : num_sms());
-  const size_t smem = split ? Layout<true>::total(s.NP) : Layout<false>::total(s.NP);
-  if (smem > 232448) return fail(RSVD_ERR_UNSUPPORTED, "tensor-core A-pass: shared memory plan too large");
+  constexpr size_t kSmemMax = 232448;
+  int s32 = kMaxS32;
+  auto need = [&](int depth) { return split ? Layout<true>::total(s.NP, depth) : Layout<false>::total(s.NP, depth); };
+  while (s32 > 2 && need(s32) > kSmemMax) --s32;
+  const size_t smem = need(s32);
+  if (smem > kSmemMax) return fail(RSVD_ERR_UNSUPPORTED, "tensor-core A-pass: shared memory plan too large");
+  ta.s32 = s32;
   auto launch = [&](auto kern) -> rsvd_status {
     RSVD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, THREADS, smem, stream>>>(mapA, mapB, mapBlo, ta);

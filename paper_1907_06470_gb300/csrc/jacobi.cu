@@ -1,151 +1,175 @@
 // Section 2.1 step 6: SVD of the small factor by one-sided (Hestenes) Jacobi
 // in FP64, with the relative stopping test of Demmel & Veselic (1992).
 //
+// Three phases for square inputs with 8 <= r <= 160: FP32 sweeps in one CTA
+// (shared memory) to FP32 convergence; one FP64 Newton-Schulz step that makes
+// the accumulated FP32 rotation exactly orthogonal in FP64, applied to M; FP64
+// sweeps to FP64 convergence, which then take few sweeps.  Other shapes run the
+// FP64 sweeps from the start.
+//
 // M (rows x r, column-major, rows >= 1) is driven to orthogonal columns by plane rotations
 // from the right, M W = U diag(sigma).  The sweep order is round-robin: in
 // each of the r'-1 rounds of a sweep (r' = r rounded up to even) the r'/2
 // column pairs are disjoint, so one CTA rotates each pair concurrently.
-// FP64 throughput on one GB300 SM is low, so the rounds are spread over up to
-// r'/2 co-resident CTAs (cooperative launch) separated by a grid barrier whose
-// waits are bounded: a barrier that times out records DEV_TIMEOUT and every
-// CTA returns.  Columns are read and written through L2 (ld/st .cg) because
-// another SM may have rotated them in the previous round.
+// FP64 throughput on one GB300 SM is low (about 2 DFMA per clock), so the
+// pairs of a round are spread over the warps of a thread-block cluster of up to
+// 16 CTAs (one warp per pair) and rounds are separated by the hardware cluster
+// barrier.  Columns are read and written through L2 (ld/st .cg) because another
+// SM may have rotated them in the previous round.
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace rsvd {
 namespace {
 
-constexpr int JT = 128;  // threads per CTA
-
-__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* p) {
-  return *reinterpret_cast<const volatile unsigned*>(p);
-}
-
-// Sense-by-generation grid barrier with a bounded spin.  bar[0] = arrivals,
-// bar[1] = generation.  Returns false if the wait timed out or another CTA
-// recorded an error.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    const unsigned gen = ld_volatile_u32(&bar[1]);
-    __threadfence();
-    const unsigned arrived = atomicAdd(&bar[0], 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&bar[0], 0u);
-      __threadfence();
-      atomicAdd(&bar[1], 1u);
-    } else {
-      long long spins = 0;
-      while (ld_volatile_u32(&bar[1]) == gen) {
-        if (++spins > kSpinLimit) { dev_set_status(status, DEV_TIMEOUT); ok = 0; break; }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    if (*reinterpret_cast<volatile int*>(status) == DEV_TIMEOUT) ok = 0;
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-#pragma unroll
-  for (int i = 0; i < JT / 32; ++i) s += red[i];
-  return s;
-}
-
 __device__ __forceinline__ int rr_column(int pos, int round, int rp) {
   return pos == 0 ? 0 : 1 + (pos - 1 + round) % (rp - 1);
 }
 
-__global__ void __launch_bounds__(JT)
-jacobi_kernel(int rows, int r, const double* __restrict__ Min, double* M, double* W, unsigned* bar,
-              int* rotated, int* sweeps_out, int* status, double* sigma, double* Uout, double* Wout) {
-  __shared__ double red[JT / 32];
-  const int tid = threadIdx.x;
-  const unsigned nblocks = gridDim.x;
+// All threads of all CTAs of the cluster: release this CTA's memory operations
+// and wait until every thread of the cluster has arrived.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One cluster of up to 16 CTAs; warp w of CTA b owns pair slot b*warps + w of
+// every round.  Rounds are separated by the hardware cluster barrier; the
+// columns live in global memory and are accessed through L2 (.cg).
+constexpr int kMaxPerLane = 8;  // rows <= 256: column values held in registers
+
+__global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict__ Min,
+                                      const double* __restrict__ W0, double* M, double* W, int* rotated,
+                                      int* sweeps_out, int* status, double* sigma, double* Uout, double* Wout) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, warps = nthr >> 5;
+  const int ncta = gridDim.x;
   const int rp = r + (r & 1);
   const int npairs = rp / 2;
   const int64_t mm = (int64_t)rows * r;
   const int64_t ww = (int64_t)r * r;
+  const int64_t gtid = (int64_t)blockIdx.x * nthr + tid, gstride = (int64_t)ncta * nthr;
 
-  // copy the input and set W = I (each CTA a strided share)
-  for (int64_t e = (int64_t)blockIdx.x * JT + tid; e < mm; e += (int64_t)nblocks * JT)
-    __stcg(&M[e], Min[e]);
-  for (int64_t e = (int64_t)blockIdx.x * JT + tid; e < ww; e += (int64_t)nblocks * JT)
-    __stcg(&W[e], (e / r) == (e % r) ? 1.0 : 0.0);
-  // Frobenius norm of the input, for the rounding-level column test
+  for (int64_t e = gtid; e < mm; e += gstride) __stcg(&M[e], Min[e]);
+  for (int64_t e = gtid; e < ww; e += gstride) __stcg(&W[e], W0 ? W0[e] : ((e / r) == (e % r) ? 1.0 : 0.0));
+  // Frobenius norm of the input (every CTA computes it), for the rounding-level column test
   double f = 0.0;
-  for (int64_t e = tid; e < mm; e += JT) f += Min[e] * Min[e];
-  const double fro2 = block_sum(f, red);
+  for (int64_t e = tid; e < mm; e += nthr) f += Min[e] * Min[e];
+  f = warp_sum_d(f);
+  if (lane == 0) red[warp] = f;
+  __syncthreads();
+  double fro2 = 0.0;
+  for (int i = 0; i < warps; ++i) fro2 += red[i];
   const double eps = 2.220446049250313e-16;
   const double big = (double)(rows > r ? rows : r);
   const double zero2 = (big * eps) * (big * eps) * fro2;
   const double tol = (double)r * eps;
-  if (!grid_barrier(bar, nblocks, status)) return;
+  cluster_sync_all();
 
   int sweep = 0;
   bool converged = false;
+  const int s = blockIdx.x * warps + warp;  // this warp's pair slot
   for (; sweep < kJacobiMaxSweeps; ++sweep) {
     for (int round = 0; round < rp - 1; ++round) {
-      for (int s = blockIdx.x; s < npairs; s += nblocks) {
+      if (s < npairs) {
         int p = rr_column(s, round, rp), q = rr_column(rp - 1 - s, round, rp);
-        if (p >= r || q >= r) continue;  // dummy column of an odd r
-        if (p > q) { const int t = p; p = q; q = t; }
-        double* mp = M + (int64_t)p * rows;
-        double* mq = M + (int64_t)q * rows;
-        double a = 0.0, b = 0.0, g = 0.0;
-        for (int i = tid; i < rows; i += JT) {
-          const double x = __ldcg(&mp[i]), y = __ldcg(&mq[i]);
-          a += x * x; b += y * y; g += x * y;
+        if (p < r && q < r) {
+          if (p > q) { const int t = p; p = q; q = t; }
+          double* mp = M + (int64_t)p * rows;
+          double* mq = M + (int64_t)q * rows;
+          double xv[kMaxPerLane], yv[kMaxPerLane];
+          double a = 0.0, b = 0.0, g = 0.0;
+          const bool in_regs = rows <= 32 * kMaxPerLane;
+#pragma unroll
+          for (int t = 0; t < kMaxPerLane; ++t) {
+            const int i = lane + 32 * t;
+            const bool ok = in_regs && i < rows;
+            xv[t] = ok ? __ldcg(&mp[i]) : 0.0;
+            yv[t] = ok ? __ldcg(&mq[i]) : 0.0;
+            a = fma(xv[t], xv[t], a); b = fma(yv[t], yv[t], b); g = fma(xv[t], yv[t], g);
+          }
+          double* wp = W + (int64_t)p * r;
+          double* wq = W + (int64_t)q * r;
+          double wu[kMaxPerLane], wv[kMaxPerLane];
+          const bool w_in_regs = r <= 32 * kMaxPerLane;
+#pragma unroll
+          for (int t = 0; t < kMaxPerLane; ++t) {
+            const int i = lane + 32 * t;
+            const bool ok = w_in_regs && i < r;
+            wu[t] = ok ? __ldcg(&wp[i]) : 0.0;
+            wv[t] = ok ? __ldcg(&wq[i]) : 0.0;
+          }
+          if (!in_regs)
+            for (int i = lane; i < rows; i += 32) {
+              const double x = __ldcg(&mp[i]), y = __ldcg(&mq[i]);
+              a = fma(x, x, a); b = fma(y, y, b); g = fma(x, y, g);
+            }
+          a = warp_sum_d(a);
+          b = warp_sum_d(b);
+          g = warp_sum_d(g);
+          if (fabs(g) > tol * sqrt(a * b) && a > zero2 && b > zero2) {
+            const double zeta = (b - a) / (2.0 * g);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+            const double c = 1.0 / sqrt(1.0 + t * t);
+            const double sn = c * t;
+            if (in_regs) {
+#pragma unroll
+              for (int u = 0; u < kMaxPerLane; ++u) {
+                const int i = lane + 32 * u;
+                if (i < rows) {
+                  __stcg(&mp[i], c * xv[u] - sn * yv[u]);
+                  __stcg(&mq[i], sn * xv[u] + c * yv[u]);
+                }
+              }
+            } else {
+              for (int i = lane; i < rows; i += 32) {
+                const double x = __ldcg(&mp[i]), y = __ldcg(&mq[i]);
+                __stcg(&mp[i], c * x - sn * y);
+                __stcg(&mq[i], sn * x + c * y);
+              }
+            }
+            if (w_in_regs) {
+#pragma unroll
+              for (int u = 0; u < kMaxPerLane; ++u) {
+                const int i = lane + 32 * u;
+                if (i < r) {
+                  __stcg(&wp[i], c * wu[u] - sn * wv[u]);
+                  __stcg(&wq[i], sn * wu[u] + c * wv[u]);
+                }
+              }
+            } else {
+              for (int i = lane; i < r; i += 32) {
+                const double u = __ldcg(&wp[i]), v = __ldcg(&wq[i]);
+                __stcg(&wp[i], c * u - sn * v);
+                __stcg(&wq[i], sn * u + c * v);
+              }
+            }
+            if (lane == 0) __stcg(&rotated[sweep], 1);
+          }
         }
-        a = block_sum(a, red);
-        b = block_sum(b, red);
-        g = block_sum(g, red);
-        if (!(fabs(g) > tol * sqrt(a * b)) || !(a > zero2) || !(b > zero2)) continue;
-        const double zeta = (b - a) / (2.0 * g);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t);
-        const double sn = c * t;
-        double* wp = W + (int64_t)p * r;
-        double* wq = W + (int64_t)q * r;
-        for (int i = tid; i < rows; i += JT) {
-          const double x = __ldcg(&mp[i]), y = __ldcg(&mq[i]);
-          __stcg(&mp[i], c * x - sn * y);
-          __stcg(&mq[i], sn * x + c * y);
-        }
-        for (int i = tid; i < r; i += JT) {
-          const double u = __ldcg(&wp[i]), v = __ldcg(&wq[i]);
-          __stcg(&wp[i], c * u - sn * v);
-          __stcg(&wq[i], sn * u + c * v);
-        }
-        if (tid == 0) *reinterpret_cast<volatile int*>(&rotated[sweep]) = 1;
       }
-      if (!grid_barrier(bar, nblocks, status)) return;
+      cluster_sync_all();
     }
-    if (*reinterpret_cast<volatile int*>(&rotated[sweep]) == 0) { converged = true; break; }
+    if (__ldcg(&rotated[sweep]) == 0) { converged = true; break; }
   }
   if (blockIdx.x != 0) return;
   if (!converged) dev_set_status(status, DEV_NO_CONVERGE);
   if (tid == 0) *sweeps_out = sweep + (converged ? 1 : 0);
   // column norms, stable descending order, normalised outputs
   extern __shared__ double sh[];  // sigma_c for c < r
-  for (int c = tid; c < r; c += JT) {
+  for (int c = tid; c < r; c += nthr) {
     double s2 = 0.0;
     for (int i = 0; i < rows; ++i) { const double x = __ldcg(&M[(int64_t)c * rows + i]); s2 += x * x; }
     sh[c] = sqrt(s2);
   }
   __syncthreads();
-  for (int c = tid; c < r; c += JT) {
+  for (int c = tid; c < r; c += nthr) {
     const double sc = sh[c];
     int rank = 0;
     for (int d = 0; d < r; ++d) rank += (sh[d] > sc) || (sh[d] == sc && d < c);
@@ -156,9 +180,116 @@ jacobi_kernel(int rows, int r, const double* __restrict__ Min, double* M, double
   }
 }
 
+// FP32 one-sided Jacobi in one CTA with M and W in shared memory: the cheap
+// first phase.  Its rotations are accumulated in W32 (column-major), which the
+// FP64 phase then orthonormalises and applies to M before finishing in FP64.
+constexpr int kF32MaxR = 160;
+constexpr int kF32PerLane = (kF32MaxR + 15) / 16;  // a half-warp holds a column
+
+__device__ __forceinline__ float half_warp_sum(float v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// FP32 one-sided Jacobi in one CTA with M and W in shared memory: the cheap
+// first phase.  Each half-warp rotates one column pair, so the 64 half-warps
+// of the CTA cover every pair of a round for r <= 128 at once.  The rotations
+// are accumulated in W32 (column-major), which the FP64 phase then
+// orthonormalises and applies to M before finishing in FP64.
+__global__ void __launch_bounds__(1024)
+jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32, int* sweeps_out) {
+  extern __shared__ __align__(16) float smf[];
+  float* M = smf;
+  float* W = smf + r * r;
+  __shared__ float redf[32];
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, warps = nt >> 5;
+  const int hw = tid >> 4, hl = tid & 15, nhw = nt >> 4;  // half-warp index, lane in it
+  const int rp = r + (r & 1), npairs = rp / 2;
+  float f = 0.f;
+  for (int e = tid; e < r * r; e += nt) {
+    const float v = (float)Mc[e];
+    M[e] = v;
+    W[e] = (e / r) == (e % r) ? 1.f : 0.f;
+    f = fmaf(v, v, f);
+  }
+  f = warp_sum(f);
+  if (lane == 0) redf[warp] = f;
+  __syncthreads();
+  float fro2 = 0.f;
+  for (int i = 0; i < warps; ++i) fro2 += redf[i];
+  const float eps = 1.1920929e-7f;
+  const float zero2 = ((float)r * eps) * ((float)r * eps) * fro2;
+  const float tol = (float)r * eps;
+  int sweep = 0;
+  for (; sweep < kJacobiMaxSweeps; ++sweep) {
+    __syncthreads();
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < rp - 1; ++round) {
+      // every half-warp takes the same number of iterations (shuffles need the full warp)
+      for (int s0 = 0; s0 < npairs; s0 += nhw) {
+        const int s = s0 + hw;
+        int p = 0, q = 0;
+        bool active = s < npairs;
+        if (active) {
+          p = rr_column(s, round, rp);
+          q = rr_column(rp - 1 - s, round, rp);
+          if (p >= r || q >= r) active = false;
+          if (p > q) { const int t = p; p = q; q = t; }
+        }
+        float xv[kF32PerLane], yv[kF32PerLane];
+        float a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+        for (int t = 0; t < kF32PerLane; ++t) {
+          const int i = hl + 16 * t;
+          const bool ok = active && i < r;
+          xv[t] = ok ? M[p * r + i] : 0.f;
+          yv[t] = ok ? M[q * r + i] : 0.f;
+          a = fmaf(xv[t], xv[t], a); b = fmaf(yv[t], yv[t], b); g = fmaf(xv[t], yv[t], g);
+        }
+        a = half_warp_sum(a); b = half_warp_sum(b); g = half_warp_sum(g);
+        if (active && fabsf(g) > tol * sqrtf(a * b) && a > zero2 && b > zero2) {
+          const float zeta = (b - a) / (2.f * g);
+          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
+          const float c = 1.f / sqrtf(1.f + t * t);
+          const float sn = c * t;
+#pragma unroll
+          for (int u = 0; u < kF32PerLane; ++u) {
+            const int i = hl + 16 * u;
+            if (i < r) {
+              M[p * r + i] = c * xv[u] - sn * yv[u];
+              M[q * r + i] = sn * xv[u] + c * yv[u];
+              const float wu = W[p * r + i], wv = W[q * r + i];
+              W[p * r + i] = c * wu - sn * wv;
+              W[q * r + i] = sn * wu + c * wv;
+            }
+          }
+          if (hl == 0) s_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!s_rot) break;
+  }
+  for (int e = tid; e < r * r; e += nt) W32[e] = W[e];
+  if (tid == 0) *sweeps_out = sweep + 1;
+}
+
+__global__ void ns_shift_kernel(int r, const double* __restrict__ P, double* __restrict__ T) {
+  // T = 1.5 I - 0.5 P
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x)
+    T[e] = ((e / r) == (e % r) ? 1.5 : 0.0) - 0.5 * P[e];
+}
+
+__global__ void widen_kernel(int n, const float* __restrict__ in, double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) out[e] = (double)in[e];
+}
+
 }  // namespace
 
-size_t jacobi_ws_bytes(int64_t rows, int r) {
+size_t jacobi_ws_bytes(int64_t rows, int r, bool precondition) {
   Sizer s;
   s.take<double>((size_t)rows * r);
   s.take<double>((size_t)r * r);
@@ -166,10 +297,15 @@ size_t jacobi_ws_bytes(int64_t rows, int r) {
   s.take<int>(kJacobiMaxSweeps);
   s.take<int>(1);
   s.take<int>(1);
+  if (precondition) {
+    s.take<float>((size_t)r * r);               // W32
+    s.take<double>((size_t)4 * r * r);          // W64, P, T, M64
+    s.take<double>((size_t)32 * r * r);         // split-K partials of the small GEMMs
+  }
   return s.used + 256;
 }
 
-JacobiWs jacobi_ws_carve(Carver& c, int64_t rows, int r) {
+JacobiWs jacobi_ws_carve(Carver& c, int64_t rows, int r, bool precondition) {
   JacobiWs w;
   w.M = c.take<double>((size_t)rows * r);
   w.W = c.take<double>((size_t)r * r);
@@ -177,43 +313,108 @@ JacobiWs jacobi_ws_carve(Carver& c, int64_t rows, int r) {
   w.rotated = c.take<int>(kJacobiMaxSweeps);
   w.sweeps = c.take<int>(1);
   w.status = c.take<int>(1);
+  if (precondition) {
+    w.W32 = c.take<float>((size_t)r * r);
+    double* d = c.take<double>((size_t)4 * r * r);
+    if (d) { w.W64 = d; w.P = d + (size_t)r * r; w.T = d + 2 * (size_t)r * r; w.M64 = d + 3 * (size_t)r * r; }
+    w.gemm_partial = c.take<double>((size_t)32 * r * r);
+  }
   return w;
 }
+
+namespace {
+
+// C (r x r, FP64) = op(A) B with the K range split over up to 32 CTAs (one
+// 128 x 128 output tile each), partials added in order.
+rsvd_status small_gemm64(int r, const double* A, bool transA, const double* B, double* C, double* partial,
+                         cudaStream_t stream) {
+  int nsplit = (int)cdiv(r, 8);
+  if (nsplit > 32) nsplit = 32;
+  const int64_t kchunk = round_up(cdiv(r, nsplit), 4);
+  nsplit = (int)cdiv(r, kchunk);
+  return simt_gemm<double>(r, r, r, A, r, transA, B, r, C, r, false, nsplit, kchunk, partial, stream);
+}
+
+rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const double* W0, double* sigma, double* U,
+                                  double* W, const JacobiWs& ws, cudaStream_t stream) {
+  RSVD_CUDA(cudaMemsetAsync(ws.rotated, 0, kJacobiMaxSweeps * sizeof(int), stream));
+  const int rp = r + (r & 1);
+  const int npairs = rp / 2;
+  // FP64 work per round is spread over up to 16 SMs (a non-portable cluster
+  // size); fall back to smaller clusters where the device refuses it.
+  int ncta = (int)cdiv(npairs, 4);
+  if (ncta > 16) ncta = 16;
+  if (ncta < 1) ncta = 1;
+  const size_t smem = (size_t)r * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    RSVD_CUDA(cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    attr_set = true;
+  }
+  for (;;) {
+    const int warps = (int)cdiv(npairs, ncta);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ncta);
+    cfg.blockDim = dim3(32 * warps);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ncta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    const cudaError_t qe = cudaOccupancyMaxActiveClusters(&clusters, jacobi_cluster_kernel, &cfg);
+    if ((qe != cudaSuccess || clusters < 1) && ncta > 1) {
+      (void)cudaGetLastError();
+      ncta = ncta > 8 ? 8 : ncta / 2;
+      continue;
+    }
+    RSVD_CUDA(cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, rows, r, Min, W0, ws.M, ws.W, ws.rotated, ws.sweeps,
+                                 ws.status, sigma, U, W));
+    RSVD_CUDA(after_launch());
+    return RSVD_OK;
+  }
+}
+
+}  // namespace
 
 rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double* U, double* W,
                        const JacobiWs& ws, cudaStream_t stream) {
   if (r <= 0) return RSVD_OK;
-  RSVD_CUDA(cudaMemsetAsync(ws.barrier, 0, 2 * sizeof(unsigned), stream));
-  RSVD_CUDA(cudaMemsetAsync(ws.rotated, 0, kJacobiMaxSweeps * sizeof(int), stream));
-  const int rp = r + (r & 1);
-  int nblocks = rp / 2;
-  if (nblocks > 128) nblocks = 128;
-  if (nblocks < 1) nblocks = 1;
-  const size_t smem = (size_t)r * sizeof(double);
-  int dev = 0, coop = 0, per_sm = 0, sms = 0;
-  RSVD_CUDA(cudaGetDevice(&dev));
-  RSVD_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  RSVD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  RSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JT, smem));
-  if (!coop || per_sm * sms < nblocks) nblocks = 1;  // a single CTA never waits on another
-  int rows_ = rows, r_ = r;
-  const double* Min = Mc;
-  double* Mw = ws.M;
-  double* Ww = ws.W;
-  unsigned* bar = ws.barrier;
-  int* rot = ws.rotated;
-  int* sw = ws.sweeps;
-  int* st = ws.status;
-  void* args[] = {&rows_, &r_, &Min, &Mw, &Ww, &bar, &rot, &sw, &st, &sigma, &U, &W};
-  if (nblocks > 1) {
-    RSVD_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(nblocks), dim3(JT), args,
-                                          smem, stream));
-    RSVD_CUDA(after_launch());
-  } else {
-    jacobi_kernel<<<1, JT, smem, stream>>>(rows_, r_, Min, Mw, Ww, bar, rot, sw, st, sigma, U, W);
-    RSVD_CUDA(after_launch());
+  if (rows != r || r > kF32MaxR || r < 8 || !ws.W32) return launch_cluster_jacobi(rows, r, Mc, nullptr, sigma, U, W, ws, stream);
+  // Phase 1: FP32 sweeps to FP32 convergence, one CTA, shared memory.
+  static bool attr = false;
+  if (!attr) {
+    RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   2 * kF32MaxR * kF32MaxR * (int)sizeof(float)));
+    attr = true;
   }
-  return RSVD_OK;
+  jacobi_f32_kernel<<<1, 1024, 2 * (size_t)r * r * sizeof(float), stream>>>(r, Mc, ws.W32, ws.sweeps);
+  RSVD_CUDA(after_launch());
+  // Phase 2: Newton-Schulz steps make W orthogonal to FP64 accuracy:
+  // W' = (1.5 I - 0.5 W W^T) W, i.e. on the column-major storage (= W^T row-major)
+  // Wt' = Wt (1.5 I - 0.5 P) with P = Wt^T Wt.  The accumulated FP32 rotation
+  // is orthogonal to about 1e-6; each step squares that error, so two steps
+  // reach FP64 rounding.
+  widen_kernel<<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r * r, ws.W32, ws.T);
+  RSVD_CUDA(after_launch());
+  for (int step = 0; step < 2; ++step) {
+    double* src = step == 0 ? ws.T : ws.W64;
+    double* dst = step == 0 ? ws.W64 : ws.T;
+    RSVD_TRY(small_gemm64(r, src, true, src, ws.P, ws.gemm_partial, stream));
+    ns_shift_kernel<<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r, ws.P, ws.P);
+    RSVD_CUDA(after_launch());
+    RSVD_TRY(small_gemm64(r, src, false, ws.P, dst, ws.gemm_partial, stream));
+  }
+  // the orthonormalised rotation is now in T; move it to W64
+  RSVD_CUDA(cudaMemcpyAsync(ws.W64, ws.T, sizeof(double) * (size_t)r * r, cudaMemcpyDeviceToDevice, stream));
+  // M64 = M W': column-major M64 = Wt' (row-major) times Mc viewed row-major.
+  RSVD_TRY(small_gemm64(r, ws.W64, false, Mc, ws.M64, ws.gemm_partial, stream));
+  // Phase 3: FP64 sweeps to convergence, starting from the rotated matrix.
+  return launch_cluster_jacobi(rows, r, ws.M64, ws.W64, sigma, U, W, ws, stream);
 }
 
 }  // namespace rsvd

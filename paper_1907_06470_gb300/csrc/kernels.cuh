@@ -25,6 +25,13 @@ rsvd_status simt_gemm(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, 
                       const T* B, int64_t ldb, T* C, int64_t ldc, bool accumulate, int nsplit,
                       int64_t kchunk, T* partial, cudaStream_t stream);
 
+// The GEMM of simt_gemm without the final reduction: partial z (the K chunk
+// [z*kchunk, (z+1)*kchunk)) is written to partial + z*M*N (M x N, ld N).
+template <typename T>
+rsvd_status simt_gemm_partials(int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, bool transA,
+                               const T* B, int64_t ldb, int nsplit, int64_t kchunk, T* partial,
+                               cudaStream_t stream);
+
 // out[i, j] (+)= sum_z P[z*pstride + i*ldp + j], z in increasing order.
 template <typename T>
 rsvd_status reduce_partials(int64_t M, int64_t N, int nsplit, const T* P, int64_t ldp, int64_t pstride, T* out,
@@ -36,10 +43,11 @@ struct OrthWs {
   double* L1 = nullptr;       // r x r Cholesky factors (lower, FP64)
   double* L2 = nullptr;
   double* Rinv = nullptr;     // r x r upper inverse (FP64)
+  double* Awork = nullptr;    // r x r Cholesky working copy when it does not fit in shared memory
   int* dead1 = nullptr;       // deflated pivots of the two sweeps (r each)
   int* dead2 = nullptr;
   void* Rinv_t = nullptr;     // the same in the panel dtype
-  double* gram_partial = nullptr;
+  void* gram_partial = nullptr;     // chunk partial Grams in the panel type
   int64_t gram_chunks = 0;
   void* tmp = nullptr;        // M x r panel (first-sweep result)
   int64_t ld_tmp = 0;
@@ -60,10 +68,18 @@ struct JacobiWs {
   int* rotated = nullptr;     // one flag per sweep
   int* sweeps = nullptr;      // sweeps used
   int* status = nullptr;
+  float* W32 = nullptr;       // FP32-phase rotations (r x r)
+  double* W64 = nullptr;      // orthonormalised rotations
+  double* P = nullptr;        // Newton-Schulz Gram / shift
+  double* T = nullptr;        // widened W32
+  double* M64 = nullptr;      // M times the rotations
+  double* gemm_partial = nullptr;
 };
 constexpr int kJacobiMaxSweeps = 64;
-size_t jacobi_ws_bytes(int64_t rows, int r);
-JacobiWs jacobi_ws_carve(Carver& c, int64_t rows, int r);
+// `precondition` adds the buffers of the FP32 first phase (without them the
+// FP64 sweeps run from the start).
+size_t jacobi_ws_bytes(int64_t rows, int r, bool precondition = true);
+JacobiWs jacobi_ws_carve(Carver& c, int64_t rows, int r, bool precondition = true);
 // Mc column-major rows x r; outputs sigma (r), U (rows x r) and W (r x r)
 // row-major with columns ordered like sigma (descending).
 rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double* U, double* W,

@@ -61,7 +61,7 @@ extern "C" rsvd_status rsvd_small_svd_noalloc(int32_t r, const double* Mc, doubl
   void* base = nullptr;
   RSVD_TRY(scratch_address(&base));
   Carver c(base, kScratchBytes);
-  JacobiWs w = jacobi_ws_carve(c, r, r);
+  JacobiWs w = jacobi_ws_carve(c, r, r, /*precondition=*/false);
   if (c.overflow) return fail(RSVD_ERR_INVALID_ARG, "rsvd_small_svd_noalloc: scratch layout overflow");
   cudaStream_t st = as_stream(stream);
   // the status word must start at zero; jacobi_svd clears the barrier and flags
