@@ -140,6 +140,23 @@ rsvd_status rsvd_run(rsvd_plan_t plan, const rsvd_matrix* A, void* U, void* S, v
  * device workspace.  Synchronises `stream`. */
 rsvd_status rsvd_full(const rsvd_matrix* A, void* U, void* S, void* V, void* stream);
 
+/* Backward pass (no counterpart in the paper): the adjoint of the rank-k
+ * truncated SVD (Townsend, "Differentiating the Singular Value
+ * Decomposition", 2016) evaluated at U, S, V as returned by rsvd_run on this
+ * plan.  With F_ij = 1/(S_j^2 - S_i^2) (i != j; 0 on the diagonal and for
+ * S_i^2, S_j^2 equal to within 1e-12 S_max^2),
+ *   dA = U M V^T + (I - U U^T) dU S^-1 V^T + U S^-1 dV^T (I - V V^T),
+ *   M  = (F o (U^T dU - dU^T U)) S + diag(dS) + S (F o (V^T dV - dV^T V)).
+ * The projector terms treat the discarded spectrum as zero: this is the exact
+ * derivative when A has rank k (or k = min(m, n)), and the usual truncated
+ * approximation otherwise.  The range finder is not differentiated.
+ * Inputs (device, plan dtype): U m x k, S k, V n x k, and the cotangents
+ * dU m x k, dS k, dV n x k, any of which may be NULL (zero).  Output dA: m x n
+ * row-major (leading dimension n), overwritten.  Uses the plan's workspace;
+ * enqueues only.  Errors: INVALID_ARG. */
+rsvd_status rsvd_backward(rsvd_plan_t plan, const void* U, const void* S, const void* V,
+                          const void* dU, const void* dS, const void* dV, void* dA, void* stream);
+
 void rsvd_destroy(rsvd_plan_t plan);
 
 /* ---- Tracing (Section 4.1 stage breakdown) ----------------------------------- */

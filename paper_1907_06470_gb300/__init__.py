@@ -104,6 +104,17 @@ class Plan:
                                C.c_void_p(V.data_ptr()), _stream_ptr()))
         return U, S, V
 
+    def backward(self, U, S, V, dU=None, dS=None, dV=None):
+        """dA of the truncated SVD (see rsvd_backward) for cotangents dU, dS, dV (None = zero)."""
+        torch = _torch()
+        dA = torch.empty(self.m, self.n, dtype=U.dtype, device=U.device)
+        p = lambda t: C.c_void_p(t.contiguous().data_ptr() if t is not None else None)
+        keep = [t.contiguous() if t is not None else None for t in (U, S, V, dU, dS, dV)]
+        ptrs = [C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(None) for t in keep]
+        _check(load().rsvd_backward(self._h, *ptrs, C.c_void_p(dA.data_ptr()), _stream_ptr()))
+        del p
+        return dA
+
     def set_profiling(self, on=True):
         _check(load().rsvd_plan_set_profiling(self._h, 1 if on else 0))
 
@@ -128,11 +139,41 @@ class Plan:
             pass
 
 
+def _rsvd_function():
+    torch = _torch()
+
+    class RSVDFunction(torch.autograd.Function):
+        """U, S, V = rsvd(A); backward through the truncated-SVD adjoint (rsvd_backward).
+
+        The range finder is not differentiated: the gradient is that of the
+        truncated SVD evaluated at the returned factors.
+        """
+
+        @staticmethod
+        def forward(ctx, A, plan):
+            U, S, V = plan.run(A.detach())
+            ctx.plan = plan
+            ctx.save_for_backward(U, S, V)
+            return U, S, V
+
+        @staticmethod
+        def backward(ctx, dU, dS, dV):
+            U, S, V = ctx.saved_tensors
+            return ctx.plan.backward(U, S, V, dU, dS, dV), None
+
+    return RSVDFunction
+
+
 def rsvd(A, k, p=10, q=2, seed=0, mem_cap=0, prec=None, mb=0, nb=0, refine=True):
-    """Rank-k randomized SVD of a dense float32/float64 matrix (CUDA or pinned host tensor)."""
+    """Rank-k randomized SVD of a dense float32/float64 matrix (CUDA or pinned host tensor).
+
+    If A requires grad, the result is differentiable through the truncated-SVD
+    adjoint (rsvd_backward)."""
     torch = _torch()
     dtype = "f64" if A.dtype == torch.float64 else "f32"
     plan = Plan(A.shape[0], A.shape[1], k, p, q, seed, mem_cap, prec, dtype, mb, nb, refine)
+    if A.requires_grad:
+        return _rsvd_function().apply(A, plan)
     try:
         return plan.run(A)
     finally:

@@ -53,6 +53,7 @@ SIGNATURES = {
     "rsvd_run": (c_i32, [c_vp, C.POINTER(RsvdMatrix), c_vp, c_vp, c_vp, c_vp]),
     "rsvd_full": (c_i32, [C.POINTER(RsvdMatrix), c_vp, c_vp, c_vp, c_vp]),
     "rsvd_destroy": (None, [c_vp]),
+    "rsvd_backward": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "rsvd_status_str": (C.c_char_p, [c_i32]),
     "rsvd_last_error": (C.c_char_p, []),
     "rsvd_plan_set_profiling": (c_i32, [c_vp, c_i32]),

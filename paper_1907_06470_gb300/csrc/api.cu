@@ -200,6 +200,8 @@ struct rsvd_plan_s {
   void* WRk = nullptr;      // r x k in dtype
   void* sign_scratch = nullptr;
   size_t sign_scratch_bytes = 0;
+  void* bwd_ws = nullptr;   // backward pass (rsvd_backward)
+  size_t bwd_ws_bytes = 0;
   int* status = nullptr;
   void* Adev = nullptr;     // device copy of a host-resident A
   Profiler prof;
@@ -269,6 +271,8 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   P->WRk = c.take<char>((size_t)P->r * P->k * esz);
   P->sign_scratch_bytes = sign_scratch_bytes(P->m, P->k);
   P->sign_scratch = c.take<char>(P->sign_scratch_bytes);
+  P->bwd_ws_bytes = backward_ws_bytes(P->m, P->n, P->k, P->dtype);
+  P->bwd_ws = c.take<char>(P->bwd_ws_bytes);
   P->status = c.take<int>(4);
   if (base) {
     P->orth.status = P->status;
@@ -537,6 +541,21 @@ rsvd_status rsvd_plan_stage_ms(rsvd_plan_t P, double* ms, int32_t* apass_calls) 
 }
 
 unsigned long long rsvd_kernel_launches(void) { return g_launches.load(); }
+
+rsvd_status rsvd_backward(rsvd_plan_t P, const void* U, const void* S, const void* V, const void* dU,
+                          const void* dS, const void* dV, void* dA, void* stream) {
+  if (!P || !U || !S || !V || !dA) return fail(RSVD_ERR_INVALID_ARG, "rsvd_backward: NULL argument");
+  cudaStream_t st = as_stream(stream);
+  if (P->dtype == RSVD_F64)
+    return backward_typed<double>(P->m, P->n, P->k, static_cast<const double*>(U), static_cast<const double*>(S),
+                                  static_cast<const double*>(V), static_cast<const double*>(dU),
+                                  static_cast<const double*>(dS), static_cast<const double*>(dV),
+                                  static_cast<double*>(dA), P->bwd_ws, P->bwd_ws_bytes, st);
+  return backward_typed<float>(P->m, P->n, P->k, static_cast<const float*>(U), static_cast<const float*>(S),
+                               static_cast<const float*>(V), static_cast<const float*>(dU),
+                               static_cast<const float*>(dS), static_cast<const float*>(dV),
+                               static_cast<float*>(dA), P->bwd_ws, P->bwd_ws_bytes, st);
+}
 
 void rsvd_destroy(rsvd_plan_t P) {
   if (!P) return;

@@ -98,6 +98,12 @@ template <typename T>
 rsvd_status gather_colmajor_f64(int64_t rows, int64_t cols, const T* A, int64_t s_row, int64_t s_col,
                                 double* out, cudaStream_t stream);
 
+// adjoint.cu -- backward pass of the truncated SVD.
+size_t backward_ws_bytes(int64_t m, int64_t n, int k, int dtype);
+template <typename T>
+rsvd_status backward_typed(int64_t m, int64_t n, int k, const T* U, const T* S, const T* V, const T* dU,
+                           const T* dS, const T* dV, T* dA, void* ws, size_t ws_bytes, cudaStream_t st);
+
 // api.cu -- A-pass dispatch.
 size_t apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t mb, int64_t nb);
 rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const void* X, int64_t ldx,
