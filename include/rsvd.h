@@ -125,6 +125,14 @@ rsvd_status rsvd_plan_info(rsvd_plan_t plan, rsvd_plan_info_t* out);
 
 /* Run the planned randomized SVD on A (Section 2.1 steps 1-7 with Eq. (3)).
  * A: dense (device or pinned host) with dtype equal to the plan's dtype.
+ * A host A is copied to the device and processed in core when the plan has no
+ * cap or the copy fits under it; otherwise it is processed out of core: its
+ * block-cyclic tiles (edges opts.mb x opts.nb, default 8192, shrunk to fit)
+ * are streamed from host memory through opts.n_slots device buffers on a side
+ * stream, overlapped with the tile products, and the tiles that fit in the
+ * rest of the cap stay resident for the later passes of the run (Section 3.5,
+ * Section 3.7).  Streaming needs A in pinned host memory for the copies to
+ * overlap.
  * Outputs (device, plan dtype): U m x k row-major, S k values descending,
  * V n x k row-major, so that A ~ U diag(S) V^T.  Each pair (u_i, v_i) is signed
  * so that the largest-magnitude entry of u_i is positive.  Synchronises
@@ -184,6 +192,13 @@ rsvd_status rsvd_plan_set_profiling(rsvd_plan_t plan, int32_t enable);
 /* Times (ms, summed per stage) of the last profiled rsvd_run: `ms` receives
  * RSVD_STAGE_COUNT values; *apass_calls (may be NULL) the number of A-passes. */
 rsvd_status rsvd_plan_stage_ms(rsvd_plan_t plan, double* ms, int32_t* apass_calls);
+
+/* Out-of-core statistics of the last rsvd_run (all zero when it ran in core):
+ * bytes copied host-to-device, tiles streamed per A-pass, and tiles kept
+ * resident in device memory across the passes of the run.  Any pointer may be
+ * NULL. */
+rsvd_status rsvd_plan_stream_stats(rsvd_plan_t plan, uint64_t* h2d_bytes, int64_t* tiles_streamed_per_pass,
+                                   int64_t* tiles_resident);
 
 /* Number of CUDA kernels this library has launched in this process so far. */
 unsigned long long rsvd_kernel_launches(void);

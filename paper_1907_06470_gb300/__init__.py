@@ -115,6 +115,12 @@ class Plan:
         del p
         return dA
 
+    def stream_stats(self) -> dict:
+        """Out-of-core statistics of the last run (zeros when it ran in core)."""
+        h2d, per_pass, resident = C.c_uint64(), C.c_int64(), C.c_int64()
+        _check(load().rsvd_plan_stream_stats(self._h, C.byref(h2d), C.byref(per_pass), C.byref(resident)))
+        return {"h2d_bytes": h2d.value, "tiles_streamed_per_pass": per_pass.value, "tiles_resident": resident.value}
+
     def set_profiling(self, on=True):
         _check(load().rsvd_plan_set_profiling(self._h, 1 if on else 0))
 

@@ -59,6 +59,7 @@ SIGNATURES = {
     "rsvd_plan_set_profiling": (c_i32, [c_vp, c_i32]),
     "rsvd_plan_stage_ms": (c_i32, [c_vp, C.POINTER(C.c_double), C.POINTER(c_i32)]),
     "rsvd_kernel_launches": (C.c_ulonglong, []),
+    "rsvd_plan_stream_stats": (c_i32, [c_vp, C.POINTER(c_u64), C.POINTER(c_i64), C.POINTER(c_i64)]),
     "rsvd_gaussian": (c_i32, [c_u64, c_i64, c_i64, c_i32, c_i32, c_vp, c_i64, c_vp]),
     "rsvd_tile_map": (c_i32, [c_i64, c_i64, c_i64, c_i64, c_i32, C.POINTER(RsvdTile), c_i64, C.POINTER(c_i64)]),
     "rsvd_apass_workspace": (c_size, [c_i64, c_i64, c_i32, c_i32, c_i32, c_i64, c_i64]),

@@ -92,7 +92,7 @@ size_t apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t 
 
 rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const void* X, int64_t ldx,
                         void* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws, size_t ws_bytes,
-                        int* status, cudaStream_t stream) {
+                        int* status, cudaStream_t stream, bool accumulate) {
   if (A.kind != RSVD_DENSE || A.location != RSVD_ON_DEVICE)
     return fail(RSVD_ERR_INVALID_ARG, "apass: A must be a dense device matrix");
   if (ws_bytes < apass_ws_bytes(A.m, A.n, r, trans, prec, mb, nb))
@@ -101,19 +101,19 @@ rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const 
   if (prec == RSVD_PREC_FP64) {
     if (A.dtype != RSVD_F64) return fail(RSVD_ERR_INVALID_ARG, "apass: FP64 precision needs FP64 A");
     return simt_gemm<double>(s.M, r, s.K, static_cast<const double*>(A.data), A.ld, trans != 0,
-                             static_cast<const double*>(X), ldx, static_cast<double*>(Y), ldy, false,
+                             static_cast<const double*>(X), ldx, static_cast<double*>(Y), ldy, accumulate,
                              s.nsplit, s.kchunk, static_cast<double*>(ws), stream);
   }
   if (A.dtype != RSVD_F32) return fail(RSVD_ERR_INVALID_ARG, "apass: FP32/BF16 precision needs FP32 A");
   if (prec == RSVD_PREC_FP32) {
     return simt_gemm<float>(s.M, r, s.K, static_cast<const float*>(A.data), A.ld, trans != 0,
-                            static_cast<const float*>(X), ldx, static_cast<float*>(Y), ldy, false,
+                            static_cast<const float*>(X), ldx, static_cast<float*>(Y), ldy, accumulate,
                             s.nsplit, s.kchunk, static_cast<float*>(ws), stream);
   }
   if (prec != RSVD_PREC_BF16 && prec != RSVD_PREC_BF16X3)
     return fail(RSVD_ERR_INVALID_ARG, "apass: unknown precision");
   return tc_apass_from_f32(A, trans, prec, r, static_cast<const float*>(X), ldx,
-                           static_cast<float*>(Y), ldy, mb, nb, ws, ws_bytes, status, stream);
+                           static_cast<float*>(Y), ldy, mb, nb, ws, ws_bytes, status, stream, accumulate);
 }
 
 }  // namespace rsvd
@@ -204,6 +204,9 @@ struct rsvd_plan_s {
   size_t bwd_ws_bytes = 0;
   int* status = nullptr;
   void* Adev = nullptr;     // device copy of a host-resident A
+  int64_t mb_req = 0, nb_req = 0;  // tile edges asked for in the options (0: none)
+  StreamState* ss = nullptr;       // out-of-core state (created on the first streamed run)
+  bool streaming = false;          // the current run streams A from the host
   Profiler prof;
 };
 
@@ -235,6 +238,8 @@ void apply_opts(rsvd_plan_s* P, const rsvd_opts* o) {
     P->refine = o->refine;
     P->mb = o->mb;
     P->nb = o->nb;
+    P->mb_req = o->mb;
+    P->nb_req = o->nb;
     P->n_slots = o->n_slots > 0 ? o->n_slots : 2;
   }
   if (P->mb <= 0) P->mb = P->m;  // in core: one block row unless asked otherwise
@@ -296,6 +301,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   auto apass = [&](int trans, int pr, const T* Xin, T* Yout) -> rsvd_status {
     Span sp(pf, trans ? RSVD_STAGE_APASS_TRANS : RSVD_STAGE_APASS_FWD, st);
     ++pf.apass_calls;
+    if (P->streaming) return apass_streamed(P->ss, A, trans, pr, r, Xin, Yout, ldr, P->status, st);
     return apass_dense(A, trans, pr, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes,
                        P->status, st);
   };
@@ -500,12 +506,24 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
   cudaStream_t st = as_stream(stream);
   rsvd_matrix Ad = *A;
   P->prof.begin();
+  P->streaming = false;
   if (A->location == RSVD_ON_HOST) {
-    // Automatic in-core switch (Section 3.5): a host matrix that fits under the
-    // cap is copied to the device once and processed in core.
+    // Automatic in-core / out-of-core switch (Section 3.5): a host matrix that
+    // fits under the cap (or any host matrix when there is no cap) is copied to
+    // the device once and processed in core; otherwise its tiles are streamed.
     const size_t bytes = (size_t)A->m * A->n * elem_size(A->dtype);
-    if (P->mem_cap && P->ws_bytes + bytes > P->mem_cap)
-      return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: host matrix larger than mem_cap needs streaming");
+    if (P->mem_cap && P->ws_bytes + bytes > P->mem_cap) {
+      if (P->Adev) { cudaFree(P->Adev); P->Adev = nullptr; P->a_copy_bytes = 0; }
+      if (P->ws_bytes >= P->mem_cap) return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: no room left for streaming");
+      const int final_prec = (P->prec == RSVD_PREC_BF16 && P->refine) ? RSVD_PREC_BF16X3 : P->prec;
+      RSVD_TRY(stream_prepare(&P->ss, A->m, A->n, elem_size(A->dtype), P->mb_req, P->nb_req, P->n_slots,
+                              P->mem_cap - P->ws_bytes, P->r, P->prec, final_prec));
+      stream_begin_run(P->ss);
+      P->streaming = true;
+      if (P->dtype == RSVD_F64)
+        return run_typed<double>(P, Ad, static_cast<double*>(U), static_cast<double*>(S), static_cast<double*>(V), st);
+      return run_typed<float>(P, Ad, static_cast<float*>(U), static_cast<float*>(S), static_cast<float*>(V), st);
+    }
     if (P->a_copy_bytes < bytes) {
       if (P->Adev) cudaFree(P->Adev);
       P->Adev = nullptr;
@@ -561,7 +579,15 @@ void rsvd_destroy(rsvd_plan_t P) {
   if (!P) return;
   if (P->ws) cudaFree(P->ws);
   if (P->Adev) cudaFree(P->Adev);
+  stream_state_free(P->ss);
   delete P;
+}
+
+rsvd_status rsvd_plan_stream_stats(rsvd_plan_t P, uint64_t* h2d_bytes, int64_t* tiles_streamed_per_pass,
+                                   int64_t* tiles_resident) {
+  if (!P) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_stream_stats: NULL plan");
+  stream_stats(P->streaming ? P->ss : nullptr, h2d_bytes, tiles_streamed_per_pass, tiles_resident);
+  return RSVD_OK;
 }
 
 rsvd_status rsvd_full(const rsvd_matrix* A, void* U, void* S, void* V, void* stream) {

@@ -41,6 +41,7 @@ constexpr int BK = 64;             // K per step: one 128-byte BF16 row
 constexpr int A32_BYTES = BM * BK * 4;
 constexpr int A16_BYTES = BM * BK * 2;
 constexpr int SOP = 2;             // operand (BF16) ring depth
+constexpr int kSplitMaxNP = 192;   // widest split-mode panel one pass supports
 constexpr int THREADS = 320;
 constexpr uint64_t kWaitNs = 1000000000ull;
 
@@ -54,6 +55,7 @@ struct TcArgs {
   int64_t ksteps;       // total K steps
   int64_t ksteps_per_split;
   int nsplit;
+  int accumulate;       // 1: C += result (direct write only, nsplit == 1)
   int s32;              // FP32 staging ring depth
   float* C;
   int64_t ldc;
@@ -300,7 +302,11 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         ptx::tmem_ld_wait();
         if (row < a.M) {
           const int nv = min(32, a.N - c0);
-          if (nv == 32 && (a.ldc & 3) == 0) {
+          if (a.accumulate) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < nv) crow[c0 + j] += __uint_as_float(v[j]);
+          } else if (nv == 32 && (a.ldc & 3) == 0) {
 #pragma unroll
             for (int j = 0; j < 32; j += 4)
               *reinterpret_cast<float4*>(crow + c0 + j) =
@@ -439,14 +445,21 @@ size_t tc_apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64
 }
 
 rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X, int64_t ldx,
-                              float* Y, int64_t ldy, int64_t, int64_t, void* ws, size_t ws_bytes,
-                              int* status, cudaStream_t stream) {
+                              float* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws, size_t ws_bytes,
+                              int* status, cudaStream_t stream, bool accumulate) {
   const bool split = prec == RSVD_PREC_BF16X3;
   if (r < 1 || r > 256) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: r must be in [1, 256]");
+  if (split && round_up(r, 16) > kSplitMaxNP) {
+    // the split-mode operand ring does not fit shared memory for this width:
+    // two passes over column halves of the panel (A is read twice)
+    const int h = (int)round_up(cdiv(r, 2), 16);
+    RSVD_TRY(tc_apass_from_f32(A, trans, prec, h, X, ldx, Y, ldy, mb, nb, ws, ws_bytes, status, stream, accumulate));
+    return tc_apass_from_f32(A, trans, prec, r - h, X + h, ldx, Y + h, ldy, mb, nb, ws, ws_bytes, status, stream,
+                             accumulate);
+  }
   if (A.ld % 4 != 0 || (reinterpret_cast<uintptr_t>(A.data) & 15) != 0)
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: A needs a 16-byte aligned base and ld % 4 == 0");
   const TcShape s = tc_shape(A.m, A.n, r, trans);
-  if (split && s.NP > 192) return fail(RSVD_ERR_UNSUPPORTED, "split-BF16 A-pass supports k + p <= 192");
   Carver c(ws, ws_bytes);
   auto* Xhi = c.take<__nv_bfloat16>((size_t)s.NP * s.ldb);
   __nv_bfloat16* Xlo = split ? c.take<__nv_bfloat16>((size_t)s.NP * s.ldb) : nullptr;
@@ -491,6 +504,7 @@ rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, 
   ta.ksteps = s.ksteps;
   ta.ksteps_per_split = s.ksteps_per_split;
   ta.nsplit = s.nsplit;
+  ta.accumulate = (s.nsplit == 1 && accumulate) ? 1 : 0;
   ta.C = s.nsplit > 1 ? partial : Y;
   ta.ldc = s.nsplit > 1 ? r : ldy;
   ta.c_split_stride = s.nsplit > 1 ? slab : 0;
@@ -516,7 +530,8 @@ rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, 
   } else {
     RSVD_TRY(split ? launch(tc_apass_kernel<false, true>) : launch(tc_apass_kernel<false, false>));
   }
-  if (s.nsplit > 1) RSVD_TRY(reduce_partials<float>(s.M, r, s.nsplit, partial, r, slab, Y, ldy, false, stream));
+  if (s.nsplit > 1)
+    RSVD_TRY(reduce_partials<float>(s.M, r, s.nsplit, partial, r, slab, Y, ldy, accumulate, stream));
   return RSVD_OK;
 }
 

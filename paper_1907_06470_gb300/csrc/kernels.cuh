@@ -104,11 +104,21 @@ template <typename T>
 rsvd_status backward_typed(int64_t m, int64_t n, int k, const T* U, const T* S, const T* V, const T* dU,
                            const T* dS, const T* dV, T* dA, void* ws, size_t ws_bytes, cudaStream_t st);
 
+// stream.cu -- out-of-core A-passes over tiles of a pinned host matrix.
+struct StreamState;
+rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, int64_t mb_req, int64_t nb_req,
+                           int slots, size_t budget, int r, int prec, int final_prec);
+void stream_begin_run(StreamState* s);
+rsvd_status apass_streamed(StreamState* s, const rsvd_matrix& Ah, int trans, int prec, int r, const void* X,
+                           void* Y, int64_t ldr, int* status, cudaStream_t st);
+void stream_state_free(StreamState* s);
+void stream_stats(const StreamState* s, uint64_t* h2d, int64_t* per_pass, int64_t* cached);
+
 // api.cu -- A-pass dispatch.
 size_t apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t mb, int64_t nb);
 rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const void* X, int64_t ldx,
                         void* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws, size_t ws_bytes,
-                        int* status, cudaStream_t stream);
+                        int* status, cudaStream_t stream, bool accumulate = false);
 
 // gemm_tc.cu -- tensor-core (tcgen05) A-passes on FP32 A with in-kernel BF16 conversion.
 size_t tc_apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t mb, int64_t nb);
@@ -116,6 +126,6 @@ size_t tc_apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64
 // pipeline wait expires.
 rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X,
                               int64_t ldx, float* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws,
-                              size_t ws_bytes, int* status, cudaStream_t stream);
+                              size_t ws_bytes, int* status, cudaStream_t stream, bool accumulate = false);
 
 }  // namespace rsvd

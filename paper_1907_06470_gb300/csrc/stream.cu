@@ -1,0 +1,182 @@
+// Out-of-core A-passes (Section 3.5 in-core / out-of-core switching, Section
+// 3.7 I/O overlapped with compute) for a dense A held in pinned host memory.
+//
+// The tiles of the block-cyclic map (Section 3.1) are visited in order
+// t = I*Tn + J.  Tile t is copied with cudaMemcpy2DAsync on a side stream into
+// device slot t mod S (S slots: double buffering for S = 2), the compute
+// stream waits for that copy's event, multiplies the tile into the panel
+// (Y[I] += A[I,J] X[J] forward, Z[J] += A[I,J]^T Y[I] transposed, in tile
+// order, so the sums do not depend on timing), and records the slot's "free"
+// event that the next copy into the slot waits for.  Tiles that fit in the
+// device memory left under the cap after the workspace and the slots stay
+// resident after their first copy of a run (the resident cache), so later
+// passes of the same run stream only the rest.
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rsvd {
+
+struct StreamState {
+  int S = 2;
+  int64_t mb = 0, nb = 0, ld_tile = 0;
+  size_t tile_bytes = 0;
+  std::vector<void*> slot;
+  std::vector<void*> cache;          // resident copies of tiles 0 .. ncache-1
+  std::vector<char> cache_valid;     // filled during the current run
+  std::vector<cudaEvent_t> copied;   // per slot
+  std::vector<cudaEvent_t> freed;    // per slot
+  std::vector<cudaEvent_t> cache_ev; // per cached tile
+  cudaStream_t copy = nullptr;
+  uint64_t h2d_bytes = 0;            // copied during the last run
+  int64_t tiles_per_pass = 0, tiles_cached = 0;
+  size_t device_bytes = 0;
+  void* ws = nullptr;                // A-pass workspace sized for one tile
+  size_t ws_bytes = 0;
+
+  ~StreamState() {
+    for (void* p : slot) cudaFree(p);
+    for (void* p : cache) cudaFree(p);
+    for (auto e : copied) cudaEventDestroy(e);
+    for (auto e : freed) cudaEventDestroy(e);
+    for (auto e : cache_ev) cudaEventDestroy(e);
+    if (copy) cudaStreamDestroy(copy);
+    if (ws) cudaFree(ws);
+  }
+};
+
+void stream_state_free(StreamState* s) { delete s; }
+
+void stream_stats(const StreamState* s, uint64_t* h2d, int64_t* per_pass, int64_t* cached) {
+  if (h2d) *h2d = s ? s->h2d_bytes : 0;
+  if (per_pass) *per_pass = s ? s->tiles_per_pass : 0;
+  if (cached) *cached = s ? s->tiles_cached : 0;
+}
+
+// Build (or reuse) the streaming state for an m x n host matrix of element
+// size esz within `budget` device bytes (the cap minus the plan workspace).
+rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, int64_t mb_req, int64_t nb_req,
+                           int slots, size_t budget, int r, int prec, int final_prec) {
+  int64_t mb = mb_req > 0 ? mb_req : 8192, nb = nb_req > 0 ? nb_req : 8192;
+  if (mb > m) mb = m;
+  if (nb > n) nb = n;
+  if (slots < 1) slots = 2;
+  // shrink the tiles until the slots fit the budget
+  while ((size_t)slots * mb * round_up(nb, 4) * esz > budget && (mb > 16 || nb > 16)) {
+    if (mb >= nb && mb > 16) mb = (mb + 1) / 2;
+    else if (nb > 16) nb = (nb + 1) / 2;
+  }
+  const int64_t ld_tile = round_up(nb, 4);
+  const size_t tile_bytes = (size_t)mb * ld_tile * esz;
+  size_t tws = 0;
+  for (int tr = 0; tr < 2; ++tr)
+    for (int pr : {prec, final_prec}) {
+      const size_t b = apass_ws_bytes(mb, nb, r, tr, pr, 0, 0) + 512;
+      if (b > tws) tws = b;
+    }
+  if ((size_t)slots * tile_bytes + tws > budget)
+    return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: mem_cap leaves no room for the streaming slots");
+  StreamState* s = *ps;
+  if (s && s->mb == mb && s->nb == nb && s->S == slots && s->tile_bytes == tile_bytes) return RSVD_OK;
+  delete s;
+  s = new StreamState();
+  *ps = s;
+  s->S = slots;
+  s->mb = mb;
+  s->nb = nb;
+  s->ld_tile = ld_tile;
+  s->tile_bytes = tile_bytes;
+  RSVD_CUDA(cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking));
+  RSVD_CUDA(cudaMalloc(&s->ws, tws));
+  s->ws_bytes = tws;
+  for (int i = 0; i < slots; ++i) {
+    void* p = nullptr;
+    RSVD_CUDA(cudaMalloc(&p, tile_bytes));
+    s->slot.push_back(p);
+    cudaEvent_t a, b;
+    RSVD_CUDA(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    RSVD_CUDA(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    s->copied.push_back(a);
+    s->freed.push_back(b);
+  }
+  const int64_t ntiles = cdiv(m, mb) * cdiv(n, nb);
+  int64_t ncache = (int64_t)((budget - (size_t)slots * tile_bytes - tws) / tile_bytes);
+  if (ncache > ntiles) ncache = ntiles;
+  for (int64_t t = 0; t < ncache; ++t) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, tile_bytes) != cudaSuccess) {
+      (void)cudaGetLastError();
+      break;
+    }
+    s->cache.push_back(p);
+    cudaEvent_t e;
+    RSVD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    s->cache_ev.push_back(e);
+  }
+  s->cache_valid.assign(s->cache.size(), 0);
+  s->tiles_cached = (int64_t)s->cache.size();
+  s->tiles_per_pass = ntiles - s->tiles_cached;
+  s->device_bytes = (size_t)(slots + s->cache.size()) * tile_bytes + tws;
+  return RSVD_OK;
+}
+
+void stream_begin_run(StreamState* s) {
+  s->h2d_bytes = 0;
+  std::fill(s->cache_valid.begin(), s->cache_valid.end(), 0);
+}
+
+// One streamed A-pass.  X: K x r panel (K = n forward, m transposed), Y: M x r
+// output, both device, leading dimension ldr; the output is zeroed first and
+// every tile adds its product in tile order.
+rsvd_status apass_streamed(StreamState* s, const rsvd_matrix& Ah, int trans, int prec, int r, const void* X,
+                           void* Y, int64_t ldr, int* status, cudaStream_t st) {
+  void* ws = s->ws;
+  const size_t ws_bytes = s->ws_bytes;
+  const int64_t m = Ah.m, n = Ah.n;
+  const size_t esz = Ah.dtype == RSVD_F64 ? 8 : 4;
+  const int64_t M = trans ? n : m;
+  const int64_t Tm = cdiv(m, s->mb), Tn = cdiv(n, s->nb);
+  RSVD_CUDA(cudaMemsetAsync(Y, 0, (size_t)M * ldr * esz, st));
+  const char* host = static_cast<const char*>(Ah.data);
+  for (int64_t I = 0; I < Tm; ++I) {
+    for (int64_t J = 0; J < Tn; ++J) {
+      const int64_t t = I * Tn + J;
+      const int64_t row0 = I * s->mb, col0 = J * s->nb;
+      const int64_t rows = (row0 + s->mb < m ? s->mb : m - row0);
+      const int64_t cols = (col0 + s->nb < n ? s->nb : n - col0);
+      const bool cached = t < (int64_t)s->cache.size();
+      const int slot = (int)(t % s->S);
+      void* tile = cached ? s->cache[t] : s->slot[slot];
+      if (!cached || !s->cache_valid[t]) {
+        if (!cached) RSVD_CUDA(cudaStreamWaitEvent(s->copy, s->freed[slot], 0));
+        RSVD_CUDA(cudaMemcpy2DAsync(tile, (size_t)s->ld_tile * esz, host + ((size_t)row0 * Ah.ld + col0) * esz,
+                                    (size_t)Ah.ld * esz, (size_t)cols * esz, (size_t)rows, cudaMemcpyHostToDevice,
+                                    s->copy));
+        cudaEvent_t done = cached ? s->cache_ev[t] : s->copied[slot];
+        RSVD_CUDA(cudaEventRecord(done, s->copy));
+        RSVD_CUDA(cudaStreamWaitEvent(st, done, 0));
+        s->h2d_bytes += (uint64_t)rows * cols * esz;
+        if (cached) s->cache_valid[t] = 1;
+      }
+      rsvd_matrix T = Ah;
+      T.location = RSVD_ON_DEVICE;
+      T.m = rows;
+      T.n = cols;
+      T.data = tile;
+      T.ld = s->ld_tile;
+      const char* Xc = static_cast<const char*>(X);
+      char* Yc = static_cast<char*>(Y);
+      if (!trans)
+        RSVD_TRY(apass_dense(T, 0, prec, r, Xc + (size_t)col0 * ldr * esz, ldr, Yc + (size_t)row0 * ldr * esz, ldr,
+                             0, 0, ws, ws_bytes, status, st, true));
+      else
+        RSVD_TRY(apass_dense(T, 1, prec, r, Xc + (size_t)row0 * ldr * esz, ldr, Yc + (size_t)col0 * ldr * esz, ldr,
+                             0, 0, ws, ws_bytes, status, st, true));
+      if (!cached) RSVD_CUDA(cudaEventRecord(s->freed[slot], st));
+    }
+  }
+  return RSVD_OK;
+}
+
+}  // namespace rsvd
