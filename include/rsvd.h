@@ -127,8 +127,9 @@ rsvd_status rsvd_plan_info(rsvd_plan_t plan, rsvd_plan_info_t* out);
  * A: dense (device or pinned host) with dtype equal to the plan's dtype.
  * A host A is copied to the device and processed in core when the plan has no
  * cap or the copy fits under it; otherwise it is processed out of core: its
- * block-cyclic tiles (edges opts.mb x opts.nb, default 8192, shrunk to fit)
- * are streamed from host memory through opts.n_slots device buffers on a side
+ * block-cyclic tiles (edges opts.mb x opts.nb; by default full-width row
+ * panels of about 512 MB, whose rows are contiguous in host memory; shrunk to
+ * fit) are streamed from host memory through opts.n_slots device buffers on a side
  * stream, overlapped with the tile products, and the tiles that fit in the
  * rest of the cap stay resident for the later passes of the run (Section 3.5,
  * Section 3.7).  Streaming needs A in pinned host memory for the copies to

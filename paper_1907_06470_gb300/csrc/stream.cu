@@ -58,10 +58,23 @@ void stream_stats(const StreamState* s, uint64_t* h2d, int64_t* per_pass, int64_
 // size esz within `budget` device bytes (the cap minus the plan workspace).
 rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, int64_t mb_req, int64_t nb_req,
                            int slots, size_t budget, int r, int prec, int final_prec) {
-  int64_t mb = mb_req > 0 ? mb_req : 8192, nb = nb_req > 0 ? nb_req : 8192;
+  if (slots < 1) slots = 2;
+  // Default tile: a full-width row panel of about 512 MB (or less, to leave room
+  // for the resident cache).  Rows of a panel are contiguous in host memory, and
+  // a contiguous copy runs at the full pinned host-to-device rate, while pitched
+  // copies of narrow tiles (tens of KB per row) reach about half of it.
+  int64_t nb = nb_req > 0 ? nb_req : n;
+  int64_t mb = mb_req;
+  if (mb <= 0) {
+    const size_t target = (size_t)512 << 20;
+    const size_t per_row = (size_t)round_up(nb, 4) * esz;
+    mb = (int64_t)(target / per_row);
+    const size_t share = budget / (size_t)(slots + 2);
+    if ((size_t)mb * per_row > share) mb = (int64_t)(share / per_row);
+    if (mb < 16) mb = 16;
+  }
   if (mb > m) mb = m;
   if (nb > n) nb = n;
-  if (slots < 1) slots = 2;
   // shrink the tiles until the slots fit the budget
   while ((size_t)slots * mb * round_up(nb, 4) * esz > budget && (mb > 16 || nb > 16)) {
     if (mb >= nb && mb > 16) mb = (mb + 1) / 2;
@@ -69,12 +82,17 @@ rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, i
   }
   const int64_t ld_tile = round_up(nb, 4);
   const size_t tile_bytes = (size_t)mb * ld_tile * esz;
+  // A-pass workspace for every tile shape (full, last tile row/column, corner)
   size_t tws = 0;
-  for (int tr = 0; tr < 2; ++tr)
-    for (int pr : {prec, final_prec}) {
-      const size_t b = apass_ws_bytes(mb, nb, r, tr, pr, 0, 0) + 512;
-      if (b > tws) tws = b;
-    }
+  const int64_t rows_opts[2] = {mb, m % mb ? m % mb : mb};
+  const int64_t cols_opts[2] = {nb, n % nb ? n % nb : nb};
+  for (int64_t tr_rows : rows_opts)
+    for (int64_t tr_cols : cols_opts)
+      for (int tr = 0; tr < 2; ++tr)
+        for (int pr : {prec, final_prec}) {
+          const size_t b = apass_ws_bytes(tr_rows, tr_cols, r, tr, pr, 0, 0) + 512;
+          if (b > tws) tws = b;
+        }
   if ((size_t)slots * tile_bytes + tws > budget)
     return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: mem_cap leaves no room for the streaming slots");
   StreamState* s = *ps;

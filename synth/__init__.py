@@ -13,6 +13,6 @@ workload c (c = 1..5); the differentiable workload also uses 4005 (X) and
 
 from .dense import (  # noqa: F401
     spectrum_geometric, spectrum_harmonic_noisy, spectrum_exp_floor,
-    prescribed_dense, prescribed_dense_torch, lowrank_plus_noise_torch,
+    prescribed_dense, prescribed_dense_torch, lowrank_plus_noise_torch, LowRankPlusNoise,
     WORKLOADS, Workload,
 )

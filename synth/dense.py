@@ -98,6 +98,31 @@ def lowrank_plus_noise_torch(m: int, n: int, rank: int, decay: float, floor: flo
     return ((UR[row0:row0 + rows] * s) @ VR.T + (floor / float(np.sqrt(m))) * G).contiguous()
 
 
+class LowRankPlusNoise:
+    """Row blocks of A = U_R diag(exp(-i/decay)) V_R^T + floor * G / sqrt(m), built on a GPU.
+
+    The factors are drawn once (QR of seeded Gaussians); each row block adds its
+    own seeded Gaussian noise, so blocks can be produced one at a time and
+    copied out (for matrices larger than device memory).
+    """
+
+    def __init__(self, m, n, rank, decay, floor, seed, noise_seed, device="cuda"):
+        import torch
+        self.m, self.n, self.floor, self.noise_seed, self.device = m, n, floor, noise_seed, device
+        gen = torch.Generator(device=device)
+        gen.manual_seed(seed)
+        self.UR, _ = torch.linalg.qr(torch.randn(m, rank, generator=gen, device=device))
+        self.VRt = torch.linalg.qr(torch.randn(n, rank, generator=gen, device=device))[0].T.contiguous()
+        self.s = torch.exp(-torch.arange(rank, device=device, dtype=torch.float32) / decay)
+
+    def rows(self, row0, nrows):
+        import torch
+        gn = torch.Generator(device=self.device)
+        gn.manual_seed(self.noise_seed * 1_000_003 + row0)
+        G = torch.randn(nrows, self.n, generator=gn, device=self.device)
+        return (self.UR[row0:row0 + nrows] * self.s) @ self.VRt + (self.floor / float(np.sqrt(self.m))) * G
+
+
 @dataclass(frozen=True)
 class Workload:
     name: str
@@ -120,6 +145,10 @@ WORKLOADS = {
     "dense_fp32_100000x20000": Workload(
         "dense_fp32_100000x20000", 100000, 20000, 100, 20, 2, 2002, 1002, 3002, 4096,
         "dense FP32 100000x20000 (8 GB), s_i = |1/i + 1e-4 g_i|, k=100 p=20 q=2, 4096^2 tiles"),
+    "dense_fp32_600000x100000_ooc": Workload(
+        "dense_fp32_600000x100000_ooc", 600000, 100000, 200, 40, 2, 2003, 1003, 3003, 8192,
+        "dense FP32 600000x100000 (240 GB) in pinned host memory, s_i = exp(-i/50) + 1e-3 floor, "
+        "k=200 p=40 q=2, 8192^2 tiles streamed under a 64 GB device cap"),
     "dense_fp32_20000x10000_diff": Workload(
         "dense_fp32_20000x10000_diff", 20000, 10000, 64, 16, 2, 2005, 1005, 3005, 4096,
         "dense FP32 20000x10000, s_i = 10*0.95^(i-1), k=64 p=16 q=2 (differentiable)"),
