@@ -21,12 +21,36 @@ import numpy as np
 EPS64 = np.finfo(np.float64).eps
 
 
+class CSR:
+    """A sparse m x n matrix in compressed sparse row form (values widened to FP64 on use)."""
+
+    def __init__(self, m, n, rowptr, colidx, val):
+        self.m, self.n = int(m), int(n)
+        self.rowptr = np.asarray(rowptr, dtype=np.int64)
+        self.colidx = np.asarray(colidx, dtype=np.int64)
+        self.val = np.asarray(val)
+
+    @property
+    def shape(self):
+        return (self.m, self.n)
+
+
+def csr_apply(A: CSR, X, trans: bool = False) -> np.ndarray:
+    """A @ X or A.T @ X for a CSR matrix, FP64 (scipy's sparse product as the library primitive)."""
+    import scipy.sparse as sp
+    M = sp.csr_matrix((A.val.astype(np.float64), A.colidx, A.rowptr), shape=(A.m, A.n))
+    X = np.asarray(X, dtype=np.float64)
+    return np.asarray((M.T @ X) if trans else (M @ X))
+
+
 def apply(A, X, trans: bool = False, block_rows: int = 4096) -> np.ndarray:
     """Return A @ X (trans=False) or A.T @ X (trans=True) in FP64.
 
-    For trans=True the partial products of the row blocks are added in
-    increasing block order.
+    A is a dense array or a CSR.  For a dense A with trans=True the partial
+    products of the row blocks are added in increasing block order.
     """
+    if isinstance(A, CSR):
+        return csr_apply(A, X, trans)
     X = np.asarray(X, dtype=np.float64)
     m, n = A.shape
     if not trans:

@@ -53,7 +53,8 @@ def small_svd_of_bt(Bt):
 
 
 def rsvd(A, k: int, p: int, q: int, seed: int, omega_dtype: str = "f64"):
-    """Rank-k randomized SVD of a dense m x n matrix A (numpy array, FP32 or FP64).
+    """Rank-k randomized SVD of an m x n matrix A (numpy array, FP32 or FP64, or an
+    ``oracle.linalg.CSR``).
 
     Returns (U m x k, S k, V n x k) in FP64 with S descending.
     ``omega_dtype`` rounds O to the working type of the path under test
