@@ -12,6 +12,8 @@ Prints one JSON line (rank 0).  Options:
   --gpus N --steps K --warmup W    replicas on N GPUs (torchrun), K timed steps
   --impl reference                 time the FP64 CPU oracle on a bounded sample
   --prec bf16|fp32|bf16x3          precision of the headline path
+  --mode apass|ooc|csr             A-passes alone; the out-of-core workload;
+                                   the sparse (CSR) workload
 """
 
 from __future__ import annotations
@@ -417,6 +419,90 @@ def run_out_of_core(args):
     return 0
 
 
+def run_sparse(args):
+    """The sparse workload's recipe (rank-size row lengths, Zipf(1.0) columns,
+    k=300, p=50, q=3) with A and the CSR of A^T resident in HBM; sizes scaled by
+    --csr-m/--csr-n/--csr-nnz (default: the full 5e6 x 1e6 matrix, 5e8 entries).
+    The transpose is built once by the library's host transpose (untimed)."""
+    import torch
+    import paper_1907_06470_gb300 as g
+    from synth import WORKLOADS, zipf_csr_torch
+    g.load()
+    w = WORKLOADS["csr_fp32_5000000x1000000"]
+    m, n, nnz = args.csr_m, args.csr_n, args.csr_nnz
+    k, p, q = w.k, w.p, w.q
+    t0 = time.perf_counter()
+    rp, ci, v = zipf_csr_torch(m, n, nnz, w.data_seed, device="cuda")
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    nnz = int(rp[-1].item())
+    A_host = torch.sparse_csr_tensor(rp.cpu(), ci.cpu(), v.cpu(), size=(m, n))
+    t0 = time.perf_counter()
+    At_host = g.csr_transpose(A_host)
+    t_tr = time.perf_counter() - t0
+    A = torch.sparse_csr_tensor(rp, ci, v, size=(m, n))
+    At = At_host.to("cuda")
+    del A_host
+    torch.cuda.empty_cache()
+    plan = g.Plan(m, n, k, p, q, w.seed, prec="fp32", kind="csr")
+    plan.set_profiling(True)
+    U, S, V = plan.run(A, At=At)
+    torch.cuda.synchronize()
+    for _ in range(max(0, args.warmup - 1)):
+        plan.run(A, U, S, V, At=At)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    stage_sum = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = g.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.run(A, U, S, V, At=At)
+        for key, val in plan.stage_ms().items():
+            stage_sum[key] = stage_sum.get(key, 0.0) + val
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = g.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    r = k + p
+    calls = stage_sum.get("apass_calls", 0) / args.steps
+    fwd_calls, tr_calls = q + 1, q + 1
+    fwd_ms = stage_sum.get("apass_fwd", 0.0) / args.steps / fwd_calls
+    tr_ms = stage_sum.get("apass_trans", 0.0) / args.steps / tr_calls
+    ldr = (r + 3) // 4 * 4
+
+    def algo_bytes(M, K):
+        # entries (column index + value), row offsets, the panel read once, the output written once
+        return nnz * 8 + (M + 1) * 4 + K * ldr * 4 + M * ldr * 4
+
+    peaks, peak_kind = _peaks()
+    fb = algo_bytes(m, n)
+    tb = algo_bytes(n, m)
+    roof = {"bound": "hbm", "kernel": "spmm_csr_vec_kernel (forward A-pass)",
+            "achieved": fb / (fwd_ms / 1e3) / 1e9, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+            "peak_source": f"hbm_gbs ({peak_kind})", "algorithmic_bytes_per_launch": fb,
+            "avg_launch_ms": fwd_ms, "traffic": _traffic_for("spmm_csr_vec_kernel"),
+            "gathered_panel_bytes_per_launch": nnz * ldr * 4,
+            "gather_GBps": nnz * ldr * 4 / (fwd_ms / 1e3) / 1e9}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    print(json.dumps({
+        "mode": "csr", "workload": w.name if (m, n) == (w.m, w.n) else f"{w.name} scaled to {m}x{n}",
+        "m": m, "n": n, "nnz": nnz, "k": k, "p": p, "q": q, "prec": "fp32", "steps": args.steps,
+        "ms_per_rsvd": ms, "rsvd_per_s": 1e3 / ms, "apass_calls_per_rsvd": calls,
+        "forward_pass_ms": fwd_ms, "transposed_pass_ms": tr_ms,
+        "transposed_GBps_algorithmic": tb / (tr_ms / 1e3) / 1e9,
+        "stages_ms_per_rsvd": {kk: vv / args.steps for kk, vv in stage_sum.items() if kk != "apass_calls"},
+        "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+        "setup_s": {"generate_on_gpu": t_gen, "host_transpose": t_tr},
+        "S_head": [float(x) for x in S[:4].cpu()],
+    }))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -427,7 +513,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--mode", default="rsvd", choices=["rsvd", "apass", "ooc"])
+    ap.add_argument("--mode", default="rsvd", choices=["rsvd", "apass", "ooc", "csr"])
+    ap.add_argument("--csr-m", type=int, default=5_000_000)
+    ap.add_argument("--csr-n", type=int, default=1_000_000)
+    ap.add_argument("--csr-nnz", type=int, default=500_000_000)
     ap.add_argument("--ooc-rows", type=int, default=150000)
     ap.add_argument("--ooc-cap-gb", type=float, default=16.0)
     ap.add_argument("--ooc-tile", type=int, default=0, help="square tile edge (0: planner default)")
@@ -439,6 +528,8 @@ def main():
         return run_apass_only(args)
     if args.mode == "ooc":
         return run_out_of_core(args)
+    if args.mode == "csr":
+        return run_sparse(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

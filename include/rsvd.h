@@ -65,6 +65,8 @@ typedef struct {
   int64_t mb, nb;    /* block-cyclic tile edges (Section 3.1); 0 = planner choice */
   int32_t n_slots;   /* block-cyclic slots = copy/compute buffer pairs (default 2) */
   int32_t dtype;     /* rsvd_dtype of A and of the outputs: F64 or F32 (default F32) */
+  int32_t kind;      /* rsvd_kind of the matrices this plan runs on (default DENSE);
+                        CSR plans take dtype F32 and prec FP32 */
 } rsvd_opts;
 
 /* Descriptor of the input matrix A (m x n). */
@@ -76,10 +78,17 @@ typedef struct {
   int64_t m, n;
   const void* data;  /* DENSE: element (i,j) at data[i*ld + j] */
   int64_t ld;        /* DENSE: leading dimension in elements, >= n */
-  const int32_t* rowptr;  /* CSR: m+1 offsets */
-  const int32_t* colidx;  /* CSR: nnz column indices, ascending inside each row */
+  const int32_t* rowptr;  /* CSR: m+1 offsets, rowptr[0] = 0, rowptr[m] = nnz */
+  const int32_t* colidx;  /* CSR: nnz column indices in [0, n) */
   const float* val;       /* CSR: nnz values */
-  int64_t nnz;
+  int64_t nnz;            /* CSR: number of stored entries, < 2^31 */
+  /* CSR only, optional: the CSR of A^T (n+1 offsets, nnz row indices of A,
+   * nnz values), used by the products A^T X; built by the library from the
+   * CSR of A (rsvd_csr_transpose) when t_rowptr is NULL.  Same location as
+   * rowptr/colidx/val. */
+  const int32_t* t_rowptr;
+  const int32_t* t_colidx;
+  const float* t_val;
 } rsvd_matrix;
 
 /* One tile of the block-cyclic map (Section 3.1): rows [row0,row1) x cols [col0,col1). */
@@ -111,7 +120,9 @@ typedef struct {
  * matrix (see rsvd_gaussian).  Device workspace is allocated here and owned by
  * the plan; `mem_cap_bytes` bounds it together with any device copy of A
  * (0 = no cap: run in core when A fits, the paper's default in Section 3.5).
- * Rules: 1 <= k, 0 <= p, k + p <= min(m, n), k + p <= 256, 0 <= q <= 64.
+ * Rules: 1 <= k, 0 <= p, k + p <= min(m, n), 0 <= q <= 64, and k + p <= 256
+ * for dense plans, k + p <= 512 for CSR plans (opts.kind = CSR: dtype F32,
+ * prec FP32; they hold no backward workspace).
  * Errors: INVALID_ARG, CAP_TOO_SMALL (see rsvd_plan_min_cap), OOM, CUDA.
  * On success *out receives a plan that must be released with rsvd_destroy. */
 rsvd_status rsvd_plan(int64_t m, int64_t n, int k, int p, int q, uint64_t seed,
@@ -124,7 +135,13 @@ rsvd_status rsvd_plan_min_cap(int64_t m, int64_t n, int k, int p, const rsvd_opt
 rsvd_status rsvd_plan_info(rsvd_plan_t plan, rsvd_plan_info_t* out);
 
 /* Run the planned randomized SVD on A (Section 2.1 steps 1-7 with Eq. (3)).
- * A: dense (device or pinned host) with dtype equal to the plan's dtype.
+ * A: of the plan's kind and dtype.  Dense: device or pinned host.  CSR
+ * (Section 3.6, sparse x dense products): device or host arrays; the products
+ * A X run on the CSR of A and the products A^T X on the CSR of A^T, which is
+ * built on the host (rsvd_csr_transpose, once per call) when A.t_rowptr is
+ * NULL.  A host CSR (and a built transpose) is copied into device memory owned
+ * by the plan; with a cap, those copies count against it (CAP_TOO_SMALL if
+ * they do not fit: CSR matrices are not streamed).
  * A host A is copied to the device and processed in core when the plan has no
  * cap or the copy fits under it; otherwise it is processed out of core: its
  * block-cyclic tiles (edges opts.mb x opts.nb; by default full-width row
@@ -231,13 +248,14 @@ rsvd_status rsvd_tile_map(int64_t m, int64_t n, int64_t mb, int64_t nb, int32_t 
 /* One A-pass (Section 2.1 steps 2 and 5, Eq. (3)): Y = A X (trans = 0) or
  * Y = A^T X (trans = 1), block-wise over the tile grid (mb, nb) of Section 2.3,
  * with the partial products of each tile row/column added in a fixed order.
- * A: dense device matrix (F64 or F32).  X: K x r row-major of A's dtype (K = n
- * for trans = 0, m for trans = 1), leading dimension ldx.  Y: M x r row-major
- * of A's dtype, leading dimension ldy.  prec: FP64 (A F64), FP32, BF16 or
- * BF16X3 (A F32; A 16-byte aligned with ld % 4 == 0; BF16X3 needs r <= 192).
- * r <= 256.  Needs `ws_bytes` >= rsvd_apass_workspace(...).  FP64/FP32 enqueue
- * only; BF16/BF16X3 synchronise `stream` and return TIMEOUT if a wait of the
- * tensor-core pipeline expired. */
+ * A: dense device matrix (F64 or F32), or a CSR device matrix (below).
+ * X: K x r row-major of A's dtype (K = n for trans = 0, m for trans = 1),
+ * leading dimension ldx.  Y: M x r row-major of A's dtype, leading dimension
+ * ldy.  prec: FP64 (A F64), FP32, BF16 or BF16X3 (A F32; A 16-byte aligned
+ * with ld % 4 == 0).  r <= 256 (CSR: 512, see below).  Needs `ws_bytes` >=
+ * rsvd_apass_workspace(...).  FP64/FP32 enqueue only; BF16/BF16X3
+ * synchronise `stream` and return TIMEOUT if a wait of the tensor-core
+ * pipeline expired. */
 size_t rsvd_apass_workspace(int64_t m, int64_t n, int32_t r, int32_t trans, int32_t prec,
                             int64_t mb, int64_t nb);
 rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_t r,
@@ -264,6 +282,23 @@ rsvd_status rsvd_orth(int32_t dtype, int64_t M, int32_t r, const void* Y, int64_
 size_t rsvd_small_svd_workspace(int32_t r);
 rsvd_status rsvd_small_svd(int32_t r, const double* Mc, double* sigma, double* U, double* W,
                            void* ws, size_t ws_bytes, void* stream);
+
+/* Section 3.6 (sparse x dense product): Y = A X (trans = 0, CSR of A) or
+ * Y = A^T X (trans = 1, using A.t_rowptr/t_colidx/t_val, which must be set)
+ * for a CSR device matrix with FP32 values, FP32 panels, FP32 accumulation in
+ * entry order (deterministic).  X: K x r row-major (ldx), Y: M x r row-major
+ * (ldy), overwritten; r <= 512.  Goes through rsvd_apass with prec FP32 and no
+ * workspace (ws may be NULL).  Enqueues only. */
+
+/* Host (CPU) transpose of a CSR matrix: from the CSR of the m x n matrix A
+ * (rowptr m+1, colidx and val nnz = rowptr[m]) writes the CSR of A^T into
+ * caller-allocated host arrays t_rowptr (n+1), t_colidx (nnz, row indices of
+ * A) and t_val (nnz).  Within each row of A^T the entries come in increasing
+ * row index of A (a stable counting sort), so the result does not depend on
+ * the number of threads it uses.  Errors: INVALID_ARG (decreasing rowptr,
+ * column index outside [0, n), NULL array). */
+rsvd_status rsvd_csr_transpose(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                               const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val);
 
 /* ---- Variant without allocation (no counterpart in the paper) --------------- */
 

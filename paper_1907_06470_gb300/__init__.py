@@ -13,6 +13,7 @@ full_svd(A)                   exact SVD of a small matrix
 gaussian / tile_map / apass / orth / small_svd
                               the individual steps (Section 2.1 steps 1-6,
                               Section 3.1 tile map)
+csr_transpose                 host CSR of A^T for the sparse A-passes (Section 3.6)
 """
 
 from __future__ import annotations
@@ -23,7 +24,7 @@ from . import _lib
 from ._lib import RsvdError, load  # noqa: F401
 
 __all__ = ["rsvd", "Plan", "full_svd", "gaussian", "tile_map", "apass", "orth", "small_svd",
-           "small_svd_noalloc", "RsvdError", "load"]
+           "small_svd_noalloc", "csr_transpose", "RsvdError", "load"]
 
 
 def _torch():
@@ -58,6 +59,45 @@ def _dense_desc(A) -> _lib.RsvdMatrix:
     return d
 
 
+def _is_csr(A) -> bool:
+    torch = _torch()
+    return getattr(A, "layout", None) == torch.sparse_csr
+
+
+def _csr_arrays(A):
+    """(rowptr int32, colidx int32, val float32) of a torch sparse CSR tensor, contiguous."""
+    torch = _torch()
+    rp = A.crow_indices().to(torch.int32).contiguous()
+    ci = A.col_indices().to(torch.int32).contiguous()
+    v = A.values()
+    if v.dtype != torch.float32:
+        raise TypeError(f"CSR values must be float32, got {v.dtype}")
+    return rp, ci, v.contiguous()
+
+
+def _csr_desc(A, At=None):
+    """Descriptor of a torch sparse CSR matrix (and optionally the CSR of its
+    transpose).  Returns (descriptor, tensors to keep alive during the call)."""
+    if A.dim() != 2:
+        raise ValueError("A must be a 2-D sparse CSR tensor")
+    rp, ci, v = _csr_arrays(A)
+    d = _lib.RsvdMatrix()
+    d.kind = _lib.CSR
+    d.dtype = _lib.DTYPE["f32"]
+    d.location = _lib.ON_DEVICE if A.is_cuda else _lib.ON_HOST
+    d.m, d.n = A.shape
+    d.rowptr, d.colidx, d.val = rp.data_ptr(), ci.data_ptr(), v.data_ptr()
+    d.nnz = v.numel()
+    keep = [rp, ci, v]
+    if At is not None:
+        if tuple(At.shape) != (A.shape[1], A.shape[0]) or At.is_cuda != A.is_cuda:
+            raise ValueError("At must be the n x m CSR of A^T, on the same device as A")
+        trp, tci, tv = _csr_arrays(At)
+        d.t_rowptr, d.t_colidx, d.t_val = trp.data_ptr(), tci.data_ptr(), tv.data_ptr()
+        keep += [trp, tci, tv]
+    return d, keep
+
+
 def _check(st):
     _lib.check(st)
 
@@ -66,7 +106,7 @@ class Plan:
     """A planned rank-k randomized SVD (rsvd_plan); owns its device workspace."""
 
     def __init__(self, m, n, k, p=10, q=2, seed=0, mem_cap=0, prec=None, dtype="f32",
-                 mb=0, nb=0, refine=True, n_slots=2):
+                 mb=0, nb=0, refine=True, n_slots=2, kind="dense"):
         lib = load()
         if prec is None:
             prec = "fp64" if dtype == "f64" else "fp32"
@@ -76,6 +116,8 @@ class Plan:
         o.mb, o.nb = mb, nb
         o.n_slots = n_slots
         o.dtype = _lib.DTYPE[dtype]
+        o.kind = {"dense": _lib.DENSE, "csr": _lib.CSR}[kind]
+        self.kind = kind
         h = C.c_void_p()
         _check(lib.rsvd_plan(m, n, k, p, q, seed, mem_cap, C.byref(o), C.byref(h)))
         self._h = h
@@ -88,8 +130,10 @@ class Plan:
         _check(load().rsvd_plan_info(self._h, C.byref(i)))
         return {f: getattr(i, f) for f, _ in i._fields_}
 
-    def run(self, A, U=None, S=None, V=None):
-        """Factor A (device tensor, or pinned host tensor); returns (U, S, V) on the device."""
+    def run(self, A, U=None, S=None, V=None, At=None):
+        """Factor A (device tensor, or pinned host tensor; for CSR plans a torch
+        sparse CSR tensor, with the CSR of A^T in `At` if the caller has it);
+        returns (U, S, V) on the device."""
         torch = _torch()
         tdt = torch.float64 if self.dtype == "f64" else torch.float32
         dev = A.device if A.is_cuda else torch.device("cuda", torch.cuda.current_device())
@@ -99,9 +143,13 @@ class Plan:
             S = torch.empty(self.k, dtype=tdt, device=dev)
         if V is None:
             V = torch.empty(self.n, self.k, dtype=tdt, device=dev)
-        d = _dense_desc(A)
+        if _is_csr(A):
+            d, keep = _csr_desc(A, At)
+        else:
+            d, keep = _dense_desc(A), [A]
         _check(load().rsvd_run(self._h, C.byref(d), C.c_void_p(U.data_ptr()), C.c_void_p(S.data_ptr()),
                                C.c_void_p(V.data_ptr()), _stream_ptr()))
+        del keep
         return U, S, V
 
     def backward(self, U, S, V, dU=None, dS=None, dV=None):
@@ -170,12 +218,21 @@ def _rsvd_function():
     return RSVDFunction
 
 
-def rsvd(A, k, p=10, q=2, seed=0, mem_cap=0, prec=None, mb=0, nb=0, refine=True):
-    """Rank-k randomized SVD of a dense float32/float64 matrix (CUDA or pinned host tensor).
+def rsvd(A, k, p=10, q=2, seed=0, mem_cap=0, prec=None, mb=0, nb=0, refine=True, At=None):
+    """Rank-k randomized SVD of a dense float32/float64 matrix (CUDA or pinned
+    host tensor) or of a float32 torch sparse CSR tensor (CUDA or host; `At`
+    optionally its transpose in CSR form, else built by the library).
 
-    If A requires grad, the result is differentiable through the truncated-SVD
-    adjoint (rsvd_backward)."""
+    If a dense A requires grad, the result is differentiable through the
+    truncated-SVD adjoint (rsvd_backward)."""
     torch = _torch()
+    if _is_csr(A):
+        plan = Plan(A.shape[0], A.shape[1], k, p, q, seed, mem_cap, prec or "fp32", "f32", mb, nb, refine,
+                    kind="csr")
+        try:
+            return plan.run(A, At=At)
+        finally:
+            plan.close()
     dtype = "f64" if A.dtype == torch.float64 else "f32"
     plan = Plan(A.shape[0], A.shape[1], k, p, q, seed, mem_cap, prec, dtype, mb, nb, refine)
     if A.requires_grad:
@@ -227,9 +284,22 @@ def tile_map(m, n, mb, nb, n_slots=2):
     return [(x.t, x.I, x.J, x.row0, x.row1, x.col0, x.col1, x.slot) for x in arr[:cnt.value]]
 
 
-def apass(A, X, trans=False, prec=None, mb=0, nb=0, out=None):
-    """One A-pass: A @ X (trans=False) or A.T @ X (trans=True), on the library's kernels."""
+def apass(A, X, trans=False, prec=None, mb=0, nb=0, out=None, At=None):
+    """One A-pass: A @ X (trans=False) or A.T @ X (trans=True), on the library's kernels.
+
+    A sparse CSR A (CUDA, float32) needs `At`, the CSR of A^T, for trans=True."""
     torch = _torch()
+    if _is_csr(A):
+        m, n = A.shape
+        r = X.shape[1]
+        if out is None:
+            out = torch.empty(n if trans else m, r, dtype=torch.float32, device=A.device)
+        d, keep = _csr_desc(A, At)
+        _check(load().rsvd_apass(C.byref(d), int(trans), _lib.PREC["fp32"], r, C.c_void_p(X.data_ptr()),
+                                 X.stride(0), C.c_void_p(out.data_ptr()), out.stride(0), 0, 0, None, 0,
+                                 _stream_ptr()))
+        del keep
+        return out
     if prec is None:
         prec = "fp64" if A.dtype == torch.float64 else "fp32"
     m, n = A.shape
@@ -245,6 +315,24 @@ def apass(A, X, trans=False, prec=None, mb=0, nb=0, out=None):
                           C.c_void_p(out.data_ptr()), out.stride(0), mb, nb, C.c_void_p(ws.data_ptr()), wsb,
                           _stream_ptr()))
     return out
+
+
+def csr_transpose(A):
+    """CSR of A^T for a host torch sparse CSR tensor A (float32), computed by the
+    library's host transpose (stable: entries of each row in increasing row of A)."""
+    torch = _torch()
+    if A.is_cuda:
+        raise ValueError("csr_transpose takes a host tensor")
+    rp, ci, v = _csr_arrays(A)
+    m, n = A.shape
+    nnz = v.numel()
+    trp = torch.empty(n + 1, dtype=torch.int32)
+    tci = torch.empty(nnz, dtype=torch.int32)
+    tv = torch.empty(nnz, dtype=torch.float32)
+    _check(load().rsvd_csr_transpose(m, n, C.c_void_p(rp.data_ptr()), C.c_void_p(ci.data_ptr()),
+                                     C.c_void_p(v.data_ptr()), C.c_void_p(trp.data_ptr()),
+                                     C.c_void_p(tci.data_ptr()), C.c_void_p(tv.data_ptr())))
+    return torch.sparse_csr_tensor(trp, tci, tv, size=(n, m))
 
 
 def orth(Y, want_R=False):

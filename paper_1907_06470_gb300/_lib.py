@@ -25,13 +25,14 @@ ON_DEVICE, ON_HOST = 0, 1
 
 class RsvdOpts(C.Structure):
     _fields_ = [("prec", c_i32), ("refine", c_i32), ("mb", c_i64), ("nb", c_i64),
-                ("n_slots", c_i32), ("dtype", c_i32)]
+                ("n_slots", c_i32), ("dtype", c_i32), ("kind", c_i32)]
 
 
 class RsvdMatrix(C.Structure):
     _fields_ = [("kind", c_i32), ("dtype", c_i32), ("location", c_i32), ("reserved", c_i32),
                 ("m", c_i64), ("n", c_i64), ("data", c_vp), ("ld", c_i64),
-                ("rowptr", c_vp), ("colidx", c_vp), ("val", c_vp), ("nnz", c_i64)]
+                ("rowptr", c_vp), ("colidx", c_vp), ("val", c_vp), ("nnz", c_i64),
+                ("t_rowptr", c_vp), ("t_colidx", c_vp), ("t_val", c_vp)]
 
 
 class RsvdTile(C.Structure):
@@ -70,6 +71,7 @@ SIGNATURES = {
     "rsvd_small_svd_workspace": (c_size, [c_i32]),
     "rsvd_small_svd": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "rsvd_small_svd_noalloc": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "rsvd_csr_transpose": (c_i32, [c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
 }
 NOALLOC_MAX_R = 256
 

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -207,6 +208,11 @@ struct rsvd_plan_s {
   int64_t mb_req = 0, nb_req = 0;  // tile edges asked for in the options (0: none)
   StreamState* ss = nullptr;       // out-of-core state (created on the first streamed run)
   bool streaming = false;          // the current run streams A from the host
+  int kind = RSVD_DENSE;           // rsvd_kind the plan runs on
+  void* csr_dev = nullptr;         // device copies of a CSR A and/or its transpose
+  size_t csr_dev_bytes = 0;
+  std::vector<int32_t> h_idx;      // host staging for a transpose built by the library
+  std::vector<float> h_val;
   Profiler prof;
 };
 
@@ -217,7 +223,12 @@ rsvd_status check_args(int64_t m, int64_t n, int k, int p, int q, const rsvd_opt
     return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: need m, n >= 1, k >= 1, p >= 0, 0 <= q <= 64");
   const int64_t r = (int64_t)k + p;
   if (r > m || r > n) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: k + p must not exceed min(m, n)");
-  if (r > 256) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: k + p must not exceed 256");
+  const bool csr = o && o->kind == RSVD_CSR;
+  if (o && o->kind != RSVD_DENSE && o->kind != RSVD_CSR) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: unknown kind");
+  if (!csr && r > 256) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: k + p must not exceed 256 (dense)");
+  if (csr && r > kSpmmMaxR) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: k + p must not exceed 512 (CSR)");
+  if (csr && (o->dtype != RSVD_F32 || o->prec != RSVD_PREC_FP32))
+    return fail(RSVD_ERR_UNSUPPORTED, "rsvd_plan: CSR plans take F32 values and FP32 precision");
   if (o) {
     if (o->dtype != RSVD_F32 && o->dtype != RSVD_F64)
       return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: dtype must be F32 or F64");
@@ -241,6 +252,7 @@ void apply_opts(rsvd_plan_s* P, const rsvd_opts* o) {
     P->mb_req = o->mb;
     P->nb_req = o->nb;
     P->n_slots = o->n_slots > 0 ? o->n_slots : 2;
+    P->kind = o->kind;
   }
   if (P->mb <= 0) P->mb = P->m;  // in core: one block row unless asked otherwise
   if (P->nb <= 0) P->nb = P->n;
@@ -258,10 +270,11 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   P->Qm = c.take<char>((size_t)P->m * P->ldr * esz);
   P->Bt = c.take<char>((size_t)P->n * P->ldr * esz);
   P->Qb = c.take<char>((size_t)P->n * P->ldr * esz);
-  const size_t a0 = apass_ws_bytes(P->m, P->n, P->r, 0, P->prec, P->mb, P->nb);
-  const size_t a1 = apass_ws_bytes(P->m, P->n, P->r, 1, P->prec, P->mb, P->nb);
+  const bool dense = P->kind == RSVD_DENSE;  // CSR passes need no workspace
+  const size_t a0 = dense ? apass_ws_bytes(P->m, P->n, P->r, 0, P->prec, P->mb, P->nb) : 0;
+  const size_t a1 = dense ? apass_ws_bytes(P->m, P->n, P->r, 1, P->prec, P->mb, P->nb) : 0;
   size_t a2 = 0;
-  if (P->prec == RSVD_PREC_BF16 && P->refine)
+  if (dense && P->prec == RSVD_PREC_BF16 && P->refine)
     a2 = apass_ws_bytes(P->m, P->n, P->r, 1, RSVD_PREC_BF16X3, P->mb, P->nb);
   P->apass_ws_bytes = a0 > a1 ? a0 : a1;
   if (a2 > P->apass_ws_bytes) P->apass_ws_bytes = a2;
@@ -276,7 +289,7 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   P->WRk = c.take<char>((size_t)P->r * P->k * esz);
   P->sign_scratch_bytes = sign_scratch_bytes(P->m, P->k);
   P->sign_scratch = c.take<char>(P->sign_scratch_bytes);
-  P->bwd_ws_bytes = backward_ws_bytes(P->m, P->n, P->k, P->dtype);
+  P->bwd_ws_bytes = dense ? backward_ws_bytes(P->m, P->n, P->k, P->dtype) : 0;
   P->bwd_ws = c.take<char>(P->bwd_ws_bytes);
   P->status = c.take<int>(4);
   if (base) {
@@ -301,6 +314,11 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   auto apass = [&](int trans, int pr, const T* Xin, T* Yout) -> rsvd_status {
     Span sp(pf, trans ? RSVD_STAGE_APASS_TRANS : RSVD_STAGE_APASS_FWD, st);
     ++pf.apass_calls;
+    if constexpr (std::is_same<T, float>::value) {
+      if (A.kind == RSVD_CSR)  // Section 3.6: sparse x dense; A^T through the CSR of A^T
+        return trans ? spmm_csr(n, r, A.t_rowptr, A.t_colidx, A.t_val, Xin, ldr, Yout, ldr, false, st)
+                     : spmm_csr(m, r, A.rowptr, A.colidx, A.val, Xin, ldr, Yout, ldr, false, st);
+    }
     if (P->streaming) return apass_streamed(P->ss, A, trans, pr, r, Xin, Yout, ldr, P->status, st);
     return apass_dense(A, trans, pr, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes,
                        P->status, st);
@@ -351,6 +369,93 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   return res;
 }
 
+// Make a device CSR descriptor (with the CSR of A^T) for rsvd_run.  Device
+// arrays of A are used in place; host arrays, and a transpose the library
+// builds on the host, are copied into the plan's CSR buffer (kept between
+// runs and grown when needed).
+rsvd_status prepare_csr(rsvd_plan_s* P, const rsvd_matrix& A, rsvd_matrix* out, cudaStream_t st) {
+  const int64_t m = A.m, n = A.n, nnz = A.nnz;
+  if (nnz < 0 || nnz > 0x7fffffffLL || !A.rowptr || (nnz > 0 && (!A.colidx || !A.val)))
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: bad CSR descriptor (nnz, rowptr, colidx, val)");
+  if (A.dtype != RSVD_F32) return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: CSR values must be F32");
+  const bool host = A.location == RSVD_ON_HOST;
+  const bool have_t = A.t_rowptr != nullptr;
+  if (have_t && nnz > 0 && (!A.t_colidx || !A.t_val))
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: t_rowptr set without t_colidx/t_val");
+  *out = A;
+  out->location = RSVD_ON_DEVICE;
+  // host views of the transpose's source, and of the transpose
+  const int32_t *hrp = nullptr, *hci = nullptr;
+  const float* hv = nullptr;
+  std::vector<int32_t> tmp_idx;
+  std::vector<float> tmp_val;
+  if (!have_t) {
+    if (host) {
+      hrp = A.rowptr; hci = A.colidx; hv = A.val;
+    } else {  // bring A to the host to build its transpose
+      tmp_idx.resize((size_t)(m + 1) + (size_t)nnz);
+      tmp_val.resize((size_t)nnz);
+      RSVD_CUDA(cudaMemcpyAsync(tmp_idx.data(), A.rowptr, (size_t)(m + 1) * 4, cudaMemcpyDeviceToHost, st));
+      if (nnz) {
+        RSVD_CUDA(cudaMemcpyAsync(tmp_idx.data() + m + 1, A.colidx, (size_t)nnz * 4, cudaMemcpyDeviceToHost, st));
+        RSVD_CUDA(cudaMemcpyAsync(tmp_val.data(), A.val, (size_t)nnz * 4, cudaMemcpyDeviceToHost, st));
+      }
+      RSVD_CUDA(cudaStreamSynchronize(st));
+      hrp = tmp_idx.data(); hci = tmp_idx.data() + m + 1; hv = tmp_val.data();
+    }
+    if (hrp[m] != nnz) return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: rowptr[m] != nnz");
+    P->h_idx.resize((size_t)(n + 1) + (size_t)nnz);
+    P->h_val.resize((size_t)nnz);
+    RSVD_TRY(csr_transpose_host(m, n, hrp, hci, hv, P->h_idx.data(), P->h_idx.data() + n + 1, P->h_val.data()));
+  } else if (host && A.rowptr[m] != nnz) {
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: rowptr[m] != nnz");
+  }
+  // device bytes needed: A's arrays when on the host, the transpose when on the host or built here
+  const size_t a_bytes = host ? (size_t)(m + 1) * 4 + (size_t)nnz * 8 : 0;
+  const size_t t_bytes = (host || !have_t) ? (size_t)(n + 1) * 4 + (size_t)nnz * 8 : 0;
+  const size_t need = a_bytes + t_bytes + 1024;
+  if (a_bytes + t_bytes > 0) {
+    if (P->mem_cap && P->ws_bytes + need > P->mem_cap)
+      return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: the CSR copies do not fit under mem_cap");
+    if (P->csr_dev_bytes < need) {
+      if (P->csr_dev) cudaFree(P->csr_dev);
+      P->csr_dev = nullptr;
+      P->csr_dev_bytes = 0;
+      RSVD_CUDA(cudaMalloc(&P->csr_dev, need));
+      P->csr_dev_bytes = need;
+    }
+    Carver c(P->csr_dev, P->csr_dev_bytes);
+    if (host) {
+      int32_t* rp = c.take<int32_t>((size_t)m + 1);
+      int32_t* ci = c.take<int32_t>((size_t)nnz);
+      float* v = c.take<float>((size_t)nnz);
+      Span sp(P->prof, RSVD_STAGE_H2D, st);
+      RSVD_CUDA(cudaMemcpyAsync(rp, A.rowptr, (size_t)(m + 1) * 4, cudaMemcpyHostToDevice, st));
+      if (nnz) {
+        RSVD_CUDA(cudaMemcpyAsync(ci, A.colidx, (size_t)nnz * 4, cudaMemcpyHostToDevice, st));
+        RSVD_CUDA(cudaMemcpyAsync(v, A.val, (size_t)nnz * 4, cudaMemcpyHostToDevice, st));
+      }
+      out->rowptr = rp; out->colidx = ci; out->val = v;
+    }
+    if (t_bytes) {
+      int32_t* trp = c.take<int32_t>((size_t)n + 1);
+      int32_t* tci = c.take<int32_t>((size_t)nnz);
+      float* tv = c.take<float>((size_t)nnz);
+      const int32_t* s_rp = have_t ? A.t_rowptr : P->h_idx.data();
+      const int32_t* s_ci = have_t ? A.t_colidx : P->h_idx.data() + n + 1;
+      const float* s_v = have_t ? A.t_val : P->h_val.data();
+      Span sp(P->prof, RSVD_STAGE_H2D, st);
+      RSVD_CUDA(cudaMemcpyAsync(trp, s_rp, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, st));
+      if (nnz) {
+        RSVD_CUDA(cudaMemcpyAsync(tci, s_ci, (size_t)nnz * 4, cudaMemcpyHostToDevice, st));
+        RSVD_CUDA(cudaMemcpyAsync(tv, s_v, (size_t)nnz * 4, cudaMemcpyHostToDevice, st));
+      }
+      out->t_rowptr = trp; out->t_colidx = tci; out->t_val = tv;
+    }
+  }
+  return RSVD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -399,8 +504,20 @@ size_t rsvd_apass_workspace(int64_t m, int64_t n, int32_t r, int32_t trans, int3
 rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_t r, const void* X,
                        int64_t ldx, void* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws,
                        size_t ws_bytes, void* stream) {
-  if (!A || !X || !Y || r < 1 || r > 256 || (trans != 0 && trans != 1) || ldx < r || ldy < r)
+  if (!A || !X || !Y || r < 1 || (trans != 0 && trans != 1) || ldx < r || ldy < r)
     return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: bad arguments");
+  if (A->kind == RSVD_CSR) {
+    if (r > kSpmmMaxR || prec != RSVD_PREC_FP32 || A->dtype != RSVD_F32 || A->location != RSVD_ON_DEVICE)
+      return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: CSR needs a device F32 matrix, prec FP32, r <= 512");
+    const int32_t* rp = trans ? A->t_rowptr : A->rowptr;
+    const int32_t* ci = trans ? A->t_colidx : A->colidx;
+    const float* v = trans ? A->t_val : A->val;
+    if (!rp || (A->nnz > 0 && (!ci || !v)))
+      return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: CSR arrays missing (trans = 1 needs t_rowptr/t_colidx/t_val)");
+    return spmm_csr(trans ? A->n : A->m, r, rp, ci, v, static_cast<const float*>(X), ldx, static_cast<float*>(Y),
+                    ldy, false, as_stream(stream));
+  }
+  if (r > 256) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: r must not exceed 256 (dense)");
   if (A->kind == RSVD_DENSE && A->ld < A->n) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: ld < n");
   if (prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3) {
     // The tensor-core pipeline reports an expired wait through a device word:
@@ -501,9 +618,16 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
   if (!P || !A || !U || !S || !V) return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: NULL argument");
   if (A->m != P->m || A->n != P->n || A->dtype != P->dtype)
     return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: A does not match the plan (shape or dtype)");
-  if (A->kind != RSVD_DENSE) return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: CSR input is not available in this build");
-  if (A->ld < A->n || !A->data) return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: bad dense descriptor");
+  if (A->kind != P->kind) return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: A's kind (dense/CSR) differs from the plan's");
   cudaStream_t st = as_stream(stream);
+  if (A->kind == RSVD_CSR) {
+    rsvd_matrix Ad;
+    P->prof.begin();
+    P->streaming = false;
+    RSVD_TRY(prepare_csr(P, *A, &Ad, st));
+    return run_typed<float>(P, Ad, static_cast<float*>(U), static_cast<float*>(S), static_cast<float*>(V), st);
+  }
+  if (A->ld < A->n || !A->data) return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: bad dense descriptor");
   rsvd_matrix Ad = *A;
   P->prof.begin();
   P->streaming = false;
@@ -544,6 +668,11 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
   return run_typed<float>(P, Ad, static_cast<float*>(U), static_cast<float*>(S), static_cast<float*>(V), st);
 }
 
+rsvd_status rsvd_csr_transpose(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                               const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val) {
+  return csr_transpose_host(m, n, rowptr, colidx, val, t_rowptr, t_colidx, t_val);
+}
+
 rsvd_status rsvd_plan_set_profiling(rsvd_plan_t P, int32_t enable) {
   if (!P) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_set_profiling: NULL plan");
   if (enable) RSVD_TRY(P->prof.reserve(16 + 4 * ((size_t)P->q + 1)));
@@ -563,6 +692,7 @@ unsigned long long rsvd_kernel_launches(void) { return g_launches.load(); }
 rsvd_status rsvd_backward(rsvd_plan_t P, const void* U, const void* S, const void* V, const void* dU,
                           const void* dS, const void* dV, void* dA, void* stream) {
   if (!P || !U || !S || !V || !dA) return fail(RSVD_ERR_INVALID_ARG, "rsvd_backward: NULL argument");
+  if (P->kind != RSVD_DENSE) return fail(RSVD_ERR_UNSUPPORTED, "rsvd_backward: CSR plans have no backward pass");
   cudaStream_t st = as_stream(stream);
   if (P->dtype == RSVD_F64)
     return backward_typed<double>(P->m, P->n, P->k, static_cast<const double*>(U), static_cast<const double*>(S),
@@ -579,6 +709,7 @@ void rsvd_destroy(rsvd_plan_t P) {
   if (!P) return;
   if (P->ws) cudaFree(P->ws);
   if (P->Adev) cudaFree(P->Adev);
+  if (P->csr_dev) cudaFree(P->csr_dev);
   stream_state_free(P->ss);
   delete P;
 }

@@ -150,9 +150,6 @@ reduce_partials_kernel(int64_t M, int64_t N, int nsplit, const T* __restrict__ P
   }
 }
 
-template <typename T>
-bool aligned16(const T* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
-
 }  // namespace
 
 template <typename T>

@@ -104,6 +104,15 @@ template <typename T>
 rsvd_status backward_typed(int64_t m, int64_t n, int k, const T* U, const T* S, const T* V, const T* dU,
                            const T* dS, const T* dV, T* dA, void* ws, size_t ws_bytes, cudaStream_t st);
 
+// spmm.cu -- A-passes for a CSR matrix (FP32 values, int32 indices).
+constexpr int kSpmmMaxR = 512;
+// Y (M x r, ldy) = (or +=) A X for the M-row CSR (rowptr, colidx, val), X row-major (ldx).
+rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
+                     const float* X, int64_t ldx, float* Y, int64_t ldy, bool accumulate, cudaStream_t stream);
+// Host CSR of A^T (n rows) from the CSR of A (m rows); stable, deterministic.
+rsvd_status csr_transpose_host(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                               const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val);
+
 // stream.cu -- out-of-core A-passes over tiles of a pinned host matrix.
 struct StreamState;
 rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, int64_t mb_req, int64_t nb_req,

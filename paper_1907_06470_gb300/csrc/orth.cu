@@ -15,9 +15,9 @@
 // vector (from the library's Gaussian stream with a fixed seed), which the
 // second sweep orthonormalises against the rest; R then has a zero row there.
 //
-// Gram accumulation: products are summed in the panel's type over chunks of at
-// most 256 rows (the SIMT GEMM, one partial per chunk) and the chunk partials
-// are added in FP64 in chunk order.
+// Gram accumulation: products are summed in the panel's type over chunks of
+// 256 rows (more for panels over 2^19 rows; the SIMT GEMM, one partial per
+// chunk) and the chunk partials are added in FP64 in chunk order.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -152,11 +152,19 @@ __global__ void rprod_kernel(int r, const double* __restrict__ L1, const int* __
   }
 }
 
-// Rows per partial Gram: each partial is a sum of at most kGramChunk products
-// in the panel's type; the partials are added in FP64 in chunk order.
+// Rows per partial Gram: each partial is a sum of gram_chunk(M) products in
+// the panel's type -- 256 rows, or more for panels over 2^19 rows so that at
+// most about kGramMaxChunks partials are stored -- and the partials are added
+// in FP64 in chunk order.
 constexpr int64_t kGramChunk = 256;
+constexpr int64_t kGramMaxChunks = 2048;
 
-int64_t gram_chunks(int64_t M) { return cdiv(M, kGramChunk); }
+int64_t gram_chunk(int64_t M) {
+  const int64_t c = round_up(cdiv(M, kGramMaxChunks), kGramChunk);
+  return c > kGramChunk ? c : kGramChunk;
+}
+
+int64_t gram_chunks(int64_t M) { return cdiv(M, gram_chunk(M)); }
 
 template <typename T>
 __global__ void gram_sum_partials_kernel(int r, int64_t nchunks, const T* __restrict__ P, double* __restrict__ G) {
@@ -177,7 +185,7 @@ template <typename T>
 rsvd_status gram(int64_t M, int r, const T* Y, int64_t ldy, const OrthWs& ws, cudaStream_t stream) {
   const int64_t nchunks = gram_chunks(M);
   T* P = static_cast<T*>(ws.gram_partial);
-  RSVD_TRY(simt_gemm_partials<T>(r, r, M, Y, ldy, true, Y, ldy, (int)nchunks, kGramChunk, P, stream));
+  RSVD_TRY(simt_gemm_partials<T>(r, r, M, Y, ldy, true, Y, ldy, (int)nchunks, gram_chunk(M), P, stream));
   const int64_t blocks = cdiv((int64_t)r * r, 256);
   gram_sum_partials_kernel<T><<<(int)blocks, 256, 0, stream>>>(r, nchunks, P, ws.G);
   RSVD_CUDA(after_launch());

@@ -1,0 +1,267 @@
+// A-passes for a sparse A in compressed sparse row form (Section 3.6: the
+// sparse x dense product; Section 2.1 step 2 and Eq. (3)).
+//
+//   forward     Y = A X      one warp per row of A
+//   transposed  Z = A^T Y    the same kernel on the CSR of A^T (the CSC of A)
+//
+// Each warp owns one output row.  The row's entries are read 32 at a time
+// (one (column, value) pair per lane, coalesced), then broadcast lane by lane;
+// for each entry the warp gathers one row of the dense panel (r values, 16-byte
+// vector loads, lane l holding columns 4l..4l+3 + 128t) and accumulates in
+// FP32 registers in entry order, so every output row is a fixed sequence of
+// FMAs and the result does not depend on scheduling.  The gathers dominate: a
+// pass reads nnz * r * 4 bytes of panel rows, which the Zipf-skewed column
+// popularity of the sparse workloads serves largely from L2.
+//
+// The CSR of A^T is built on the host once (csr_transpose_host): a stable
+// counting sort over columns, split over threads by row ranges, so its entry
+// order (increasing row of A within each column) and hence the transposed
+// pass are deterministic.
+#include <algorithm>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rsvd {
+namespace {
+
+constexpr int kSpmmThreads = 256;
+
+__device__ __forceinline__ void fma4(float4& a, float v, const float4& x) {
+  a.x = fmaf(v, x.x, a.x);
+  a.y = fmaf(v, x.y, a.y);
+  a.z = fmaf(v, x.z, a.z);
+  a.w = fmaf(v, x.w, a.w);
+}
+
+// V4 float4 slots per lane: panel rows of at most 128*V4 floats.  X rows start
+// 16-byte aligned (X aligned, ldx % 4 == 0); columns r..4*ceil(r/4)-1 are read
+// (inside ldx) but never written to Y.
+template <int V4>
+__global__ void __launch_bounds__(kSpmmThreads)
+spmm_csr_vec_kernel(int64_t M, int r, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                    const float* __restrict__ val, const float* __restrict__ X, int64_t ldx, float* __restrict__ Y,
+                    int64_t ldy, int accumulate) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (kSpmmThreads / 32) + (threadIdx.x >> 5);
+  if (row >= M) return;
+  const int nv = (r + 3) >> 2;
+  float4 acc[V4];
+#pragma unroll
+  for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
+  for (int64_t b = e0; b < e1; b += 32) {
+    const int64_t e = b + lane;
+    int c = 0;
+    float v = 0.f;
+    if (e < e1) {
+      c = __ldg(colidx + e);
+      v = __ldg(val + e);
+    }
+    const int cnt = (int)(e1 - b < 32 ? e1 - b : 32);
+    int j = 0;
+    // four entries at a time: their gathers are issued before the FMAs
+    for (; j + 4 <= cnt; j += 4) {
+      int cj[4];
+      float vj[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cj[u] = __shfl_sync(0xffffffffu, c, j + u);
+        vj[u] = __shfl_sync(0xffffffffu, v, j + u);
+      }
+      float4 x[4][V4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4* xr = reinterpret_cast<const float4*>(X + (int64_t)cj[u] * ldx);
+#pragma unroll
+        for (int t = 0; t < V4; ++t) {
+          const int q = lane + 32 * t;
+          x[u][t] = q < nv ? __ldg(xr + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int t = 0; t < V4; ++t) fma4(acc[t], vj[u], x[u][t]);
+    }
+    for (; j < cnt; ++j) {
+      const int cj = __shfl_sync(0xffffffffu, c, j);
+      const float vj = __shfl_sync(0xffffffffu, v, j);
+      const float4* xr = reinterpret_cast<const float4*>(X + (int64_t)cj * ldx);
+#pragma unroll
+      for (int t = 0; t < V4; ++t) {
+        const int q = lane + 32 * t;
+        if (q < nv) fma4(acc[t], vj, __ldg(xr + q));
+      }
+    }
+  }
+  float* yr = Y + row * ldy;
+#pragma unroll
+  for (int t = 0; t < V4; ++t) {
+    const int q = lane + 32 * t;
+    if (q >= nv) continue;
+    const int c0 = 4 * q;
+    float4 o = acc[t];
+    if (c0 + 4 <= r) {
+      float4* p = reinterpret_cast<float4*>(yr + c0);
+      if (accumulate) {
+        const float4 y = *p;
+        o.x += y.x; o.y += y.y; o.z += y.z; o.w += y.w;
+      }
+      *p = o;
+    } else {  // the panel's last, partial group of four columns
+      yr[c0] = accumulate ? yr[c0] + o.x : o.x;
+      if (c0 + 1 < r) yr[c0 + 1] = accumulate ? yr[c0 + 1] + o.y : o.y;
+      if (c0 + 2 < r) yr[c0 + 2] = accumulate ? yr[c0 + 2] + o.z : o.z;
+    }
+  }
+}
+
+// Scalar variant for panels that are not 16-byte aligned: lane l holds columns
+// l + 32t, t < VS.
+template <int VS>
+__global__ void __launch_bounds__(kSpmmThreads)
+spmm_csr_scalar_kernel(int64_t M, int r, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                       const float* __restrict__ val, const float* __restrict__ X, int64_t ldx,
+                       float* __restrict__ Y, int64_t ldy, int accumulate) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (kSpmmThreads / 32) + (threadIdx.x >> 5);
+  if (row >= M) return;
+  float acc[VS];
+#pragma unroll
+  for (int t = 0; t < VS; ++t) acc[t] = 0.f;
+  const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
+  for (int64_t b = e0; b < e1; b += 32) {
+    const int64_t e = b + lane;
+    int c = 0;
+    float v = 0.f;
+    if (e < e1) {
+      c = __ldg(colidx + e);
+      v = __ldg(val + e);
+    }
+    const int cnt = (int)(e1 - b < 32 ? e1 - b : 32);
+    for (int j = 0; j < cnt; ++j) {
+      const int cj = __shfl_sync(0xffffffffu, c, j);
+      const float vj = __shfl_sync(0xffffffffu, v, j);
+      const float* xr = X + (int64_t)cj * ldx;
+#pragma unroll
+      for (int t = 0; t < VS; ++t) {
+        const int q = lane + 32 * t;
+        if (q < r) acc[t] = fmaf(vj, __ldg(xr + q), acc[t]);
+      }
+    }
+  }
+  float* yr = Y + row * ldy;
+#pragma unroll
+  for (int t = 0; t < VS; ++t) {
+    const int q = lane + 32 * t;
+    if (q < r) yr[q] = accumulate ? yr[q] + acc[t] : acc[t];
+  }
+}
+
+}  // namespace
+
+rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
+                     const float* X, int64_t ldx, float* Y, int64_t ldy, bool accumulate, cudaStream_t stream) {
+  if (M <= 0) return RSVD_OK;
+  if (r < 1 || r > kSpmmMaxR || ldx < r || ldy < r || !rowptr || !X || !Y)
+    return fail(RSVD_ERR_INVALID_ARG, "spmm_csr: bad arguments");
+  const int64_t blocks = cdiv(M, kSpmmThreads / 32);
+  if (blocks > 0x7fffffffLL) return fail(RSVD_ERR_INVALID_ARG, "spmm_csr: too many rows");
+  const int acc = accumulate ? 1 : 0;
+  const bool vec = ldx % 4 == 0 && ldy % 4 == 0 && aligned16(X) && aligned16(Y);
+  const dim3 grid((unsigned)blocks);
+  if (vec) {
+    const int v4 = (int)cdiv(cdiv(r, 4), 32);
+#define RSVD_VEC(V) spmm_csr_vec_kernel<V><<<grid, kSpmmThreads, 0, stream>>>(M, r, rowptr, colidx, val, X, ldx, Y, ldy, acc)
+    switch (v4) {
+      case 1: RSVD_VEC(1); break;
+      case 2: RSVD_VEC(2); break;
+      case 3: RSVD_VEC(3); break;
+      default: RSVD_VEC(4); break;
+    }
+#undef RSVD_VEC
+  } else {
+    const int vs = (int)cdiv(r, 32);
+#define RSVD_SCA(V) spmm_csr_scalar_kernel<V><<<grid, kSpmmThreads, 0, stream>>>(M, r, rowptr, colidx, val, X, ldx, Y, ldy, acc)
+    if (vs <= 4) RSVD_SCA(4);
+    else if (vs <= 8) RSVD_SCA(8);
+    else RSVD_SCA(16);
+#undef RSVD_SCA
+  }
+  RSVD_CUDA(after_launch());
+  return RSVD_OK;
+}
+
+// Stable counting-sort transpose on the host.  Rows are split into T ranges of
+// about equal entry counts; thread t counts its entries per column, the
+// per-(thread, column) offsets are laid out column-major (thread 0 first), and
+// every thread scatters its rows in increasing order, so the entries of each
+// output row come in increasing row index of A whatever T is.
+rsvd_status csr_transpose_host(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                               const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val) {
+  if (m < 0 || n < 0 || !rowptr || !t_rowptr) return fail(RSVD_ERR_INVALID_ARG, "csr_transpose: bad arguments");
+  if (rowptr[0] != 0) return fail(RSVD_ERR_INVALID_ARG, "csr_transpose: rowptr[0] != 0");
+  for (int64_t i = 0; i < m; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return fail(RSVD_ERR_INVALID_ARG, "csr_transpose: rowptr decreases");
+  const int64_t nnz = rowptr[m];
+  if (nnz > 0 && (!colidx || !val || !t_colidx || !t_val))
+    return fail(RSVD_ERR_INVALID_ARG, "csr_transpose: NULL index or value array");
+  unsigned hw = std::thread::hardware_concurrency();
+  int T = (int)std::min<int64_t>({(int64_t)(hw ? hw : 1), 32, std::max<int64_t>(1, nnz >> 20)});
+  if (T < 1) T = 1;
+  std::vector<int64_t> r0(T + 1);
+  for (int t = 0; t <= T; ++t) {
+    const int64_t target = nnz * t / T;
+    r0[t] = t == T ? m : std::lower_bound(rowptr, rowptr + m + 1, (int32_t)target) - rowptr;
+    if (r0[t] > m) r0[t] = m;
+  }
+  for (int t = 1; t <= T; ++t)
+    if (r0[t] < r0[t - 1]) r0[t] = r0[t - 1];
+  std::vector<int64_t> cnt((size_t)T * n, 0);  // cnt[t*n + j]
+  std::vector<int> bad(T, 0);
+  auto count = [&](int t) {
+    int64_t* c = cnt.data() + (size_t)t * n;
+    for (int64_t i = r0[t]; i < r0[t + 1]; ++i)
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int32_t j = colidx[e];
+        if (j < 0 || j >= n) { bad[t] = 1; return; }
+        ++c[j];
+      }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < T; ++t) th.emplace_back(count, t);
+  count(0);
+  for (auto& x : th) x.join();
+  th.clear();
+  for (int t = 0; t < T; ++t)
+    if (bad[t]) return fail(RSVD_ERR_INVALID_ARG, "csr_transpose: column index out of range");
+  // offsets: column j's block starts at t_rowptr[j]; thread t writes after threads < t
+  int64_t run = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    t_rowptr[j] = (int32_t)run;
+    for (int t = 0; t < T; ++t) {
+      const int64_t c = cnt[(size_t)t * n + j];
+      cnt[(size_t)t * n + j] = run;
+      run += c;
+    }
+  }
+  t_rowptr[n] = (int32_t)run;
+  auto scatter = [&](int t) {
+    int64_t* off = cnt.data() + (size_t)t * n;
+    for (int64_t i = r0[t]; i < r0[t + 1]; ++i)
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int64_t pos = off[colidx[e]]++;
+        t_colidx[pos] = (int32_t)i;
+        t_val[pos] = val[e];
+      }
+  };
+  for (int t = 1; t < T; ++t) th.emplace_back(scatter, t);
+  scatter(0);
+  for (auto& x : th) x.join();
+  return RSVD_OK;
+}
+
+}  // namespace rsvd

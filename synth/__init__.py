@@ -16,4 +16,4 @@ from .dense import (  # noqa: F401
     prescribed_dense, prescribed_dense_torch, lowrank_plus_noise_torch, LowRankPlusNoise,
     WORKLOADS, Workload,
 )
-from .sparse import zipf_csr  # noqa: F401
+from .sparse import zipf_csr, zipf_csr_torch  # noqa: F401

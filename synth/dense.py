@@ -149,6 +149,10 @@ WORKLOADS = {
         "dense_fp32_600000x100000_ooc", 600000, 100000, 200, 40, 2, 2003, 1003, 3003, 8192,
         "dense FP32 600000x100000 (240 GB) in pinned host memory, s_i = exp(-i/50) + 1e-3 floor, "
         "k=200 p=40 q=2, 8192^2 tiles streamed under a 64 GB device cap"),
+    "csr_fp32_5000000x1000000": Workload(
+        "csr_fp32_5000000x1000000", 5_000_000, 1_000_000, 300, 50, 3, 2004, 1004, 3004, 0,
+        "CSR 5e6 x 1e6, 5e8 entries: rank-size row lengths min(20000, C rho^-1.1), Zipf(1.0) "
+        "columns, values log(1 + Poisson(3 | >= 1)) * idf; k=300 p=50 q=3"),
     "dense_fp32_20000x10000_diff": Workload(
         "dense_fp32_20000x10000_diff", 20000, 10000, 64, 16, 2, 2005, 1005, 3005, 4096,
         "dense FP32 20000x10000, s_i = 10*0.95^(i-1), k=64 p=16 q=2 (differentiable)"),

@@ -19,19 +19,21 @@ def _row_lengths(m, nnz_target, cap, n):
     if not m <= nnz_target <= m * cap:
         raise ValueError(f"nnz target {nnz_target} outside [m, m*cap] = [{m}, {m * cap}]")
 
+    w = rho ** -1.1
+
     def total(C):
-        return np.minimum(cap, np.maximum(1, np.floor(C * rho ** -1.1))).sum()
+        return np.minimum(cap, np.maximum(1, np.floor(C * w))).sum()
 
     lo, hi = 0.0, 1.0
     while total(hi) < nnz_target:
         hi *= 2
-    for _ in range(200):
+    for _ in range(64):          # hi - lo shrinks to below one unit in the last place
         mid = 0.5 * (lo + hi)
         if total(mid) < nnz_target:
             lo = mid
         else:
             hi = mid
-    return np.minimum(cap, np.maximum(1, np.floor(hi * rho ** -1.1))).astype(np.int64)
+    return np.minimum(cap, np.maximum(1, np.floor(hi * w))).astype(np.int64)
 
 
 def zipf_csr(m, n, nnz_target, seed, cap=20000):
@@ -85,3 +87,79 @@ def zipf_csr(m, n, nnz_target, seed, cap=20000):
         P[z] = rng.poisson(3.0, size=int(z.sum()))
     val = (np.log1p(P) * idf[cols]).astype(np.float32)
     return rowptr.astype(np.int32), cols.astype(np.int32), val
+
+
+def zipf_csr_torch(m, n, nnz_target, seed, cap=20000, device="cuda"):
+    """The same recipe drawn with torch on a device, for sizes the host draws
+    too slowly (the full sparse workload has 5e8 entries).
+
+    Returns (rowptr int32, colidx int32, val float32) as device tensors.  Row
+    lengths and their permutation are those of ``zipf_csr`` for the same seed;
+    column and value draws come from a torch generator seeded with ``seed``, so
+    the matrix is the same recipe but not the same matrix as ``zipf_csr``.
+    """
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cap = max(1, min(cap, n // 50))
+    L_np = _row_lengths(m, nnz_target, cap, n)[rng.permutation(m)]
+    L = torch.as_tensor(L_np, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    w = 1.0 / torch.arange(1, n + 1, dtype=torch.float64, device=device)
+    cdf = torch.cumsum(w, 0)
+    cdf /= cdf[-1].clone()
+    done = []
+    pend = torch.empty(0, dtype=torch.int64, device=device)
+    need = L.clone()
+    for _ in range(200):
+        short = torch.nonzero(need > 0).flatten()
+        if short.numel() == 0:
+            break
+        rows = torch.repeat_interleave(short, 2 * need[short] + 4)
+        u = torch.rand(rows.numel(), generator=gen, dtype=torch.float64, device=device)
+        cols = torch.searchsorted(cdf, u).clamp_(max=n - 1)
+        del u
+        pend = torch.unique(torch.cat([pend, rows * n + cols]))
+        del rows, cols
+        prow = pend // n
+        cnt = torch.bincount(prow, minlength=m)
+        need = torch.where(need > 0, (L - cnt).clamp(min=0), torch.zeros_like(need))
+        complete = (need == 0)[prow]
+        done.append(pend[complete])
+        pend = pend[~complete]
+        del prow, cnt, complete
+    keys = torch.cat(done)
+    del done, pend
+    rows = keys // n
+    # rows with more distinct columns than their length keep a random subset:
+    # order by (row, random priority), keep the first L[row]
+    prio = torch.randint(0, 1 << 30, (keys.numel(),), generator=gen, device=device)
+    order = torch.argsort(rows * (1 << 30) + prio)
+    del prio
+    keys = keys[order]
+    rows = rows[order]
+    del order
+    cnt = torch.bincount(rows, minlength=m)
+    start = torch.cumsum(cnt, 0) - cnt
+    rank = torch.arange(keys.numel(), device=device) - start[rows]
+    keep = rank < L[rows]
+    del rank, start
+    keys = torch.sort(keys[keep]).values
+    del keep, rows
+    rows = keys // n
+    cols = keys % n
+    del keys
+    rowptr = torch.zeros(m + 1, dtype=torch.int64, device=device)
+    rowptr[1:] = torch.cumsum(torch.bincount(rows, minlength=m), 0)
+    del rows
+    df = torch.bincount(cols, minlength=n).to(torch.float64)
+    idf = torch.log1p(m / (1.0 + df))
+    P = torch.poisson(torch.full((cols.numel(),), 3.0, device=device), generator=gen)
+    while True:
+        z = P == 0
+        nz = int(z.sum())
+        if nz == 0:
+            break
+        P[z] = torch.poisson(torch.full((nz,), 3.0, device=device), generator=gen)
+    val = (torch.log1p(P.to(torch.float64)) * idf[cols]).to(torch.float32)
+    return rowptr.to(torch.int32), cols.to(torch.int32), val

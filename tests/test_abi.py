@@ -75,3 +75,74 @@ def test_min_cap_grows_with_the_problem(lib):
 def test_status_strings(lib):
     for code, name in {0: b"RSVD_OK", 5: b"RSVD_ERR_NOT_SPD", 7: b"RSVD_ERR_TIMEOUT"}.items():
         assert lib.rsvd_status_str(code) == name
+
+
+def _csr_ptrs(rp, ci, v):
+    import numpy as np
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    ci = np.ascontiguousarray(ci, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    return rp, ci, v
+
+
+def _lib_transpose(lib, m, n, rp, ci, v):
+    import numpy as np
+    rp, ci, v = _csr_ptrs(rp, ci, v)
+    nnz = int(rp[-1]) if rp.size else 0
+    trp = np.full(n + 1, -7, dtype=np.int32)
+    tci = np.full(max(nnz, 1), -7, dtype=np.int32)
+    tv = np.full(max(nnz, 1), np.nan, dtype=np.float32)
+    P = lambda a: a.ctypes.data_as(C.c_void_p)
+    st = lib.rsvd_csr_transpose(m, n, P(rp), P(ci), P(v), P(trp), P(tci), P(tv))
+    return st, trp, tci[:nnz], tv[:nnz]
+
+
+@pytest.mark.parametrize("m,n,nnz,seed", [(300, 200, 1000, 3), (20000, 5000, 400000, 1004),
+                                          (200000, 50000, 4_000_000, 1104)])
+def test_csr_transpose_is_bit_exact_with_oracle(lib, m, n, nnz, seed):
+    """The library's host transpose (threaded for large nnz) against the oracle's
+    entry-by-entry scatter, on the sparse workload's generator."""
+    import numpy as np
+    from synth import zipf_csr
+    rp, ci, v = zipf_csr(m, n, nnz, seed)
+    st, trp, tci, tv = _lib_transpose(lib, m, n, rp, ci, v)
+    assert st == 0
+    if nnz <= 400000:
+        orp, oci, ov = T.csr_transpose(m, n, rp, ci, v)
+    else:  # the oracle's Python scatter is slow at 4e6 entries: use its definition via a stable sort
+        order = np.lexsort((np.repeat(np.arange(m), np.diff(rp)), ci))
+        oci = np.repeat(np.arange(m), np.diff(rp))[order]
+        ov = v[order]
+        orp = np.concatenate([[0], np.cumsum(np.bincount(ci, minlength=n))])
+    assert np.array_equal(trp, orp) and np.array_equal(tci, oci) and np.array_equal(tv.view(np.uint32), np.asarray(ov, np.float32).view(np.uint32))
+
+
+def test_csr_transpose_edge_cases(lib):
+    import numpy as np
+    # empty rows and columns, one dense row, nnz = 0
+    rp = [0, 0, 3, 3, 4]
+    ci = [0, 2, 5, 5]
+    v = [1.0, 2.0, 3.0, 4.0]
+    st, trp, tci, tv = _lib_transpose(lib, 4, 6, rp, ci, v)
+    assert st == 0
+    assert trp.tolist() == [0, 1, 1, 2, 2, 2, 4]
+    assert tci.tolist() == [1, 1, 1, 3] and tv.tolist() == [1.0, 2.0, 3.0, 4.0]
+    st, trp, tci, tv = _lib_transpose(lib, 3, 2, [0, 0, 0, 0], [], [])
+    assert st == 0 and trp.tolist() == [0, 0, 0]
+    # a column index out of range and a decreasing rowptr are rejected
+    assert _lib_transpose(lib, 2, 3, [0, 1, 2], [0, 3], [1.0, 1.0])[0] == 1
+    assert _lib_transpose(lib, 2, 3, [0, 2, 1], [0, 1], [1.0, 1.0])[0] == 1
+
+
+def test_csr_plan_rules(lib):
+    from paper_1907_06470_gb300 import _lib
+    h = C.c_void_p()
+    # CSR plans take r up to 512, FP32 values and precision only
+    o = _lib.RsvdOpts(prec=1, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
+    out = C.c_size_t()
+    assert lib.rsvd_plan_min_cap(100000, 50000, 300, 50, C.byref(o), C.byref(out)) == 0
+    o513 = _lib.RsvdOpts(prec=1, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
+    assert lib.rsvd_plan_min_cap(100000, 50000, 500, 13, C.byref(o513), C.byref(out)) == 1
+    ob = _lib.RsvdOpts(prec=2, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
+    assert lib.rsvd_plan(1000, 500, 10, 5, 1, 1, 0, C.byref(ob), C.byref(h)) == 8
+    assert h.value is None

@@ -1,0 +1,170 @@
+"""Sparse (CSR) A-passes and the randomized SVD of a CSR matrix (Section 3.6
+sparse x dense products, Section 2.1 steps 1-7) against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+from oracle import linalg as OL
+from oracle import rsvd as OR
+from oracle import tiles as OT
+from synth import zipf_csr
+from tests.metrics import cluster_safe_angles, sigma_rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1907_06470_gb300 as g
+    g.load()
+    return g
+
+
+@pytest.fixture(scope="module")
+def zipf():
+    """The sparse workload's recipe scaled to 20000 x 5000 with 4e5 entries."""
+    m, n = 20000, 5000
+    rp, ci, v = zipf_csr(m, n, 400000, 1004)
+    return m, n, rp, ci, v
+
+
+@pytest.fixture(scope="module")
+def zipf_abs(zipf):
+    """|A| and |A|^T (oracle CSR) for the rounding bounds."""
+    m, n, rp, ci, v = zipf
+    trp, tci, tv = OT.csr_transpose(m, n, rp, ci, np.abs(v))
+    return OL.CSR(m, n, rp, ci, np.abs(v)), OL.CSR(n, m, trp, tci, tv)
+
+
+def _torch_csr(m, n, rp, ci, v, device):
+    return torch.sparse_csr_tensor(torch.as_tensor(rp), torch.as_tensor(ci), torch.as_tensor(v),
+                                   size=(m, n), device=device)
+
+
+def _fp32_product_bound(A_abs_csr, X):
+    """Per-entry bound on the FP32 accumulation error: gamma_L |A| |X| with L the
+    longest row, gamma_L = L u / (1 - L u), u = 2^-24."""
+    L = int(np.max(np.diff(A_abs_csr.rowptr)))
+    u = 2.0 ** -24
+    gam = (L + 1) * u / (1 - (L + 1) * u)
+    return gam * OL.csr_apply(A_abs_csr, np.abs(X))
+
+
+@pytest.mark.parametrize("r", [1, 7, 120, 350, 512])
+@pytest.mark.parametrize("aligned", [True, False])
+def test_csr_apass_matches_oracle(g, zipf, zipf_abs, r, aligned):
+    m, n, rp, ci, v = zipf
+    A = OL.CSR(m, n, rp, ci, v)
+    Aabs, Atabs = zipf_abs
+    rng = np.random.default_rng(r)
+    # the panel is rounded to FP32 first, so both sides multiply the same numbers
+    X = rng.standard_normal((n, r)).astype(np.float32)
+    Yt = rng.standard_normal((m, r)).astype(np.float32)
+    Ad = _torch_csr(m, n, rp, ci, v, "cuda")
+    Atd = g.csr_transpose(_torch_csr(m, n, rp, ci, v, "cpu")).to("cuda")
+    if aligned:
+        Xd = torch.as_tensor(X, device="cuda")
+        Ytd = torch.as_tensor(Yt, device="cuda")
+    else:  # leading dimension r + 1: the scalar kernel
+        Xd = torch.zeros(n, r + 1, device="cuda")[:, :r]
+        Xd.copy_(torch.as_tensor(X))
+        Ytd = torch.zeros(m, r + 1, device="cuda")[:, :r]
+        Ytd.copy_(torch.as_tensor(Yt))
+    Y = g.apass(Ad, Xd, trans=False).cpu().numpy().astype(np.float64)
+    Z = g.apass(Ad, Ytd, trans=True, At=Atd).cpu().numpy().astype(np.float64)
+    Yo = OL.csr_apply(A, X.astype(np.float64))
+    Zo = OL.csr_apply(A, Yt.astype(np.float64), trans=True)
+    assert np.all(np.abs(Y - Yo) <= _fp32_product_bound(Aabs, X) + 1e-30)
+    assert np.all(np.abs(Z - Zo) <= _fp32_product_bound(Atabs, Yt) + 1e-30)
+
+
+def test_csr_apass_is_deterministic(g, zipf):
+    m, n, rp, ci, v = zipf
+    Ad = _torch_csr(m, n, rp, ci, v, "cuda")
+    X = torch.randn(n, 120, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    Y1 = g.apass(Ad, X)
+    Y2 = g.apass(Ad, X)
+    assert torch.equal(Y1, Y2)
+
+
+def test_csr_rsvd_scaled_sparse_workload_matches_oracle(g, zipf):
+    """k=64 p=16 q=3 on the scaled recipe; FP32 path against the FP64 oracle."""
+    m, n, rp, ci, v = zipf
+    k, p, q, seed = 64, 16, 3, 2004
+    U, S, V = g.rsvd(_torch_csr(m, n, rp, ci, v, "cuda"), k, p, q, seed)
+    U, S, V = (t.cpu().numpy().astype(np.float64) for t in (U, S, V))
+    Uo, So, Vo = OR.rsvd(OL.CSR(m, n, rp, ci, v), k, p, q, seed, "f32")
+    assert sigma_rel_err(S, So) <= 1e-5
+    assert cluster_safe_angles(U, Uo, So, 8, rel_gap=1e-2) <= 1e-4
+    assert cluster_safe_angles(V, Vo, So, 8, rel_gap=1e-2) <= 1e-4
+
+
+def test_csr_input_locations_agree_bitwise(g, zipf):
+    """Device CSR with the library-built transpose, device CSR with a caller
+    transpose, and host CSR: the same kernels on the same arrays."""
+    m, n, rp, ci, v = zipf
+    k, p, q, seed = 20, 10, 2, 7
+    host = _torch_csr(m, n, rp, ci, v, "cpu")
+    At = g.csr_transpose(host)
+    a = g.rsvd(host.to("cuda"), k, p, q, seed)
+    b = g.rsvd(host.to("cuda"), k, p, q, seed, At=At.to("cuda"))
+    c = g.rsvd(host, k, p, q, seed)
+    d = g.rsvd(host, k, p, q, seed, At=At)
+    for x in (b, c, d):
+        for s, t in zip(a, x):
+            assert torch.equal(s, t)
+
+
+def test_csr_rsvd_r350_matches_oracle(g):
+    """r = k + p = 350 (the sparse workload's sketch width): the FP64-only Jacobi
+    and the global-memory Cholesky."""
+    m, n = 6000, 3000
+    rp, ci, v = zipf_csr(m, n, 120000, 1005)
+    k, p, q, seed = 300, 50, 1, 2005
+    U, S, V = g.rsvd(_torch_csr(m, n, rp, ci, v, "cuda"), k, p, q, seed)
+    S = S.cpu().numpy().astype(np.float64)
+    Uo, So, Vo = OR.rsvd(OL.CSR(m, n, rp, ci, v), k, p, q, seed, "f32")
+    assert sigma_rel_err(S, So) <= 1e-5
+    U = U.cpu().numpy().astype(np.float64)
+    assert cluster_safe_angles(U, Uo, So, 4, rel_gap=1e-2) <= 1e-4
+
+
+def test_csr_with_empty_rows_and_columns(g):
+    rng = np.random.default_rng(5)
+    m, n = 3000, 1000
+    D = (rng.random((m, n)) < 0.01) * rng.random((m, n))
+    D[::7] = 0.0          # empty rows
+    D[:, ::5] = 0.0       # empty columns
+    D = D.astype(np.float32)
+    Ssp = torch.as_tensor(D).to_sparse_csr()
+    k, p, q, seed = 16, 8, 2, 11
+    U, S, V = g.rsvd(Ssp.to("cuda"), k, p, q, seed)
+    Uo, So, Vo = OR.rsvd(D, k, p, q, seed, "f32")
+    assert sigma_rel_err(S.cpu().numpy(), So) <= 1e-5
+    # V has no weight on the empty columns
+    assert float(V[::5].abs().max()) < 1e-6
+
+
+def test_csr_zero_matrix_gives_zero_spectrum(g):
+    m, n = 500, 300
+    Z = torch.sparse_csr_tensor(torch.zeros(m + 1, dtype=torch.int32), torch.zeros(0, dtype=torch.int32),
+                                torch.zeros(0), size=(m, n))
+    U, S, V = g.rsvd(Z.to("cuda"), 5, 5, 1, 3)
+    assert float(S.abs().max()) == 0.0
+    assert torch.isfinite(U).all() and torch.isfinite(V).all()
+
+
+def test_csr_cap_too_small_for_the_copies(g, zipf):
+    m, n, rp, ci, v = zipf
+    from paper_1907_06470_gb300 import _lib
+    import ctypes as C
+    o = _lib.RsvdOpts(prec=1, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
+    out = C.c_size_t()
+    assert g.load().rsvd_plan_min_cap(m, n, 10, 5, C.byref(o), C.byref(out)) == 0
+    plan = g.Plan(m, n, 10, 5, 1, 0, mem_cap=out.value + 4096, kind="csr")
+    with pytest.raises(g.RsvdError) as e:
+        plan.run(_torch_csr(m, n, rp, ci, v, "cpu"))
+    assert "CAP_TOO_SMALL" in str(e.value)
+    plan.close()
