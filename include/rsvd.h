@@ -287,8 +287,13 @@ rsvd_status rsvd_small_svd(int32_t r, const double* Mc, double* sigma, double* U
  * Y = A^T X (trans = 1, using A.t_rowptr/t_colidx/t_val, which must be set)
  * for a CSR device matrix with FP32 values, FP32 panels, FP32 accumulation in
  * entry order (deterministic).  X: K x r row-major (ldx), Y: M x r row-major
- * (ldy), overwritten; r <= 512.  Goes through rsvd_apass with prec FP32 and no
- * workspace (ws may be NULL).  Enqueues only. */
+ * (ldy), overwritten; r <= 512.  Goes through rsvd_apass with prec FP32 (mb,
+ * nb ignored).  The workspace is optional: ws may be NULL, and then every row
+ * is summed by one warp; with ws_bytes >= rsvd_spmm_workspace(A.nnz, r), rows
+ * of more than 4096 entries are split into 4096-entry segments summed by
+ * separate warps and added in segment order (same result for any timing).
+ * A.nnz must equal rowptr[M] of the CSR used.  Enqueues only. */
+size_t rsvd_spmm_workspace(int64_t nnz, int32_t r);
 
 /* Host (CPU) transpose of a CSR matrix: from the CSR of the m x n matrix A
  * (rowptr m+1, colidx and val nnz = rowptr[m]) writes the CSR of A^T into

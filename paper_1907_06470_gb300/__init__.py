@@ -284,10 +284,11 @@ def tile_map(m, n, mb, nb, n_slots=2):
     return [(x.t, x.I, x.J, x.row0, x.row1, x.col0, x.col1, x.slot) for x in arr[:cnt.value]]
 
 
-def apass(A, X, trans=False, prec=None, mb=0, nb=0, out=None, At=None):
+def apass(A, X, trans=False, prec=None, mb=0, nb=0, out=None, At=None, split_long_rows=True):
     """One A-pass: A @ X (trans=False) or A.T @ X (trans=True), on the library's kernels.
 
-    A sparse CSR A (CUDA, float32) needs `At`, the CSR of A^T, for trans=True."""
+    A sparse CSR A (CUDA, float32) needs `At`, the CSR of A^T, for trans=True;
+    `split_long_rows` gives the call the workspace that splits long rows."""
     torch = _torch()
     if _is_csr(A):
         m, n = A.shape
@@ -295,9 +296,12 @@ def apass(A, X, trans=False, prec=None, mb=0, nb=0, out=None, At=None):
         if out is None:
             out = torch.empty(n if trans else m, r, dtype=torch.float32, device=A.device)
         d, keep = _csr_desc(A, At)
-        _check(load().rsvd_apass(C.byref(d), int(trans), _lib.PREC["fp32"], r, C.c_void_p(X.data_ptr()),
-                                 X.stride(0), C.c_void_p(out.data_ptr()), out.stride(0), 0, 0, None, 0,
-                                 _stream_ptr()))
+        lib = load()
+        wsb = lib.rsvd_spmm_workspace(d.nnz, r) if split_long_rows else 0
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=A.device)
+        _check(lib.rsvd_apass(C.byref(d), int(trans), _lib.PREC["fp32"], r, C.c_void_p(X.data_ptr()),
+                              X.stride(0), C.c_void_p(out.data_ptr()), out.stride(0), 0, 0,
+                              C.c_void_p(ws.data_ptr() if wsb else None), wsb, _stream_ptr()))
         del keep
         return out
     if prec is None:

@@ -72,6 +72,7 @@ SIGNATURES = {
     "rsvd_small_svd": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "rsvd_small_svd_noalloc": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "rsvd_csr_transpose": (c_i32, [c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "rsvd_spmm_workspace": (c_size, [c_i64, c_i32]),
 }
 NOALLOC_MAX_R = 256
 

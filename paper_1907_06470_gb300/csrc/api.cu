@@ -209,8 +209,10 @@ struct rsvd_plan_s {
   StreamState* ss = nullptr;       // out-of-core state (created on the first streamed run)
   bool streaming = false;          // the current run streams A from the host
   int kind = RSVD_DENSE;           // rsvd_kind the plan runs on
-  void* csr_dev = nullptr;         // device copies of a CSR A and/or its transpose
+  void* csr_dev = nullptr;         // device copies of a CSR A and/or its transpose, SpMM workspace
   size_t csr_dev_bytes = 0;
+  void* spmm_ws = nullptr;         // long-row tasks of the CSR passes (inside csr_dev)
+  size_t spmm_ws_bytes = 0;
   std::vector<int32_t> h_idx;      // host staging for a transpose built by the library
   std::vector<float> h_val;
   Profiler prof;
@@ -316,8 +318,10 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     ++pf.apass_calls;
     if constexpr (std::is_same<T, float>::value) {
       if (A.kind == RSVD_CSR)  // Section 3.6: sparse x dense; A^T through the CSR of A^T
-        return trans ? spmm_csr(n, r, A.t_rowptr, A.t_colidx, A.t_val, Xin, ldr, Yout, ldr, false, st)
-                     : spmm_csr(m, r, A.rowptr, A.colidx, A.val, Xin, ldr, Yout, ldr, false, st);
+        return trans ? spmm_csr(n, r, A.t_rowptr, A.t_colidx, A.t_val, A.nnz, Xin, ldr, Yout, ldr, false,
+                                P->spmm_ws, P->spmm_ws_bytes, st)
+                     : spmm_csr(m, r, A.rowptr, A.colidx, A.val, A.nnz, Xin, ldr, Yout, ldr, false, P->spmm_ws,
+                                P->spmm_ws_bytes, st);
     }
     if (P->streaming) return apass_streamed(P->ss, A, trans, pr, r, Xin, Yout, ldr, P->status, st);
     return apass_dense(A, trans, pr, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes,
@@ -413,10 +417,11 @@ rsvd_status prepare_csr(rsvd_plan_s* P, const rsvd_matrix& A, rsvd_matrix* out, 
   // device bytes needed: A's arrays when on the host, the transpose when on the host or built here
   const size_t a_bytes = host ? (size_t)(m + 1) * 4 + (size_t)nnz * 8 : 0;
   const size_t t_bytes = (host || !have_t) ? (size_t)(n + 1) * 4 + (size_t)nnz * 8 : 0;
-  const size_t need = a_bytes + t_bytes + 1024;
-  if (a_bytes + t_bytes > 0) {
+  const size_t sws = spmm_ws_bytes(nnz, P->r);
+  const size_t need = a_bytes + t_bytes + sws + 1024;
+  {
     if (P->mem_cap && P->ws_bytes + need > P->mem_cap)
-      return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: the CSR copies do not fit under mem_cap");
+      return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: the CSR copies and SpMM workspace do not fit under mem_cap");
     if (P->csr_dev_bytes < need) {
       if (P->csr_dev) cudaFree(P->csr_dev);
       P->csr_dev = nullptr;
@@ -425,6 +430,8 @@ rsvd_status prepare_csr(rsvd_plan_s* P, const rsvd_matrix& A, rsvd_matrix* out, 
       P->csr_dev_bytes = need;
     }
     Carver c(P->csr_dev, P->csr_dev_bytes);
+    P->spmm_ws = c.take<char>(sws);
+    P->spmm_ws_bytes = sws;
     if (host) {
       int32_t* rp = c.take<int32_t>((size_t)m + 1);
       int32_t* ci = c.take<int32_t>((size_t)nnz);
@@ -496,6 +503,8 @@ rsvd_status rsvd_tile_map(int64_t m, int64_t n, int64_t mb, int64_t nb, int32_t 
   return RSVD_OK;
 }
 
+size_t rsvd_spmm_workspace(int64_t nnz, int32_t r) { return spmm_ws_bytes(nnz < 0 ? 0 : nnz, r); }
+
 size_t rsvd_apass_workspace(int64_t m, int64_t n, int32_t r, int32_t trans, int32_t prec, int64_t mb,
                             int64_t nb) {
   return apass_ws_bytes(m, n, r, trans, prec, mb, nb) + 512;
@@ -514,8 +523,8 @@ rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_
     const float* v = trans ? A->t_val : A->val;
     if (!rp || (A->nnz > 0 && (!ci || !v)))
       return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: CSR arrays missing (trans = 1 needs t_rowptr/t_colidx/t_val)");
-    return spmm_csr(trans ? A->n : A->m, r, rp, ci, v, static_cast<const float*>(X), ldx, static_cast<float*>(Y),
-                    ldy, false, as_stream(stream));
+    return spmm_csr(trans ? A->n : A->m, r, rp, ci, v, A->nnz, static_cast<const float*>(X), ldx,
+                    static_cast<float*>(Y), ldy, false, ws, ws_bytes, as_stream(stream));
   }
   if (r > 256) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: r must not exceed 256 (dense)");
   if (A->kind == RSVD_DENSE && A->ld < A->n) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: ld < n");

@@ -106,9 +106,18 @@ rsvd_status backward_typed(int64_t m, int64_t n, int k, const T* U, const T* S, 
 
 // spmm.cu -- A-passes for a CSR matrix (FP32 values, int32 indices).
 constexpr int kSpmmMaxR = 512;
-// Y (M x r, ldy) = (or +=) A X for the M-row CSR (rowptr, colidx, val), X row-major (ldx).
+// Rows with more entries than this are split into segments of this many
+// entries, one warp each, when the workspace allows.
+constexpr int kSpmmSeg = 4096;
+// Upper bound on the segment tasks of a matrix with nnz entries: each long
+// row of len entries takes ceil(len/kSpmmSeg) < 2 len/kSpmmSeg tasks.
+inline int64_t spmm_max_tasks(int64_t nnz) { return 2 * (nnz / kSpmmSeg) + 1; }
+size_t spmm_ws_bytes(int64_t nnz, int r);
+// Y (M x r, ldy) = (or +=) A X for the M-row CSR (rowptr, colidx, val; nnz
+// entries), X row-major (ldx).  ws (may be NULL) enables the long-row split.
 rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
-                     const float* X, int64_t ldx, float* Y, int64_t ldy, bool accumulate, cudaStream_t stream);
+                     int64_t nnz, const float* X, int64_t ldx, float* Y, int64_t ldy, bool accumulate, void* ws,
+                     size_t ws_bytes, cudaStream_t stream);
 // Host CSR of A^T (n rows) from the CSR of A (m rows); stable, deterministic.
 rsvd_status csr_transpose_host(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                                const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val);

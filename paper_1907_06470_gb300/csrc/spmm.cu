@@ -39,19 +39,11 @@ __device__ __forceinline__ void fma4(float4& a, float v, const float4& x) {
 // V4 float4 slots per lane: panel rows of at most 128*V4 floats.  X rows start
 // 16-byte aligned (X aligned, ldx % 4 == 0); columns r..4*ceil(r/4)-1 are read
 // (inside ldx) but never written to Y.
+// Sum over entries [e0, e1) of one row into acc (lane l: columns 4l..4l+3 + 128t).
 template <int V4>
-__global__ void __launch_bounds__(kSpmmThreads)
-spmm_csr_vec_kernel(int64_t M, int r, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                    const float* __restrict__ val, const float* __restrict__ X, int64_t ldx, float* __restrict__ Y,
-                    int64_t ldy, int accumulate) {
-  const int lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (kSpmmThreads / 32) + (threadIdx.x >> 5);
-  if (row >= M) return;
-  const int nv = (r + 3) >> 2;
-  float4 acc[V4];
-#pragma unroll
-  for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
+__device__ __forceinline__ void row_segment_vec(int64_t e0, int64_t e1, int lane, int nv,
+                                                const int32_t* __restrict__ colidx, const float* __restrict__ val,
+                                                const float* __restrict__ X, int64_t ldx, float4 (&acc)[V4]) {
   for (int64_t b = e0; b < e1; b += 32) {
     const int64_t e = b + lane;
     int c = 0;
@@ -97,7 +89,12 @@ spmm_csr_vec_kernel(int64_t M, int r, const int32_t* __restrict__ rowptr, const 
       }
     }
   }
-  float* yr = Y + row * ldy;
+}
+
+// Write (or add) acc to the output row yr, columns < r only.
+template <int V4>
+__device__ __forceinline__ void store_row_vec(float* yr, int r, int lane, int nv, int accumulate,
+                                              const float4 (&acc)[V4]) {
 #pragma unroll
   for (int t = 0; t < V4; ++t) {
     const int q = lane + 32 * t;
@@ -117,6 +114,104 @@ spmm_csr_vec_kernel(int64_t M, int r, const int32_t* __restrict__ rowptr, const 
       if (c0 + 2 < r) yr[c0 + 2] = accumulate ? yr[c0 + 2] + o.z : o.z;
     }
   }
+}
+
+// One warp per row.  With split != 0, rows of more than kSpmmSeg entries are
+// left to the segment tasks (spmm_segment_kernel + spmm_combine_kernel).
+template <int V4>
+__global__ void __launch_bounds__(kSpmmThreads)
+spmm_csr_vec_kernel(int64_t M, int r, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                    const float* __restrict__ val, const float* __restrict__ X, int64_t ldx, float* __restrict__ Y,
+                    int64_t ldy, int accumulate, int split) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (kSpmmThreads / 32) + (threadIdx.x >> 5);
+  if (row >= M) return;
+  const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
+  if (split && e1 - e0 > kSpmmSeg) return;
+  const int nv = (r + 3) >> 2;
+  float4 acc[V4];
+#pragma unroll
+  for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  row_segment_vec<V4>(e0, e1, lane, nv, colidx, val, X, ldx, acc);
+  store_row_vec<V4>(Y + row * ldy, r, lane, nv, accumulate, acc);
+}
+
+// Task list of the long rows: a row of len > kSpmmSeg entries takes
+// ceil(len / kSpmmSeg) consecutive task slots (segment s of the row in slot
+// base + s) from an atomic counter.  Which base a row gets depends on timing,
+// but the partials of a row are always added in segment order.
+__global__ void spmm_tasks_kernel(int64_t M, const int32_t* __restrict__ rowptr, int* counter, int max_tasks,
+                                  int* __restrict__ task_row, int* __restrict__ task_seg) {
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < M; row += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t len = (int64_t)rowptr[row + 1] - rowptr[row];
+    if (len <= kSpmmSeg) continue;
+    const int nseg = (int)((len + kSpmmSeg - 1) / kSpmmSeg);
+    const int base = atomicAdd(counter, nseg);
+    for (int s = 0; s < nseg && base + s < max_tasks; ++s) {
+      task_row[base + s] = (int)row;
+      task_seg[base + s] = s;
+    }
+  }
+}
+
+// One warp per task: the partial product of one segment of a long row, written
+// to partial[task * ldp ...] (ldp = 4 ceil(r/4)).
+template <int V4>
+__global__ void __launch_bounds__(kSpmmThreads)
+spmm_segment_kernel(int r, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                    const float* __restrict__ val, const float* __restrict__ X, int64_t ldx,
+                    const int* __restrict__ counter, const int* __restrict__ task_row,
+                    const int* __restrict__ task_seg, float* __restrict__ partial, int64_t ldp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t task = (int64_t)blockIdx.x * (kSpmmThreads / 32) + (threadIdx.x >> 5);
+  if (task >= *counter) return;  // the grid covers max_tasks tasks
+  const int row = task_row[task], seg = task_seg[task];
+  const int64_t e0 = (int64_t)rowptr[row] + (int64_t)seg * kSpmmSeg;
+  const int64_t e1 = min((int64_t)rowptr[row + 1], e0 + kSpmmSeg);
+  const int nv = (r + 3) >> 2;
+  float4 acc[V4];
+#pragma unroll
+  for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  row_segment_vec<V4>(e0, e1, lane, nv, colidx, val, X, ldx, acc);
+  float4* p = reinterpret_cast<float4*>(partial + task * ldp);
+#pragma unroll
+  for (int t = 0; t < V4; ++t) {
+    const int q = lane + 32 * t;
+    if (q < nv) p[q] = acc[t];
+  }
+}
+
+// One warp per long row (its segment-0 task): the row's partials added in
+// segment order, then stored like a short row.
+template <int V4>
+__global__ void __launch_bounds__(kSpmmThreads)
+spmm_combine_kernel(int r, const int32_t* __restrict__ rowptr, const int* __restrict__ counter,
+                    const int* __restrict__ task_row, const int* __restrict__ task_seg, int64_t max_tasks,
+                    const float* __restrict__ partial, int64_t ldp, float* __restrict__ Y, int64_t ldy,
+                    int accumulate) {
+  const int lane = threadIdx.x & 31;
+  const int64_t task = (int64_t)blockIdx.x * (kSpmmThreads / 32) + (threadIdx.x >> 5);
+  if (task >= *counter || task_seg[task] != 0) return;
+  const int row = task_row[task];
+  const int64_t len = (int64_t)rowptr[row + 1] - rowptr[row];
+  const int nseg = (int)((len + kSpmmSeg - 1) / kSpmmSeg);
+  if (task + nseg > max_tasks) return;  // only if rowptr holds more than nnz entries
+  const int nv = (r + 3) >> 2;
+  float4 acc[V4];
+#pragma unroll
+  for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int s = 0; s < nseg; ++s) {
+    const float4* p = reinterpret_cast<const float4*>(partial + (task + s) * ldp);
+#pragma unroll
+    for (int t = 0; t < V4; ++t) {
+      const int q = lane + 32 * t;
+      if (q < nv) {
+        const float4 x = p[q];
+        acc[t].x += x.x; acc[t].y += x.y; acc[t].z += x.z; acc[t].w += x.w;
+      }
+    }
+  }
+  store_row_vec<V4>(Y + (int64_t)row * ldy, r, lane, nv, accumulate, acc);
 }
 
 // Scalar variant for panels that are not 16-byte aligned: lane l holds columns
@@ -163,8 +258,19 @@ spmm_csr_scalar_kernel(int64_t M, int r, const int32_t* __restrict__ rowptr, con
 
 }  // namespace
 
+size_t spmm_ws_bytes(int64_t nnz, int r) {
+  const int64_t tasks = spmm_max_tasks(nnz);
+  Sizer s;
+  s.take<int>(4);
+  s.take<int>((size_t)tasks);
+  s.take<int>((size_t)tasks);
+  s.take<float>((size_t)tasks * round_up(r, 4));
+  return s.used + 256;
+}
+
 rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
-                     const float* X, int64_t ldx, float* Y, int64_t ldy, bool accumulate, cudaStream_t stream) {
+                     int64_t nnz, const float* X, int64_t ldx, float* Y, int64_t ldy, bool accumulate, void* ws,
+                     size_t ws_bytes, cudaStream_t stream) {
   if (M <= 0) return RSVD_OK;
   if (r < 1 || r > kSpmmMaxR || ldx < r || ldy < r || !rowptr || !X || !Y)
     return fail(RSVD_ERR_INVALID_ARG, "spmm_csr: bad arguments");
@@ -175,7 +281,40 @@ rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* col
   const dim3 grid((unsigned)blocks);
   if (vec) {
     const int v4 = (int)cdiv(cdiv(r, 4), 32);
-#define RSVD_VEC(V) spmm_csr_vec_kernel<V><<<grid, kSpmmThreads, 0, stream>>>(M, r, rowptr, colidx, val, X, ldx, Y, ldy, acc)
+    // rows of more than kSpmmSeg entries are split into segment tasks when the
+    // workspace allows
+    const int64_t max_tasks = spmm_max_tasks(nnz);
+    const bool split = ws && ws_bytes >= spmm_ws_bytes(nnz, r) && nnz > kSpmmSeg;
+    int *counter = nullptr, *task_row = nullptr, *task_seg = nullptr;
+    float* partial = nullptr;
+    const int64_t ldp = round_up(r, 4);
+    if (split) {
+      Carver c(ws, ws_bytes);
+      counter = c.take<int>(4);
+      task_row = c.take<int>((size_t)max_tasks);
+      task_seg = c.take<int>((size_t)max_tasks);
+      partial = c.take<float>((size_t)max_tasks * ldp);
+      RSVD_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), stream));
+      int tb = (int)cdiv(M, 256);
+      if (tb > 152 * 16) tb = 152 * 16;
+      spmm_tasks_kernel<<<tb, 256, 0, stream>>>(M, rowptr, counter, (int)max_tasks, task_row, task_seg);
+      RSVD_CUDA(after_launch());
+    }
+    const dim3 tgrid((unsigned)cdiv(max_tasks, kSpmmThreads / 32));
+    const int sp = split ? 1 : 0;
+#define RSVD_VEC(V)                                                                                            \
+  do {                                                                                                         \
+    spmm_csr_vec_kernel<V><<<grid, kSpmmThreads, 0, stream>>>(M, r, rowptr, colidx, val, X, ldx, Y, ldy, acc, sp); \
+    RSVD_CUDA(after_launch());                                                                                 \
+    if (split) {                                                                                               \
+      spmm_segment_kernel<V><<<tgrid, kSpmmThreads, 0, stream>>>(r, rowptr, colidx, val, X, ldx, counter,      \
+                                                                 task_row, task_seg, partial, ldp);            \
+      RSVD_CUDA(after_launch());                                                                               \
+      spmm_combine_kernel<V><<<tgrid, kSpmmThreads, 0, stream>>>(r, rowptr, counter, task_row, task_seg,       \
+                                                                 max_tasks, partial, ldp, Y, ldy, acc);        \
+      RSVD_CUDA(after_launch());                                                                               \
+    }                                                                                                          \
+  } while (0)
     switch (v4) {
       case 1: RSVD_VEC(1); break;
       case 2: RSVD_VEC(2); break;
@@ -183,6 +322,7 @@ rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* col
       default: RSVD_VEC(4); break;
     }
 #undef RSVD_VEC
+    return RSVD_OK;
   } else {
     const int vs = (int)cdiv(r, 32);
 #define RSVD_SCA(V) spmm_csr_scalar_kernel<V><<<grid, kSpmmThreads, 0, stream>>>(M, r, rowptr, colidx, val, X, ldx, Y, ldy, acc)

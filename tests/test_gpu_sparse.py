@@ -168,3 +168,37 @@ def test_csr_cap_too_small_for_the_copies(g, zipf):
         plan.run(_torch_csr(m, n, rp, ci, v, "cpu"))
     assert "CAP_TOO_SMALL" in str(e.value)
     plan.close()
+
+
+@pytest.mark.parametrize("split", [True, False])
+def test_csr_long_rows_at_segment_boundaries(g, split):
+    """Rows of 0, 1, 4095, 4096, 4097, 8192, 8193 and 30000 entries: the
+    segment split (4096 entries per warp, partials added in order) against the
+    oracle, with and without the split workspace."""
+    rng = np.random.default_rng(17)
+    n, r = 40000, 130
+    lens = [0, 1, 4095, 4096, 4097, 8192, 8193, 30000, 5, 12000]
+    rows_c, rows_v = [], []
+    for L in lens:
+        c = np.sort(rng.choice(n, size=L, replace=False))
+        rows_c.append(c)
+        rows_v.append(rng.standard_normal(L).astype(np.float32))
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    ci = np.concatenate(rows_c).astype(np.int32)
+    v = np.concatenate(rows_v).astype(np.float32)
+    m = len(lens)
+    X = rng.standard_normal((n, r)).astype(np.float32)
+    Ad = _torch_csr(m, n, rp, ci, v, "cuda")
+    Y = g.apass(Ad, torch.as_tensor(X, device="cuda"), split_long_rows=split).cpu().numpy().astype(np.float64)
+    A = OL.CSR(m, n, rp, ci, v)
+    Yo = OL.csr_apply(A, X.astype(np.float64))
+    bound = _fp32_product_bound(OL.CSR(m, n, rp, ci, np.abs(v)), X)
+    assert np.all(np.abs(Y - Yo) <= bound + 1e-30)
+    assert np.all(Y[0] == 0.0)
+    # the transposed pass over the same long rows (columns of A^T)
+    At = g.csr_transpose(_torch_csr(m, n, rp, ci, v, "cpu")).to("cuda")
+    Yt = rng.standard_normal((n, r)).astype(np.float32)
+    Z = g.apass(At, torch.as_tensor(Yt, device="cuda"), trans=True, At=Ad,
+                split_long_rows=split).cpu().numpy().astype(np.float64)
+    Zo = OL.csr_apply(A, Yt.astype(np.float64))
+    assert np.all(np.abs(Z - Zo) <= _fp32_product_bound(OL.CSR(m, n, rp, ci, np.abs(v)), Yt) + 1e-30)
