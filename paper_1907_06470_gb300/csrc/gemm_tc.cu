@@ -145,7 +145,11 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const uint32_t b_bytes = (uint32_t)NP * 128u;
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- TMA producers ----------------
+    // Lane 0 streams the FP32 tiles of A into their ring as far ahead as it
+    // has free slots; lane 1 loads the panel tiles into the operand slots as
+    // the MMAs free them.  Separate lanes, so that a panel slot still in use
+    // never holds back the prefetch of A.
     if (lane == 0) {
       int64_t it = 0;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
@@ -160,6 +164,15 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           void* dstA = smem + L::a32_off(NP, s32);
           if (TRANS) ptx::tma_load_2d(dstA, &mapA, &full32[s32], (int32_t)(mt * BM), (int32_t)(ks * BK));
           else ptx::tma_load_2d(dstA, &mapA, &full32[s32], (int32_t)(ks * BK), (int32_t)(mt * BM));
+        }
+      }
+    } else if (lane == 1) {
+      int64_t it = 0;
+      for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
+        const int64_t z = u / a.mtiles;
+        const int64_t k0 = z * a.ksteps_per_split;
+        const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
+        for (int64_t ks = k0; ks < k1; ++ks, ++it) {
           const int sop = (int)(it % SOP);
           const uint32_t phop = (uint32_t)((it / SOP) & 1);
           if (!ptx::mbar_wait(&emptyOp[sop], phop ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
