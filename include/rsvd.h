@@ -264,10 +264,14 @@ rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_
 
 /* Section 2.1 steps 3-4: orthonormal basis of the columns of a device panel
  * Y (M x r row-major, F64 or F32, leading dimension ldy) by CholeskyQR2:
- * G = Y^T Y accumulated in FP64, G = R1^T R1 (FP64 Cholesky), Q1 = Y R1^-1,
- * repeated once on Q1.  Writes Q (M x r, same dtype, leading dimension ldq, may
+ * G = Y^T Y, G = R1^T R1 (Cholesky), Q1 = Y R1^-1, repeated once on Q1.  F64:
+ * all in FP64.  F32: FP32 products summed in FP64 over row chunks, FP32
+ * Cholesky and inverse (accurate while cond(Y) is below about 4e3).  Pivots
+ * below 1e-13 (F64) / 1e-5 (F32) of their diagonal entry are deflated: the
+ * column of Q is replaced by a fresh random direction and R gets a zero row.
+ * Writes Q (M x r, same dtype, leading dimension ldq, may
  * not alias Y) and, when R is not NULL, the FP64 upper-triangular r x r factor
- * R = R2 R1 (row-major) with Y = Q R.  r <= 256, M >= r.  Needs `ws_bytes` >=
+ * R = R2 R1 (row-major) with Y = Q R.  r <= 512, M >= r.  Needs `ws_bytes` >=
  * rsvd_orth_workspace(M, r).  Errors: NOT_SPD.  Synchronises `stream`. */
 size_t rsvd_orth_workspace(int64_t M, int32_t r);
 rsvd_status rsvd_orth(int32_t dtype, int64_t M, int32_t r, const void* Y, int64_t ldy,

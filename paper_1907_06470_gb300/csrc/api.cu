@@ -546,7 +546,7 @@ size_t rsvd_orth_workspace(int64_t M, int32_t r) { return orth_ws_bytes(M, r, RS
 
 rsvd_status rsvd_orth(int32_t dtype, int64_t M, int32_t r, const void* Y, int64_t ldy, void* Q,
                       int64_t ldq, double* R, void* ws, size_t ws_bytes, void* stream) {
-  if (r < 1 || r > 256 || M < r || ldy < r || ldq < r || !Y || !Q || (dtype != RSVD_F32 && dtype != RSVD_F64))
+  if (r < 1 || r > 512 || M < r || ldy < r || ldq < r || !Y || !Q || (dtype != RSVD_F32 && dtype != RSVD_F64))
     return fail(RSVD_ERR_INVALID_ARG, "rsvd_orth: bad arguments");
   if (ws_bytes < rsvd_orth_workspace(M, r)) return fail(RSVD_ERR_INVALID_ARG, "rsvd_orth: workspace too small");
   Carver c(ws, ws_bytes);

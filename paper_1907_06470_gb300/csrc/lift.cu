@@ -4,7 +4,8 @@
 // Sign rule (the paper leaves signs free): each pair (u_i, v_i) is negated
 // when the largest-magnitude entry of u_i is negative; among entries of equal
 // magnitude the lowest row index decides.  The column maxima are found per
-// row chunk and combined in chunk order, so the first maximum wins.
+// row chunk and combined with ties going to the lower chunk, so the first
+// maximum wins.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -33,33 +34,56 @@ __global__ void gather_colmajor_kernel(int64_t rows, int64_t cols, const T* __re
   }
 }
 
-constexpr int kSignRows = 512;
+// Rows per chunk: 64, more for tall panels so that at most about 4096 chunk
+// maxima are stored.
+inline int64_t sign_chunk(int64_t m) {
+  const int64_t c = round_up(cdiv(m, 4096), 8);
+  return c > 64 ? c : 64;
+}
 
+// Per chunk of rows and column j: the first entry of largest
+// magnitude (value and magnitude).
 template <typename T>
-__global__ void colmax_kernel(int64_t m, int k, const T* __restrict__ U, int64_t ldu,
+__global__ void colmax_kernel(int64_t m, int k, int64_t chunk, const T* __restrict__ U, int64_t ldu,
                               double* __restrict__ part) {
   const int j = threadIdx.x + blockIdx.y * blockDim.x;
   if (j >= k) return;
-  const int64_t r0 = (int64_t)blockIdx.x * kSignRows;
-  const int64_t r1 = min(m, r0 + kSignRows);
+  const int64_t r0 = (int64_t)blockIdx.x * chunk;
+  const int64_t r1 = min(m, r0 + chunk);
   double best = -1.0, val = 0.0;
-  for (int64_t i = r0; i < r1; ++i) {
-    const double x = (double)U[i * ldu + j];
-    if (fabs(x) > best) { best = fabs(x); val = x; }
+  for (int64_t i0 = r0; i0 < r1; i0 += 8) {
+    double x[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) x[t] = i0 + t < r1 ? (double)U[(i0 + t) * ldu + j] : 0.0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (i0 + t < r1 && fabs(x[t]) > best) { best = fabs(x[t]); val = x[t]; }
   }
   part[((int64_t)blockIdx.x * k + j) * 2 + 0] = best;
   part[((int64_t)blockIdx.x * k + j) * 2 + 1] = val;
 }
 
+// One warp per column: the chunk maxima combined so that the largest
+// magnitude wins and, among equal magnitudes, the lowest chunk (row) does.
 __global__ void choose_flip_kernel(int k, int nchunks, const double* __restrict__ part,
                                    int* __restrict__ flip) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int j = w0; j < k; j += nw) {
     double best = -1.0, val = 0.0;
-    for (int c = 0; c < nchunks; ++c) {
+    int idx = 0x7fffffff;
+    for (int c = lane; c < nchunks; c += 32) {
       const double b = part[((int64_t)c * k + j) * 2];
-      if (b > best) { best = b; val = part[((int64_t)c * k + j) * 2 + 1]; }
+      if (b > best) { best = b; val = part[((int64_t)c * k + j) * 2 + 1]; idx = c; }
     }
-    flip[j] = val < 0.0 ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double b2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const double v2 = __shfl_xor_sync(0xffffffffu, val, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (b2 > best || (b2 == best && i2 < idx)) { best = b2; val = v2; idx = i2; }
+    }
+    if (lane == 0) flip[j] = val < 0.0 ? 1 : 0;
   }
 }
 
@@ -116,7 +140,7 @@ template rsvd_status gather_colmajor_f64<float>(int64_t, int64_t, const float*, 
                                                 cudaStream_t);
 
 size_t sign_scratch_bytes(int64_t m, int k) {
-  return (size_t)cdiv(m, kSignRows) * k * 2 * sizeof(double) + (size_t)k * sizeof(int) + 256;
+  return (size_t)cdiv(m, sign_chunk(m)) * k * 2 * sizeof(double) + (size_t)k * sizeof(int) + 256;
 }
 
 template <typename T>
@@ -125,14 +149,15 @@ rsvd_status normalise_signs(int64_t m, int64_t n, int k, T* U, int64_t ldu, T* V
   if (k <= 0 || m <= 0) return RSVD_OK;
   if (sign_scratch_bytes(m, k) > scratch_bytes)
     return fail(RSVD_ERR_INVALID_ARG, "normalise_signs: scratch too small");
-  const int64_t nchunks = cdiv(m, kSignRows);
+  const int64_t chunk = sign_chunk(m);
+  const int64_t nchunks = cdiv(m, chunk);
   double* part = static_cast<double*>(scratch);
   int* flip = reinterpret_cast<int*>(part + nchunks * k * 2);
   const int tpb = k < 128 ? 32 * (int)cdiv(k, 32) : 128;
-  colmax_kernel<T><<<dim3((unsigned)nchunks, (unsigned)cdiv(k, tpb)), tpb, 0, stream>>>(m, k, U, ldu,
+  colmax_kernel<T><<<dim3((unsigned)nchunks, (unsigned)cdiv(k, tpb)), tpb, 0, stream>>>(m, k, chunk, U, ldu,
                                                                                         part);
   RSVD_CUDA(after_launch());
-  choose_flip_kernel<<<(int)cdiv(k, 128), 128, 0, stream>>>(k, (int)nchunks, part, flip);
+  choose_flip_kernel<<<(int)cdiv((int64_t)k * 32, 256), 256, 0, stream>>>(k, (int)nchunks, part, flip);
   RSVD_CUDA(after_launch());
   int64_t blocks = cdiv((m + n) * k, 256);
   if (blocks > 152 * 4) blocks = 152 * 4;

@@ -1,8 +1,11 @@
 // Section 2.1 steps 3-4: orthonormal basis Q_r of the sketch Y by CholeskyQR2.
 //
 //   G = Y^T Y          chunk partials (simt_gemm) added in FP64
-//   G = L L^T          FP64 Cholesky, one CTA (cholesky_kernel)
-//   Rinv = L^-T        triangular inverse, one warp per column (trilinv_kernel)
+//   G = L L^T          Cholesky (FP64 for FP64 panels, FP32 for FP32 panels), one CTA
+//   Rinv = L^-T        triangular inverse in the panel's type (for r up to
+//                      about 120 both in one shared-memory kernel,
+//                      chol_inv_fused_kernel; else cholesky_kernel +
+//                      trilinv_kernel)
 //   Q1 = Y Rinv        panel product in the panel's precision (simt_gemm)
 // and the same once more on Q1 (Fukaya, Nakatsukasa, Yanagisawa, Yamamoto,
 // "CholeskyQR2", 2014), which restores orthogonality to working precision
@@ -17,7 +20,7 @@
 //
 // Gram accumulation: products are summed in the panel's type over chunks of
 // 256 rows (more for panels over 2^19 rows; the SIMT GEMM, one partial per
-// chunk) and the chunk partials are added in FP64 in chunk order.
+// chunk) and the chunk partials are added in FP64 in a fixed order.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -135,11 +138,207 @@ trilinv_kernel(int r, const T* __restrict__ L, T* __restrict__ Rinv, TOUT* __res
   }
 }
 
+// Cholesky and triangular inverse in one CTA with everything in shared memory
+// (for r small enough; larger r takes cholesky_kernel + trilinv_kernel).
+//
+// Cholesky, blocked right-looking with kCholB columns per panel: warp 0
+// factors the diagonal block column by column (the same pivot test and
+// deflation as cholesky_kernel), then each thread solves one row of the
+// panel below it, then the trailing lower triangle takes the panel's rank-kB
+// update -- three barriers per panel instead of two per column.  The factor
+// L (TF) goes to global memory.
+//
+// Inverse X = L^-1 in TI (the panel type), blocked by block diagonals: the
+// diagonal blocks are inverted by one warp each; then for d = 1, 2, ... every
+// block X_ij with i - j = d is X_ij = -X_ii (sum_{j<=t<i} L_it X_tj), whose
+// right-hand side only needs blocks of smaller d.  Rinv_t = X^T (upper).
+constexpr int kCholB = 16;
+constexpr int kFusedThreads = 512;
+constexpr size_t kFusedSmemMax = 220 * 1024;
+
+template <typename TF, typename TI>
+__host__ __device__ inline size_t fused_smem_bytes(int r) {
+  const size_t lda = (size_t)r + 1;
+  const int nb = (r + kCholB - 1) / kCholB;
+  return (size_t)r * lda * sizeof(TF) + 2 * (size_t)r * sizeof(TF) + (size_t)r * lda * sizeof(TI) +
+         (size_t)nb * kCholB * kCholB * sizeof(TI) + 64;
+}
+
+template <typename TF, typename TI>
+__global__ void __launch_bounds__(kFusedThreads)
+chol_inv_fused_kernel(int r, const double* __restrict__ G, TF* __restrict__ Lout, int* __restrict__ dead,
+                      double tau, int* status, TI* __restrict__ Rinv_t) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  constexpr int NB = kCholB;
+  const int lda = r + 1;
+  const int nb = (r + NB - 1) / NB;
+  TF* A = reinterpret_cast<TF*>(fsm);            // r x lda, lower triangle used
+  TF* gdiag = A + (size_t)r * lda;               // tau * G_kk
+  TF* invs = gdiag + r;                          // 1 / L_kk (0 for a dead pivot)
+  TI* X = reinterpret_cast<TI*>(invs + r);       // r x lda: L^-1
+  TI* S = X + (size_t)r * lda;                   // nb blocks of NB^2 scratch
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+
+  for (int i = warp; i < r; i += nwarps)
+    for (int j = lane; j < r; j += 32) A[i * lda + j] = (TF)G[(int64_t)i * r + j];
+  for (int k = tid; k < r; k += nt) gdiag[k] = (TF)(tau * G[(int64_t)k * r + k]);
+  __syncthreads();
+
+  for (int p = 0; p < r; p += NB) {
+    const int pe = min(p + NB, r), w = pe - p;
+    if (warp == 0) {
+      // Diagonal block in registers: lane i (< w) holds row p+i.  Every lane
+      // forms each pivot from the broadcast diagonal entry, so no lane waits
+      // on another beyond the shuffles.
+      TF row[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t) row[t] = (lane < w && t < w) ? A[(p + lane) * lda + p + t] : TF(0);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        if (k < w) {
+          const TF d = __shfl_sync(0xffffffffu, row[k], k);
+          const TF floor_k = gdiag[p + k];
+          int is_dead = 0;
+          if (!isfinite(d) || !isfinite(floor_k)) is_dead = 2;
+          else if (!(d > floor_k) || !(d > TF(0))) is_dead = 1;
+          const TF piv = is_dead ? TF(0) : sqrt(d);
+          const TF inv = is_dead ? TF(0) : TF(1) / piv;
+          if (lane == 0) {
+            dead[p + k] = is_dead ? 1 : 0;
+            if (is_dead == 2) dev_set_status(status, DEV_NOT_SPD);
+            invs[p + k] = inv;
+          }
+          if (lane == k) row[k] = is_dead ? TF(1) : piv;
+          if (lane > k) row[k] *= inv;                 // L_{lane,k}
+#pragma unroll
+          for (int j = k + 1; j < NB; ++j) {
+            const TF ljk = __shfl_sync(0xffffffffu, row[k], j);  // L_{j,k}
+            if (lane >= j) row[j] -= row[k] * ljk;
+          }
+        }
+      }
+      if (lane < w)
+#pragma unroll
+        for (int t = 0; t < NB; ++t)
+          if (t <= lane) A[(p + lane) * lda + p + t] = row[t];
+    }
+    __syncthreads();
+    // Panel rows below the block: x L_D^T = a, one thread per row, x in registers.
+    for (int i = pe + tid; i < r; i += nt) {
+      TF x[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t) x[t] = t < w ? A[i * lda + p + t] : TF(0);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        if (k < w) {
+          TF v = x[k];
+#pragma unroll
+          for (int t = 0; t < k; ++t) v -= x[t] * A[(p + k) * lda + p + t];
+          x[k] = v * invs[p + k];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NB; ++t)
+        if (t < w) A[i * lda + p + t] = x[t];
+    }
+    __syncthreads();
+    // Trailing lower triangle: lane owns column j, the warp's rows i >= j in
+    // pairs (two independent FMA chains).
+    for (int j = pe + lane; j < r; j += 32) {
+      TF lj[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t) lj[t] = t < w ? A[j * lda + p + t] : TF(0);
+      int i = pe + warp;
+      if (i < j) i += ((j - i + nwarps - 1) / nwarps) * nwarps;  // first of the warp's rows >= j
+      for (; i + nwarps < r; i += 2 * nwarps) {
+        const int i2 = i + nwarps;
+        TF s1 = A[i * lda + j], s2 = A[i2 * lda + j];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          s1 -= A[i * lda + p + t] * lj[t];
+          s2 -= A[i2 * lda + p + t] * lj[t];
+        }
+        A[i * lda + j] = s1;
+        A[i2 * lda + j] = s2;
+      }
+      if (i < r) {
+        TF s1 = A[i * lda + j];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) s1 -= A[i * lda + p + t] * lj[t];
+        A[i * lda + j] = s1;
+      }
+    }
+    __syncthreads();
+  }
+  // L to global (zero above the diagonal)
+  for (int i = warp; i < r; i += nwarps)
+    for (int j = lane; j < r; j += 32) Lout[(int64_t)i * r + j] = j <= i ? A[i * lda + j] : TF(0);
+  // diagonal blocks: X_bb = L_bb^-1, lane c of warp b solves column c of block b
+  for (int b = warp; b < nb; b += nwarps) {
+    const int o = b * NB, w = min(NB, r - o);
+    if (lane < w) {
+      TI col[NB];
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        if (i < w) {
+          TI x = i == lane ? TI(1) : TI(0);
+#pragma unroll
+          for (int t = 0; t < NB; ++t)
+            if (t >= lane && t < i) x -= (TI)A[(o + i) * lda + o + t] * col[t];
+          col[i] = i < lane ? TI(0) : x / (TI)A[(o + i) * lda + o + i];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i < w) X[(o + i) * lda + o + lane] = col[i];
+    }
+  }
+  __syncthreads();
+  // off-diagonal blocks by block diagonal d: S_ij = sum_{j<=t<i} L_it X_tj, then X_ij = -X_ii S_ij.
+  // L is read from A (unchanged since the factorisation); X_tj for t in blocks j .. i-1 lies on
+  // block diagonals below d, finished in earlier steps.
+  for (int d = 1; d < nb; ++d) {
+    const int nblk = nb - d;
+    for (int e = tid; e < nblk * NB * NB; e += nt) {
+      const int q = e / (NB * NB), rem = e % (NB * NB);
+      const int bi = q + d, bj = q;
+      const int pi = rem / NB, pj = rem % NB;
+      const int i = bi * NB + pi, j = bj * NB + pj;
+      TI s0 = TI(0), s1 = TI(0), s2 = TI(0), s3 = TI(0);
+      if (i < r && j < r) {
+        for (int t = bj * NB; t < bi * NB; t += 4) {  // d * NB terms, a multiple of 4
+          s0 += (TI)A[i * lda + t] * X[t * lda + j];
+          s1 += (TI)A[i * lda + t + 1] * X[(t + 1) * lda + j];
+          s2 += (TI)A[i * lda + t + 2] * X[(t + 2) * lda + j];
+          s3 += (TI)A[i * lda + t + 3] * X[(t + 3) * lda + j];
+        }
+      }
+      S[q * NB * NB + rem] = (s0 + s1) + (s2 + s3);
+    }
+    __syncthreads();
+    for (int e = tid; e < nblk * NB * NB; e += nt) {
+      const int q = e / (NB * NB), rem = e % (NB * NB);
+      const int bi = q + d, bj = q;
+      const int pi = rem / NB, pj = rem % NB;
+      const int i = bi * NB + pi, j = bj * NB + pj;
+      if (i < r && j < r) {
+        TI x = TI(0);
+        for (int s2 = 0; s2 <= pi; ++s2) x -= X[i * lda + bi * NB + s2] * S[q * NB * NB + s2 * NB + pj];
+        X[i * lda + j] = x;
+      }
+    }
+    __syncthreads();
+  }
+  for (int j = warp; j < r; j += nwarps)  // Rinv_t[j][i] = X[i][j]
+    for (int i = lane; i < r; i += 32) Rinv_t[(int64_t)j * r + i] = i >= j ? X[i * lda + j] : TI(0);
+}
+
 // R = R2 R1 with R1 = L1^T, R2 = L2^T (both upper triangular).  A dead pivot l
 // of the first sweep carries no part of Y (its column was a negligible
 // residual), so row l of R1 counts as zero.
-template <typename T2>
-__global__ void rprod_kernel(int r, const double* __restrict__ L1, const int* __restrict__ dead1,
+template <typename T1, typename T2>
+__global__ void rprod_kernel(int r, const T1* __restrict__ L1, const int* __restrict__ dead1,
                              const T2* __restrict__ L2, double* __restrict__ R) {
   const int64_t total = (int64_t)r * r;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -147,7 +346,7 @@ __global__ void rprod_kernel(int r, const double* __restrict__ L1, const int* __
     const int i = (int)(e / r), j = (int)(e % r);
     double s = 0.0;
     for (int l = i; l <= j; ++l)
-      if (!dead1[l]) s += (double)L2[(int64_t)l * r + i] * L1[(int64_t)j * r + l];
+      if (!dead1[l]) s += (double)L2[(int64_t)l * r + i] * (double)L1[(int64_t)j * r + l];
     R[e] = j >= i ? s : 0.0;
   }
 }
@@ -155,7 +354,7 @@ __global__ void rprod_kernel(int r, const double* __restrict__ L1, const int* __
 // Rows per partial Gram: each partial is a sum of gram_chunk(M) products in
 // the panel's type -- 256 rows, or more for panels over 2^19 rows so that at
 // most about kGramMaxChunks partials are stored -- and the partials are added
-// in FP64 in chunk order.
+// in FP64 in a fixed order (gram_sum_partials_kernel).
 constexpr int64_t kGramChunk = 256;
 constexpr int64_t kGramMaxChunks = 2048;
 
@@ -166,16 +365,26 @@ int64_t gram_chunk(int64_t M) {
 
 int64_t gram_chunks(int64_t M) { return cdiv(M, gram_chunk(M)); }
 
+// One warp per upper-triangle entry (a, b): lane l adds chunks l, l+32, ... in
+// order, then the 32 lane sums are combined by a fixed shuffle tree, so the
+// result does not depend on scheduling.
 template <typename T>
 __global__ void gram_sum_partials_kernel(int r, int64_t nchunks, const T* __restrict__ P, double* __restrict__ G) {
   const int64_t rr = (int64_t)r * r;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rr; e += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = w0; e < rr; e += nw) {
     const int a = (int)(e / r), b = (int)(e % r);
     if (b < a) continue;
     double s = 0.0;
-    for (int64_t c = 0; c < nchunks; ++c) s += (double)P[c * rr + e];
-    G[(int64_t)a * r + b] = s;
-    G[(int64_t)b * r + a] = s;
+    for (int64_t c = lane; c < nchunks; c += 32) s += (double)P[c * rr + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      G[(int64_t)a * r + b] = s;
+      G[(int64_t)b * r + a] = s;
+    }
   }
 }
 
@@ -186,7 +395,8 @@ rsvd_status gram(int64_t M, int r, const T* Y, int64_t ldy, const OrthWs& ws, cu
   const int64_t nchunks = gram_chunks(M);
   T* P = static_cast<T*>(ws.gram_partial);
   RSVD_TRY(simt_gemm_partials<T>(r, r, M, Y, ldy, true, Y, ldy, (int)nchunks, gram_chunk(M), P, stream));
-  const int64_t blocks = cdiv((int64_t)r * r, 256);
+  int64_t blocks = cdiv((int64_t)r * r * 32, 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
   gram_sum_partials_kernel<T><<<(int)blocks, 256, 0, stream>>>(r, nchunks, P, ws.G);
   RSVD_CUDA(after_launch());
   return RSVD_OK;
@@ -201,8 +411,19 @@ double pivot_tau<double>() { return 1e-13; }
 template <>
 double pivot_tau<float>() { return 1e-5; }
 
-// The second sweep factors Q1^T Q1, close to the identity: FP32 panels do it in
-// FP32 (pivots far from the deflation floor), FP64 panels in FP64.
+// Arithmetic of the two factorisations.  FP64 panels: FP64 for both.  FP32
+// panels: FP32 for both.  The Gram of an FP32 panel carries FP32 accuracy
+// (FP32 products summed in chunks), and CholeskyQR in working precision u
+// leaves Q1 orthogonal to about u cond(Y)^2, which the second sweep restores to
+// u whenever cond(Y) is below about u^-1/2 (about 4e3 in FP32) -- the range
+// finder's panels Y = A Z with orthonormal Z have cond(Y) near
+// sigma_1 / sigma_r of A.  Pivots below tau = 1e-5 of their diagonal (the
+// deflation floor of FP32 panels) are deflated either way.  The second sweep
+// factors Q1^T Q1, close to the identity.
+template <typename T>
+struct FirstSweep { using type = double; };
+template <>
+struct FirstSweep<float> { using type = float; };
 template <typename T>
 struct SecondSweep { using type = double; };
 template <>
@@ -213,6 +434,19 @@ struct SecondSweep<float> { using type = float; };
 // panel); T is the panel type that receives Rinv.
 template <typename TF, typename T>
 rsvd_status chol_inv(int r, const OrthWs& ws, TF* L, int* dead, double tau, cudaStream_t stream) {
+  const size_t fused = fused_smem_bytes<TF, T>(r);
+  if (fused <= kFusedSmemMax) {
+    static bool fattr = false;
+    if (!fattr) {
+      RSVD_CUDA(cudaFuncSetAttribute(chol_inv_fused_kernel<TF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kFusedSmemMax));
+      fattr = true;
+    }
+    chol_inv_fused_kernel<TF, T><<<1, kFusedThreads, fused, stream>>>(r, ws.G, L, dead, tau, ws.status,
+                                                                      static_cast<T*>(ws.Rinv_t));
+    RSVD_CUDA(after_launch());
+    return RSVD_OK;
+  }
   static bool attrs = false;
   if (!attrs) {
     RSVD_CUDA(cudaFuncSetAttribute(cholesky_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmemBytes));
@@ -274,7 +508,9 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
   // sweep 1 (dead pivots: the panel is rank deficient to the Gram's accuracy;
   // their columns of Q1 are replaced by unit random directions)
   RSVD_TRY(gram<T>(M, r, Y, ldy, ws, stream));
-  RSVD_TRY((chol_inv<double, T>(r, ws, ws.L1, ws.dead1, pivot_tau<T>(), stream)));
+  using TF1 = typename FirstSweep<T>::type;
+  TF1* L1 = reinterpret_cast<TF1*>(ws.L1);
+  RSVD_TRY((chol_inv<TF1, T>(r, ws, L1, ws.dead1, pivot_tau<T>(), stream)));
   RSVD_TRY(simt_gemm<T>(M, r, r, Y, ldy, false, Rt, r, Q1, ws.ld_tmp, false, 1, r, nullptr, stream));
   RSVD_TRY(fill_dead_columns(M, r, ws.dead1, Q1, ws.ld_tmp, sizeof(T) == 8 ? RSVD_F64 : RSVD_F32,
                              kDeadFillSeed, stream));
@@ -287,7 +523,7 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
   RSVD_CUDA(after_launch());
   RSVD_TRY(simt_gemm<T>(M, r, r, Q1, ws.ld_tmp, false, Rt, r, Q, ldq, false, 1, r, nullptr, stream));
   if (R) {
-    rprod_kernel<TF2><<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r, ws.L1, ws.dead1, L2, R);
+    rprod_kernel<TF1, TF2><<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r, L1, ws.dead1, L2, R);
     RSVD_CUDA(after_launch());
   }
   return RSVD_OK;

@@ -101,7 +101,10 @@ def test_apass_fp32_matches_oracle(g, m, n, r, mb, nb):
 # ---- CholeskyQR2 (Section 2.1 steps 3-4) ---------------------------------------------
 
 @pytest.mark.parametrize("dtype,M,r", [("f64", 2000, 30), ("f64", 257, 256), ("f32", 100000, 120),
-                                       ("f32", 20000, 120), ("f32", 513, 65)])
+                                       ("f32", 20000, 120), ("f32", 513, 65), ("f64", 500, 1),
+                                       ("f64", 3000, 112), ("f64", 3000, 113), ("f32", 5000, 17),
+                                       ("f32", 5000, 128), ("f32", 5000, 129), ("f32", 6000, 350),
+                                       ("f64", 4000, 512)])
 def test_orth_is_orthonormal_and_spans_y(g, dtype, M, r):
     rng = np.random.default_rng(M + r)
     Y = rng.standard_normal((M, r)) * np.logspace(0, -2, r)
