@@ -42,11 +42,14 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // every round.  Rounds are separated by the hardware cluster barrier; the
 // columns live in global memory and are accessed through L2 (.cg).
 constexpr int kMaxPerLane = 8;  // rows <= 256: column values held in registers
+constexpr int kClusterCheckSmem = 200 * 1024;
 
 __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict__ Min,
                                       const double* __restrict__ W0, double* M, double* W, int* rotated,
-                                      int* sweeps_out, int* status, double* sigma, double* Uout, double* Wout) {
+                                      int* sweeps_out, int* status, double* sigma, double* Uout, double* Wout,
+                                      int check) {
   __shared__ double red[32];
+  extern __shared__ double sh[];  // check pass: M staged (rows x r) + column norms (r); end: sigma_c
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, warps = nthr >> 5;
   const int ncta = gridDim.x;
@@ -114,6 +117,7 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
           b = warp_sum_d(b);
           g = warp_sum_d(g);
           if (fabs(g) > tol * sqrt(a * b) && a > zero2 && b > zero2) {
+            if (lane == 0) atomicMax(&rotated[2 * kJacobiMaxSweeps + sweep], __float_as_int((float)(fabs(g) / sqrt(a * b))));
             const double zeta = (b - a) / (2.0 * g);
             const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
             const double c = 1.0 / sqrt(1.0 + t * t);
@@ -157,12 +161,55 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
       cluster_sync_all();
     }
     if (__ldcg(&rotated[sweep]) == 0) { converged = true; break; }
+    // Jacobi converges quadratically near the end: when the largest relative
+    // off-diagonal rotated in this sweep, squared, is below the tolerance, the
+    // next sweep would most likely find nothing -- check instead of sweeping.
+    const float mrel = __int_as_float(__ldcg(&rotated[2 * kJacobiMaxSweeps + sweep]));
+    if (check && (double)mrel * (double)mrel <= tol) {
+      // Check pass instead of one more sweep: every pair's test on the
+      // current columns (a sweep that found no pair to rotate would leave the
+      // columns as they are, so this is the same stopping test), as dot
+      // products from a staged copy of M, spread over all warps of the cluster.
+      double* Ms = sh;
+      double* nrm = sh + mm;
+      for (int64_t e = tid; e < mm; e += nthr) Ms[e] = __ldcg(&M[e]);
+      __syncthreads();
+      for (int c = warp; c < r; c += warps) {
+        double s2 = 0.0;
+        for (int i = lane; i < rows; i += 32) s2 = fma(Ms[(int64_t)c * rows + i], Ms[(int64_t)c * rows + i], s2);
+        s2 = warp_sum_d(s2);
+        if (lane == 0) nrm[c] = s2;
+      }
+      __syncthreads();
+      bool bad = false;
+      for (int p = blockIdx.x * warps + warp; p < r; p += ncta * warps) {
+        const double* xp = Ms + (int64_t)p * rows;
+        const double a = nrm[p];
+        for (int q = p + 1 + lane; q < r; q += 32) {
+          const double* xq = Ms + (int64_t)q * rows;
+          double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
+          int i = 0;
+          for (; i + 4 <= rows; i += 4) {
+            g0 = fma(xp[i], xq[i], g0);
+            g1 = fma(xp[i + 1], xq[i + 1], g1);
+            g2 = fma(xp[i + 2], xq[i + 2], g2);
+            g3 = fma(xp[i + 3], xq[i + 3], g3);
+          }
+          for (; i < rows; ++i) g0 = fma(xp[i], xq[i], g0);
+          const double g = (g0 + g1) + (g2 + g3);
+          const double b = nrm[q];
+          if (fabs(g) > tol * sqrt(a * b) && a > zero2 && b > zero2) bad = true;
+        }
+      }
+      if (__any_sync(0xffffffffu, bad) && lane == 0) __stcg(&rotated[kJacobiMaxSweeps + sweep], 1);
+      cluster_sync_all();
+      if (__ldcg(&rotated[kJacobiMaxSweeps + sweep]) == 0) { converged = true; break; }
+    }
   }
   if (blockIdx.x != 0) return;
   if (!converged) dev_set_status(status, DEV_NO_CONVERGE);
   if (tid == 0) *sweeps_out = sweep + (converged ? 1 : 0);
-  // column norms, stable descending order, normalised outputs
-  extern __shared__ double sh[];  // sigma_c for c < r
+  // column norms, stable descending order, normalised outputs (sh: sigma_c for c < r)
   for (int c = tid; c < r; c += nthr) {
     double s2 = 0.0;
     for (int i = 0; i < rows; ++i) { const double x = __ldcg(&M[(int64_t)c * rows + i]); s2 += x * x; }
@@ -204,6 +251,7 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
   float* W = smf + r * r;
   __shared__ float redf[32];
   __shared__ int s_rot;
+  __shared__ int s_maxrel;  // bits of the largest relative off-diagonal rotated in the sweep
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, warps = nt >> 5;
   const int hw = tid >> 4, hl = tid & 15, nhw = nt >> 4;  // half-warp index, lane in it
   const int rp = r + (r & 1), npairs = rp / 2;
@@ -225,7 +273,7 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
   int sweep = 0;
   for (; sweep < kJacobiMaxSweeps; ++sweep) {
     __syncthreads();
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) { s_rot = 0; s_maxrel = 0; }
     __syncthreads();
     for (int round = 0; round < rp - 1; ++round) {
       // every half-warp takes the same number of iterations (shuffles need the full warp)
@@ -251,6 +299,7 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
         }
         a = half_warp_sum(a); b = half_warp_sum(b); g = half_warp_sum(g);
         if (active && fabsf(g) > tol * sqrtf(a * b) && a > zero2 && b > zero2) {
+          if (hl == 0) atomicMax(&s_maxrel, __float_as_int(fabsf(g) / sqrtf(a * b)));
           const float zeta = (b - a) / (2.f * g);
           const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
           const float c = 1.f / sqrtf(1.f + t * t);
@@ -271,10 +320,46 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
       }
       __syncthreads();
     }
-    if (!s_rot) break;
+    const int rot = s_rot;
+    const float mrel = __int_as_float(s_maxrel);
+    __syncthreads();  // every thread has read s_rot before it is reset below
+    if (!rot) { ++sweep; break; }
+    if (mrel * mrel > tol) continue;  // far from convergence: sweep again without checking
+    // check pass: the same stopping test on every pair, from the current
+    // columns, without rotating (replaces the final sweep that finds nothing)
+    float* nrm = W + r * r;
+    for (int c = warp; c < r; c += warps) {
+      float s2 = 0.f;
+      for (int i = lane; i < r; i += 32) s2 = fmaf(M[c * r + i], M[c * r + i], s2);
+      s2 = warp_sum(s2);
+      if (lane == 0) nrm[c] = s2;
+    }
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    bool bad = false;
+    for (int p = warp; p < r; p += warps) {
+      const float a = nrm[p];
+      for (int q = p + 1 + lane; q < r; q += 32) {
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+        int i = 0;
+        for (; i + 4 <= r; i += 4) {
+          g0 = fmaf(M[p * r + i], M[q * r + i], g0);
+          g1 = fmaf(M[p * r + i + 1], M[q * r + i + 1], g1);
+          g2 = fmaf(M[p * r + i + 2], M[q * r + i + 2], g2);
+          g3 = fmaf(M[p * r + i + 3], M[q * r + i + 3], g3);
+        }
+        for (; i < r; ++i) g0 = fmaf(M[p * r + i], M[q * r + i], g0);
+        const float g = (g0 + g1) + (g2 + g3);
+        const float b = nrm[q];
+        if (fabsf(g) > tol * sqrtf(a * b) && a > zero2 && b > zero2) bad = true;
+      }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) s_rot = 1;
+    __syncthreads();
+    if (!s_rot) { ++sweep; break; }
   }
   for (int e = tid; e < r * r; e += nt) W32[e] = W[e];
-  if (tid == 0) *sweeps_out = sweep + 1;
+  if (tid == 0) *sweeps_out = sweep;
 }
 
 __global__ void ns_shift_kernel(int r, const double* __restrict__ P, double* __restrict__ T) {
@@ -294,7 +379,7 @@ size_t jacobi_ws_bytes(int64_t rows, int r, bool precondition) {
   s.take<double>((size_t)rows * r);
   s.take<double>((size_t)r * r);
   s.take<unsigned>(2);
-  s.take<int>(kJacobiMaxSweeps);
+  s.take<int>(3 * kJacobiMaxSweeps);
   s.take<int>(1);
   s.take<int>(1);
   if (precondition) {
@@ -310,7 +395,7 @@ JacobiWs jacobi_ws_carve(Carver& c, int64_t rows, int r, bool precondition) {
   w.M = c.take<double>((size_t)rows * r);
   w.W = c.take<double>((size_t)r * r);
   w.barrier = c.take<unsigned>(2);
-  w.rotated = c.take<int>(kJacobiMaxSweeps);
+  w.rotated = c.take<int>(3 * kJacobiMaxSweeps);
   w.sweeps = c.take<int>(1);
   w.status = c.take<int>(1);
   if (precondition) {
@@ -337,7 +422,7 @@ rsvd_status small_gemm64(int r, const double* A, bool transA, const double* B, d
 
 rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const double* W0, double* sigma, double* U,
                                   double* W, const JacobiWs& ws, cudaStream_t stream) {
-  RSVD_CUDA(cudaMemsetAsync(ws.rotated, 0, kJacobiMaxSweeps * sizeof(int), stream));
+  RSVD_CUDA(cudaMemsetAsync(ws.rotated, 0, 3 * kJacobiMaxSweeps * sizeof(int), stream));
   const int rp = r + (r & 1);
   const int npairs = rp / 2;
   // FP64 work per round is spread over up to 16 SMs (a non-portable cluster
@@ -345,10 +430,15 @@ rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const doub
   int ncta = (int)cdiv(npairs, 4);
   if (ncta > 16) ncta = 16;
   if (ncta < 1) ncta = 1;
-  const size_t smem = (size_t)r * sizeof(double);
+  // the check pass stages M in shared memory when it fits
+  const size_t check_bytes = ((size_t)rows * r + r) * sizeof(double);
+  const int check = check_bytes <= (size_t)kClusterCheckSmem ? 1 : 0;
+  const size_t smem = check ? check_bytes : (size_t)r * sizeof(double);
   static bool attr_set = false;
   if (!attr_set) {
     RSVD_CUDA(cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    RSVD_CUDA(cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kClusterCheckSmem));
     attr_set = true;
   }
   for (;;) {
@@ -373,7 +463,7 @@ rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const doub
       continue;
     }
     RSVD_CUDA(cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, rows, r, Min, W0, ws.M, ws.W, ws.rotated, ws.sweeps,
-                                 ws.status, sigma, U, W));
+                                 ws.status, sigma, U, W, check));
     RSVD_CUDA(after_launch());
     return RSVD_OK;
   }
@@ -389,10 +479,10 @@ rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double*
   static bool attr = false;
   if (!attr) {
     RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   2 * kF32MaxR * kF32MaxR * (int)sizeof(float)));
+                                   (2 * kF32MaxR * kF32MaxR + kF32MaxR) * (int)sizeof(float)));
     attr = true;
   }
-  jacobi_f32_kernel<<<1, 1024, 2 * (size_t)r * r * sizeof(float), stream>>>(r, Mc, ws.W32, ws.sweeps);
+  jacobi_f32_kernel<<<1, 1024, (2 * (size_t)r * r + r) * sizeof(float), stream>>>(r, Mc, ws.W32, ws.sweeps);
   RSVD_CUDA(after_launch());
   // Phase 2: Newton-Schulz steps make W orthogonal to FP64 accuracy:
   // W' = (1.5 I - 0.5 W W^T) W, i.e. on the column-major storage (= W^T row-major)

@@ -65,7 +65,7 @@ struct JacobiWs {
   double* M = nullptr;        // rows x r working columns (column-major)
   double* W = nullptr;        // r x r accumulated rotations (column-major)
   unsigned* barrier = nullptr;  // grid barrier words (count, generation)
-  int* rotated = nullptr;     // one flag per sweep
+  int* rotated = nullptr;     // per sweep: rotation flag, check-pass flag, largest rotated off-diagonal
   int* sweeps = nullptr;      // sweeps used
   int* status = nullptr;
   float* W32 = nullptr;       // FP32-phase rotations (r x r)
