@@ -136,7 +136,7 @@ rsvd_status rsvd_plan_info(rsvd_plan_t plan, rsvd_plan_info_t* out);
 
 /* Run the planned randomized SVD on A (Section 2.1 steps 1-7 with Eq. (3)).
  * A: of the plan's kind and dtype.  Dense: device or pinned host.  CSR
- * (Section 3.6, sparse x dense products): device or host arrays; the products
+ * (Section 3.3, sparse x dense products): device or host arrays; the products
  * A X run on the CSR of A and the products A^T X on the CSR of A^T, which is
  * built on the host (rsvd_csr_transpose, once per call) when A.t_rowptr is
  * NULL.  A host CSR (and a built transpose) is copied into device memory owned
@@ -287,7 +287,7 @@ size_t rsvd_small_svd_workspace(int32_t r);
 rsvd_status rsvd_small_svd(int32_t r, const double* Mc, double* sigma, double* U, double* W,
                            void* ws, size_t ws_bytes, void* stream);
 
-/* Section 3.6 (sparse x dense product): Y = A X (trans = 0, CSR of A) or
+/* Section 3.3 (sparse x dense product): Y = A X (trans = 0, CSR of A) or
  * Y = A^T X (trans = 1, using A.t_rowptr/t_colidx/t_val, which must be set)
  * for a CSR device matrix with FP32 values, FP32 panels, FP32 accumulation in
  * entry order (deterministic).  X: K x r row-major (ldx), Y: M x r row-major

@@ -13,7 +13,7 @@ full_svd(A)                   exact SVD of a small matrix
 gaussian / tile_map / apass / orth / small_svd
                               the individual steps (Section 2.1 steps 1-6,
                               Section 3.1 tile map)
-csr_transpose                 host CSR of A^T for the sparse A-passes (Section 3.6)
+csr_transpose                 host CSR of A^T for the sparse A-passes (Section 3.3)
 """
 
 from __future__ import annotations

@@ -317,7 +317,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     Span sp(pf, trans ? RSVD_STAGE_APASS_TRANS : RSVD_STAGE_APASS_FWD, st);
     ++pf.apass_calls;
     if constexpr (std::is_same<T, float>::value) {
-      if (A.kind == RSVD_CSR)  // Section 3.6: sparse x dense; A^T through the CSR of A^T
+      if (A.kind == RSVD_CSR)  // Section 3.3: sparse x dense; A^T through the CSR of A^T
         return trans ? spmm_csr(n, r, A.t_rowptr, A.t_colidx, A.t_val, A.nnz, Xin, ldr, Yout, ldr, false,
                                 P->spmm_ws, P->spmm_ws_bytes, st)
                      : spmm_csr(m, r, A.rowptr, A.colidx, A.val, A.nnz, Xin, ldr, Yout, ldr, false, P->spmm_ws,

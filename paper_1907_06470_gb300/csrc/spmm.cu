@@ -1,4 +1,4 @@
-// A-passes for a sparse A in compressed sparse row form (Section 3.6: the
+// A-passes for a sparse A in compressed sparse row form (Section 3.3: the
 // sparse x dense product; Section 2.1 step 2 and Eq. (3)).
 //
 //   forward     Y = A X      one warp per row of A

@@ -1,4 +1,4 @@
-"""Sparse (CSR) A-passes and the randomized SVD of a CSR matrix (Section 3.6
+"""Sparse (CSR) A-passes and the randomized SVD of a CSR matrix (Section 3.3
 sparse x dense products, Section 2.1 steps 1-7) against the FP64 oracle."""
 
 import numpy as np
