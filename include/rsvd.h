@@ -46,12 +46,19 @@ typedef enum {
  * A and the panel rounded to bfloat16, products on the tensor cores with FP32
  * accumulation; the final pass B^T = A^T Q is recomputed in split-BF16
  * (hi+lo, three products, about FP32 accuracy) when opts.refine != 0.
- * BF16X3: every A-pass in split-BF16. */
+ * BF16X3: every A-pass in split-BF16.  FP8 (an experiment): A is stored once
+ * per run as E4M3 codes with one power-of-two scale per tile (the plan's
+ * tiles rounded up to multiples of 128; one tile when no tiles are set; see
+ * rsvd_fp8_quantize), the A-passes decode the codes to BF16 on the fly and
+ * multiply with the BF16 panel on the tensor cores (FP32 accumulation); the
+ * final B^T = A^T Q is recomputed in split-BF16 from the FP32 A when
+ * opts.refine != 0.  Dense F32 matrices held in device memory during the run. */
 typedef enum {
   RSVD_PREC_FP64 = 0,
   RSVD_PREC_FP32 = 1,
   RSVD_PREC_BF16 = 2,
-  RSVD_PREC_BF16X3 = 3
+  RSVD_PREC_BF16X3 = 3,
+  RSVD_PREC_FP8 = 4
 } rsvd_prec;
 
 typedef enum { RSVD_F64 = 0, RSVD_F32 = 1, RSVD_BF16 = 2 } rsvd_dtype;
@@ -200,7 +207,8 @@ typedef enum {
   RSVD_STAGE_LIFT = 5,        /* U = Q U_B, V = Q_b W, signs */
   RSVD_STAGE_H2D = 6,         /* copy of a host-resident A */
   RSVD_STAGE_TOTAL = 7,       /* whole rsvd_run on the device */
-  RSVD_STAGE_COUNT = 8
+  RSVD_STAGE_QUANTIZE = 8,    /* FP8 codes of A (FP8 precision only) */
+  RSVD_STAGE_COUNT = 9
 } rsvd_stage;
 
 /* Enable (1) or disable (0) stage timing: rsvd_run then records CUDA events
@@ -251,8 +259,9 @@ rsvd_status rsvd_tile_map(int64_t m, int64_t n, int64_t mb, int64_t nb, int32_t 
  * A: dense device matrix (F64 or F32), or a CSR device matrix (below).
  * X: K x r row-major of A's dtype (K = n for trans = 0, m for trans = 1),
  * leading dimension ldx.  Y: M x r row-major of A's dtype, leading dimension
- * ldy.  prec: FP64 (A F64), FP32, BF16 or BF16X3 (A F32; A 16-byte aligned
- * with ld % 4 == 0).  r <= 256 (CSR: 512, see below).  Needs `ws_bytes` >=
+ * ldy.  prec: FP64 (A F64), FP32, BF16, BF16X3 or FP8 (A F32; A 16-byte
+ * aligned with ld % 4 == 0; FP8 quantises A into the workspace with tiles
+ * mb x nb rounded up to multiples of 128, or one tile when mb/nb are 0).  r <= 256 (CSR: 512, see below).  Needs `ws_bytes` >=
  * rsvd_apass_workspace(...).  FP64/FP32 enqueue only; BF16/BF16X3
  * synchronise `stream` and return TIMEOUT if a wait of the tensor-core
  * pipeline expired. */
@@ -308,6 +317,20 @@ size_t rsvd_spmm_workspace(int64_t nnz, int32_t r);
  * column index outside [0, n), NULL array). */
 rsvd_status rsvd_csr_transpose(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                                const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val);
+
+/* FP8 storage of a dense F32 device matrix A (m x n): E4M3 codes (OCP 8-bit
+ * floating point, 2023: bias 7, three mantissa bits, largest finite 448,
+ * rounding to nearest even, saturating) with one scale per tile of rows
+ * [I*qm, ...) x columns [J*qn, ...) (qm, qn multiples of 128, or at least m /
+ * n for a single tile row / column).  The scale of a tile is the smallest
+ * power of two s with amax / s <= 448 (amax: the tile's largest magnitude; s =
+ * 1 for an all-zero tile, NaN for a tile holding NaN or infinity); entry
+ * (i, j) is stored as code(a_ij / s).  Outputs (device, caller-owned): codes
+ * m x ldc bytes (ldc >= n, ldc % 4 == 0, 4-byte aligned base), scales
+ * cdiv(m, qm) x cdiv(n, qn) floats, row-major.  Enqueues only (one
+ * stream-ordered allocation of the tile maxima).  Errors: INVALID_ARG. */
+rsvd_status rsvd_fp8_quantize(const rsvd_matrix* A, int64_t qm, int64_t qn, uint8_t* codes, int64_t ldc,
+                              float* scales, void* stream);
 
 /* ---- Variant without allocation (no counterpart in the paper) --------------- */
 

@@ -14,6 +14,7 @@ gaussian / tile_map / apass / orth / small_svd
                               the individual steps (Section 2.1 steps 1-6,
                               Section 3.1 tile map)
 csr_transpose                 host CSR of A^T for the sparse A-passes (Section 3.3)
+fp8_quantize                  E4M3 codes of A with per-tile scales (the FP8 variant)
 """
 
 from __future__ import annotations
@@ -24,7 +25,7 @@ from . import _lib
 from ._lib import RsvdError, load  # noqa: F401
 
 __all__ = ["rsvd", "Plan", "full_svd", "gaussian", "tile_map", "apass", "orth", "small_svd",
-           "small_svd_noalloc", "csr_transpose", "RsvdError", "load"]
+           "small_svd_noalloc", "csr_transpose", "fp8_quantize", "RsvdError", "load"]
 
 
 def _torch():
@@ -337,6 +338,22 @@ def csr_transpose(A):
                                      C.c_void_p(v.data_ptr()), C.c_void_p(trp.data_ptr()),
                                      C.c_void_p(tci.data_ptr()), C.c_void_p(tv.data_ptr())))
     return torch.sparse_csr_tensor(trp, tci, tv, size=(n, m))
+
+
+def fp8_quantize(A, qm=0, qn=0):
+    """E4M3 codes (uint8, m x n) and per-tile power-of-two scales of a dense
+    float32 CUDA matrix (rsvd_fp8_quantize); qm / qn = 0 means one tile."""
+    torch = _torch()
+    m, n = A.shape
+    qm = qm or m
+    qn = qn or n
+    ldc = (n + 15) // 16 * 16
+    codes = torch.empty(m, ldc, dtype=torch.uint8, device=A.device)
+    scales = torch.empty(-(-m // min(qm, m)), -(-n // min(qn, n)), dtype=torch.float32, device=A.device)
+    d = _dense_desc(A)
+    _check(load().rsvd_fp8_quantize(C.byref(d), qm, qn, C.c_void_p(codes.data_ptr()), ldc,
+                                    C.c_void_p(scales.data_ptr()), _stream_ptr()))
+    return codes[:, :n], scales
 
 
 def orth(Y, want_R=False):

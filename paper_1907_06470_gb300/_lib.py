@@ -11,13 +11,13 @@ from . import build as _build
 c_i32, c_i64, c_u64, c_size, c_vp = C.c_int32, C.c_int64, C.c_uint64, C.c_size_t, C.c_void_p
 
 RSVD_OK = 0
-STAGES = ["gaussian", "apass_fwd", "apass_trans", "orth", "small_svd", "lift", "h2d", "total"]
+STAGES = ["gaussian", "apass_fwd", "apass_trans", "orth", "small_svd", "lift", "h2d", "total", "quantize"]
 STATUS_NAMES = {
     0: "RSVD_OK", 1: "RSVD_ERR_INVALID_ARG", 2: "RSVD_ERR_OOM", 3: "RSVD_ERR_CAP_TOO_SMALL",
     4: "RSVD_ERR_CUDA", 5: "RSVD_ERR_NOT_SPD", 6: "RSVD_ERR_NO_CONVERGE", 7: "RSVD_ERR_TIMEOUT",
     8: "RSVD_ERR_UNSUPPORTED",
 }
-PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3, "fp8": 4}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2}
 DENSE, CSR = 0, 1
 ON_DEVICE, ON_HOST = 0, 1
@@ -73,6 +73,7 @@ SIGNATURES = {
     "rsvd_small_svd_noalloc": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "rsvd_csr_transpose": (c_i32, [c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "rsvd_spmm_workspace": (c_size, [c_i64, c_i32]),
+    "rsvd_fp8_quantize": (c_i32, [C.POINTER(RsvdMatrix), c_i64, c_i64, c_vp, c_i64, c_vp, c_vp]),
 }
 NOALLOC_MAX_R = 256
 

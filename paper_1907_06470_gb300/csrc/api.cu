@@ -86,8 +86,8 @@ size_t elem_size(int dtype) { return dtype == RSVD_F64 ? 8 : (dtype == RSVD_BF16
 size_t apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t mb, int64_t nb) {
   const PassShape s = pass_shape(m, n, trans, mb, nb);
   const size_t esz = prec == RSVD_PREC_FP64 ? 8 : 4;
-  if (prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3)
-    return tc_apass_ws_bytes(m, n, r, trans, prec, mb, nb);
+  if (prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3 || prec == RSVD_PREC_FP8)
+    return tc_apass_ws_bytes(m, n, r, trans, prec == RSVD_PREC_FP8 ? RSVD_PREC_BF16 : prec, mb, nb);
   return s.nsplit > 1 ? (size_t)s.nsplit * s.M * r * esz + 256 : 256;
 }
 
@@ -209,6 +209,8 @@ struct rsvd_plan_s {
   StreamState* ss = nullptr;       // out-of-core state (created on the first streamed run)
   bool streaming = false;          // the current run streams A from the host
   int kind = RSVD_DENSE;           // rsvd_kind the plan runs on
+  Fp8Source f8;                    // FP8 plans: E4M3 codes of A and tile scales (in the workspace)
+  unsigned* f8_amax = nullptr;
   void* csr_dev = nullptr;         // device copies of a CSR A and/or its transpose, SpMM workspace
   size_t csr_dev_bytes = 0;
   void* spmm_ws = nullptr;         // long-row tasks of the CSR passes (inside csr_dev)
@@ -234,8 +236,10 @@ rsvd_status check_args(int64_t m, int64_t n, int k, int p, int q, const rsvd_opt
   if (o) {
     if (o->dtype != RSVD_F32 && o->dtype != RSVD_F64)
       return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: dtype must be F32 or F64");
-    if (o->prec < RSVD_PREC_FP64 || o->prec > RSVD_PREC_BF16X3)
+    if (o->prec < RSVD_PREC_FP64 || o->prec > RSVD_PREC_FP8)
       return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: unknown precision");
+    if (o->prec == RSVD_PREC_FP8 && (csr || o->dtype != RSVD_F32))
+      return fail(RSVD_ERR_UNSUPPORTED, "rsvd_plan: FP8 precision takes dense F32 matrices");
     if ((o->prec == RSVD_PREC_FP64) != (o->dtype == RSVD_F64))
       return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: FP64 precision goes with FP64 data and only with it");
     if (o->mb < 0 || o->nb < 0 || o->n_slots < 0)
@@ -276,7 +280,7 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   const size_t a0 = dense ? apass_ws_bytes(P->m, P->n, P->r, 0, P->prec, P->mb, P->nb) : 0;
   const size_t a1 = dense ? apass_ws_bytes(P->m, P->n, P->r, 1, P->prec, P->mb, P->nb) : 0;
   size_t a2 = 0;
-  if (dense && P->prec == RSVD_PREC_BF16 && P->refine)
+  if (dense && (P->prec == RSVD_PREC_BF16 || P->prec == RSVD_PREC_FP8) && P->refine)
     a2 = apass_ws_bytes(P->m, P->n, P->r, 1, RSVD_PREC_BF16X3, P->mb, P->nb);
   P->apass_ws_bytes = a0 > a1 ? a0 : a1;
   if (a2 > P->apass_ws_bytes) P->apass_ws_bytes = a2;
@@ -293,6 +297,20 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   P->sign_scratch = c.take<char>(P->sign_scratch_bytes);
   P->bwd_ws_bytes = dense ? backward_ws_bytes(P->m, P->n, P->k, P->dtype) : 0;
   P->bwd_ws = c.take<char>(P->bwd_ws_bytes);
+  if (P->prec == RSVD_PREC_FP8) {
+    // quantisation tiles: the plan's tiles rounded up to multiples of 128
+    Fp8Source& f = P->f8;
+    f.m = P->m;
+    f.n = P->n;
+    f.ldc = round_up(P->n, 16);
+    f.qm = P->mb >= P->m ? P->m : round_up(P->mb, 128);
+    f.qn = P->nb >= P->n ? P->n : round_up(P->nb, 128);
+    if (f.qm > P->m) f.qm = P->m;
+    if (f.qn > P->n) f.qn = P->n;
+    f.codes = c.take<uint8_t>((size_t)P->m * f.ldc);
+    f.scales = c.take<float>((size_t)cdiv(P->m, f.qm) * cdiv(P->n, f.qn));
+    P->f8_amax = c.take<unsigned>((size_t)cdiv(P->m, f.qm) * cdiv(P->n, f.qn));
+  }
   P->status = c.take<int>(4);
   if (base) {
     P->orth.status = P->status;
@@ -311,7 +329,8 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   T* Bt = static_cast<T*>(P->Bt);
   T* Qb = static_cast<T*>(P->Qb);
   const int prec = P->prec;
-  const int final_prec = (prec == RSVD_PREC_BF16 && P->refine) ? RSVD_PREC_BF16X3 : prec;
+  const int final_prec =
+      ((prec == RSVD_PREC_BF16 || prec == RSVD_PREC_FP8) && P->refine) ? RSVD_PREC_BF16X3 : prec;
   Profiler& pf = P->prof;
   auto apass = [&](int trans, int pr, const T* Xin, T* Yout) -> rsvd_status {
     Span sp(pf, trans ? RSVD_STAGE_APASS_TRANS : RSVD_STAGE_APASS_FWD, st);
@@ -324,6 +343,10 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
                                 P->spmm_ws_bytes, st);
     }
     if (P->streaming) return apass_streamed(P->ss, A, trans, pr, r, Xin, Yout, ldr, P->status, st);
+    if constexpr (std::is_same<T, float>::value) {
+      if (pr == RSVD_PREC_FP8)
+        return tc_apass_from_fp8(P->f8, trans, r, Xin, ldr, Yout, ldr, P->apass_ws, P->apass_ws_bytes, P->status, st);
+    }
     return apass_dense(A, trans, pr, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes,
                        P->status, st);
   };
@@ -336,8 +359,16 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     RSVD_CUDA(cudaMemsetAsync(P->status, 0, sizeof(int), st));
     {  // step 1: Gaussian test matrix (n x r)
       Span sp(pf, RSVD_STAGE_GAUSSIAN, st);
-      const bool bf16_panel = prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3;
+      const bool bf16_panel = prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3 || prec == RSVD_PREC_FP8;
       RSVD_TRY(launch_gaussian(P->seed, n, r, bf16_panel ? kF32HoldingBf16 : P->dtype, 0, X, ldr, st));
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      if (prec == RSVD_PREC_FP8) {  // E4M3 codes of A with tile scales, once per run
+        Span sp(pf, RSVD_STAGE_QUANTIZE, st);
+        RSVD_TRY(fp8_quantize(static_cast<const float*>(A.data), m, n, A.ld, P->f8.qm, P->f8.qn,
+                              const_cast<uint8_t*>(P->f8.codes), P->f8.ldc, const_cast<float*>(P->f8.scales),
+                              P->f8_amax, st));
+      }
     }
     // step 2 and steps 3-4: Y = A O, Q = orth(Y)
     RSVD_TRY(apass(0, prec, X, Y));
@@ -507,7 +538,37 @@ size_t rsvd_spmm_workspace(int64_t nnz, int32_t r) { return spmm_ws_bytes(nnz < 
 
 size_t rsvd_apass_workspace(int64_t m, int64_t n, int32_t r, int32_t trans, int32_t prec, int64_t mb,
                             int64_t nb) {
+  if (prec == RSVD_PREC_FP8) {
+    const int64_t qm = (mb <= 0 || mb >= m) ? m : round_up(mb, 128);
+    const int64_t qn = (nb <= 0 || nb >= n) ? n : round_up(nb, 128);
+    const int64_t tiles = cdiv(m, qm < m ? qm : m) * cdiv(n, qn < n ? qn : n);
+    Sizer z;
+    z.take<uint8_t>((size_t)m * round_up(n, 16));
+    z.take<float>((size_t)tiles);
+    z.take<unsigned>((size_t)tiles);
+    z.take<int>(4);
+    z.take<char>(tc_apass_ws_bytes(m, n, r, trans, RSVD_PREC_BF16, mb, nb));
+    return z.used + 512;
+  }
   return apass_ws_bytes(m, n, r, trans, prec, mb, nb) + 512;
+}
+
+rsvd_status rsvd_fp8_quantize(const rsvd_matrix* A, int64_t qm, int64_t qn, uint8_t* codes, int64_t ldc,
+                              float* scales, void* stream) {
+  if (!A || !codes || !scales || A->kind != RSVD_DENSE || A->dtype != RSVD_F32 || A->location != RSVD_ON_DEVICE ||
+      A->ld < A->n || A->m < 1 || A->n < 1)
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_fp8_quantize: need a dense F32 device matrix and outputs");
+  if (!fp8_tiles_ok(A->m, A->n, qm, qn))
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_fp8_quantize: tile edges must be multiples of 128 or cover the matrix");
+  const int64_t cqm = qm > A->m ? A->m : qm, cqn = qn > A->n ? A->n : qn;
+  const size_t tiles = (size_t)cdiv(A->m, cqm) * cdiv(A->n, cqn);
+  cudaStream_t st = as_stream(stream);
+  unsigned* amax = nullptr;
+  RSVD_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&amax), tiles * sizeof(unsigned), st));
+  const rsvd_status s = fp8_quantize(static_cast<const float*>(A->data), A->m, A->n, A->ld, cqm, cqn, codes, ldc,
+                                     scales, amax, st);
+  cudaFreeAsync(amax, st);
+  return s;
 }
 
 rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_t r, const void* X,
@@ -528,6 +589,34 @@ rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_
   }
   if (r > 256) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: r must not exceed 256 (dense)");
   if (A->kind == RSVD_DENSE && A->ld < A->n) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: ld < n");
+  if (prec == RSVD_PREC_FP8) {
+    // quantise A (tiles mb x nb, rounded up to multiples of 128) into the
+    // workspace, then the pass on the codes
+    if (A->kind != RSVD_DENSE || A->dtype != RSVD_F32 || A->location != RSVD_ON_DEVICE)
+      return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: FP8 needs a dense F32 device matrix");
+    Fp8Source f;
+    f.m = A->m; f.n = A->n; f.ldc = round_up(A->n, 16);
+    f.qm = (mb <= 0 || mb >= A->m) ? A->m : round_up(mb, 128);
+    f.qn = (nb <= 0 || nb >= A->n) ? A->n : round_up(nb, 128);
+    if (f.qm > A->m) f.qm = A->m;
+    if (f.qn > A->n) f.qn = A->n;
+    const size_t need = rsvd_apass_workspace(A->m, A->n, r, trans, prec, mb, nb);
+    if (!ws || ws_bytes < need) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: workspace too small");
+    Carver c(ws, ws_bytes);
+    f.codes = c.take<uint8_t>((size_t)A->m * f.ldc);
+    f.scales = c.take<float>((size_t)cdiv(A->m, f.qm) * cdiv(A->n, f.qn));
+    unsigned* amax = c.take<unsigned>((size_t)cdiv(A->m, f.qm) * cdiv(A->n, f.qn));
+    int* st_word = c.take<int>(4);
+    const size_t tws = tc_apass_ws_bytes(A->m, A->n, r, trans, RSVD_PREC_BF16, mb, nb);
+    void* tw = c.take<char>(tws);
+    cudaStream_t st = as_stream(stream);
+    RSVD_CUDA(cudaMemsetAsync(st_word, 0, sizeof(int), st));
+    RSVD_TRY(fp8_quantize(static_cast<const float*>(A->data), A->m, A->n, A->ld, f.qm, f.qn,
+                          const_cast<uint8_t*>(f.codes), f.ldc, const_cast<float*>(f.scales), amax, st));
+    RSVD_TRY(tc_apass_from_fp8(f, trans, r, static_cast<const float*>(X), ldx, static_cast<float*>(Y), ldy, tw, tws,
+                               st_word, st));
+    return read_device_status(st_word, st);
+  }
   if (prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3) {
     // The tensor-core pipeline reports an expired wait through a device word:
     // this call synchronises the stream and returns it.
@@ -648,7 +737,10 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
     if (P->mem_cap && P->ws_bytes + bytes > P->mem_cap) {
       if (P->Adev) { cudaFree(P->Adev); P->Adev = nullptr; P->a_copy_bytes = 0; }
       if (P->ws_bytes >= P->mem_cap) return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: no room left for streaming");
-      const int final_prec = (P->prec == RSVD_PREC_BF16 && P->refine) ? RSVD_PREC_BF16X3 : P->prec;
+      if (P->prec == RSVD_PREC_FP8)
+        return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: FP8 precision needs A in device memory (no streaming)");
+      const int final_prec =
+          ((P->prec == RSVD_PREC_BF16 || P->prec == RSVD_PREC_FP8) && P->refine) ? RSVD_PREC_BF16X3 : P->prec;
       RSVD_TRY(stream_prepare(&P->ss, A->m, A->n, elem_size(A->dtype), P->mb_req, P->nb_req, P->n_slots,
                               P->mem_cap - P->ws_bytes, P->r, P->prec, final_prec));
       stream_begin_run(P->ss);

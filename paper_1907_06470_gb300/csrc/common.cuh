@@ -37,7 +37,7 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 template <typename T>
-inline bool aligned16(const T* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+__host__ __device__ inline bool aligned16(const T* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 // ---- device status word ----------------------------------------------------
 // Kernels that can fail write one of these codes (first writer wins through

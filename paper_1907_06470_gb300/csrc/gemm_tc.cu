@@ -20,11 +20,17 @@
 // Split mode (BF16X3): A = A_hi + A_lo and X = X_hi + X_lo, each part BF16,
 // C = A_hi X_hi + A_hi X_lo + A_lo X_hi, about 16 significant bits per operand.
 //
+// FP8 source (SRC8): A is read as E4M3 codes with one power-of-two scale per
+// block-cyclic tile; the converters decode each code to BF16 times its tile's
+// scale (exact) -- a quarter of the HBM bytes of the FP32 source.
+//
 // Every wait is bounded (about one second of global time); a wait that expires
 // records DEV_TIMEOUT, every role stops issuing work, and the CTA frees its
 // TMEM before returning.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <mutex>
@@ -39,6 +45,7 @@ namespace {
 constexpr int BM = 128;            // output rows per tile (MMA M)
 constexpr int BK = 64;             // K per step: one 128-byte BF16 row
 constexpr int A32_BYTES = BM * BK * 4;
+constexpr int A8_BYTES = BM * BK;
 constexpr int A16_BYTES = BM * BK * 2;
 constexpr int SOP = 2;             // operand (BF16) ring depth
 constexpr int kSplitMaxNP = 192;   // widest split-mode panel one pass supports
@@ -61,26 +68,29 @@ struct TcArgs {
   int64_t ldc;
   int64_t c_split_stride;
   int* status;
+  const float* qscale;  // SRC8: per-tile scales, qtn per tile row
+  int64_t qm, qn, qtn;  // SRC8: tile edges (in rows / columns of A)
 };
 
 #ifndef RSVD_TC_MAX_S32
-#define RSVD_TC_MAX_S32 4
+#define RSVD_TC_MAX_S32 8
 #endif
 constexpr int kMaxS32 = RSVD_TC_MAX_S32;  // deepest FP32 staging ring
 
 // Shared-memory plan: BF16 operand slots (A then panel), then the FP32 staging
 // ring of depth S32 (a runtime choice: as deep as the 227 KB allow), then the
 // barriers and the TMEM address word.
-template <bool SPLIT>
+template <bool SPLIT, bool SRC8 = false>
 struct Layout {
   static constexpr int PARTS = SPLIT ? 2 : 1;
+  static constexpr int STAGE_BYTES = SRC8 ? A8_BYTES : A32_BYTES;
   __host__ __device__ static size_t a16_off(int s, int part) { return ((size_t)s * PARTS + part) * A16_BYTES; }
   __host__ __device__ static size_t b16_base() { return (size_t)SOP * PARTS * A16_BYTES; }
   __host__ __device__ static size_t b16_off(int NP, int s, int part) {
     return b16_base() + ((size_t)s * PARTS + part) * (size_t)NP * 128;
   }
   __host__ __device__ static size_t a32_off(int NP, int s) {
-    return b16_base() + (size_t)SOP * PARTS * NP * 128 + (size_t)s * A32_BYTES;
+    return b16_base() + (size_t)SOP * PARTS * NP * 128 + (size_t)s * STAGE_BYTES;
   }
   __host__ __device__ static size_t bar_off(int NP, int S32) { return a32_off(NP, S32); }
   // barriers: full32, empty32 (kMaxS32 each), fullA, fullB, emptyOp (SOP each),
@@ -92,11 +102,19 @@ struct Layout {
 
 __device__ __forceinline__ void flag_timeout(int* status) { dev_set_status(status, DEV_TIMEOUT); }
 
-template <bool TRANS, bool SPLIT>
+// Two E4M3 codes (low byte first) to two floats, each times s.
+__device__ __forceinline__ float2 e4m3x2_scaled(uint16_t codes, float s) {
+  const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)codes, __NV_E4M3);
+  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+  return make_float2(f.x * s, f.y * s);
+}
+
+template <bool TRANS, bool SPLIT, bool SRC8 = false>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const __grid_constant__ CUtensorMap mapBlo, const TcArgs a) {
-  using L = Layout<SPLIT>;
+  static_assert(!(SPLIT && SRC8), "the FP8 source has no split mode");
+  using L = Layout<SPLIT, SRC8>;
   const int S32 = a.s32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -160,7 +178,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           const int s32 = (int)(it % S32);
           const uint32_t ph32 = (uint32_t)((it / S32) & 1);
           if (!ptx::mbar_wait(&empty32[s32], ph32 ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
-          ptx::mbar_arrive_expect_tx(&full32[s32], A32_BYTES);
+          ptx::mbar_arrive_expect_tx(&full32[s32], L::STAGE_BYTES);
           void* dstA = smem + L::a32_off(NP, s32);
           if (TRANS) ptx::tma_load_2d(dstA, &mapA, &full32[s32], (int32_t)(mt * BM), (int32_t)(ks * BK));
           else ptx::tma_load_2d(dstA, &mapA, &full32[s32], (int32_t)(ks * BK), (int32_t)(mt * BM));
@@ -231,7 +249,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     const int cw = warp - 2;
     int64_t it = 0;
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-      const int64_t z = u / a.mtiles;
+      const int64_t z = u / a.mtiles, mt = u % a.mtiles;
       const int64_t k0 = z * a.ksteps_per_split;
       const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
       bool ok = true;
@@ -246,7 +264,39 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         const float* src = reinterpret_cast<const float*>(smem + L::a32_off(NP, s32));
         uint8_t* hi = smem + L::a16_off(sop, 0);
         uint8_t* lo = smem + L::a16_off(sop, SPLIT ? 1 : 0);
-        if (!TRANS) {
+        if (SRC8) {
+          const uint8_t* src8 = smem + L::a32_off(NP, s32);
+          if (!TRANS) {
+            // codes[i][k], 128 rows of 64 bytes; the block lies in one tile
+            const float sc = a.qscale[(mt * BM / a.qm) * a.qtn + (ks * BK / a.qn)];
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+              const int i = cw * 32 + rr;
+              const uint16_t c2 = reinterpret_cast<const uint16_t*>(src8 + i * BK)[lane];
+              const __nv_bfloat162 h = __float22bfloat162_rn(e4m3x2_scaled(c2, sc));
+              const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)lane >> 2) ^ ((uint32_t)i & 7u)) << 4) +
+                                   (((uint32_t)lane & 3u) << 2);
+              *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
+            }
+          } else {
+            // codes[k][i], 64 rows of 128 bytes: lane owns output row i
+            const float sc = a.qscale[(ks * BK / a.qm) * a.qtn + (mt * BM / a.qn)];
+            const int i = cw * 32 + lane;
+#pragma unroll 2
+            for (int c = 0; c < BK / 8; ++c) {
+              uint32_t hw[4];
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const uint16_t c2 = (uint16_t)src8[(c * 8 + 2 * t) * BM + i] |
+                                    (uint16_t)((uint16_t)src8[(c * 8 + 2 * t + 1) * BM + i] << 8);
+                const __nv_bfloat162 h = __float22bfloat162_rn(e4m3x2_scaled(c2, sc));
+                hw[t] = *reinterpret_cast<const uint32_t*>(&h);
+              }
+              const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)c) ^ ((uint32_t)i & 7u)) << 4);
+              *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            }
+          }
+        } else if (!TRANS) {
           // src[i][k], 128 rows of 64 floats: lane converts k = 2*lane, 2*lane+1 of row i
 #pragma unroll 4
           for (int rr = 0; rr < 32; ++rr) {
@@ -457,22 +507,34 @@ size_t tc_apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64
   return z.used + 256;
 }
 
-rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X, int64_t ldx,
-                              float* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws, size_t ws_bytes,
-                              int* status, cudaStream_t stream, bool accumulate) {
+namespace {
+
+// The FP32 source (A) or the FP8 source (E4M3 codes of A with tile scales).
+struct TcSource {
+  const rsvd_matrix* A = nullptr;   // FP32 source
+  const Fp8Source* f8 = nullptr;    // FP8 source
+};
+
+rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, int prec, int r, const float* X,
+                         int64_t ldx, float* Y, int64_t ldy, void* ws, size_t ws_bytes, int* status,
+                         cudaStream_t stream, bool accumulate) {
   const bool split = prec == RSVD_PREC_BF16X3;
+  const bool src8 = src.f8 != nullptr;
   if (r < 1 || r > 256) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: r must be in [1, 256]");
+  if (split && src8) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: no split mode for the FP8 source");
   if (split && round_up(r, 16) > kSplitMaxNP) {
     // the split-mode operand ring does not fit shared memory for this width:
     // two passes over column halves of the panel (A is read twice)
     const int h = (int)round_up(cdiv(r, 2), 16);
-    RSVD_TRY(tc_apass_from_f32(A, trans, prec, h, X, ldx, Y, ldy, mb, nb, ws, ws_bytes, status, stream, accumulate));
-    return tc_apass_from_f32(A, trans, prec, r - h, X + h, ldx, Y + h, ldy, mb, nb, ws, ws_bytes, status, stream,
-                             accumulate);
+    RSVD_TRY(tc_apass_run(src, m, n, trans, prec, h, X, ldx, Y, ldy, ws, ws_bytes, status, stream, accumulate));
+    return tc_apass_run(src, m, n, trans, prec, r - h, X + h, ldx, Y + h, ldy, ws, ws_bytes, status, stream,
+                        accumulate);
   }
-  if (A.ld % 4 != 0 || (reinterpret_cast<uintptr_t>(A.data) & 15) != 0)
+  if (!src8 && (src.A->ld % 4 != 0 || (reinterpret_cast<uintptr_t>(src.A->data) & 15) != 0))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: A needs a 16-byte aligned base and ld % 4 == 0");
-  const TcShape s = tc_shape(A.m, A.n, r, trans);
+  if (src8 && (src.f8->ldc % 16 != 0 || (reinterpret_cast<uintptr_t>(src.f8->codes) & 15) != 0))
+    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: FP8 codes need a 16-byte aligned base and ld % 16 == 0");
+  const TcShape s = tc_shape(m, n, r, trans);
   Carver c(ws, ws_bytes);
   auto* Xhi = c.take<__nv_bfloat16>((size_t)s.NP * s.ldb);
   __nv_bfloat16* Xlo = split ? c.take<__nv_bfloat16>((size_t)s.NP * s.ldb) : nullptr;
@@ -491,12 +553,13 @@ rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, 
     RSVD_CUDA(after_launch());
   }
   CUtensorMap mapA, mapB, mapBlo;
-  if (trans)
-    RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A.data, (uint64_t)A.n, (uint64_t)A.m,
-                       (uint64_t)A.ld * 4, BM, BK, CU_TENSOR_MAP_SWIZZLE_NONE));
+  const uint32_t box_in = trans ? BM : BK, box_out = trans ? BK : BM;
+  if (src8)
+    RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_UINT8, src.f8->codes, (uint64_t)n, (uint64_t)m,
+                       (uint64_t)src.f8->ldc, box_in, box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
   else
-    RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A.data, (uint64_t)A.n, (uint64_t)A.m,
-                       (uint64_t)A.ld * 4, BK, BM, CU_TENSOR_MAP_SWIZZLE_NONE));
+    RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, src.A->data, (uint64_t)n, (uint64_t)m,
+                       (uint64_t)src.A->ld * 4, box_in, box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
   RSVD_TRY(encode_2d(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Xhi, (uint64_t)s.K, (uint64_t)s.NP,
                      (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP, CU_TENSOR_MAP_SWIZZLE_128B));
   if (split)
@@ -522,12 +585,19 @@ rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, 
   ta.ldc = s.nsplit > 1 ? r : ldy;
   ta.c_split_stride = s.nsplit > 1 ? slab : 0;
   ta.status = status;
+  ta.qscale = src8 ? src.f8->scales : nullptr;
+  ta.qm = src8 ? src.f8->qm : 1;
+  ta.qn = src8 ? src.f8->qn : 1;
+  ta.qtn = src8 ? cdiv(n, src.f8->qn) : 1;
 
   const int64_t units = s.mtiles * s.nsplit;
   const int grid = (int)(units < num_sms() ? units : num_sms());
   constexpr size_t kSmemMax = 232448;
   int s32 = kMaxS32;
-  auto need = [&](int depth) { return split ? Layout<true>::total(s.NP, depth) : Layout<false>::total(s.NP, depth); };
+  auto need = [&](int depth) {
+    return split ? Layout<true>::total(s.NP, depth)
+                 : (src8 ? Layout<false, true>::total(s.NP, depth) : Layout<false>::total(s.NP, depth));
+  };
   while (s32 > 2 && need(s32) > kSmemMax) --s32;
   const size_t smem = need(s32);
   if (smem > kSmemMax) return fail(RSVD_ERR_UNSUPPORTED, "tensor-core A-pass: shared memory plan too large");
@@ -538,7 +608,9 @@ rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, 
     RSVD_CUDA(after_launch());
     return RSVD_OK;
   };
-  if (trans) {
+  if (src8) {
+    RSVD_TRY(trans ? launch(tc_apass_kernel<true, false, true>) : launch(tc_apass_kernel<false, false, true>));
+  } else if (trans) {
     RSVD_TRY(split ? launch(tc_apass_kernel<true, true>) : launch(tc_apass_kernel<true, false>));
   } else {
     RSVD_TRY(split ? launch(tc_apass_kernel<false, true>) : launch(tc_apass_kernel<false, false>));
@@ -546,6 +618,25 @@ rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, 
   if (s.nsplit > 1)
     RSVD_TRY(reduce_partials<float>(s.M, r, s.nsplit, partial, r, slab, Y, ldy, accumulate, stream));
   return RSVD_OK;
+}
+
+}  // namespace
+
+rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X, int64_t ldx,
+                              float* Y, int64_t ldy, int64_t, int64_t, void* ws, size_t ws_bytes,
+                              int* status, cudaStream_t stream, bool accumulate) {
+  TcSource src;
+  src.A = &A;
+  return tc_apass_run(src, A.m, A.n, trans, prec, r, X, ldx, Y, ldy, ws, ws_bytes, status, stream, accumulate);
+}
+
+rsvd_status tc_apass_from_fp8(const Fp8Source& f8, int trans, int r, const float* X, int64_t ldx, float* Y,
+                              int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream,
+                              bool accumulate) {
+  TcSource src;
+  src.f8 = &f8;
+  return tc_apass_run(src, f8.m, f8.n, trans, RSVD_PREC_BF16, r, X, ldx, Y, ldy, ws, ws_bytes, status, stream,
+                      accumulate);
 }
 
 }  // namespace rsvd

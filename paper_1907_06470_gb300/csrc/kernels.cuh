@@ -142,6 +142,21 @@ rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const 
 size_t tc_apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t mb, int64_t nb);
 // `status` (may be NULL: a workspace word is used) receives DEV_TIMEOUT if a
 // pipeline wait expires.
+// fp8.cu -- E4M3 codes of A with one power-of-two scale per block-cyclic tile.
+struct Fp8Source {
+  const uint8_t* codes = nullptr;  // m x ldc bytes
+  int64_t m = 0, n = 0, ldc = 0;
+  const float* scales = nullptr;   // cdiv(m, qm) x cdiv(n, qn)
+  int64_t qm = 0, qn = 0;          // tile edges, clamped to m and n
+};
+bool fp8_tiles_ok(int64_t m, int64_t n, int64_t qm, int64_t qn);
+size_t fp8_amax_ws_bytes(int64_t m, int64_t n, int64_t qm, int64_t qn);
+rsvd_status fp8_quantize(const float* A, int64_t m, int64_t n, int64_t lda, int64_t qm, int64_t qn, uint8_t* codes,
+                         int64_t ldc, float* scales, unsigned* amax_ws, cudaStream_t stream);
+// The A-pass on the FP8 source (BF16 panel, FP32 accumulation).
+rsvd_status tc_apass_from_fp8(const Fp8Source& f8, int trans, int r, const float* X, int64_t ldx, float* Y,
+                              int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream,
+                              bool accumulate = false);
 rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X,
                               int64_t ldx, float* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws,
                               size_t ws_bytes, int* status, cudaStream_t stream, bool accumulate = false);
