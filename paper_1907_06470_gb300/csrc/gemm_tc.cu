@@ -267,16 +267,25 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         if (SRC8) {
           const uint8_t* src8 = smem + L::a32_off(NP, s32);
           if (!TRANS) {
-            // codes[i][k], 128 rows of 64 bytes; the block lies in one tile
+            // codes[i][k], 128 rows of 64 bytes; the block lies in one tile.  Four
+            // rows per step: lane l takes the 8 codes of 16-byte chunk c = l & 7
+            // of row 4 step + l / 8 and writes the whole BF16 chunk.
             const float sc = a.qscale[(mt * BM / a.qm) * a.qtn + (ks * BK / a.qn)];
-#pragma unroll 4
-            for (int rr = 0; rr < 32; ++rr) {
-              const int i = cw * 32 + rr;
-              const uint16_t c2 = reinterpret_cast<const uint16_t*>(src8 + i * BK)[lane];
-              const __nv_bfloat162 h = __float22bfloat162_rn(e4m3x2_scaled(c2, sc));
-              const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)lane >> 2) ^ ((uint32_t)i & 7u)) << 4) +
-                                   (((uint32_t)lane & 3u) << 2);
-              *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
+            const int c = lane & 7;
+#pragma unroll 2
+            for (int rr = 0; rr < 32; rr += 4) {
+              const int i = cw * 32 + rr + (lane >> 3);
+              const uint2 b = *reinterpret_cast<const uint2*>(src8 + i * BK + 8 * c);
+              uint32_t hw[4];
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const uint32_t word = t < 2 ? b.x : b.y;
+                const __nv_bfloat162 h =
+                    __float22bfloat162_rn(e4m3x2_scaled((uint16_t)(word >> (16 * (t & 1))), sc));
+                hw[t] = *reinterpret_cast<const uint32_t*>(&h);
+              }
+              const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)c) ^ ((uint32_t)i & 7u)) << 4);
+              *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
             }
           } else {
             // codes[k][i], 64 rows of 128 bytes: lane owns output row i
@@ -297,19 +306,26 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             }
           }
         } else if (!TRANS) {
-          // src[i][k], 128 rows of 64 floats: lane converts k = 2*lane, 2*lane+1 of row i
+          // src[i][k], 128 rows of 64 floats.  Two rows per step: lane l converts
+          // the float4 q = l & 15 (k = 4q .. 4q+3) of row 2 step + l / 16, i.e.
+          // half of 16-byte BF16 chunk q / 2.
+          const int q = lane & 15;
+          const uint32_t sub = ((uint32_t)q & 1u) << 3;
 #pragma unroll 4
-          for (int rr = 0; rr < 32; ++rr) {
-            const int i = cw * 32 + rr;
-            const float2 v = reinterpret_cast<const float2*>(src + i * BK)[lane];
-            const __nv_bfloat162 h = __float22bfloat162_rn(v);
-            const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)lane >> 2) ^ ((uint32_t)i & 7u)) << 4) +
-                                 (((uint32_t)lane & 3u) << 2);
-            *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
+          for (int rr = 0; rr < 32; rr += 2) {
+            const int i = cw * 32 + rr + (lane >> 4);
+            const float4 v = reinterpret_cast<const float4*>(src + i * BK)[q];
+            const __nv_bfloat162 h0 = __float22bfloat162_rn(make_float2(v.x, v.y));
+            const __nv_bfloat162 h1 = __float22bfloat162_rn(make_float2(v.z, v.w));
+            const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)q >> 1) ^ ((uint32_t)i & 7u)) << 4) + sub;
+            *reinterpret_cast<uint2*>(hi + off) =
+                make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
             if (SPLIT) {
-              const float2 hf = __bfloat1622float2(h);
-              const __nv_bfloat162 l = __float22bfloat162_rn(make_float2(v.x - hf.x, v.y - hf.y));
-              *reinterpret_cast<__nv_bfloat162*>(lo + off) = l;
+              const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+              const __nv_bfloat162 l0 = __float22bfloat162_rn(make_float2(v.x - f0.x, v.y - f0.y));
+              const __nv_bfloat162 l1 = __float22bfloat162_rn(make_float2(v.z - f1.x, v.w - f1.y));
+              *reinterpret_cast<uint2*>(lo + off) =
+                  make_uint2(*reinterpret_cast<const uint32_t*>(&l0), *reinterpret_cast<const uint32_t*>(&l1));
             }
           }
         } else {
