@@ -95,8 +95,14 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
             const bool ok = in_regs && i < rows;
             xv[t] = ok ? __ldcg(&mp[i]) : 0.0;
             yv[t] = ok ? __ldcg(&mq[i]) : 0.0;
-            a = fma(xv[t], xv[t], a); b = fma(yv[t], yv[t], b); g = fma(xv[t], yv[t], g);
           }
+          // FP64 instructions are expensive here (about 2 FMA per clock per SM):
+          // skip the slots no lane of the warp holds
+#pragma unroll
+          for (int t = 0; t < kMaxPerLane; ++t)
+            if (in_regs && 32 * t < rows) {
+              a = fma(xv[t], xv[t], a); b = fma(yv[t], yv[t], b); g = fma(xv[t], yv[t], g);
+            }
           double* wp = W + (int64_t)p * r;
           double* wq = W + (int64_t)q * r;
           double wu[kMaxPerLane], wv[kMaxPerLane];
