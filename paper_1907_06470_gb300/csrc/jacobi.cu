@@ -38,6 +38,28 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Rotation that annihilates g in the 2 x 2 Gram [[a, g], [g, b]] of a column
+// pair: t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / (2 g),
+// c = (1 + t^2)^-1/2, s = c t.  FP64 instructions are costly on this GPU
+// (about 2 FMA per clock per SM), so only what must hold to double precision is
+// formed in FP64: the angle itself may be off in the 8th digit (the sweep then
+// leaves |g| ~ 1e-7 |g| instead of 0, far below what the next sweep needs),
+// but c^2 + s^2 = c^2 (1 + t^2) must be 1 to rounding, so t is taken in FP32
+// (exact in FP64, 1 + t^2 exact) and c is refined from the FP32 estimate by two
+// Newton steps for (1 + t^2)^-1/2.  |zeta| stays below about 1e27 here (both
+// columns are above the rounding-level floor), so no FP32 overflow.
+__device__ __forceinline__ void jacobi_rotation(double a, double b, double g, double& c, double& s) {
+  const float z = (float)((b - a) / (2.0 * g));
+  const float tf = fabsf(z) > 1e18f ? 0.5f / z : copysignf(1.f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.f)));
+  const double t = (double)tf;
+  const double x = fma(t, t, 1.0);
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  c = y;
+  s = y * t;
+}
+
 // One cluster of up to 16 CTAs; warp w of CTA b owns pair slot b*warps + w of
 // every round.  Rounds are separated by the hardware cluster barrier; the
 // columns live in global memory and are accessed through L2 (.cg).
@@ -73,6 +95,7 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
   const double big = (double)(rows > r ? rows : r);
   const double zero2 = (big * eps) * (big * eps) * fro2;
   const double tol = (double)r * eps;
+  const double tol2 = tol * tol;
   cluster_sync_all();
 
   int sweep = 0;
@@ -122,12 +145,12 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
           a = warp_sum_d(a);
           b = warp_sum_d(b);
           g = warp_sum_d(g);
-          if (fabs(g) > tol * sqrt(a * b) && a > zero2 && b > zero2) {
-            if (lane == 0) atomicMax(&rotated[2 * kJacobiMaxSweeps + sweep], __float_as_int((float)(fabs(g) / sqrt(a * b))));
-            const double zeta = (b - a) / (2.0 * g);
-            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-            const double c = 1.0 / sqrt(1.0 + t * t);
-            const double sn = c * t;
+          if (g * g > tol2 * (a * b) && a > zero2 && b > zero2) {
+            if (lane == 0)
+              atomicMax(&rotated[2 * kJacobiMaxSweeps + sweep],
+                        __float_as_int(fabsf((float)g) * rsqrtf((float)a) * rsqrtf((float)b)));
+            double c, sn;
+            jacobi_rotation(a, b, g, c, sn);
             if (in_regs) {
 #pragma unroll
               for (int u = 0; u < kMaxPerLane; ++u) {
@@ -204,7 +227,7 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
           for (; i < rows; ++i) g0 = fma(xp[i], xq[i], g0);
           const double g = (g0 + g1) + (g2 + g3);
           const double b = nrm[q];
-          if (fabs(g) > tol * sqrt(a * b) && a > zero2 && b > zero2) bad = true;
+          if (g * g > tol2 * (a * b) && a > zero2 && b > zero2) bad = true;
         }
       }
       if (__any_sync(0xffffffffu, bad) && lane == 0) __stcg(&rotated[kJacobiMaxSweeps + sweep], 1);
@@ -234,10 +257,15 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
 }
 
 // FP32 one-sided Jacobi in one CTA with M and W in shared memory: the cheap
-// first phase.  Its rotations are accumulated in W32 (column-major), which the
-// FP64 phase then orthonormalises and applies to M before finishing in FP64.
+// first phase.  Columns are stored with stride ldm = r rounded up to 4; each
+// half-warp rotates one column pair, lane l holding the rows [4 V l, 4 V l +
+// 4 V) of both columns as V float4 (V = ceil(r / 64)), so a column moves in V
+// 16-byte loads per lane.  The 64 half-warps of the CTA cover every pair of a
+// round for r <= 128 at once.  The rotations are accumulated in W32
+// (column-major r x r), which the FP64 phase then orthonormalises and applies
+// to M before finishing in FP64.
 constexpr int kF32MaxR = 160;
-constexpr int kF32PerLane = (kF32MaxR + 15) / 16;  // a half-warp holds a column
+constexpr int kF32MaxV = (kF32MaxR + 63) / 64;  // float4 per lane and column
 
 __device__ __forceinline__ float half_warp_sum(float v) {
 #pragma unroll
@@ -245,29 +273,42 @@ __device__ __forceinline__ float half_warp_sum(float v) {
   return v;
 }
 
-// FP32 one-sided Jacobi in one CTA with M and W in shared memory: the cheap
-// first phase.  Each half-warp rotates one column pair, so the 64 half-warps
-// of the CTA cover every pair of a round for r <= 128 at once.  The rotations
-// are accumulated in W32 (column-major), which the FP64 phase then
-// orthonormalises and applies to M before finishing in FP64.
+// column of round-robin position pos in round `round` (positions 1 .. rp-1 rotate)
+__device__ __forceinline__ int rr_col_fast(int pos, int round, int rp) {
+  if (pos == 0) return 0;
+  int v = pos - 1 + round;
+  if (v >= rp - 1) v -= rp - 1;
+  return 1 + v;
+}
+
+size_t f32_jacobi_smem(int r) {
+  const size_t ldm = (size_t)round_up(r, 4);
+  return (2 * (size_t)r * ldm + r) * sizeof(float);
+}
+
 __global__ void __launch_bounds__(1024)
 jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32, int* sweeps_out) {
   extern __shared__ __align__(16) float smf[];
+  const int ldm = (r + 3) & ~3;
   float* M = smf;
-  float* W = smf + r * r;
+  float* W = smf + (size_t)r * ldm;
+  float* nrm = W + (size_t)r * ldm;
   __shared__ float redf[32];
   __shared__ int s_rot;
   __shared__ int s_maxrel;  // bits of the largest relative off-diagonal rotated in the sweep
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, warps = nt >> 5;
   const int hw = tid >> 4, hl = tid & 15, nhw = nt >> 4;  // half-warp index, lane in it
   const int rp = r + (r & 1), npairs = rp / 2;
+  const int V = (r + 63) / 64;          // float4 per lane and column
+  const int row0 = 4 * V * hl;          // first row this lane holds
   float f = 0.f;
-  for (int e = tid; e < r * r; e += nt) {
-    const float v = (float)Mc[e];
-    M[e] = v;
-    W[e] = (e / r) == (e % r) ? 1.f : 0.f;
-    f = fmaf(v, v, f);
-  }
+  for (int c = warp; c < r; c += warps)
+    for (int i = lane; i < ldm; i += 32) {
+      const float v = i < r ? (float)Mc[(int64_t)c * r + i] : 0.f;
+      M[c * ldm + i] = v;
+      W[c * ldm + i] = (i == c) ? 1.f : 0.f;
+      f = fmaf(v, v, f);
+    }
   f = warp_sum(f);
   if (lane == 0) redf[warp] = f;
   __syncthreads();
@@ -284,24 +325,26 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
     for (int round = 0; round < rp - 1; ++round) {
       // every half-warp takes the same number of iterations (shuffles need the full warp)
       for (int s0 = 0; s0 < npairs; s0 += nhw) {
-        const int s = s0 + hw;
+        const int sl = s0 + hw;
         int p = 0, q = 0;
-        bool active = s < npairs;
+        bool active = sl < npairs;
         if (active) {
-          p = rr_column(s, round, rp);
-          q = rr_column(rp - 1 - s, round, rp);
+          p = rr_col_fast(sl, round, rp);
+          q = rr_col_fast(rp - 1 - sl, round, rp);
           if (p >= r || q >= r) active = false;
           if (p > q) { const int t = p; p = q; q = t; }
         }
-        float xv[kF32PerLane], yv[kF32PerLane];
+        float4 xv[kF32MaxV], yv[kF32MaxV];
         float a = 0.f, b = 0.f, g = 0.f;
 #pragma unroll
-        for (int t = 0; t < kF32PerLane; ++t) {
-          const int i = hl + 16 * t;
-          const bool ok = active && i < r;
-          xv[t] = ok ? M[p * r + i] : 0.f;
-          yv[t] = ok ? M[q * r + i] : 0.f;
-          a = fmaf(xv[t], xv[t], a); b = fmaf(yv[t], yv[t], b); g = fmaf(xv[t], yv[t], g);
+        for (int t = 0; t < kF32MaxV; ++t) {
+          const int i = row0 + 4 * t;
+          const bool ok = active && t < V && i < ldm;
+          xv[t] = ok ? *reinterpret_cast<const float4*>(M + p * ldm + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+          yv[t] = ok ? *reinterpret_cast<const float4*>(M + q * ldm + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+          a = fmaf(xv[t].x, xv[t].x, fmaf(xv[t].y, xv[t].y, fmaf(xv[t].z, xv[t].z, fmaf(xv[t].w, xv[t].w, a))));
+          b = fmaf(yv[t].x, yv[t].x, fmaf(yv[t].y, yv[t].y, fmaf(yv[t].z, yv[t].z, fmaf(yv[t].w, yv[t].w, b))));
+          g = fmaf(xv[t].x, yv[t].x, fmaf(xv[t].y, yv[t].y, fmaf(xv[t].z, yv[t].z, fmaf(xv[t].w, yv[t].w, g))));
         }
         a = half_warp_sum(a); b = half_warp_sum(b); g = half_warp_sum(g);
         if (active && fabsf(g) > tol * sqrtf(a * b) && a > zero2 && b > zero2) {
@@ -311,14 +354,19 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
           const float c = 1.f / sqrtf(1.f + t * t);
           const float sn = c * t;
 #pragma unroll
-          for (int u = 0; u < kF32PerLane; ++u) {
-            const int i = hl + 16 * u;
-            if (i < r) {
-              M[p * r + i] = c * xv[u] - sn * yv[u];
-              M[q * r + i] = sn * xv[u] + c * yv[u];
-              const float wu = W[p * r + i], wv = W[q * r + i];
-              W[p * r + i] = c * wu - sn * wv;
-              W[q * r + i] = sn * wu + c * wv;
+          for (int u = 0; u < kF32MaxV; ++u) {
+            const int i = row0 + 4 * u;
+            if (u < V && i < ldm) {
+              float4* mp = reinterpret_cast<float4*>(M + p * ldm + i);
+              float4* mq = reinterpret_cast<float4*>(M + q * ldm + i);
+              const float4 x = xv[u], y = yv[u];
+              *mp = make_float4(c * x.x - sn * y.x, c * x.y - sn * y.y, c * x.z - sn * y.z, c * x.w - sn * y.w);
+              *mq = make_float4(sn * x.x + c * y.x, sn * x.y + c * y.y, sn * x.z + c * y.z, sn * x.w + c * y.w);
+              float4* wp = reinterpret_cast<float4*>(W + p * ldm + i);
+              float4* wq = reinterpret_cast<float4*>(W + q * ldm + i);
+              const float4 wu = *wp, wv = *wq;
+              *wp = make_float4(c * wu.x - sn * wv.x, c * wu.y - sn * wv.y, c * wu.z - sn * wv.z, c * wu.w - sn * wv.w);
+              *wq = make_float4(sn * wu.x + c * wv.x, sn * wu.y + c * wv.y, sn * wu.z + c * wv.z, sn * wu.w + c * wv.w);
             }
           }
           if (hl == 0) s_rot = 1;
@@ -333,10 +381,9 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
     if (mrel * mrel > tol) continue;  // far from convergence: sweep again without checking
     // check pass: the same stopping test on every pair, from the current
     // columns, without rotating (replaces the final sweep that finds nothing)
-    float* nrm = W + r * r;
     for (int c = warp; c < r; c += warps) {
       float s2 = 0.f;
-      for (int i = lane; i < r; i += 32) s2 = fmaf(M[c * r + i], M[c * r + i], s2);
+      for (int i = lane; i < r; i += 32) s2 = fmaf(M[c * ldm + i], M[c * ldm + i], s2);
       s2 = warp_sum(s2);
       if (lane == 0) nrm[c] = s2;
     }
@@ -345,17 +392,16 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
     bool bad = false;
     for (int p = warp; p < r; p += warps) {
       const float a = nrm[p];
+      const float4* xp = reinterpret_cast<const float4*>(M + p * ldm);
       for (int q = p + 1 + lane; q < r; q += 32) {
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
-        int i = 0;
-        for (; i + 4 <= r; i += 4) {
-          g0 = fmaf(M[p * r + i], M[q * r + i], g0);
-          g1 = fmaf(M[p * r + i + 1], M[q * r + i + 1], g1);
-          g2 = fmaf(M[p * r + i + 2], M[q * r + i + 2], g2);
-          g3 = fmaf(M[p * r + i + 3], M[q * r + i + 3], g3);
+        const float4* xq = reinterpret_cast<const float4*>(M + q * ldm);
+        float g0 = 0.f, g1 = 0.f;
+        for (int i = 0; i < ldm / 4; ++i) {
+          const float4 x = xp[i], y = xq[i];
+          g0 = fmaf(x.x, y.x, fmaf(x.y, y.y, g0));
+          g1 = fmaf(x.z, y.z, fmaf(x.w, y.w, g1));
         }
-        for (; i < r; ++i) g0 = fmaf(M[p * r + i], M[q * r + i], g0);
-        const float g = (g0 + g1) + (g2 + g3);
+        const float g = g0 + g1;
         const float b = nrm[q];
         if (fabsf(g) > tol * sqrtf(a * b) && a > zero2 && b > zero2) bad = true;
       }
@@ -364,7 +410,8 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
     __syncthreads();
     if (!s_rot) { ++sweep; break; }
   }
-  for (int e = tid; e < r * r; e += nt) W32[e] = W[e];
+  for (int c = warp; c < r; c += warps)
+    for (int i = lane; i < r; i += 32) W32[(int64_t)c * r + i] = W[c * ldm + i];
   if (tid == 0) *sweeps_out = sweep;
 }
 
@@ -485,10 +532,10 @@ rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double*
   static bool attr = false;
   if (!attr) {
     RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (2 * kF32MaxR * kF32MaxR + kF32MaxR) * (int)sizeof(float)));
+                                   (int)f32_jacobi_smem(kF32MaxR)));
     attr = true;
   }
-  jacobi_f32_kernel<<<1, 1024, (2 * (size_t)r * r + r) * sizeof(float), stream>>>(r, Mc, ws.W32, ws.sweeps);
+  jacobi_f32_kernel<<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
   RSVD_CUDA(after_launch());
   // Phase 2: Newton-Schulz steps make W orthogonal to FP64 accuracy:
   // W' = (1.5 I - 0.5 W W^T) W, i.e. on the column-major storage (= W^T row-major)
