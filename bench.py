@@ -97,6 +97,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_time_and_value(elapsed_ms: float, steps: int, device=None):
+    """Whole-job timing over replicas: the slowest rank's time (max over ranks)
+    and the aggregate throughput, world_size * steps / that time.  Without an
+    initialised process group this is the single-GPU case."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    return elapsed_ms, ws * steps / (elapsed_ms / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -225,12 +239,8 @@ def run_ours(args):
     elapsed_ms = e0.elapsed_time(e1)
     launches = g.kernel_launches() - launches0
     clocks = sampler.stop()
-    if ws > 1:
-        t = torch.tensor([elapsed_ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms, value = job_time_and_value(elapsed_ms, args.steps, device)
     ms_per_step = elapsed_ms / args.steps
-    value = ws * args.steps / (elapsed_ms / 1e3)
     S_head = S.double().cpu().numpy()
 
     # --- roofline of the dominant kernel: the A-pass ---------------------------
