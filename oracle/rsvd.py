@@ -72,6 +72,46 @@ def rsvd(A, k: int, p: int, q: int, seed: int, omega_dtype: str = "f64"):
     return U, sigma[:k], V
 
 
+def rsvd_auto_q(A, k: int, p: int, q_max: int, seed: int, tol: float = 1e-3, omega_dtype: str = "f64"):
+    """Randomized SVD with the iteration parameter chosen automatically
+    (Section 2.2: the decay of the singular values of A_q is measured with
+    increasing q, and iterations stop when the change falls below a threshold).
+
+    Reading taken: after i power iterations the estimates sigma^(i) are the
+    singular values of B_i = Q_i^T A (i = 0, 1, ...); the change
+    delta_i = ||sigma^(i)_{1..k} - sigma^(i-1)_{1..k}||_2 / ||sigma^(i)_{1..k}||_2
+    is monitored and the iterations stop at the first i >= 1 with delta_i <= tol,
+    or at i = q_max.  The basis for the next iteration is the orthonormal
+    factor of B_i^T = A^T Q_i (as in ``range_finder``), so no product with A is
+    spent on the monitoring.  Returns (U, S, V, q_used); the result equals
+    ``rsvd(A, k, p, q_used, seed, omega_dtype)``.
+    """
+    m, n = A.shape
+    r = k + p
+    if not (1 <= k and 0 <= p and r <= min(m, n) and q_max >= 0):
+        raise ValueError("need 1 <= k, 0 <= p, k + p <= min(m, n), q_max >= 0")
+    O = gaussian_matrix_as_f64(n, r, seed, omega_dtype)
+    Q, _ = householder_qr(apply(A, O))
+    prev = None
+    i = 0
+    while True:
+        Bt = apply(A, Q, trans=True)
+        UB, sigma, V = small_svd_of_bt(Bt)
+        if prev is not None:
+            delta = np.linalg.norm(sigma[:k] - prev[:k]) / np.linalg.norm(sigma[:k])
+            if delta <= tol:
+                break
+        if i == q_max:
+            break
+        prev = sigma
+        Z, _ = householder_qr(Bt)
+        Q, _ = householder_qr(apply(A, Z))
+        i += 1
+    U = Q @ UB[:, :k]
+    U, V = normalise_signs(U, V[:, :k])
+    return U, sigma[:k], V, i
+
+
 def full_svd(A):
     """Exact thin SVD of a small dense matrix by one-sided Jacobi.
 

@@ -121,3 +121,30 @@ def test_fp32_input_is_widened_exactly():
     assert np.array_equal(apply(A32, X), A32.astype(np.float64) @ X)
     Q, _ = householder_qr(apply(A32, X))
     assert Q.shape == (50, 3)
+
+
+def test_auto_q_equals_fixed_q_at_the_chosen_count():
+    """The automatic loop is the fixed-q computation stopped early: bit-identical."""
+    A, _, _ = prescribed_dense(600, 300, spectrum_geometric(300, 0.97), 21)
+    for tol in (1e-1, 1e-3, 1e-6):
+        U, S, V, qu = R.rsvd_auto_q(A, 10, 5, 6, 2001, tol)
+        Uf, Sf, Vf = R.rsvd(A, 10, 5, qu, 2001)
+        assert np.array_equal(S, Sf) and np.array_equal(U, Uf) and np.array_equal(V, Vf)
+
+
+def test_auto_q_stops_at_one_for_an_exactly_low_rank_matrix():
+    """rank(A) <= r: the first sketch already spans the range, sigma^(1) = sigma^(0)
+    to rounding, so one iteration is used."""
+    s = np.concatenate([spectrum_geometric(12, 0.8), np.zeros(188)])
+    A, _, _ = prescribed_dense(400, 200, s, 22)
+    _, S, _, qu = R.rsvd_auto_q(A, 8, 6, 5, 2001, 1e-8)
+    assert qu == 1
+    assert np.max(np.abs(S - s[:8]) / s[:8]) < 1e-12
+
+
+def test_auto_q_runs_to_the_limit_when_the_spectrum_keeps_moving():
+    A, _, _ = prescribed_dense(500, 400, spectrum_geometric(400, 0.999), 23)
+    _, _, _, qu = R.rsvd_auto_q(A, 20, 5, 3, 2001, 1e-12)
+    assert qu == 3
+    with pytest.raises(ValueError):
+        R.rsvd_auto_q(A, 20, 5, -1, 2001)
