@@ -74,6 +74,14 @@ typedef struct {
   int32_t dtype;     /* rsvd_dtype of A and of the outputs: F64 or F32 (default F32) */
   int32_t kind;      /* rsvd_kind of the matrices this plan runs on (default DENSE);
                         CSR plans take dtype F32 and prec FP32 */
+  int32_t auto_q;    /* 1: choose the number of power iterations automatically,
+                        with q (rsvd_plan) as the maximum (Section 2.2): after i
+                        iterations the singular values sigma^(i) of B_i = Q_i^T A
+                        are formed; iterations stop at the first i >= 1 with
+                        ||sigma^(i) - sigma^(i-1)||_2 <= auto_q_tol ||sigma^(i)||_2
+                        over the top k, or at i = q.  Costs one small SVD per
+                        iteration; rsvd_plan_info reports the count used. */
+  double auto_q_tol; /* tolerance of auto_q; 0 selects 1e-3 */
 } rsvd_opts;
 
 /* Descriptor of the input matrix A (m x n). */
@@ -117,6 +125,7 @@ typedef struct {
   size_t workspace_bytes;    /* device memory owned by the plan */
   size_t min_cap_bytes;      /* smallest mem_cap this problem can be planned in */
   uint64_t seed;
+  int32_t q_used;            /* power iterations applied by the last rsvd_run */
 } rsvd_plan_info_t;
 
 /* ---- Section 2.1 / 2.2: plan and run -------------------------------------- */

@@ -107,7 +107,7 @@ class Plan:
     """A planned rank-k randomized SVD (rsvd_plan); owns its device workspace."""
 
     def __init__(self, m, n, k, p=10, q=2, seed=0, mem_cap=0, prec=None, dtype="f32",
-                 mb=0, nb=0, refine=True, n_slots=2, kind="dense"):
+                 mb=0, nb=0, refine=True, n_slots=2, kind="dense", auto_q=False, auto_q_tol=0.0):
         lib = load()
         if prec is None:
             prec = "fp64" if dtype == "f64" else "fp32"
@@ -118,6 +118,8 @@ class Plan:
         o.n_slots = n_slots
         o.dtype = _lib.DTYPE[dtype]
         o.kind = {"dense": _lib.DENSE, "csr": _lib.CSR}[kind]
+        o.auto_q = 1 if auto_q else 0
+        o.auto_q_tol = float(auto_q_tol)
         self.kind = kind
         h = C.c_void_p()
         _check(lib.rsvd_plan(m, n, k, p, q, seed, mem_cap, C.byref(o), C.byref(h)))

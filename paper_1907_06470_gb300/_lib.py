@@ -25,7 +25,8 @@ ON_DEVICE, ON_HOST = 0, 1
 
 class RsvdOpts(C.Structure):
     _fields_ = [("prec", c_i32), ("refine", c_i32), ("mb", c_i64), ("nb", c_i64),
-                ("n_slots", c_i32), ("dtype", c_i32), ("kind", c_i32)]
+                ("n_slots", c_i32), ("dtype", c_i32), ("kind", c_i32), ("auto_q", c_i32),
+                ("auto_q_tol", C.c_double)]
 
 
 class RsvdMatrix(C.Structure):
@@ -43,7 +44,7 @@ class RsvdPlanInfo(C.Structure):
     _fields_ = [("m", c_i64), ("n", c_i64), ("k", c_i32), ("p", c_i32), ("q", c_i32), ("r", c_i32),
                 ("prec", c_i32), ("dtype", c_i32), ("mb", c_i64), ("nb", c_i64),
                 ("tiles_m", c_i64), ("tiles_n", c_i64), ("n_slots", c_i32), ("resident", c_i32),
-                ("workspace_bytes", c_size), ("min_cap_bytes", c_size), ("seed", c_u64)]
+                ("workspace_bytes", c_size), ("min_cap_bytes", c_size), ("seed", c_u64), ("q_used", c_i32)]
 
 
 # Every function the header declares, with its ctypes signature.

@@ -195,6 +195,11 @@ struct rsvd_plan_s {
   JacobiWs jac;
   double* R = nullptr;      // r x r
   double* sigma = nullptr;  // r
+  double* sigma_prev = nullptr;  // r: estimates of the previous power iteration (automatic q)
+  int* q_flag = nullptr;    // device word: 1 when the change fell below the tolerance
+  int auto_q = 0;           // choose q automatically (q is then the maximum)
+  double auto_q_tol = 1e-3;
+  int q_used = 0;           // power iterations applied by the last run
   double* UR = nullptr;     // r x r
   double* WR = nullptr;     // r x r
   void* URk = nullptr;      // r x k in dtype
@@ -244,6 +249,8 @@ rsvd_status check_args(int64_t m, int64_t n, int k, int p, int q, const rsvd_opt
       return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: FP64 precision goes with FP64 data and only with it");
     if (o->mb < 0 || o->nb < 0 || o->n_slots < 0)
       return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: negative tile edge or slot count");
+    if (o->auto_q_tol < 0.0 || !(o->auto_q_tol == o->auto_q_tol))
+      return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: auto_q_tol must be >= 0 (0: default 1e-3)");
   }
   return RSVD_OK;
 }
@@ -259,6 +266,8 @@ void apply_opts(rsvd_plan_s* P, const rsvd_opts* o) {
     P->nb_req = o->nb;
     P->n_slots = o->n_slots > 0 ? o->n_slots : 2;
     P->kind = o->kind;
+    P->auto_q = o->auto_q ? 1 : 0;
+    if (o->auto_q_tol > 0.0) P->auto_q_tol = o->auto_q_tol;
   }
   if (P->mb <= 0) P->mb = P->m;  // in core: one block row unless asked otherwise
   if (P->nb <= 0) P->nb = P->n;
@@ -289,6 +298,8 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   P->jac = jacobi_ws_carve(c, P->r, P->r);
   P->R = c.take<double>((size_t)P->r * P->r);
   P->sigma = c.take<double>((size_t)P->r);
+  P->sigma_prev = c.take<double>((size_t)P->r);
+  P->q_flag = c.take<int>(4);
   P->UR = c.take<double>((size_t)P->r * P->r);
   P->WR = c.take<double>((size_t)P->r * P->r);
   P->URk = c.take<char>((size_t)P->r * P->k * esz);
@@ -373,19 +384,51 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     // step 2 and steps 3-4: Y = A O, Q = orth(Y)
     RSVD_TRY(apass(0, prec, X, Y));
     RSVD_TRY(orth(m, Y, Q));
-    // Eq. (3), right to left: q times Z = orth(A^T Q), Q = orth(A Z)
-    for (int it = 0; it < P->q; ++it) {
-      RSVD_TRY(apass(1, prec, Q, Bt));
-      RSVD_TRY(orth(n, Bt, X));
-      RSVD_TRY(apass(0, prec, X, Y));
-      RSVD_TRY(orth(m, Y, Q));
-    }
-    // step 5: B^T = A^T Q
-    RSVD_TRY(apass(1, final_prec, Q, Bt));
-    {  // step 6: B^T = Q_b R, R^T = U_R diag(sigma) W^T  =>  B = U_R diag(sigma) (Q_b W)^T
+    auto small_svd = [&]() -> rsvd_status {  // step 6 on the current B^T
       Span sp(pf, RSVD_STAGE_SMALL_SVD, st);
       RSVD_TRY(orth_panel<T>(n, r, Bt, ldr, Qb, ldr, P->R, P->orth, st));
-      RSVD_TRY(jacobi_svd(r, r, P->R, P->sigma, P->UR, P->WR, P->jac, st));
+      return jacobi_svd(r, r, P->R, P->sigma, P->UR, P->WR, P->jac, st);
+    };
+    bool have_final = false;  // Bt, Qb, R and the small SVD already hold the final result
+    P->q_used = P->q;
+    if (!P->auto_q) {
+      // Eq. (3), right to left: q times Z = orth(A^T Q), Q = orth(A Z)
+      for (int it = 0; it < P->q; ++it) {
+        RSVD_TRY(apass(1, prec, Q, Bt));
+        RSVD_TRY(orth(n, Bt, X));
+        RSVD_TRY(apass(0, prec, X, Y));
+        RSVD_TRY(orth(m, Y, Q));
+      }
+    } else {
+      // Section 2.2, automatic iteration parameter: after each power iteration
+      // the small SVD of B_i^T = A^T Q_i gives sigma^(i); stop once
+      // ||sigma^(i) - sigma^(i-1)|| / ||sigma^(i)|| (top k) <= tol, or at q.  The
+      // next basis is Q_b of that small SVD (= orth(A^T Q_i)), so the
+      // monitoring costs one small SVD per iteration and no extra pass.
+      int it = 0;
+      for (;; ++it) {
+        RSVD_TRY(apass(1, prec, Q, Bt));
+        RSVD_TRY(small_svd());
+        if (it > 0) {
+          RSVD_TRY(sigma_change_below(k, P->sigma, P->sigma_prev, P->auto_q_tol, P->q_flag, st));
+          int h = 0;
+          RSVD_CUDA(cudaMemcpyAsync(&h, P->q_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+          RSVD_CUDA(cudaStreamSynchronize(st));
+          if (h) break;
+        }
+        if (it == P->q) break;
+        RSVD_CUDA(cudaMemcpyAsync(P->sigma_prev, P->sigma, (size_t)r * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        RSVD_TRY(apass(0, prec, Qb, Y));
+        RSVD_TRY(orth(m, Y, Q));
+      }
+      P->q_used = it;
+      have_final = final_prec == prec;  // else recompute B^T in the refinement precision
+    }
+    if (!have_final) {
+      // step 5: B^T = A^T Q
+      RSVD_TRY(apass(1, final_prec, Q, Bt));
+      // step 6: B^T = Q_b R, R^T = U_R diag(sigma) W^T  =>  B = U_R diag(sigma) (Q_b W)^T
+      RSVD_TRY(small_svd());
     }
     {  // step 7: U = Q U_R[:, :k], V = Q_b W[:, :k]
       Span sp(pf, RSVD_STAGE_LIFT, st);
@@ -709,6 +752,7 @@ rsvd_status rsvd_plan_info(rsvd_plan_t P, rsvd_plan_info_t* o) {
   o->prec = P->prec; o->dtype = P->dtype; o->mb = P->mb; o->nb = P->nb;
   o->tiles_m = cdiv(P->m, P->mb); o->tiles_n = cdiv(P->n, P->nb); o->n_slots = P->n_slots;
   o->resident = 1; o->workspace_bytes = P->ws_bytes; o->min_cap_bytes = P->ws_bytes; o->seed = P->seed;
+  o->q_used = P->q_used;
   return RSVD_OK;
 }
 

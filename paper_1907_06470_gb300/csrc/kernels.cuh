@@ -93,6 +93,9 @@ template <typename T>
 rsvd_status normalise_signs(int64_t m, int64_t n, int k, T* U, int64_t ldu, T* V, int64_t ldv,
                             void* scratch, size_t scratch_bytes, cudaStream_t stream);
 size_t sign_scratch_bytes(int64_t m, int k);
+// *flag = 1 when ||sigma[:k] - prev[:k]|| <= tol ||sigma[:k]|| (automatic q)
+rsvd_status sigma_change_below(int k, const double* sigma, const double* prev, double tol, int* flag,
+                               cudaStream_t stream);
 // out[c*rows + i] = (double) A[i*s_row + c*s_col]  (column-major FP64 gather)
 template <typename T>
 rsvd_status gather_colmajor_f64(int64_t rows, int64_t cols, const T* A, int64_t s_row, int64_t s_col,

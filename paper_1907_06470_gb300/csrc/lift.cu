@@ -166,6 +166,37 @@ rsvd_status normalise_signs(int64_t m, int64_t n, int k, T* U, int64_t ldu, T* V
   return RSVD_OK;
 }
 
+namespace {
+// flag = 1 when ||s[:k] - prev[:k]||^2 <= tol^2 ||s[:k]||^2 (one block, fixed-order sums)
+__global__ void sigma_change_kernel(int k, const double* __restrict__ s, const double* __restrict__ prev, double tol,
+                                    int* flag) {
+  __shared__ double red[2][32];
+  double num = 0.0, den = 0.0;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    const double d = s[j] - prev[j];
+    num += d * d;
+    den += s[j] * s[j];
+  }
+  num = warp_sum(num);
+  den = warp_sum(den);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[0][w] = num; red[1][w] = den; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += red[0][i]; b += red[1][i]; }
+    *flag = (a <= tol * tol * b) ? 1 : 0;
+  }
+}
+}  // namespace
+
+rsvd_status sigma_change_below(int k, const double* sigma, const double* prev, double tol, int* flag,
+                               cudaStream_t stream) {
+  sigma_change_kernel<<<1, 256, 0, stream>>>(k, sigma, prev, tol, flag);
+  RSVD_CUDA(after_launch());
+  return RSVD_OK;
+}
+
 template rsvd_status normalise_signs<float>(int64_t, int64_t, int, float*, int64_t, float*, int64_t,
                                             void*, size_t, cudaStream_t);
 template rsvd_status normalise_signs<double>(int64_t, int64_t, int, double*, int64_t, double*, int64_t,

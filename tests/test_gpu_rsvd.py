@@ -98,3 +98,41 @@ def test_repeated_runs_are_bit_identical(g):
     b = plan.run(Ad)
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_automatic_q_matches_oracle(g, prec):
+    """Section 2.2 automatic iteration parameter: the same stopping point as the
+    oracle (tolerance 1e-3 sits between consecutive changes by a factor >= 1.7)
+    and the oracle's result at that point."""
+    if prec == "fp64":
+        A, _, _ = prescribed_dense(2000, 1000, spectrum_geometric(1000, 0.97), 1001)
+        k, p, seed, od, qexp = 20, 10, 2001, "f64", 4
+    else:
+        A, _, _ = prescribed_dense(4000, 2000, spectrum_harmonic_noisy(2000, 1e-4, 3002), 1002, dtype=np.float32)
+        k, p, seed, od, qexp = 50, 10, 2002, "f32", 3
+    Ad = torch.as_tensor(A, device="cuda")
+    plan = g.Plan(A.shape[0], A.shape[1], k, p, 6, seed, prec=prec, dtype="f64" if prec == "fp64" else "f32",
+                  auto_q=True, auto_q_tol=1e-3)
+    U, S, V = (t.cpu().numpy().astype(np.float64) for t in plan.run(Ad))
+    qu = plan.info()["q_used"]
+    plan.close()
+    Uo, So, Vo, quo = OR.rsvd_auto_q(A, k, p, 6, seed, 1e-3, od)
+    assert quo == qexp and qu == quo
+    assert sigma_rel_err(S, So) <= (1e-11 if prec == "fp64" else 1e-5)
+    assert max_principal_angle(U, Uo) <= (1e-9 if prec == "fp64" else 1e-4)
+    # and the same as a fixed-q plan with that count
+    Uf, Sf, Vf = (t.cpu().numpy().astype(np.float64) for t in g.rsvd(Ad, k, p, qu, seed, prec=prec))
+    assert sigma_rel_err(S, Sf) <= (1e-12 if prec == "fp64" else 1e-6)
+
+
+def test_automatic_q_bf16_refines_the_final_pass(g):
+    A, _, _ = prescribed_dense(4000, 2000, spectrum_harmonic_noisy(2000, 1e-4, 3002), 1002, dtype=np.float32)
+    Ad = torch.as_tensor(A, device="cuda")
+    plan = g.Plan(4000, 2000, 50, 10, 6, 2002, prec="bf16", auto_q=True, auto_q_tol=1e-3)
+    U, S, V = plan.run(Ad)
+    qu = plan.info()["q_used"]
+    plan.close()
+    assert 2 <= qu <= 4
+    Uo, So, Vo = OR.rsvd(A, 50, 10, qu, 2002, "bf16")
+    assert sigma_rel_err(S.cpu().numpy(), So) <= 5e-4
