@@ -38,7 +38,8 @@ typedef enum {
   RSVD_ERR_NOT_SPD = 5,       /* Cholesky breakdown: Gram matrix not positive definite */
   RSVD_ERR_NO_CONVERGE = 6,   /* Jacobi sweep limit reached */
   RSVD_ERR_TIMEOUT = 7,       /* a device-side wait exceeded its spin limit */
-  RSVD_ERR_UNSUPPORTED = 8    /* valid request this build does not implement */
+  RSVD_ERR_UNSUPPORTED = 8,   /* valid request this build does not implement */
+  RSVD_ERR_INTERRUPTED = 9    /* the run stopped on request after writing a checkpoint */
 } rsvd_status;
 
 /* Arithmetic of the A-passes (the products with A of Section 2.1 steps 2 and 5
@@ -126,7 +127,18 @@ typedef struct {
   size_t min_cap_bytes;      /* smallest mem_cap this problem can be planned in */
   uint64_t seed;
   int32_t q_used;            /* power iterations applied by the last rsvd_run */
+  int32_t resumed_from;      /* checkpoint step the last rsvd_run resumed after; -1: none */
 } rsvd_plan_info_t;
+
+/* Header of a checkpoint file (rsvd_plan_set_checkpoint). */
+typedef struct {
+  int64_t m, n;
+  int32_t k, p, q, r, prec, dtype, kind;
+  uint64_t seed, fingerprint;
+  int32_t step;               /* range-finder step whose basis the file holds */
+  int64_t panel_rows;         /* m (Q after an even step) or n (Z after an odd step) */
+  uint64_t panel_bytes;
+} rsvd_checkpoint_info_t;
 
 /* ---- Section 2.1 / 2.2: plan and run -------------------------------------- */
 
@@ -174,6 +186,25 @@ rsvd_status rsvd_plan_info(rsvd_plan_t plan, rsvd_plan_info_t* out);
  * TIMEOUT, CUDA.  The plan stays valid after an error. */
 rsvd_status rsvd_run(rsvd_plan_t plan, const rsvd_matrix* A, void* U, void* S, void* V,
                      void* stream);
+
+/* Persistence and recoverability (Section 3.8).  With a path set, rsvd_run
+ * writes the range finder's basis after each of its steps -- step 0: Q_0 =
+ * orth(A O); step 2i+1: Z_{i+1} = orth(A^T Q_i); step 2i+2: Q_{i+1} =
+ * orth(A Z_{i+1}) -- to `path` (through path.tmp and a rename), with a header
+ * holding the plan's m, n, k, p, q, seed, precision, dtype, kind, the step and
+ * a fingerprint of A (sampled entries).  An rsvd_run whose plan and A match a
+ * valid checkpoint at `path` loads its basis and continues after that step
+ * (rsvd_plan_info: resumed_from); the result is the same as without the
+ * interruption.  The file is removed when the run completes.
+ * stop_after_step >= 0 makes rsvd_run return RSVD_ERR_INTERRUPTED right after
+ * writing that step's checkpoint (a planned interruption).  path NULL or ""
+ * turns checkpoints off.  Fixed q only (UNSUPPORTED with auto_q).  Host only. */
+rsvd_status rsvd_plan_set_checkpoint(rsvd_plan_t plan, const char* path, int32_t stop_after_step);
+
+/* Reads and validates the header of a checkpoint file (host only; magic,
+ * version and header checksum).  Errors: INVALID_ARG if there is no valid
+ * checkpoint at `path`. */
+rsvd_status rsvd_checkpoint_info(const char* path, rsvd_checkpoint_info_t* out);
 
 /* Exact thin SVD of a small dense device matrix (Section 3: the library's
  * non-approximate path), t = min(m, n) <= 256 and m*n <= 2^24: U m x t, S t,

@@ -25,7 +25,7 @@ from . import _lib
 from ._lib import RsvdError, load  # noqa: F401
 
 __all__ = ["rsvd", "Plan", "full_svd", "gaussian", "tile_map", "apass", "orth", "small_svd",
-           "small_svd_noalloc", "csr_transpose", "fp8_quantize", "RsvdError", "load"]
+           "small_svd_noalloc", "csr_transpose", "fp8_quantize", "checkpoint_info", "RsvdError", "load"]
 
 
 def _torch():
@@ -171,6 +171,11 @@ class Plan:
         h2d, per_pass, resident = C.c_uint64(), C.c_int64(), C.c_int64()
         _check(load().rsvd_plan_stream_stats(self._h, C.byref(h2d), C.byref(per_pass), C.byref(resident)))
         return {"h2d_bytes": h2d.value, "tiles_streamed_per_pass": per_pass.value, "tiles_resident": resident.value}
+
+    def set_checkpoint(self, path, stop_after_step=-1):
+        """Persist the range finder's basis after each step to `path` and resume
+        from a matching checkpoint there (Section 3.8); None turns it off."""
+        _check(load().rsvd_plan_set_checkpoint(self._h, path.encode() if path else None, stop_after_step))
 
     def set_profiling(self, on=True):
         _check(load().rsvd_plan_set_profiling(self._h, 1 if on else 0))
@@ -356,6 +361,13 @@ def fp8_quantize(A, qm=0, qn=0):
     _check(load().rsvd_fp8_quantize(C.byref(d), qm, qn, C.c_void_p(codes.data_ptr()), ldc,
                                     C.c_void_p(scales.data_ptr()), _stream_ptr()))
     return codes[:, :n], scales
+
+
+def checkpoint_info(path) -> dict:
+    """Header of a checkpoint file written by a plan with set_checkpoint."""
+    info = _lib.RsvdCheckpointInfo()
+    _check(load().rsvd_checkpoint_info(str(path).encode(), C.byref(info)))
+    return {f: getattr(info, f) for f, _ in info._fields_}
 
 
 def orth(Y, want_R=False):

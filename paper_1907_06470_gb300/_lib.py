@@ -15,7 +15,7 @@ STAGES = ["gaussian", "apass_fwd", "apass_trans", "orth", "small_svd", "lift", "
 STATUS_NAMES = {
     0: "RSVD_OK", 1: "RSVD_ERR_INVALID_ARG", 2: "RSVD_ERR_OOM", 3: "RSVD_ERR_CAP_TOO_SMALL",
     4: "RSVD_ERR_CUDA", 5: "RSVD_ERR_NOT_SPD", 6: "RSVD_ERR_NO_CONVERGE", 7: "RSVD_ERR_TIMEOUT",
-    8: "RSVD_ERR_UNSUPPORTED",
+    8: "RSVD_ERR_UNSUPPORTED", 9: "RSVD_ERR_INTERRUPTED",
 }
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3, "fp8": 4}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2}
@@ -44,7 +44,14 @@ class RsvdPlanInfo(C.Structure):
     _fields_ = [("m", c_i64), ("n", c_i64), ("k", c_i32), ("p", c_i32), ("q", c_i32), ("r", c_i32),
                 ("prec", c_i32), ("dtype", c_i32), ("mb", c_i64), ("nb", c_i64),
                 ("tiles_m", c_i64), ("tiles_n", c_i64), ("n_slots", c_i32), ("resident", c_i32),
-                ("workspace_bytes", c_size), ("min_cap_bytes", c_size), ("seed", c_u64), ("q_used", c_i32)]
+                ("workspace_bytes", c_size), ("min_cap_bytes", c_size), ("seed", c_u64), ("q_used", c_i32),
+                ("resumed_from", c_i32)]
+
+
+class RsvdCheckpointInfo(C.Structure):
+    _fields_ = [("m", c_i64), ("n", c_i64), ("k", c_i32), ("p", c_i32), ("q", c_i32), ("r", c_i32),
+                ("prec", c_i32), ("dtype", c_i32), ("kind", c_i32), ("seed", c_u64), ("fingerprint", c_u64),
+                ("step", c_i32), ("panel_rows", c_i64), ("panel_bytes", c_u64)]
 
 
 # Every function the header declares, with its ctypes signature.
@@ -74,6 +81,8 @@ SIGNATURES = {
     "rsvd_small_svd_noalloc": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "rsvd_csr_transpose": (c_i32, [c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "rsvd_spmm_workspace": (c_size, [c_i64, c_i32]),
+    "rsvd_plan_set_checkpoint": (c_i32, [c_vp, C.c_char_p, c_i32]),
+    "rsvd_checkpoint_info": (c_i32, [C.c_char_p, C.POINTER(RsvdCheckpointInfo)]),
     "rsvd_fp8_quantize": (c_i32, [C.POINTER(RsvdMatrix), c_i64, c_i64, c_vp, c_i64, c_vp, c_vp]),
 }
 NOALLOC_MAX_R = 256

@@ -200,6 +200,9 @@ struct rsvd_plan_s {
   int auto_q = 0;           // choose q automatically (q is then the maximum)
   double auto_q_tol = 1e-3;
   int q_used = 0;           // power iterations applied by the last run
+  std::string ckpt_path;    // checkpoint file of the range finder ("" = off)
+  int ckpt_stop_after = -1; // stop (RSVD_ERR_INTERRUPTED) after writing this step's checkpoint
+  int resumed_from = -1;    // step the last run resumed after (-1: started afresh)
   double* UR = nullptr;     // r x r
   double* WR = nullptr;     // r x r
   void* URk = nullptr;      // r x k in dtype
@@ -365,6 +368,35 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     Span sp(pf, RSVD_STAGE_ORTH, st);
     return orth_panel<T>(M, r, Yin, ldr, Qout, ldr, nullptr, P->orth, st);
   };
+  // Section 3.8 persistence: the header of each checkpoint places its basis in
+  // the execution plan; a matching checkpoint lets the run skip its steps.
+  const bool ckpt_on = !P->ckpt_path.empty() && !P->auto_q;
+  CkptHeader hdr;
+  std::memset(&hdr, 0, sizeof(hdr));
+  int first_step = 0;
+  P->resumed_from = -1;
+  if (ckpt_on) {
+    hdr.m = m; hdr.n = n; hdr.k = k; hdr.p = P->p; hdr.q = P->q; hdr.r = r; hdr.ldr = ldr;
+    hdr.prec = prec; hdr.dtype = P->dtype; hdr.kind = A.kind; hdr.seed = P->seed;
+    RSVD_TRY(matrix_fingerprint(A, &hdr.fingerprint, st));
+    const int done = ckpt_try_load(P->ckpt_path, hdr, Q, X, st);
+    if (done >= 0) {
+      first_step = done + 1;
+      P->resumed_from = done;
+    }
+  }
+  auto checkpoint = [&](int step) -> rsvd_status {
+    if (!ckpt_on) return RSVD_OK;
+    CkptHeader h = hdr;
+    h.step = step;
+    h.panel_rows = (step % 2 == 0) ? m : n;
+    h.panel_bytes = (uint64_t)h.panel_rows * ldr * (P->dtype == RSVD_F64 ? 8 : 4);
+    RSVD_TRY(read_device_status(P->status, st));  // never persist a basis from a failed step
+    RSVD_TRY(ckpt_save(P->ckpt_path, h, (step % 2 == 0) ? (const void*)Q : (const void*)X, st));
+    if (P->ckpt_stop_after == step)
+      return fail(RSVD_ERR_INTERRUPTED, "rsvd_run: stopped after checkpoint step " + std::to_string(step));
+    return RSVD_OK;
+  };
   {
     Span total(pf, RSVD_STAGE_TOTAL, st);
     RSVD_CUDA(cudaMemsetAsync(P->status, 0, sizeof(int), st));
@@ -381,9 +413,13 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
                               P->f8_amax, st));
       }
     }
-    // step 2 and steps 3-4: Y = A O, Q = orth(Y)
-    RSVD_TRY(apass(0, prec, X, Y));
-    RSVD_TRY(orth(m, Y, Q));
+    // step 2 and steps 3-4: Y = A O, Q = orth(Y) (range-finder step 0), unless
+    // a checkpoint of this plan and this A lets the run resume later
+    if (first_step == 0) {
+      RSVD_TRY(apass(0, prec, X, Y));
+      RSVD_TRY(orth(m, Y, Q));
+      RSVD_TRY(checkpoint(0));
+    }
     auto small_svd = [&]() -> rsvd_status {  // step 6 on the current B^T
       Span sp(pf, RSVD_STAGE_SMALL_SVD, st);
       RSVD_TRY(orth_panel<T>(n, r, Bt, ldr, Qb, ldr, P->R, P->orth, st));
@@ -392,12 +428,17 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     bool have_final = false;  // Bt, Qb, R and the small SVD already hold the final result
     P->q_used = P->q;
     if (!P->auto_q) {
-      // Eq. (3), right to left: q times Z = orth(A^T Q), Q = orth(A Z)
-      for (int it = 0; it < P->q; ++it) {
-        RSVD_TRY(apass(1, prec, Q, Bt));
-        RSVD_TRY(orth(n, Bt, X));
-        RSVD_TRY(apass(0, prec, X, Y));
-        RSVD_TRY(orth(m, Y, Q));
+      // Eq. (3), right to left: q times Z = orth(A^T Q), Q = orth(A Z); step
+      // 2i+1 leaves Z in X, step 2i+2 leaves Q (checkpointed when enabled)
+      for (int s = first_step > 0 ? first_step : 1; s <= 2 * P->q; ++s) {
+        if (s & 1) {
+          RSVD_TRY(apass(1, prec, Q, Bt));
+          RSVD_TRY(orth(n, Bt, X));
+        } else {
+          RSVD_TRY(apass(0, prec, X, Y));
+          RSVD_TRY(orth(m, Y, Q));
+        }
+        RSVD_TRY(checkpoint(s));
       }
     } else {
       // Section 2.2, automatic iteration parameter: after each power iteration
@@ -444,6 +485,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   }
   const rsvd_status res = read_device_status(P->status, st);
   if (pf.on) pf.collect();
+  if (res == RSVD_OK && ckpt_on) std::remove(P->ckpt_path.c_str());  // the run is complete
   return res;
 }
 
@@ -552,6 +594,7 @@ const char* rsvd_status_str(rsvd_status s) {
     case RSVD_ERR_NO_CONVERGE: return "RSVD_ERR_NO_CONVERGE";
     case RSVD_ERR_TIMEOUT: return "RSVD_ERR_TIMEOUT";
     case RSVD_ERR_UNSUPPORTED: return "RSVD_ERR_UNSUPPORTED";
+    case RSVD_ERR_INTERRUPTED: return "RSVD_ERR_INTERRUPTED";
   }
   return "RSVD_ERR_UNKNOWN";
 }
@@ -753,6 +796,7 @@ rsvd_status rsvd_plan_info(rsvd_plan_t P, rsvd_plan_info_t* o) {
   o->tiles_m = cdiv(P->m, P->mb); o->tiles_n = cdiv(P->n, P->nb); o->n_slots = P->n_slots;
   o->resident = 1; o->workspace_bytes = P->ws_bytes; o->min_cap_bytes = P->ws_bytes; o->seed = P->seed;
   o->q_used = P->q_used;
+  o->resumed_from = P->resumed_from;
   return RSVD_OK;
 }
 
@@ -816,6 +860,15 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
 rsvd_status rsvd_csr_transpose(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                                const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val) {
   return csr_transpose_host(m, n, rowptr, colidx, val, t_rowptr, t_colidx, t_val);
+}
+
+rsvd_status rsvd_plan_set_checkpoint(rsvd_plan_t P, const char* path, int32_t stop_after_step) {
+  if (!P) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_set_checkpoint: NULL plan");
+  if (path && *path && P->auto_q)
+    return fail(RSVD_ERR_UNSUPPORTED, "rsvd_plan_set_checkpoint: not available with automatic q");
+  P->ckpt_path = path ? path : "";
+  P->ckpt_stop_after = stop_after_step;
+  return RSVD_OK;
 }
 
 rsvd_status rsvd_plan_set_profiling(rsvd_plan_t P, int32_t enable) {

@@ -1,5 +1,6 @@
 // Internal launchers shared by the translation units of the library.
 #pragma once
+#include <string>
 
 #include "common.cuh"
 
@@ -124,6 +125,23 @@ rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* col
 // Host CSR of A^T (n rows) from the CSR of A (m rows); stable, deterministic.
 rsvd_status csr_transpose_host(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                                const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val);
+
+// checkpoint.cu -- persistence of the range finder's basis (Section 3.8).
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  int64_t m, n;
+  int32_t k, p, q, r, ldr, prec, dtype, kind;
+  uint64_t seed, fingerprint;
+  int32_t step, pad;
+  int64_t panel_rows;
+  uint64_t panel_bytes, panel_checksum, header_checksum;
+};
+rsvd_status matrix_fingerprint(const rsvd_matrix& A, uint64_t* out, cudaStream_t st);
+// writes header + device panel (h.panel_bytes) to path (via path.tmp and rename)
+rsvd_status ckpt_save(const std::string& path, CkptHeader h, const void* dev_panel, cudaStream_t st);
+// loads the checkpoint at path if it matches `expect`; returns its step (or -1)
+int ckpt_try_load(const std::string& path, const CkptHeader& expect, void* dev_q, void* dev_z, cudaStream_t st);
 
 // stream.cu -- out-of-core A-passes over tiles of a pinned host matrix.
 struct StreamState;

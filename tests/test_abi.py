@@ -146,3 +146,39 @@ def test_csr_plan_rules(lib):
     ob = _lib.RsvdOpts(prec=2, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
     assert lib.rsvd_plan(1000, 500, 10, 5, 1, 1, 0, C.byref(ob), C.byref(h)) == 8
     assert h.value is None
+
+
+def _ckpt_header(step=3, corrupt=False, **kw):
+    """A checkpoint header in the library's layout, with its FNV-1a checksum."""
+    import struct
+    f = dict(m=1000, n=800, k=20, p=10, q=2, r=30, ldr=32, prec=1, dtype=1, kind=0, seed=7, fingerprint=99,
+             step=step, panel_rows=800, panel_bytes=800 * 32 * 4, panel_checksum=0)
+    f.update(kw)
+    fmt = "<8sII" + "qq" + "8i" + "QQ" + "ii" + "q" + "QQQ"
+    def pack(hc):
+        return struct.pack(fmt, b"RSVDCKP1", 1, struct.calcsize(fmt), f["m"], f["n"], f["k"], f["p"], f["q"],
+                           f["r"], f["ldr"], f["prec"], f["dtype"], f["kind"], f["seed"], f["fingerprint"],
+                           f["step"], 0, f["panel_rows"], f["panel_bytes"], f["panel_checksum"], hc)
+    h = 1469598103934665603
+    for b in pack(0):
+        h = ((h ^ b) * 1099511628211) & (2 ** 64 - 1)
+    data = bytearray(pack(h))
+    if corrupt:
+        data[20] ^= 1
+    return bytes(data)
+
+
+def test_checkpoint_header_is_read_and_validated(lib, tmp_path):
+    """Section 3.8 persistence: the header places the basis in the execution plan."""
+    import paper_1907_06470_gb300 as g
+    path = tmp_path / "ck.bin"
+    path.write_bytes(_ckpt_header(step=3))
+    info = g.checkpoint_info(path)
+    assert (info["m"], info["n"], info["k"], info["p"], info["q"], info["r"]) == (1000, 800, 20, 10, 2, 30)
+    assert info["step"] == 3 and info["seed"] == 7 and info["fingerprint"] == 99 and info["panel_rows"] == 800
+    for bad in (_ckpt_header(corrupt=True), _ckpt_header()[:40], b"garbage" * 20):
+        path.write_bytes(bad)
+        with pytest.raises(g.RsvdError):
+            g.checkpoint_info(path)
+    with pytest.raises(g.RsvdError):
+        g.checkpoint_info(tmp_path / "missing.bin")
