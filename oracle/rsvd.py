@@ -74,8 +74,8 @@ def rsvd(A, k: int, p: int, q: int, seed: int, omega_dtype: str = "f64"):
 
 def rsvd_auto_q(A, k: int, p: int, q_max: int, seed: int, tol: float = 1e-3, omega_dtype: str = "f64"):
     """Randomized SVD with the iteration parameter chosen automatically
-    (Section 2.2: the decay of the singular values of A_q is measured with
-    increasing q, and iterations stop when the change falls below a threshold).
+    (Section 2.2 leaves the rule open: q grows while the estimated spectrum
+    still moves by more than a threshold).
 
     Reading taken: after i power iterations the estimates sigma^(i) are the
     singular values of B_i = Q_i^T A (i = 0, 1, ...); the change

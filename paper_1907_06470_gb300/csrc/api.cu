@@ -400,7 +400,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   {
     Span total(pf, RSVD_STAGE_TOTAL, st);
     RSVD_CUDA(cudaMemsetAsync(P->status, 0, sizeof(int), st));
-    {  // step 1: Gaussian test matrix (n x r)
+    if (first_step == 0) {  // step 1: Gaussian test matrix (n x r); X may hold a resumed Z otherwise
       Span sp(pf, RSVD_STAGE_GAUSSIAN, st);
       const bool bf16_panel = prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3 || prec == RSVD_PREC_FP8;
       RSVD_TRY(launch_gaussian(P->seed, n, r, bf16_panel ? kF32HoldingBf16 : P->dtype, 0, X, ldr, st));
