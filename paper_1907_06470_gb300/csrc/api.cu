@@ -423,7 +423,11 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     auto small_svd = [&]() -> rsvd_status {  // step 6 on the current B^T
       Span sp(pf, RSVD_STAGE_SMALL_SVD, st);
       RSVD_TRY(orth_panel<T>(n, r, Bt, ldr, Qb, ldr, P->R, P->orth, st));
-      return jacobi_svd(r, r, P->R, P->sigma, P->UR, P->WR, P->jac, st);
+      // FP32 outputs: off-diagonals below 1e-11 r (relative) change sigma by their
+      // square and the vectors by them over the relative gap, both far below the
+      // FP32 rounding of U, S, V; FP64 outputs take the FP64 test (r eps)
+      return jacobi_svd(r, r, P->R, P->sigma, P->UR, P->WR, P->jac, st,
+                        P->dtype == RSVD_F64 ? 0.0 : 1e-11 * (double)r);
     };
     bool have_final = false;  // Bt, Qb, R and the small SVD already hold the final result
     P->q_used = P->q;

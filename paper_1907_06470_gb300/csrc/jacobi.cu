@@ -69,7 +69,7 @@ constexpr int kClusterCheckSmem = 200 * 1024;
 __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict__ Min,
                                       const double* __restrict__ W0, double* M, double* W, int* rotated,
                                       int* sweeps_out, int* status, double* sigma, double* Uout, double* Wout,
-                                      int check) {
+                                      int check, double tol) {
   __shared__ double red[32];
   extern __shared__ double sh[];  // check pass: M staged (rows x r) + column norms (r); end: sigma_c
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -94,7 +94,6 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
   const double eps = 2.220446049250313e-16;
   const double big = (double)(rows > r ? rows : r);
   const double zero2 = (big * eps) * (big * eps) * fro2;
-  const double tol = (double)r * eps;
   const double tol2 = tol * tol;
   cluster_sync_all();
 
@@ -474,7 +473,7 @@ rsvd_status small_gemm64(int r, const double* A, bool transA, const double* B, d
 }
 
 rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const double* W0, double* sigma, double* U,
-                                  double* W, const JacobiWs& ws, cudaStream_t stream) {
+                                  double* W, const JacobiWs& ws, cudaStream_t stream, double tol) {
   RSVD_CUDA(cudaMemsetAsync(ws.rotated, 0, 3 * kJacobiMaxSweeps * sizeof(int), stream));
   const int rp = r + (r & 1);
   const int npairs = rp / 2;
@@ -516,7 +515,7 @@ rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const doub
       continue;
     }
     RSVD_CUDA(cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, rows, r, Min, W0, ws.M, ws.W, ws.rotated, ws.sweeps,
-                                 ws.status, sigma, U, W, check));
+                                 ws.status, sigma, U, W, check, tol));
     RSVD_CUDA(after_launch());
     return RSVD_OK;
   }
@@ -525,9 +524,11 @@ rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const doub
 }  // namespace
 
 rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double* U, double* W,
-                       const JacobiWs& ws, cudaStream_t stream) {
+                       const JacobiWs& ws, cudaStream_t stream, double tol) {
   if (r <= 0) return RSVD_OK;
-  if (rows != r || r > kF32MaxR || r < 8 || !ws.W32) return launch_cluster_jacobi(rows, r, Mc, nullptr, sigma, U, W, ws, stream);
+  if (!(tol > 0.0)) tol = (double)r * 2.220446049250313e-16;  // r eps: the FP64 stopping test
+  if (rows != r || r > kF32MaxR || r < 8 || !ws.W32)
+    return launch_cluster_jacobi(rows, r, Mc, nullptr, sigma, U, W, ws, stream, tol);
   // Phase 1: FP32 sweeps to FP32 convergence, one CTA, shared memory.
   static bool attr = false;
   if (!attr) {
@@ -557,7 +558,7 @@ rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double*
   // M64 = M W': column-major M64 = Wt' (row-major) times Mc viewed row-major.
   RSVD_TRY(small_gemm64(r, ws.W64, false, Mc, ws.M64, ws.gemm_partial, stream));
   // Phase 3: FP64 sweeps to convergence, starting from the rotated matrix.
-  return launch_cluster_jacobi(rows, r, ws.M64, ws.W64, sigma, U, W, ws, stream);
+  return launch_cluster_jacobi(rows, r, ws.M64, ws.W64, sigma, U, W, ws, stream, tol);
 }
 
 }  // namespace rsvd

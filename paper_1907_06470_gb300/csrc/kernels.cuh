@@ -83,8 +83,9 @@ size_t jacobi_ws_bytes(int64_t rows, int r, bool precondition = true);
 JacobiWs jacobi_ws_carve(Carver& c, int64_t rows, int r, bool precondition = true);
 // Mc column-major rows x r; outputs sigma (r), U (rows x r) and W (r x r)
 // row-major with columns ordered like sigma (descending).
+// tol: relative off-diagonal stopping test |c_ij| <= tol sqrt(c_ii c_jj) (0: r eps, FP64)
 rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double* U, double* W,
-                       const JacobiWs& ws, cudaStream_t stream);
+                       const JacobiWs& ws, cudaStream_t stream, double tol = 0.0);
 
 // lift.cu -- conversions, sign normalisation.
 template <typename Tin, typename Tout>
