@@ -180,18 +180,27 @@ __global__ void __launch_bounds__(256) gaussian_kernel(uint64_t seed, int64_t n,
   }
 }
 
+// Each block first scans the r flags (almost always all zero) and returns at
+// once when no column is dead; otherwise it fills its share of the rows of the
+// dead columns.  Entry (i, k) is element k*M + i of the stream.
 template <typename T>
 __global__ void fill_dead_kernel(int64_t M, int r, const int* __restrict__ dead, T* __restrict__ Q,
                                  int64_t ldq, uint64_t seed, double scale) {
-  const int64_t total = M * r;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e / M);
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < r; k += blockDim.x)
+    if (dead[k]) any = 1;
+  __syncthreads();
+  if (!any) return;
+  for (int k = 0; k < r; ++k) {
     if (!dead[k]) continue;
-    const int64_t i = e - (int64_t)k * M;
-    double a, b;
-    gaussian_pair(seed, (uint64_t)e >> 1, &a, &b);
-    Q[i * ldq + k] = (T)(((e & 1) ? b : a) * scale);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t e = (int64_t)k * M + i;
+      double a, b;
+      gaussian_pair(seed, (uint64_t)e >> 1, &a, &b);
+      Q[i * ldq + k] = (T)(((e & 1) ? b : a) * scale);
+    }
   }
 }
 
@@ -200,8 +209,8 @@ __global__ void fill_dead_kernel(int64_t M, int r, const int* __restrict__ dead,
 rsvd_status fill_dead_columns(int64_t M, int r, const int* dead, void* Q, int64_t ldq, int dtype,
                               uint64_t seed, cudaStream_t stream) {
   if (M * r == 0) return RSVD_OK;
-  int64_t blocks = cdiv(M * r, 256);
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  int64_t blocks = cdiv(M, 256);
+  if (blocks > 152 * 4) blocks = 152 * 4;
   const double scale = 1.0 / sqrt((double)M);
   if (dtype == RSVD_F64)
     fill_dead_kernel<double><<<(int)blocks, 256, 0, stream>>>(M, r, dead, static_cast<double*>(Q), ldq, seed, scale);

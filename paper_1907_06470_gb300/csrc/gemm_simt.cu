@@ -12,6 +12,8 @@
 // Tiling: 128 x 128 output tile per 256-thread CTA, 8 x 8 outputs per thread
 // as two 4-wide halves in each direction (conflict-free shared-memory
 // broadcasts), K step 8, double-buffered shared memory.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -150,6 +152,39 @@ reduce_partials_kernel(int64_t M, int64_t N, int nsplit, const T* __restrict__ P
   }
 }
 
+// The same sum with 4 consecutive columns per thread (16-byte loads) and the
+// split loop unrolled so the partial loads are in flight together; the order
+// of the additions (split 0, 1, 2, ...) is the same as above.
+__global__ void reduce_partials_vec4_kernel(int64_t M, int64_t N4, int nsplit, const float4* __restrict__ P,
+                                            int64_t ldp4, int64_t pstride4, float4* __restrict__ out, int64_t ldo4,
+                                            int accumulate) {
+  const int64_t total = M * N4;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / N4, j = e - i * N4;
+    const float4* src = P + i * ldp4 + j;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    int z = 0;
+    for (; z + 4 <= nsplit; z += 4) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = src[(int64_t)(z + u) * pstride4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { s.x += v[u].x; s.y += v[u].y; s.z += v[u].z; s.w += v[u].w; }
+    }
+    for (; z < nsplit; ++z) {
+      const float4 v = src[(int64_t)z * pstride4];
+      s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+    }
+    float4* dst = out + i * ldo4 + j;
+    if (accumulate) {
+      const float4 d = *dst;
+      s.x += d.x; s.y += d.y; s.z += d.z; s.w += d.w;
+    }
+    *dst = s;
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -220,6 +255,17 @@ template <typename T>
 rsvd_status reduce_partials(int64_t M, int64_t N, int nsplit, const T* P, int64_t ldp, int64_t pstride, T* out,
                             int64_t ldo, bool accumulate, cudaStream_t stream) {
   if (M * N == 0) return RSVD_OK;
+  if constexpr (std::is_same<T, float>::value) {
+    if (N % 4 == 0 && ldp % 4 == 0 && pstride % 4 == 0 && ldo % 4 == 0 && aligned16(P) && aligned16(out)) {
+      int64_t blocks = cdiv(M * (N / 4), 256);
+      if (blocks > 152 * 8) blocks = 152 * 8;
+      reduce_partials_vec4_kernel<<<(int)blocks, 256, 0, stream>>>(
+          M, N / 4, nsplit, reinterpret_cast<const float4*>(P), ldp / 4, pstride / 4, reinterpret_cast<float4*>(out),
+          ldo / 4, accumulate ? 1 : 0);
+      RSVD_CUDA(after_launch());
+      return RSVD_OK;
+    }
+  }
   int64_t blocks = cdiv(M * N, 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
   reduce_partials_kernel<T><<<(int)blocks, 256, 0, stream>>>(M, N, nsplit, P, ldp, pstride, out, ldo,

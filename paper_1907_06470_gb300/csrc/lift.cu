@@ -41,23 +41,26 @@ inline int64_t sign_chunk(int64_t m) {
   return c > 64 ? c : 64;
 }
 
-// Per chunk of rows and column j: the first entry of largest
-// magnitude (value and magnitude).
+// Per chunk of rows and column j: the first entry of largest magnitude (value
+// and magnitude), compared in the panel's own type (FP64 arithmetic is costly
+// on this GPU).
 template <typename T>
 __global__ void colmax_kernel(int64_t m, int k, int64_t chunk, const T* __restrict__ U, int64_t ldu,
-                              double* __restrict__ part) {
+                              T* __restrict__ part) {
   const int j = threadIdx.x + blockIdx.y * blockDim.x;
   if (j >= k) return;
   const int64_t r0 = (int64_t)blockIdx.x * chunk;
   const int64_t r1 = min(m, r0 + chunk);
-  double best = -1.0, val = 0.0;
+  T best = T(-1), val = T(0);
   for (int64_t i0 = r0; i0 < r1; i0 += 8) {
-    double x[8];
+    T x[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) x[t] = i0 + t < r1 ? (double)U[(i0 + t) * ldu + j] : 0.0;
+    for (int t = 0; t < 8; ++t) x[t] = i0 + t < r1 ? U[(i0 + t) * ldu + j] : T(0);
 #pragma unroll
-    for (int t = 0; t < 8; ++t)
-      if (i0 + t < r1 && fabs(x[t]) > best) { best = fabs(x[t]); val = x[t]; }
+    for (int t = 0; t < 8; ++t) {
+      const T ax = x[t] < T(0) ? -x[t] : x[t];
+      if (i0 + t < r1 && ax > best) { best = ax; val = x[t]; }
+    }
   }
   part[((int64_t)blockIdx.x * k + j) * 2 + 0] = best;
   part[((int64_t)blockIdx.x * k + j) * 2 + 1] = val;
@@ -65,42 +68,40 @@ __global__ void colmax_kernel(int64_t m, int k, int64_t chunk, const T* __restri
 
 // One warp per column: the chunk maxima combined so that the largest
 // magnitude wins and, among equal magnitudes, the lowest chunk (row) does.
-__global__ void choose_flip_kernel(int k, int nchunks, const double* __restrict__ part,
-                                   int* __restrict__ flip) {
+template <typename T>
+__global__ void choose_flip_kernel(int k, int nchunks, const T* __restrict__ part, int* __restrict__ flip) {
   const int lane = threadIdx.x & 31;
   const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int j = w0; j < k; j += nw) {
-    double best = -1.0, val = 0.0;
+    T best = T(-1), val = T(0);
     int idx = 0x7fffffff;
     for (int c = lane; c < nchunks; c += 32) {
-      const double b = part[((int64_t)c * k + j) * 2];
+      const T b = part[((int64_t)c * k + j) * 2];
       if (b > best) { best = b; val = part[((int64_t)c * k + j) * 2 + 1]; idx = c; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double b2 = __shfl_xor_sync(0xffffffffu, best, o);
-      const double v2 = __shfl_xor_sync(0xffffffffu, val, o);
+      const T b2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const T v2 = __shfl_xor_sync(0xffffffffu, val, o);
       const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
       if (b2 > best || (b2 == best && i2 < idx)) { best = b2; val = v2; idx = i2; }
     }
-    if (lane == 0) flip[j] = val < 0.0 ? 1 : 0;
+    if (lane == 0) flip[j] = val < T(0) ? 1 : 0;
   }
 }
 
+// One warp per row of U (then of V): lanes over the columns, negating those
+// whose pair was chosen for a flip.
 template <typename T>
 __global__ void flip_kernel(int64_t m, int64_t n, int k, const int* __restrict__ flip,
                             T* __restrict__ U, int64_t ldu, T* __restrict__ V, int64_t ldv) {
-  const int64_t tu = m * k, tv = n * k;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tu + tv;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    if (e < tu) {
-      const int64_t i = e / k; const int j = (int)(e - i * k);
-      if (flip[j]) U[i * ldu + j] = -U[i * ldu + j];
-    } else {
-      const int64_t f = e - tu;
-      const int64_t i = f / k; const int j = (int)(f - i * k);
-      if (flip[j]) V[i * ldv + j] = -V[i * ldv + j];
-    }
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w0; row < m + n; row += nw) {
+    T* p = row < m ? U + row * ldu : V + (row - m) * ldv;
+    for (int j = lane; j < k; j += 32)
+      if (flip[j]) p[j] = -p[j];
   }
 }
 
@@ -151,16 +152,16 @@ rsvd_status normalise_signs(int64_t m, int64_t n, int k, T* U, int64_t ldu, T* V
     return fail(RSVD_ERR_INVALID_ARG, "normalise_signs: scratch too small");
   const int64_t chunk = sign_chunk(m);
   const int64_t nchunks = cdiv(m, chunk);
-  double* part = static_cast<double*>(scratch);
-  int* flip = reinterpret_cast<int*>(part + nchunks * k * 2);
+  T* part = static_cast<T*>(scratch);
+  int* flip = reinterpret_cast<int*>(static_cast<double*>(scratch) + nchunks * k * 2);
   const int tpb = k < 128 ? 32 * (int)cdiv(k, 32) : 128;
   colmax_kernel<T><<<dim3((unsigned)nchunks, (unsigned)cdiv(k, tpb)), tpb, 0, stream>>>(m, k, chunk, U, ldu,
                                                                                         part);
   RSVD_CUDA(after_launch());
-  choose_flip_kernel<<<(int)cdiv((int64_t)k * 32, 256), 256, 0, stream>>>(k, (int)nchunks, part, flip);
+  choose_flip_kernel<T><<<(int)cdiv((int64_t)k * 32, 256), 256, 0, stream>>>(k, (int)nchunks, part, flip);
   RSVD_CUDA(after_launch());
-  int64_t blocks = cdiv((m + n) * k, 256);
-  if (blocks > 152 * 4) blocks = 152 * 4;
+  int64_t blocks = cdiv((m + n) * 32, 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
   flip_kernel<T><<<(int)blocks, 256, 0, stream>>>(m, n, k, flip, U, ldu, V, ldv);
   RSVD_CUDA(after_launch());
   return RSVD_OK;
