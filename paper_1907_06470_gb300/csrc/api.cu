@@ -217,6 +217,7 @@ struct rsvd_plan_s {
   StreamState* ss = nullptr;       // out-of-core state (created on the first streamed run)
   bool streaming = false;          // the current run streams A from the host
   int kind = RSVD_DENSE;           // rsvd_kind the plan runs on
+  bool tc_orth = false;            // range-finder Grams / panel products on the tensor cores
   Fp8Source f8;                    // FP8 plans: E4M3 codes of A and tile scales (in the workspace)
   unsigned* f8_amax = nullptr;
   void* csr_dev = nullptr;         // device copies of a CSR A and/or its transpose, SpMM workspace
@@ -297,7 +298,10 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   P->apass_ws_bytes = a0 > a1 ? a0 : a1;
   if (a2 > P->apass_ws_bytes) P->apass_ws_bytes = a2;
   P->apass_ws = c.take<char>(P->apass_ws_bytes);
-  P->orth = orth_ws_carve(c, mx, P->r, P->dtype);
+  // the range finder of the BF16 / FP8 paths orthonormalises on the tensor cores
+  P->tc_orth = dense && P->dtype == RSVD_F32 &&
+               (P->prec == RSVD_PREC_BF16 || P->prec == RSVD_PREC_BF16X3 || P->prec == RSVD_PREC_FP8);
+  P->orth = orth_ws_carve(c, mx, P->r, P->dtype, P->tc_orth);
   P->jac = jacobi_ws_carve(c, P->r, P->r);
   P->R = c.take<double>((size_t)P->r * P->r);
   P->sigma = c.take<double>((size_t)P->r);
@@ -366,7 +370,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   };
   auto orth = [&](int64_t M, const T* Yin, T* Qout) -> rsvd_status {
     Span sp(pf, RSVD_STAGE_ORTH, st);
-    return orth_panel<T>(M, r, Yin, ldr, Qout, ldr, nullptr, P->orth, st);
+    return orth_panel<T>(M, r, Yin, ldr, Qout, ldr, nullptr, P->orth, st, P->tc_orth);
   };
   // Section 3.8 persistence: the header of each checkpoint places its basis in
   // the execution plan; a matching checkpoint lets the run skip its steps.

@@ -497,7 +497,7 @@ TcShape tc_shape(int64_t m, int64_t n, int r, int trans) {
   const int64_t sms = num_sms();
   double best = 1e300;
   int bestS = 1;
-  for (int S = 1; S <= 64 && S <= s.ksteps; ++S) {
+  for (int S = 1; S <= 256 && S <= s.ksteps; ++S) {
     const int64_t per = cdiv(s.ksteps, S);
     const int64_t used = cdiv(s.ksteps, per);
     const double rounds = (double)cdiv(s.mtiles * used, sms);

@@ -53,13 +53,19 @@ struct OrthWs {
   void* tmp = nullptr;        // M x r panel (first-sweep result)
   int64_t ld_tmp = 0;
   int* status = nullptr;      // device status word
+  void* tc_ws = nullptr;      // tensor-core Gram / panel product workspace (tc mode)
+  size_t tc_ws_bytes = 0;
+  float* gram32 = nullptr;    // r x r FP32 Gram from the tensor cores (tc mode)
 };
-size_t orth_ws_bytes(int64_t M, int r, int dtype);
-OrthWs orth_ws_carve(Carver& c, int64_t M, int r, int dtype);
+// tc: FP32 panels may take their Grams and panel products on the tensor cores
+// (split BF16, about 2e-5 relative) -- for bases whose only job is to span
+// the sketch (the range finder of the BF16 / FP8 paths)
+size_t orth_ws_bytes(int64_t M, int r, int dtype, bool tc = false);
+OrthWs orth_ws_carve(Carver& c, int64_t M, int r, int dtype, bool tc = false);
 
 template <typename T>
 rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t ldq, double* R,
-                       const OrthWs& ws, cudaStream_t stream);
+                       const OrthWs& ws, cudaStream_t stream, bool tc = false);
 
 // jacobi.cu -- Section 2.1 step 6 core.
 struct JacobiWs {

@@ -21,6 +21,8 @@
 // Gram accumulation: products are summed in the panel's type over chunks of
 // 256 rows (more for panels over 2^19 rows; the SIMT GEMM, one partial per
 // chunk) and the chunk partials are added in FP64 in a fixed order.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -469,7 +471,24 @@ rsvd_status chol_inv(int r, const OrthWs& ws, TF* L, int* dead, double tau, cuda
 
 }  // namespace
 
-size_t orth_ws_bytes(int64_t M, int r, int dtype) {
+namespace {
+size_t tc_orth_ws(int64_t M, int r) {
+  const size_t g = tc_apass_ws_bytes(M, r, r, 1, RSVD_PREC_BF16X3, 0, 0);
+  const size_t p = tc_apass_ws_bytes(M, r, r, 0, RSVD_PREC_BF16X3, 0, 0);
+  return g > p ? g : p;
+}
+bool tc_orth_ok(int r, int dtype, bool tc) { return tc && dtype == RSVD_F32 && r <= 256; }
+
+// G = widened lower triangle of the FP32 Gram, mirrored
+__global__ void widen_gram_kernel(int r, const float* __restrict__ g32, double* __restrict__ G) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+    const int i = e / r, j = e % r;
+    G[e] = (double)(i >= j ? g32[i * r + j] : g32[j * r + i]);
+  }
+}
+}  // namespace
+
+size_t orth_ws_bytes(int64_t M, int r, int dtype, bool tc) {
   Sizer s;
   const size_t esz = dtype == RSVD_F64 ? 8 : 4;
   s.take<double>((size_t)r * r * 5);
@@ -478,10 +497,14 @@ size_t orth_ws_bytes(int64_t M, int r, int dtype) {
   s.take<char>((size_t)gram_chunks(M) * r * r * esz);
   s.take<char>((size_t)M * round_up(r, 4) * esz);
   s.take<int>(4);
+  if (tc_orth_ok(r, dtype, tc)) {
+    s.take<float>((size_t)r * r);
+    s.take<char>(tc_orth_ws(M, r));
+  }
   return s.used + 256;
 }
 
-OrthWs orth_ws_carve(Carver& c, int64_t M, int r, int dtype) {
+OrthWs orth_ws_carve(Carver& c, int64_t M, int r, int dtype, bool tc) {
   OrthWs w;
   const size_t esz = dtype == RSVD_F64 ? 8 : 4;
   double* base = c.take<double>((size_t)r * r * 5);
@@ -497,14 +520,62 @@ OrthWs orth_ws_carve(Carver& c, int64_t M, int r, int dtype) {
   w.ld_tmp = round_up(r, 4);
   w.tmp = c.take<char>((size_t)M * w.ld_tmp * esz);
   w.status = c.take<int>(4);
+  if (tc_orth_ok(r, dtype, tc)) {
+    w.gram32 = c.take<float>((size_t)r * r);
+    w.tc_ws_bytes = tc_orth_ws(M, r);
+    w.tc_ws = c.take<char>(w.tc_ws_bytes);
+  }
   return w;
+}
+
+// Tensor-core Gram G = Y^T Y (split BF16, FP32 accumulation), widened to FP64.
+rsvd_status gram_tc(int64_t M, int r, const float* Y, int64_t ldy, const OrthWs& ws, cudaStream_t stream) {
+  rsvd_matrix A = {};
+  A.kind = RSVD_DENSE; A.dtype = RSVD_F32; A.location = RSVD_ON_DEVICE;
+  A.m = M; A.n = r; A.data = Y; A.ld = ldy;
+  RSVD_TRY(tc_apass_from_f32(A, 1, RSVD_PREC_BF16X3, r, Y, ldy, ws.gram32, r, 0, 0, ws.tc_ws, ws.tc_ws_bytes,
+                             ws.status, stream));
+  widen_gram_kernel<<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r, ws.gram32, ws.G);
+  RSVD_CUDA(after_launch());
+  return RSVD_OK;
+}
+
+// Tensor-core panel product Q = Y Rinv (split BF16).
+rsvd_status panel_times_tc(int64_t M, int r, const float* Y, int64_t ldy, const float* Rt, float* Q, int64_t ldq,
+                           const OrthWs& ws, cudaStream_t stream) {
+  rsvd_matrix A = {};
+  A.kind = RSVD_DENSE; A.dtype = RSVD_F32; A.location = RSVD_ON_DEVICE;
+  A.m = M; A.n = r; A.data = Y; A.ld = ldy;
+  return tc_apass_from_f32(A, 0, RSVD_PREC_BF16X3, r, Rt, r, Q, ldq, 0, 0, ws.tc_ws, ws.tc_ws_bytes, ws.status,
+                           stream);
 }
 
 template <typename T>
 rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t ldq, double* R,
-                       const OrthWs& ws, cudaStream_t stream) {
+                       const OrthWs& ws, cudaStream_t stream, bool tc) {
   T* Q1 = static_cast<T*>(ws.tmp);
   const T* Rt = static_cast<const T*>(ws.Rinv_t);
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc && ws.tc_ws && ldy % 4 == 0 && ldq % 4 == 0 && aligned16(Y) && aligned16(Q)) {
+      // the same two sweeps with the Grams and panel products on the tensor cores
+      RSVD_TRY(gram_tc(M, r, Y, ldy, ws, stream));
+      float* L1 = reinterpret_cast<float*>(ws.L1);
+      RSVD_TRY((chol_inv<float, float>(r, ws, L1, ws.dead1, pivot_tau<float>(), stream)));
+      RSVD_TRY(panel_times_tc(M, r, Y, ldy, Rt, Q1, ws.ld_tmp, ws, stream));
+      RSVD_TRY(fill_dead_columns(M, r, ws.dead1, Q1, ws.ld_tmp, RSVD_F32, kDeadFillSeed, stream));
+      RSVD_TRY(gram_tc(M, r, Q1, ws.ld_tmp, ws, stream));
+      float* L2 = reinterpret_cast<float*>(ws.L2);
+      RSVD_TRY((chol_inv<float, float>(r, ws, L2, ws.dead2, pivot_tau<float>(), stream)));
+      check_dead_kernel<<<1, 256, 0, stream>>>(r, ws.dead2, ws.status);
+      RSVD_CUDA(after_launch());
+      RSVD_TRY(panel_times_tc(M, r, Q1, ws.ld_tmp, Rt, Q, ldq, ws, stream));
+      if (R) {
+        rprod_kernel<float, float><<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r, L1, ws.dead1, L2, R);
+        RSVD_CUDA(after_launch());
+      }
+      return RSVD_OK;
+    }
+  }
   // sweep 1 (dead pivots: the panel is rank deficient to the Gram's accuracy;
   // their columns of Q1 are replaced by unit random directions)
   RSVD_TRY(gram<T>(M, r, Y, ldy, ws, stream));
@@ -530,8 +601,8 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
 }
 
 template rsvd_status orth_panel<float>(int64_t, int, const float*, int64_t, float*, int64_t, double*,
-                                       const OrthWs&, cudaStream_t);
+                                       const OrthWs&, cudaStream_t, bool);
 template rsvd_status orth_panel<double>(int64_t, int, const double*, int64_t, double*, int64_t,
-                                        double*, const OrthWs&, cudaStream_t);
+                                        double*, const OrthWs&, cudaStream_t, bool);
 
 }  // namespace rsvd
