@@ -217,7 +217,8 @@ struct rsvd_plan_s {
   StreamState* ss = nullptr;       // out-of-core state (created on the first streamed run)
   bool streaming = false;          // the current run streams A from the host
   int kind = RSVD_DENSE;           // rsvd_kind the plan runs on
-  bool tc_orth = false;            // range-finder Grams / panel products on the tensor cores
+  bool tc_orth_all = false;        // range-finder Grams / panel products on the tensor cores
+  bool tc_orth_inner = false;      // the same except for the final Q
   Fp8Source f8;                    // FP8 plans: E4M3 codes of A and tile scales (in the workspace)
   unsigned* f8_amax = nullptr;
   void* csr_dev = nullptr;         // device copies of a CSR A and/or its transpose, SpMM workspace
@@ -298,10 +299,14 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   P->apass_ws_bytes = a0 > a1 ? a0 : a1;
   if (a2 > P->apass_ws_bytes) P->apass_ws_bytes = a2;
   P->apass_ws = c.take<char>(P->apass_ws_bytes);
-  // the range finder of the BF16 / FP8 paths orthonormalises on the tensor cores
-  P->tc_orth = dense && P->dtype == RSVD_F32 &&
-               (P->prec == RSVD_PREC_BF16 || P->prec == RSVD_PREC_BF16X3 || P->prec == RSVD_PREC_FP8);
-  P->orth = orth_ws_carve(c, mx, P->r, P->dtype, P->tc_orth);
+  // Range-finder bases only have to span the sketch: FP32 data orthonormalises
+  // them on the tensor cores (split BF16) -- every basis for the BF16 / FP8
+  // paths, every basis but the final Q (whose orthonormality enters B = Q^T A)
+  // for the FP32 paths
+  P->tc_orth_all = P->dtype == RSVD_F32 &&
+                   (P->prec == RSVD_PREC_BF16 || P->prec == RSVD_PREC_BF16X3 || P->prec == RSVD_PREC_FP8);
+  P->tc_orth_inner = P->dtype == RSVD_F32;
+  P->orth = orth_ws_carve(c, mx, P->r, P->dtype, P->tc_orth_inner);
   P->jac = jacobi_ws_carve(c, P->r, P->r);
   P->R = c.take<double>((size_t)P->r * P->r);
   P->sigma = c.take<double>((size_t)P->r);
@@ -368,9 +373,10 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     return apass_dense(A, trans, pr, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes,
                        P->status, st);
   };
-  auto orth = [&](int64_t M, const T* Yin, T* Qout) -> rsvd_status {
+  auto orth = [&](int64_t M, const T* Yin, T* Qout, bool final_q) -> rsvd_status {
     Span sp(pf, RSVD_STAGE_ORTH, st);
-    return orth_panel<T>(M, r, Yin, ldr, Qout, ldr, nullptr, P->orth, st, P->tc_orth);
+    const bool tc = P->tc_orth_all || (P->tc_orth_inner && !final_q);
+    return orth_panel<T>(M, r, Yin, ldr, Qout, ldr, nullptr, P->orth, st, tc);
   };
   // Section 3.8 persistence: the header of each checkpoint places its basis in
   // the execution plan; a matching checkpoint lets the run skip its steps.
@@ -421,7 +427,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     // a checkpoint of this plan and this A lets the run resume later
     if (first_step == 0) {
       RSVD_TRY(apass(0, prec, X, Y));
-      RSVD_TRY(orth(m, Y, Q));
+      RSVD_TRY(orth(m, Y, Q, P->q == 0));
       RSVD_TRY(checkpoint(0));
     }
     auto small_svd = [&]() -> rsvd_status {  // step 6 on the current B^T
@@ -441,10 +447,10 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
       for (int s = first_step > 0 ? first_step : 1; s <= 2 * P->q; ++s) {
         if (s & 1) {
           RSVD_TRY(apass(1, prec, Q, Bt));
-          RSVD_TRY(orth(n, Bt, X));
+          RSVD_TRY(orth(n, Bt, X, false));
         } else {
           RSVD_TRY(apass(0, prec, X, Y));
-          RSVD_TRY(orth(m, Y, Q));
+          RSVD_TRY(orth(m, Y, Q, s == 2 * P->q));
         }
         RSVD_TRY(checkpoint(s));
       }
@@ -468,7 +474,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
         if (it == P->q) break;
         RSVD_CUDA(cudaMemcpyAsync(P->sigma_prev, P->sigma, (size_t)r * sizeof(double), cudaMemcpyDeviceToDevice, st));
         RSVD_TRY(apass(0, prec, Qb, Y));
-        RSVD_TRY(orth(m, Y, Q));
+        RSVD_TRY(orth(m, Y, Q, true));  // any Q may turn out to be the final one
       }
       P->q_used = it;
       have_final = final_prec == prec;  // else recompute B^T in the refinement precision

@@ -536,11 +536,11 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
                          cudaStream_t stream, bool accumulate) {
   const bool split = prec == RSVD_PREC_BF16X3;
   const bool src8 = src.f8 != nullptr;
-  if (r < 1 || r > 256) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: r must be in [1, 256]");
+  if (r < 1 || r > 512) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: r must be in [1, 512]");
   if (split && src8) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: no split mode for the FP8 source");
-  if (split && round_up(r, 16) > kSplitMaxNP) {
-    // the split-mode operand ring does not fit shared memory for this width:
-    // two passes over column halves of the panel (A is read twice)
+  if (round_up(r, 16) > (split ? kSplitMaxNP : 256)) {
+    // wider than one accumulator (256 columns) or than the split-mode operand
+    // ring fits: passes over column halves of the panel (A is read per half)
     const int h = (int)round_up(cdiv(r, 2), 16);
     RSVD_TRY(tc_apass_run(src, m, n, trans, prec, h, X, ldx, Y, ldy, ws, ws_bytes, status, stream, accumulate));
     return tc_apass_run(src, m, n, trans, prec, r - h, X + h, ldx, Y + h, ldy, ws, ws_bytes, status, stream,

@@ -477,7 +477,7 @@ size_t tc_orth_ws(int64_t M, int r) {
   const size_t p = tc_apass_ws_bytes(M, r, r, 0, RSVD_PREC_BF16X3, 0, 0);
   return g > p ? g : p;
 }
-bool tc_orth_ok(int r, int dtype, bool tc) { return tc && dtype == RSVD_F32 && r <= 256; }
+bool tc_orth_ok(int r, int dtype, bool tc) { return tc && dtype == RSVD_F32 && r <= 512; }
 
 // G = widened lower triangle of the FP32 Gram, mirrored
 __global__ void widen_gram_kernel(int r, const float* __restrict__ g32, double* __restrict__ G) {
