@@ -56,6 +56,8 @@ struct OrthWs {
   void* tc_ws = nullptr;      // tensor-core Gram / panel product workspace (tc mode)
   size_t tc_ws_bytes = 0;
   float* gram32 = nullptr;    // r x r FP32 Gram from the tensor cores (tc mode)
+  void* chol_scratch = nullptr;  // factorisation matrices when r is too large for shared memory
+  size_t chol_scratch_bytes = 0;
 };
 // tc: FP32 panels may take their Grams and panel products on the tensor cores
 // (split BF16, about 2e-5 relative) -- for bases whose only job is to span

@@ -158,26 +158,39 @@ constexpr int kCholB = 16;
 constexpr int kFusedThreads = 512;
 constexpr size_t kFusedSmemMax = 220 * 1024;
 
+// bytes of the matrices the fused kernel keeps in shared or global memory
 template <typename TF, typename TI>
-__host__ __device__ inline size_t fused_smem_bytes(int r) {
+__host__ __device__ inline size_t fused_big_bytes(int r) {
   const size_t lda = (size_t)r + 1;
   const int nb = (r + kCholB - 1) / kCholB;
-  return (size_t)r * lda * sizeof(TF) + 2 * (size_t)r * sizeof(TF) + (size_t)r * lda * sizeof(TI) +
-         (size_t)nb * kCholB * kCholB * sizeof(TI) + 64;
+  return (size_t)r * lda * sizeof(TF) + (size_t)r * lda * sizeof(TI) + (size_t)nb * kCholB * kCholB * sizeof(TI) + 64;
+}
+
+template <typename TF>
+__host__ __device__ inline size_t fused_small_bytes(int r) {
+  return ((2 * (size_t)r * sizeof(TF) + 15) & ~(size_t)15);
+}
+
+template <typename TF, typename TI>
+__host__ __device__ inline size_t fused_smem_bytes(int r) {
+  return fused_small_bytes<TF>(r) + fused_big_bytes<TF, TI>(r);
 }
 
 template <typename TF, typename TI>
 __global__ void __launch_bounds__(kFusedThreads)
 chol_inv_fused_kernel(int r, const double* __restrict__ G, TF* __restrict__ Lout, int* __restrict__ dead,
-                      double tau, int* status, TI* __restrict__ Rinv_t) {
+                      double tau, int* status, TI* __restrict__ Rinv_t, unsigned char* gscratch) {
   extern __shared__ __align__(16) unsigned char fsm[];
   constexpr int NB = kCholB;
   const int lda = r + 1;
   const int nb = (r + NB - 1) / NB;
-  TF* A = reinterpret_cast<TF*>(fsm);            // r x lda, lower triangle used
-  TF* gdiag = A + (size_t)r * lda;               // tau * G_kk
+  // Working matrices in shared memory, or -- for r too large for it -- in a
+  // global scratch (L2 resident at these sizes); the algorithm is the same.
+  TF* gdiag = reinterpret_cast<TF*>(fsm);        // tau * G_kk
   TF* invs = gdiag + r;                          // 1 / L_kk (0 for a dead pivot)
-  TI* X = reinterpret_cast<TI*>(invs + r);       // r x lda: L^-1
+  unsigned char* big = gscratch ? gscratch : fsm + ((2 * (size_t)r * sizeof(TF) + 15) & ~(size_t)15);
+  TF* A = reinterpret_cast<TF*>(big);            // r x lda, lower triangle used
+  TI* X = reinterpret_cast<TI*>(A + (size_t)r * lda);  // r x lda: L^-1
   TI* S = X + (size_t)r * lda;                   // nb blocks of NB^2 scratch
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
@@ -437,15 +450,17 @@ struct SecondSweep<float> { using type = float; };
 template <typename TF, typename T>
 rsvd_status chol_inv(int r, const OrthWs& ws, TF* L, int* dead, double tau, cudaStream_t stream) {
   const size_t fused = fused_smem_bytes<TF, T>(r);
-  if (fused <= kFusedSmemMax) {
+  const bool in_smem = fused <= kFusedSmemMax;
+  if (in_smem || (ws.chol_scratch && ws.chol_scratch_bytes >= fused_big_bytes<TF, T>(r))) {
     static bool fattr = false;
     if (!fattr) {
       RSVD_CUDA(cudaFuncSetAttribute(chol_inv_fused_kernel<TF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kFusedSmemMax));
       fattr = true;
     }
-    chol_inv_fused_kernel<TF, T><<<1, kFusedThreads, fused, stream>>>(r, ws.G, L, dead, tau, ws.status,
-                                                                      static_cast<T*>(ws.Rinv_t));
+    chol_inv_fused_kernel<TF, T><<<1, kFusedThreads, in_smem ? fused : fused_small_bytes<TF>(r), stream>>>(
+        r, ws.G, L, dead, tau, ws.status, static_cast<T*>(ws.Rinv_t),
+        in_smem ? nullptr : static_cast<unsigned char*>(ws.chol_scratch));
     RSVD_CUDA(after_launch());
     return RSVD_OK;
   }
@@ -472,6 +487,14 @@ rsvd_status chol_inv(int r, const OrthWs& ws, TF* L, int* dead, double tau, cuda
 }  // namespace
 
 namespace {
+// global scratch for the fused factorisation when r is too large for shared memory
+size_t chol_scratch_bytes(int r) {
+  if (fused_smem_bytes<double, float>(r) <= kFusedSmemMax && fused_smem_bytes<float, float>(r) <= kFusedSmemMax &&
+      fused_smem_bytes<double, double>(r) <= kFusedSmemMax)
+    return 0;
+  return fused_big_bytes<double, double>(r);
+}
+
 size_t tc_orth_ws(int64_t M, int r) {
   const size_t g = tc_apass_ws_bytes(M, r, r, 1, RSVD_PREC_BF16X3, 0, 0);
   const size_t p = tc_apass_ws_bytes(M, r, r, 0, RSVD_PREC_BF16X3, 0, 0);
@@ -501,6 +524,7 @@ size_t orth_ws_bytes(int64_t M, int r, int dtype, bool tc) {
     s.take<float>((size_t)r * r);
     s.take<char>(tc_orth_ws(M, r));
   }
+  s.take<char>(chol_scratch_bytes(r));
   return s.used + 256;
 }
 
@@ -525,6 +549,8 @@ OrthWs orth_ws_carve(Carver& c, int64_t M, int r, int dtype, bool tc) {
     w.tc_ws_bytes = tc_orth_ws(M, r);
     w.tc_ws = c.take<char>(w.tc_ws_bytes);
   }
+  w.chol_scratch_bytes = chol_scratch_bytes(r);
+  w.chol_scratch = w.chol_scratch_bytes ? c.take<char>(w.chol_scratch_bytes) : nullptr;
   return w;
 }
 
