@@ -69,7 +69,7 @@ constexpr int kClusterCheckSmem = 200 * 1024;
 __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict__ Min,
                                       const double* __restrict__ W0, double* M, double* W, int* rotated,
                                       int* sweeps_out, int* status, double* sigma, double* Uout, double* Wout,
-                                      int check, double tol) {
+                                      int check, double tol, int max_sweeps) {
   __shared__ double red[32];
   extern __shared__ double sh[];  // check pass: M staged (rows x r) + column norms (r); end: sigma_c
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -100,7 +100,11 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
   int sweep = 0;
   bool converged = false;
   const int s = blockIdx.x * warps + warp;  // this warp's pair slot
-  for (; sweep < kJacobiMaxSweeps; ++sweep) {
+  for (; sweep < max_sweeps; ++sweep) {
+    // this warp's rotations in the sweep (one flag and one maximum per warp,
+    // published before the barrier that ends the sweep's last round)
+    bool my_rot = false;
+    float my_mrel = 0.f;
     for (int round = 0; round < rp - 1; ++round) {
       if (s < npairs) {
         int p = rr_column(s, round, rp), q = rr_column(rp - 1 - s, round, rp);
@@ -145,9 +149,8 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
           b = warp_sum_d(b);
           g = warp_sum_d(g);
           if (g * g > tol2 * (a * b) && a > zero2 && b > zero2) {
-            if (lane == 0)
-              atomicMax(&rotated[2 * kJacobiMaxSweeps + sweep],
-                        __float_as_int(fabsf((float)g) * rsqrtf((float)a) * rsqrtf((float)b)));
+            my_rot = true;
+            my_mrel = fmaxf(my_mrel, fabsf((float)g) * rsqrtf((float)a) * rsqrtf((float)b));
             double c, sn;
             jacobi_rotation(a, b, g, c, sn);
             if (in_regs) {
@@ -182,9 +185,12 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
                 __stcg(&wq[i], sn * u + c * v);
               }
             }
-            if (lane == 0) __stcg(&rotated[sweep], 1);
           }
         }
+      }
+      if (round == rp - 2 && lane == 0 && my_rot) {
+        atomicMax(&rotated[2 * kJacobiMaxSweeps + sweep], __float_as_int(my_mrel));
+        __stcg(&rotated[sweep], 1);
       }
       cluster_sync_all();
     }
@@ -235,6 +241,10 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
     }
   }
   if (blockIdx.x != 0) return;
+  if (max_sweeps == 0) {
+    converged = true;  // finish only: the columns were orthogonalised before (FP32 phase)
+    sweep = -1;
+  }
   if (!converged) dev_set_status(status, DEV_NO_CONVERGE);
   if (tid == 0) *sweeps_out = sweep + (converged ? 1 : 0);
   // column norms, stable descending order, normalised outputs (sh: sigma_c for c < r)
@@ -321,6 +331,10 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
     __syncthreads();
     if (tid == 0) { s_rot = 0; s_maxrel = 0; }
     __syncthreads();
+    // whether this thread's pairs rotated in the sweep, and the largest relative
+    // off-diagonal they rotated: kept in registers, reduced once per sweep
+    bool my_rot = false;
+    float my_mrel = 0.f;
     for (int round = 0; round < rp - 1; ++round) {
       // every half-warp takes the same number of iterations (shuffles need the full warp)
       for (int s0 = 0; s0 < npairs; s0 += nhw) {
@@ -347,7 +361,8 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
         }
         a = half_warp_sum(a); b = half_warp_sum(b); g = half_warp_sum(g);
         if (active && fabsf(g) > tol * sqrtf(a * b) && a > zero2 && b > zero2) {
-          if (hl == 0) atomicMax(&s_maxrel, __float_as_int(fabsf(g) / sqrtf(a * b)));
+          my_rot = true;
+          my_mrel = fmaxf(my_mrel, fabsf(g) / sqrtf(a * b));
           const float zeta = (b - a) / (2.f * g);
           const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
           const float c = 1.f / sqrtf(1.f + t * t);
@@ -368,8 +383,17 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
               *wq = make_float4(sn * wu.x + c * wv.x, sn * wu.y + c * wv.y, sn * wu.z + c * wv.z, sn * wu.w + c * wv.w);
             }
           }
-          if (hl == 0) s_rot = 1;
         }
+      }
+      __syncthreads();
+    }
+    {
+      const bool wr = __any_sync(0xffffffffu, my_rot);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) my_mrel = fmaxf(my_mrel, __shfl_xor_sync(0xffffffffu, my_mrel, o));
+      if (lane == 0 && wr) {
+        s_rot = 1;
+        atomicMax(&s_maxrel, __float_as_int(my_mrel));  // non-negative floats order like their bits
       }
       __syncthreads();
     }
@@ -473,7 +497,8 @@ rsvd_status small_gemm64(int r, const double* A, bool transA, const double* B, d
 }
 
 rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const double* W0, double* sigma, double* U,
-                                  double* W, const JacobiWs& ws, cudaStream_t stream, double tol) {
+                                  double* W, const JacobiWs& ws, cudaStream_t stream, double tol,
+                                  int max_sweeps = kJacobiMaxSweeps) {
   RSVD_CUDA(cudaMemsetAsync(ws.rotated, 0, 3 * kJacobiMaxSweeps * sizeof(int), stream));
   const int rp = r + (r & 1);
   const int npairs = rp / 2;
@@ -515,7 +540,7 @@ rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const doub
       continue;
     }
     RSVD_CUDA(cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, rows, r, Min, W0, ws.M, ws.W, ws.rotated, ws.sweeps,
-                                 ws.status, sigma, U, W, check, tol));
+                                 ws.status, sigma, U, W, check, tol, max_sweeps));
     RSVD_CUDA(after_launch());
     return RSVD_OK;
   }
@@ -524,7 +549,7 @@ rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const doub
 }  // namespace
 
 rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double* U, double* W,
-                       const JacobiWs& ws, cudaStream_t stream, double tol) {
+                       const JacobiWs& ws, cudaStream_t stream, double tol, bool fp64_sweeps) {
   if (r <= 0) return RSVD_OK;
   if (!(tol > 0.0)) tol = (double)r * 2.220446049250313e-16;  // r eps: the FP64 stopping test
   if (rows != r || r > kF32MaxR || r < 8 || !ws.W32)
@@ -557,8 +582,12 @@ rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double*
   RSVD_CUDA(cudaMemcpyAsync(ws.W64, ws.T, sizeof(double) * (size_t)r * r, cudaMemcpyDeviceToDevice, stream));
   // M64 = M W': column-major M64 = Wt' (row-major) times Mc viewed row-major.
   RSVD_TRY(small_gemm64(r, ws.W64, false, Mc, ws.M64, ws.gemm_partial, stream));
-  // Phase 3: FP64 sweeps to convergence, starting from the rotated matrix.
-  return launch_cluster_jacobi(rows, r, ws.M64, ws.W64, sigma, U, W, ws, stream, tol);
+  // Phase 3: FP64 sweeps to convergence, starting from the rotated matrix --
+  // or, where the caller's inputs carry far less than FP32 accuracy, none: the
+  // FP32 convergence stands and only the outputs are formed (norms, order,
+  // normalisation) from the FP64 product M W.
+  return launch_cluster_jacobi(rows, r, ws.M64, ws.W64, sigma, U, W, ws, stream, tol,
+                               fp64_sweeps ? kJacobiMaxSweeps : 0);
 }
 
 }  // namespace rsvd

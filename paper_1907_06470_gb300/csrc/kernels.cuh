@@ -92,8 +92,10 @@ JacobiWs jacobi_ws_carve(Carver& c, int64_t rows, int r, bool precondition = tru
 // Mc column-major rows x r; outputs sigma (r), U (rows x r) and W (r x r)
 // row-major with columns ordered like sigma (descending).
 // tol: relative off-diagonal stopping test |c_ij| <= tol sqrt(c_ii c_jj) (0: r eps, FP64)
+// fp64_sweeps = false (square inputs with the FP32 phase only): stop at FP32
+// convergence (tol = r eps32) and form the outputs from the FP64 product M W.
 rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double* U, double* W,
-                       const JacobiWs& ws, cudaStream_t stream, double tol = 0.0);
+                       const JacobiWs& ws, cudaStream_t stream, double tol = 0.0, bool fp64_sweeps = true);
 
 // lift.cu -- conversions, sign normalisation.
 template <typename Tin, typename Tout>

@@ -106,6 +106,10 @@ def test_bf16_rsvd_against_oracle(g, prec):
     Uo, So, Vo = OR.rsvd(A, k, p, q, seed, "bf16")
     es, eu, ev = sigma_rel_err(S, So), max_principal_angle(U, Uo), max_principal_angle(V, Vo)
     print(f"{prec}: sigma rel err {es:.2e}, U angle {eu:.2e}, V angle {ev:.2e}")
+    # the BF16 plan's small SVD stops at FP32 convergence: U and V stay
+    # orthonormal far below the BF16 error
+    I = np.eye(k)
+    assert np.abs(U.T @ U - I).max() <= 1e-4 and np.abs(V.T @ V - I).max() <= 1e-4
     if prec == "bf16x3":
         assert es <= 1e-4 and eu <= 1e-2
     else:
