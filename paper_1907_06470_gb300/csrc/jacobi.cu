@@ -267,14 +267,13 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
 
 // FP32 one-sided Jacobi in one CTA with M and W in shared memory: the cheap
 // first phase.  Columns are stored with stride ldm = r rounded up to 4; each
-// half-warp rotates one column pair, lane l holding the rows [4 V l, 4 V l +
-// 4 V) of both columns as V float4 (V = ceil(r / 64)), so a column moves in V
-// 16-byte loads per lane.  The 64 half-warps of the CTA cover every pair of a
-// round for r <= 128 at once.  The rotations are accumulated in W32
-// (column-major r x r), which the FP64 phase then orthonormalises and applies
-// to M before finishing in FP64.
+// half-warp rotates one column pair, lane l holding the float4s l, l + 16, ...
+// (V of them, V = ceil(r / 64)) of both columns, so a half-warp reads 256
+// contiguous bytes per access (no bank conflicts).  The 64 half-warps of the
+// CTA cover every pair of a round for r <= 128 at once.  The rotations are
+// accumulated in W32 (column-major r x r), which the FP64 phase then
+// orthonormalises and applies to M before finishing in FP64.
 constexpr int kF32MaxR = 160;
-constexpr int kF32MaxV = (kF32MaxR + 63) / 64;  // float4 per lane and column
 
 __device__ __forceinline__ float half_warp_sum(float v) {
 #pragma unroll
@@ -295,10 +294,12 @@ size_t f32_jacobi_smem(int r) {
   return (2 * (size_t)r * ldm + r) * sizeof(float);
 }
 
+template <int V>
 __global__ void __launch_bounds__(1024)
 jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32, int* sweeps_out) {
   extern __shared__ __align__(16) float smf[];
   const int ldm = (r + 3) & ~3;
+  const int ld4 = ldm / 4;                // float4 per column
   float* M = smf;
   float* W = smf + (size_t)r * ldm;
   float* nrm = W + (size_t)r * ldm;
@@ -308,8 +309,6 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, warps = nt >> 5;
   const int hw = tid >> 4, hl = tid & 15, nhw = nt >> 4;  // half-warp index, lane in it
   const int rp = r + (r & 1), npairs = rp / 2;
-  const int V = (r + 63) / 64;          // float4 per lane and column
-  const int row0 = 4 * V * hl;          // first row this lane holds
   float f = 0.f;
   for (int c = warp; c < r; c += warps)
     for (int i = lane; i < ldm; i += 32) {
@@ -347,14 +346,16 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
           if (p >= r || q >= r) active = false;
           if (p > q) { const int t = p; p = q; q = t; }
         }
-        float4 xv[kF32MaxV], yv[kF32MaxV];
+        const float4* mp4 = reinterpret_cast<const float4*>(M + p * ldm);
+        const float4* mq4 = reinterpret_cast<const float4*>(M + q * ldm);
+        float4 xv[V], yv[V];
         float a = 0.f, b = 0.f, g = 0.f;
 #pragma unroll
-        for (int t = 0; t < kF32MaxV; ++t) {
-          const int i = row0 + 4 * t;
-          const bool ok = active && t < V && i < ldm;
-          xv[t] = ok ? *reinterpret_cast<const float4*>(M + p * ldm + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-          yv[t] = ok ? *reinterpret_cast<const float4*>(M + q * ldm + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int t = 0; t < V; ++t) {
+          const int i4 = hl + 16 * t;
+          const bool ok = active && i4 < ld4;
+          xv[t] = ok ? mp4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+          yv[t] = ok ? mq4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
           a = fmaf(xv[t].x, xv[t].x, fmaf(xv[t].y, xv[t].y, fmaf(xv[t].z, xv[t].z, fmaf(xv[t].w, xv[t].w, a))));
           b = fmaf(yv[t].x, yv[t].x, fmaf(yv[t].y, yv[t].y, fmaf(yv[t].z, yv[t].z, fmaf(yv[t].w, yv[t].w, b))));
           g = fmaf(xv[t].x, yv[t].x, fmaf(xv[t].y, yv[t].y, fmaf(xv[t].z, yv[t].z, fmaf(xv[t].w, yv[t].w, g))));
@@ -362,25 +363,33 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
         a = half_warp_sum(a); b = half_warp_sum(b); g = half_warp_sum(g);
         if (active && fabsf(g) > tol * sqrtf(a * b) && a > zero2 && b > zero2) {
           my_rot = true;
-          my_mrel = fmaxf(my_mrel, fabsf(g) / sqrtf(a * b));
+          my_mrel = fmaxf(my_mrel, fabsf(g) * rsqrtf(a * b));
+          // t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / 2g; for
+          // |zeta| > 1e18 (zeta^2 would overflow) t = 1 / (2 zeta) to rounding.
+          // c = (1 + t^2)^-1/2 from the hardware estimate and one Newton step:
+          // the FP32 rotations only need to converge, W32 is orthonormalised
+          // in FP64 afterwards.
           const float zeta = (b - a) / (2.f * g);
-          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
-          const float c = 1.f / sqrtf(1.f + t * t);
+          const float az = fabsf(zeta);
+          const float t = az > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(fmaf(zeta, zeta, 1.f)));
+          const float x = fmaf(t, t, 1.f);
+          float c = rsqrtf(x);
+          c = c * fmaf(-0.5f * x, c * c, 1.5f);
           const float sn = c * t;
+          float4* mp = reinterpret_cast<float4*>(M + p * ldm);
+          float4* mq = reinterpret_cast<float4*>(M + q * ldm);
+          float4* wp = reinterpret_cast<float4*>(W + p * ldm);
+          float4* wq = reinterpret_cast<float4*>(W + q * ldm);
 #pragma unroll
-          for (int u = 0; u < kF32MaxV; ++u) {
-            const int i = row0 + 4 * u;
-            if (u < V && i < ldm) {
-              float4* mp = reinterpret_cast<float4*>(M + p * ldm + i);
-              float4* mq = reinterpret_cast<float4*>(M + q * ldm + i);
-              const float4 x = xv[u], y = yv[u];
-              *mp = make_float4(c * x.x - sn * y.x, c * x.y - sn * y.y, c * x.z - sn * y.z, c * x.w - sn * y.w);
-              *mq = make_float4(sn * x.x + c * y.x, sn * x.y + c * y.y, sn * x.z + c * y.z, sn * x.w + c * y.w);
-              float4* wp = reinterpret_cast<float4*>(W + p * ldm + i);
-              float4* wq = reinterpret_cast<float4*>(W + q * ldm + i);
-              const float4 wu = *wp, wv = *wq;
-              *wp = make_float4(c * wu.x - sn * wv.x, c * wu.y - sn * wv.y, c * wu.z - sn * wv.z, c * wu.w - sn * wv.w);
-              *wq = make_float4(sn * wu.x + c * wv.x, sn * wu.y + c * wv.y, sn * wu.z + c * wv.z, sn * wu.w + c * wv.w);
+          for (int u = 0; u < V; ++u) {
+            const int i4 = hl + 16 * u;
+            if (i4 < ld4) {
+              const float4 xx = xv[u], yy = yv[u];
+              const float4 wu = wp[i4], wv = wq[i4];
+              mp[i4] = make_float4(c * xx.x - sn * yy.x, c * xx.y - sn * yy.y, c * xx.z - sn * yy.z, c * xx.w - sn * yy.w);
+              mq[i4] = make_float4(sn * xx.x + c * yy.x, sn * xx.y + c * yy.y, sn * xx.z + c * yy.z, sn * xx.w + c * yy.w);
+              wp[i4] = make_float4(c * wu.x - sn * wv.x, c * wu.y - sn * wv.y, c * wu.z - sn * wv.z, c * wu.w - sn * wv.w);
+              wq[i4] = make_float4(sn * wu.x + c * wv.x, sn * wu.y + c * wv.y, sn * wu.z + c * wv.z, sn * wu.w + c * wv.w);
             }
           }
         }
@@ -419,7 +428,7 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
       for (int q = p + 1 + lane; q < r; q += 32) {
         const float4* xq = reinterpret_cast<const float4*>(M + q * ldm);
         float g0 = 0.f, g1 = 0.f;
-        for (int i = 0; i < ldm / 4; ++i) {
+        for (int i = 0; i < ld4; ++i) {
           const float4 x = xp[i], y = xq[i];
           g0 = fmaf(x.x, y.x, fmaf(x.y, y.y, g0));
           g1 = fmaf(x.z, y.z, fmaf(x.w, y.w, g1));
@@ -557,11 +566,17 @@ rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double*
   // Phase 1: FP32 sweeps to FP32 convergence, one CTA, shared memory.
   static bool attr = false;
   if (!attr) {
-    RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)f32_jacobi_smem(kF32MaxR)));
+    const int mx = (int)f32_jacobi_smem(kF32MaxR);
+    RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     attr = true;
   }
-  jacobi_f32_kernel<<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
+  // float4s per lane and column: ceil(ceil(r / 4) / 16)
+  const int V = (int)cdiv(cdiv(r, 4), 16);
+  if (V <= 1) jacobi_f32_kernel<1><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
+  else if (V == 2) jacobi_f32_kernel<2><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
+  else jacobi_f32_kernel<3><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
   RSVD_CUDA(after_launch());
   // Phase 2: Newton-Schulz steps make W orthogonal to FP64 accuracy:
   // W' = (1.5 I - 0.5 W W^T) W, i.e. on the column-major storage (= W^T row-major)

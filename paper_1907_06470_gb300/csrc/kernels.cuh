@@ -41,10 +41,8 @@ rsvd_status reduce_partials(int64_t M, int64_t N, int nsplit, const T* P, int64_
 // orth.cu -- CholeskyQR2 pieces.
 struct OrthWs {
   double* G = nullptr;        // r x r Gram (FP64)
-  double* L1 = nullptr;       // r x r Cholesky factors (lower, FP64)
+  double* L1 = nullptr;       // r x r Cholesky factors (lower, in the panel's type)
   double* L2 = nullptr;
-  double* Rinv = nullptr;     // r x r upper inverse (FP64)
-  double* Awork = nullptr;    // r x r Cholesky working copy when it does not fit in shared memory
   int* dead1 = nullptr;       // deflated pivots of the two sweeps (r each)
   int* dead2 = nullptr;
   void* Rinv_t = nullptr;     // the same in the panel dtype

@@ -1,17 +1,13 @@
 // Section 2.1 steps 3-4: orthonormal basis Q_r of the sketch Y by CholeskyQR2.
 //
 //   G = Y^T Y          chunk partials (simt_gemm) added in FP64
-//   G = L L^T          Cholesky (FP64 for FP64 panels, FP32 for FP32 panels), one CTA
-//   Rinv = L^-T        triangular inverse in the panel's type (for r up to
-//                      about 120 both in one shared-memory kernel,
-//                      chol_inv_fused_kernel; else cholesky_kernel +
-//                      trilinv_kernel)
+//   G = L L^T,         Cholesky and triangular inverse together, one CTA, in
+//   Rinv = L^-T        the panel's type (chol_inv_fused_kernel)
 //   Q1 = Y Rinv        panel product in the panel's precision (simt_gemm)
 // and the same once more on Q1 (Fukaya, Nakatsukasa, Yanagisawa, Yamamoto,
 // "CholeskyQR2", 2014), which restores orthogonality to working precision
-// whenever the first Cholesky succeeds.  The second Gram is close to the
-// identity, so for FP32 panels its Cholesky and inverse run in FP32.
-// R = R2 R1 is formed (in FP64) on request.
+// whenever the first Cholesky succeeds.  R = R2 R1 is formed (in FP64) on
+// request.
 //
 // Rank deficiency: a Cholesky pivot that has lost all but a tau fraction of its
 // column's mass is deflated and the column of Q1 replaced by a unit random
@@ -29,63 +25,11 @@
 namespace rsvd {
 namespace {
 
-// Right-looking Cholesky G = L L^T of an r x r symmetric matrix in one CTA of
-// 256 threads (the per-column barriers dominate, so fewer warps are faster).  The working copy A lives in shared memory when it fits
-// (r <= kCholSmemMaxR), else in global memory (L2); the factor L (lower,
-// row-major, zero above the diagonal) is written to `L`.  Step k: thread 0
-// forms the pivot; then every thread writes its part of column k of L and
-// applies the rank-1 update A[i][j] -= A[i][k] A[j][k] / d to the trailing
-// lower triangle, reading column k unscaled (it is not written in that phase),
-// so two barriers per column suffice.
-//
 // Pivot deflation: a pivot whose remaining mass d is at most tau * G_kk (the
 // column is linearly dependent on the previous ones to the accuracy of G) is
 // marked dead: L[k][k] = 1 and L[i][k] = 0 below it, so Y L^-T leaves that
 // column as a negligible residual, to be replaced by a fresh random direction
 // (fill_dead_columns).  A NaN or infinite pivot records DEV_NOT_SPD.
-constexpr int kCholSmemBytes = 160 * 160 * 8;
-
-template <typename T>
-__global__ void __launch_bounds__(256)
-cholesky_kernel(int r, const double* __restrict__ G, T* __restrict__ L, T* __restrict__ Awork,
-                int* __restrict__ dead, double tau, int* status) {
-  extern __shared__ __align__(16) unsigned char chol_smem[];
-  __shared__ T s_inv, s_inv2;
-  __shared__ int s_dead;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int tx = tid & 31, ty = tid >> 5, nty = nt >> 5;
-  const bool in_smem = (size_t)r * r * sizeof(T) + (size_t)r * sizeof(double) <= (size_t)kCholSmemBytes;
-  T* gdiag = reinterpret_cast<T*>(chol_smem);  // tau * G_kk, the deflation floor
-  T* A = in_smem ? reinterpret_cast<T*>(chol_smem + (size_t)r * sizeof(double)) : Awork;
-  for (int e = tid; e < r * r; e += nt) { A[e] = (T)G[e]; L[e] = T(0); }
-  for (int k = tid; k < r; k += nt) gdiag[k] = (T)(tau * G[(int64_t)k * r + k]);
-  __syncthreads();
-  for (int k = 0; k < r; ++k) {
-    if (tid == 0) {
-      const T d = A[k * r + k];
-      const T floor_k = gdiag[k];
-      int is_dead = 0;
-      if (!isfinite(d) || !isfinite(floor_k)) { is_dead = 1; dev_set_status(status, DEV_NOT_SPD); }
-      else if (!(d > floor_k) || !(d > T(0))) is_dead = 1;
-      dead[k] = is_dead;
-      const T piv = is_dead ? T(0) : sqrt(d);
-      s_inv = is_dead ? T(0) : T(1) / piv;
-      s_inv2 = is_dead ? T(0) : T(1) / d;
-      s_dead = is_dead;
-      L[(int64_t)k * r + k] = is_dead ? T(1) : piv;
-    }
-    __syncthreads();
-    const T inv = s_inv, inv2 = s_inv2;
-    for (int i = k + 1 + tid; i < r; i += nt) L[(int64_t)i * r + k] = A[i * r + k] * inv;
-    if (!s_dead) {
-      for (int i = k + 1 + ty; i < r; i += nty) {
-        const T cik = A[i * r + k] * inv2;
-        for (int j = k + 1 + tx; j <= i; j += 32) A[i * r + j] -= cik * A[j * r + k];
-      }
-    }
-    __syncthreads();
-  }
-}
 
 // Any pivot dead in the second sweep means the panel stayed rank deficient
 // after its dead columns were replaced: report it.
@@ -94,58 +38,14 @@ __global__ void check_dead_kernel(int r, const int* __restrict__ dead, int* stat
     if (dead[k]) dev_set_status(status, DEV_NOT_SPD);
 }
 
-// X = L^-1 by forward substitution; Rinv = X^T (upper), in T and in the panel
-// type TOUT.  Each CTA has four warps, one column j each; the rows of L from
-// the CTA's first column down are staged in shared memory when they fit, and
-// the reciprocals of the diagonal are formed once up front, so each sequential
-// step of a column is a shared-memory dot product and one multiply.
-constexpr int kInvCols = 4;
-constexpr int kInvSmemBytes = 200 * 1024;
 
-template <typename T, typename TOUT>
-__global__ void __launch_bounds__(32 * kInvCols)
-trilinv_kernel(int r, const T* __restrict__ L, T* __restrict__ Rinv, TOUT* __restrict__ Rinv_t, int staged) {
-  extern __shared__ __align__(16) unsigned char inv_smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j0 = blockIdx.x * kInvCols;
-  const int rows = r - j0;                                  // rows/cols j0..r-1 of L
-  T* xs = reinterpret_cast<T*>(inv_smem);                   // kInvCols x r solution vectors
-  T* dinv = xs + kInvCols * r;                              // 1 / L[i][i]
-  T* Ls = dinv + r;                                         // staged rows x rows block
-  for (int e = threadIdx.x; e < kInvCols * r; e += blockDim.x) xs[e] = T(0);
-  for (int i = j0 + threadIdx.x; i < r; i += blockDim.x) dinv[i] = T(1) / L[(int64_t)i * r + i];
-  if (staged)
-    for (int e = threadIdx.x; e < rows * rows; e += blockDim.x) {
-      const int i = e / rows, l = e % rows;
-      Ls[e] = l <= i ? L[(int64_t)(j0 + i) * r + (j0 + l)] : T(0);
-    }
-  __syncthreads();
-  const int j = j0 + warp;
-  if (j < r) {
-    T* x = xs + warp * r;
-    auto Lat = [&](int i, int l) -> T { return staged ? Ls[(i - j0) * rows + (l - j0)] : L[(int64_t)i * r + l]; };
-    if (lane == 0) x[j] = dinv[j];
-    __syncwarp();
-    for (int i = j + 1; i < r; ++i) {
-      T s = T(0);
-      for (int l = j + lane; l < i; l += 32) s += Lat(i, l) * x[l];
-      s = warp_sum(s);
-      if (lane == 0) x[i] = -s * dinv[i];
-      __syncwarp();
-    }
-    for (int i = lane; i < r; i += 32) {
-      Rinv[(int64_t)j * r + i] = x[i];  // Rinv[j][i] = X[i][j]
-      Rinv_t[(int64_t)j * r + i] = (TOUT)x[i];
-    }
-  }
-}
-
-// Cholesky and triangular inverse in one CTA with everything in shared memory
-// (for r small enough; larger r takes cholesky_kernel + trilinv_kernel).
+// Cholesky and triangular inverse in one CTA: the working matrices in shared
+// memory when they fit, else in a global scratch (L2 resident at these sizes;
+// the algorithm is the same).
 //
 // Cholesky, blocked right-looking with kCholB columns per panel: warp 0
-// factors the diagonal block column by column (the same pivot test and
-// deflation as cholesky_kernel), then each thread solves one row of the
+// factors the diagonal block column by column (the pivot test and deflation
+// above), then each thread solves one row of the
 // panel below it, then the trailing lower triangle takes the panel's rank-kB
 // update -- three barriers per panel instead of two per column.  The factor
 // L (TF) goes to global memory.
@@ -195,9 +95,25 @@ chol_inv_fused_kernel(int r, const double* __restrict__ G, TF* __restrict__ Lout
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
 
-  for (int i = warp; i < r; i += nwarps)
-    for (int j = lane; j < r; j += 32) A[i * lda + j] = (TF)G[(int64_t)i * r + j];
+  // G (L2 resident, just written): eight loads in flight per thread per round
   for (int k = tid; k < r; k += nt) gdiag[k] = (TF)(tau * G[(int64_t)k * r + k]);
+  {
+    const int rr = r * r;
+    constexpr int U = 8;
+    for (int e0 = tid; e0 < rr; e0 += U * nt) {
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = e0 + u * nt < rr ? G[e0 + u * nt] : 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * nt;
+        if (e < rr) {
+          const int i = e / r;
+          A[i * lda + (e - i * r)] = (TF)v[u];
+        }
+      }
+    }
+  }
   __syncthreads();
 
   for (int p = 0; p < r; p += NB) {
@@ -349,6 +265,7 @@ chol_inv_fused_kernel(int r, const double* __restrict__ G, TF* __restrict__ Lout
     for (int i = lane; i < r; i += 32) Rinv_t[(int64_t)j * r + i] = i >= j ? X[i * lda + j] : TI(0);
 }
 
+
 // R = R2 R1 with R1 = L1^T, R2 = L2^T (both upper triangular).  A dead pivot l
 // of the first sweep carries no part of Y (its column was a negligible
 // residual), so row l of R1 counts as zero.
@@ -426,60 +343,33 @@ double pivot_tau<double>() { return 1e-13; }
 template <>
 double pivot_tau<float>() { return 1e-5; }
 
-// Arithmetic of the two factorisations.  FP64 panels: FP64 for both.  FP32
-// panels: FP32 for both.  The Gram of an FP32 panel carries FP32 accuracy
-// (FP32 products summed in chunks), and CholeskyQR in working precision u
-// leaves Q1 orthogonal to about u cond(Y)^2, which the second sweep restores to
-// u whenever cond(Y) is below about u^-1/2 (about 4e3 in FP32) -- the range
-// finder's panels Y = A Z with orthonormal Z have cond(Y) near
-// sigma_1 / sigma_r of A.  Pivots below tau = 1e-5 of their diagonal (the
-// deflation floor of FP32 panels) are deflated either way.  The second sweep
-// factors Q1^T Q1, close to the identity.
-template <typename T>
-struct FirstSweep { using type = double; };
-template <>
-struct FirstSweep<float> { using type = float; };
-template <typename T>
-struct SecondSweep { using type = double; };
-template <>
-struct SecondSweep<float> { using type = float; };
+// Arithmetic of the two factorisations: the panel's type.  The Gram of an FP32
+// panel carries FP32 accuracy (FP32 products summed in chunks), and
+// CholeskyQR in working precision u leaves Q1 orthogonal to about
+// u cond(Y)^2, which the second sweep restores to u whenever cond(Y) is below
+// about u^-1/2 (about 4e3 in FP32) -- the range finder's panels Y = A Z with
+// orthonormal Z have cond(Y) near sigma_1 / sigma_r of A.  Pivots below
+// tau = 1e-5 of their diagonal (the deflation floor of FP32 panels) are
+// deflated either way.  The second sweep factors Q1^T Q1, close to the identity.
 
-// Cholesky + triangular inverse.  TF is the arithmetic of the factorisation
-// (FP64, or FP32 for the near-identity Gram of a second sweep on an FP32
-// panel); T is the panel type that receives Rinv.
-template <typename TF, typename T>
-rsvd_status chol_inv(int r, const OrthWs& ws, TF* L, int* dead, double tau, cudaStream_t stream) {
-  const size_t fused = fused_smem_bytes<TF, T>(r);
+// Cholesky + triangular inverse in the arithmetic T of the factorisation
+// (FP64 for FP64 panels, FP32 for FP32 panels), which is also the panel type
+// that receives Rinv.
+template <typename T>
+rsvd_status chol_inv(int r, const OrthWs& ws, T* L, int* dead, double tau, cudaStream_t stream) {
+  const size_t fused = fused_smem_bytes<T, T>(r);
   const bool in_smem = fused <= kFusedSmemMax;
-  if (in_smem || (ws.chol_scratch && ws.chol_scratch_bytes >= fused_big_bytes<TF, T>(r))) {
-    static bool fattr = false;
-    if (!fattr) {
-      RSVD_CUDA(cudaFuncSetAttribute(chol_inv_fused_kernel<TF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kFusedSmemMax));
-      fattr = true;
-    }
-    chol_inv_fused_kernel<TF, T><<<1, kFusedThreads, in_smem ? fused : fused_small_bytes<TF>(r), stream>>>(
-        r, ws.G, L, dead, tau, ws.status, static_cast<T*>(ws.Rinv_t),
-        in_smem ? nullptr : static_cast<unsigned char*>(ws.chol_scratch));
-    RSVD_CUDA(after_launch());
-    return RSVD_OK;
+  if (!in_smem && !(ws.chol_scratch && ws.chol_scratch_bytes >= fused_big_bytes<T, T>(r)))
+    return fail(RSVD_ERR_INVALID_ARG, "orth: workspace lacks the factorisation scratch for this r");
+  static bool fattr = false;
+  if (!fattr) {
+    RSVD_CUDA(cudaFuncSetAttribute(chol_inv_fused_kernel<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kFusedSmemMax));
+    fattr = true;
   }
-  static bool attrs = false;
-  if (!attrs) {
-    RSVD_CUDA(cudaFuncSetAttribute(cholesky_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmemBytes));
-    RSVD_CUDA(cudaFuncSetAttribute(trilinv_kernel<TF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSmemBytes));
-    attrs = true;
-  }
-  const size_t chol_need = (size_t)r * r * sizeof(TF) + (size_t)r * sizeof(double);
-  const size_t chol_smem = chol_need <= (size_t)kCholSmemBytes ? chol_need : (size_t)r * sizeof(double);
-  cholesky_kernel<TF><<<1, 256, chol_smem, stream>>>(r, ws.G, L, reinterpret_cast<TF*>(ws.Awork), dead, tau,
-                                                      ws.status);
-  RSVD_CUDA(after_launch());
-  const size_t base = ((size_t)kInvCols * r + r) * sizeof(TF);
-  const size_t staged_bytes = base + (size_t)r * r * sizeof(TF);
-  const int staged = staged_bytes <= (size_t)kInvSmemBytes ? 1 : 0;
-  trilinv_kernel<TF, T><<<(int)cdiv(r, kInvCols), 32 * kInvCols, staged ? staged_bytes : base, stream>>>(
-      r, L, reinterpret_cast<TF*>(ws.Rinv), static_cast<T*>(ws.Rinv_t), staged);
+  chol_inv_fused_kernel<T, T><<<1, kFusedThreads, in_smem ? fused : fused_small_bytes<T>(r), stream>>>(
+      r, ws.G, L, dead, tau, ws.status, static_cast<T*>(ws.Rinv_t),
+      in_smem ? nullptr : static_cast<unsigned char*>(ws.chol_scratch));
   RSVD_CUDA(after_launch());
   return RSVD_OK;
 }
@@ -487,11 +377,10 @@ rsvd_status chol_inv(int r, const OrthWs& ws, TF* L, int* dead, double tau, cuda
 }  // namespace
 
 namespace {
-// global scratch for the fused factorisation when r is too large for shared memory
+// global scratch for the blocked factorisation when r is too large for shared
+// memory (sized for FP64, which covers FP32)
 size_t chol_scratch_bytes(int r) {
-  if (fused_smem_bytes<double, float>(r) <= kFusedSmemMax && fused_smem_bytes<float, float>(r) <= kFusedSmemMax &&
-      fused_smem_bytes<double, double>(r) <= kFusedSmemMax)
-    return 0;
+  if (fused_smem_bytes<double, double>(r) <= kFusedSmemMax) return 0;
   return fused_big_bytes<double, double>(r);
 }
 
@@ -514,7 +403,7 @@ __global__ void widen_gram_kernel(int r, const float* __restrict__ g32, double* 
 size_t orth_ws_bytes(int64_t M, int r, int dtype, bool tc) {
   Sizer s;
   const size_t esz = dtype == RSVD_F64 ? 8 : 4;
-  s.take<double>((size_t)r * r * 5);
+  s.take<double>((size_t)r * r * 3);
   s.take<int>((size_t)2 * r);
   s.take<char>((size_t)r * r * esz);
   s.take<char>((size_t)gram_chunks(M) * r * r * esz);
@@ -531,11 +420,8 @@ size_t orth_ws_bytes(int64_t M, int r, int dtype, bool tc) {
 OrthWs orth_ws_carve(Carver& c, int64_t M, int r, int dtype, bool tc) {
   OrthWs w;
   const size_t esz = dtype == RSVD_F64 ? 8 : 4;
-  double* base = c.take<double>((size_t)r * r * 5);
-  if (base) {
-    w.G = base; w.L1 = base + r * r; w.L2 = base + 2 * r * r; w.Rinv = base + 3 * r * r;
-    w.Awork = base + 4 * r * r;
-  }
+  double* base = c.take<double>((size_t)r * r * 3);
+  if (base) { w.G = base; w.L1 = base + r * r; w.L2 = base + 2 * r * r; }
   int* dd = c.take<int>((size_t)2 * r);
   if (dd) { w.dead1 = dd; w.dead2 = dd + r; }
   w.Rinv_t = c.take<char>((size_t)r * r * esz);
@@ -586,12 +472,12 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
       // the same two sweeps with the Grams and panel products on the tensor cores
       RSVD_TRY(gram_tc(M, r, Y, ldy, ws, stream));
       float* L1 = reinterpret_cast<float*>(ws.L1);
-      RSVD_TRY((chol_inv<float, float>(r, ws, L1, ws.dead1, pivot_tau<float>(), stream)));
+      RSVD_TRY(chol_inv<float>(r, ws, L1, ws.dead1, pivot_tau<float>(), stream));
       RSVD_TRY(panel_times_tc(M, r, Y, ldy, Rt, Q1, ws.ld_tmp, ws, stream));
       RSVD_TRY(fill_dead_columns(M, r, ws.dead1, Q1, ws.ld_tmp, RSVD_F32, kDeadFillSeed, stream));
       RSVD_TRY(gram_tc(M, r, Q1, ws.ld_tmp, ws, stream));
       float* L2 = reinterpret_cast<float*>(ws.L2);
-      RSVD_TRY((chol_inv<float, float>(r, ws, L2, ws.dead2, pivot_tau<float>(), stream)));
+      RSVD_TRY(chol_inv<float>(r, ws, L2, ws.dead2, pivot_tau<float>(), stream));
       check_dead_kernel<<<1, 256, 0, stream>>>(r, ws.dead2, ws.status);
       RSVD_CUDA(after_launch());
       RSVD_TRY(panel_times_tc(M, r, Q1, ws.ld_tmp, Rt, Q, ldq, ws, stream));
@@ -605,22 +491,20 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
   // sweep 1 (dead pivots: the panel is rank deficient to the Gram's accuracy;
   // their columns of Q1 are replaced by unit random directions)
   RSVD_TRY(gram<T>(M, r, Y, ldy, ws, stream));
-  using TF1 = typename FirstSweep<T>::type;
-  TF1* L1 = reinterpret_cast<TF1*>(ws.L1);
-  RSVD_TRY((chol_inv<TF1, T>(r, ws, L1, ws.dead1, pivot_tau<T>(), stream)));
+  T* L1 = reinterpret_cast<T*>(ws.L1);
+  RSVD_TRY(chol_inv<T>(r, ws, L1, ws.dead1, pivot_tau<T>(), stream));
   RSVD_TRY(simt_gemm<T>(M, r, r, Y, ldy, false, Rt, r, Q1, ws.ld_tmp, false, 1, r, nullptr, stream));
   RSVD_TRY(fill_dead_columns(M, r, ws.dead1, Q1, ws.ld_tmp, sizeof(T) == 8 ? RSVD_F64 : RSVD_F32,
                              kDeadFillSeed, stream));
   // sweep 2
   RSVD_TRY(gram<T>(M, r, Q1, ws.ld_tmp, ws, stream));
-  using TF2 = typename SecondSweep<T>::type;
-  TF2* L2 = reinterpret_cast<TF2*>(ws.L2);
-  RSVD_TRY((chol_inv<TF2, T>(r, ws, L2, ws.dead2, pivot_tau<T>(), stream)));
+  T* L2 = reinterpret_cast<T*>(ws.L2);
+  RSVD_TRY(chol_inv<T>(r, ws, L2, ws.dead2, pivot_tau<T>(), stream));
   check_dead_kernel<<<1, 256, 0, stream>>>(r, ws.dead2, ws.status);
   RSVD_CUDA(after_launch());
   RSVD_TRY(simt_gemm<T>(M, r, r, Q1, ws.ld_tmp, false, Rt, r, Q, ldq, false, 1, r, nullptr, stream));
   if (R) {
-    rprod_kernel<TF1, TF2><<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r, L1, ws.dead1, L2, R);
+    rprod_kernel<T, T><<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r, L1, ws.dead1, L2, R);
     RSVD_CUDA(after_launch());
   }
   return RSVD_OK;
