@@ -43,60 +43,168 @@ __global__ void check_dead_kernel(int r, const int* __restrict__ dead, int* stat
 // memory when they fit, else in a global scratch (L2 resident at these sizes;
 // the algorithm is the same).
 //
-// Cholesky, blocked right-looking with kCholB columns per panel: warp 0
-// factors the diagonal block column by column (the pivot test and deflation
-// above), then each thread solves one row of the
-// panel below it, then the trailing lower triangle takes the panel's rank-kB
-// update -- three barriers per panel instead of two per column.  The factor
-// L (TF) goes to global memory.
+// Cholesky, blocked right-looking with kCholB = 16 columns per panel: warp 0
+// factors the diagonal block column by column in registers (the pivot test
+// and deflation above), each thread solves one row of the panel below it, and
+// the trailing lower triangle takes the panel's rank-16 update -- with
+// lookahead: warp 0 updates and factors the next diagonal block while the
+// other warps update the rest, two barriers per panel.  Rows are stored with a stride that is a multiple of 16
+// bytes, so a row segment of the panel moves in 16-byte loads (4 for FP32,
+// 8 for FP64); the padding columns are zero.  The factor L goes to global
+// memory.
 //
-// Inverse X = L^-1 in TI (the panel type), blocked by block diagonals: the
-// diagonal blocks are inverted by one warp each; then for d = 1, 2, ... every
-// block X_ij with i - j = d is X_ij = -X_ii (sum_{j<=t<i} L_it X_tj), whose
-// right-hand side only needs blocks of smaller d.  Rinv_t = X^T (upper).
+// Inverse X = L^-1 blocked by block diagonals: the diagonal blocks are inverted
+// by one warp each; then for d = 1, 2, ... every block X_ij with i - j = d is
+// X_ij = -X_ii (sum_{j<=t<i} L_it X_tj), whose right-hand side only needs
+// blocks of smaller d.  Each thread forms a 2 x 4 tile of a block (two rows of
+// L against a 16-byte row segment of X per term).  Rinv_t = X^T (upper) and L
+// are written to global memory as their entries become final.
 constexpr int kCholB = 16;
 constexpr int kFusedThreads = 512;
 constexpr size_t kFusedSmemMax = 220 * 1024;
 
-// bytes of the matrices the fused kernel keeps in shared or global memory
-template <typename TF, typename TI>
+template <typename T>
+__host__ __device__ inline int fused_ld(int r) {
+  constexpr int e = 16 / (int)sizeof(T);
+  return (r + e - 1) / e * e + e;
+}
+
+// bytes of the matrices the fused kernel keeps in shared or global memory:
+// A (L), X (L^-1) and the block scratch S
+// slices of the block scratch S: the inverse splits the terms of a block over
+// up to this many slices when a block diagonal has few blocks
+template <typename T>
+__host__ __device__ constexpr int inv_slices() { return 64 / (int)sizeof(T); }
+
+template <typename T>
 __host__ __device__ inline size_t fused_big_bytes(int r) {
-  const size_t lda = (size_t)r + 1;
   const int nb = (r + kCholB - 1) / kCholB;
-  return (size_t)r * lda * sizeof(TF) + (size_t)r * lda * sizeof(TI) + (size_t)nb * kCholB * kCholB * sizeof(TI) + 64;
+  const int ns = nb > inv_slices<T>() ? nb : inv_slices<T>();
+  return 2 * (size_t)r * fused_ld<T>(r) * sizeof(T) + (size_t)ns * kCholB * kCholB * sizeof(T) + 64;
 }
 
-template <typename TF>
+// bytes of the per-pivot vectors (always in shared memory)
+template <typename T>
 __host__ __device__ inline size_t fused_small_bytes(int r) {
-  return ((2 * (size_t)r * sizeof(TF) + 15) & ~(size_t)15);
+  return ((3 * (size_t)r * sizeof(T) + 15) & ~(size_t)15);
 }
 
-template <typename TF, typename TI>
+template <typename T>
 __host__ __device__ inline size_t fused_smem_bytes(int r) {
-  return fused_small_bytes<TF>(r) + fused_big_bytes<TF, TI>(r);
+  return fused_small_bytes<T>(r) + fused_big_bytes<T>(r);
 }
 
-template <typename TF, typename TI>
-__global__ void __launch_bounds__(kFusedThreads)
-chol_inv_fused_kernel(int r, const double* __restrict__ G, TF* __restrict__ Lout, int* __restrict__ dead,
-                      double tau, int* status, TI* __restrict__ Rinv_t, unsigned char* gscratch) {
+template <typename T>
+struct alignas(16) Vec16 {
+  static constexpr int E = 16 / (int)sizeof(T);
+  T v[E];
+};
+
+template <typename T>
+__device__ __forceinline__ Vec16<T> ld16(const T* p) { return *reinterpret_cast<const Vec16<T>*>(p); }
+
+// L_kk = sqrt(d) and its reciprocal (0, 0 for a dead pivot).  FP32: from the
+// hardware reciprocal square root refined by one Newton step (within about an
+// ulp; the Gram itself carries errors far above that); FP64: IEEE sqrt and
+// division.
+__device__ __forceinline__ void pivot_sqrt(float d, int is_dead, float& piv, float& inv) {
+  float y = rsqrtf(d);
+  y = y * fmaf(-0.5f * d, y * y, 1.5f);
+  inv = is_dead ? 0.f : y;
+  piv = is_dead ? 0.f : d * y;
+}
+__device__ __forceinline__ void pivot_sqrt(double d, int is_dead, double& piv, double& inv) {
+  piv = is_dead ? 0.0 : sqrt(d);
+  inv = is_dead ? 0.0 : 1.0 / piv;
+}
+
+// Warp 0: Cholesky of the diagonal block at p (w <= 16 columns) in place in A,
+// with its pivot test and the reciprocals of its diagonal.
+template <typename T>
+__device__ __forceinline__ void factor_diag_block(T* A, int lda, int p, int w, const T* gdiag, T* invs, T* xdg,
+                                                  int* dead, int* status, int lane, T* Lout, int r) {
+  constexpr int NB = kCholB;
+  constexpr int E = Vec16<T>::E;
+  constexpr int NV = NB / E;
+
+  // Diagonal block in registers: lane i (< w) holds row p+i.  Every lane
+  // forms each pivot from the broadcast diagonal entry, so no lane waits
+  // on another beyond the shuffles.
+  T row[NB];
+  if (lane < w) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const Vec16<T> x = ld16(A + (p + lane) * lda + p + E * v);
+#pragma unroll
+      for (int e = 0; e < E; ++e) row[E * v + e] = x.v[e];
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < NB; ++t) row[t] = T(0);
+  }
+  const T fl = lane < w ? gdiag[p + lane] : T(0);
+  int my_dead = 0;
+  T my_inv = T(0);
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    if (k < w) {
+      const T d = __shfl_sync(0xffffffffu, row[k], k);
+      const T floor_k = __shfl_sync(0xffffffffu, fl, k);
+      int is_dead = 0;
+      if (!isfinite(d) || !isfinite(floor_k)) is_dead = 2;
+      else if (!(d > floor_k) || !(d > T(0))) is_dead = 1;
+      T piv, inv;
+      pivot_sqrt(d, is_dead, piv, inv);
+      if (lane == k) {
+        my_dead = is_dead;
+        my_inv = inv;
+        row[k] = is_dead ? T(1) : piv;
+      }
+      if (lane > k) row[k] *= inv;                 // L_{lane,k}
+#pragma unroll
+      for (int j = k + 1; j < NB; ++j) {
+        const T ljk = __shfl_sync(0xffffffffu, row[k], j);  // L_{j,k}
+        if (lane >= j) row[j] -= row[k] * ljk;
+      }
+    }
+  }
+  if (lane < w) {
+    dead[p + lane] = my_dead ? 1 : 0;
+    if (my_dead == 2) dev_set_status(status, DEV_NOT_SPD);
+    invs[p + lane] = my_inv;
+    xdg[p + lane] = my_dead ? T(1) : my_inv;
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+      if (t <= lane) {
+        A[(p + lane) * lda + p + t] = row[t];
+        Lout[(int64_t)(p + lane) * r + p + t] = row[t];
+      }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFusedThreads, 1)
+chol_inv_fused_kernel(int r, const double* __restrict__ G, T* __restrict__ Lout, int* __restrict__ dead,
+                      double tau, int* status, T* __restrict__ Rinv_t, unsigned char* gscratch) {
   extern __shared__ __align__(16) unsigned char fsm[];
   constexpr int NB = kCholB;
-  const int lda = r + 1;
+  constexpr int E = Vec16<T>::E;       // entries per 16 bytes
+  constexpr int NV = NB / E;           // 16-byte vectors per panel row segment
+  const int lda = fused_ld<T>(r);
   const int nb = (r + NB - 1) / NB;
-  // Working matrices in shared memory, or -- for r too large for it -- in a
-  // global scratch (L2 resident at these sizes); the algorithm is the same.
-  TF* gdiag = reinterpret_cast<TF*>(fsm);        // tau * G_kk
-  TF* invs = gdiag + r;                          // 1 / L_kk (0 for a dead pivot)
-  unsigned char* big = gscratch ? gscratch : fsm + ((2 * (size_t)r * sizeof(TF) + 15) & ~(size_t)15);
-  TF* A = reinterpret_cast<TF*>(big);            // r x lda, lower triangle used
-  TI* X = reinterpret_cast<TI*>(A + (size_t)r * lda);  // r x lda: L^-1
-  TI* S = X + (size_t)r * lda;                   // nb blocks of NB^2 scratch
+  T* gdiag = reinterpret_cast<T*>(fsm);  // tau * G_kk
+  T* invs = gdiag + r;                   // 1 / L_kk (0 for a dead pivot)
+  T* xdg = invs + r;                     // X_kk = 1 / L_kk (1 for a dead pivot)
+  unsigned char* big = gscratch ? gscratch : fsm + fused_small_bytes<T>(r);
+  T* A = reinterpret_cast<T*>(big);      // r x lda, lower triangle used
+  T* X = A + (size_t)r * lda;            // r x lda: L^-1
+  T* S = X + (size_t)r * lda;            // nb blocks of NB^2 scratch
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
 
-  // G (L2 resident, just written): eight loads in flight per thread per round
-  for (int k = tid; k < r; k += nt) gdiag[k] = (TF)(tau * G[(int64_t)k * r + k]);
+  // G (L2 resident, just written): eight loads in flight per thread per round;
+  // the padding columns r .. lda-1 are zeroed (they enter masked products)
+  for (int k = tid; k < r; k += nt) gdiag[k] = (T)(tau * G[(int64_t)k * r + k]);
   {
     const int rr = r * r;
     constexpr int U = 8;
@@ -109,61 +217,40 @@ chol_inv_fused_kernel(int r, const double* __restrict__ G, TF* __restrict__ Lout
         const int e = e0 + u * nt;
         if (e < rr) {
           const int i = e / r;
-          A[i * lda + (e - i * r)] = (TF)v[u];
+          A[i * lda + (e - i * r)] = (T)v[u];
         }
       }
     }
+    const int pad = lda - r;
+    for (int e = tid; e < r * pad; e += nt) A[(e / pad) * lda + r + e % pad] = T(0);
+    // the zero triangles of the outputs: L above its diagonal, Rinv_t below
+    for (int i = warp; i < r; i += nwarps)
+      for (int j = lane; j < r; j += 32) {
+        if (j > i) Lout[(int64_t)i * r + j] = T(0);
+        else if (j < i) Rinv_t[(int64_t)i * r + j] = T(0);
+      }
   }
   __syncthreads();
 
-  for (int p = 0; p < r; p += NB) {
+  // Panels with lookahead: while warps 1.. apply panel p's rank-16 update to
+  // the trailing matrix, warp 0 applies it to the next diagonal block alone and
+  // factors that block, so the diagonal factorisations overlap the updates.
+  // (p = -NB: only the first diagonal block, so that its code exists once)
+  for (int p = -NB; p < r; p += NB) {
     const int pe = min(p + NB, r), w = pe - p;
-    if (warp == 0) {
-      // Diagonal block in registers: lane i (< w) holds row p+i.  Every lane
-      // forms each pivot from the broadcast diagonal entry, so no lane waits
-      // on another beyond the shuffles.
-      TF row[NB];
-#pragma unroll
-      for (int t = 0; t < NB; ++t) row[t] = (lane < w && t < w) ? A[(p + lane) * lda + p + t] : TF(0);
-#pragma unroll
-      for (int k = 0; k < NB; ++k) {
-        if (k < w) {
-          const TF d = __shfl_sync(0xffffffffu, row[k], k);
-          const TF floor_k = gdiag[p + k];
-          int is_dead = 0;
-          if (!isfinite(d) || !isfinite(floor_k)) is_dead = 2;
-          else if (!(d > floor_k) || !(d > TF(0))) is_dead = 1;
-          const TF piv = is_dead ? TF(0) : sqrt(d);
-          const TF inv = is_dead ? TF(0) : TF(1) / piv;
-          if (lane == 0) {
-            dead[p + k] = is_dead ? 1 : 0;
-            if (is_dead == 2) dev_set_status(status, DEV_NOT_SPD);
-            invs[p + k] = inv;
-          }
-          if (lane == k) row[k] = is_dead ? TF(1) : piv;
-          if (lane > k) row[k] *= inv;                 // L_{lane,k}
-#pragma unroll
-          for (int j = k + 1; j < NB; ++j) {
-            const TF ljk = __shfl_sync(0xffffffffu, row[k], j);  // L_{j,k}
-            if (lane >= j) row[j] -= row[k] * ljk;
-          }
-        }
-      }
-      if (lane < w)
-#pragma unroll
-        for (int t = 0; t < NB; ++t)
-          if (t <= lane) A[(p + lane) * lda + p + t] = row[t];
-    }
-    __syncthreads();
     // Panel rows below the block: x L_D^T = a, one thread per row, x in registers.
-    for (int i = pe + tid; i < r; i += nt) {
-      TF x[NB];
+    for (int i = p < 0 ? r : pe + tid; i < r; i += nt) {
+      T x[NB];
 #pragma unroll
-      for (int t = 0; t < NB; ++t) x[t] = t < w ? A[i * lda + p + t] : TF(0);
+      for (int v = 0; v < NV; ++v) {
+        const Vec16<T> y = ld16(A + i * lda + p + E * v);
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[E * v + e] = y.v[e];
+      }
 #pragma unroll
       for (int k = 0; k < NB; ++k) {
         if (k < w) {
-          TF v = x[k];
+          T v = x[k];
 #pragma unroll
           for (int t = 0; t < k; ++t) v -= x[t] * A[(p + k) * lda + p + t];
           x[k] = v * invs[p + k];
@@ -171,100 +258,204 @@ chol_inv_fused_kernel(int r, const double* __restrict__ G, TF* __restrict__ Lout
       }
 #pragma unroll
       for (int t = 0; t < NB; ++t)
-        if (t < w) A[i * lda + p + t] = x[t];
+        if (t < w) {
+          A[i * lda + p + t] = x[t];
+          Lout[(int64_t)i * r + p + t] = x[t];
+        }
     }
     __syncthreads();
-    // Trailing lower triangle: lane owns column j, the warp's rows i >= j in
-    // pairs (two independent FMA chains).
-    for (int j = pe + lane; j < r; j += 32) {
-      TF lj[NB];
+    const int pn = pe, wn = min(NB, r - pn);  // the next panel (wn <= 0: none); w == NB when it exists
+    if (warp == 0) {
+      if (wn > 0) {
+        // next diagonal block: lane l updates row pn + l (entries pn .. pn + l)
+        if (p >= 0 && lane < wn) {
+          T li[NB];
 #pragma unroll
-      for (int t = 0; t < NB; ++t) lj[t] = t < w ? A[j * lda + p + t] : TF(0);
-      int i = pe + warp;
-      if (i < j) i += ((j - i + nwarps - 1) / nwarps) * nwarps;  // first of the warp's rows >= j
-      for (; i + nwarps < r; i += 2 * nwarps) {
-        const int i2 = i + nwarps;
-        TF s1 = A[i * lda + j], s2 = A[i2 * lda + j];
+          for (int v = 0; v < NV; ++v) {
+            const Vec16<T> y = ld16(A + (pn + lane) * lda + p + E * v);
 #pragma unroll
-        for (int t = 0; t < NB; ++t) {
-          s1 -= A[i * lda + p + t] * lj[t];
-          s2 -= A[i2 * lda + p + t] * lj[t];
+            for (int e = 0; e < E; ++e) li[E * v + e] = y.v[e];
+          }
+          for (int jj = 0; jj <= lane; ++jj) {
+            T sum = A[(pn + lane) * lda + pn + jj];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              const Vec16<T> y = ld16(A + (pn + jj) * lda + p + E * v);
+#pragma unroll
+              for (int e = 0; e < E; ++e) sum -= li[E * v + e] * y.v[e];
+            }
+            A[(pn + lane) * lda + pn + jj] = sum;
+          }
         }
-        A[i * lda + j] = s1;
-        A[i2 * lda + j] = s2;
+        __syncwarp();
+        factor_diag_block(A, lda, pn, wn, gdiag, invs, xdg, dead, status, lane, Lout, r);
       }
-      if (i < r) {
-        TF s1 = A[i * lda + j];
+    } else {
+      // Trailing lower triangle without the next diagonal block: lane owns
+      // column j, warps 1.. the rows i >= max(j, next block end) in pairs.
+      const int wi = warp - 1, nw = nwarps - 1;
+      for (int j = p < 0 ? r : pe + lane; j < r; j += 32) {
+        T lj[NB];
 #pragma unroll
-        for (int t = 0; t < NB; ++t) s1 -= A[i * lda + p + t] * lj[t];
-        A[i * lda + j] = s1;
+        for (int v = 0; v < NV; ++v) {
+          const Vec16<T> y = ld16(A + j * lda + p + E * v);
+#pragma unroll
+          for (int e = 0; e < E; ++e) lj[E * v + e] = E * v + e < w ? y.v[e] : T(0);
+        }
+        const int i_lo = j < pn + wn ? pn + wn : j;
+        int i = pe + wi;
+        if (i < i_lo) i += ((i_lo - i + nw - 1) / nw) * nw;  // first of the warp's rows >= i_lo
+        for (; i + nw < r; i += 2 * nw) {
+          const int i2 = i + nw;
+          T s1 = A[i * lda + j], s2 = A[i2 * lda + j];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const Vec16<T> y1 = ld16(A + i * lda + p + E * v), y2 = ld16(A + i2 * lda + p + E * v);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              s1 -= y1.v[e] * lj[E * v + e];
+              s2 -= y2.v[e] * lj[E * v + e];
+            }
+          }
+          A[i * lda + j] = s1;
+          A[i2 * lda + j] = s2;
+        }
+        if (i < r) {
+          T s1 = A[i * lda + j];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const Vec16<T> y1 = ld16(A + i * lda + p + E * v);
+#pragma unroll
+            for (int e = 0; e < E; ++e) s1 -= y1.v[e] * lj[E * v + e];
+          }
+          A[i * lda + j] = s1;
+        }
       }
     }
     __syncthreads();
   }
-  // L to global (zero above the diagonal)
-  for (int i = warp; i < r; i += nwarps)
-    for (int j = lane; j < r; j += 32) Lout[(int64_t)i * r + j] = j <= i ? A[i * lda + j] : TF(0);
   // diagonal blocks: X_bb = L_bb^-1, lane c of warp b solves column c of block b
   for (int b = warp; b < nb; b += nwarps) {
     const int o = b * NB, w = min(NB, r - o);
     if (lane < w) {
-      TI col[NB];
+      T col[NB];
 #pragma unroll
       for (int i = 0; i < NB; ++i) {
         if (i < w) {
-          TI x = i == lane ? TI(1) : TI(0);
+          // row i of the block (entries past w are padding or later columns, masked by t < i < w)
+          T li[NB];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const Vec16<T> y = ld16(A + (o + i) * lda + o + E * v);
+#pragma unroll
+            for (int e = 0; e < E; ++e) li[E * v + e] = y.v[e];
+          }
+          T x = i == lane ? T(1) : T(0);
 #pragma unroll
           for (int t = 0; t < NB; ++t)
-            if (t >= lane && t < i) x -= (TI)A[(o + i) * lda + o + t] * col[t];
-          col[i] = i < lane ? TI(0) : x / (TI)A[(o + i) * lda + o + i];
+            if (t >= lane && t < i) x -= li[t] * col[t];
+          col[i] = i < lane ? T(0) : x * xdg[o + i];
         }
       }
 #pragma unroll
       for (int i = 0; i < NB; ++i)
-        if (i < w) X[(o + i) * lda + o + lane] = col[i];
+        if (i < w) {
+          X[(o + i) * lda + o + lane] = col[i];
+          if (i >= lane) Rinv_t[(int64_t)(o + lane) * r + o + i] = col[i];  // Rinv_t[j][i] = X[i][j]
+        }
     }
   }
   __syncthreads();
-  // off-diagonal blocks by block diagonal d: S_ij = sum_{j<=t<i} L_it X_tj, then X_ij = -X_ii S_ij.
-  // L is read from A (unchanged since the factorisation); X_tj for t in blocks j .. i-1 lies on
-  // block diagonals below d, finished in earlier steps.
+  // off-diagonal blocks by block diagonal d: S_ij = sum_{j<=t<i} L_it X_tj, then
+  // X_ij = -X_ii S_ij.  L is read from A (unchanged since the factorisation);
+  // X_tj for t in blocks j .. i-1 lies on block diagonals below d, finished in
+  // earlier steps.  Work unit: block q (bi = q + d, bj = q), a slice of its d
+  // sub-blocks of terms (when the diagonal has few blocks), and a 2 x 4 tile
+  // (rows 2 ti, 2 ti + 1; columns 4 tj .. 4 tj + 3).  The slices' partial sums
+  // are added in slice order.
   for (int d = 1; d < nb; ++d) {
     const int nblk = nb - d;
-    for (int e = tid; e < nblk * NB * NB; e += nt) {
-      const int q = e / (NB * NB), rem = e % (NB * NB);
+    int ks = inv_slices<T>() / nblk;
+    ks = ks < 1 ? 1 : (ks > d ? d : ks);
+    const int db = (d + ks - 1) / ks;          // sub-blocks per slice
+    ks = (d + db - 1) / db;
+    for (int u = tid; u < nblk * ks * 32; u += nt) {
+      const int q = u / (ks * 32), sl = (u >> 5) % ks, tl = u & 31;
       const int bi = q + d, bj = q;
-      const int pi = rem / NB, pj = rem % NB;
-      const int i = bi * NB + pi, j = bj * NB + pj;
-      TI s0 = TI(0), s1 = TI(0), s2 = TI(0), s3 = TI(0);
-      if (i < r && j < r) {
-        for (int t = bj * NB; t < bi * NB; t += 4) {  // d * NB terms, a multiple of 4
-          s0 += (TI)A[i * lda + t] * X[t * lda + j];
-          s1 += (TI)A[i * lda + t + 1] * X[(t + 1) * lda + j];
-          s2 += (TI)A[i * lda + t + 2] * X[(t + 2) * lda + j];
-          s3 += (TI)A[i * lda + t + 3] * X[(t + 3) * lda + j];
+      const int pi = 2 * (tl >> 2), pj = 4 * (tl & 3);
+      const int i0 = bi * NB + pi, j0 = bj * NB + pj;
+      const bool r0 = i0 < r, r1 = i0 + 1 < r;
+      const int t0 = (bj + sl * db) * NB, t1 = (bj + min(d, (sl + 1) * db)) * NB;
+      T acc[2][4] = {};
+#pragma unroll 4
+      for (int t = t0; t < t1; ++t) {
+        const T a0 = r0 ? A[i0 * lda + t] : T(0);
+        const T a1 = r1 ? A[(i0 + 1) * lda + t] : T(0);
+        T xv[4];
+#pragma unroll
+        for (int h = 0; h < 4 / E; ++h) {
+          const Vec16<T> y = ld16(X + t * lda + j0 + E * h);
+#pragma unroll
+          for (int e = 0; e < E; ++e) xv[E * h + e] = y.v[e];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[0][c] += a0 * xv[c];
+          acc[1][c] += a1 * xv[c];
         }
       }
-      S[q * NB * NB + rem] = (s0 + s1) + (s2 + s3);
+      T* Sq = S + (q * ks + sl) * NB * NB;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        Sq[pi * NB + pj + c] = acc[0][c];
+        Sq[(pi + 1) * NB + pj + c] = acc[1][c];
+      }
     }
     __syncthreads();
-    for (int e = tid; e < nblk * NB * NB; e += nt) {
-      const int q = e / (NB * NB), rem = e % (NB * NB);
+    if (ks > 1) {
+      for (int e = tid; e < nblk * NB * NB; e += nt) {
+        const int q = e / (NB * NB), o = e % (NB * NB);
+        T* Sq = S + q * ks * NB * NB + o;
+        T sum = Sq[0];
+        for (int sl = 1; sl < ks; ++sl) sum += Sq[sl * NB * NB];
+        Sq[0] = sum;
+      }
+      __syncthreads();
+    }
+    for (int u = tid; u < nblk * 32; u += nt) {
+      const int q = u >> 5, tl = u & 31;
       const int bi = q + d, bj = q;
-      const int pi = rem / NB, pj = rem % NB;
-      const int i = bi * NB + pi, j = bj * NB + pj;
-      if (i < r && j < r) {
-        TI x = TI(0);
-        for (int s2 = 0; s2 <= pi; ++s2) x -= X[i * lda + bi * NB + s2] * S[q * NB * NB + s2 * NB + pj];
-        X[i * lda + j] = x;
+      const int pi = 2 * (tl >> 2), pj = 4 * (tl & 3);
+      const int i0 = bi * NB + pi, j0 = bj * NB + pj;
+      const T* Sq = S + q * ks * NB * NB;
+      T acc[2][4] = {};
+#pragma unroll
+      for (int s2 = 0; s2 < NB; ++s2) {
+        const int t = bi * NB + s2;   // X_ii is zero above its diagonal and outside r
+        const T x0 = i0 < r && t < r ? X[i0 * lda + t] : T(0);
+        const T x1 = i0 + 1 < r && t < r ? X[(i0 + 1) * lda + t] : T(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const T sv = Sq[s2 * NB + pj + c];
+          acc[0][c] -= x0 * sv;
+          acc[1][c] -= x1 * sv;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (i0 < r) {
+          X[i0 * lda + j0 + c] = acc[0][c];
+          Rinv_t[(int64_t)(j0 + c) * r + i0] = acc[0][c];
+        }
+        if (i0 + 1 < r) {
+          X[(i0 + 1) * lda + j0 + c] = acc[1][c];
+          Rinv_t[(int64_t)(j0 + c) * r + i0 + 1] = acc[1][c];
+        }
       }
     }
     __syncthreads();
   }
-  for (int j = warp; j < r; j += nwarps)  // Rinv_t[j][i] = X[i][j]
-    for (int i = lane; i < r; i += 32) Rinv_t[(int64_t)j * r + i] = i >= j ? X[i * lda + j] : TI(0);
 }
-
 
 // R = R2 R1 with R1 = L1^T, R2 = L2^T (both upper triangular).  A dead pivot l
 // of the first sweep carries no part of Y (its column was a negligible
@@ -357,17 +548,17 @@ double pivot_tau<float>() { return 1e-5; }
 // that receives Rinv.
 template <typename T>
 rsvd_status chol_inv(int r, const OrthWs& ws, T* L, int* dead, double tau, cudaStream_t stream) {
-  const size_t fused = fused_smem_bytes<T, T>(r);
+  const size_t fused = fused_smem_bytes<T>(r);
   const bool in_smem = fused <= kFusedSmemMax;
-  if (!in_smem && !(ws.chol_scratch && ws.chol_scratch_bytes >= fused_big_bytes<T, T>(r)))
+  if (!in_smem && !(ws.chol_scratch && ws.chol_scratch_bytes >= fused_big_bytes<T>(r)))
     return fail(RSVD_ERR_INVALID_ARG, "orth: workspace lacks the factorisation scratch for this r");
   static bool fattr = false;
   if (!fattr) {
-    RSVD_CUDA(cudaFuncSetAttribute(chol_inv_fused_kernel<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    RSVD_CUDA(cudaFuncSetAttribute(chol_inv_fused_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kFusedSmemMax));
     fattr = true;
   }
-  chol_inv_fused_kernel<T, T><<<1, kFusedThreads, in_smem ? fused : fused_small_bytes<T>(r), stream>>>(
+  chol_inv_fused_kernel<T><<<1, kFusedThreads, in_smem ? fused : fused_small_bytes<T>(r), stream>>>(
       r, ws.G, L, dead, tau, ws.status, static_cast<T*>(ws.Rinv_t),
       in_smem ? nullptr : static_cast<unsigned char*>(ws.chol_scratch));
   RSVD_CUDA(after_launch());
@@ -380,8 +571,8 @@ namespace {
 // global scratch for the blocked factorisation when r is too large for shared
 // memory (sized for FP64, which covers FP32)
 size_t chol_scratch_bytes(int r) {
-  if (fused_smem_bytes<double, double>(r) <= kFusedSmemMax) return 0;
-  return fused_big_bytes<double, double>(r);
+  if (fused_smem_bytes<double>(r) <= kFusedSmemMax) return 0;
+  return fused_big_bytes<double>(r);
 }
 
 size_t tc_orth_ws(int64_t M, int r) {
