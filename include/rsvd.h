@@ -330,7 +330,9 @@ rsvd_status rsvd_orth(int32_t dtype, int64_t M, int32_t r, const void* Y, int64_
  * Demmel & Veselic) of a device FP64 square matrix, given column-major as Mc
  * (column c at Mc + c*r, r <= 256): Mc W = U diag(sigma).  Outputs (device,
  * FP64): sigma (r, descending), U and W as r x r row-major with the columns
- * ordered like sigma.  Needs `ws_bytes` >= rsvd_small_svd_workspace(r).
+ * ordered like sigma, each pair (U_c, W_c) signed so that the entry of W_c
+ * largest in magnitude is positive.  Needs `ws_bytes` >=
+ * rsvd_small_svd_workspace(r).
  * Errors: NO_CONVERGE, TIMEOUT.  Synchronises `stream`. */
 size_t rsvd_small_svd_workspace(int32_t r);
 rsvd_status rsvd_small_svd(int32_t r, const double* Mc, double* sigma, double* U, double* W,
@@ -382,8 +384,10 @@ rsvd_status rsvd_fp8_quantize(const rsvd_matrix* A, int64_t qm, int64_t qn, uint
  * or latency-sensitive code that must not let cudaMalloc/cudaFree synchronise
  * the device -- and therefore cannot provide the workspace rsvd_small_svd
  * takes.  Same arguments and results as rsvd_small_svd, minus the workspace;
- * it calls no allocation routine.  Its scratch is one static device array of
- * about 1 MiB (two RSVD_NOALLOC_MAX_R^2 FP64 matrices plus a few words) that
+ * it calls no allocation routine, and runs the same phases as rsvd_small_svd
+ * (so both give the same results).  Its scratch is one static device array of
+ * about 19 MiB (rsvd_small_svd's workspace at r = RSVD_NOALLOC_MAX_R: 38
+ * FP64 and one FP32 RSVD_NOALLOC_MAX_R^2 matrices plus a few words) that
  * every GPU loading this library keeps until the process exits.  The first
  * call on a device looks up that array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture.  Every call uses the same

@@ -247,7 +247,10 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
   }
   if (!converged) dev_set_status(status, DEV_NO_CONVERGE);
   if (tid == 0) *sweeps_out = sweep + (converged ? 1 : 0);
-  // column norms, stable descending order, normalised outputs (sh: sigma_c for c < r)
+  // column norms, stable descending order, normalised outputs (sh: sigma_c for
+  // c < r).  Signs: each pair of columns (U_c, W_c) is turned so that the entry
+  // of W_c largest in magnitude (the first such) is positive, so that the
+  // output does not depend on the path the sweeps took.
   for (int c = tid; c < r; c += nthr) {
     double s2 = 0.0;
     for (int i = 0; i < rows; ++i) { const double x = __ldcg(&M[(int64_t)c * rows + i]); s2 += x * x; }
@@ -259,10 +262,110 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
     int rank = 0;
     for (int d = 0; d < r; ++d) rank += (sh[d] > sc) || (sh[d] == sc && d < c);
     sigma[rank] = sc;
-    const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+    double wmax = -1.0, wsgn = 1.0;
+    for (int i = 0; i < r; ++i) {
+      const double x = __ldcg(&W[(int64_t)c * r + i]);
+      if (fabs(x) > wmax) { wmax = fabs(x); wsgn = x < 0.0 ? -1.0 : 1.0; }
+    }
+    const double inv = sc > 0.0 ? wsgn / sc : 0.0;
     for (int i = 0; i < rows; ++i) Uout[(int64_t)i * r + rank] = __ldcg(&M[(int64_t)c * rows + i]) * inv;
-    for (int i = 0; i < r; ++i) Wout[(int64_t)i * r + rank] = __ldcg(&W[(int64_t)c * r + i]);
+    for (int i = 0; i < r; ++i) Wout[(int64_t)i * r + rank] = wsgn * __ldcg(&W[(int64_t)c * r + i]);
   }
+}
+
+// FP32 first phase for r too large for one CTA's shared memory: the same
+// round-robin sweeps as jacobi_cluster_kernel in FP32, with the columns of M
+// (rows x r) and W (r x r) in global memory.  It stops once the largest
+// relative off-diagonal rotated in a sweep, squared, is below r eps32 (the next
+// sweep would leave only FP32 rounding; the FP64 phase finishes from there).
+constexpr int kF32ClusterPerLane = 16;  // rows <= 512 in registers
+
+__global__ void jacobi_cluster_f32_kernel(int rows, int r, const double* __restrict__ Min, float* M, float* W,
+                                          int* rotated, int* sweeps_out) {
+  __shared__ float red[32];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, warps = nthr >> 5;
+  const int rp = r + (r & 1);
+  const int npairs = rp / 2;
+  const int64_t mm = (int64_t)rows * r;
+  const int64_t ww = (int64_t)r * r;
+  const int64_t gtid = (int64_t)blockIdx.x * nthr + tid, gstride = (int64_t)gridDim.x * nthr;
+  for (int64_t e = gtid; e < mm; e += gstride) __stcg(&M[e], (float)Min[e]);
+  for (int64_t e = gtid; e < ww; e += gstride) __stcg(&W[e], (e / r) == (e % r) ? 1.f : 0.f);
+  float f = 0.f;
+  for (int64_t e = tid; e < mm; e += nthr) { const float v = (float)Min[e]; f = fmaf(v, v, f); }
+  f = warp_sum(f);
+  if (lane == 0) red[warp] = f;
+  __syncthreads();
+  float fro2 = 0.f;
+  for (int i = 0; i < warps; ++i) fro2 += red[i];
+  const float eps = 1.1920929e-7f;
+  const float big = (float)(rows > r ? rows : r);
+  const float zero2 = (big * eps) * (big * eps) * fro2;
+  const float tol = (float)r * eps;
+  cluster_sync_all();
+
+  int sweep = 0;
+  const int s = blockIdx.x * warps + warp;  // this warp's pair slot
+  for (; sweep < kJacobiMaxSweeps; ++sweep) {
+    bool my_rot = false;
+    float my_mrel = 0.f;
+    for (int round = 0; round < rp - 1; ++round) {
+      if (s < npairs) {
+        int p = rr_column(s, round, rp), q = rr_column(rp - 1 - s, round, rp);
+        if (p < r && q < r) {
+          if (p > q) { const int t = p; p = q; q = t; }
+          float* mp = M + (int64_t)p * rows;
+          float* mq = M + (int64_t)q * rows;
+          float* wp = W + (int64_t)p * r;
+          float* wq = W + (int64_t)q * r;
+          float xv[kF32ClusterPerLane], yv[kF32ClusterPerLane];
+          float a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+          for (int t = 0; t < kF32ClusterPerLane; ++t) {
+            const int i = lane + 32 * t;
+            xv[t] = i < rows ? __ldcg(&mp[i]) : 0.f;
+            yv[t] = i < rows ? __ldcg(&mq[i]) : 0.f;
+            a = fmaf(xv[t], xv[t], a); b = fmaf(yv[t], yv[t], b); g = fmaf(xv[t], yv[t], g);
+          }
+          a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
+          if (fabsf(g) > tol * sqrtf(a * b) && a > zero2 && b > zero2) {
+            my_rot = true;
+            my_mrel = fmaxf(my_mrel, fabsf(g) * rsqrtf(a * b));
+            const float zeta = (b - a) / (2.f * g);
+            const float az = fabsf(zeta);
+            const float t = az > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(fmaf(zeta, zeta, 1.f)));
+            const float x = fmaf(t, t, 1.f);
+            float c = rsqrtf(x);
+            c = c * fmaf(-0.5f * x, c * c, 1.5f);
+            const float sn = c * t;
+#pragma unroll
+            for (int u = 0; u < kF32ClusterPerLane; ++u) {
+              const int i = lane + 32 * u;
+              if (i < rows) {
+                __stcg(&mp[i], c * xv[u] - sn * yv[u]);
+                __stcg(&mq[i], sn * xv[u] + c * yv[u]);
+              }
+              if (i < r) {
+                const float wu = __ldcg(&wp[i]), wv = __ldcg(&wq[i]);
+                __stcg(&wp[i], c * wu - sn * wv);
+                __stcg(&wq[i], sn * wu + c * wv);
+              }
+            }
+          }
+        }
+      }
+      if (round == rp - 2 && lane == 0 && my_rot) {
+        atomicMax(&rotated[2 * kJacobiMaxSweeps + sweep], __float_as_int(my_mrel));
+        __stcg(&rotated[sweep], 1);
+      }
+      cluster_sync_all();
+    }
+    if (__ldcg(&rotated[sweep]) == 0) { ++sweep; break; }
+    const float mrel = __int_as_float(__ldcg(&rotated[2 * kJacobiMaxSweeps + sweep]));
+    if (mrel * mrel <= tol) { ++sweep; break; }
+  }
+  if (blockIdx.x == 0 && tid == 0) *sweeps_out = sweep;
 }
 
 // FP32 one-sided Jacobi in one CTA with M and W in shared memory: the cheap
@@ -555,29 +658,74 @@ rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const doub
   }
 }
 
+// Phase 1 for 160 < r <= 512: FP32 sweeps over a cluster (up to 16 CTAs, one
+// warp per pair), with M staged in the FP64 phase's working buffer.
+rsvd_status launch_cluster_f32(int r, const double* Mc, const JacobiWs& ws, cudaStream_t stream) {
+  RSVD_CUDA(cudaMemsetAsync(ws.rotated, 0, 3 * kJacobiMaxSweeps * sizeof(int), stream));
+  const int npairs = (r + (r & 1)) / 2;
+  int ncta = (int)cdiv(npairs, 4);
+  if (ncta > 16) ncta = 16;
+  static bool attr_set = false;
+  if (!attr_set) {
+    RSVD_CUDA(cudaFuncSetAttribute(jacobi_cluster_f32_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    attr_set = true;
+  }
+  for (;;) {
+    const int warps = (int)cdiv(npairs, ncta);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ncta);
+    cfg.blockDim = dim3(32 * warps);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ncta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    const cudaError_t qe = cudaOccupancyMaxActiveClusters(&clusters, jacobi_cluster_f32_kernel, &cfg);
+    if ((qe != cudaSuccess || clusters < 1) && ncta > 1) {
+      (void)cudaGetLastError();
+      ncta = ncta > 8 ? 8 : ncta / 2;
+      continue;
+    }
+    RSVD_CUDA(cudaLaunchKernelEx(&cfg, jacobi_cluster_f32_kernel, r, r, Mc, reinterpret_cast<float*>(ws.M), ws.W32,
+                                 ws.rotated, ws.sweeps));
+    RSVD_CUDA(after_launch());
+    return RSVD_OK;
+  }
+}
+
 }  // namespace
 
 rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double* U, double* W,
                        const JacobiWs& ws, cudaStream_t stream, double tol, bool fp64_sweeps) {
   if (r <= 0) return RSVD_OK;
   if (!(tol > 0.0)) tol = (double)r * 2.220446049250313e-16;  // r eps: the FP64 stopping test
-  if (rows != r || r > kF32MaxR || r < 8 || !ws.W32)
+  if (rows != r || r > 32 * kF32ClusterPerLane || r < 8 || !ws.W32)
     return launch_cluster_jacobi(rows, r, Mc, nullptr, sigma, U, W, ws, stream, tol);
-  // Phase 1: FP32 sweeps to FP32 convergence, one CTA, shared memory.
-  static bool attr = false;
-  if (!attr) {
-    const int mx = (int)f32_jacobi_smem(kF32MaxR);
-    RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    attr = true;
+  // Phase 1: FP32 sweeps to FP32 convergence -- one CTA with M and W in shared
+  // memory, or for r > 160 a cluster with them in global memory.
+  if (r > kF32MaxR) {
+    RSVD_TRY(launch_cluster_f32(r, Mc, ws, stream));
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      const int mx = (int)f32_jacobi_smem(kF32MaxR);
+      RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      attr = true;
+    }
+    // float4s per lane and column: ceil(ceil(r / 4) / 16)
+    const int V = (int)cdiv(cdiv(r, 4), 16);
+    if (V <= 1) jacobi_f32_kernel<1><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
+    else if (V == 2) jacobi_f32_kernel<2><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
+    else jacobi_f32_kernel<3><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
+    RSVD_CUDA(after_launch());
   }
-  // float4s per lane and column: ceil(ceil(r / 4) / 16)
-  const int V = (int)cdiv(cdiv(r, 4), 16);
-  if (V <= 1) jacobi_f32_kernel<1><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
-  else if (V == 2) jacobi_f32_kernel<2><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
-  else jacobi_f32_kernel<3><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
-  RSVD_CUDA(after_launch());
   // Phase 2: Newton-Schulz steps make W orthogonal to FP64 accuracy:
   // W' = (1.5 I - 0.5 W W^T) W, i.e. on the column-major storage (= W^T row-major)
   // Wt' = Wt (1.5 I - 0.5 P) with P = Wt^T Wt.  The accumulated FP32 rotation

@@ -45,7 +45,8 @@ struct OrthWs {
   double* L2 = nullptr;
   int* dead1 = nullptr;       // deflated pivots of the two sweeps (r each)
   int* dead2 = nullptr;
-  void* Rinv_t = nullptr;     // the same in the panel dtype
+  void* Rinv_t = nullptr;     // R^-1 = L^-T (upper) in the panel dtype, row stride ld_rt
+  int ld_rt = 0;              // r rounded up to 4 (16-byte rows for the vector loads of the products)
   void* gram_partial = nullptr;     // chunk partial Grams in the panel type
   int64_t gram_chunks = 0;
   void* tmp = nullptr;        // M x r panel (first-sweep result)
@@ -88,7 +89,8 @@ constexpr int kJacobiMaxSweeps = 64;
 size_t jacobi_ws_bytes(int64_t rows, int r, bool precondition = true);
 JacobiWs jacobi_ws_carve(Carver& c, int64_t rows, int r, bool precondition = true);
 // Mc column-major rows x r; outputs sigma (r), U (rows x r) and W (r x r)
-// row-major with columns ordered like sigma (descending).
+// row-major with columns ordered like sigma (descending), each pair (U_c, W_c)
+// signed so that the entry of W_c largest in magnitude is positive.
 // tol: relative off-diagonal stopping test |c_ij| <= tol sqrt(c_ii c_jj) (0: r eps, FP64)
 // fp64_sweeps = false (square inputs with the FP32 phase only): stop at FP32
 // convergence (tol = r eps32) and form the outputs from the FP64 product M W.

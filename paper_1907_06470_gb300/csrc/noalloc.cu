@@ -20,9 +20,14 @@ namespace rsvd {
 namespace {
 
 constexpr int kMaxR = RSVD_NOALLOC_MAX_R;
-// M and W (kMaxR^2 doubles each) plus the barrier, per-sweep flags, sweep
-// count and status words, each carve rounded to 256 bytes.
-constexpr size_t kScratchBytes = 2 * (size_t)kMaxR * kMaxR * sizeof(double) + 4096;
+// The same workspace as rsvd_small_svd at r = kMaxR, so that both entry points
+// run the same phases: M and W (kMaxR^2 doubles each), the FP32 rotations
+// (kMaxR^2 floats), the FP64 rotations, Newton-Schulz and product buffers
+// (4 kMaxR^2 doubles), the split-K partials of the small GEMMs (32 kMaxR^2
+// doubles), and the barrier, per-sweep flags, sweep count and status words;
+// each carve rounded to 256 bytes.
+constexpr size_t kScratchBytes =
+    (2 + 4 + 32) * (size_t)kMaxR * kMaxR * sizeof(double) + (size_t)kMaxR * kMaxR * sizeof(float) + 8192;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -61,7 +66,7 @@ extern "C" rsvd_status rsvd_small_svd_noalloc(int32_t r, const double* Mc, doubl
   void* base = nullptr;
   RSVD_TRY(scratch_address(&base));
   Carver c(base, kScratchBytes);
-  JacobiWs w = jacobi_ws_carve(c, r, r, /*precondition=*/false);
+  JacobiWs w = jacobi_ws_carve(c, r, r);
   if (c.overflow) return fail(RSVD_ERR_INVALID_ARG, "rsvd_small_svd_noalloc: scratch layout overflow");
   cudaStream_t st = as_stream(stream);
   // the status word must start at zero; jacobi_svd clears the barrier and flags

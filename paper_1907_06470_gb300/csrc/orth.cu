@@ -185,7 +185,7 @@ __device__ __forceinline__ void factor_diag_block(T* A, int lda, int p, int w, c
 template <typename T>
 __global__ void __launch_bounds__(kFusedThreads, 1)
 chol_inv_fused_kernel(int r, const double* __restrict__ G, T* __restrict__ Lout, int* __restrict__ dead,
-                      double tau, int* status, T* __restrict__ Rinv_t, unsigned char* gscratch) {
+                      double tau, int* status, T* __restrict__ Rinv_t, int ldr, unsigned char* gscratch) {
   extern __shared__ __align__(16) unsigned char fsm[];
   constexpr int NB = kCholB;
   constexpr int E = Vec16<T>::E;       // entries per 16 bytes
@@ -227,7 +227,7 @@ chol_inv_fused_kernel(int r, const double* __restrict__ G, T* __restrict__ Lout,
     for (int i = warp; i < r; i += nwarps)
       for (int j = lane; j < r; j += 32) {
         if (j > i) Lout[(int64_t)i * r + j] = T(0);
-        else if (j < i) Rinv_t[(int64_t)i * r + j] = T(0);
+        else if (j < i) Rinv_t[(int64_t)i * ldr + j] = T(0);
       }
   }
   __syncthreads();
@@ -361,7 +361,7 @@ chol_inv_fused_kernel(int r, const double* __restrict__ G, T* __restrict__ Lout,
       for (int i = 0; i < NB; ++i)
         if (i < w) {
           X[(o + i) * lda + o + lane] = col[i];
-          if (i >= lane) Rinv_t[(int64_t)(o + lane) * r + o + i] = col[i];  // Rinv_t[j][i] = X[i][j]
+          if (i >= lane) Rinv_t[(int64_t)(o + lane) * ldr + o + i] = col[i];  // Rinv_t[j][i] = X[i][j]
         }
     }
   }
@@ -445,11 +445,11 @@ chol_inv_fused_kernel(int r, const double* __restrict__ G, T* __restrict__ Lout,
       for (int c = 0; c < 4; ++c) {
         if (i0 < r) {
           X[i0 * lda + j0 + c] = acc[0][c];
-          Rinv_t[(int64_t)(j0 + c) * r + i0] = acc[0][c];
+          Rinv_t[(int64_t)(j0 + c) * ldr + i0] = acc[0][c];
         }
         if (i0 + 1 < r) {
           X[(i0 + 1) * lda + j0 + c] = acc[1][c];
-          Rinv_t[(int64_t)(j0 + c) * r + i0 + 1] = acc[1][c];
+          Rinv_t[(int64_t)(j0 + c) * ldr + i0 + 1] = acc[1][c];
         }
       }
     }
@@ -559,7 +559,7 @@ rsvd_status chol_inv(int r, const OrthWs& ws, T* L, int* dead, double tau, cudaS
     fattr = true;
   }
   chol_inv_fused_kernel<T><<<1, kFusedThreads, in_smem ? fused : fused_small_bytes<T>(r), stream>>>(
-      r, ws.G, L, dead, tau, ws.status, static_cast<T*>(ws.Rinv_t),
+      r, ws.G, L, dead, tau, ws.status, static_cast<T*>(ws.Rinv_t), ws.ld_rt,
       in_smem ? nullptr : static_cast<unsigned char*>(ws.chol_scratch));
   RSVD_CUDA(after_launch());
   return RSVD_OK;
@@ -596,7 +596,7 @@ size_t orth_ws_bytes(int64_t M, int r, int dtype, bool tc) {
   const size_t esz = dtype == RSVD_F64 ? 8 : 4;
   s.take<double>((size_t)r * r * 3);
   s.take<int>((size_t)2 * r);
-  s.take<char>((size_t)r * r * esz);
+  s.take<char>((size_t)r * round_up(r, 4) * esz);
   s.take<char>((size_t)gram_chunks(M) * r * r * esz);
   s.take<char>((size_t)M * round_up(r, 4) * esz);
   s.take<int>(4);
@@ -615,7 +615,8 @@ OrthWs orth_ws_carve(Carver& c, int64_t M, int r, int dtype, bool tc) {
   if (base) { w.G = base; w.L1 = base + r * r; w.L2 = base + 2 * r * r; }
   int* dd = c.take<int>((size_t)2 * r);
   if (dd) { w.dead1 = dd; w.dead2 = dd + r; }
-  w.Rinv_t = c.take<char>((size_t)r * r * esz);
+  w.ld_rt = (int)round_up(r, 4);
+  w.Rinv_t = c.take<char>((size_t)r * w.ld_rt * esz);
   w.gram_partial = c.take<char>((size_t)gram_chunks(M) * r * r * esz);
   w.gram_chunks = gram_chunks(M);
   w.ld_tmp = round_up(r, 4);
@@ -649,7 +650,7 @@ rsvd_status panel_times_tc(int64_t M, int r, const float* Y, int64_t ldy, const 
   rsvd_matrix A = {};
   A.kind = RSVD_DENSE; A.dtype = RSVD_F32; A.location = RSVD_ON_DEVICE;
   A.m = M; A.n = r; A.data = Y; A.ld = ldy;
-  return tc_apass_from_f32(A, 0, RSVD_PREC_BF16X3, r, Rt, r, Q, ldq, 0, 0, ws.tc_ws, ws.tc_ws_bytes, ws.status,
+  return tc_apass_from_f32(A, 0, RSVD_PREC_BF16X3, r, Rt, ws.ld_rt, Q, ldq, 0, 0, ws.tc_ws, ws.tc_ws_bytes, ws.status,
                            stream);
 }
 
@@ -684,7 +685,7 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
   RSVD_TRY(gram<T>(M, r, Y, ldy, ws, stream));
   T* L1 = reinterpret_cast<T*>(ws.L1);
   RSVD_TRY(chol_inv<T>(r, ws, L1, ws.dead1, pivot_tau<T>(), stream));
-  RSVD_TRY(simt_gemm<T>(M, r, r, Y, ldy, false, Rt, r, Q1, ws.ld_tmp, false, 1, r, nullptr, stream));
+  RSVD_TRY(simt_gemm<T>(M, r, r, Y, ldy, false, Rt, ws.ld_rt, Q1, ws.ld_tmp, false, 1, r, nullptr, stream));
   RSVD_TRY(fill_dead_columns(M, r, ws.dead1, Q1, ws.ld_tmp, sizeof(T) == 8 ? RSVD_F64 : RSVD_F32,
                              kDeadFillSeed, stream));
   // sweep 2
@@ -693,7 +694,7 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
   RSVD_TRY(chol_inv<T>(r, ws, L2, ws.dead2, pivot_tau<T>(), stream));
   check_dead_kernel<<<1, 256, 0, stream>>>(r, ws.dead2, ws.status);
   RSVD_CUDA(after_launch());
-  RSVD_TRY(simt_gemm<T>(M, r, r, Q1, ws.ld_tmp, false, Rt, r, Q, ldq, false, 1, r, nullptr, stream));
+  RSVD_TRY(simt_gemm<T>(M, r, r, Q1, ws.ld_tmp, false, Rt, ws.ld_rt, Q, ldq, false, 1, r, nullptr, stream));
   if (R) {
     rprod_kernel<T, T><<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r, L1, ws.dead1, L2, R);
     RSVD_CUDA(after_launch());
