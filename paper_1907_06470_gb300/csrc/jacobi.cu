@@ -71,7 +71,7 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
                                       int* sweeps_out, int* status, double* sigma, double* Uout, double* Wout,
                                       int check, double tol, int max_sweeps) {
   __shared__ double red[32];
-  extern __shared__ double sh[];  // check pass: M staged (rows x r) + column norms (r); end: sigma_c
+  extern __shared__ double sh[];  // check pass: M staged (rows x r) + column norms (r); end: sigma_c, signs
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, warps = nthr >> 5;
   const int ncta = gridDim.x;
@@ -83,9 +83,11 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
 
   for (int64_t e = gtid; e < mm; e += gstride) __stcg(&M[e], Min[e]);
   for (int64_t e = gtid; e < ww; e += gstride) __stcg(&W[e], W0 ? W0[e] : ((e / r) == (e % r) ? 1.0 : 0.0));
-  // Frobenius norm of the input (every CTA computes it), for the rounding-level column test
+  // Frobenius norm of the input (every CTA computes it), for the rounding-level
+  // column test of the sweeps (none in the finish-only mode)
   double f = 0.0;
-  for (int64_t e = tid; e < mm; e += nthr) f += Min[e] * Min[e];
+  if (max_sweeps > 0)
+    for (int64_t e = tid; e < mm; e += nthr) f += Min[e] * Min[e];
   f = warp_sum_d(f);
   if (lane == 0) red[warp] = f;
   __syncthreads();
@@ -247,29 +249,45 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
   }
   if (!converged) dev_set_status(status, DEV_NO_CONVERGE);
   if (tid == 0) *sweeps_out = sweep + (converged ? 1 : 0);
-  // column norms, stable descending order, normalised outputs (sh: sigma_c for
-  // c < r).  Signs: each pair of columns (U_c, W_c) is turned so that the entry
-  // of W_c largest in magnitude (the first such) is positive, so that the
-  // output does not depend on the path the sweeps took.
-  for (int c = tid; c < r; c += nthr) {
+  // column norms, stable descending order, normalised outputs.  Signs: each
+  // pair of columns (U_c, W_c) is turned so that the entry of W_c largest in
+  // magnitude (the first such) is positive, so that the output does not depend
+  // on the path the sweeps took.  One warp per column (sh: sigma_c, then the
+  // signs at sh + r).
+  double* sgn = sh + r;
+  for (int c = warp; c < r; c += warps) {
     double s2 = 0.0;
-    for (int i = 0; i < rows; ++i) { const double x = __ldcg(&M[(int64_t)c * rows + i]); s2 += x * x; }
-    sh[c] = sqrt(s2);
+    for (int i = lane; i < rows; i += 32) { const double x = __ldcg(&M[(int64_t)c * rows + i]); s2 = fma(x, x, s2); }
+    s2 = warp_sum_d(s2);
+    double wm = -1.0;
+    int wi = r;
+    for (int i = lane; i < r; i += 32) {
+      const double x = fabs(__ldcg(&W[(int64_t)c * r + i]));
+      if (x > wm) { wm = x; wi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double om = __shfl_xor_sync(0xffffffffu, wm, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, wi, o);
+      if (om > wm || (om == wm && oi < wi)) { wm = om; wi = oi; }
+    }
+    if (lane == 0) {
+      sh[c] = sqrt(s2);
+      sgn[c] = wi < r && __ldcg(&W[(int64_t)c * r + wi]) < 0.0 ? -1.0 : 1.0;
+    }
   }
   __syncthreads();
-  for (int c = tid; c < r; c += nthr) {
+  for (int c = warp; c < r; c += warps) {
     const double sc = sh[c];
-    int rank = 0;
-    for (int d = 0; d < r; ++d) rank += (sh[d] > sc) || (sh[d] == sc && d < c);
-    sigma[rank] = sc;
-    double wmax = -1.0, wsgn = 1.0;
-    for (int i = 0; i < r; ++i) {
-      const double x = __ldcg(&W[(int64_t)c * r + i]);
-      if (fabs(x) > wmax) { wmax = fabs(x); wsgn = x < 0.0 ? -1.0 : 1.0; }
-    }
-    const double inv = sc > 0.0 ? wsgn / sc : 0.0;
-    for (int i = 0; i < rows; ++i) Uout[(int64_t)i * r + rank] = __ldcg(&M[(int64_t)c * rows + i]) * inv;
-    for (int i = 0; i < r; ++i) Wout[(int64_t)i * r + rank] = wsgn * __ldcg(&W[(int64_t)c * r + i]);
+    int cnt = 0;
+    for (int d = lane; d < r; d += 32) cnt += (sh[d] > sc) || (sh[d] == sc && d < c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    const int rank = cnt;
+    if (lane == 0) sigma[rank] = sc;
+    const double inv = sc > 0.0 ? sgn[c] / sc : 0.0;
+    for (int i = lane; i < rows; i += 32) Uout[(int64_t)i * r + rank] = __ldcg(&M[(int64_t)c * rows + i]) * inv;
+    for (int i = lane; i < r; i += 32) Wout[(int64_t)i * r + rank] = sgn[c] * __ldcg(&W[(int64_t)c * r + i]);
   }
 }
 
@@ -621,8 +639,11 @@ rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const doub
   if (ncta < 1) ncta = 1;
   // the check pass stages M in shared memory when it fits
   const size_t check_bytes = ((size_t)rows * r + r) * sizeof(double);
-  const int check = check_bytes <= (size_t)kClusterCheckSmem ? 1 : 0;
-  const size_t smem = check ? check_bytes : (size_t)r * sizeof(double);
+  const int check = max_sweeps > 0 && check_bytes <= (size_t)kClusterCheckSmem ? 1 : 0;
+  const size_t smem = check ? check_bytes : 2 * (size_t)r * sizeof(double);
+  // finish only (no sweeps): one CTA of 16 warps forms the outputs (the
+  // kernel's register use allows 512 threads)
+  if (max_sweeps == 0) ncta = 1;
   static bool attr_set = false;
   if (!attr_set) {
     RSVD_CUDA(cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -631,7 +652,7 @@ rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const doub
     attr_set = true;
   }
   for (;;) {
-    const int warps = (int)cdiv(npairs, ncta);
+    const int warps = max_sweeps == 0 ? 16 : (int)cdiv(npairs, ncta);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ncta);
     cfg.blockDim = dim3(32 * warps);
