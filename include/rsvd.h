@@ -128,6 +128,7 @@ typedef struct {
   uint64_t seed;
   int32_t q_used;            /* power iterations applied by the last rsvd_run */
   int32_t resumed_from;      /* checkpoint step the last rsvd_run resumed after; -1: none */
+  int32_t bf16_copy;         /* 1: the last rsvd_run's later BF16 passes read a BF16 copy of A */
 } rsvd_plan_info_t;
 
 /* Header of a checkpoint file (rsvd_plan_set_checkpoint). */
@@ -179,6 +180,11 @@ rsvd_status rsvd_plan_info(rsvd_plan_t plan, rsvd_plan_info_t* out);
  * rest of the cap stay resident for the later passes of the run (Section 3.5,
  * Section 3.7).  Streaming needs A in pinned host memory for the copies to
  * overlap.
+ * BF16 plans processing A in core also keep a BF16 copy of A (2 m
+ * round_up(n, 64) bytes, owned by the plan from the first such run, within the
+ * cap when there is one): the first forward pass writes it and the later
+ * BF16 passes read it (the same operands, so the same result; half the bytes
+ * per pass).  Without room for it every pass reads the FP32 A.
  * Outputs (device, plan dtype): U m x k row-major, S k values descending,
  * V n x k row-major, so that A ~ U diag(S) V^T.  Each pair (u_i, v_i) is signed
  * so that the largest-magnitude entry of u_i is positive.  Synchronises

@@ -45,7 +45,8 @@ class RsvdPlanInfo(C.Structure):
                 ("prec", c_i32), ("dtype", c_i32), ("mb", c_i64), ("nb", c_i64),
                 ("tiles_m", c_i64), ("tiles_n", c_i64), ("n_slots", c_i32), ("resident", c_i32),
                 ("workspace_bytes", c_size), ("min_cap_bytes", c_size), ("seed", c_u64), ("q_used", c_i32),
-                ("resumed_from", c_i32)]
+                ("resumed_from", c_i32),
+                ("bf16_copy", c_i32)]
 
 
 class RsvdCheckpointInfo(C.Structure):

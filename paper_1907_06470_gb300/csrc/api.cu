@@ -213,6 +213,10 @@ struct rsvd_plan_s {
   size_t bwd_ws_bytes = 0;
   int* status = nullptr;
   void* Adev = nullptr;     // device copy of a host-resident A
+  uint16_t* a16 = nullptr;  // BF16 plans in core: BF16 copy of A, written by the first forward pass
+  size_t a16_bytes = 0;
+  int64_t a16_ld = 0;
+  bool a16_ready = false;   // the current run's copy is complete (enqueued)
   int64_t mb_req = 0, nb_req = 0;  // tile edges asked for in the options (0: none)
   StreamState* ss = nullptr;       // out-of-core state (created on the first streamed run)
   bool streaming = false;          // the current run streams A from the host
@@ -355,9 +359,48 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   const int final_prec =
       ((prec == RSVD_PREC_BF16 || prec == RSVD_PREC_FP8) && P->refine) ? RSVD_PREC_BF16X3 : prec;
   Profiler& pf = P->prof;
+  // BF16 plans in core stream a BF16 copy of A after the first plain forward
+  // pass has written it: half the bytes per pass, the same operands.
+  bool use16 = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (prec == RSVD_PREC_BF16 && A.kind == RSVD_DENSE && !P->streaming && round_up(r, 16) <= 256) {
+      const int64_t ld16 = round_up(n, 64);
+      const size_t need = (size_t)m * ld16 * sizeof(uint16_t);
+      const bool fits = P->mem_cap == 0 || P->ws_bytes + P->a_copy_bytes + need <= P->mem_cap;
+      if (fits && P->a16_bytes < need) {
+        if (P->a16) cudaFree(P->a16);
+        P->a16 = nullptr;
+        P->a16_bytes = 0;
+        if (cudaMalloc(reinterpret_cast<void**>(&P->a16), need) == cudaSuccess) {
+          P->a16_bytes = need;
+        } else {
+          (void)cudaGetLastError();  // no room: the passes read the FP32 A (same results)
+          P->a16 = nullptr;
+        }
+      }
+      use16 = fits && P->a16 && P->a16_bytes >= need;
+      P->a16_ld = ld16;
+    }
+  }
+  P->a16_ready = false;
   auto apass = [&](int trans, int pr, const T* Xin, T* Yout) -> rsvd_status {
     Span sp(pf, trans ? RSVD_STAGE_APASS_TRANS : RSVD_STAGE_APASS_FWD, st);
     ++pf.apass_calls;
+    if constexpr (std::is_same<T, float>::value) {
+      if (use16 && pr == RSVD_PREC_BF16) {
+        if (P->a16_ready) {
+          Bf16Source b;
+          b.data = P->a16; b.m = m; b.n = n; b.ld = P->a16_ld;
+          return tc_apass_from_bf16(b, trans, r, Xin, ldr, Yout, ldr, P->apass_ws, P->apass_ws_bytes, P->status, st);
+        }
+        if (!trans) {
+          RSVD_TRY(tc_apass_from_f32(A, 0, RSVD_PREC_BF16, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws,
+                                     P->apass_ws_bytes, P->status, st, false, P->a16, P->a16_ld));
+          P->a16_ready = true;
+          return RSVD_OK;
+        }
+      }
+    }
     if constexpr (std::is_same<T, float>::value) {
       if (A.kind == RSVD_CSR)  // Section 3.3: sparse x dense; A^T through the CSR of A^T
         return trans ? spmm_csr(n, r, A.t_rowptr, A.t_colidx, A.t_val, A.nnz, Xin, ldr, Yout, ldr, false,
@@ -815,6 +858,7 @@ rsvd_status rsvd_plan_info(rsvd_plan_t P, rsvd_plan_info_t* o) {
   o->resident = 1; o->workspace_bytes = P->ws_bytes; o->min_cap_bytes = P->ws_bytes; o->seed = P->seed;
   o->q_used = P->q_used;
   o->resumed_from = P->resumed_from;
+  o->bf16_copy = P->a16_ready ? 1 : 0;
   return RSVD_OK;
 }
 
@@ -857,6 +901,7 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
     }
     if (P->a_copy_bytes < bytes) {
       if (P->Adev) cudaFree(P->Adev);
+  if (P->a16) cudaFree(P->a16);
       P->Adev = nullptr;
       P->a_copy_bytes = 0;
       RSVD_CUDA(cudaMalloc(&P->Adev, bytes));
@@ -925,6 +970,7 @@ void rsvd_destroy(rsvd_plan_t P) {
   if (!P) return;
   if (P->ws) cudaFree(P->ws);
   if (P->Adev) cudaFree(P->Adev);
+  if (P->a16) cudaFree(P->a16);
   if (P->csr_dev) cudaFree(P->csr_dev);
   stream_state_free(P->ss);
   delete P;

@@ -20,9 +20,15 @@
 // Split mode (BF16X3): A = A_hi + A_lo and X = X_hi + X_lo, each part BF16,
 // C = A_hi X_hi + A_hi X_lo + A_lo X_hi, about 16 significant bits per operand.
 //
-// FP8 source (SRC8): A is read as E4M3 codes with one power-of-two scale per
+// FP8 source: A is read as E4M3 codes with one power-of-two scale per
 // block-cyclic tile; the converters decode each code to BF16 times its tile's
 // scale (exact) -- a quarter of the HBM bytes of the FP32 source.
+//
+// BF16 source: A is read as a BF16 copy (half the bytes of FP32); the
+// converters only move (or, for A^T, transpose) the 16-bit values into the
+// operand layout.  The copy is written by the first forward pass over the FP32
+// A, whose converters store the BF16 values they form anyway, so the later
+// passes see exactly the operands the FP32 source would give.
 //
 // Every wait is bounded (about one second of global time); a wait that expires
 // records DEV_TIMEOUT, every role stops issuing work, and the CTA frees its
@@ -47,7 +53,12 @@ constexpr int BK = 64;             // K per step: one 128-byte BF16 row
 constexpr int A32_BYTES = BM * BK * 4;
 constexpr int A8_BYTES = BM * BK;
 constexpr int A16_BYTES = BM * BK * 2;
-constexpr int SOP = 2;             // operand (BF16) ring depth
+// operand (BF16 A + panel) ring depth: a runtime choice of 2 or 4 (4 when the
+// FP32 staging ring keeps at least 3 stages next to it); deeper rings let the
+// panel tiles, which come from L2, be requested further ahead
+constexpr int kMaxSop = 4;
+// source of A: FP32, FP8 (E4M3 codes + tile scales) or a BF16 copy
+constexpr int kSrc32 = 0, kSrc8 = 1, kSrc16 = 2;
 constexpr int kSplitMaxNP = 192;   // widest split-mode panel one pass supports
 constexpr int THREADS = 320;
 constexpr uint64_t kWaitNs = 1000000000ull;
@@ -64,12 +75,15 @@ struct TcArgs {
   int nsplit;
   int accumulate;       // 1: C += result (direct write only, nsplit == 1)
   int s32;              // FP32 staging ring depth
+  int sop;              // operand ring depth (2 or 4)
   float* C;
   int64_t ldc;
   int64_t c_split_stride;
   int* status;
-  const float* qscale;  // SRC8: per-tile scales, qtn per tile row
-  int64_t qm, qn, qtn;  // SRC8: tile edges (in rows / columns of A)
+  const float* qscale;  // FP8 source: per-tile scales, qtn per tile row
+  int64_t qm, qn, qtn;  // FP8 source: tile edges (in rows / columns of A)
+  uint16_t* a16;        // FP32 forward pass: also store BF16(A) here (row stride ld16), or null
+  int64_t ld16;
 };
 
 #ifndef RSVD_TC_MAX_S32
@@ -80,27 +94,36 @@ constexpr int kMaxS32 = RSVD_TC_MAX_S32;  // deepest FP32 staging ring
 // Shared-memory plan: BF16 operand slots (A then panel), then the FP32 staging
 // ring of depth S32 (a runtime choice: as deep as the 227 KB allow), then the
 // barriers and the TMEM address word.
-template <bool SPLIT, bool SRC8 = false>
+template <bool SPLIT, int SRC = kSrc32>
 struct Layout {
   static constexpr int PARTS = SPLIT ? 2 : 1;
-  static constexpr int STAGE_BYTES = SRC8 ? A8_BYTES : A32_BYTES;
+  static constexpr int STAGE_BYTES = SRC == kSrc8 ? A8_BYTES : (SRC == kSrc16 ? A16_BYTES : A32_BYTES);
   __host__ __device__ static size_t a16_off(int s, int part) { return ((size_t)s * PARTS + part) * A16_BYTES; }
-  __host__ __device__ static size_t b16_base() { return (size_t)SOP * PARTS * A16_BYTES; }
-  __host__ __device__ static size_t b16_off(int NP, int s, int part) {
-    return b16_base() + ((size_t)s * PARTS + part) * (size_t)NP * 128;
+  __host__ __device__ static size_t b16_base(int sop) { return (size_t)sop * PARTS * A16_BYTES; }
+  __host__ __device__ static size_t b16_off(int NP, int sop, int s, int part) {
+    return b16_base(sop) + ((size_t)s * PARTS + part) * (size_t)NP * 128;
   }
-  __host__ __device__ static size_t a32_off(int NP, int s) {
-    return b16_base() + (size_t)SOP * PARTS * NP * 128 + (size_t)s * STAGE_BYTES;
+  __host__ __device__ static size_t a32_off(int NP, int sop, int s) {
+    return b16_base(sop) + (size_t)sop * PARTS * NP * 128 + (size_t)s * STAGE_BYTES;
   }
-  __host__ __device__ static size_t bar_off(int NP, int S32) { return a32_off(NP, S32); }
-  // barriers: full32, empty32 (kMaxS32 each), fullA, fullB, emptyOp (SOP each),
-  // accFull, accEmpty (2 each), then the TMEM address word
-  __host__ __device__ static size_t total(int NP, int S32) {
-    return bar_off(NP, S32) + (size_t)(2 * kMaxS32 + 3 * SOP + 4) * 8 + 16 + 1024;
+  __host__ __device__ static size_t bar_off(int NP, int sop, int S32) { return a32_off(NP, sop, S32); }
+  // barriers: full32, empty32 (kMaxS32 each), fullA, fullB, emptyOp (kMaxSop
+  // each), accFull, accEmpty (2 each), then the TMEM address word
+  __host__ __device__ static size_t total(int NP, int sop, int S32) {
+    return bar_off(NP, sop, S32) + (size_t)(2 * kMaxS32 + 3 * kMaxSop + 4) * 8 + 16 + 1024;
   }
 };
 
 __device__ __forceinline__ void flag_timeout(int* status) { dev_set_status(status, DEV_TIMEOUT); }
+
+// Position in a ring of n slots (slot, phase parity), advanced once per item.
+struct RingPos {
+  int slot = 0;
+  uint32_t phase = 0;
+  __device__ __forceinline__ void next(int n) {
+    if (++slot == n) { slot = 0; phase ^= 1u; }
+  }
+};
 
 // Two E4M3 codes (low byte first) to two floats, each times s.
 __device__ __forceinline__ float2 e4m3x2_scaled(uint16_t codes, float s) {
@@ -109,23 +132,25 @@ __device__ __forceinline__ float2 e4m3x2_scaled(uint16_t codes, float s) {
   return make_float2(f.x * s, f.y * s);
 }
 
-template <bool TRANS, bool SPLIT, bool SRC8 = false>
+template <bool TRANS, bool SPLIT, int SRC = kSrc32>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const __grid_constant__ CUtensorMap mapBlo, const TcArgs a) {
-  static_assert(!(SPLIT && SRC8), "the FP8 source has no split mode");
-  using L = Layout<SPLIT, SRC8>;
+  static_assert(!(SPLIT && SRC != kSrc32), "only the FP32 source has a split mode");
+  constexpr bool SRC8 = SRC == kSrc8;
+  using L = Layout<SPLIT, SRC>;
+  const int SOP = a.sop;
   const int S32 = a.s32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int NP = a.NP;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::bar_off(NP, S32));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::bar_off(NP, SOP, S32));
   uint64_t* full32 = bars;
   uint64_t* empty32 = full32 + kMaxS32;
   uint64_t* fullA = empty32 + kMaxS32;
-  uint64_t* fullB = fullA + SOP;
-  uint64_t* emptyOp = fullB + SOP;
-  uint64_t* accFull = emptyOp + SOP;
+  uint64_t* fullB = fullA + kMaxSop;
+  uint64_t* emptyOp = fullB + kMaxSop;
+  uint64_t* accFull = emptyOp + kMaxSop;
   uint64_t* accEmpty = accFull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accEmpty + 2);
   __shared__ int s_abort;
@@ -169,34 +194,32 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     // the MMAs free them.  Separate lanes, so that a panel slot still in use
     // never holds back the prefetch of A.
     if (lane == 0) {
-      int64_t it = 0;
+      RingPos r32;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
         const int64_t z = u / a.mtiles, mt = u % a.mtiles;
         const int64_t k0 = z * a.ksteps_per_split;
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
-        for (int64_t ks = k0; ks < k1; ++ks, ++it) {
-          const int s32 = (int)(it % S32);
-          const uint32_t ph32 = (uint32_t)((it / S32) & 1);
-          if (!ptx::mbar_wait(&empty32[s32], ph32 ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
+        for (int64_t ks = k0; ks < k1; ++ks, r32.next(S32)) {
+          const int s32 = r32.slot;
+          if (!ptx::mbar_wait(&empty32[s32], r32.phase ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
           ptx::mbar_arrive_expect_tx(&full32[s32], L::STAGE_BYTES);
-          void* dstA = smem + L::a32_off(NP, s32);
+          void* dstA = smem + L::a32_off(NP, SOP, s32);
           if (TRANS) ptx::tma_load_2d(dstA, &mapA, &full32[s32], (int32_t)(mt * BM), (int32_t)(ks * BK));
           else ptx::tma_load_2d(dstA, &mapA, &full32[s32], (int32_t)(ks * BK), (int32_t)(mt * BM));
         }
       }
     } else if (lane == 1) {
-      int64_t it = 0;
+      RingPos rop;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
         const int64_t z = u / a.mtiles;
         const int64_t k0 = z * a.ksteps_per_split;
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
-        for (int64_t ks = k0; ks < k1; ++ks, ++it) {
-          const int sop = (int)(it % SOP);
-          const uint32_t phop = (uint32_t)((it / SOP) & 1);
-          if (!ptx::mbar_wait(&emptyOp[sop], phop ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
+        for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
+          const int sop = rop.slot;
+          if (!ptx::mbar_wait(&emptyOp[sop], rop.phase ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
           ptx::mbar_arrive_expect_tx(&fullB[sop], b_bytes * L::PARTS);
-          ptx::tma_load_2d(smem + L::b16_off(NP, sop, 0), &mapB, &fullB[sop], (int32_t)(ks * BK), 0);
-          if (SPLIT) ptx::tma_load_2d(smem + L::b16_off(NP, sop, 1), &mapBlo, &fullB[sop], (int32_t)(ks * BK), 0);
+          ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 0), &mapB, &fullB[sop], (int32_t)(ks * BK), 0);
+          if (SPLIT) ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 1), &mapBlo, &fullB[sop], (int32_t)(ks * BK), 0);
         }
       }
     }
@@ -204,7 +227,8 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = ptx::idesc_bf16_f32(BM, (uint32_t)NP);
-      int64_t it = 0, ua = 0;
+      RingPos rop;
+      int64_t ua = 0;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x, ++ua) {
         const int64_t z = u / a.mtiles;
         const int64_t k0 = z * a.ksteps_per_split;
@@ -216,16 +240,16 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * a.acc_stride);
         uint32_t accumulate = 0;
         bool ok = true;
-        for (int64_t ks = k0; ks < k1; ++ks, ++it) {
-          const int sop = (int)(it % SOP);
-          const uint32_t phop = (uint32_t)((it / SOP) & 1);
+        for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
+          const int sop = rop.slot;
+          const uint32_t phop = rop.phase;
           if (!ptx::mbar_wait(&fullA[sop], phop, vstatus, kWaitNs) ||
               !ptx::mbar_wait(&fullB[sop], phop, vstatus, kWaitNs)) {
             flag_timeout(a.status); s_abort = 1; ok = false; break;
           }
           ptx::tc_fence_after();
           const uint64_t ad = ptx::smem_desc_sw128(smem + L::a16_off(sop, 0));
-          const uint64_t bd = ptx::smem_desc_sw128(smem + L::b16_off(NP, sop, 0));
+          const uint64_t bd = ptx::smem_desc_sw128(smem + L::b16_off(NP, SOP, sop, 0));
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             // advance 16 BF16 (32 bytes) along K inside the swizzled row
@@ -233,7 +257,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             accumulate = 1;
             if (SPLIT) {
               const uint64_t adl = ptx::smem_desc_sw128(smem + L::a16_off(sop, 1));
-              const uint64_t bdl = ptx::smem_desc_sw128(smem + L::b16_off(NP, sop, 1));
+              const uint64_t bdl = ptx::smem_desc_sw128(smem + L::b16_off(NP, SOP, sop, 1));
               ptx::mma_bf16(d_tmem, ad + 2 * kk, bdl + 2 * kk, idesc, 1);
               ptx::mma_bf16(d_tmem, adl + 2 * kk, bd + 2 * kk, idesc, 1);
             }
@@ -247,25 +271,23 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   } else if (warp < 6) {
     // ---------------- converters ----------------
     const int cw = warp - 2;
-    int64_t it = 0;
+    RingPos r32, rop;
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
       const int64_t z = u / a.mtiles, mt = u % a.mtiles;
       const int64_t k0 = z * a.ksteps_per_split;
       const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
       bool ok = true;
-      for (int64_t ks = k0; ks < k1; ++ks, ++it) {
-        const int s32 = (int)(it % S32);
-        const uint32_t ph32 = (uint32_t)((it / S32) & 1);
-        const int sop = (int)(it % SOP);
-        const uint32_t phop = (uint32_t)((it / SOP) & 1);
-        const bool w = ptx::mbar_wait(&full32[s32], ph32, vstatus, kWaitNs) &&
-                       ptx::mbar_wait(&emptyOp[sop], phop ^ 1, vstatus, kWaitNs);
+      for (int64_t ks = k0; ks < k1; ++ks, r32.next(S32), rop.next(SOP)) {
+        const int s32 = r32.slot;
+        const int sop = rop.slot;
+        const bool w = ptx::mbar_wait(&full32[s32], r32.phase, vstatus, kWaitNs) &&
+                       ptx::mbar_wait(&emptyOp[sop], rop.phase ^ 1, vstatus, kWaitNs);
         if (!__all_sync(0xffffffffu, w)) { if (lane == 0) flag_timeout(a.status); ok = false; break; }
-        const float* src = reinterpret_cast<const float*>(smem + L::a32_off(NP, s32));
+        const float* src = reinterpret_cast<const float*>(smem + L::a32_off(NP, SOP, s32));
         uint8_t* hi = smem + L::a16_off(sop, 0);
         uint8_t* lo = smem + L::a16_off(sop, SPLIT ? 1 : 0);
         if (SRC8) {
-          const uint8_t* src8 = smem + L::a32_off(NP, s32);
+          const uint8_t* src8 = smem + L::a32_off(NP, SOP, s32);
           if (!TRANS) {
             // codes[i][k], 128 rows of 64 bytes; the block lies in one tile.  Four
             // rows per step: lane l takes the 8 codes of 16-byte chunk c = l & 7
@@ -305,6 +327,33 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
               *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
             }
           }
+        } else if (SRC == kSrc16) {
+          const uint8_t* s16 = smem + L::a32_off(NP, SOP, s32);
+          if (!TRANS) {
+            // v[i][k], 128 rows of 64 values (128 bytes): lane l moves 16-byte
+            // chunk c = l & 7 of row 4 step + l / 8 to its swizzled place
+            const int c = lane & 7;
+#pragma unroll 4
+            for (int rr = 0; rr < 32; rr += 4) {
+              const int i = cw * 32 + rr + (lane >> 3);
+              const uint4 v = *reinterpret_cast<const uint4*>(s16 + i * 128 + 16 * c);
+              const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)c) ^ ((uint32_t)i & 7u)) << 4);
+              *reinterpret_cast<uint4*>(hi + off) = v;
+            }
+          } else {
+            // v[k][i], 64 rows of 128 values: lane owns output row i, 8 K values per chunk
+            const uint16_t* v16 = reinterpret_cast<const uint16_t*>(s16);
+            const int i = cw * 32 + lane;
+#pragma unroll 2
+            for (int c = 0; c < BK / 8; ++c) {
+              uint32_t hw[4];
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                hw[t] = (uint32_t)v16[(c * 8 + 2 * t) * BM + i] | ((uint32_t)v16[(c * 8 + 2 * t + 1) * BM + i] << 16);
+              const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)c) ^ ((uint32_t)i & 7u)) << 4);
+              *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            }
+          }
         } else if (!TRANS) {
           // src[i][k], 128 rows of 64 floats.  Two rows per step: lane l converts
           // the float4 q = l & 15 (k = 4q .. 4q+3) of row 2 step + l / 16, i.e.
@@ -318,8 +367,13 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             const __nv_bfloat162 h0 = __float22bfloat162_rn(make_float2(v.x, v.y));
             const __nv_bfloat162 h1 = __float22bfloat162_rn(make_float2(v.z, v.w));
             const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)q >> 1) ^ ((uint32_t)i & 7u)) << 4) + sub;
-            *reinterpret_cast<uint2*>(hi + off) =
+            const uint2 hv =
                 make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
+            *reinterpret_cast<uint2*>(hi + off) = hv;
+            // the BF16 copy of A for later passes (rows past M are TMA fill; the
+            // copy's rows are padded to whole 64-column tiles)
+            if (!SPLIT && a.a16 && mt * BM + i < a.M)
+              *reinterpret_cast<uint2*>(a.a16 + (mt * BM + i) * a.ld16 + ks * BK + 4 * q) = hv;
             if (SPLIT) {
               const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
               const __nv_bfloat162 l0 = __float22bfloat162_rn(make_float2(v.x - f0.x, v.y - f0.y));
@@ -525,10 +579,14 @@ size_t tc_apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64
 
 namespace {
 
-// The FP32 source (A) or the FP8 source (E4M3 codes of A with tile scales).
+// The FP32 source (A), the FP8 source (E4M3 codes of A with tile scales) or
+// the BF16 copy of A.
 struct TcSource {
   const rsvd_matrix* A = nullptr;   // FP32 source
   const Fp8Source* f8 = nullptr;    // FP8 source
+  const Bf16Source* b16 = nullptr;  // BF16 source
+  uint16_t* copy16 = nullptr;       // FP32 forward pass: write the BF16 copy here
+  int64_t ld16 = 0;
 };
 
 rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, int prec, int r, const float* X,
@@ -536,8 +594,14 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
                          cudaStream_t stream, bool accumulate) {
   const bool split = prec == RSVD_PREC_BF16X3;
   const bool src8 = src.f8 != nullptr;
+  const bool src16 = src.b16 != nullptr;
   if (r < 1 || r > 512) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: r must be in [1, 512]");
-  if (split && src8) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: no split mode for the FP8 source");
+  if (split && (src8 || src16))
+    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: only the FP32 source has a split mode");
+  if (src.copy16 && (split || trans || src8 || src16 || round_up(r, 16) > 256 || src.ld16 < round_up(n, BK) ||
+                     src.ld16 % BK != 0))
+    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: the BF16 copy is written by one plain forward pass "
+                                      "over FP32 A (ld16 a multiple of 64 covering n)");
   if (round_up(r, 16) > (split ? kSplitMaxNP : 256)) {
     // wider than one accumulator (256 columns) or than the split-mode operand
     // ring fits: passes over column halves of the panel (A is read per half)
@@ -546,8 +610,10 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
     return tc_apass_run(src, m, n, trans, prec, r - h, X + h, ldx, Y + h, ldy, ws, ws_bytes, status, stream,
                         accumulate);
   }
-  if (!src8 && (src.A->ld % 4 != 0 || (reinterpret_cast<uintptr_t>(src.A->data) & 15) != 0))
+  if (!src8 && !src16 && (src.A->ld % 4 != 0 || (reinterpret_cast<uintptr_t>(src.A->data) & 15) != 0))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: A needs a 16-byte aligned base and ld % 4 == 0");
+  if (src16 && (src.b16->ld % 8 != 0 || (reinterpret_cast<uintptr_t>(src.b16->data) & 15) != 0))
+    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: the BF16 copy needs a 16-byte aligned base and ld % 8 == 0");
   if (src8 && (src.f8->ldc % 16 != 0 || (reinterpret_cast<uintptr_t>(src.f8->codes) & 15) != 0))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: FP8 codes need a 16-byte aligned base and ld % 16 == 0");
   const TcShape s = tc_shape(m, n, r, trans);
@@ -573,6 +639,9 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   if (src8)
     RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_UINT8, src.f8->codes, (uint64_t)n, (uint64_t)m,
                        (uint64_t)src.f8->ldc, box_in, box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
+  else if (src16)
+    RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, src.b16->data, (uint64_t)n, (uint64_t)m,
+                       (uint64_t)src.b16->ld * 2, box_in, box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
   else
     RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, src.A->data, (uint64_t)n, (uint64_t)m,
                        (uint64_t)src.A->ld * 4, box_in, box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
@@ -605,19 +674,26 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   ta.qm = src8 ? src.f8->qm : 1;
   ta.qn = src8 ? src.f8->qn : 1;
   ta.qtn = src8 ? cdiv(n, src.f8->qn) : 1;
+  ta.a16 = src.copy16;
+  ta.ld16 = src.ld16;
 
   const int64_t units = s.mtiles * s.nsplit;
   const int grid = (int)(units < num_sms() ? units : num_sms());
   constexpr size_t kSmemMax = 232448;
-  int s32 = kMaxS32;
-  auto need = [&](int depth) {
-    return split ? Layout<true>::total(s.NP, depth)
-                 : (src8 ? Layout<false, true>::total(s.NP, depth) : Layout<false>::total(s.NP, depth));
+  auto need = [&](int sop, int depth) {
+    return split ? Layout<true>::total(s.NP, sop, depth)
+                 : (src8 ? Layout<false, kSrc8>::total(s.NP, sop, depth)
+                         : (src16 ? Layout<false, kSrc16>::total(s.NP, sop, depth)
+                                  : Layout<false>::total(s.NP, sop, depth)));
   };
-  while (s32 > 2 && need(s32) > kSmemMax) --s32;
-  const size_t smem = need(s32);
+  // four operand slots when at least three staging stages still fit, else two
+  int sop = need(kMaxSop, 3) <= kSmemMax ? kMaxSop : 2;
+  int s32 = kMaxS32;
+  while (s32 > 2 && need(sop, s32) > kSmemMax) --s32;
+  const size_t smem = need(sop, s32);
   if (smem > kSmemMax) return fail(RSVD_ERR_UNSUPPORTED, "tensor-core A-pass: shared memory plan too large");
   ta.s32 = s32;
+  ta.sop = sop;
   auto launch = [&](auto kern) -> rsvd_status {
     RSVD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, THREADS, smem, stream>>>(mapA, mapB, mapBlo, ta);
@@ -625,7 +701,9 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
     return RSVD_OK;
   };
   if (src8) {
-    RSVD_TRY(trans ? launch(tc_apass_kernel<true, false, true>) : launch(tc_apass_kernel<false, false, true>));
+    RSVD_TRY(trans ? launch(tc_apass_kernel<true, false, kSrc8>) : launch(tc_apass_kernel<false, false, kSrc8>));
+  } else if (src16) {
+    RSVD_TRY(trans ? launch(tc_apass_kernel<true, false, kSrc16>) : launch(tc_apass_kernel<false, false, kSrc16>));
   } else if (trans) {
     RSVD_TRY(split ? launch(tc_apass_kernel<true, true>) : launch(tc_apass_kernel<true, false>));
   } else {
@@ -640,10 +718,21 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
 
 rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X, int64_t ldx,
                               float* Y, int64_t ldy, int64_t, int64_t, void* ws, size_t ws_bytes,
-                              int* status, cudaStream_t stream, bool accumulate) {
+                              int* status, cudaStream_t stream, bool accumulate, uint16_t* copy16,
+                              int64_t ld16) {
   TcSource src;
   src.A = &A;
+  src.copy16 = copy16;
+  src.ld16 = ld16;
   return tc_apass_run(src, A.m, A.n, trans, prec, r, X, ldx, Y, ldy, ws, ws_bytes, status, stream, accumulate);
+}
+
+rsvd_status tc_apass_from_bf16(const Bf16Source& b16, int trans, int r, const float* X, int64_t ldx, float* Y,
+                               int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream) {
+  TcSource src;
+  src.b16 = &b16;
+  return tc_apass_run(src, b16.m, b16.n, trans, RSVD_PREC_BF16, r, X, ldx, Y, ldy, ws, ws_bytes, status, stream,
+                      false);
 }
 
 rsvd_status tc_apass_from_fp8(const Fp8Source& f8, int trans, int r, const float* X, int64_t ldx, float* Y,

@@ -189,8 +189,21 @@ rsvd_status fp8_quantize(const float* A, int64_t m, int64_t n, int64_t lda, int6
 rsvd_status tc_apass_from_fp8(const Fp8Source& f8, int trans, int r, const float* X, int64_t ldx, float* Y,
                               int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream,
                               bool accumulate = false);
+// copy16 (optional, plain BF16 forward pass only): the pass also stores
+// BF16(A), rounded as its operands are, row-major with stride ld16 (a multiple
+// of 64 >= n), for tc_apass_from_bf16.
 rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X,
                               int64_t ldx, float* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws,
-                              size_t ws_bytes, int* status, cudaStream_t stream, bool accumulate = false);
+                              size_t ws_bytes, int* status, cudaStream_t stream, bool accumulate = false,
+                              uint16_t* copy16 = nullptr, int64_t ld16 = 0);
+// A BF16 copy of a dense m x n A (row-major, stride ld elements).
+struct Bf16Source {
+  const uint16_t* data = nullptr;
+  int64_t m = 0, n = 0, ld = 0;
+};
+// The BF16 A-pass over the copy: the same operands, hence the same result, as
+// tc_apass_from_f32 with prec BF16 on the FP32 A the copy was made from.
+rsvd_status tc_apass_from_bf16(const Bf16Source& b16, int trans, int r, const float* X, int64_t ldx, float* Y,
+                               int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream);
 
 }  // namespace rsvd

@@ -114,3 +114,22 @@ def test_bf16_rsvd_against_oracle(g, prec):
         assert es <= 1e-4 and eu <= 1e-2
     else:
         assert es <= 1e-2
+
+
+def test_bf16_copy_of_a_gives_the_same_bits(g):
+    """In-core BF16 plans read a BF16 copy of A that the first forward pass
+    writes: the same operands as converting the FP32 A in every pass, hence
+    the same result bit for bit.  A memory cap with no room for the copy makes
+    every pass read the FP32 A.  Ragged sizes: a partial last row tile and
+    columns padded to whole 64-column tiles in the copy."""
+    m, n, k, p, q, seed = 6007, 3004, 40, 8, 2, 11
+    A, _, _ = prescribed_dense(m, n, spectrum_harmonic_noisy(n, 1e-4, 5), 7, dtype=np.float32)
+    Ad = torch.as_tensor(A, device="cuda")
+    p1 = g.Plan(m, n, k, p, q, seed, prec="bf16")
+    U1, S1, V1 = p1.run(Ad)
+    ws = p1.info()["workspace_bytes"]
+    p1.close()
+    p2 = g.Plan(m, n, k, p, q, seed, mem_cap=ws + 4096, prec="bf16")
+    U2, S2, V2 = p2.run(Ad)
+    p2.close()
+    assert torch.equal(S1, S2) and torch.equal(U1, U2) and torch.equal(V1, V2)
