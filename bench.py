@@ -136,6 +136,7 @@ def _build_A(device):
 # sources that define each profiled kernel (its code and everything it includes)
 KERNEL_SOURCES = {
     "tc_apass_kernel": ["gemm_tc.cu", "tc_ptx.cuh", "common.cuh", "kernels.cuh"],
+    "tc_apass_kernel_bf16_run": ["gemm_tc.cu", "tc_ptx.cuh", "common.cuh", "kernels.cuh"],
     "simt_gemm_kernel": ["gemm_simt.cu", "common.cuh", "kernels.cuh"],
 }
 
@@ -307,7 +308,7 @@ def run_ours(args):
     if prec == "bf16" and plan_info.get("bf16_copy"):
         roof["passes"] = ("1 forward pass over FP32 A writing its BF16 copy, 2q passes over the copy, "
                           "1 split-BF16 pass over FP32 A; bytes and time averaged over the run's passes")
-        roof["traffic"] = None  # the committed capture is of the FP32-source launches
+        roof["traffic"] = _traffic_for("tc_apass_kernel_bf16_run", m * n)
 
     # --- end to end through the public API with host buffers ----------------------
     e2e = None
@@ -324,7 +325,7 @@ def run_ours(args):
         for _ in range(max(0, args.warmup - 1)):
             plan_h.run(A_host, Ud, Sd, Vd)
         torch.cuda.synchronize()
-        steps_e2e = max(1, min(args.steps, 5))
+        steps_e2e = max(1, min(args.steps, 10))
         host_split = []
         t0 = time.perf_counter()
         for _ in range(steps_e2e):
@@ -408,6 +409,33 @@ def run_ours(args):
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_rsvd_rows(args):
+    """The dense workload's recipe and BF16 plan at --m x --n (default
+    25000 x 20000): a small whole-rSVD target for kernel profiling."""
+    import torch
+    import paper_1907_06470_gb300 as g
+    from synth import WORKLOADS, prescribed_dense_torch
+    g.load()
+    w = WORKLOADS[WORKLOAD]
+    m, n = args.m, args.n
+    A = prescribed_dense_torch(m, n, _spectrum(n, w.noise_seed), w.data_seed, device="cuda")
+    plan = g.Plan(m, n, w.k, w.p, w.q, w.seed, prec=args.prec, mb=w.tile, nb=w.tile)
+    U, S, V = plan.run(A)
+    for _ in range(max(0, args.warmup - 1)):
+        plan.run(A, U, S, V)
+    torch.cuda.synchronize()
+    plan.set_profiling(True)
+    stages = {}
+    for _ in range(args.steps):
+        plan.run(A, U, S, V)
+        for key, val in plan.stage_ms().items():
+            stages[key] = stages.get(key, 0.0) + val / args.steps
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "rsvd_rows", "m": m, "n": n, "k": w.k, "p": w.p, "q": w.q, "prec": args.prec,
+                      "steps": args.steps, "stages_ms_per_rsvd": stages, "info": plan.info()}))
     return 0
 
 
@@ -589,7 +617,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--mode", default="rsvd", choices=["rsvd", "apass", "ooc", "csr"])
+    ap.add_argument("--mode", default="rsvd", choices=["rsvd", "apass", "ooc", "csr", "rsvd_rows"])
     ap.add_argument("--csr-m", type=int, default=5_000_000)
     ap.add_argument("--csr-n", type=int, default=1_000_000)
     ap.add_argument("--csr-nnz", type=int, default=500_000_000)
@@ -600,6 +628,8 @@ def main():
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--r", type=int, default=120)
     args = ap.parse_args()
+    if args.mode == "rsvd_rows":
+        return run_rsvd_rows(args)
     if args.mode == "apass":
         return run_apass_only(args)
     if args.mode == "ooc":
