@@ -341,17 +341,32 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
               *reinterpret_cast<uint4*>(hi + off) = v;
             }
           } else {
-            // v[k][i], 64 rows of 128 values: lane owns output row i, 8 K values per chunk
-            const uint16_t* v16 = reinterpret_cast<const uint16_t*>(s16);
-            const int i = cw * 32 + lane;
+            // v[k][i], 64 rows of 128 values.  Thread t = 32 cw + lane takes the
+            // row pair (2p, 2p+1), p = t & 63, for the chunks 4h .. 4h+3,
+            // h = t >> 6: one 32-bit load gives both rows' values at one k, and
+            // byte permutes split them into the two rows' K-major chunks.  The
+            // pairs with bit 2 of p set store the odd row first, so that the 8
+            // lanes of each store phase cover all 8 swizzle positions.
+            const uint32_t* v32 = reinterpret_cast<const uint32_t*>(s16);
+            const int t = cw * 32 + lane, p = t & 63, h = t >> 6;
+            const bool sw = (p >> 2) & 1;
+            const uint32_t sel_a = sw ? 0x7632u : 0x5410u, sel_b = sw ? 0x5410u : 0x7632u;
+            const uint32_t row_a = (uint32_t)(2 * p + (sw ? 1 : 0)), row_b = (uint32_t)(2 * p + (sw ? 0 : 1));
 #pragma unroll 2
-            for (int c = 0; c < BK / 8; ++c) {
-              uint32_t hw[4];
+            for (int c = 4 * h; c < 4 * h + 4; ++c) {
+              uint32_t w[8];
 #pragma unroll
-              for (int t = 0; t < 4; ++t)
-                hw[t] = (uint32_t)v16[(c * 8 + 2 * t) * BM + i] | ((uint32_t)v16[(c * 8 + 2 * t + 1) * BM + i] << 16);
-              const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)c) ^ ((uint32_t)i & 7u)) << 4);
-              *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              for (int kk = 0; kk < 8; ++kk) w[kk] = v32[(c * 8 + kk) * (BM / 2) + p];
+              uint32_t fa[4], fb[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                fa[j] = __byte_perm(w[2 * j], w[2 * j + 1], sel_a);
+                fb[j] = __byte_perm(w[2 * j], w[2 * j + 1], sel_b);
+              }
+              const uint32_t offa = row_a * 128u + ((((uint32_t)c) ^ (row_a & 7u)) << 4);
+              const uint32_t offb = row_b * 128u + ((((uint32_t)c) ^ (row_b & 7u)) << 4);
+              *reinterpret_cast<uint4*>(hi + offa) = make_uint4(fa[0], fa[1], fa[2], fa[3]);
+              *reinterpret_cast<uint4*>(hi + offb) = make_uint4(fb[0], fb[1], fb[2], fb[3]);
             }
           }
         } else if (!TRANS) {
