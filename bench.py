@@ -439,6 +439,60 @@ def run_rsvd_rows(args):
     return 0
 
 
+def run_backward(args):
+    """The differentiable workload (FP32 A 20000 x 10000, s_i = 10 * 0.95^(i-1),
+    k=64, p=16, q=2): forward rSVD and the adjoint pass dA (rsvd_backward) for
+    seeded cotangents of the workload's loss sum_i w_i s_i + ||U_k^T X||_F^2."""
+    import torch
+    import paper_1907_06470_gb300 as g
+    from synth import WORKLOADS, prescribed_dense_torch
+    g.load()
+    w = WORKLOADS["dense_fp32_20000x10000_diff"]
+    m, n, k = w.m, w.n, w.k
+    s = 10.0 * 0.95 ** np.arange(n)
+    A = prescribed_dense_torch(m, n, s, w.data_seed, device="cuda")
+    plan = g.Plan(m, n, k, w.p, w.q, w.seed, prec="fp32", mb=w.tile, nb=w.tile)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w.noise_seed)
+    X = torch.randn(m, 32, generator=gen, device="cuda")
+    wv = torch.rand(k, generator=gen, device="cuda")
+    U, S, V = plan.run(A)
+
+    def cotangents(U):
+        # d/dU ||U^T X||_F^2 = 2 X X^T U; d/dS sum w_i s_i = w
+        return 2.0 * X @ (X.T @ U), wv, None
+
+    for _ in range(args.warmup):
+        plan.run(A, U, S, V)
+        dU, dS, dV = cotangents(U)
+        plan.backward(U, S, V, dU, dS, dV)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd_ms = bwd_ms = 0.0
+    for _ in range(args.steps):
+        e[0].record()
+        plan.run(A, U, S, V)
+        dU, dS, dV = cotangents(U)
+        e[1].record()
+        dA = plan.backward(U, S, V, dU, dS, dV)
+        e[2].record()
+        torch.cuda.synchronize()
+        fwd_ms += e[0].elapsed_time(e[1]) / args.steps
+        bwd_ms += e[1].elapsed_time(e[2]) / args.steps
+    peaks, peak_kind = _peaks()
+    # dA written once (4 m n bytes); U, V, dU read (the k-wide panels)
+    bwd_bytes = 4 * m * n + 4 * (2 * m + n) * k
+    print(json.dumps({
+        "mode": "backward", "workload": w.name, "m": m, "n": n, "k": k, "p": w.p, "q": w.q, "prec": "fp32",
+        "steps": args.steps, "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+        "backward_roofline": {"bound": "hbm", "algorithmic_bytes": bwd_bytes,
+                              "achieved": bwd_bytes / (bwd_ms / 1e3) / 1e9, "peak": float(peaks["hbm_gbs"]),
+                              "unit": "GB/s", "frac": bwd_bytes / (bwd_ms / 1e3) / 1e9 / float(peaks["hbm_gbs"]),
+                              "peak_source": f"hbm_gbs ({peak_kind})"},
+        "dA_fro": float(torch.linalg.norm(dA)), "data": "synthetic"}))
+    return 0
+
+
 def run_apass_only(args):
     """Forward and transposed A-passes alone on a random FP32 matrix (a small,
     quick target for kernel profiling and tuning)."""
@@ -617,7 +671,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--mode", default="rsvd", choices=["rsvd", "apass", "ooc", "csr", "rsvd_rows"])
+    ap.add_argument("--mode", default="rsvd", choices=["rsvd", "apass", "ooc", "csr", "rsvd_rows", "backward"])
     ap.add_argument("--csr-m", type=int, default=5_000_000)
     ap.add_argument("--csr-n", type=int, default=1_000_000)
     ap.add_argument("--csr-nnz", type=int, default=500_000_000)
@@ -630,6 +684,8 @@ def main():
     args = ap.parse_args()
     if args.mode == "rsvd_rows":
         return run_rsvd_rows(args)
+    if args.mode == "backward":
+        return run_backward(args)
     if args.mode == "apass":
         return run_apass_only(args)
     if args.mode == "ooc":
