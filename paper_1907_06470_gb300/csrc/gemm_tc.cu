@@ -84,6 +84,7 @@ struct TcArgs {
   int64_t qm, qn, qtn;  // FP8 source: tile edges (in rows / columns of A)
   uint16_t* a16;        // FP32 forward pass: also store BF16(A) here (row stride ld16), or null
   int64_t ld16;
+  int gram;             // 1: C = A^T A with one row tile: the panel operand is the converted A tile
 };
 
 #ifndef RSVD_TC_MAX_S32
@@ -208,7 +209,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           else ptx::tma_load_2d(dstA, &mapA, &full32[s32], (int32_t)(ks * BK), (int32_t)(mt * BM));
         }
       }
-    } else if (lane == 1) {
+    } else if (lane == 1 && !a.gram) {
       RingPos rop;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
         const int64_t z = u / a.mtiles;
@@ -244,12 +245,13 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           const int sop = rop.slot;
           const uint32_t phop = rop.phase;
           if (!ptx::mbar_wait(&fullA[sop], phop, vstatus, kWaitNs) ||
-              !ptx::mbar_wait(&fullB[sop], phop, vstatus, kWaitNs)) {
+              (!a.gram && !ptx::mbar_wait(&fullB[sop], phop, vstatus, kWaitNs))) {
             flag_timeout(a.status); s_abort = 1; ok = false; break;
           }
           ptx::tc_fence_after();
+          // Gram mode: the K-major tile of A^T is also the panel tile (its first NP rows)
           const uint64_t ad = ptx::smem_desc_sw128(smem + L::a16_off(sop, 0));
-          const uint64_t bd = ptx::smem_desc_sw128(smem + L::b16_off(NP, SOP, sop, 0));
+          const uint64_t bd = a.gram ? ad : ptx::smem_desc_sw128(smem + L::b16_off(NP, SOP, sop, 0));
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             // advance 16 BF16 (32 bytes) along K inside the swizzled row
@@ -257,7 +259,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             accumulate = 1;
             if (SPLIT) {
               const uint64_t adl = ptx::smem_desc_sw128(smem + L::a16_off(sop, 1));
-              const uint64_t bdl = ptx::smem_desc_sw128(smem + L::b16_off(NP, SOP, sop, 1));
+              const uint64_t bdl = a.gram ? adl : ptx::smem_desc_sw128(smem + L::b16_off(NP, SOP, sop, 1));
               ptx::mma_bf16(d_tmem, ad + 2 * kk, bdl + 2 * kk, idesc, 1);
               ptx::mma_bf16(d_tmem, adl + 2 * kk, bd + 2 * kk, idesc, 1);
             }
@@ -644,7 +646,11 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
     RSVD_CUDA(cudaMemsetAsync(status, 0, sizeof(int), stream));
   }
 
-  {  // panel -> BF16 (hi, lo), K-major
+  // Gram C = A^T A of a matrix of at most 128 columns: the converters' K-major
+  // tile of A^T (one row tile) already is the panel tile, rounded the same way
+  const bool gram = trans && !src8 && !src16 && !src.copy16 && X == static_cast<const float*>(src.A->data) &&
+                    ldx == src.A->ld && (int64_t)r == n && s.mtiles == 1;
+  if (!gram) {  // panel -> BF16 (hi, lo), K-major
     dim3 grid((unsigned)cdiv(s.K, 32), (unsigned)cdiv(s.NP, 32));
     panel_to_bf16_kernel<<<grid, dim3(32, 8), 0, stream>>>(s.K, r, s.NP, X, ldx, Xhi, Xlo, s.ldb);
     RSVD_CUDA(after_launch());
@@ -691,6 +697,7 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   ta.qtn = src8 ? cdiv(n, src.f8->qn) : 1;
   ta.a16 = src.copy16;
   ta.ld16 = src.ld16;
+  ta.gram = gram ? 1 : 0;
 
   const int64_t units = s.mtiles * s.nsplit;
   const int grid = (int)(units < num_sms() ? units : num_sms());

@@ -133,3 +133,19 @@ def test_bf16_copy_of_a_gives_the_same_bits(g):
     U2, S2, V2 = p2.run(Ad)
     p2.close()
     assert torch.equal(S1, S2) and torch.equal(U1, U2) and torch.equal(V1, V2)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("M,r", [(100000, 120), (5003, 36), (4096, 128)])
+def test_gram_of_a_panel_matches_the_general_path(g, prec, M, r):
+    """Y^T Y with one row tile of output uses the converted tile of Y^T as the
+    panel operand too: the same rounded operands as converting the panel
+    separately, so the same bits."""
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(M + r)
+    Y = torch.randn(M, r, generator=gen, device="cuda")
+    G1 = g.apass(Y, Y, True, prec)            # X is A: the Gram path
+    G2 = g.apass(Y, Y.clone(), True, prec)    # a separate panel
+    assert torch.equal(G1, G2)
+    ref = (Y.double().T @ Y.double()).cpu().numpy()
+    assert np.abs(G1.double().cpu().numpy() - ref).max() <= (2e-2 if prec == "bf16" else 1e-4) * np.abs(ref).max()
