@@ -155,6 +155,41 @@ reduce_partials_kernel(int64_t M, int64_t N, int nsplit, const T* __restrict__ P
 // The same sum with 4 consecutive columns per thread (16-byte loads) and the
 // split loop unrolled so the partial loads are in flight together; the order
 // of the additions (split 0, 1, 2, ...) is the same as above.
+// One warp per output float4: lane l adds the partials of a contiguous block
+// of splits in order, then the 32 lane sums are combined by a fixed butterfly,
+// so the result does not depend on scheduling.
+__global__ void reduce_partials_warp_vec4_kernel(int64_t M, int64_t N4, int nsplit, const float4* __restrict__ P,
+                                                 int64_t ldp4, int64_t pstride4, float4* __restrict__ out,
+                                                 int64_t ldo4, int accumulate) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= M * N4) return;  // whole warps only (blockDim is a multiple of 32)
+  const int64_t i = w / N4, j = w - i * N4;
+  const float4* src = P + i * ldp4 + j;
+  const int per = (nsplit + 31) / 32;
+  const int z0 = lane * per, z1 = min(nsplit, z0 + per);
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int z = z0; z < z1; ++z) {
+    const float4 v = src[(int64_t)z * pstride4];
+    s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+    s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
+    s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
+  }
+  if (lane == 0) {
+    float4* dst = out + i * ldo4 + j;
+    if (accumulate) {
+      const float4 d = *dst;
+      s.x += d.x; s.y += d.y; s.z += d.z; s.w += d.w;
+    }
+    *dst = s;
+  }
+}
+
 __global__ void reduce_partials_vec4_kernel(int64_t M, int64_t N4, int nsplit, const float4* __restrict__ P,
                                             int64_t ldp4, int64_t pstride4, float4* __restrict__ out, int64_t ldo4,
                                             int accumulate) {
@@ -256,7 +291,17 @@ rsvd_status reduce_partials(int64_t M, int64_t N, int nsplit, const T* P, int64_
                             int64_t ldo, bool accumulate, cudaStream_t stream) {
   if (M * N == 0) return RSVD_OK;
   if constexpr (std::is_same<T, float>::value) {
-    if (N % 4 == 0 && ldp % 4 == 0 && pstride % 4 == 0 && ldo % 4 == 0 && aligned16(P) && aligned16(out)) {
+    const bool vec = N % 4 == 0 && ldp % 4 == 0 && pstride % 4 == 0 && ldo % 4 == 0 && aligned16(P) && aligned16(out);
+    if (vec && nsplit >= 64 && M * (N / 4) <= 152 * 64) {
+      // few outputs, many partials (the Grams of tall panels): a warp per float4
+      const int64_t warps = M * (N / 4);
+      reduce_partials_warp_vec4_kernel<<<(int)cdiv(warps * 32, 256), 256, 0, stream>>>(
+          M, N / 4, nsplit, reinterpret_cast<const float4*>(P), ldp / 4, pstride / 4, reinterpret_cast<float4*>(out),
+          ldo / 4, accumulate ? 1 : 0);
+      RSVD_CUDA(after_launch());
+      return RSVD_OK;
+    }
+    if (vec) {
       int64_t blocks = cdiv(M * (N / 4), 256);
       if (blocks > 152 * 8) blocks = 152 * 8;
       reduce_partials_vec4_kernel<<<(int)blocks, 256, 0, stream>>>(

@@ -14,8 +14,10 @@
 //   warps 6-9  epilogue: tcgen05.ld of the FP32 accumulator, stores to C
 // Two TMEM accumulators let the epilogue of one 128-row tile overlap the MMAs
 // of the next.  The reduction dimension may be split across CTAs for load
-// balance; the partial products are then added in split order by a second
-// kernel, so the result does not depend on scheduling.
+// balance; the partial products are then added in a fixed order by a second
+// kernel (in split order; with many splits and few outputs, contiguous blocks
+// of splits combined by a fixed butterfly), so the result does not depend on
+// scheduling.
 //
 // Split mode (BF16X3): A = A_hi + A_lo and X = X_hi + X_lo, each part BF16,
 // C = A_hi X_hi + A_hi X_lo + A_lo X_hi, about 16 significant bits per operand.
