@@ -1,14 +1,16 @@
 // Section 2.1 step 6: SVD of the small factor by one-sided (Hestenes) Jacobi
 // in FP64, with the relative stopping test of Demmel & Veselic (1992).
 //
-// Three phases for square inputs with 8 <= r <= 160: FP32 sweeps in one CTA
-// (shared memory) to FP32 convergence; one FP64 Newton-Schulz step that makes
-// the accumulated FP32 rotation exactly orthogonal in FP64, applied to M; FP64
-// sweeps to FP64 convergence, which then take few sweeps.  Other shapes run the
-// FP64 sweeps from the start.
+// Three phases for square inputs with 8 <= r <= 512: FP32 sweeps to FP32
+// convergence (one CTA with shared memory for r <= 160, a 16-CTA cluster over
+// global memory above); Newton-Schulz steps that make the accumulated FP32
+// rotation orthogonal in FP64, applied to M; FP64 sweeps to FP64
+// convergence, which then take few sweeps -- or none, for callers whose
+// inputs carry far less than FP32 accuracy (only the outputs are formed).
+// Other shapes run the FP64 sweeps from the start.
 //
-// M (rows x r, column-major, rows >= 1) is driven to orthogonal columns by plane rotations
-// from the right, M W = U diag(sigma).  The sweep order is round-robin: in
+// M (rows x r, column-major, rows >= 1) is driven to orthogonal columns by
+// plane rotations from the right, M W = U diag(sigma).  The sweep order is round-robin: in
 // each of the r'-1 rounds of a sweep (r' = r rounded up to even) the r'/2
 // column pairs are disjoint, so one CTA rotates each pair concurrently.
 // FP64 throughput on one GB300 SM is low (about 2 DFMA per clock), so the

@@ -48,10 +48,9 @@ __global__ void check_dead_kernel(int r, const int* __restrict__ dead, int* stat
 // and deflation above), each thread solves one row of the panel below it, and
 // the trailing lower triangle takes the panel's rank-16 update -- with
 // lookahead: warp 0 updates and factors the next diagonal block while the
-// other warps update the rest, two barriers per panel.  Rows are stored with a stride that is a multiple of 16
-// bytes, so a row segment of the panel moves in 16-byte loads (4 for FP32,
-// 8 for FP64); the padding columns are zero.  The factor L goes to global
-// memory.
+// other warps update the rest, two barriers per panel.  Rows are stored with
+// a stride that is a multiple of 16 bytes, so a row segment of the panel moves
+// in 16-byte loads (4 for FP32, 8 for FP64); the padding columns are zero.
 //
 // Inverse X = L^-1 blocked by block diagonals: the diagonal blocks are inverted
 // by one warp each; then for d = 1, 2, ... every block X_ij with i - j = d is
