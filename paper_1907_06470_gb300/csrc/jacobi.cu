@@ -753,10 +753,13 @@ rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double*
   // W' = (1.5 I - 0.5 W W^T) W, i.e. on the column-major storage (= W^T row-major)
   // Wt' = Wt (1.5 I - 0.5 P) with P = Wt^T Wt.  The accumulated FP32 rotation
   // is orthogonal to about 1e-6; each step squares that error, so two steps
-  // reach FP64 rounding.
+  // reach FP64 rounding.  Without FP64 sweeps (inputs far less accurate than
+  // FP32) the FP32 rotation is kept as it is: 1e-6 is already below the
+  // orthogonality of U that the FP32 stopping test leaves (r eps32).
   widen_kernel<<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r * r, ws.W32, ws.T);
   RSVD_CUDA(after_launch());
-  for (int step = 0; step < 2; ++step) {
+  const int ns_steps = fp64_sweeps ? 2 : 0;
+  for (int step = 0; step < ns_steps; ++step) {
     double* src = step == 0 ? ws.T : ws.W64;
     double* dst = step == 0 ? ws.W64 : ws.T;
     RSVD_TRY(small_gemm64(r, src, true, src, ws.P, ws.gemm_partial, stream));
@@ -764,7 +767,7 @@ rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double*
     RSVD_CUDA(after_launch());
     RSVD_TRY(small_gemm64(r, src, false, ws.P, dst, ws.gemm_partial, stream));
   }
-  // the orthonormalised rotation is now in T; move it to W64
+  // the (orthonormalised) rotation is now in T; move it to W64
   RSVD_CUDA(cudaMemcpyAsync(ws.W64, ws.T, sizeof(double) * (size_t)r * r, cudaMemcpyDeviceToDevice, stream));
   // M64 = M W': column-major M64 = Wt' (row-major) times Mc viewed row-major.
   RSVD_TRY(small_gemm64(r, ws.W64, false, Mc, ws.M64, ws.gemm_partial, stream));
