@@ -212,11 +212,17 @@ rsvd_status rsvd_plan_set_checkpoint(rsvd_plan_t plan, const char* path, int32_t
  * checkpoint at `path`. */
 rsvd_status rsvd_checkpoint_info(const char* path, rsvd_checkpoint_info_t* out);
 
-/* Exact thin SVD of a small dense device matrix (Section 3: the library's
- * non-approximate path), t = min(m, n) <= 256 and m*n <= 2^24: U m x t, S t,
- * V n x t, same dtype as A, signs as in rsvd_run.  FP64 one-sided Jacobi on
- * the columns of A (m >= n) or of A^T (m < n).  Allocates and frees its own
- * device workspace.  Synchronises `stream`. */
+/* Exact thin SVD of a dense device matrix (Section 3: the library's
+ * non-approximate path), t = min(m, n) <= 512: U m x t, S t, V n x t, same
+ * dtype as A, signs as in rsvd_run.  All arithmetic in FP64 on T = A (m >= n)
+ * or A^T (m < n).  t <= 256 and m*n <= 2^24: one-sided Jacobi on the columns
+ * of T.  Otherwise T = Q R by CholeskyQR2 and the one-sided Jacobi on the t x t
+ * R.  That path forms the Gram of T, so singular values below about 1e-7 of
+ * the largest keep an absolute, not a relative, FP64 accuracy (columns
+ * dependent to that level give zeros in S, with orthonormal vectors); a
+ * non-finite entry gives RSVD_ERR_NOT_SPD.  Allocates and frees its own device
+ * workspace (about 3 m n + 4 t^2 doubles on the CholeskyQR2 path).
+ * Synchronises `stream`. */
 rsvd_status rsvd_full(const rsvd_matrix* A, void* U, void* S, void* V, void* stream);
 
 /* Backward pass (no counterpart in the paper): the adjoint of the rank-k

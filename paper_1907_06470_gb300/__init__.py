@@ -257,7 +257,7 @@ def kernel_launches() -> int:
 
 
 def full_svd(A):
-    """Exact thin SVD (U, S, V) of a small dense CUDA matrix, min(m, n) <= 256."""
+    """Exact thin SVD (U, S, V) of a dense CUDA matrix, min(m, n) <= 512."""
     torch = _torch()
     m, n = A.shape
     t = min(m, n)

@@ -642,6 +642,85 @@ rsvd_status prepare_csr(rsvd_plan_s* P, const rsvd_matrix& A, rsvd_matrix* out, 
 
 }  // namespace
 
+namespace {
+
+// rsvd_full for the larger shapes: T = A (m >= n) or A^T (m < n), rows x cols
+// with cols = min(m, n) <= 512, in FP64.  T = Q R by CholeskyQR2, R^T W =
+// U_J diag(s) by the square one-sided Jacobi (the column-major view of the
+// row-major R is R^T), so T = (Q W) diag(s) U_J^T: the left singular vectors
+// of T are Q W, the right ones U_J.
+rsvd_status full_svd_tall(const rsvd_matrix& A, void* U, void* S, void* V, cudaStream_t st) {
+  const int64_t m = A.m, n = A.n;
+  const int64_t rows = m >= n ? m : n;
+  const int cols = (int)(m >= n ? n : m);
+  const size_t rc = (size_t)rows * cols, cc = (size_t)cols * cols;
+  const size_t ob = orth_ws_bytes(rows, cols, RSVD_F64, false);
+  const size_t jb = jacobi_ws_bytes(cols, cols);
+  const size_t sb = sign_scratch_bytes(m, cols);
+  Sizer sz;
+  sz.take<double>(rc); sz.take<double>(rc); sz.take<double>(rc);
+  sz.take<double>(cc); sz.take<double>(cols); sz.take<double>(cc); sz.take<double>(cc);
+  sz.take<char>(ob); sz.take<char>(jb); sz.take<char>(sb);
+  const size_t total = sz.used + 1024;
+  void* ws = nullptr;
+  RSVD_CUDA(cudaMalloc(&ws, total));
+  Carver c(ws, total);
+  double* T = c.take<double>(rc);
+  double* Q = c.take<double>(rc);
+  double* UA = c.take<double>(rc);
+  double* R = c.take<double>(cc);
+  double* sig = c.take<double>(cols);
+  double* UJ = c.take<double>(cc);
+  double* W = c.take<double>(cc);
+  char* obase = c.take<char>(ob);
+  char* jbase = c.take<char>(jb);
+  void* sc = c.take<char>(sb);
+  Carver oc(obase, ob), jc(jbase, jb);
+  OrthWs ow = orth_ws_carve(oc, rows, cols, RSVD_F64, false);
+  JacobiWs jw = jacobi_ws_carve(jc, cols, cols);
+  rsvd_status s = RSVD_OK;
+  auto run = [&]() -> rsvd_status {
+    RSVD_CUDA(cudaMemsetAsync(ow.status, 0, sizeof(int), st));
+    RSVD_CUDA(cudaMemsetAsync(jw.status, 0, sizeof(int), st));
+    // row-major FP64 T: T[i][c] = A[i][c] (m >= n) or A[c][i] (m < n), written
+    // as the column-major cols x rows gather
+    if (A.dtype == RSVD_F64)
+      RSVD_TRY(gather_colmajor_f64<double>(cols, rows, static_cast<const double*>(A.data), m >= n ? 1 : A.ld,
+                                           m >= n ? A.ld : 1, T, st));
+    else
+      RSVD_TRY(gather_colmajor_f64<float>(cols, rows, static_cast<const float*>(A.data), m >= n ? 1 : A.ld,
+                                          m >= n ? A.ld : 1, T, st));
+    RSVD_TRY(orth_panel<double>(rows, cols, T, cols, Q, cols, R, ow, st, false));
+    RSVD_TRY(jacobi_svd(cols, cols, R, sig, UJ, W, jw, st));
+    RSVD_TRY(simt_gemm<double>(rows, cols, cols, Q, cols, false, W, cols, UA, cols, false, 1, cols, nullptr, st));
+    const double* Usrc = m >= n ? UA : UJ;  // m x t
+    const double* Vsrc = m >= n ? UJ : UA;  // n x t
+    if (A.dtype == RSVD_F64) {
+      double* Ud = static_cast<double*>(U);
+      double* Vd = static_cast<double*>(V);
+      RSVD_TRY((convert_matrix<double, double>(m, cols, Usrc, cols, Ud, cols, st)));
+      RSVD_TRY((convert_matrix<double, double>(n, cols, Vsrc, cols, Vd, cols, st)));
+      RSVD_TRY((convert_matrix<double, double>(1, cols, sig, cols, static_cast<double*>(S), cols, st)));
+      RSVD_TRY(normalise_signs<double>(m, n, cols, Ud, cols, Vd, cols, sc, sb, st));
+    } else {
+      float* Uf = static_cast<float*>(U);
+      float* Vf = static_cast<float*>(V);
+      RSVD_TRY((convert_matrix<double, float>(m, cols, Usrc, cols, Uf, cols, st)));
+      RSVD_TRY((convert_matrix<double, float>(n, cols, Vsrc, cols, Vf, cols, st)));
+      RSVD_TRY((convert_matrix<double, float>(1, cols, sig, cols, static_cast<float*>(S), cols, st)));
+      RSVD_TRY(normalise_signs<float>(m, n, cols, Uf, cols, Vf, cols, sc, sb, st));
+    }
+    RSVD_TRY(read_device_status(ow.status, st));
+    return read_device_status(jw.status, st);
+  };
+  s = run();
+  cudaStreamSynchronize(st);
+  cudaFree(ws);
+  return s;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* rsvd_status_str(rsvd_status s) {
@@ -987,10 +1066,10 @@ rsvd_status rsvd_full(const rsvd_matrix* A, void* U, void* S, void* V, void* str
   if (!A || !U || !S || !V || A->kind != RSVD_DENSE || A->location != RSVD_ON_DEVICE || !A->data)
     return fail(RSVD_ERR_INVALID_ARG, "rsvd_full: need a dense device matrix and outputs");
   const int64_t m = A->m, n = A->n, t = m < n ? m : n;
-  if (m < 1 || n < 1 || t > 256 || A->ld < n || (A->dtype != RSVD_F64 && A->dtype != RSVD_F32))
-    return fail(RSVD_ERR_INVALID_ARG, "rsvd_full: need min(m, n) <= 256, ld >= n, F32 or F64");
-  if (m * n > ((int64_t)1 << 24)) return fail(RSVD_ERR_INVALID_ARG, "rsvd_full: more than 2^24 entries");
+  if (m < 1 || n < 1 || t > 512 || A->ld < n || (A->dtype != RSVD_F64 && A->dtype != RSVD_F32))
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_full: need min(m, n) <= 512, ld >= n, F32 or F64");
   cudaStream_t st = as_stream(stream);
+  if (t > 256 || m * n > ((int64_t)1 << 24)) return full_svd_tall(*A, U, S, V, st);
   // One-sided Jacobi on the columns of A (m >= n) or of A^T (m < n), in FP64.
   //   m >= n: A W = U diag(s)   -> U = Uo, V = W
   //   m <  n: A^T W = V diag(s) -> V = Uo, U = W

@@ -197,3 +197,41 @@ def test_full_svd_matches_oracle(g, m, n, dtype):
     tol = 1e-12 if dtype == "f64" else 1e-5
     assert np.max(np.abs(S - So) / So) < tol
     assert np.linalg.norm((U * S) @ V.T - Ad.cpu().numpy()) < 10 * tol * np.linalg.norm(A)
+
+
+# min(m, n) above 256 or more than 2^24 entries: CholeskyQR2 of A (or A^T) and
+# the square Jacobi on R
+@pytest.mark.parametrize("m,n,dtype", [(6000, 264, "f64"), (264, 6000, "f32")])
+def test_full_svd_large_path_matches_oracle(g, m, n, dtype):
+    rng = np.random.default_rng(m + 7 * n)
+    A = rng.standard_normal((m, n))
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    Ad = torch.as_tensor(A, dtype=tdt, device="cuda")
+    U, S, V = (t.cpu().numpy().astype(np.float64) for t in g.full_svd(Ad))
+    Ah = Ad.cpu().numpy().astype(np.float64)
+    Uo, So, Vo = OR.full_svd(Ah)
+    tol = 1e-11 if dtype == "f64" else 1e-5
+    t = min(m, n)
+    assert np.max(np.abs(S - So) / So) < tol
+    assert np.linalg.norm(U.T @ U - np.eye(t)) < 10 * tol and np.linalg.norm(V.T @ V - np.eye(t)) < 10 * tol
+    assert np.linalg.norm((U * S) @ V.T - Ah) < 10 * tol * np.linalg.norm(Ah)
+
+
+@pytest.mark.parametrize("m,n,dtype", [(200000, 88, "f32"), (600, 512, "f64")])
+def test_full_svd_large_path_properties(g, m, n, dtype):
+    # sizes beyond what the oracle finishes in seconds: orthonormal factors,
+    # descending S and A V = U S, A^T U = V S, which fix the SVD
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    gen = torch.Generator(device="cuda").manual_seed(m * n)
+    Ad = torch.randn(m, n, generator=gen, dtype=tdt, device="cuda")
+    U, S, V = (t.double() for t in g.full_svd(Ad))
+    A64 = Ad.double()
+    tol = 1e-12 if dtype == "f64" else 1e-6
+    t = min(m, n)
+    eye = torch.eye(t, dtype=torch.float64, device="cuda")
+    assert bool((S[:-1] >= S[1:]).all()) and float(S[-1]) > 0
+    assert float(torch.linalg.norm(U.T @ U - eye)) < 100 * tol
+    assert float(torch.linalg.norm(V.T @ V - eye)) < 100 * tol
+    nA = float(torch.linalg.norm(A64))
+    assert float(torch.linalg.norm(A64 @ V - U * S)) < 100 * tol * nA
+    assert float(torch.linalg.norm(A64.T @ U - V * S)) < 100 * tol * nA
