@@ -372,6 +372,22 @@ size_t rsvd_spmm_workspace(int64_t nnz, int32_t r);
 rsvd_status rsvd_csr_transpose(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                                const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val);
 
+/* Host (CPU) conversion of a sparse m x n matrix in coordinate (COO) format
+ * (Section 3.3: structure of arrays, row and column indices of 32 or 64 bits)
+ * into the CSR the sparse A-passes take.  Inputs: nnz entries (rowidx[e],
+ * colidx[e], val[e]), index arrays of index_bits = 32 (int32_t) or 64
+ * (int64_t), in any order; repeated (i, j) pairs stay separate entries, so the
+ * products see their sum.  Outputs, caller-allocated host arrays: rowptr
+ * (m+1), out_colidx and out_val (nnz).  Within each row the entries keep their
+ * COO order (a stable counting sort; the result does not depend on the
+ * number of threads used).  The CSR of A^T, for A.t_rowptr/t_colidx/t_val,
+ * is the same call with m and n and the two index arrays swapped.
+ * Errors: INVALID_ARG (index outside [0, m) x [0, n), index_bits not 32 or 64,
+ * nnz >= 2^31 or n >= 2^31, NULL array). */
+rsvd_status rsvd_coo_to_csr(int64_t m, int64_t n, int64_t nnz, int32_t index_bits, const void* rowidx,
+                            const void* colidx, const float* val, int32_t* rowptr, int32_t* out_colidx,
+                            float* out_val);
+
 /* FP8 storage of a dense F32 device matrix A (m x n): E4M3 codes (OCP 8-bit
  * floating point, 2023: bias 7, three mantissa bits, largest finite 448,
  * rounding to nearest even, saturating) with one scale per tile of rows

@@ -71,3 +71,29 @@ def csr_transpose(m: int, n: int, rowptr, colidx, vals):
         trp.append(len(tci))
     return (np.array(trp, dtype=np.int64), np.array(tci, dtype=np.int64),
             np.array(tv, dtype=np.asarray(vals).dtype))
+
+
+def coo_to_csr(m: int, n: int, rowidx, colidx, vals):
+    """CSR of an m x n matrix given in coordinate format (Section 3.3).
+
+    Every entry e = (rowidx[e], colidx[e], vals[e]) goes to the list of its
+    row, in the order the entries are given; repeated positions stay separate
+    entries (the matrix is their sum).  Raises ValueError for an index outside
+    [0, m) x [0, n).
+    """
+    rows_of = [[] for _ in range(m)]
+    for e in range(len(vals)):
+        i, j = int(rowidx[e]), int(colidx[e])
+        if not (0 <= i < m and 0 <= j < n):
+            raise ValueError("COO index out of range")
+        rows_of[i].append((j, vals[e]))
+    rp = [0]
+    ci = []
+    v = []
+    for i in range(m):
+        for j, x in rows_of[i]:
+            ci.append(j)
+            v.append(x)
+        rp.append(len(ci))
+    return (np.array(rp, dtype=np.int64), np.array(ci, dtype=np.int64),
+            np.array(v, dtype=np.asarray(vals).dtype))

@@ -14,6 +14,7 @@ gaussian / tile_map / apass / orth / small_svd
                               the individual steps (Section 2.1 steps 1-6,
                               Section 3.1 tile map)
 csr_transpose                 host CSR of A^T for the sparse A-passes (Section 3.3)
+coo_to_csr                    host CSR of a COO matrix (or of its transpose)
 fp8_quantize                  E4M3 codes of A with per-tile scales (the FP8 variant)
 """
 
@@ -25,7 +26,7 @@ from . import _lib
 from ._lib import RsvdError, load  # noqa: F401
 
 __all__ = ["rsvd", "Plan", "full_svd", "gaussian", "tile_map", "apass", "orth", "small_svd",
-           "small_svd_noalloc", "csr_transpose", "fp8_quantize", "checkpoint_info", "RsvdError", "load"]
+           "small_svd_noalloc", "csr_transpose", "coo_to_csr", "fp8_quantize", "checkpoint_info", "RsvdError", "load"]
 
 
 def _torch():
@@ -74,6 +75,16 @@ def _csr_arrays(A):
     if v.dtype != torch.float32:
         raise TypeError(f"CSR values must be float32, got {v.dtype}")
     return rp, ci, v.contiguous()
+
+
+def _is_coo(A) -> bool:
+    torch = _torch()
+    return getattr(A, "layout", None) == torch.sparse_coo
+
+
+def _coo_pair(A):
+    """Host CSR of a torch sparse COO matrix and of its transpose (library conversion)."""
+    return coo_to_csr(A), coo_to_csr(A, transpose=True)
 
 
 def _csr_desc(A, At=None):
@@ -135,7 +146,8 @@ class Plan:
 
     def run(self, A, U=None, S=None, V=None, At=None):
         """Factor A (device tensor, or pinned host tensor; for CSR plans a torch
-        sparse CSR tensor, with the CSR of A^T in `At` if the caller has it);
+        sparse CSR tensor, with the CSR of A^T in `At` if the caller has it, or a
+        torch sparse COO tensor);
         returns (U, S, V) on the device."""
         torch = _torch()
         tdt = torch.float64 if self.dtype == "f64" else torch.float32
@@ -146,6 +158,8 @@ class Plan:
             S = torch.empty(self.k, dtype=tdt, device=dev)
         if V is None:
             V = torch.empty(self.n, self.k, dtype=tdt, device=dev)
+        if _is_coo(A):
+            A, At = _coo_pair(A)
         if _is_csr(A):
             d, keep = _csr_desc(A, At)
         else:
@@ -228,12 +242,16 @@ def _rsvd_function():
 
 def rsvd(A, k, p=10, q=2, seed=0, mem_cap=0, prec=None, mb=0, nb=0, refine=True, At=None):
     """Rank-k randomized SVD of a dense float32/float64 matrix (CUDA or pinned
-    host tensor) or of a float32 torch sparse CSR tensor (CUDA or host; `At`
-    optionally its transpose in CSR form, else built by the library).
+    host tensor), of a float32 torch sparse CSR tensor (CUDA or host; `At`
+    optionally its transpose in CSR form, else built by the library), or of a
+    float32 torch sparse COO tensor (converted to the CSR of A and of A^T on
+    the host by the library; repeated entries add up).
 
     If a dense A requires grad, the result is differentiable through the
     truncated-SVD adjoint (rsvd_backward)."""
     torch = _torch()
+    if _is_coo(A):
+        A, At = _coo_pair(A)
     if _is_csr(A):
         plan = Plan(A.shape[0], A.shape[1], k, p, q, seed, mem_cap, prec or "fp32", "f32", mb, nb, refine,
                     kind="csr")
@@ -345,6 +363,36 @@ def csr_transpose(A):
                                      C.c_void_p(v.data_ptr()), C.c_void_p(trp.data_ptr()),
                                      C.c_void_p(tci.data_ptr()), C.c_void_p(tv.data_ptr())))
     return torch.sparse_csr_tensor(trp, tci, tv, size=(n, m))
+
+
+def coo_to_csr(A, transpose=False):
+    """Host CSR (torch sparse CSR tensor) of a torch sparse COO matrix A with
+    float32 values, or of A^T with transpose=True, by the library's stable
+    counting sort (rsvd_coo_to_csr): entries keep their COO order within each
+    row, repeated entries stay separate.  A may be uncoalesced; CUDA tensors
+    are copied to the host first."""
+    torch = _torch()
+    if A.dim() != 2:
+        raise ValueError("A must be a 2-D sparse COO tensor")
+    A = A.cpu()
+    idx = A._indices()
+    ri = idx[1 if transpose else 0].to(torch.int64).contiguous()
+    ci = idx[0 if transpose else 1].to(torch.int64).contiguous()
+    v = A._values()
+    if v.dtype != torch.float32:
+        raise TypeError(f"COO values must be float32, got {v.dtype}")
+    v = v.contiguous()
+    m, n = A.shape
+    if transpose:
+        m, n = n, m
+    nnz = v.numel()
+    rp = torch.empty(m + 1, dtype=torch.int32)
+    oci = torch.empty(nnz, dtype=torch.int32)
+    ov = torch.empty(nnz, dtype=torch.float32)
+    _check(load().rsvd_coo_to_csr(m, n, nnz, 64, C.c_void_p(ri.data_ptr()), C.c_void_p(ci.data_ptr()),
+                                  C.c_void_p(v.data_ptr()), C.c_void_p(rp.data_ptr()),
+                                  C.c_void_p(oci.data_ptr()), C.c_void_p(ov.data_ptr())))
+    return torch.sparse_csr_tensor(rp, oci, ov, size=(m, n))
 
 
 def fp8_quantize(A, qm=0, qn=0):

@@ -1004,6 +1004,12 @@ rsvd_status rsvd_csr_transpose(int64_t m, int64_t n, const int32_t* rowptr, cons
   return csr_transpose_host(m, n, rowptr, colidx, val, t_rowptr, t_colidx, t_val);
 }
 
+rsvd_status rsvd_coo_to_csr(int64_t m, int64_t n, int64_t nnz, int32_t index_bits, const void* rowidx,
+                            const void* colidx, const float* val, int32_t* rowptr, int32_t* out_colidx,
+                            float* out_val) {
+  return coo_to_csr_host(m, n, nnz, index_bits, rowidx, colidx, val, rowptr, out_colidx, out_val);
+}
+
 rsvd_status rsvd_plan_set_checkpoint(rsvd_plan_t P, const char* path, int32_t stop_after_step) {
   if (!P) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_set_checkpoint: NULL plan");
   if (path && *path && P->auto_q)

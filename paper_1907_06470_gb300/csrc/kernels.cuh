@@ -136,6 +136,10 @@ rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* col
 // Host CSR of A^T (n rows) from the CSR of A (m rows); stable, deterministic.
 rsvd_status csr_transpose_host(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                                const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val);
+// COO (index arrays of index_bits = 32 or 64) to CSR, stable within rows.
+rsvd_status coo_to_csr_host(int64_t m, int64_t n, int64_t nnz, int index_bits, const void* rowidx,
+                            const void* colidx, const float* val, int32_t* rowptr, int32_t* out_colidx,
+                            float* out_val);
 
 // checkpoint.cu -- persistence of the range finder's basis (Section 3.8).
 struct CkptHeader {

@@ -404,4 +404,75 @@ rsvd_status csr_transpose_host(int64_t m, int64_t n, const int32_t* rowptr, cons
   return RSVD_OK;
 }
 
+// COO (Section 3.3: the paper's sparse format, row and column index arrays of
+// 32 or 64 bits, structure of arrays) to CSR on the host: a stable counting
+// sort by row.  T threads take contiguous chunks of the entries; the
+// per-(thread, row) offsets are laid out row-major over threads, so thread t's
+// entries of a row follow those of threads < t and the entries of each row
+// keep their COO order whatever T is.
+template <typename I>
+rsvd_status coo_to_csr_typed(int64_t m, int64_t n, int64_t nnz, const I* rowidx, const I* colidx,
+                             const float* val, int32_t* rowptr, int32_t* out_colidx, float* out_val) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int T = (int)std::min<int64_t>({(int64_t)(hw ? hw : 1), 32, std::max<int64_t>(1, nnz >> 20)});
+  if (T < 1) T = 1;
+  std::vector<int64_t> e0(T + 1);
+  for (int t = 0; t <= T; ++t) e0[t] = nnz * t / T;
+  std::vector<int64_t> cnt((size_t)T * m, 0);  // cnt[t*m + i]
+  std::vector<int> bad(T, 0);
+  auto count = [&](int t) {
+    int64_t* c = cnt.data() + (size_t)t * m;
+    for (int64_t e = e0[t]; e < e0[t + 1]; ++e) {
+      const int64_t i = (int64_t)rowidx[e], j = (int64_t)colidx[e];
+      if (i < 0 || i >= m || j < 0 || j >= n) { bad[t] = 1; return; }
+      ++c[i];
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < T; ++t) th.emplace_back(count, t);
+  count(0);
+  for (auto& x : th) x.join();
+  th.clear();
+  for (int t = 0; t < T; ++t)
+    if (bad[t]) return fail(RSVD_ERR_INVALID_ARG, "coo_to_csr: index out of range");
+  int64_t run = 0;
+  for (int64_t i = 0; i < m; ++i) {
+    rowptr[i] = (int32_t)run;
+    for (int t = 0; t < T; ++t) {
+      const int64_t c = cnt[(size_t)t * m + i];
+      cnt[(size_t)t * m + i] = run;
+      run += c;
+    }
+  }
+  rowptr[m] = (int32_t)run;
+  auto scatter = [&](int t) {
+    int64_t* off = cnt.data() + (size_t)t * m;
+    for (int64_t e = e0[t]; e < e0[t + 1]; ++e) {
+      const int64_t pos = off[(int64_t)rowidx[e]]++;
+      out_colidx[pos] = (int32_t)colidx[e];
+      out_val[pos] = val[e];
+    }
+  };
+  for (int t = 1; t < T; ++t) th.emplace_back(scatter, t);
+  scatter(0);
+  for (auto& x : th) x.join();
+  return RSVD_OK;
+}
+
+rsvd_status coo_to_csr_host(int64_t m, int64_t n, int64_t nnz, int index_bits, const void* rowidx,
+                            const void* colidx, const float* val, int32_t* rowptr, int32_t* out_colidx,
+                            float* out_val) {
+  if (m < 0 || n < 0 || nnz < 0 || !rowptr) return fail(RSVD_ERR_INVALID_ARG, "coo_to_csr: bad arguments");
+  if (index_bits != 32 && index_bits != 64) return fail(RSVD_ERR_INVALID_ARG, "coo_to_csr: index_bits must be 32 or 64");
+  if (nnz >= ((int64_t)1 << 31) || n > ((int64_t)1 << 31) - 1)
+    return fail(RSVD_ERR_INVALID_ARG, "coo_to_csr: the CSR holds 32-bit offsets and column indices");
+  if (nnz > 0 && (!rowidx || !colidx || !val || !out_colidx || !out_val))
+    return fail(RSVD_ERR_INVALID_ARG, "coo_to_csr: NULL index or value array");
+  if (index_bits == 32)
+    return coo_to_csr_typed<int32_t>(m, n, nnz, static_cast<const int32_t*>(rowidx),
+                                     static_cast<const int32_t*>(colidx), val, rowptr, out_colidx, out_val);
+  return coo_to_csr_typed<int64_t>(m, n, nnz, static_cast<const int64_t*>(rowidx),
+                                   static_cast<const int64_t*>(colidx), val, rowptr, out_colidx, out_val);
+}
+
 }  // namespace rsvd

@@ -134,6 +134,77 @@ def test_csr_transpose_edge_cases(lib):
     assert _lib_transpose(lib, 2, 3, [0, 2, 1], [0, 1], [1.0, 1.0])[0] == 1
 
 
+def _lib_coo(lib, m, n, ri, ci, v, bits):
+    import numpy as np
+    it = np.int32 if bits == 32 else np.int64
+    ri = np.ascontiguousarray(ri, dtype=it)
+    ci = np.ascontiguousarray(ci, dtype=it)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    nnz = v.size
+    rp = np.full(m + 1, -7, dtype=np.int32)
+    oci = np.full(max(nnz, 1), -7, dtype=np.int32)
+    ov = np.full(max(nnz, 1), np.nan, dtype=np.float32)
+    P = lambda a: a.ctypes.data_as(C.c_void_p)
+    st = lib.rsvd_coo_to_csr(m, n, nnz, bits, P(ri), P(ci), P(v), P(rp), P(oci), P(ov))
+    return st, rp, oci[:nnz], ov[:nnz]
+
+
+@pytest.mark.parametrize("m,n,nnz,bits,seed", [(300, 200, 1000, 32, 3), (300, 200, 1000, 64, 4),
+                                               (20000, 5000, 400000, 64, 1004),
+                                               (200000, 50000, 4_000_000, 32, 1104)])
+def test_coo_to_csr_is_bit_exact_with_oracle(lib, m, n, nnz, bits, seed):
+    """The library's host COO -> CSR (threaded for large nnz) against the
+    oracle's row-by-row bucketing, on the sparse workload's entries given in a
+    shuffled order with some of them split into repeated entries."""
+    import numpy as np
+    from synth import zipf_csr
+    rp, ci, v = zipf_csr(m, n, nnz, seed)
+    rows = np.repeat(np.arange(m), np.diff(rp))
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(rows.size)
+    ri, cj, vv = rows[order], np.asarray(ci)[order], np.asarray(v, np.float32)[order]
+    dup = rng.choice(ri.size, size=ri.size // 50, replace=False)   # split 2% of the entries in two
+    ri = np.concatenate([ri, ri[dup]])
+    cj = np.concatenate([cj, cj[dup]])
+    half = (vv[dup] * np.float32(0.5)).astype(np.float32)
+    vv = vv.copy()
+    vv[dup] = half
+    vv = np.concatenate([vv, half])
+    st, orp, oci, ov = _lib_coo(lib, m, n, ri, cj, vv, bits)
+    assert st == 0
+    if nnz <= 400000:
+        erp, eci, ev = T.coo_to_csr(m, n, ri, cj, vv)
+    else:  # the oracle's Python loop is slow at 4e6 entries: its definition via a stable sort
+        perm = np.argsort(ri, kind="stable")
+        eci, ev = cj[perm], vv[perm]
+        erp = np.concatenate([[0], np.cumsum(np.bincount(ri, minlength=m))])
+    assert np.array_equal(orp, erp) and np.array_equal(oci, eci)
+    assert np.array_equal(ov.view(np.uint32), np.asarray(ev, np.float32).view(np.uint32))
+
+
+def test_coo_to_csr_edge_cases(lib):
+    import numpy as np
+    st, rp, ci, v = _lib_coo(lib, 3, 2, [], [], [], 32)
+    assert st == 0 and rp.tolist() == [0, 0, 0, 0]
+    st, rp, ci, v = _lib_coo(lib, 0, 4, [], [], [], 64)
+    assert st == 0 and rp.tolist() == [0]
+    # the hand example of the oracle's pin
+    st, rp, ci, v = _lib_coo(lib, 3, 4, [2, 0, 2, 1, 2, 0], [1, 3, 0, 2, 1, 0], [1, 2, 3, 4, 5, 6], 64)
+    assert st == 0 and rp.tolist() == [0, 2, 3, 6]
+    assert ci.tolist() == [3, 0, 2, 1, 0, 1] and v.tolist() == [2.0, 6.0, 4.0, 1.0, 3.0, 5.0]
+    # indices out of range (row, column, negative, 64-bit beyond 2^32) and bad index widths
+    assert _lib_coo(lib, 3, 4, [3], [0], [1.0], 32)[0] == 1
+    assert _lib_coo(lib, 3, 4, [0], [4], [1.0], 32)[0] == 1
+    assert _lib_coo(lib, 3, 4, [-1], [0], [1.0], 64)[0] == 1
+    assert _lib_coo(lib, 3, 4, [0], [(1 << 32) + 1], [1.0], 64)[0] == 1
+    z = np.zeros(1, dtype=np.int32)
+    P = lambda a: a.ctypes.data_as(C.c_void_p)
+    rp = np.zeros(4, dtype=np.int32)
+    f = np.zeros(1, dtype=np.float32)
+    assert lib.rsvd_coo_to_csr(3, 4, 1, 16, P(z), P(z), P(f), P(rp), P(z), P(f)) == 1
+    assert lib.rsvd_coo_to_csr(3, 4, 1, 32, None, P(z), P(f), P(rp), P(z), P(f)) == 1
+
+
 def test_csr_plan_rules(lib):
     from paper_1907_06470_gb300 import _lib
     h = C.c_void_p()

@@ -117,6 +117,37 @@ def test_csr_input_locations_agree_bitwise(g, zipf):
             assert torch.equal(s, t)
 
 
+def test_coo_input(g, zipf):
+    """A COO matrix (Section 3.3's format) is converted to the CSR of A and of
+    A^T: in row order it runs bitwise like the CSR input; shuffled, with 2% of
+    the entries split in two, it is the same matrix summed in another order
+    and agrees with the FP64 oracle to the FP32 bar."""
+    m, n, rp, ci, v = zipf
+    k, p, q, seed = 20, 10, 2, 7
+    rows = np.repeat(np.arange(m), np.diff(rp))
+    idx = torch.as_tensor(np.stack([rows, np.asarray(ci)]), dtype=torch.int64)
+    coo = torch.sparse_coo_tensor(idx, torch.as_tensor(v), size=(m, n))
+    a = g.rsvd(_torch_csr(m, n, rp, ci, v, "cpu"), k, p, q, seed)
+    b = g.rsvd(coo, k, p, q, seed)
+    c = g.rsvd(coo.to("cuda"), k, p, q, seed)
+    for x in (b, c):
+        for s_, t_ in zip(a, x):
+            assert torch.equal(s_, t_)
+    rng = np.random.default_rng(11)
+    order = rng.permutation(rows.size)
+    ri, cj, vv = rows[order], np.asarray(ci)[order], np.asarray(v, np.float32)[order].copy()
+    dup = rng.choice(ri.size, size=ri.size // 50, replace=False)
+    half = (vv[dup] * np.float32(0.5)).astype(np.float32)
+    vv[dup] = half
+    idx = torch.as_tensor(np.stack([np.concatenate([ri, ri[dup]]), np.concatenate([cj, cj[dup]])]),
+                          dtype=torch.int64)
+    shuffled = torch.sparse_coo_tensor(idx, torch.as_tensor(np.concatenate([vv, half])), size=(m, n))
+    U, S, V = (t.cpu().numpy().astype(np.float64) for t in g.rsvd(shuffled, k, p, q, seed))
+    Uo, So, Vo = OR.rsvd(OL.CSR(m, n, rp, ci, v), k, p, q, seed, "f32")
+    assert sigma_rel_err(S, So) <= 1e-5
+    assert cluster_safe_angles(U, Uo, So, 8, rel_gap=1e-2) <= 1e-4
+
+
 def test_csr_rsvd_r350_matches_oracle(g):
     """r = k + p = 350 (the sparse workload's sketch width): the FP64-only Jacobi
     and the global-memory Cholesky."""

@@ -69,3 +69,50 @@ def test_csr_transpose_is_exact():
         for e in range(trp[j], trp[j + 1]):
             Dt[j, tci[e]] = tv[e]
     assert np.array_equal(Dt, D.T)
+
+
+def test_coo_to_csr_hand_example():
+    # a 3 x 4 matrix given out of order, with (2, 1) stored twice; rows keep
+    # the given order of their entries
+    ri = [2, 0, 2, 1, 2, 0]
+    ci = [1, 3, 0, 2, 1, 0]
+    v = np.array([1.0, 2.0, 3.0, 4.0, 5.0, 6.0], dtype=np.float32)
+    rp, oci, ov = T.coo_to_csr(3, 4, ri, ci, v)
+    assert rp.tolist() == [0, 2, 3, 6]
+    assert oci.tolist() == [3, 0, 2, 1, 0, 1]
+    assert ov.tolist() == [2.0, 6.0, 4.0, 1.0, 3.0, 5.0]
+    with pytest.raises(ValueError):
+        T.coo_to_csr(3, 4, [3], [0], np.ones(1, np.float32))
+    with pytest.raises(ValueError):
+        T.coo_to_csr(3, 4, [0], [-1], np.ones(1, np.float32))
+    rp, oci, ov = T.coo_to_csr(2, 2, [], [], np.zeros(0, np.float32))
+    assert rp.tolist() == [0, 0, 0] and oci.size == 0
+
+
+def test_coo_to_csr_gives_the_same_matrix():
+    # the dense matrix summed from the COO entries equals the one read back
+    # from the CSR, on shuffled entries with repeats
+    rng = np.random.default_rng(5)
+    m, n, nnz = 17, 13, 120
+    ri = rng.integers(0, m, nnz)
+    ci = rng.integers(0, n, nnz)
+    v = rng.standard_normal(nnz)
+    D = np.zeros((m, n))
+    np.add.at(D, (ri, ci), v)
+    rp, oci, ov = T.coo_to_csr(m, n, ri, ci, v)
+    Dc = np.zeros((m, n))
+    for i in range(m):
+        for e in range(rp[i], rp[i + 1]):
+            Dc[i, oci[e]] += ov[e]
+    assert np.allclose(Dc, D, rtol=0, atol=1e-12)
+    assert np.all(np.diff(rp) == np.bincount(ri, minlength=m))
+
+
+def test_coo_of_the_swapped_indices_is_the_csr_transpose():
+    # the COO of A in row order, read with rows and columns swapped, gives the
+    # CSR of A^T that the entry-by-entry transpose builds
+    D, rp, ci, v = _random_csr(19, 11, 0.3, 4)
+    rows = np.repeat(np.arange(19), np.diff(rp))
+    trp, tci, tv = T.coo_to_csr(11, 19, ci, rows, v)
+    erp, eci, ev = T.csr_transpose(19, 11, rp, ci, v)
+    assert np.array_equal(trp, erp) and np.array_equal(tci, eci) and np.array_equal(tv, ev)
