@@ -62,7 +62,7 @@ typedef enum {
   RSVD_PREC_FP8 = 4
 } rsvd_prec;
 
-typedef enum { RSVD_F64 = 0, RSVD_F32 = 1, RSVD_BF16 = 2 } rsvd_dtype;
+typedef enum { RSVD_F64 = 0, RSVD_F32 = 1, RSVD_BF16 = 2, RSVD_F16 = 3 } rsvd_dtype;
 typedef enum { RSVD_DENSE = 0, RSVD_CSR = 1 } rsvd_kind;
 typedef enum { RSVD_ON_DEVICE = 0, RSVD_ON_HOST = 1 } rsvd_location;
 
@@ -88,7 +88,9 @@ typedef struct {
 /* Descriptor of the input matrix A (m x n). */
 typedef struct {
   int32_t kind;      /* rsvd_kind: DENSE row-major, or CSR */
-  int32_t dtype;     /* rsvd_dtype of the values: F64 or F32 (CSR: F32) */
+  int32_t dtype;     /* rsvd_dtype of the values: F64 or F32 (CSR: F32); a dense
+                        A may also be stored in 16 bits, BF16 or F16 (IEEE
+                        half), for F32 plans with BF16 precision (rsvd_run) */
   int32_t location;  /* rsvd_location of the data */
   int32_t reserved;
   int64_t m, n;
@@ -185,6 +187,14 @@ rsvd_status rsvd_plan_info(rsvd_plan_t plan, rsvd_plan_info_t* out);
  * cap when there is one): the first forward pass writes it and the later
  * BF16 passes read it (the same operands, so the same result; half the bytes
  * per pass).  Without room for it every pass reads the FP32 A.
+ * 16-bit storage (Section 3.2): an F32 plan with BF16 precision also takes a
+ * dense A stored as BF16 or F16 (IEEE half; device: ld % 8 == 0 and a 16-byte
+ * aligned base; host: copied to the device in core, never streamed), read
+ * as is by every pass: the panels are rounded to A's 16-bit type (one
+ * tensor-core product takes both operands in one type), and with opts.refine
+ * the pass forming B^T splits its panel in two 16-bit parts (A X_hi + A X_lo,
+ * about 16 significant bits) instead of splitting A, which is exact.  The
+ * SVD is that of the matrix the 16-bit values represent.
  * Outputs (device, plan dtype): U m x k row-major, S k values descending,
  * V n x k row-major, so that A ~ U diag(S) V^T.  Each pair (u_i, v_i) is signed
  * so that the largest-magnitude entry of u_i is positive.  Synchronises

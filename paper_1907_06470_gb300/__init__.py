@@ -45,7 +45,11 @@ def _dtype_code(t):
         return _lib.DTYPE["f64"]
     if t.dtype == torch.float32:
         return _lib.DTYPE["f32"]
-    raise TypeError(f"A must be float32 or float64, got {t.dtype}")
+    if t.dtype == torch.bfloat16:
+        return _lib.DTYPE["bf16"]
+    if t.dtype == torch.float16:
+        return _lib.DTYPE["f16"]
+    raise TypeError(f"A must be float64, float32, bfloat16 or float16, got {t.dtype}")
 
 
 def _dense_desc(A) -> _lib.RsvdMatrix:
@@ -241,7 +245,8 @@ def _rsvd_function():
 
 
 def rsvd(A, k, p=10, q=2, seed=0, mem_cap=0, prec=None, mb=0, nb=0, refine=True, At=None):
-    """Rank-k randomized SVD of a dense float32/float64 matrix (CUDA or pinned
+    """Rank-k randomized SVD of a dense float64/float32 matrix, or of one stored
+    as bfloat16/float16 (FP32 outputs, BF16-precision plan) (CUDA or pinned
     host tensor), of a float32 torch sparse CSR tensor (CUDA or host; `At`
     optionally its transpose in CSR form, else built by the library), or of a
     float32 torch sparse COO tensor (converted to the CSR of A and of A^T on
@@ -260,6 +265,10 @@ def rsvd(A, k, p=10, q=2, seed=0, mem_cap=0, prec=None, mb=0, nb=0, refine=True,
         finally:
             plan.close()
     dtype = "f64" if A.dtype == torch.float64 else "f32"
+    if A.dtype in (torch.bfloat16, torch.float16):  # 16-bit storage: FP32 outputs, tensor-core passes
+        if A.requires_grad:
+            raise TypeError("a bfloat16 or float16 A has no backward pass")
+        prec = prec or "bf16"
     plan = Plan(A.shape[0], A.shape[1], k, p, q, seed, mem_cap, prec, dtype, mb, nb, refine)
     if A.requires_grad:
         return _rsvd_function().apply(A, plan)
@@ -330,13 +339,14 @@ def apass(A, X, trans=False, prec=None, mb=0, nb=0, out=None, At=None, split_lon
                               C.c_void_p(ws.data_ptr() if wsb else None), wsb, _stream_ptr()))
         del keep
         return out
+    a16 = A.dtype in (torch.bfloat16, torch.float16)  # stored in 16 bits: FP32 panels and output
     if prec is None:
-        prec = "fp64" if A.dtype == torch.float64 else "fp32"
+        prec = "fp64" if A.dtype == torch.float64 else ("bf16" if a16 else "fp32")
     m, n = A.shape
     r = X.shape[1]
     M = n if trans else m
     if out is None:
-        out = torch.empty(M, r, dtype=A.dtype, device=A.device)
+        out = torch.empty(M, r, dtype=torch.float32 if a16 else A.dtype, device=A.device)
     lib = load()
     wsb = lib.rsvd_apass_workspace(m, n, r, int(trans), _lib.PREC[prec], mb, nb)
     ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=A.device)

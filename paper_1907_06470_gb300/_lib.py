@@ -18,7 +18,7 @@ STATUS_NAMES = {
     8: "RSVD_ERR_UNSUPPORTED", 9: "RSVD_ERR_INTERRUPTED",
 }
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3, "fp8": 4}
-DTYPE = {"f64": 0, "f32": 1, "bf16": 2}
+DTYPE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 DENSE, CSR = 0, 1
 ON_DEVICE, ON_HOST = 0, 1
 

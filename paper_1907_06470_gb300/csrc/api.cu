@@ -79,7 +79,7 @@ PassShape pass_shape(int64_t m, int64_t n, int trans, int64_t mb, int64_t nb) {
   return s;
 }
 
-size_t elem_size(int dtype) { return dtype == RSVD_F64 ? 8 : (dtype == RSVD_BF16 ? 2 : 4); }
+size_t elem_size(int dtype) { return dtype == RSVD_F64 ? 8 : ((dtype == RSVD_BF16 || dtype == RSVD_F16) ? 2 : 4); }
 
 }  // namespace
 
@@ -104,6 +104,14 @@ rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const 
     return simt_gemm<double>(s.M, r, s.K, static_cast<const double*>(A.data), A.ld, trans != 0,
                              static_cast<const double*>(X), ldx, static_cast<double*>(Y), ldy, accumulate,
                              s.nsplit, s.kchunk, static_cast<double*>(ws), stream);
+  }
+  if (A.dtype == RSVD_BF16 || A.dtype == RSVD_F16) {  // Section 3.2: A stored in 16 bits
+    Bf16Source a16;
+    a16.data = static_cast<const uint16_t*>(A.data);
+    a16.m = A.m; a16.n = A.n; a16.ld = A.ld;
+    a16.f16 = A.dtype == RSVD_F16 ? 1 : 0;
+    return tc_apass_from_16(a16, trans, prec, r, static_cast<const float*>(X), ldx, static_cast<float*>(Y), ldy, ws,
+                            ws_bytes, status, stream, accumulate);
   }
   if (A.dtype != RSVD_F32) return fail(RSVD_ERR_INVALID_ARG, "apass: FP32/BF16 precision needs FP32 A");
   if (prec == RSVD_PREC_FP32) {
@@ -362,8 +370,10 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   // BF16 plans in core stream a BF16 copy of A after the first plain forward
   // pass has written it: half the bytes per pass, the same operands.
   bool use16 = false;
+  // A stored in 16 bits by the caller (Section 3.2): every pass reads it as is
+  const bool a16_in = A.kind == RSVD_DENSE && (A.dtype == RSVD_BF16 || A.dtype == RSVD_F16);
   if constexpr (std::is_same<T, float>::value) {
-    if (prec == RSVD_PREC_BF16 && A.kind == RSVD_DENSE && !P->streaming && round_up(r, 16) <= 256) {
+    if (prec == RSVD_PREC_BF16 && A.kind == RSVD_DENSE && !a16_in && !P->streaming && round_up(r, 16) <= 256) {
       const int64_t ld16 = round_up(n, 64);
       const size_t need = (size_t)m * ld16 * sizeof(uint16_t);
       const bool fits = P->mem_cap == 0 || P->ws_bytes + P->a_copy_bytes + need <= P->mem_cap;
@@ -387,6 +397,12 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     Span sp(pf, trans ? RSVD_STAGE_APASS_TRANS : RSVD_STAGE_APASS_FWD, st);
     ++pf.apass_calls;
     if constexpr (std::is_same<T, float>::value) {
+      if (a16_in) {
+        Bf16Source b;
+        b.data = static_cast<const uint16_t*>(A.data); b.m = m; b.n = n; b.ld = A.ld;
+        b.f16 = A.dtype == RSVD_F16 ? 1 : 0;
+        return tc_apass_from_16(b, trans, pr, r, Xin, ldr, Yout, ldr, P->apass_ws, P->apass_ws_bytes, P->status, st);
+      }
       if (use16 && pr == RSVD_PREC_BF16) {
         if (P->a16_ready) {
           Bf16Source b;
@@ -943,8 +959,13 @@ rsvd_status rsvd_plan_info(rsvd_plan_t P, rsvd_plan_info_t* o) {
 
 rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void* V, void* stream) {
   if (!P || !A || !U || !S || !V) return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: NULL argument");
-  if (A->m != P->m || A->n != P->n || A->dtype != P->dtype)
+  const bool a16 = A->dtype == RSVD_BF16 || A->dtype == RSVD_F16;
+  if (A->m != P->m || A->n != P->n || (A->dtype != P->dtype && !a16))
     return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: A does not match the plan (shape or dtype)");
+  if (a16 && (P->dtype != RSVD_F32 || P->prec != RSVD_PREC_BF16 || A->kind != RSVD_DENSE))
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: a BF16 or FP16 A needs a dense F32 plan with BF16 precision");
+  if (a16 && A->location == RSVD_ON_DEVICE && (A->ld % 8 != 0 || (reinterpret_cast<uintptr_t>(A->data) & 15) != 0))
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: a BF16 or FP16 A needs ld % 8 == 0 and a 16-byte aligned base");
   if (A->kind != P->kind) return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: A's kind (dense/CSR) differs from the plan's");
   cudaStream_t st = as_stream(stream);
   if (A->kind == RSVD_CSR) {
@@ -962,8 +983,11 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
     // Automatic in-core / out-of-core switch (Section 3.5): a host matrix that
     // fits under the cap (or any host matrix when there is no cap) is copied to
     // the device once and processed in core; otherwise its tiles are streamed.
-    const size_t bytes = (size_t)A->m * A->n * elem_size(A->dtype);
+    // device copy: rows of n values (16-bit A: padded to a multiple of 8 for the TMA)
+    const int64_t ldd = a16 ? round_up(A->n, 8) : A->n;
+    const size_t bytes = (size_t)A->m * ldd * elem_size(A->dtype);
     if (P->mem_cap && P->ws_bytes + bytes > P->mem_cap) {
+      if (a16) return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: a BF16 or FP16 A is not streamed (it must fit the cap)");
       if (P->Adev) { cudaFree(P->Adev); P->Adev = nullptr; P->a_copy_bytes = 0; }
       if (P->ws_bytes >= P->mem_cap) return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: no room left for streaming");
       if (P->prec == RSVD_PREC_FP8)
@@ -988,10 +1012,10 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
     }
     const size_t row = (size_t)A->n * elem_size(A->dtype);
     Span sp(P->prof, RSVD_STAGE_H2D, st);
-    RSVD_CUDA(cudaMemcpy2DAsync(P->Adev, row, A->data, (size_t)A->ld * elem_size(A->dtype), row, A->m,
-                                cudaMemcpyHostToDevice, st));
+    RSVD_CUDA(cudaMemcpy2DAsync(P->Adev, (size_t)ldd * elem_size(A->dtype), A->data,
+                                (size_t)A->ld * elem_size(A->dtype), row, A->m, cudaMemcpyHostToDevice, st));
     Ad.data = P->Adev;
-    Ad.ld = A->n;
+    Ad.ld = ldd;
     Ad.location = RSVD_ON_DEVICE;
   }
   if (P->dtype == RSVD_F64)

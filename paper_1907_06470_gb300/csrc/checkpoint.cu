@@ -84,6 +84,8 @@ rsvd_status matrix_fingerprint(const rsvd_matrix& A, uint64_t* out, cudaStream_t
         const int64_t i = ((int64_t)t * 7919 + 13) % A.m, j = ((int64_t)t * 104729 + 7) % A.n;
         double v;
         if (A.dtype == RSVD_F64) v = static_cast<const double*>(A.data)[i * A.ld + j];
+        else if (A.dtype == RSVD_BF16 || A.dtype == RSVD_F16)  // the 16-bit pattern itself
+          v = (double)static_cast<const uint16_t*>(A.data)[i * A.ld + j];
         else v = (double)static_cast<const float*>(A.data)[i * A.ld + j];
         std::memcpy(&h[t], &v, 8);
       }
@@ -96,6 +98,8 @@ rsvd_status matrix_fingerprint(const rsvd_matrix& A, uint64_t* out, cudaStream_t
     if (A.kind == RSVD_DENSE) {
       if (A.dtype == RSVD_F64)
         sample_dense_kernel<double><<<4, 256, 0, st>>>(A.m, A.n, static_cast<const double*>(A.data), A.ld, d);
+      else if (A.dtype == RSVD_BF16 || A.dtype == RSVD_F16)
+        sample_dense_kernel<uint16_t><<<4, 256, 0, st>>>(A.m, A.n, static_cast<const uint16_t*>(A.data), A.ld, d);
       else
         sample_dense_kernel<float><<<4, 256, 0, st>>>(A.m, A.n, static_cast<const float*>(A.data), A.ld, d);
     } else {

@@ -30,7 +30,11 @@
 // converters only move (or, for A^T, transpose) the 16-bit values into the
 // operand layout.  The copy is written by the first forward pass over the FP32
 // A, whose converters store the BF16 values they form anyway, so the later
-// passes see exactly the operands the FP32 source would give.
+// passes see exactly the operands the FP32 source would give.  The same
+// kernels read an A the caller stores in 16 bits (Section 3.2: half-precision
+// storage), BF16 or IEEE FP16; for FP16 the panel is rounded to FP16 too (one
+// tcgen05.mma takes A and B of one type), and the split mode becomes two
+// launches, A X_hi then A X_lo added, since A itself is exact.
 //
 // Every wait is bounded (about one second of global time); a wait that expires
 // records DEV_TIMEOUT, every role stops issuing work, and the CTA frees its
@@ -87,6 +91,7 @@ struct TcArgs {
   uint16_t* a16;        // FP32 forward pass: also store BF16(A) here (row stride ld16), or null
   int64_t ld16;
   int gram;             // 1: C = A^T A with one row tile: the panel operand is the converted A tile
+  uint32_t idesc;       // tcgen05 instruction descriptor (operand type BF16 or FP16, FP32 accumulator)
 };
 
 #ifndef RSVD_TC_MAX_S32
@@ -139,7 +144,7 @@ template <bool TRANS, bool SPLIT, int SRC = kSrc32>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const __grid_constant__ CUtensorMap mapBlo, const TcArgs a) {
-  static_assert(!(SPLIT && SRC != kSrc32), "only the FP32 source has a split mode");
+  static_assert(!(SPLIT && SRC != kSrc32), "only the FP32 source has a one-launch split mode");
   constexpr bool SRC8 = SRC == kSrc8;
   using L = Layout<SPLIT, SRC>;
   const int SOP = a.sop;
@@ -229,7 +234,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = ptx::idesc_bf16_f32(BM, (uint32_t)NP);
+      const uint32_t idesc = a.idesc;
       RingPos rop;
       int64_t ua = 0;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x, ++ua) {
@@ -487,9 +492,20 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 
 // Xt[j][k] = bf16(X[k][j]) for j < r, 0 for r <= j < NP (and the residual
 // into Xlo): the K-major panel operand of the MMA.
-__global__ void panel_to_bf16_kernel(int64_t K, int r, int NP, const float* __restrict__ X, int64_t ldx,
-                                     __nv_bfloat16* __restrict__ Xhi, __nv_bfloat16* __restrict__ Xlo,
-                                     int64_t ldb) {
+__device__ __forceinline__ uint16_t round16(float v, __nv_bfloat16*) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+__device__ __forceinline__ uint16_t round16(float v, __half*) { return __half_as_ushort(__float2half_rn(v)); }
+__device__ __forceinline__ float widen16(uint16_t h, __nv_bfloat16*) {
+  return __bfloat162float(__ushort_as_bfloat16(h));
+}
+__device__ __forceinline__ float widen16(uint16_t h, __half*) { return __half2float(__ushort_as_half(h)); }
+
+// X (K x r, FP32) -> the K-major 16-bit panel hi = round(X) and, when Xlo is
+// set, lo = round(X - hi); H = __nv_bfloat16 or __half; columns r..NP-1 are 0
+template <typename H>
+__global__ void panel_to_16_kernel(int64_t K, int r, int NP, const float* __restrict__ X, int64_t ldx,
+                                   uint16_t* __restrict__ Xhi, uint16_t* __restrict__ Xlo, int64_t ldb) {
   __shared__ float tile[32][33];
   const int64_t k0 = (int64_t)blockIdx.x * 32;
   const int j0 = blockIdx.y * 32;
@@ -504,9 +520,9 @@ __global__ void panel_to_bf16_kernel(int64_t K, int r, int NP, const float* __re
     const int64_t k = k0 + threadIdx.x;
     if (j < NP && k < K) {
       const float v = tile[threadIdx.x][t];
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      const uint16_t h = round16(v, (H*)nullptr);
       Xhi[(int64_t)j * ldb + k] = h;
-      if (Xlo) Xlo[(int64_t)j * ldb + k] = __float2bfloat16_rn(v - __bfloat162float(h));
+      if (Xlo) Xlo[(int64_t)j * ldb + k] = round16(v - widen16(h, (H*)nullptr), (H*)nullptr);
     }
   }
 }
@@ -614,14 +630,16 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   const bool split = prec == RSVD_PREC_BF16X3;
   const bool src8 = src.f8 != nullptr;
   const bool src16 = src.b16 != nullptr;
+  const bool f16 = src16 && src.b16->f16;
+  // 16-bit source in split mode: A is exact, the panel is split; two launches
+  const bool split2 = split && src16;
   if (r < 1 || r > 512) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: r must be in [1, 512]");
-  if (split && (src8 || src16))
-    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: only the FP32 source has a split mode");
+  if (split && src8) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: the FP8 source has no split mode");
   if (src.copy16 && (split || trans || src8 || src16 || round_up(r, 16) > 256 || src.ld16 < round_up(n, BK) ||
                      src.ld16 % BK != 0))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: the BF16 copy is written by one plain forward pass "
                                       "over FP32 A (ld16 a multiple of 64 covering n)");
-  if (round_up(r, 16) > (split ? kSplitMaxNP : 256)) {
+  if (round_up(r, 16) > ((split && !split2) ? kSplitMaxNP : 256)) {
     // wider than one accumulator (256 columns) or than the split-mode operand
     // ring fits: passes over column halves of the panel (A is read per half)
     const int h = (int)round_up(cdiv(r, 2), 16);
@@ -632,13 +650,13 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   if (!src8 && !src16 && (src.A->ld % 4 != 0 || (reinterpret_cast<uintptr_t>(src.A->data) & 15) != 0))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: A needs a 16-byte aligned base and ld % 4 == 0");
   if (src16 && (src.b16->ld % 8 != 0 || (reinterpret_cast<uintptr_t>(src.b16->data) & 15) != 0))
-    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: the BF16 copy needs a 16-byte aligned base and ld % 8 == 0");
+    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: a 16-bit A needs a 16-byte aligned base and ld % 8 == 0");
   if (src8 && (src.f8->ldc % 16 != 0 || (reinterpret_cast<uintptr_t>(src.f8->codes) & 15) != 0))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: FP8 codes need a 16-byte aligned base and ld % 16 == 0");
   const TcShape s = tc_shape(m, n, r, trans);
   Carver c(ws, ws_bytes);
-  auto* Xhi = c.take<__nv_bfloat16>((size_t)s.NP * s.ldb);
-  __nv_bfloat16* Xlo = split ? c.take<__nv_bfloat16>((size_t)s.NP * s.ldb) : nullptr;
+  auto* Xhi = c.take<uint16_t>((size_t)s.NP * s.ldb);
+  uint16_t* Xlo = split ? c.take<uint16_t>((size_t)s.NP * s.ldb) : nullptr;
   const int64_t slab = round_up(s.M * r, 4);
   float* partial = s.nsplit > 1 ? c.take<float>((size_t)s.nsplit * slab) : nullptr;
   int* own_status = c.take<int>(4);
@@ -652,27 +670,29 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   // tile of A^T (one row tile) already is the panel tile, rounded the same way
   const bool gram = trans && !src8 && !src16 && !src.copy16 && X == static_cast<const float*>(src.A->data) &&
                     ldx == src.A->ld && (int64_t)r == n && s.mtiles == 1;
-  if (!gram) {  // panel -> BF16 (hi, lo), K-major
+  if (!gram) {  // panel -> BF16 or FP16 (hi, lo), K-major
     dim3 grid((unsigned)cdiv(s.K, 32), (unsigned)cdiv(s.NP, 32));
-    panel_to_bf16_kernel<<<grid, dim3(32, 8), 0, stream>>>(s.K, r, s.NP, X, ldx, Xhi, Xlo, s.ldb);
+    if (f16) panel_to_16_kernel<__half><<<grid, dim3(32, 8), 0, stream>>>(s.K, r, s.NP, X, ldx, Xhi, Xlo, s.ldb);
+    else panel_to_16_kernel<__nv_bfloat16><<<grid, dim3(32, 8), 0, stream>>>(s.K, r, s.NP, X, ldx, Xhi, Xlo, s.ldb);
     RSVD_CUDA(after_launch());
   }
+  const CUtensorMapDataType t16 = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CUtensorMap mapA, mapB, mapBlo;
   const uint32_t box_in = trans ? BM : BK, box_out = trans ? BK : BM;
   if (src8)
     RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_UINT8, src.f8->codes, (uint64_t)n, (uint64_t)m,
                        (uint64_t)src.f8->ldc, box_in, box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
   else if (src16)
-    RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, src.b16->data, (uint64_t)n, (uint64_t)m,
-                       (uint64_t)src.b16->ld * 2, box_in, box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
+    RSVD_TRY(encode_2d(&mapA, t16, src.b16->data, (uint64_t)n, (uint64_t)m, (uint64_t)src.b16->ld * 2, box_in,
+                       box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
   else
     RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, src.A->data, (uint64_t)n, (uint64_t)m,
                        (uint64_t)src.A->ld * 4, box_in, box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
-  RSVD_TRY(encode_2d(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Xhi, (uint64_t)s.K, (uint64_t)s.NP,
-                     (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP, CU_TENSOR_MAP_SWIZZLE_128B));
+  RSVD_TRY(encode_2d(&mapB, t16, Xhi, (uint64_t)s.K, (uint64_t)s.NP, (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP,
+                     CU_TENSOR_MAP_SWIZZLE_128B));
   if (split)
-    RSVD_TRY(encode_2d(&mapBlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Xlo, (uint64_t)s.K, (uint64_t)s.NP,
-                       (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP, CU_TENSOR_MAP_SWIZZLE_128B));
+    RSVD_TRY(encode_2d(&mapBlo, t16, Xlo, (uint64_t)s.K, (uint64_t)s.NP, (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP,
+                       CU_TENSOR_MAP_SWIZZLE_128B));
   else
     mapBlo = mapB;
 
@@ -700,12 +720,13 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   ta.a16 = src.copy16;
   ta.ld16 = src.ld16;
   ta.gram = gram ? 1 : 0;
+  ta.idesc = f16 ? ptx::idesc_f16_f32(BM, (uint32_t)s.NP) : ptx::idesc_bf16_f32(BM, (uint32_t)s.NP);
 
   const int64_t units = s.mtiles * s.nsplit;
   const int grid = (int)(units < num_sms() ? units : num_sms());
   constexpr size_t kSmemMax = 232448;
   auto need = [&](int sop, int depth) {
-    return split ? Layout<true>::total(s.NP, sop, depth)
+    return (split && !split2) ? Layout<true>::total(s.NP, sop, depth)
                  : (src8 ? Layout<false, kSrc8>::total(s.NP, sop, depth)
                          : (src16 ? Layout<false, kSrc16>::total(s.NP, sop, depth)
                                   : Layout<false>::total(s.NP, sop, depth)));
@@ -728,6 +749,15 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
     RSVD_TRY(trans ? launch(tc_apass_kernel<true, false, kSrc8>) : launch(tc_apass_kernel<false, false, kSrc8>));
   } else if (src16) {
     RSVD_TRY(trans ? launch(tc_apass_kernel<true, false, kSrc16>) : launch(tc_apass_kernel<false, false, kSrc16>));
+    if (split2) {  // + A X_lo: added by the epilogue, or as a second set of partials
+      if (s.nsplit > 1)
+        RSVD_TRY(reduce_partials<float>(s.M, r, s.nsplit, partial, r, slab, Y, ldy, accumulate, stream));
+      ta.accumulate = s.nsplit == 1 ? 1 : 0;
+      mapB = mapBlo;
+      RSVD_TRY(trans ? launch(tc_apass_kernel<true, false, kSrc16>) : launch(tc_apass_kernel<false, false, kSrc16>));
+      if (s.nsplit > 1) RSVD_TRY(reduce_partials<float>(s.M, r, s.nsplit, partial, r, slab, Y, ldy, true, stream));
+      return RSVD_OK;
+    }
   } else if (trans) {
     RSVD_TRY(split ? launch(tc_apass_kernel<true, true>) : launch(tc_apass_kernel<true, false>));
   } else {
@@ -753,10 +783,18 @@ rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, 
 
 rsvd_status tc_apass_from_bf16(const Bf16Source& b16, int trans, int r, const float* X, int64_t ldx, float* Y,
                                int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream) {
+  return tc_apass_from_16(b16, trans, RSVD_PREC_BF16, r, X, ldx, Y, ldy, ws, ws_bytes, status, stream);
+}
+
+rsvd_status tc_apass_from_16(const Bf16Source& a16, int trans, int prec, int r, const float* X, int64_t ldx,
+                             float* Y, int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream,
+                             bool accumulate) {
+  if (prec != RSVD_PREC_BF16 && prec != RSVD_PREC_BF16X3)
+    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: a 16-bit A takes BF16 or BF16X3 precision");
   TcSource src;
-  src.b16 = &b16;
-  return tc_apass_run(src, b16.m, b16.n, trans, RSVD_PREC_BF16, r, X, ldx, Y, ldy, ws, ws_bytes, status, stream,
-                      false);
+  src.b16 = &a16;
+  return tc_apass_run(src, a16.m, a16.n, trans, prec, r, X, ldx, Y, ldy, ws, ws_bytes, status, stream,
+                      accumulate);
 }
 
 rsvd_status tc_apass_from_fp8(const Fp8Source& f8, int trans, int r, const float* X, int64_t ldx, float* Y,

@@ -204,10 +204,17 @@ rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, 
 struct Bf16Source {
   const uint16_t* data = nullptr;
   int64_t m = 0, n = 0, ld = 0;
+  int f16 = 0;  // 1: the values are IEEE FP16 (the panel is then rounded to FP16)
 };
 // The BF16 A-pass over the copy: the same operands, hence the same result, as
 // tc_apass_from_f32 with prec BF16 on the FP32 A the copy was made from.
 rsvd_status tc_apass_from_bf16(const Bf16Source& b16, int trans, int r, const float* X, int64_t ldx, float* Y,
                                int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream);
+// A-pass over a 16-bit A (BF16 or FP16, m x n, row stride ld % 8 == 0, 16-byte
+// aligned): prec BF16 rounds the panel to A's type; BF16X3 splits it in two
+// (hi + lo) and adds the two products.
+rsvd_status tc_apass_from_16(const Bf16Source& a16, int trans, int prec, int r, const float* X, int64_t ldx,
+                             float* Y, int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream,
+                             bool accumulate = false);
 
 }  // namespace rsvd

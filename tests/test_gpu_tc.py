@@ -149,3 +149,95 @@ def test_gram_of_a_panel_matches_the_general_path(g, prec, M, r):
     assert torch.equal(G1, G2)
     ref = (Y.double().T @ Y.double()).cpu().numpy()
     assert np.abs(G1.double().cpu().numpy() - ref).max() <= (2e-2 if prec == "bf16" else 1e-4) * np.abs(ref).max()
+
+
+# ---- A stored in 16 bits (BF16 or IEEE FP16) --------------------------------------
+
+TDT16 = {"bf16": torch.bfloat16, "f16": torch.float16}
+
+
+def _round16(x, fmt):
+    """x rounded to the 16-bit format (round to nearest even), as FP64."""
+    if fmt == "f16":
+        return np.asarray(x, np.float32).astype(np.float16).astype(np.float64)
+    return _bf16(x)
+
+
+# row strides are multiples of 8 values (16 bytes) for a 16-bit A
+SHAPES16 = [(300, 200, 17), (513, 392, 120), (257, 1000, 200), (129, 72, 30), (640, 320, 256)]
+
+
+@pytest.mark.parametrize("m,n,r", SHAPES16)
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_16bit_source_exact_on_small_integers(g, m, n, r, trans, prec, fmt):
+    rng = np.random.default_rng(m * 7 + n * 3 + r + (fmt == "f16"))
+    A = rng.integers(-4, 5, size=(m, n)).astype(np.float32)
+    K = m if trans else n
+    X = rng.integers(-4, 5, size=(K, r)).astype(np.float32)
+    A16 = torch.as_tensor(A, device="cuda").to(TDT16[fmt])
+    got = g.apass(A16, torch.as_tensor(X, device="cuda"), trans, prec).cpu().numpy()
+    ref = OL.apply(A, X, trans=trans).astype(np.float32)
+    assert got.dtype == np.float32 and np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_16bit_source_error_model(g, trans, fmt):
+    """prec BF16 on a 16-bit A: the exact product of A and the panel rounded to
+    A's format, accumulated in FP32.  prec BF16X3: the panel split in two
+    16-bit parts, close to the FP32 product of the stored A."""
+    m, n, r = 2000, 1504, 120
+    rng = np.random.default_rng(3 + trans + 2 * (fmt == "f16"))
+    A16 = torch.as_tensor(rng.standard_normal((m, n)).astype(np.float32)).to(TDT16[fmt])
+    Ad = A16.double().numpy()
+    K = m if trans else n
+    X = rng.standard_normal((K, r)).astype(np.float32)
+    Xd = torch.as_tensor(X, device="cuda")
+    got = g.apass(A16.to("cuda"), Xd, trans, "bf16").cpu().numpy()
+    Xr = _round16(X, fmt)
+    ref = OL.apply(Ad, Xr, trans=trans)
+    bound = (K + 2) * 2.0 ** -24 * OL.apply(np.abs(Ad), np.abs(Xr), trans=trans)
+    assert np.all(np.abs(got - ref) <= bound)
+    split = g.apass(A16.to("cuda"), Xd, trans, "bf16x3").cpu().numpy()
+    ref = OL.apply(Ad, X.astype(np.float64), trans=trans)
+    scale = OL.apply(np.abs(Ad), np.abs(X.astype(np.float64)), trans=trans)
+    rel = np.max(np.abs(split - ref) / scale)
+    assert rel < 2.0 ** -14
+    assert rel < np.max(np.abs(got - ref) / scale) / 30
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_16bit_storage_rsvd_against_oracle(g, fmt):
+    """rsvd of a matrix stored in 16 bits against the FP64 oracle on the
+    values that matrix holds (the same BF16-rounded test matrix)."""
+    m, n, k, p, q, seed = 8000, 4000, 100, 20, 2, 2002
+    s = spectrum_harmonic_noisy(n, 1e-4, 3002)
+    A, _, _ = prescribed_dense(m, n, s, 1002, dtype=np.float32)
+    A16 = torch.as_tensor(A * np.float32(256.0)).to(TDT16[fmt])   # entries in FP16's normal range
+    Ad = A16.double().numpy()
+    U, S, V = (t.cpu().numpy().astype(np.float64) for t in g.rsvd(A16.to("cuda"), k, p, q, seed))
+    Uo, So, Vo = OR.rsvd(Ad, k, p, q, seed, "bf16")
+    es, eu, ev = sigma_rel_err(S, So), max_principal_angle(U, Uo), max_principal_angle(V, Vo)
+    print(f"{fmt}: sigma rel err {es:.2e}, U angle {eu:.2e}, V angle {ev:.2e}")
+    I = np.eye(k)
+    assert np.abs(U.T @ U - I).max() <= 1e-4 and np.abs(V.T @ V - I).max() <= 1e-4
+    assert es <= 1e-4 and eu <= 1e-2
+
+
+def test_16bit_storage_host_copy_and_row_stride(g):
+    """A host 16-bit A with n not a multiple of 8 is copied with padded rows:
+    the same bits as the device A with the same padded stride; a device A
+    whose stride is not a multiple of 8 values is rejected."""
+    m, n, k, p, q, seed = 3001, 1003, 30, 10, 1, 5
+    A, _, _ = prescribed_dense(m, n, spectrum_harmonic_noisy(n, 1e-4, 8), 9, dtype=np.float32)
+    A16 = torch.as_tensor(A * np.float32(256.0)).to(torch.float16)
+    pad = torch.zeros(m, 1008, dtype=torch.float16, device="cuda")
+    pad[:, :n] = A16.to("cuda")
+    a = g.rsvd(A16, k, p, q, seed)
+    b = g.rsvd(pad[:, :n], k, p, q, seed)
+    for s_, t_ in zip(a, b):
+        assert torch.equal(s_, t_)
+    with pytest.raises(g.RsvdError):
+        g.rsvd(A16.to("cuda"), k, p, q, seed)
