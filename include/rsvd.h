@@ -229,8 +229,10 @@ rsvd_status rsvd_checkpoint_info(const char* path, rsvd_checkpoint_info_t* out);
  * of T.  Otherwise T = Q R by CholeskyQR2 and the one-sided Jacobi on the t x t
  * R.  That path forms the Gram of T, so singular values below about 1e-7 of
  * the largest keep an absolute, not a relative, FP64 accuracy (columns
- * dependent to that level give zeros in S, with orthonormal vectors); a
- * non-finite entry gives RSVD_ERR_NOT_SPD.  Allocates and frees its own device
+ * dependent to that level give zeros in S); a non-finite entry gives
+ * RSVD_ERR_NOT_SPD.  On both paths the singular vectors of zero (or
+ * rounding-level) singular values are not completed to an orthonormal set:
+ * such columns of U or V may be zero.  Allocates and frees its own device
  * workspace (about 3 m n + 4 t^2 doubles on the CholeskyQR2 path).
  * Synchronises `stream`. */
 rsvd_status rsvd_full(const rsvd_matrix* A, void* U, void* S, void* V, void* stream);

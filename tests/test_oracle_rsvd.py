@@ -91,11 +91,22 @@ def test_small_svd_of_bt_reconstructs_b():
 
 def test_full_svd_matches_library():
     rng = np.random.default_rng(13)
-    for shape in [(9, 4), (4, 9), (6, 6)]:
+    for shape in [(9, 4), (4, 9), (6, 6), (40, 17)]:
         A = rng.standard_normal(shape)
         U, S, V = R.full_svd(A)
+        t = min(shape)
         assert np.allclose(S, np.linalg.svd(A, compute_uv=False), rtol=1e-13)
         assert np.linalg.norm((U * S) @ V.T - A) < 1e-13 * np.linalg.norm(A)
+        assert np.linalg.norm(U.T @ U - np.eye(t)) < 1e-13 and np.linalg.norm(V.T @ V - np.eye(t)) < 1e-13
+    # rank 2 in a 7 x 5: three singular values at rounding level; the vectors
+    # of the two nonzero ones are orthonormal (those of the null part are not
+    # completed to an orthonormal set)
+    A = rng.standard_normal((7, 2)) @ rng.standard_normal((2, 5))
+    U, S, V = R.full_svd(A)
+    assert np.all(S[2:] < 1e-14 * S[0])
+    assert np.linalg.norm(U[:, :2].T @ U[:, :2] - np.eye(2)) < 1e-13
+    assert np.linalg.norm(V[:, :2].T @ V[:, :2] - np.eye(2)) < 1e-13
+    assert np.linalg.norm((U * S) @ V.T - A) < 1e-13 * np.linalg.norm(A)
 
 
 def test_signs_are_normalised():
