@@ -205,6 +205,49 @@ def test_coo_to_csr_edge_cases(lib):
     assert lib.rsvd_coo_to_csr(3, 4, 1, 32, None, P(z), P(f), P(rp), P(z), P(f)) == 1
 
 
+def test_coo_binding_converts_torch_coo(lib):
+    """The binding's coo_to_csr on an uncoalesced host torch COO tensor (int64
+    indices, repeats): the CSR of A and of A^T the library builds, against the
+    oracle (host only, no GPU call)."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    import paper_1907_06470_gb300 as g
+    rng = np.random.default_rng(21)
+    m, n, nnz = 40, 25, 300
+    ri = rng.integers(0, m, nnz)
+    ci = rng.integers(0, n, nnz)
+    v = rng.standard_normal(nnz).astype(np.float32)
+    coo = torch.sparse_coo_tensor(torch.as_tensor(np.stack([ri, ci])), torch.as_tensor(v), size=(m, n))
+    assert not coo.is_coalesced()
+    A = g.coo_to_csr(coo)
+    At = g.coo_to_csr(coo, transpose=True)
+    for got, (erp, eci, ev), shape in ((A, T.coo_to_csr(m, n, ri, ci, v), (m, n)),
+                                       (At, T.coo_to_csr(n, m, ci, ri, v), (n, m))):
+        assert tuple(got.shape) == shape
+        assert np.array_equal(got.crow_indices().numpy(), erp)
+        assert np.array_equal(got.col_indices().numpy(), eci)
+        assert np.array_equal(got.values().numpy().view(np.uint32), ev.view(np.uint32))
+    with pytest.raises(TypeError):
+        g.coo_to_csr(coo.double())
+
+
+def test_binding_maps_16bit_dtypes():
+    torch = pytest.importorskip("torch")
+    import paper_1907_06470_gb300 as g
+    from paper_1907_06470_gb300 import _lib
+    codes = {t: g._dtype_code(torch.zeros(1, dtype=t)) for t in
+             (torch.float64, torch.float32, torch.bfloat16, torch.float16)}
+    assert codes == {torch.float64: _lib.DTYPE["f64"], torch.float32: _lib.DTYPE["f32"],
+                     torch.bfloat16: _lib.DTYPE["bf16"], torch.float16: _lib.DTYPE["f16"]}
+    with open(os.path.join(ROOT, "include", "rsvd.h")) as fh:
+        hdr = fh.read()
+    for name, val in (("F64", 0), ("F32", 1), ("BF16", 2), ("F16", 3)):
+        assert re.search(rf"RSVD_{name} = {val}\b", hdr)
+        assert _lib.DTYPE[name.lower()] == val
+    with pytest.raises(TypeError):
+        g._dtype_code(torch.zeros(1, dtype=torch.int32))
+
+
 def test_csr_plan_rules(lib):
     from paper_1907_06470_gb300 import _lib
     h = C.c_void_p()
