@@ -340,6 +340,10 @@ rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* col
 // per-(thread, column) offsets are laid out column-major (thread 0 first), and
 // every thread scatters its rows in increasing order, so the entries of each
 // output row come in increasing row index of A whatever T is.
+// per-(thread, row) counters of the host counting sorts: 32-bit (nnz < 2^31),
+// at most 64 Mi of them (256 MB), which bounds the thread count for long outputs
+constexpr int64_t kCountScratch = (int64_t)1 << 26;
+
 rsvd_status csr_transpose_host(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                                const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val) {
   if (m < 0 || n < 0 || !rowptr || !t_rowptr) return fail(RSVD_ERR_INVALID_ARG, "csr_transpose: bad arguments");
@@ -350,7 +354,8 @@ rsvd_status csr_transpose_host(int64_t m, int64_t n, const int32_t* rowptr, cons
   if (nnz > 0 && (!colidx || !val || !t_colidx || !t_val))
     return fail(RSVD_ERR_INVALID_ARG, "csr_transpose: NULL index or value array");
   unsigned hw = std::thread::hardware_concurrency();
-  int T = (int)std::min<int64_t>({(int64_t)(hw ? hw : 1), 32, std::max<int64_t>(1, nnz >> 20)});
+  int T = (int)std::min<int64_t>({(int64_t)(hw ? hw : 1), 32, std::max<int64_t>(1, nnz >> 20),
+                                    std::max<int64_t>(1, kCountScratch / std::max<int64_t>(1, n))});
   if (T < 1) T = 1;
   std::vector<int64_t> r0(T + 1);
   for (int t = 0; t <= T; ++t) {
@@ -360,10 +365,10 @@ rsvd_status csr_transpose_host(int64_t m, int64_t n, const int32_t* rowptr, cons
   }
   for (int t = 1; t <= T; ++t)
     if (r0[t] < r0[t - 1]) r0[t] = r0[t - 1];
-  std::vector<int64_t> cnt((size_t)T * n, 0);  // cnt[t*n + j]
+  std::vector<int32_t> cnt((size_t)T * n, 0);  // cnt[t*n + j]
   std::vector<int> bad(T, 0);
   auto count = [&](int t) {
-    int64_t* c = cnt.data() + (size_t)t * n;
+    int32_t* c = cnt.data() + (size_t)t * n;
     for (int64_t i = r0[t]; i < r0[t + 1]; ++i)
       for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
         const int32_t j = colidx[e];
@@ -384,13 +389,13 @@ rsvd_status csr_transpose_host(int64_t m, int64_t n, const int32_t* rowptr, cons
     t_rowptr[j] = (int32_t)run;
     for (int t = 0; t < T; ++t) {
       const int64_t c = cnt[(size_t)t * n + j];
-      cnt[(size_t)t * n + j] = run;
+      cnt[(size_t)t * n + j] = (int32_t)run;
       run += c;
     }
   }
   t_rowptr[n] = (int32_t)run;
   auto scatter = [&](int t) {
-    int64_t* off = cnt.data() + (size_t)t * n;
+    int32_t* off = cnt.data() + (size_t)t * n;
     for (int64_t i = r0[t]; i < r0[t + 1]; ++i)
       for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
         const int64_t pos = off[colidx[e]]++;
@@ -414,14 +419,15 @@ template <typename I>
 rsvd_status coo_to_csr_typed(int64_t m, int64_t n, int64_t nnz, const I* rowidx, const I* colidx,
                              const float* val, int32_t* rowptr, int32_t* out_colidx, float* out_val) {
   unsigned hw = std::thread::hardware_concurrency();
-  int T = (int)std::min<int64_t>({(int64_t)(hw ? hw : 1), 32, std::max<int64_t>(1, nnz >> 20)});
+  int T = (int)std::min<int64_t>({(int64_t)(hw ? hw : 1), 32, std::max<int64_t>(1, nnz >> 20),
+                                    std::max<int64_t>(1, kCountScratch / std::max<int64_t>(1, m))});
   if (T < 1) T = 1;
   std::vector<int64_t> e0(T + 1);
   for (int t = 0; t <= T; ++t) e0[t] = nnz * t / T;
-  std::vector<int64_t> cnt((size_t)T * m, 0);  // cnt[t*m + i]
+  std::vector<int32_t> cnt((size_t)T * m, 0);  // cnt[t*m + i]
   std::vector<int> bad(T, 0);
   auto count = [&](int t) {
-    int64_t* c = cnt.data() + (size_t)t * m;
+    int32_t* c = cnt.data() + (size_t)t * m;
     for (int64_t e = e0[t]; e < e0[t + 1]; ++e) {
       const int64_t i = (int64_t)rowidx[e], j = (int64_t)colidx[e];
       if (i < 0 || i >= m || j < 0 || j >= n) { bad[t] = 1; return; }
@@ -440,13 +446,13 @@ rsvd_status coo_to_csr_typed(int64_t m, int64_t n, int64_t nnz, const I* rowidx,
     rowptr[i] = (int32_t)run;
     for (int t = 0; t < T; ++t) {
       const int64_t c = cnt[(size_t)t * m + i];
-      cnt[(size_t)t * m + i] = run;
+      cnt[(size_t)t * m + i] = (int32_t)run;
       run += c;
     }
   }
   rowptr[m] = (int32_t)run;
   auto scatter = [&](int t) {
-    int64_t* off = cnt.data() + (size_t)t * m;
+    int32_t* off = cnt.data() + (size_t)t * m;
     for (int64_t e = e0[t]; e < e0[t + 1]; ++e) {
       const int64_t pos = off[(int64_t)rowidx[e]]++;
       out_colidx[pos] = (int32_t)colidx[e];
