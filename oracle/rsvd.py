@@ -45,6 +45,25 @@ def range_finder(A, r: int, q: int, seed: int, omega_dtype: str = "f64"):
     return Q
 
 
+def range_finder_fused(A, r: int, q: int, seed: int, omega_dtype: str = "f64"):
+    """Q spanning the same sketch (A A^T)^q A O as ``range_finder``, with each
+    power iteration taken as one sweep Z = A^T (A W) and only the n-side
+    orthonormalised (Section 2.2 evaluates the product right to left with no
+    re-orthonormalisation; here W = orth(Z) after every sweep, Halko,
+    Martinsson & Tropp (2011) Algorithm 4.3 with that step added):
+        W = O;  q times: W = orth(A^T (A W));  Q = orth(A W).
+    Equal to ``range_finder``'s span in exact arithmetic; in floating point
+    the sweep squares the spectrum, so directions below about sqrt(eps) of
+    sigma_1 are not resolved.  One read of A per sweep when A (A W) and
+    A^T (A W) are formed tile by tile."""
+    m, n = A.shape
+    W = gaussian_matrix_as_f64(n, r, seed, omega_dtype)
+    for _ in range(q):
+        W, _ = householder_qr(apply(A, apply(A, W), trans=True))
+    Q, _ = householder_qr(apply(A, W))
+    return Q
+
+
 def small_svd_of_bt(Bt):
     """SVD of B from B^T (n x r): returns U_B (r x r), sigma (r), V (n x r)."""
     Qb, R = householder_qr(Bt)
@@ -65,6 +84,21 @@ def rsvd(A, k: int, p: int, q: int, seed: int, omega_dtype: str = "f64"):
     if not (1 <= k and 0 <= p and r <= min(m, n) and q >= 0):
         raise ValueError("need 1 <= k, 0 <= p, k + p <= min(m, n), q >= 0")
     Q = range_finder(A, r, q, seed, omega_dtype)
+    Bt = apply(A, Q, trans=True)
+    UB, sigma, V = small_svd_of_bt(Bt)
+    U = Q @ UB[:, :k]
+    U, V = normalise_signs(U, V[:, :k])
+    return U, sigma[:k], V
+
+
+def rsvd_fused_sweeps(A, k: int, p: int, q: int, seed: int, omega_dtype: str = "f64"):
+    """``rsvd`` with the range finder of ``range_finder_fused`` (steps 5-7 as
+    in ``rsvd``)."""
+    m, n = A.shape
+    r = k + p
+    if not (1 <= k and 0 <= p and r <= min(m, n) and q >= 0):
+        raise ValueError("need 1 <= k, 0 <= p, k + p <= min(m, n), q >= 0")
+    Q = range_finder_fused(A, r, q, seed, omega_dtype)
     Bt = apply(A, Q, trans=True)
     UB, sigma, V = small_svd_of_bt(Bt)
     U = Q @ UB[:, :k]

@@ -159,3 +159,53 @@ def test_auto_q_runs_to_the_limit_when_the_spectrum_keeps_moving():
     assert qu == 3
     with pytest.raises(ValueError):
         R.rsvd_auto_q(A, 20, 5, -1, 2001)
+
+
+# ---- fused power sweeps: W = orth(A^T (A W)) ------------------------------------
+
+def test_fused_sweeps_exact_when_sketch_spans_the_range():
+    m, n, k, p = 300, 120, 20, 10
+    s = spectrum_geometric(25, 0.8)
+    A, U0, V0 = prescribed_dense(m, n, s, seed=11)
+    for q in (0, 1, 2):
+        U, S, V = R.rsvd_fused_sweeps(A, k, p, q, seed=21)
+        assert np.max(np.abs(S - s[:k]) / s[:k]) < 1e-12
+        assert max_principal_angle(U, U0[:, :k]) < 1e-10
+        assert max_principal_angle(V, V0[:, :k]) < 1e-10
+
+
+def test_fused_sweeps_without_iterations_is_the_plain_scheme():
+    A, _, _ = prescribed_dense(200, 90, spectrum_geometric(90, 0.93), seed=5)
+    a = R.rsvd(A, 10, 5, 0, seed=6)
+    b = R.rsvd_fused_sweeps(A, 10, 5, 0, seed=6)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_fused_sweeps_span_the_same_sketch(q):
+    """(A A^T)^q A O has one span however the products are grouped: with the
+    spectrum far above sqrt(eps) the two range finders agree to rounding."""
+    m, n, k, p = 400, 150, 12, 8
+    s = 1.0 / np.arange(1, n + 1)          # sigma_n / sigma_1 ~ 7e-3, squared 4e-5 >> eps
+    A, _, _ = prescribed_dense(m, n, s, seed=8)
+    Qa = R.range_finder(A, k + p, q, 9)
+    Qb = R.range_finder_fused(A, k + p, q, 9)
+    assert max_principal_angle(Qa, Qb) < 1e-9
+    Ua, Sa, Va = R.rsvd(A, k, p, q, seed=9)
+    Ub, Sb, Vb = R.rsvd_fused_sweeps(A, k, p, q, seed=9)
+    assert np.max(np.abs(Sa - Sb) / Sa) < 1e-12
+    assert max_principal_angle(Ua, Ub) < 1e-9 and max_principal_angle(Va, Vb) < 1e-9
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_fused_sweeps_meet_the_hmt_bound(q):
+    m, n, k, p = 300, 200, 10, 5
+    s = spectrum_geometric(200, 0.95)
+    A, _, _ = prescribed_dense(m, n, s, seed=17)
+    bound = _hmt_factor(k, p, m, n, q) * s[k]
+    for seed in range(5):
+        U, S, V = R.rsvd_fused_sweeps(A, k + p, 0, q, seed=100 + seed)
+        Q = U  # the rank-(k+p) basis
+        err = np.linalg.norm(A - Q @ (Q.T @ A), 2)
+        assert err <= bound
