@@ -9,7 +9,7 @@ Main entry points
 -----------------
 rsvd(A, k, p, q, seed, ...)   rank-k randomized SVD (Section 2.1, Section 2.2)
 Plan                          reusable plan + workspace for repeated runs
-full_svd(A)                   exact SVD of a small matrix
+full_svd(A)                   exact SVD, min(m, n) <= 512
 gaussian / tile_map / apass / orth / small_svd
                               the individual steps (Section 2.1 steps 1-6,
                               Section 3.1 tile map)
