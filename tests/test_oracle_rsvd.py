@@ -209,3 +209,47 @@ def test_fused_sweeps_meet_the_hmt_bound(q):
         Q = U  # the rank-(k+p) basis
         err = np.linalg.norm(A - Q @ (Q.T @ A), 2)
         assert err <= bound
+
+
+def test_fused_sweeps_accuracy_under_bf16_rounding():
+    """The accuracy cost of the fused reading where the arithmetic is BF16: the
+    range finder run with A, the panels and (fused) the intermediate A W
+    rounded to BF16, on the harmonic-plus-noise spectrum of the dense
+    workload, against the FP64 per-product result.  Rounding A W to BF16 costs
+    up to a few times the per-product error; carrying A W as two BF16 parts
+    (hi + lo, as the split panel of the tensor-core passes does) removes it."""
+    from oracle.gaussian import bf16_bits_to_f64, gaussian_matrix_as_f64, to_bf16_bits
+    from synth import spectrum_harmonic_noisy
+
+    def bf(x):
+        return bf16_bits_to_f64(to_bf16_bits(x))
+
+    def orth(Y):
+        return householder_qr(Y)[0]
+
+    m, n, k, p, q = 3000, 1500, 50, 10, 2
+    A, _, _ = prescribed_dense(m, n, spectrum_harmonic_noisy(n, 1e-4, 7), 8)
+    Ab = bf(A)
+    O = gaussian_matrix_as_f64(n, k + p, 9, "bf16")
+
+    def top_sigma(Q):
+        return np.linalg.svd(A.T @ Q, compute_uv=False)[:k]
+
+    ref = top_sigma(R.range_finder(A, k + p, q, 9, "bf16"))
+    Q = orth(Ab @ O)
+    for _ in range(q):
+        Q = orth(Ab @ bf(orth(Ab.T @ bf(Q))))
+    per_product = np.max(np.abs(top_sigma(Q) - ref) / ref)
+    W = O
+    for _ in range(q):
+        W = orth(Ab.T @ bf(Ab @ bf(W)))
+    fused = np.max(np.abs(top_sigma(orth(Ab @ bf(W))) - ref) / ref)
+    W = O
+    for _ in range(q):
+        Y = Ab @ bf(W)
+        hi = bf(Y)
+        W = orth(Ab.T @ (hi + bf(Y - hi)))
+    fused_split = np.max(np.abs(top_sigma(orth(Ab @ bf(W))) - ref) / ref)
+    assert per_product < 1e-3
+    assert fused <= 4 * per_product and fused < 5e-4
+    assert fused_split <= 1.3 * per_product
