@@ -172,7 +172,13 @@ def gaussian_stream(e0: int, count: int, seed: int) -> np.ndarray:
     """FP64 values of stream elements e0 .. e0+count-1 (see module docstring)."""
     if count <= 0:
         return np.zeros(0, dtype=np.float64)
-    e = np.arange(e0, e0 + count, dtype=np.uint64)
+    return gaussian_elements(np.arange(e0, e0 + count, dtype=np.uint64), seed)
+
+
+def gaussian_elements(e, seed: int) -> np.ndarray:
+    """FP64 values of the stream elements with the given indices (any order,
+    repeats allowed); element e is the one ``gaussian_stream`` gives at e."""
+    e = np.asarray(e, dtype=np.uint64)
     g = e >> np.uint64(1)
     x0, x1, x2, x3 = philox4x32(g & _MASK32, g >> np.uint64(32),
                                 np.zeros_like(g), np.zeros_like(g),
@@ -227,6 +233,22 @@ def gaussian_matrix(n: int, r: int, seed: int, dtype: str = "f64") -> np.ndarray
         return vals.astype(np.float32)
     if dtype == "bf16":
         return to_bf16_bits(vals)
+    raise ValueError(dtype)
+
+
+def gaussian_rows(rows, r: int, seed: int, dtype: str = "f64") -> np.ndarray:
+    """Rows ``rows`` of the n x r matrix O (entry (i, j) is element i*r + j),
+    rounded to ``dtype`` and widened back to FP64, without forming O: for
+    checks that touch a few rows of a test matrix with many rows."""
+    rows = np.asarray(rows, dtype=np.uint64)
+    e = (rows[:, None] * np.uint64(r) + np.arange(r, dtype=np.uint64)[None, :]).ravel()
+    vals = gaussian_elements(e, seed).reshape(len(rows), r)
+    if dtype == "f64":
+        return vals
+    if dtype == "f32":
+        return vals.astype(np.float32).astype(np.float64)
+    if dtype == "bf16":
+        return bf16_bits_to_f64(to_bf16_bits(vals))
     raise ValueError(dtype)
 
 

@@ -1004,7 +1004,6 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
     }
     if (P->a_copy_bytes < bytes) {
       if (P->Adev) cudaFree(P->Adev);
-  if (P->a16) cudaFree(P->a16);
       P->Adev = nullptr;
       P->a_copy_bytes = 0;
       RSVD_CUDA(cudaMalloc(&P->Adev, bytes));

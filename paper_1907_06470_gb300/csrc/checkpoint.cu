@@ -90,7 +90,18 @@ rsvd_status matrix_fingerprint(const rsvd_matrix& A, uint64_t* out, cudaStream_t
         std::memcpy(&h[t], &v, 8);
       }
     } else {
-      return fail(RSVD_ERR_UNSUPPORTED, "checkpoint: CSR matrices are fingerprinted in device memory");
+      // the same samples as sample_csr_kernel, read from the host arrays
+      for (int t = 0; t < kSamples; ++t) {
+        const int64_t i = ((int64_t)t * 7919 + 13) % (A.m + 1);
+        unsigned long long v = (unsigned long long)(uint32_t)A.rowptr[i];
+        if (A.nnz > 0) {
+          const int64_t e = ((int64_t)t * 104729 + 7) % A.nnz;
+          uint32_t vb;
+          std::memcpy(&vb, &A.val[e], 4);
+          v = v * 1099511628211ull ^ ((unsigned long long)(uint32_t)A.colidx[e] << 32 | vb);
+        }
+        h[t] = v;
+      }
     }
   } else {
     unsigned long long* d = nullptr;

@@ -6,7 +6,9 @@ import os
 import numpy as np
 import pytest
 
-from synth import prescribed_dense, spectrum_geometric
+from oracle import rsvd as OR
+from synth import prescribed_dense, spectrum_geometric, zipf_csr
+from tests.metrics import max_principal_angle, sigma_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -47,6 +49,40 @@ def test_interrupted_run_resumes_to_the_same_result(g, tmp_path, prec, dtype, st
     for a, b in zip(ref, out):
         assert torch.equal(a, b)
     assert not os.path.exists(path)  # removed once the run completed
+    # and the resumed result is the oracle's (the bars of the plan's precision)
+    Uo, So, Vo = OR.rsvd(A.cpu().numpy(), k, p, q, seed, {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[prec])
+    U, S, V = (t.numpy().astype(np.float64) for t in out)
+    es, eu = sigma_rel_err(S, So), max_principal_angle(U, Uo)
+    if prec == "fp64":
+        assert es <= 1e-11 and eu <= 1e-9
+    elif prec == "fp32":
+        assert es <= 1e-5 and eu <= 1e-4
+    else:
+        assert es <= 1e-3
+
+
+def test_host_csr_resumes_from_its_checkpoint(g, tmp_path):
+    """A CSR matrix held in host memory: the checkpoint's fingerprint is taken
+    from the host arrays, so a restarted plan given the same host CSR resumes."""
+    m, n, k, p, q, seed = 6000, 2000, 20, 10, 2, 2004
+    rp, ci, v = zipf_csr(m, n, 60000, 1004)
+    Ah = torch.sparse_csr_tensor(torch.as_tensor(rp), torch.as_tensor(ci), torch.as_tensor(v), size=(m, n))
+    ref = [t.cpu() for t in g.Plan(m, n, k, p, q, seed, kind="csr").run(Ah)]
+    path = str(tmp_path / "csr.ckpt")
+    p1 = g.Plan(m, n, k, p, q, seed, kind="csr")
+    p1.set_checkpoint(path, stop_after_step=2)
+    with pytest.raises(g.RsvdError):
+        p1.run(Ah)
+    p1.close()
+    p2 = g.Plan(m, n, k, p, q, seed, kind="csr")
+    p2.set_checkpoint(path)
+    out = [t.cpu() for t in p2.run(Ah)]
+    assert p2.info()["resumed_from"] == 2
+    for a, b in zip(ref, out):
+        assert torch.equal(a, b)
+    from oracle.linalg import CSR
+    Uo, So, Vo = OR.rsvd(CSR(m, n, rp, ci, v), k, p, q, seed, "f32")
+    assert sigma_rel_err(out[1].numpy(), So) <= 1e-5
 
 
 def test_checkpoint_of_another_matrix_or_a_damaged_file_is_not_used(g, tmp_path):

@@ -136,3 +136,21 @@ def test_automatic_q_bf16_refines_the_final_pass(g):
     assert 2 <= qu <= 4
     Uo, So, Vo = OR.rsvd(A, 50, 10, qu, 2002, "bf16")
     assert sigma_rel_err(S.cpu().numpy(), So) <= 5e-4
+
+
+def test_bf16_plan_on_device_then_host_input(g):
+    """One BF16 plan run first on a device A (which makes the plan's BF16 copy
+    of A) and then on the same A in pinned host memory (copied to the device
+    in core): both runs read the same operands, so the results are the same
+    bits, and both meet the oracle at the BF16 plan's bound."""
+    m, n, k, p, q, seed = 3000, 1500, 30, 10, 2, 77
+    A, _, _ = prescribed_dense(m, n, spectrum_harmonic_noisy(n, 1e-4, 3), 4, dtype=np.float32)
+    plan = g.Plan(m, n, k, p, q, seed, prec="bf16")
+    a = [t.clone() for t in plan.run(torch.as_tensor(A, device="cuda"))]
+    assert plan.info()["bf16_copy"] == 1
+    b = plan.run(torch.as_tensor(A).pin_memory())
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    Uo, So, Vo = OR.rsvd(A, k, p, q, seed, "bf16")
+    assert sigma_rel_err(b[1].cpu().numpy(), So) <= 1e-3
+    plan.close()

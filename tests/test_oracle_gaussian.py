@@ -163,3 +163,13 @@ def test_matrix_dtypes_round_once():
     assert np.array_equal(G.gaussian_matrix(30, 7, 5, "f32"), v.astype(np.float32))
     assert np.array_equal(G.gaussian_matrix_as_f64(30, 7, 5, "bf16"),
                           G.bf16_bits_to_f64(G.to_bf16_bits(v)).reshape(30, 7))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_rows_of_o_without_forming_it(dtype):
+    """gaussian_rows gives the rows of the full matrix, in any order and with
+    repeats, for even and odd r (odd r splits Box-Muller pairs across rows)."""
+    for n, r in ((50, 8), (37, 7)):
+        full = G.gaussian_matrix_as_f64(n, r, 31, dtype)
+        rows = np.array([36, 0, 5, 5, 17, 1])
+        assert np.array_equal(G.gaussian_rows(rows, r, 31, dtype), full[rows])
