@@ -83,6 +83,21 @@ typedef struct {
                         over the top k, or at i = q.  Costs one small SVD per
                         iteration; rsvd_plan_info reports the count used. */
   double auto_q_tol; /* tolerance of auto_q; 0 selects 1e-3 */
+  int32_t fused;     /* 1: fused power sweeps (Section 2.2, Eq. (3) evaluated
+                        right to left with the products A^T (A W) grouped):
+                        W = O; q times W = orth(A^T (A W)); Q = orth(A W).  Only
+                        the n-side basis is orthonormalised between products;
+                        the span is that of the default scheme in exact
+                        arithmetic, but the sweep squares the spectrum, so
+                        directions below about sqrt(eps) sigma_1 are lost.  Out
+                        of core each sweep streams every row panel once (Y_I =
+                        A_I W, then Z += A_I^T Y_I while the panel is on the
+                        device): q + 2 reads of A instead of 2q + 2.  BF16 plans
+                        form A^T Y in split BF16.  Dense plans of FP64, FP32,
+                        BF16 or BF16X3 precision with a fixed q; streamed
+                        tiles must be full-width row panels (nb = 0 or n);
+                        no checkpoints. */
+  int32_t reserved;
 } rsvd_opts;
 
 /* Descriptor of the input matrix A (m x n). */
@@ -130,7 +145,8 @@ typedef struct {
   uint64_t seed;
   int32_t q_used;            /* power iterations applied by the last rsvd_run */
   int32_t resumed_from;      /* checkpoint step the last rsvd_run resumed after; -1: none */
-  int32_t bf16_copy;         /* 1: the last rsvd_run's later BF16 passes read a BF16 copy of A */
+  int32_t bf16_copy;         /* 1: the last rsvd_run's later passes read a BF16 copy of A
+                                (BF16X3 plans: the split copy) */
 } rsvd_plan_info_t;
 
 /* Header of a checkpoint file (rsvd_plan_set_checkpoint). */
@@ -186,7 +202,10 @@ rsvd_status rsvd_plan_info(rsvd_plan_t plan, rsvd_plan_info_t* out);
  * round_up(n, 64) bytes, owned by the plan from the first such run, within the
  * cap when there is one): the first forward pass writes it and the later
  * BF16 passes read it (the same operands, so the same result; half the bytes
- * per pass).  Without room for it every pass reads the FP32 A.
+ * per pass).  BF16X3 plans (k + p <= 192) keep the split copy instead, BF16(A)
+ * and BF16(A - BF16(A)) (4 m round_up(n, 64) bytes): the later passes read the
+ * two parts the FP32 A would be split into, with no conversion.  Without room
+ * for the copy every pass reads the FP32 A (the same results).
  * 16-bit storage (Section 3.2): an F32 plan with BF16 precision also takes a
  * dense A stored as BF16 or F16 (IEEE half; device: ld % 8 == 0 and a 16-byte
  * aligned base; host: copied to the device in core, never streamed), read
@@ -272,7 +291,8 @@ typedef enum {
   RSVD_STAGE_H2D = 6,         /* copy of a host-resident A */
   RSVD_STAGE_TOTAL = 7,       /* whole rsvd_run on the device */
   RSVD_STAGE_QUANTIZE = 8,    /* FP8 codes of A (FP8 precision only) */
-  RSVD_STAGE_COUNT = 9
+  RSVD_STAGE_SWEEP = 9,       /* fused sweeps A^T (A W) over streamed row panels */
+  RSVD_STAGE_COUNT = 10
 } rsvd_stage;
 
 /* Enable (1) or disable (0) stage timing: rsvd_run then records CUDA events

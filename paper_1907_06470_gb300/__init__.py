@@ -122,7 +122,7 @@ class Plan:
     """A planned rank-k randomized SVD (rsvd_plan); owns its device workspace."""
 
     def __init__(self, m, n, k, p=10, q=2, seed=0, mem_cap=0, prec=None, dtype="f32",
-                 mb=0, nb=0, refine=True, n_slots=2, kind="dense", auto_q=False, auto_q_tol=0.0):
+                 mb=0, nb=0, refine=True, n_slots=2, kind="dense", auto_q=False, auto_q_tol=0.0, fused=False):
         lib = load()
         if prec is None:
             prec = "fp64" if dtype == "f64" else "fp32"
@@ -135,6 +135,7 @@ class Plan:
         o.kind = {"dense": _lib.DENSE, "csr": _lib.CSR}[kind]
         o.auto_q = 1 if auto_q else 0
         o.auto_q_tol = float(auto_q_tol)
+        o.fused = 1 if fused else 0
         self.kind = kind
         h = C.c_void_p()
         _check(lib.rsvd_plan(m, n, k, p, q, seed, mem_cap, C.byref(o), C.byref(h)))
@@ -244,7 +245,7 @@ def _rsvd_function():
     return RSVDFunction
 
 
-def rsvd(A, k, p=10, q=2, seed=0, mem_cap=0, prec=None, mb=0, nb=0, refine=True, At=None):
+def rsvd(A, k, p=10, q=2, seed=0, mem_cap=0, prec=None, mb=0, nb=0, refine=True, At=None, fused=False):
     """Rank-k randomized SVD of a dense float64/float32 matrix, or of one stored
     as bfloat16/float16 (FP32 outputs, BF16-precision plan) (CUDA or pinned
     host tensor), of a float32 torch sparse CSR tensor (CUDA or host; `At`
@@ -269,7 +270,7 @@ def rsvd(A, k, p=10, q=2, seed=0, mem_cap=0, prec=None, mb=0, nb=0, refine=True,
         if A.requires_grad:
             raise TypeError("a bfloat16 or float16 A has no backward pass")
         prec = prec or "bf16"
-    plan = Plan(A.shape[0], A.shape[1], k, p, q, seed, mem_cap, prec, dtype, mb, nb, refine)
+    plan = Plan(A.shape[0], A.shape[1], k, p, q, seed, mem_cap, prec, dtype, mb, nb, refine, fused=fused)
     if A.requires_grad:
         return _rsvd_function().apply(A, plan)
     try:

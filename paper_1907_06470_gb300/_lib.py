@@ -11,7 +11,7 @@ from . import build as _build
 c_i32, c_i64, c_u64, c_size, c_vp = C.c_int32, C.c_int64, C.c_uint64, C.c_size_t, C.c_void_p
 
 RSVD_OK = 0
-STAGES = ["gaussian", "apass_fwd", "apass_trans", "orth", "small_svd", "lift", "h2d", "total", "quantize"]
+STAGES = ["gaussian", "apass_fwd", "apass_trans", "orth", "small_svd", "lift", "h2d", "total", "quantize", "sweep"]
 STATUS_NAMES = {
     0: "RSVD_OK", 1: "RSVD_ERR_INVALID_ARG", 2: "RSVD_ERR_OOM", 3: "RSVD_ERR_CAP_TOO_SMALL",
     4: "RSVD_ERR_CUDA", 5: "RSVD_ERR_NOT_SPD", 6: "RSVD_ERR_NO_CONVERGE", 7: "RSVD_ERR_TIMEOUT",
@@ -26,7 +26,7 @@ ON_DEVICE, ON_HOST = 0, 1
 class RsvdOpts(C.Structure):
     _fields_ = [("prec", c_i32), ("refine", c_i32), ("mb", c_i64), ("nb", c_i64),
                 ("n_slots", c_i32), ("dtype", c_i32), ("kind", c_i32), ("auto_q", c_i32),
-                ("auto_q_tol", C.c_double)]
+                ("auto_q_tol", C.c_double), ("fused", c_i32), ("reserved", c_i32)]
 
 
 class RsvdMatrix(C.Structure):

@@ -206,6 +206,7 @@ struct rsvd_plan_s {
   double* sigma_prev = nullptr;  // r: estimates of the previous power iteration (automatic q)
   int* q_flag = nullptr;    // device word: 1 when the change fell below the tolerance
   int auto_q = 0;           // choose q automatically (q is then the maximum)
+  int fused = 0;            // power iterations as fused sweeps W = orth(A^T (A W))
   double auto_q_tol = 1e-3;
   int q_used = 0;           // power iterations applied by the last run
   std::string ckpt_path;    // checkpoint file of the range finder ("" = off)
@@ -268,6 +269,9 @@ rsvd_status check_args(int64_t m, int64_t n, int k, int p, int q, const rsvd_opt
       return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: negative tile edge or slot count");
     if (o->auto_q_tol < 0.0 || !(o->auto_q_tol == o->auto_q_tol))
       return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: auto_q_tol must be >= 0 (0: default 1e-3)");
+    if (o->fused && (csr || o->prec == RSVD_PREC_FP8 || o->auto_q))
+      return fail(RSVD_ERR_UNSUPPORTED, "rsvd_plan: fused sweeps take dense plans of FP64, FP32, BF16 or BF16X3 "
+                                        "precision with a fixed q");
   }
   return RSVD_OK;
 }
@@ -284,6 +288,7 @@ void apply_opts(rsvd_plan_s* P, const rsvd_opts* o) {
     P->n_slots = o->n_slots > 0 ? o->n_slots : 2;
     P->kind = o->kind;
     P->auto_q = o->auto_q ? 1 : 0;
+    P->fused = o->fused ? 1 : 0;
     if (o->auto_q_tol > 0.0) P->auto_q_tol = o->auto_q_tol;
   }
   if (P->mb <= 0) P->mb = P->m;  // in core: one block row unless asked otherwise
@@ -313,10 +318,10 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   P->apass_ws = c.take<char>(P->apass_ws_bytes);
   // Range-finder bases only have to span the sketch: FP32 data orthonormalises
   // them on the tensor cores (split BF16) -- every basis for the BF16 / FP8
-  // paths, every basis but the final Q (whose orthonormality enters B = Q^T A)
-  // for the FP32 paths
-  P->tc_orth_all = P->dtype == RSVD_F32 &&
-                   (P->prec == RSVD_PREC_BF16 || P->prec == RSVD_PREC_BF16X3 || P->prec == RSVD_PREC_FP8);
+  // paths, every basis but the final Q (whose orthonormality enters B = Q^T A:
+  // a Q orthonormal to 2^-16 moves the singular values of Q^T A by about as
+  // much) for the FP32 and split-BF16 paths, which aim at FP32 accuracy
+  P->tc_orth_all = P->dtype == RSVD_F32 && (P->prec == RSVD_PREC_BF16 || P->prec == RSVD_PREC_FP8);
   P->tc_orth_inner = P->dtype == RSVD_F32;
   P->orth = orth_ws_carve(c, mx, P->r, P->dtype, P->tc_orth_inner);
   P->jac = jacobi_ws_carve(c, P->r, P->r);
@@ -368,14 +373,18 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
       ((prec == RSVD_PREC_BF16 || prec == RSVD_PREC_FP8) && P->refine) ? RSVD_PREC_BF16X3 : prec;
   Profiler& pf = P->prof;
   // BF16 plans in core stream a BF16 copy of A after the first plain forward
-  // pass has written it: half the bytes per pass, the same operands.
+  // pass has written it: half the bytes per pass, the same operands.  BF16X3
+  // plans keep the split copy (hi and lo parts, 4 bytes per entry like the
+  // FP32 A) so that their later passes move the operands without converting.
   bool use16 = false;
+  const bool split_copy = prec == RSVD_PREC_BF16X3;
   // A stored in 16 bits by the caller (Section 3.2): every pass reads it as is
   const bool a16_in = A.kind == RSVD_DENSE && (A.dtype == RSVD_BF16 || A.dtype == RSVD_F16);
   if constexpr (std::is_same<T, float>::value) {
-    if (prec == RSVD_PREC_BF16 && A.kind == RSVD_DENSE && !a16_in && !P->streaming && round_up(r, 16) <= 256) {
+    if ((prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3) && A.kind == RSVD_DENSE && !a16_in &&
+        !P->streaming && round_up(r, 16) <= (split_copy ? 192 : 256)) {
       const int64_t ld16 = round_up(n, 64);
-      const size_t need = (size_t)m * ld16 * sizeof(uint16_t);
+      const size_t need = (size_t)m * ld16 * sizeof(uint16_t) * (split_copy ? 2 : 1);
       const bool fits = P->mem_cap == 0 || P->ws_bytes + P->a_copy_bytes + need <= P->mem_cap;
       if (fits && P->a16_bytes < need) {
         if (P->a16) cudaFree(P->a16);
@@ -403,15 +412,17 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
         b.f16 = A.dtype == RSVD_F16 ? 1 : 0;
         return tc_apass_from_16(b, trans, pr, r, Xin, ldr, Yout, ldr, P->apass_ws, P->apass_ws_bytes, P->status, st);
       }
-      if (use16 && pr == RSVD_PREC_BF16) {
+      if (use16 && pr == prec) {
+        uint16_t* lo = split_copy ? P->a16 + (size_t)m * P->a16_ld : nullptr;
         if (P->a16_ready) {
           Bf16Source b;
-          b.data = P->a16; b.m = m; b.n = n; b.ld = P->a16_ld;
-          return tc_apass_from_bf16(b, trans, r, Xin, ldr, Yout, ldr, P->apass_ws, P->apass_ws_bytes, P->status, st);
+          b.data = P->a16; b.m = m; b.n = n; b.ld = P->a16_ld; b.lo = lo;
+          return tc_apass_from_16(b, trans, pr, r, Xin, ldr, Yout, ldr, P->apass_ws, P->apass_ws_bytes, P->status,
+                                  st);
         }
         if (!trans) {
-          RSVD_TRY(tc_apass_from_f32(A, 0, RSVD_PREC_BF16, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws,
-                                     P->apass_ws_bytes, P->status, st, false, P->a16, P->a16_ld));
+          RSVD_TRY(tc_apass_from_f32(A, 0, pr, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws,
+                                     P->apass_ws_bytes, P->status, st, false, P->a16, P->a16_ld, lo));
           P->a16_ready = true;
           return RSVD_OK;
         }
@@ -439,7 +450,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   };
   // Section 3.8 persistence: the header of each checkpoint places its basis in
   // the execution plan; a matching checkpoint lets the run skip its steps.
-  const bool ckpt_on = !P->ckpt_path.empty() && !P->auto_q;
+  const bool ckpt_on = !P->ckpt_path.empty() && !P->auto_q && !P->fused;
   CkptHeader hdr;
   std::memset(&hdr, 0, sizeof(hdr));
   int first_step = 0;
@@ -484,7 +495,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     }
     // step 2 and steps 3-4: Y = A O, Q = orth(Y) (range-finder step 0), unless
     // a checkpoint of this plan and this A lets the run resume later
-    if (first_step == 0) {
+    if (first_step == 0 && !P->fused) {
       RSVD_TRY(apass(0, prec, X, Y));
       RSVD_TRY(orth(m, Y, Q, P->q == 0));
       RSVD_TRY(checkpoint(0));
@@ -504,7 +515,25 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     };
     bool have_final = false;  // Bt, Qb, R and the small SVD already hold the final result
     P->q_used = P->q;
-    if (!P->auto_q) {
+    if (P->fused) {
+      // Eq. (3) right to left with the products A^T (A W) grouped per sweep
+      // and only the n-side orthonormalised: W = O; q times W = orth(A^T (A W));
+      // then Q = orth(A W).  Streamed, each sweep reads every row panel once.
+      const int prec_t = sweep_trans_prec(prec);
+      for (int i = 0; i < P->q; ++i) {
+        if (P->streaming) {
+          Span sp(pf, RSVD_STAGE_SWEEP, st);
+          ++pf.apass_calls;
+          RSVD_TRY(sweep_streamed(P->ss, A, prec, prec_t, r, X, Bt, ldr, P->status, st));
+        } else {
+          RSVD_TRY(apass(0, prec, X, Y));
+          RSVD_TRY(apass(1, prec_t, Y, Bt));
+        }
+        RSVD_TRY(orth(n, Bt, X, false));
+      }
+      RSVD_TRY(apass(0, prec, X, Y));
+      RSVD_TRY(orth(m, Y, Q, true));
+    } else if (!P->auto_q) {
       // Eq. (3), right to left: q times Z = orth(A^T Q), Q = orth(A Z); step
       // 2i+1 leaves Z in X, step 2i+2 leaves Q (checkpointed when enabled)
       for (int s = first_step > 0 ? first_step : 1; s <= 2 * P->q; ++s) {
@@ -994,6 +1023,9 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
         return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: FP8 precision needs A in device memory (no streaming)");
       const int final_prec =
           ((P->prec == RSVD_PREC_BF16 || P->prec == RSVD_PREC_FP8) && P->refine) ? RSVD_PREC_BF16X3 : P->prec;
+      // fused sweeps stream full-width row panels (the default tile shape)
+      if (P->fused && P->nb_req > 0 && P->nb_req < A->n)
+        return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: fused sweeps stream full-width row panels (nb = 0 or n)");
       RSVD_TRY(stream_prepare(&P->ss, A->m, A->n, elem_size(A->dtype), P->mb_req, P->nb_req, P->n_slots,
                               P->mem_cap - P->ws_bytes, P->r, P->prec, final_prec));
       stream_begin_run(P->ss);
@@ -1035,8 +1067,8 @@ rsvd_status rsvd_coo_to_csr(int64_t m, int64_t n, int64_t nnz, int32_t index_bit
 
 rsvd_status rsvd_plan_set_checkpoint(rsvd_plan_t P, const char* path, int32_t stop_after_step) {
   if (!P) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_set_checkpoint: NULL plan");
-  if (path && *path && P->auto_q)
-    return fail(RSVD_ERR_UNSUPPORTED, "rsvd_plan_set_checkpoint: not available with automatic q");
+  if (path && *path && (P->auto_q || P->fused))
+    return fail(RSVD_ERR_UNSUPPORTED, "rsvd_plan_set_checkpoint: not available with automatic q or fused sweeps");
   P->ckpt_path = path ? path : "";
   P->ckpt_stop_after = stop_after_step;
   return RSVD_OK;
@@ -1044,7 +1076,7 @@ rsvd_status rsvd_plan_set_checkpoint(rsvd_plan_t P, const char* path, int32_t st
 
 rsvd_status rsvd_plan_set_profiling(rsvd_plan_t P, int32_t enable) {
   if (!P) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_set_profiling: NULL plan");
-  if (enable) RSVD_TRY(P->prof.reserve(16 + 4 * ((size_t)P->q + 1)));
+  if (enable) RSVD_TRY(P->prof.reserve(20 + 4 * ((size_t)P->q + 1)));
   P->prof.on = enable != 0;
   return RSVD_OK;
 }

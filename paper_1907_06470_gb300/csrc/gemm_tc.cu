@@ -59,11 +59,15 @@ constexpr int BK = 64;             // K per step: one 128-byte BF16 row
 constexpr int A32_BYTES = BM * BK * 4;
 constexpr int A8_BYTES = BM * BK;
 constexpr int A16_BYTES = BM * BK * 2;
-// operand (BF16 A + panel) ring depth: a runtime choice of 2 or 4 (4 when the
-// FP32 staging ring keeps at least 3 stages next to it); deeper rings let the
-// panel tiles, which come from L2, be requested further ahead
-constexpr int kMaxSop = 4;
-// source of A: FP32, FP8 (E4M3 codes + tile scales) or a BF16 copy
+// operand (BF16 A + panel) ring depth: a runtime choice.  Converted sources
+// take 2 or 4 slots (4 when the FP32 staging ring keeps at least 3 stages next
+// to it); the 16-bit source, whose tiles TMA writes straight into the operand
+// slots, takes as many as fit (up to 8).  Deeper rings let the panel tiles,
+// which come from L2, be requested further ahead.
+constexpr int kMaxSop = 8;
+constexpr int kMaxSopConverted = 4;
+// source of A: FP32, FP8 (E4M3 codes + tile scales) or 16-bit values (the
+// plan's BF16 copy, or an A stored in BF16 / FP16)
 constexpr int kSrc32 = 0, kSrc8 = 1, kSrc16 = 2;
 constexpr int kSplitMaxNP = 192;   // widest split-mode panel one pass supports
 constexpr int THREADS = 320;
@@ -89,7 +93,9 @@ struct TcArgs {
   const float* qscale;  // FP8 source: per-tile scales, qtn per tile row
   int64_t qm, qn, qtn;  // FP8 source: tile edges (in rows / columns of A)
   uint16_t* a16;        // FP32 forward pass: also store BF16(A) here (row stride ld16), or null
+  uint16_t* a16lo;      // FP32 forward pass in split mode: also store BF16(A - BF16(A)) here, or null
   int64_t ld16;
+  int a_lo;             // 16-bit source in split mode: 1 when A has a lo part (A = hi + lo)
   int gram;             // 1: C = A^T A with one row tile: the panel operand is the converted A tile
   uint32_t idesc;       // tcgen05 instruction descriptor (operand type BF16 or FP16, FP32 accumulator)
 };
@@ -105,7 +111,8 @@ constexpr int kMaxS32 = RSVD_TC_MAX_S32;  // deepest FP32 staging ring
 template <bool SPLIT, int SRC = kSrc32>
 struct Layout {
   static constexpr int PARTS = SPLIT ? 2 : 1;
-  static constexpr int STAGE_BYTES = SRC == kSrc8 ? A8_BYTES : (SRC == kSrc16 ? A16_BYTES : A32_BYTES);
+  // the 16-bit source needs no staging ring: TMA fills the operand slots
+  static constexpr int STAGE_BYTES = SRC == kSrc8 ? A8_BYTES : (SRC == kSrc16 ? 0 : A32_BYTES);
   __host__ __device__ static size_t a16_off(int s, int part) { return ((size_t)s * PARTS + part) * A16_BYTES; }
   __host__ __device__ static size_t b16_base(int sop) { return (size_t)sop * PARTS * A16_BYTES; }
   __host__ __device__ static size_t b16_off(int NP, int sop, int s, int part) {
@@ -142,10 +149,14 @@ __device__ __forceinline__ float2 e4m3x2_scaled(uint16_t codes, float s) {
 
 template <bool TRANS, bool SPLIT, int SRC = kSrc32>
 __global__ void __launch_bounds__(THREADS, 1)
-tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                const __grid_constant__ CUtensorMap mapBlo, const TcArgs a) {
-  static_assert(!(SPLIT && SRC != kSrc32), "only the FP32 source has a one-launch split mode");
+tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapAlo,
+                const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapBlo,
+                const TcArgs a) {
+  static_assert(!(SPLIT && SRC == kSrc8), "the FP8 source has no split mode");
   constexpr bool SRC8 = SRC == kSrc8;
+  // 16-bit source: TMA lands A tiles in the operand slots in the MMA's layout
+  // (128-byte swizzle; K-major for A, MN-major for A^T) and no converter runs
+  constexpr bool DIRECT = SRC == kSrc16;
   using L = Layout<SPLIT, SRC>;
   const int SOP = a.sop;
   const int S32 = a.s32;
@@ -170,7 +181,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   if (threadIdx.x == 0) {
     for (int i = 0; i < S32; ++i) { ptx::mbar_init(&full32[i], 1); ptx::mbar_init(&empty32[i], 4); }
     for (int i = 0; i < SOP; ++i) {
-      ptx::mbar_init(&fullA[i], 4);
+      ptx::mbar_init(&fullA[i], DIRECT ? 1 : 4);
       ptx::mbar_init(&fullB[i], 1);
       ptx::mbar_init(&emptyOp[i], 1);
     }
@@ -182,6 +193,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     ptx::prefetch_tensormap(&mapA);
     ptx::prefetch_tensormap(&mapB);
     if (SPLIT) ptx::prefetch_tensormap(&mapBlo);
+    if (DIRECT && SPLIT && a.a_lo) ptx::prefetch_tensormap(&mapAlo);
   }
   if (warp == 1) {
     ptx::tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
@@ -201,7 +213,34 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     // has free slots; lane 1 loads the panel tiles into the operand slots as
     // the MMAs free them.  Separate lanes, so that a panel slot still in use
     // never holds back the prefetch of A.
-    if (lane == 0) {
+    if (lane == 0 && DIRECT) {
+      // A tiles straight into the operand slots: forward, one 64 x 128 box
+      // (K-major rows of 128 bytes); transposed, two 64 x 64 boxes (the two
+      // 64-row halves of the MN-major tile, 8 KB apart)
+      const int nA = (SPLIT && a.a_lo) ? 2 : 1;
+      const uint32_t a_bytes = (uint32_t)(A16_BYTES * nA);
+      RingPos rop;
+      for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
+        const int64_t z = u / a.mtiles, mt = u % a.mtiles;
+        const int64_t k0 = z * a.ksteps_per_split;
+        const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
+        for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
+          const int sop = rop.slot;
+          if (!ptx::mbar_wait(&emptyOp[sop], rop.phase ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
+          ptx::mbar_arrive_expect_tx(&fullA[sop], a_bytes);
+          for (int part = 0; part < nA; ++part) {
+            const CUtensorMap* map = part ? &mapAlo : &mapA;
+            uint8_t* dst = smem + L::a16_off(sop, part);
+            if (TRANS) {
+              ptx::tma_load_2d(dst, map, &fullA[sop], (int32_t)(mt * BM), (int32_t)(ks * BK));
+              ptx::tma_load_2d(dst + A16_BYTES / 2, map, &fullA[sop], (int32_t)(mt * BM + BM / 2), (int32_t)(ks * BK));
+            } else {
+              ptx::tma_load_2d(dst, map, &fullA[sop], (int32_t)(ks * BK), (int32_t)(mt * BM));
+            }
+          }
+        }
+      }
+    } else if (lane == 0) {
       RingPos r32;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
         const int64_t z = u / a.mtiles, mt = u % a.mtiles;
@@ -257,18 +296,25 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           }
           ptx::tc_fence_after();
           // Gram mode: the K-major tile of A^T is also the panel tile (its first NP rows)
-          const uint64_t ad = ptx::smem_desc_sw128(smem + L::a16_off(sop, 0));
+          // A^T from a 16-bit source is MN-major: 16 K values span two 8-row
+          // groups of 1024 bytes; K-major operands advance 32 bytes in the row
+          constexpr bool MN = DIRECT && TRANS;
+          const uint64_t astep = MN ? 2048 >> 4 : 2;
+          const uint64_t ad = MN ? ptx::smem_desc_sw128_mn(smem + L::a16_off(sop, 0), A16_BYTES / 2)
+                                 : ptx::smem_desc_sw128(smem + L::a16_off(sop, 0));
           const uint64_t bd = a.gram ? ad : ptx::smem_desc_sw128(smem + L::b16_off(NP, SOP, sop, 0));
+          const bool alo = SPLIT && (!DIRECT || a.a_lo);
+          const uint64_t adl = !alo ? 0
+                               : (MN ? ptx::smem_desc_sw128_mn(smem + L::a16_off(sop, 1), A16_BYTES / 2)
+                                     : ptx::smem_desc_sw128(smem + L::a16_off(sop, 1)));
+          const uint64_t bdl = !SPLIT ? 0 : (a.gram ? adl : ptx::smem_desc_sw128(smem + L::b16_off(NP, SOP, sop, 1)));
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            // advance 16 BF16 (32 bytes) along K inside the swizzled row
-            ptx::mma_bf16(d_tmem, ad + 2 * kk, bd + 2 * kk, idesc, accumulate);
+            ptx::mma_bf16(d_tmem, ad + astep * kk, bd + 2 * kk, idesc, accumulate);
             accumulate = 1;
             if (SPLIT) {
-              const uint64_t adl = ptx::smem_desc_sw128(smem + L::a16_off(sop, 1));
-              const uint64_t bdl = a.gram ? adl : ptx::smem_desc_sw128(smem + L::b16_off(NP, SOP, sop, 1));
-              ptx::mma_bf16(d_tmem, ad + 2 * kk, bdl + 2 * kk, idesc, 1);
-              ptx::mma_bf16(d_tmem, adl + 2 * kk, bd + 2 * kk, idesc, 1);
+              ptx::mma_bf16(d_tmem, ad + astep * kk, bdl + 2 * kk, idesc, 1);
+              if (alo) ptx::mma_bf16(d_tmem, adl + astep * kk, bd + 2 * kk, idesc, 1);
             }
           }
           ptx::mma_commit(&emptyOp[sop]);
@@ -277,7 +323,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         ptx::mma_commit(&accFull[acc]);
       }
     }
-  } else if (warp < 6) {
+  } else if (warp < 6 && !DIRECT) {
     // ---------------- converters ----------------
     const int cw = warp - 2;
     RingPos r32, rop;
@@ -336,48 +382,6 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
               *reinterpret_cast<uint4*>(hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
             }
           }
-        } else if (SRC == kSrc16) {
-          const uint8_t* s16 = smem + L::a32_off(NP, SOP, s32);
-          if (!TRANS) {
-            // v[i][k], 128 rows of 64 values (128 bytes): lane l moves 16-byte
-            // chunk c = l & 7 of row 4 step + l / 8 to its swizzled place
-            const int c = lane & 7;
-#pragma unroll 4
-            for (int rr = 0; rr < 32; rr += 4) {
-              const int i = cw * 32 + rr + (lane >> 3);
-              const uint4 v = *reinterpret_cast<const uint4*>(s16 + i * 128 + 16 * c);
-              const uint32_t off = (uint32_t)i * 128u + ((((uint32_t)c) ^ ((uint32_t)i & 7u)) << 4);
-              *reinterpret_cast<uint4*>(hi + off) = v;
-            }
-          } else {
-            // v[k][i], 64 rows of 128 values.  Thread t = 32 cw + lane takes the
-            // row pair (2p, 2p+1), p = t & 63, for the chunks 4h .. 4h+3,
-            // h = t >> 6: one 32-bit load gives both rows' values at one k, and
-            // byte permutes split them into the two rows' K-major chunks.  The
-            // pairs with bit 2 of p set store the odd row first, so that the 8
-            // lanes of each store phase cover all 8 swizzle positions.
-            const uint32_t* v32 = reinterpret_cast<const uint32_t*>(s16);
-            const int t = cw * 32 + lane, p = t & 63, h = t >> 6;
-            const bool sw = (p >> 2) & 1;
-            const uint32_t sel_a = sw ? 0x7632u : 0x5410u, sel_b = sw ? 0x5410u : 0x7632u;
-            const uint32_t row_a = (uint32_t)(2 * p + (sw ? 1 : 0)), row_b = (uint32_t)(2 * p + (sw ? 0 : 1));
-#pragma unroll 2
-            for (int c = 4 * h; c < 4 * h + 4; ++c) {
-              uint32_t w[8];
-#pragma unroll
-              for (int kk = 0; kk < 8; ++kk) w[kk] = v32[(c * 8 + kk) * (BM / 2) + p];
-              uint32_t fa[4], fb[4];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                fa[j] = __byte_perm(w[2 * j], w[2 * j + 1], sel_a);
-                fb[j] = __byte_perm(w[2 * j], w[2 * j + 1], sel_b);
-              }
-              const uint32_t offa = row_a * 128u + ((((uint32_t)c) ^ (row_a & 7u)) << 4);
-              const uint32_t offb = row_b * 128u + ((((uint32_t)c) ^ (row_b & 7u)) << 4);
-              *reinterpret_cast<uint4*>(hi + offa) = make_uint4(fa[0], fa[1], fa[2], fa[3]);
-              *reinterpret_cast<uint4*>(hi + offb) = make_uint4(fb[0], fb[1], fb[2], fb[3]);
-            }
-          }
         } else if (!TRANS) {
           // src[i][k], 128 rows of 64 floats.  Two rows per step: lane l converts
           // the float4 q = l & 15 (k = 4q .. 4q+3) of row 2 step + l / 16, i.e.
@@ -395,15 +399,19 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
                 make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
             *reinterpret_cast<uint2*>(hi + off) = hv;
             // the BF16 copy of A for later passes (rows past M are TMA fill; the
-            // copy's rows are padded to whole 64-column tiles)
-            if (!SPLIT && a.a16 && mt * BM + i < a.M)
-              *reinterpret_cast<uint2*>(a.a16 + (mt * BM + i) * a.ld16 + ks * BK + 4 * q) = hv;
+            // copy's rows are padded to whole 64-column tiles); split mode: its
+            // lo part too
+            const bool keep = a.a16 && mt * BM + i < a.M;
+            const int64_t coff = (mt * BM + i) * a.ld16 + ks * BK + 4 * q;
+            if (keep) *reinterpret_cast<uint2*>(a.a16 + coff) = hv;
             if (SPLIT) {
               const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
               const __nv_bfloat162 l0 = __float22bfloat162_rn(make_float2(v.x - f0.x, v.y - f0.y));
               const __nv_bfloat162 l1 = __float22bfloat162_rn(make_float2(v.z - f1.x, v.w - f1.y));
-              *reinterpret_cast<uint2*>(lo + off) =
+              const uint2 lv =
                   make_uint2(*reinterpret_cast<const uint32_t*>(&l0), *reinterpret_cast<const uint32_t*>(&l1));
+              *reinterpret_cast<uint2*>(lo + off) = lv;
+              if (keep && a.a16lo) *reinterpret_cast<uint2*>(a.a16lo + coff) = lv;
             }
           }
         } else {
@@ -619,8 +627,9 @@ namespace {
 struct TcSource {
   const rsvd_matrix* A = nullptr;   // FP32 source
   const Fp8Source* f8 = nullptr;    // FP8 source
-  const Bf16Source* b16 = nullptr;  // BF16 source
+  const Bf16Source* b16 = nullptr;  // 16-bit source (optionally with a lo part)
   uint16_t* copy16 = nullptr;       // FP32 forward pass: write the BF16 copy here
+  uint16_t* copy16lo = nullptr;     // FP32 forward pass in split mode: and its lo part here
   int64_t ld16 = 0;
 };
 
@@ -631,15 +640,18 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   const bool src8 = src.f8 != nullptr;
   const bool src16 = src.b16 != nullptr;
   const bool f16 = src16 && src.b16->f16;
-  // 16-bit source in split mode: A is exact, the panel is split; two launches
-  const bool split2 = split && src16;
+  // 16-bit source in split mode: A X_hi + A X_lo, plus A_lo X_hi when A has a
+  // lo part (the split copy of an FP32 A)
+  const bool a_lo = split && src16 && src.b16->lo != nullptr;
   if (r < 1 || r > 512) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: r must be in [1, 512]");
   if (split && src8) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: the FP8 source has no split mode");
-  if (src.copy16 && (split || trans || src8 || src16 || round_up(r, 16) > 256 || src.ld16 < round_up(n, BK) ||
-                     src.ld16 % BK != 0))
-    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: the BF16 copy is written by one plain forward pass "
-                                      "over FP32 A (ld16 a multiple of 64 covering n)");
-  if (round_up(r, 16) > ((split && !split2) ? kSplitMaxNP : 256)) {
+  if (src16 && src.b16->lo && f16)
+    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: a split 16-bit source is BF16");
+  if (src.copy16 && (trans || src8 || src16 || round_up(r, 16) > (split ? kSplitMaxNP : 256) ||
+                     src.ld16 < round_up(n, BK) || src.ld16 % BK != 0 || (src.copy16lo && !split)))
+    return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: the BF16 copy is written by one forward pass "
+                                      "over FP32 A (ld16 a multiple of 64 covering n; its lo part in split mode)");
+  if (round_up(r, 16) > (split ? kSplitMaxNP : 256)) {
     // wider than one accumulator (256 columns) or than the split-mode operand
     // ring fits: passes over column halves of the panel (A is read per half)
     const int h = (int)round_up(cdiv(r, 2), 16);
@@ -649,7 +661,8 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   }
   if (!src8 && !src16 && (src.A->ld % 4 != 0 || (reinterpret_cast<uintptr_t>(src.A->data) & 15) != 0))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: A needs a 16-byte aligned base and ld % 4 == 0");
-  if (src16 && (src.b16->ld % 8 != 0 || (reinterpret_cast<uintptr_t>(src.b16->data) & 15) != 0))
+  if (src16 && (src.b16->ld % 8 != 0 || (reinterpret_cast<uintptr_t>(src.b16->data) & 15) != 0 ||
+                (reinterpret_cast<uintptr_t>(src.b16->lo) & 15) != 0))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: a 16-bit A needs a 16-byte aligned base and ld % 8 == 0");
   if (src8 && (src.f8->ldc % 16 != 0 || (reinterpret_cast<uintptr_t>(src.f8->codes) & 15) != 0))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: FP8 codes need a 16-byte aligned base and ld % 16 == 0");
@@ -677,17 +690,24 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
     RSVD_CUDA(after_launch());
   }
   const CUtensorMapDataType t16 = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  CUtensorMap mapA, mapB, mapBlo;
+  CUtensorMap mapA, mapAlo, mapB, mapBlo;
   const uint32_t box_in = trans ? BM : BK, box_out = trans ? BK : BM;
-  if (src8)
+  if (src8) {
     RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_UINT8, src.f8->codes, (uint64_t)n, (uint64_t)m,
                        (uint64_t)src.f8->ldc, box_in, box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
-  else if (src16)
-    RSVD_TRY(encode_2d(&mapA, t16, src.b16->data, (uint64_t)n, (uint64_t)m, (uint64_t)src.b16->ld * 2, box_in,
-                       box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
-  else
+  } else if (src16) {
+    // tiles land in the operand slots in the MMA's layout: 128-byte rows
+    // (64 values) with the 128-byte swizzle; A^T in two 64-wide halves
+    const uint32_t bi = BK, bo = trans ? BK : BM;
+    RSVD_TRY(encode_2d(&mapA, t16, src.b16->data, (uint64_t)n, (uint64_t)m, (uint64_t)src.b16->ld * 2, bi, bo,
+                       CU_TENSOR_MAP_SWIZZLE_128B));
+    if (a_lo)
+      RSVD_TRY(encode_2d(&mapAlo, t16, src.b16->lo, (uint64_t)n, (uint64_t)m, (uint64_t)src.b16->ld * 2, bi, bo,
+                         CU_TENSOR_MAP_SWIZZLE_128B));
+  } else
     RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, src.A->data, (uint64_t)n, (uint64_t)m,
                        (uint64_t)src.A->ld * 4, box_in, box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
+  if (!a_lo) mapAlo = mapA;
   RSVD_TRY(encode_2d(&mapB, t16, Xhi, (uint64_t)s.K, (uint64_t)s.NP, (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP,
                      CU_TENSOR_MAP_SWIZZLE_128B));
   if (split)
@@ -718,46 +738,51 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   ta.qn = src8 ? src.f8->qn : 1;
   ta.qtn = src8 ? cdiv(n, src.f8->qn) : 1;
   ta.a16 = src.copy16;
+  ta.a16lo = src.copy16lo;
   ta.ld16 = src.ld16;
+  ta.a_lo = a_lo ? 1 : 0;
   ta.gram = gram ? 1 : 0;
   ta.idesc = f16 ? ptx::idesc_f16_f32(BM, (uint32_t)s.NP) : ptx::idesc_bf16_f32(BM, (uint32_t)s.NP);
+  if (src16 && trans) ta.idesc |= ptx::kIdescAMajorMN;
 
   const int64_t units = s.mtiles * s.nsplit;
   const int grid = (int)(units < num_sms() ? units : num_sms());
   constexpr size_t kSmemMax = 232448;
   auto need = [&](int sop, int depth) {
-    return (split && !split2) ? Layout<true>::total(s.NP, sop, depth)
-                 : (src8 ? Layout<false, kSrc8>::total(s.NP, sop, depth)
-                         : (src16 ? Layout<false, kSrc16>::total(s.NP, sop, depth)
-                                  : Layout<false>::total(s.NP, sop, depth)));
+    if (src16)
+      return split ? Layout<true, kSrc16>::total(s.NP, sop, depth) : Layout<false, kSrc16>::total(s.NP, sop, depth);
+    return split ? Layout<true>::total(s.NP, sop, depth)
+                 : (src8 ? Layout<false, kSrc8>::total(s.NP, sop, depth) : Layout<false>::total(s.NP, sop, depth));
   };
-  // four operand slots when at least three staging stages still fit, else two
-  int sop = need(kMaxSop, 3) <= kSmemMax ? kMaxSop : 2;
-  int s32 = kMaxS32;
-  while (s32 > 2 && need(sop, s32) > kSmemMax) --s32;
+  int sop, s32;
+  if (src16) {
+    // no staging ring: as many operand slots as fit
+    s32 = 0;
+    sop = kMaxSop;
+    while (sop > 2 && need(sop, 0) > kSmemMax) --sop;
+  } else {
+    // four operand slots when at least three staging stages still fit, else two
+    sop = need(kMaxSopConverted, 3) <= kSmemMax ? kMaxSopConverted : 2;
+    s32 = kMaxS32;
+    while (s32 > 2 && need(sop, s32) > kSmemMax) --s32;
+  }
   const size_t smem = need(sop, s32);
   if (smem > kSmemMax) return fail(RSVD_ERR_UNSUPPORTED, "tensor-core A-pass: shared memory plan too large");
   ta.s32 = s32;
   ta.sop = sop;
   auto launch = [&](auto kern) -> rsvd_status {
     RSVD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, THREADS, smem, stream>>>(mapA, mapB, mapBlo, ta);
+    kern<<<grid, THREADS, smem, stream>>>(mapA, mapAlo, mapB, mapBlo, ta);
     RSVD_CUDA(after_launch());
     return RSVD_OK;
   };
   if (src8) {
     RSVD_TRY(trans ? launch(tc_apass_kernel<true, false, kSrc8>) : launch(tc_apass_kernel<false, false, kSrc8>));
   } else if (src16) {
-    RSVD_TRY(trans ? launch(tc_apass_kernel<true, false, kSrc16>) : launch(tc_apass_kernel<false, false, kSrc16>));
-    if (split2) {  // + A X_lo: added by the epilogue, or as a second set of partials
-      if (s.nsplit > 1)
-        RSVD_TRY(reduce_partials<float>(s.M, r, s.nsplit, partial, r, slab, Y, ldy, accumulate, stream));
-      ta.accumulate = s.nsplit == 1 ? 1 : 0;
-      mapB = mapBlo;
+    if (split)
+      RSVD_TRY(trans ? launch(tc_apass_kernel<true, true, kSrc16>) : launch(tc_apass_kernel<false, true, kSrc16>));
+    else
       RSVD_TRY(trans ? launch(tc_apass_kernel<true, false, kSrc16>) : launch(tc_apass_kernel<false, false, kSrc16>));
-      if (s.nsplit > 1) RSVD_TRY(reduce_partials<float>(s.M, r, s.nsplit, partial, r, slab, Y, ldy, true, stream));
-      return RSVD_OK;
-    }
   } else if (trans) {
     RSVD_TRY(split ? launch(tc_apass_kernel<true, true>) : launch(tc_apass_kernel<true, false>));
   } else {
@@ -773,10 +798,11 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
 rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X, int64_t ldx,
                               float* Y, int64_t ldy, int64_t, int64_t, void* ws, size_t ws_bytes,
                               int* status, cudaStream_t stream, bool accumulate, uint16_t* copy16,
-                              int64_t ld16) {
+                              int64_t ld16, uint16_t* copy16lo) {
   TcSource src;
   src.A = &A;
   src.copy16 = copy16;
+  src.copy16lo = copy16lo;
   src.ld16 = ld16;
   return tc_apass_run(src, A.m, A.n, trans, prec, r, X, ldx, Y, ldy, ws, ws_bytes, status, stream, accumulate);
 }

@@ -165,6 +165,11 @@ rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, i
 void stream_begin_run(StreamState* s);
 rsvd_status apass_streamed(StreamState* s, const rsvd_matrix& Ah, int trans, int prec, int r, const void* X,
                            void* Y, int64_t ldr, int* status, cudaStream_t st);
+// Precision of the products A^T (A W) in a fused sweep for a plan precision.
+int sweep_trans_prec(int prec);
+// One fused power sweep Z = A^T (A W) over streamed full-width row panels.
+rsvd_status sweep_streamed(StreamState* s, const rsvd_matrix& Ah, int prec, int prec_t, int r, const void* W,
+                           void* Z, int64_t ldr, int* status, cudaStream_t st);
 void stream_state_free(StreamState* s);
 void stream_stats(const StreamState* s, uint64_t* h2d, int64_t* per_pass, int64_t* cached);
 
@@ -193,18 +198,22 @@ rsvd_status fp8_quantize(const float* A, int64_t m, int64_t n, int64_t lda, int6
 rsvd_status tc_apass_from_fp8(const Fp8Source& f8, int trans, int r, const float* X, int64_t ldx, float* Y,
                               int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream,
                               bool accumulate = false);
-// copy16 (optional, plain BF16 forward pass only): the pass also stores
-// BF16(A), rounded as its operands are, row-major with stride ld16 (a multiple
-// of 64 >= n), for tc_apass_from_bf16.
+// copy16 (optional, forward pass only): the pass also stores BF16(A), rounded
+// as its operands are, row-major with stride ld16 (a multiple of 64 >= n),
+// for tc_apass_from_bf16; copy16lo (optional, split mode only) receives
+// BF16(A - BF16(A)) in the same layout, the lo part of the split operand.
 rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X,
                               int64_t ldx, float* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws,
                               size_t ws_bytes, int* status, cudaStream_t stream, bool accumulate = false,
-                              uint16_t* copy16 = nullptr, int64_t ld16 = 0);
+                              uint16_t* copy16 = nullptr, int64_t ld16 = 0, uint16_t* copy16lo = nullptr);
 // A BF16 copy of a dense m x n A (row-major, stride ld elements).
 struct Bf16Source {
   const uint16_t* data = nullptr;
   int64_t m = 0, n = 0, ld = 0;
   int f16 = 0;  // 1: the values are IEEE FP16 (the panel is then rounded to FP16)
+  // optional second part of the same layout: A = data + lo (the split copy of
+  // an FP32 A, BF16 only); split-mode passes then form three products
+  const uint16_t* lo = nullptr;
 };
 // The BF16 A-pass over the copy: the same operands, hence the same result, as
 // tc_apass_from_f32 with prec BF16 on the FP32 A the copy was made from.
@@ -212,7 +221,8 @@ rsvd_status tc_apass_from_bf16(const Bf16Source& b16, int trans, int r, const fl
                                int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream);
 // A-pass over a 16-bit A (BF16 or FP16, m x n, row stride ld % 8 == 0, 16-byte
 // aligned): prec BF16 rounds the panel to A's type; BF16X3 splits it in two
-// (hi + lo) and adds the two products.
+// (hi + lo) and adds the two products, and when A has a lo part (the split
+// copy of an FP32 A) the product of that part with the panel's hi part too.
 rsvd_status tc_apass_from_16(const Bf16Source& a16, int trans, int prec, int r, const float* X, int64_t ldx,
                              float* Y, int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream,
                              bool accumulate = false);

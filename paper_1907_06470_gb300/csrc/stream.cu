@@ -34,6 +34,8 @@ struct StreamState {
   size_t device_bytes = 0;
   void* ws = nullptr;                // A-pass workspace sized for one tile
   size_t ws_bytes = 0;
+  void* ytile = nullptr;             // fused sweeps: A_I W of the current row panel (mb x ldr)
+  size_t ytile_bytes = 0;
 
   ~StreamState() {
     for (void* p : slot) cudaFree(p);
@@ -43,10 +45,13 @@ struct StreamState {
     for (auto e : cache_ev) cudaEventDestroy(e);
     if (copy) cudaStreamDestroy(copy);
     if (ws) cudaFree(ws);
+    if (ytile) cudaFree(ytile);
   }
 };
 
 void stream_state_free(StreamState* s) { delete s; }
+
+static int slot_of(const StreamState* s, int64_t t) { return (int)(t % s->S); }
 
 void stream_stats(const StreamState* s, uint64_t* h2d, int64_t* per_pass, int64_t* cached) {
   if (h2d) *h2d = s ? s->h2d_bytes : 0;
@@ -89,11 +94,13 @@ rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, i
   for (int64_t tr_rows : rows_opts)
     for (int64_t tr_cols : cols_opts)
       for (int tr = 0; tr < 2; ++tr)
-        for (int pr : {prec, final_prec}) {
+        for (int pr : {prec, final_prec, sweep_trans_prec(prec)}) {
           const size_t b = apass_ws_bytes(tr_rows, tr_cols, r, tr, pr, 0, 0) + 512;
           if (b > tws) tws = b;
         }
-  if ((size_t)slots * tile_bytes + tws > budget)
+  // fused sweeps keep A_I W of one row panel (FP32 or FP64, ldr columns)
+  const size_t ytile_bytes = (size_t)mb * round_up(r, 4) * (esz == 8 ? 8 : 4) + 256;
+  if ((size_t)slots * tile_bytes + tws + ytile_bytes > budget)
     return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: mem_cap leaves no room for the streaming slots");
   StreamState* s = *ps;
   if (s && s->mb == mb && s->nb == nb && s->S == slots && s->tile_bytes == tile_bytes) return RSVD_OK;
@@ -108,6 +115,8 @@ rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, i
   RSVD_CUDA(cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking));
   RSVD_CUDA(cudaMalloc(&s->ws, tws));
   s->ws_bytes = tws;
+  RSVD_CUDA(cudaMalloc(&s->ytile, ytile_bytes));
+  s->ytile_bytes = ytile_bytes;
   for (int i = 0; i < slots; ++i) {
     void* p = nullptr;
     RSVD_CUDA(cudaMalloc(&p, tile_bytes));
@@ -119,7 +128,7 @@ rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, i
     s->freed.push_back(b);
   }
   const int64_t ntiles = cdiv(m, mb) * cdiv(n, nb);
-  int64_t ncache = (int64_t)((budget - (size_t)slots * tile_bytes - tws) / tile_bytes);
+  int64_t ncache = (int64_t)((budget - (size_t)slots * tile_bytes - tws - ytile_bytes) / tile_bytes);
   if (ncache > ntiles) ncache = ntiles;
   for (int64_t t = 0; t < ncache; ++t) {
     void* p = nullptr;
@@ -135,7 +144,7 @@ rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, i
   s->cache_valid.assign(s->cache.size(), 0);
   s->tiles_cached = (int64_t)s->cache.size();
   s->tiles_per_pass = ntiles - s->tiles_cached;
-  s->device_bytes = (size_t)(slots + s->cache.size()) * tile_bytes + tws;
+  s->device_bytes = (size_t)(slots + s->cache.size()) * tile_bytes + tws + ytile_bytes;
   return RSVD_OK;
 }
 
@@ -144,55 +153,98 @@ void stream_begin_run(StreamState* s) {
   std::fill(s->cache_valid.begin(), s->cache_valid.end(), 0);
 }
 
+namespace {
+
+// Make tile t (rows [row0, row0+rows) x cols [col0, col0+cols)) available on
+// the device for the compute stream: a resident copy, or a copy into its slot
+// on the side stream that the compute stream waits for.  Returns the device
+// tile (row stride ld_tile) and whether it is resident.
+rsvd_status fetch_tile(StreamState* s, const rsvd_matrix& Ah, int64_t t, int64_t row0, int64_t col0, int64_t rows,
+                       int64_t cols, size_t esz, cudaStream_t st, rsvd_matrix* T, bool* cached_out) {
+  const bool cached = t < (int64_t)s->cache.size();
+  const int slot = (int)(t % s->S);
+  void* tile = cached ? s->cache[t] : s->slot[slot];
+  if (!cached || !s->cache_valid[t]) {
+    const char* host = static_cast<const char*>(Ah.data);
+    if (!cached) RSVD_CUDA(cudaStreamWaitEvent(s->copy, s->freed[slot], 0));
+    RSVD_CUDA(cudaMemcpy2DAsync(tile, (size_t)s->ld_tile * esz, host + ((size_t)row0 * Ah.ld + col0) * esz,
+                                (size_t)Ah.ld * esz, (size_t)cols * esz, (size_t)rows, cudaMemcpyHostToDevice,
+                                s->copy));
+    cudaEvent_t done = cached ? s->cache_ev[t] : s->copied[slot];
+    RSVD_CUDA(cudaEventRecord(done, s->copy));
+    RSVD_CUDA(cudaStreamWaitEvent(st, done, 0));
+    s->h2d_bytes += (uint64_t)rows * cols * esz;
+    if (cached) s->cache_valid[t] = 1;
+  }
+  *T = Ah;
+  T->location = RSVD_ON_DEVICE;
+  T->m = rows;
+  T->n = cols;
+  T->data = tile;
+  T->ld = s->ld_tile;
+  *cached_out = cached;
+  return RSVD_OK;
+}
+
+}  // namespace
+
+int sweep_trans_prec(int prec) { return prec == RSVD_PREC_BF16 ? RSVD_PREC_BF16X3 : prec; }
+
 // One streamed A-pass.  X: K x r panel (K = n forward, m transposed), Y: M x r
 // output, both device, leading dimension ldr; the output is zeroed first and
 // every tile adds its product in tile order.
 rsvd_status apass_streamed(StreamState* s, const rsvd_matrix& Ah, int trans, int prec, int r, const void* X,
                            void* Y, int64_t ldr, int* status, cudaStream_t st) {
-  void* ws = s->ws;
-  const size_t ws_bytes = s->ws_bytes;
   const int64_t m = Ah.m, n = Ah.n;
   const size_t esz = Ah.dtype == RSVD_F64 ? 8 : 4;
   const int64_t M = trans ? n : m;
   const int64_t Tm = cdiv(m, s->mb), Tn = cdiv(n, s->nb);
   RSVD_CUDA(cudaMemsetAsync(Y, 0, (size_t)M * ldr * esz, st));
-  const char* host = static_cast<const char*>(Ah.data);
   for (int64_t I = 0; I < Tm; ++I) {
     for (int64_t J = 0; J < Tn; ++J) {
       const int64_t t = I * Tn + J;
       const int64_t row0 = I * s->mb, col0 = J * s->nb;
       const int64_t rows = (row0 + s->mb < m ? s->mb : m - row0);
       const int64_t cols = (col0 + s->nb < n ? s->nb : n - col0);
-      const bool cached = t < (int64_t)s->cache.size();
-      const int slot = (int)(t % s->S);
-      void* tile = cached ? s->cache[t] : s->slot[slot];
-      if (!cached || !s->cache_valid[t]) {
-        if (!cached) RSVD_CUDA(cudaStreamWaitEvent(s->copy, s->freed[slot], 0));
-        RSVD_CUDA(cudaMemcpy2DAsync(tile, (size_t)s->ld_tile * esz, host + ((size_t)row0 * Ah.ld + col0) * esz,
-                                    (size_t)Ah.ld * esz, (size_t)cols * esz, (size_t)rows, cudaMemcpyHostToDevice,
-                                    s->copy));
-        cudaEvent_t done = cached ? s->cache_ev[t] : s->copied[slot];
-        RSVD_CUDA(cudaEventRecord(done, s->copy));
-        RSVD_CUDA(cudaStreamWaitEvent(st, done, 0));
-        s->h2d_bytes += (uint64_t)rows * cols * esz;
-        if (cached) s->cache_valid[t] = 1;
-      }
-      rsvd_matrix T = Ah;
-      T.location = RSVD_ON_DEVICE;
-      T.m = rows;
-      T.n = cols;
-      T.data = tile;
-      T.ld = s->ld_tile;
+      rsvd_matrix T;
+      bool cached;
+      RSVD_TRY(fetch_tile(s, Ah, t, row0, col0, rows, cols, esz, st, &T, &cached));
       const char* Xc = static_cast<const char*>(X);
       char* Yc = static_cast<char*>(Y);
       if (!trans)
         RSVD_TRY(apass_dense(T, 0, prec, r, Xc + (size_t)col0 * ldr * esz, ldr, Yc + (size_t)row0 * ldr * esz, ldr,
-                             0, 0, ws, ws_bytes, status, st, true));
+                             0, 0, s->ws, s->ws_bytes, status, st, true));
       else
         RSVD_TRY(apass_dense(T, 1, prec, r, Xc + (size_t)row0 * ldr * esz, ldr, Yc + (size_t)col0 * ldr * esz, ldr,
-                             0, 0, ws, ws_bytes, status, st, true));
-      if (!cached) RSVD_CUDA(cudaEventRecord(s->freed[slot], st));
+                             0, 0, s->ws, s->ws_bytes, status, st, true));
+      if (!cached) RSVD_CUDA(cudaEventRecord(s->freed[slot_of(s, t)], st));
     }
+  }
+  return RSVD_OK;
+}
+
+// One fused power sweep over full-width row panels (Section 2.2, Eq. (3) with
+// the product A^T (A W) grouped per panel): for each row panel A_I, in order,
+// Y_I = A_I W and then Z += A_I^T Y_I with the panel still on the device, so A
+// crosses the host link once per sweep instead of twice.  W and Z: n x r
+// (leading dimension ldr); Z is zeroed first.  prec_t is the precision of the
+// products A_I^T Y_I (BF16 plans carry Y_I as two BF16 parts there).
+rsvd_status sweep_streamed(StreamState* s, const rsvd_matrix& Ah, int prec, int prec_t, int r, const void* W,
+                           void* Z, int64_t ldr, int* status, cudaStream_t st) {
+  const int64_t m = Ah.m, n = Ah.n;
+  if (s->nb < n) return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: fused sweeps stream full-width row panels (nb = n)");
+  const size_t esz = Ah.dtype == RSVD_F64 ? 8 : 4;
+  const int64_t Tm = cdiv(m, s->mb);
+  RSVD_CUDA(cudaMemsetAsync(Z, 0, (size_t)n * ldr * esz, st));
+  for (int64_t I = 0; I < Tm; ++I) {
+    const int64_t row0 = I * s->mb;
+    const int64_t rows = (row0 + s->mb < m ? s->mb : m - row0);
+    rsvd_matrix T;
+    bool cached;
+    RSVD_TRY(fetch_tile(s, Ah, I, row0, 0, rows, n, esz, st, &T, &cached));
+    RSVD_TRY(apass_dense(T, 0, prec, r, W, ldr, s->ytile, ldr, 0, 0, s->ws, s->ws_bytes, status, st, false));
+    RSVD_TRY(apass_dense(T, 1, prec_t, r, s->ytile, ldr, Z, ldr, 0, 0, s->ws, s->ws_bytes, status, st, true));
+    if (!cached) RSVD_CUDA(cudaEventRecord(s->freed[slot_of(s, I)], st));
   }
   return RSVD_OK;
 }

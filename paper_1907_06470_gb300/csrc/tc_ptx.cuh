@@ -161,6 +161,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(const void* tile) {
   return ((addr & 0x3FFFFull) >> 4) | (1ull << 16) | ((1024ull >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 
+// Descriptor of an MN-major operand tile with the 128-byte swizzle, as TMA
+// writes it from 64-element boxes: each 64-element run of M (or N) is one
+// 128-byte row, 8 consecutive K rows form a 1024-byte swizzle atom, atoms
+// follow each other along K at a 1024-byte stride (stride byte offset) and
+// the next 64 elements of M start `mn_stride` bytes further (leading byte
+// offset).
+__device__ __forceinline__ uint64_t smem_desc_sw128_mn(const void* tile, uint32_t mn_stride) {
+  const uint64_t addr = smem_u32(tile);
+  return ((addr & 0x3FFFFull) >> 4) | ((uint64_t)((mn_stride >> 4) & 0x3FFF) << 16) | ((1024ull >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, both operands
 // K-major: D format (bits 4-5) = 1, A format (7-9) = 1, B format (10-12) = 1,
 // N >> 3 (bits 17-22), M >> 4 (bits 24-28).
@@ -171,6 +183,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N) {
 __host__ __device__ constexpr uint32_t idesc_f16_f32(uint32_t M, uint32_t N) {
   return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
+// Bit 15 of the instruction descriptor: A is MN-major (transposed).
+constexpr uint32_t kIdescAMajorMN = 1u << 15;
 
 }  // namespace ptx
 }  // namespace rsvd

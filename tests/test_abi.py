@@ -296,3 +296,27 @@ def test_checkpoint_header_is_read_and_validated(lib, tmp_path):
             g.checkpoint_info(path)
     with pytest.raises(g.RsvdError):
         g.checkpoint_info(tmp_path / "missing.bin")
+
+
+def test_fused_sweep_plan_rules(lib):
+    """Fused sweeps: dense plans with a fixed q and a precision other than FP8
+    (checked on the host before any device call)."""
+    from paper_1907_06470_gb300 import _lib
+    h = C.c_void_p()
+    out = C.c_size_t()
+    ok = _lib.RsvdOpts(prec=1, refine=1, mb=0, nb=0, n_slots=2, dtype=1, fused=1)
+    assert lib.rsvd_plan_min_cap(1000, 500, 10, 5, C.byref(ok), C.byref(out)) == 0
+    for bad in (dict(kind=1), dict(prec=4), dict(auto_q=1)):
+        kw = dict(prec=1, refine=1, mb=0, nb=0, n_slots=2, dtype=1, fused=1)
+        kw.update(bad)
+        o = _lib.RsvdOpts(**kw)
+        assert lib.rsvd_plan(1000, 500, 10, 5, 1, 1, 0, C.byref(o), C.byref(h)) == 8
+        assert h.value is None
+
+
+def test_opts_layout_matches_the_header():
+    """The binding's rsvd_opts mirrors the header's field order and size."""
+    from paper_1907_06470_gb300 import _lib
+    assert [f for f, _ in _lib.RsvdOpts._fields_] == ["prec", "refine", "mb", "nb", "n_slots", "dtype", "kind",
+                                                      "auto_q", "auto_q_tol", "fused", "reserved"]
+    assert C.sizeof(_lib.RsvdOpts) == 56

@@ -135,6 +135,28 @@ def test_bf16_copy_of_a_gives_the_same_bits(g):
     assert torch.equal(S1, S2) and torch.equal(U1, U2) and torch.equal(V1, V2)
 
 
+@pytest.mark.parametrize("r", [48, 120])
+def test_split_copy_of_a_gives_the_same_bits(g, r):
+    """In-core BF16X3 plans keep BF16(A) and BF16(A - BF16(A)) from the first
+    forward pass and read the two parts in the later passes (three products,
+    no conversion): the operands the FP32 A splits into, so the same bits as
+    a plan without room for the copy."""
+    m, n, q, seed = 6007, 3004, 2, 11
+    k, p = r - 8, 8
+    A, _, _ = prescribed_dense(m, n, spectrum_harmonic_noisy(n, 1e-4, 5), 7, dtype=np.float32)
+    Ad = torch.as_tensor(A, device="cuda")
+    p1 = g.Plan(m, n, k, p, q, seed, prec="bf16x3")
+    U1, S1, V1 = p1.run(Ad)
+    assert p1.info()["bf16_copy"] == 1
+    ws = p1.info()["workspace_bytes"]
+    p1.close()
+    p2 = g.Plan(m, n, k, p, q, seed, mem_cap=ws + 4096, prec="bf16x3")
+    U2, S2, V2 = p2.run(Ad)
+    assert p2.info()["bf16_copy"] == 0
+    p2.close()
+    assert torch.equal(S1, S2) and torch.equal(U1, U2) and torch.equal(V1, V2)
+
+
 @pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
 @pytest.mark.parametrize("M,r", [(100000, 120), (5003, 36), (4096, 128)])
 def test_gram_of_a_panel_matches_the_general_path(g, prec, M, r):
