@@ -187,8 +187,17 @@ rsvd_status rsvd_plan_info(rsvd_plan_t plan, rsvd_plan_info_t* out);
  * A X run on the CSR of A and the products A^T X on the CSR of A^T, which is
  * built on the host (rsvd_csr_transpose, once per call) when A.t_rowptr is
  * NULL.  A host CSR (and a built transpose) is copied into device memory owned
- * by the plan; with a cap, those copies count against it (CAP_TOO_SMALL if
- * they do not fit: CSR matrices are not streamed).
+ * by the plan when the copies fit under the cap (or there is no cap);
+ * otherwise it is processed out of core (Section 3.5): the blocks of the CSR
+ * of A (forward products) and of the CSR of A^T (transposed products) are
+ * streamed from host memory through opts.n_slots device buffers, overlapped
+ * with the products, and the blocks that fit in the rest of the cap stay
+ * resident for the later passes.  Blocks: with opts.mb / opts.nb set, the
+ * block-cyclic grid mb x nb of A (nb x mb for A^T; narrower than the matrix:
+ * cut once per call into a pinned host store, see rsvd_csr_tile); by default
+ * full-width row ranges of at most 2^25 entries (fewer when the cap is
+ * tight), copied straight from the host arrays (pinned memory lets the
+ * copies overlap; a transpose the library builds is pinned).
  * A host A is copied to the device and processed in core when the plan has no
  * cap or the copy fits under it; otherwise it is processed out of core: its
  * block-cyclic tiles (edges opts.mb x opts.nb; by default full-width row
@@ -403,6 +412,21 @@ size_t rsvd_spmm_workspace(int64_t nnz, int32_t r);
  * column index outside [0, n), NULL array). */
 rsvd_status rsvd_csr_transpose(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
                                const float* val, int32_t* t_rowptr, int32_t* t_colidx, float* t_val);
+
+/* Block (I, J) of the block-cyclic map of Section 3.1 for a CSR matrix (host
+ * only, Section 3.3 sparse storage): the entries of the m x n CSR (rowptr
+ * m+1, colidx and val rowptr[m]) that lie in rows [row0, row1) and columns
+ * [col0, col1), as a CSR of row1 - row0 rows: t_rowptr (row1 - row0 + 1
+ * offsets from 0), t_colidx (column indices minus col0) and t_val, each row's
+ * entries in the order of the source row.  Caller-allocated arrays; with
+ * cap = 0 only t_rowptr (may be NULL) and *nnz are written (a counting call),
+ * otherwise t_colidx and t_val receive the entries and cap must be at least
+ * their count.  The out-of-core sparse passes stream such blocks.
+ * Errors: INVALID_ARG (ranges outside the matrix, decreasing rowptr, cap
+ * below the count, NULL arrays with cap > 0). */
+rsvd_status rsvd_csr_tile(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx, const float* val,
+                          int64_t row0, int64_t row1, int64_t col0, int64_t col1, int32_t* t_rowptr,
+                          int32_t* t_colidx, float* t_val, int64_t cap, int64_t* nnz);
 
 /* Host (CPU) conversion of a sparse m x n matrix in coordinate (COO) format
  * (Section 3.3: structure of arrays, row and column indices of 32 or 64 bits)

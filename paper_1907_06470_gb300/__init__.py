@@ -376,6 +376,29 @@ def csr_transpose(A):
     return torch.sparse_csr_tensor(trp, tci, tv, size=(n, m))
 
 
+def csr_tile(A, row0, row1, col0, col1):
+    """Entries of a host torch sparse CSR tensor A (float32) inside rows
+    [row0, row1) x columns [col0, col1), as a host sparse CSR tensor of shape
+    (row1 - row0, col1 - col0) with local indices (the block of Section 3.1),
+    cut by the library's host tile builder."""
+    torch = _torch()
+    if A.is_cuda:
+        raise ValueError("csr_tile takes a host tensor")
+    rp, ci, v = _csr_arrays(A)
+    m, n = A.shape
+    lib = load()
+    cnt = C.c_int64()
+    args = (m, n, C.c_void_p(rp.data_ptr()), C.c_void_p(ci.data_ptr()), C.c_void_p(v.data_ptr()),
+            row0, row1, col0, col1)
+    _check(lib.rsvd_csr_tile(*args, None, None, None, 0, C.byref(cnt)))
+    trp = torch.empty(row1 - row0 + 1, dtype=torch.int32)
+    tci = torch.empty(max(cnt.value, 1), dtype=torch.int32)
+    tv = torch.empty(max(cnt.value, 1), dtype=torch.float32)
+    _check(lib.rsvd_csr_tile(*args, C.c_void_p(trp.data_ptr()), C.c_void_p(tci.data_ptr()),
+                             C.c_void_p(tv.data_ptr()), cnt.value, C.byref(cnt)))
+    return torch.sparse_csr_tensor(trp, tci[:cnt.value], tv[:cnt.value], size=(row1 - row0, col1 - col0))
+
+
 def coo_to_csr(A, transpose=False):
     """Host CSR (torch sparse CSR tensor) of a torch sparse COO matrix A with
     float32 values, or of A^T with transpose=True, by the library's stable

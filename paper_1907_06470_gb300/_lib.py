@@ -81,6 +81,8 @@ SIGNATURES = {
     "rsvd_small_svd": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_size, c_vp]),
     "rsvd_small_svd_noalloc": (c_i32, [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "rsvd_csr_transpose": (c_i32, [c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "rsvd_csr_tile": (c_i32, [c_i64, c_i64, c_vp, c_vp, c_vp, c_i64, c_i64, c_i64, c_i64, c_vp, c_vp, c_vp, c_i64,
+                              C.POINTER(c_i64)]),
     "rsvd_coo_to_csr": (c_i32, [c_i64, c_i64, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "rsvd_spmm_workspace": (c_size, [c_i64, c_i32]),
     "rsvd_plan_set_checkpoint": (c_i32, [c_vp, C.c_char_p, c_i32]),

@@ -53,6 +53,21 @@ rsvd_status read_device_status(const int* d_status, cudaStream_t stream) {
   int h = 0;
   RSVD_CUDA(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
   RSVD_CUDA(cudaStreamSynchronize(stream));
+  if (h == DEV_TIMEOUT) {
+    // the tensor-core pipeline records where its first expired wait was (the
+    // words after the status of the workspaces it writes to)
+    int w[2] = {0, 0};
+    if (cudaMemcpy(w, d_status + 1, sizeof(w), cudaMemcpyDeviceToHost) == cudaSuccess && w[0]) {
+      static const char* roles[] = {"?", "A loads (operand slot free)", "A loads (staging slot free)",
+                                    "panel loads (operand slot free)", "MMA (accumulator free)",
+                                    "MMA (A operand full)", "MMA (panel full)", "converter", "epilogue"};
+      const int role = (w[0] >> 24) & 15;
+      return fail(RSVD_ERR_TIMEOUT, std::string("a device-side wait exceeded its spin limit: ") +
+                                        roles[role < 9 ? role : 0] + ", ring slot " +
+                                        std::to_string((w[0] >> 16) & 255) + ", K step " +
+                                        std::to_string(w[0] & 0xffff) + ", unit " + std::to_string(w[1]));
+    }
+  }
   return status_from_device(h);
 }
 
@@ -229,6 +244,12 @@ struct rsvd_plan_s {
   int64_t mb_req = 0, nb_req = 0;  // tile edges asked for in the options (0: none)
   StreamState* ss = nullptr;       // out-of-core state (created on the first streamed run)
   bool streaming = false;          // the current run streams A from the host
+  CsrStream* cs = nullptr;         // out-of-core state of a host CSR A
+  bool csr_streaming = false;      // the current run streams CSR tiles from the host
+  int32_t* h_tpinned = nullptr;    // pinned host CSR of A^T built for streaming (n + 1 + nnz indices)
+  float* h_tval_pinned = nullptr;
+  size_t h_tpinned_nnz = 0;
+  int64_t h_tpinned_n = -1;
   int kind = RSVD_DENSE;           // rsvd_kind the plan runs on
   bool tc_orth_all = false;        // range-finder Grams / panel products on the tensor cores
   bool tc_orth_inner = false;      // the same except for the final Q
@@ -429,6 +450,8 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
       }
     }
     if constexpr (std::is_same<T, float>::value) {
+      if (A.kind == RSVD_CSR && P->csr_streaming)  // Sections 3.5, 3.7: CSR tiles streamed from the host
+        return csr_apass_streamed(P->cs, trans, r, Xin, ldr, Yout, ldr, st);
       if (A.kind == RSVD_CSR)  // Section 3.3: sparse x dense; A^T through the CSR of A^T
         return trans ? spmm_csr(n, r, A.t_rowptr, A.t_colidx, A.t_val, A.nnz, Xin, ldr, Yout, ldr, false,
                                 P->spmm_ws, P->spmm_ws_bytes, st)
@@ -479,7 +502,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   };
   {
     Span total(pf, RSVD_STAGE_TOTAL, st);
-    RSVD_CUDA(cudaMemsetAsync(P->status, 0, sizeof(int), st));
+    RSVD_CUDA(cudaMemsetAsync(P->status, 0, 4 * sizeof(int), st));
     if (first_step == 0) {  // step 1: Gaussian test matrix (n x r); X may hold a resumed Z otherwise
       Span sp(pf, RSVD_STAGE_GAUSSIAN, st);
       const bool bf16_panel = prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3 || prec == RSVD_PREC_FP8;
@@ -610,6 +633,14 @@ rsvd_status prepare_csr(rsvd_plan_s* P, const rsvd_matrix& A, rsvd_matrix* out, 
     return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: t_rowptr set without t_colidx/t_val");
   *out = A;
   out->location = RSVD_ON_DEVICE;
+  // device bytes needed: A's arrays when on the host, the transpose when on the host or built here
+  const size_t a_bytes = host ? (size_t)(m + 1) * 4 + (size_t)nnz * 8 : 0;
+  const size_t t_bytes = (host || !have_t) ? (size_t)(n + 1) * 4 + (size_t)nnz * 8 : 0;
+  const size_t sws = spmm_ws_bytes(nnz, P->r);
+  const size_t need = a_bytes + t_bytes + sws + 1024;
+  // Section 3.5: a host CSR whose copies do not fit under the cap is processed
+  // out of core, its tiles (and those of its transpose) streamed per pass
+  const bool stream_it = host && P->mem_cap && P->ws_bytes + need > P->mem_cap;
   // host views of the transpose's source, and of the transpose
   const int32_t *hrp = nullptr, *hci = nullptr;
   const float* hv = nullptr;
@@ -630,17 +661,48 @@ rsvd_status prepare_csr(rsvd_plan_s* P, const rsvd_matrix& A, rsvd_matrix* out, 
       hrp = tmp_idx.data(); hci = tmp_idx.data() + m + 1; hv = tmp_val.data();
     }
     if (hrp[m] != nnz) return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: rowptr[m] != nnz");
-    P->h_idx.resize((size_t)(n + 1) + (size_t)nnz);
-    P->h_val.resize((size_t)nnz);
-    RSVD_TRY(csr_transpose_host(m, n, hrp, hci, hv, P->h_idx.data(), P->h_idx.data() + n + 1, P->h_val.data()));
+    int32_t* ti;
+    float* tv;
+    if (stream_it) {  // pinned, for copies that overlap the products
+      if (P->h_tpinned_nnz < (size_t)nnz || P->h_tpinned_n != n) {
+        if (P->h_tpinned) cudaFreeHost(P->h_tpinned);
+        if (P->h_tval_pinned) cudaFreeHost(P->h_tval_pinned);
+        P->h_tpinned = nullptr;
+        P->h_tval_pinned = nullptr;
+        P->h_tpinned_nnz = 0;
+        RSVD_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&P->h_tpinned), ((size_t)n + 1 + (size_t)nnz) * 4,
+                                cudaHostAllocDefault));
+        RSVD_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&P->h_tval_pinned), (size_t)nnz * 4 + 4,
+                                cudaHostAllocDefault));
+        P->h_tpinned_nnz = (size_t)nnz;
+        P->h_tpinned_n = n;
+      }
+      ti = P->h_tpinned;
+      tv = P->h_tval_pinned;
+    } else {
+      P->h_idx.resize((size_t)(n + 1) + (size_t)nnz);
+      P->h_val.resize((size_t)nnz);
+      ti = P->h_idx.data();
+      tv = P->h_val.data();
+    }
+    RSVD_TRY(csr_transpose_host(m, n, hrp, hci, hv, ti, ti + n + 1, tv));
   } else if (host && A.rowptr[m] != nnz) {
     return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: rowptr[m] != nnz");
   }
-  // device bytes needed: A's arrays when on the host, the transpose when on the host or built here
-  const size_t a_bytes = host ? (size_t)(m + 1) * 4 + (size_t)nnz * 8 : 0;
-  const size_t t_bytes = (host || !have_t) ? (size_t)(n + 1) * 4 + (size_t)nnz * 8 : 0;
-  const size_t sws = spmm_ws_bytes(nnz, P->r);
-  const size_t need = a_bytes + t_bytes + sws + 1024;
+  if (stream_it) {
+    if (P->ws_bytes >= P->mem_cap) return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: no room left for streaming");
+    rsvd_matrix H = A;
+    if (!have_t) {  // the transpose built above, in pinned host memory
+      H.t_rowptr = P->h_tpinned;
+      H.t_colidx = P->h_tpinned + n + 1;
+      H.t_val = P->h_tval_pinned;
+    }
+    RSVD_TRY(csr_stream_prepare(&P->cs, H, P->mb_req, P->nb_req, P->n_slots, P->mem_cap - P->ws_bytes, P->r));
+    csr_stream_begin_run(P->cs);
+    P->csr_streaming = true;
+    *out = H;
+    return RSVD_OK;
+  }
   {
     if (P->mem_cap && P->ws_bytes + need > P->mem_cap)
       return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: the CSR copies and SpMM workspace do not fit under mem_cap");
@@ -881,7 +943,7 @@ rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_
     const size_t tws = tc_apass_ws_bytes(A->m, A->n, r, trans, RSVD_PREC_BF16, mb, nb);
     void* tw = c.take<char>(tws);
     cudaStream_t st = as_stream(stream);
-    RSVD_CUDA(cudaMemsetAsync(st_word, 0, sizeof(int), st));
+    RSVD_CUDA(cudaMemsetAsync(st_word, 0, 4 * sizeof(int), st));
     RSVD_TRY(fp8_quantize(static_cast<const float*>(A->data), A->m, A->n, A->ld, f.qm, f.qn,
                           const_cast<uint8_t*>(f.codes), f.ldc, const_cast<float*>(f.scales), amax, st));
     RSVD_TRY(tc_apass_from_fp8(f, trans, r, static_cast<const float*>(X), ldx, static_cast<float*>(Y), ldy, tw, tws,
@@ -895,7 +957,7 @@ rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_
     if (ws_bytes < need + 512) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: workspace too small");
     int* st_word = reinterpret_cast<int*>(static_cast<char*>(ws) + ((need + 255) & ~size_t(255)));
     cudaStream_t st = as_stream(stream);
-    RSVD_CUDA(cudaMemsetAsync(st_word, 0, sizeof(int), st));
+    RSVD_CUDA(cudaMemsetAsync(st_word, 0, 4 * sizeof(int), st));
     RSVD_TRY(apass_dense(*A, trans, prec, r, X, ldx, Y, ldy, mb, nb, ws, need, st_word, st));
     return read_device_status(st_word, st);
   }
@@ -913,7 +975,7 @@ rsvd_status rsvd_orth(int32_t dtype, int64_t M, int32_t r, const void* Y, int64_
   OrthWs w = orth_ws_carve(c, M, r, dtype);
   if (c.overflow) return fail(RSVD_ERR_INVALID_ARG, "rsvd_orth: workspace too small");
   cudaStream_t st = as_stream(stream);
-  RSVD_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+  RSVD_CUDA(cudaMemsetAsync(w.status, 0, 4 * sizeof(int), st));
   if (dtype == RSVD_F64) {
     RSVD_TRY(orth_panel<double>(M, r, static_cast<const double*>(Y), ldy, static_cast<double*>(Q), ldq, R, w, st));
   } else {
@@ -1001,6 +1063,7 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
     rsvd_matrix Ad;
     P->prof.begin();
     P->streaming = false;
+    P->csr_streaming = false;
     RSVD_TRY(prepare_csr(P, *A, &Ad, st));
     return run_typed<float>(P, Ad, static_cast<float*>(U), static_cast<float*>(S), static_cast<float*>(V), st);
   }
@@ -1008,6 +1071,7 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
   rsvd_matrix Ad = *A;
   P->prof.begin();
   P->streaming = false;
+  P->csr_streaming = false;
   if (A->location == RSVD_ON_HOST) {
     // Automatic in-core / out-of-core switch (Section 3.5): a host matrix that
     // fits under the cap (or any host matrix when there is no cap) is copied to
@@ -1052,6 +1116,12 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
   if (P->dtype == RSVD_F64)
     return run_typed<double>(P, Ad, static_cast<double*>(U), static_cast<double*>(S), static_cast<double*>(V), st);
   return run_typed<float>(P, Ad, static_cast<float*>(U), static_cast<float*>(S), static_cast<float*>(V), st);
+}
+
+rsvd_status rsvd_csr_tile(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx, const float* val,
+                          int64_t row0, int64_t row1, int64_t col0, int64_t col1, int32_t* t_rowptr,
+                          int32_t* t_colidx, float* t_val, int64_t cap, int64_t* nnz) {
+  return csr_tile_host(m, n, rowptr, colidx, val, row0, row1, col0, col1, t_rowptr, t_colidx, t_val, cap, nnz);
 }
 
 rsvd_status rsvd_csr_transpose(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx,
@@ -1112,14 +1182,18 @@ void rsvd_destroy(rsvd_plan_t P) {
   if (P->Adev) cudaFree(P->Adev);
   if (P->a16) cudaFree(P->a16);
   if (P->csr_dev) cudaFree(P->csr_dev);
+  if (P->h_tpinned) cudaFreeHost(P->h_tpinned);
+  if (P->h_tval_pinned) cudaFreeHost(P->h_tval_pinned);
   stream_state_free(P->ss);
+  csr_stream_free(P->cs);
   delete P;
 }
 
 rsvd_status rsvd_plan_stream_stats(rsvd_plan_t P, uint64_t* h2d_bytes, int64_t* tiles_streamed_per_pass,
                                    int64_t* tiles_resident) {
   if (!P) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_stream_stats: NULL plan");
-  stream_stats(P->streaming ? P->ss : nullptr, h2d_bytes, tiles_streamed_per_pass, tiles_resident);
+  if (P->csr_streaming) csr_stream_stats(P->cs, h2d_bytes, tiles_streamed_per_pass, tiles_resident);
+  else stream_stats(P->streaming ? P->ss : nullptr, h2d_bytes, tiles_streamed_per_pass, tiles_resident);
   return RSVD_OK;
 }
 

@@ -123,13 +123,24 @@ struct Layout {
   }
   __host__ __device__ static size_t bar_off(int NP, int sop, int S32) { return a32_off(NP, sop, S32); }
   // barriers: full32, empty32 (kMaxS32 each), fullA, fullB, emptyOp (kMaxSop
-  // each), accFull, accEmpty (2 each), then the TMEM address word
+  // each), accFull, accEmpty (2 each), drain, then the TMEM address word
   __host__ __device__ static size_t total(int NP, int sop, int S32) {
-    return bar_off(NP, sop, S32) + (size_t)(2 * kMaxS32 + 3 * kMaxSop + 4) * 8 + 16 + 1024;
+    return bar_off(NP, sop, S32) + (size_t)(2 * kMaxS32 + 3 * kMaxSop + 5) * 8 + 16 + 1024;
   }
 };
 
-__device__ __forceinline__ void flag_timeout(int* status) { dev_set_status(status, DEV_TIMEOUT); }
+// Roles whose waits can expire, recorded with the first expired wait.
+enum : int { kWaitAFree = 1, kWaitStageFree = 2, kWaitPanelFree = 3, kWaitAccFree = 4, kWaitAFull = 5,
+             kWaitPanelFull = 6, kWaitConvert = 7, kWaitAccFull = 8 };
+
+// Record DEV_TIMEOUT, and in the two words after the status where the first
+// expired wait was: role, ring slot and K step, then the unit.
+__device__ __forceinline__ void flag_timeout(int* status, int role, int slot, int64_t ks, int64_t unit) {
+  if (!status) return;
+  if (atomicCAS(status + 1, 0, (role << 24) | ((slot & 255) << 16) | (int)(ks & 0xffff)) == 0)
+    status[2] = (int)unit;
+  dev_set_status(status, DEV_TIMEOUT);
+}
 
 // Position in a ring of n slots (slot, phase parity), advanced once per item.
 struct RingPos {
@@ -171,7 +182,8 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   uint64_t* emptyOp = fullB + kMaxSop;
   uint64_t* accFull = emptyOp + kMaxSop;
   uint64_t* accEmpty = accFull + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accEmpty + 2);
+  uint64_t* drain = accEmpty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -186,6 +198,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       ptx::mbar_init(&emptyOp[i], 1);
     }
     for (int i = 0; i < 2; ++i) { ptx::mbar_init(&accFull[i], 1); ptx::mbar_init(&accEmpty[i], 4); }
+    ptx::mbar_init(drain, 1);
     ptx::fence_mbar_init();
     s_abort = 0;
   }
@@ -220,14 +233,19 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       const int nA = (SPLIT && a.a_lo) ? 2 : 1;
       const uint32_t a_bytes = (uint32_t)(A16_BYTES * nA);
       RingPos rop;
+      uint32_t issued = 0, parity = 0;  // per slot: loaded at least once, phase of the last load
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
         const int64_t z = u / a.mtiles, mt = u % a.mtiles;
         const int64_t k0 = z * a.ksteps_per_split;
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
         for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
           const int sop = rop.slot;
-          if (!ptx::mbar_wait(&emptyOp[sop], rop.phase ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
+          if (!ptx::mbar_wait(&emptyOp[sop], rop.phase ^ 1, vstatus, kWaitNs)) {
+            flag_timeout(a.status, kWaitAFree, sop, ks, u); s_abort = 1; break;
+          }
           ptx::mbar_arrive_expect_tx(&fullA[sop], a_bytes);
+          issued |= 1u << sop;
+          parity = (parity & ~(1u << sop)) | (rop.phase << sop);
           for (int part = 0; part < nA; ++part) {
             const CUtensorMap* map = part ? &mapAlo : &mapA;
             uint8_t* dst = smem + L::a16_off(sop, part);
@@ -240,35 +258,52 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           }
         }
       }
+      // every load issued has landed before the CTA may exit (immediate unless stopped early)
+      for (int i = 0; i < SOP; ++i)
+        if (issued >> i & 1) ptx::mbar_wait_drain(&fullA[i], parity >> i & 1, kWaitNs);
     } else if (lane == 0) {
       RingPos r32;
+      uint32_t issued = 0, parity = 0;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
         const int64_t z = u / a.mtiles, mt = u % a.mtiles;
         const int64_t k0 = z * a.ksteps_per_split;
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
         for (int64_t ks = k0; ks < k1; ++ks, r32.next(S32)) {
           const int s32 = r32.slot;
-          if (!ptx::mbar_wait(&empty32[s32], r32.phase ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
+          if (!ptx::mbar_wait(&empty32[s32], r32.phase ^ 1, vstatus, kWaitNs)) {
+            flag_timeout(a.status, kWaitStageFree, s32, ks, u); s_abort = 1; break;
+          }
           ptx::mbar_arrive_expect_tx(&full32[s32], L::STAGE_BYTES);
+          issued |= 1u << s32;
+          parity = (parity & ~(1u << s32)) | (r32.phase << s32);
           void* dstA = smem + L::a32_off(NP, SOP, s32);
           if (TRANS) ptx::tma_load_2d(dstA, &mapA, &full32[s32], (int32_t)(mt * BM), (int32_t)(ks * BK));
           else ptx::tma_load_2d(dstA, &mapA, &full32[s32], (int32_t)(ks * BK), (int32_t)(mt * BM));
         }
       }
+      for (int i = 0; i < S32; ++i)
+        if (issued >> i & 1) ptx::mbar_wait_drain(&full32[i], parity >> i & 1, kWaitNs);
     } else if (lane == 1 && !a.gram) {
       RingPos rop;
+      uint32_t issued = 0, parity = 0;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
         const int64_t z = u / a.mtiles;
         const int64_t k0 = z * a.ksteps_per_split;
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
         for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
           const int sop = rop.slot;
-          if (!ptx::mbar_wait(&emptyOp[sop], rop.phase ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
+          if (!ptx::mbar_wait(&emptyOp[sop], rop.phase ^ 1, vstatus, kWaitNs)) {
+            flag_timeout(a.status, kWaitPanelFree, sop, ks, u); s_abort = 1; break;
+          }
           ptx::mbar_arrive_expect_tx(&fullB[sop], b_bytes * L::PARTS);
+          issued |= 1u << sop;
+          parity = (parity & ~(1u << sop)) | (rop.phase << sop);
           ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 0), &mapB, &fullB[sop], (int32_t)(ks * BK), 0);
           if (SPLIT) ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 1), &mapBlo, &fullB[sop], (int32_t)(ks * BK), 0);
         }
       }
+      for (int i = 0; i < SOP; ++i)
+        if (issued >> i & 1) ptx::mbar_wait_drain(&fullB[i], parity >> i & 1, kWaitNs);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -282,7 +317,9 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
         const int acc = (int)(ua & 1);
         const uint32_t pha = (uint32_t)((ua >> 1) & 1);
-        if (!ptx::mbar_wait(&accEmpty[acc], pha ^ 1, vstatus, kWaitNs)) { flag_timeout(a.status); s_abort = 1; break; }
+        if (!ptx::mbar_wait(&accEmpty[acc], pha ^ 1, vstatus, kWaitNs)) {
+          flag_timeout(a.status, kWaitAccFree, acc, k0, u); s_abort = 1; break;
+        }
         ptx::tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * a.acc_stride);
         uint32_t accumulate = 0;
@@ -290,9 +327,11 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
           const int sop = rop.slot;
           const uint32_t phop = rop.phase;
-          if (!ptx::mbar_wait(&fullA[sop], phop, vstatus, kWaitNs) ||
-              (!a.gram && !ptx::mbar_wait(&fullB[sop], phop, vstatus, kWaitNs))) {
-            flag_timeout(a.status); s_abort = 1; ok = false; break;
+          if (!ptx::mbar_wait(&fullA[sop], phop, vstatus, kWaitNs)) {
+            flag_timeout(a.status, kWaitAFull, sop, ks, u); s_abort = 1; ok = false; break;
+          }
+          if (!a.gram && !ptx::mbar_wait(&fullB[sop], phop, vstatus, kWaitNs)) {
+            flag_timeout(a.status, kWaitPanelFull, sop, ks, u); s_abort = 1; ok = false; break;
           }
           ptx::tc_fence_after();
           // Gram mode: the K-major tile of A^T is also the panel tile (its first NP rows)
@@ -322,6 +361,9 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         if (!ok) break;
         ptx::mma_commit(&accFull[acc]);
       }
+      // every product issued has completed before TMEM is released
+      ptx::mma_commit(drain);
+      ptx::mbar_wait_drain(drain, 0, kWaitNs);
     }
   } else if (warp < 6 && !DIRECT) {
     // ---------------- converters ----------------
@@ -337,7 +379,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         const int sop = rop.slot;
         const bool w = ptx::mbar_wait(&full32[s32], r32.phase, vstatus, kWaitNs) &&
                        ptx::mbar_wait(&emptyOp[sop], rop.phase ^ 1, vstatus, kWaitNs);
-        if (!__all_sync(0xffffffffu, w)) { if (lane == 0) flag_timeout(a.status); ok = false; break; }
+        if (!__all_sync(0xffffffffu, w)) { if (lane == 0) flag_timeout(a.status, kWaitConvert, sop, ks, u); ok = false; break; }
         const float* src = reinterpret_cast<const float*>(smem + L::a32_off(NP, SOP, s32));
         uint8_t* hi = smem + L::a16_off(sop, 0);
         uint8_t* lo = smem + L::a16_off(sop, SPLIT ? 1 : 0);
@@ -448,8 +490,9 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       }
       if (!ok) break;
     }
-  } else {
+  } else if (warp >= 6) {
     // ---------------- epilogue ----------------
+    // (warps 6-9 only: with a 16-bit source the converter warps 2-5 stay idle)
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
     int64_t ua = 0;
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++ua) {
@@ -457,7 +500,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       const int acc = (int)(ua & 1);
       const uint32_t pha = (uint32_t)((ua >> 1) & 1);
       const bool w = ptx::mbar_wait(&accFull[acc], pha, vstatus, kWaitNs);
-      if (!__all_sync(0xffffffffu, w)) { if (lane == 0) flag_timeout(a.status); break; }
+      if (!__all_sync(0xffffffffu, w)) { if (lane == 0) flag_timeout(a.status, kWaitAccFull, acc, 0, u); break; }
       ptx::tc_fence_after();
       const int64_t row = mt * BM + q * 32 + lane;
       float* crow = a.C + z * a.c_split_stride + row * a.ldc;
@@ -676,7 +719,7 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   if (c.overflow) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: workspace too small");
   if (!status) {
     status = own_status;
-    RSVD_CUDA(cudaMemsetAsync(status, 0, sizeof(int), stream));
+    RSVD_CUDA(cudaMemsetAsync(status, 0, 4 * sizeof(int), stream));
   }
 
   // Gram C = A^T A of a matrix of at most 128 columns: the converters' K-major

@@ -173,6 +173,22 @@ rsvd_status sweep_streamed(StreamState* s, const rsvd_matrix& Ah, int prec, int 
 void stream_state_free(StreamState* s);
 void stream_stats(const StreamState* s, uint64_t* h2d, int64_t* per_pass, int64_t* cached);
 
+// csr_stream.cu -- out-of-core sparse A-passes over CSR tiles of a host matrix.
+// Entries of rows [row0, row1) x columns [col0, col1) of a host CSR as a local
+// CSR (offsets from 0, column indices minus col0); with cap == 0 only counts.
+rsvd_status csr_tile_host(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx, const float* val,
+                          int64_t row0, int64_t row1, int64_t col0, int64_t col1, int32_t* t_rowptr,
+                          int32_t* t_colidx, float* t_val, int64_t cap, int64_t* nnz_out);
+struct CsrStream;
+// A: host CSR with host t_rowptr/t_colidx/t_val (the CSR of A^T).
+rsvd_status csr_stream_prepare(CsrStream** ps, const rsvd_matrix& A, int64_t mb_req, int64_t nb_req, int slots,
+                               size_t budget, int r);
+void csr_stream_begin_run(CsrStream* s);
+rsvd_status csr_apass_streamed(CsrStream* s, int trans, int r, const float* X, int64_t ldx, float* Y, int64_t ldy,
+                               cudaStream_t st);
+void csr_stream_free(CsrStream* s);
+void csr_stream_stats(const CsrStream* s, uint64_t* h2d, int64_t* per_pass, int64_t* cached);
+
 // api.cu -- A-pass dispatch.
 size_t apass_ws_bytes(int64_t m, int64_t n, int r, int trans, int prec, int64_t mb, int64_t nb);
 rsvd_status apass_dense(const rsvd_matrix& A, int trans, int prec, int r, const void* X, int64_t ldx,

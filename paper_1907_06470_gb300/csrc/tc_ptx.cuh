@@ -66,6 +66,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const 
   return true;
 }
 
+// Bounded wait that ignores error flags: for draining work already issued
+// (copies, products) before a CTA that stopped early exits.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_timer_ns() - t0 > limit_ns) return false;
+  return true;
+}
+
 // ---- proxy fences -----------------------------------------------------------
 
 // Make this thread's generic-proxy shared-memory writes visible to the async

@@ -201,6 +201,54 @@ def test_csr_cap_too_small_for_the_copies(g, zipf):
     plan.close()
 
 
+def _csr_min_cap(g, m, n, k, p):
+    from paper_1907_06470_gb300 import _lib
+    import ctypes as C
+    o = _lib.RsvdOpts(prec=1, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
+    out = C.c_size_t()
+    assert g.load().rsvd_plan_min_cap(m, n, k, p, C.byref(o), C.byref(out)) == 0
+    return out.value
+
+
+def test_csr_streamed_full_width_blocks_match_in_core_bits(g, zipf):
+    """A host CSR over the cap is streamed in full-width row blocks (of A for
+    the forward products, of A^T for the transposed ones): every output row is
+    summed by the same kernel over the same entries as in core, so the result
+    is the same bits; and it meets the oracle at the FP32 bars."""
+    m, n, rp, ci, v = zipf
+    k, p, q, seed = 20, 10, 2, 2004
+    A_bytes = (m + 1) * 4 + len(v) * 8
+    cap = _csr_min_cap(g, m, n, k, p) + A_bytes // 2
+    Ah = _torch_csr(m, n, rp, ci, v, "cpu")
+    plan = g.Plan(m, n, k, p, q, seed, mem_cap=cap, kind="csr")
+    Us, Ss, Vs = plan.run(Ah)
+    st = plan.stream_stats()
+    assert st["tiles_streamed_per_pass"] > 0 and st["h2d_bytes"] > A_bytes
+    plan.close()
+    Ui, Si, Vi = g.rsvd(_torch_csr(m, n, rp, ci, v, "cuda"), k, p, q, seed)
+    assert torch.equal(Ss, Si) and torch.equal(Us, Ui) and torch.equal(Vs, Vi)
+    Uo, So, Vo = OR.rsvd(OL.CSR(m, n, rp, ci, v), k, p, q, seed, "f32")
+    assert sigma_rel_err(Ss.cpu().numpy(), So) <= 1e-5
+    assert cluster_safe_angles(Us.cpu().numpy().astype(np.float64), Uo, So, k) <= 1e-4
+
+
+@pytest.mark.parametrize("mb,nb", [(3000, 1500), (7001, 5000), (20000, 999)])
+def test_csr_streamed_block_cyclic_grid_matches_oracle(g, zipf, mb, nb):
+    """Streamed on the block-cyclic grid mb x nb (blocks cut on the host,
+    partial products of a row block added in block order), against the oracle."""
+    m, n, rp, ci, v = zipf
+    k, p, q, seed = 20, 10, 2, 2004
+    A_bytes = (m + 1) * 4 + len(v) * 8
+    cap = _csr_min_cap(g, m, n, k, p) + A_bytes // 2
+    plan = g.Plan(m, n, k, p, q, seed, mem_cap=cap, kind="csr", mb=mb, nb=nb)
+    U, S, V = (t.cpu().numpy().astype(np.float64) for t in plan.run(_torch_csr(m, n, rp, ci, v, "cpu")))
+    assert plan.stream_stats()["tiles_streamed_per_pass"] > 0
+    plan.close()
+    Uo, So, Vo = OR.rsvd(OL.CSR(m, n, rp, ci, v), k, p, q, seed, "f32")
+    assert sigma_rel_err(S, So) <= 1e-5
+    assert cluster_safe_angles(U, Uo, So, k) <= 1e-4 and cluster_safe_angles(V, Vo, So, k) <= 1e-4
+
+
 @pytest.mark.parametrize("split", [True, False])
 def test_csr_long_rows_at_segment_boundaries(g, split):
     """Rows of 0, 1, 4095, 4096, 4097, 8192, 8193 and 30000 entries: the

@@ -205,6 +205,23 @@ def test_16bit_source_exact_on_small_integers(g, m, n, r, trans, prec, fmt):
 
 
 @pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_16bit_source_many_units_per_cta(g, trans, prec):
+    """Enough 128-row output tiles that every CTA of the persistent grid takes
+    three or more of them (the accumulator double buffer cycles), exact on
+    small integers."""
+    rng = np.random.default_rng(11 + trans)
+    m, n = (60000, 1024) if not trans else (1024, 60000)
+    A = rng.integers(-4, 5, size=(m, n)).astype(np.float32)
+    K = m if trans else n
+    X = rng.integers(-4, 5, size=(K, 64)).astype(np.float32)
+    A16 = torch.as_tensor(A, device="cuda").to(torch.bfloat16)
+    got = g.apass(A16, torch.as_tensor(X, device="cuda"), trans, prec).cpu().numpy()
+    ref = (A.T if trans else A).astype(np.float64) @ X.astype(np.float64)
+    assert np.array_equal(got, ref.astype(np.float32))
+
+
+@pytest.mark.parametrize("trans", [False, True])
 @pytest.mark.parametrize("fmt", ["bf16", "f16"])
 def test_16bit_source_error_model(g, trans, fmt):
     """prec BF16 on a 16-bit A: the exact product of A and the panel rounded to

@@ -116,3 +116,28 @@ def test_coo_of_the_swapped_indices_is_the_csr_transpose():
     trp, tci, tv = T.coo_to_csr(11, 19, ci, rows, v)
     erp, eci, ev = T.csr_transpose(19, 11, rp, ci, v)
     assert np.array_equal(trp, erp) and np.array_equal(tci, eci) and np.array_equal(tv, ev)
+
+
+@pytest.mark.parametrize("m,n,nnz,seed", [(50, 40, 300, 1), (7, 300, 900, 2), (200, 3, 150, 3)])
+def test_library_csr_tile_is_bit_exact_with_oracle(m, n, nnz, seed):
+    """The library's host block cutter (the tiles the out-of-core sparse
+    passes stream) against the oracle's csr_tile on every block of a ragged
+    grid, including empty blocks and zero-width ranges."""
+    torch = pytest.importorskip("torch")
+    import paper_1907_06470_gb300 as g
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.integers(0, m, nnz))
+    cols = rng.integers(0, n, nnz)
+    vals = rng.standard_normal(nnz).astype(np.float32)
+    rp = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(rp, rows + 1, 1)
+    rp = np.cumsum(rp)
+    A = torch.sparse_csr_tensor(torch.as_tensor(rp, dtype=torch.int32), torch.as_tensor(cols, dtype=torch.int32),
+                                torch.as_tensor(vals), size=(m, n))
+    for (r0, r1, c0, c1) in [(0, m, 0, n), (3, m - 2, 1, n - 1), (m // 2, m // 2, 0, n), (1, 4, n - 1, n),
+                             (0, m, n // 3, n // 3)]:
+        lrp, lci, lv = T.csr_tile(rp, cols, vals, r0, r1, c0, c1)
+        t = g.csr_tile(A, r0, r1, c0, c1)
+        assert np.array_equal(t.crow_indices().numpy(), lrp)
+        assert np.array_equal(t.col_indices().numpy(), lci)
+        assert np.array_equal(t.values().numpy(), lv)
