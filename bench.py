@@ -385,6 +385,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         steps_e2e = max(1, min(args.steps, 10))
         host_split = []
+        # no collector pauses inside the timed host loop
+        import gc
+        gc.collect()
+        gc.disable()
         t0 = time.perf_counter()
         for _ in range(steps_e2e):
             ta = time.perf_counter()
@@ -396,6 +400,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             host_split.append([round((tb - ta) * 1e3, 2), round((time.perf_counter() - tb) * 1e3, 2)])
         t_e2e = (time.perf_counter() - t0) / steps_e2e
+        gc.enable()
         plan_h.set_profiling(True)  # one more call with stage events, outside the timed loop
         plan_h.run(A_host, Ud, Sd, Vd)
         torch.cuda.synchronize()
@@ -403,6 +408,7 @@ def run_ours(args):
                "d2h_bytes_per_step": (m * k + k + n * k) * 4, "ms_per_step": t_e2e * 1e3,
                "stages_ms_untimed_call": {kk: round(vv, 3) for kk, vv in plan_h.stage_ms().items()
                                           if kk in ("h2d", "total")},
+               "median_step_ms": statistics.median(a + b for a, b in host_split),
                "host_ms_run_and_readback": host_split}
         plan_h.close()
         del A_host
@@ -613,7 +619,7 @@ def run_out_of_core(args):
     torch.cuda.empty_cache()
     cap = int(args.ooc_cap_gb * (1 << 30))
     tile = args.ooc_tile
-    plan = g.Plan(m, n, w.k, w.p, w.q, w.seed, mem_cap=cap, prec=args.prec, mb=tile, nb=tile)
+    plan = g.Plan(m, n, w.k, w.p, w.q, w.seed, mem_cap=cap, prec=args.prec, mb=tile, nb=tile, fused=args.fused)
     plan.set_profiling(True)
     U, S, V = plan.run(A_host)
     torch.cuda.synchronize()
@@ -625,11 +631,13 @@ def run_out_of_core(args):
         times.append(time.perf_counter() - t0)
         stages.append(plan.stage_ms())
     st = plan.stream_stats()
-    apass_ms = stages[-1]["apass_fwd"] + stages[-1]["apass_trans"]
+    apass_ms = stages[-1]["apass_fwd"] + stages[-1]["apass_trans"] + stages[-1].get("sweep", 0.0)
     link = st["h2d_bytes"] / (apass_ms / 1e3) / 1e9
     print(json.dumps({
         "mode": "out_of_core", "workload": w.name, "m": m, "n": n, "k": w.k, "p": w.p, "q": w.q,
         "tile": tile if tile else "full-width row panels (planner default)", "prec": args.prec,
+        "fused_sweeps": bool(args.fused),
+        "passes_over_A": (w.q + 2) if args.fused else (2 * w.q + 2),
         "host_bytes": m * n * 4, "device_cap_bytes": cap,
         "ms_per_rsvd": 1e3 * sum(times) / len(times), "stream": st,
         "h2d_bytes_per_rsvd": st["h2d_bytes"], "apass_ms_per_rsvd": apass_ms,
@@ -767,6 +775,7 @@ def main():
     ap.add_argument("--ooc-rows", type=int, default=150000)
     ap.add_argument("--ooc-cap-gb", type=float, default=16.0)
     ap.add_argument("--ooc-tile", type=int, default=0, help="square tile edge (0: planner default)")
+    ap.add_argument("--fused", action="store_true", help="out-of-core mode: fused power sweeps (q + 2 passes)")
     ap.add_argument("--m", type=int, default=25000)
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--r", type=int, default=120)

@@ -1,6 +1,7 @@
 // C ABI: planner (Section 3.4 / 3.5), the randomized SVD driver (Section 2.1
 // steps 1-7 with the power scheme of Section 2.2), the exact small SVD, and
 // the per-step entry points.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -237,6 +238,14 @@ struct rsvd_plan_s {
   size_t bwd_ws_bytes = 0;
   int* status = nullptr;
   void* Adev = nullptr;     // device copy of a host-resident A
+  // In-core copy of a host A in row chunks on a side stream (Section 3.7: I/O
+  // overlapped with compute): the first forward pass takes each chunk as it
+  // lands; everything else waits for the whole copy.
+  cudaStream_t h2d_stream = nullptr;
+  std::vector<cudaEvent_t> h2d_ev;  // one per chunk, then one for "all landed"
+  int64_t h2d_chunk_rows = 0;
+  int h2d_chunks = 0;
+  bool h2d_pending = false;          // the current run's copy is in flight
   uint16_t* a16 = nullptr;  // BF16 plans in core: BF16 copy of A, written by the first forward pass
   size_t a16_bytes = 0;
   int64_t a16_ld = 0;
@@ -423,9 +432,70 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     }
   }
   P->a16_ready = false;
+  // A copied from the host in chunks: the first forward pass may take the
+  // chunks as they land; any other use of A waits for the whole copy
+  auto await_copy = [&]() -> rsvd_status {
+    if (P->h2d_pending) {
+      RSVD_CUDA(cudaStreamWaitEvent(st, P->h2d_ev[P->h2d_chunks], 0));
+      P->h2d_pending = false;
+    }
+    return RSVD_OK;
+  };
+  // the first forward pass over A chunk by chunk (rows [r0, r0 + rows)), each
+  // chunk after its copy: the same products per row as one pass over A
+  auto chunked_forward = [&](int pr, const T* Xin, T* Yout, bool& done) -> rsvd_status {
+    done = false;
+    if (!P->h2d_pending || P->streaming || A.kind != RSVD_DENSE || pr == RSVD_PREC_FP8) return RSVD_OK;
+    const size_t esz = elem_size(A.dtype);
+    uint16_t* lo = (prec == RSVD_PREC_BF16X3 && P->a16) ? P->a16 + (size_t)m * P->a16_ld : nullptr;
+    const bool write_copy = use16 && pr == prec && !P->a16_ready;
+    // every chunk takes the K split of the whole pass: the same sums per row
+    const int64_t kps = tc_ksteps_per_split(m, n, r, 0, pr);
+    for (int c = 0; c < P->h2d_chunks; ++c) {
+      const int64_t r0 = (int64_t)c * P->h2d_chunk_rows, rows = std::min<int64_t>(P->h2d_chunk_rows, m - r0);
+      RSVD_CUDA(cudaStreamWaitEvent(st, P->h2d_ev[c], 0));
+      rsvd_matrix Ac = A;
+      Ac.m = rows;
+      Ac.data = static_cast<const char*>(A.data) + (size_t)r0 * A.ld * esz;
+      T* Yc = Yout + (size_t)r0 * ldr;
+      if constexpr (std::is_same<T, float>::value) {
+        if (write_copy) {
+          RSVD_TRY(tc_apass_from_f32(Ac, 0, pr, r, Xin, ldr, Yc, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes,
+                                     P->status, st, false, P->a16 + (size_t)r0 * P->a16_ld, P->a16_ld,
+                                     lo ? lo + (size_t)r0 * P->a16_ld : nullptr, kps));
+          continue;
+        }
+        if (a16_in) {
+          Bf16Source b;
+          b.data = static_cast<const uint16_t*>(Ac.data); b.m = rows; b.n = n; b.ld = A.ld;
+          b.f16 = A.dtype == RSVD_F16 ? 1 : 0;
+          RSVD_TRY(tc_apass_from_16(b, 0, pr, r, Xin, ldr, Yc, ldr, P->apass_ws, P->apass_ws_bytes, P->status, st,
+                                    false, kps));
+          continue;
+        }
+        if (pr == RSVD_PREC_BF16 || pr == RSVD_PREC_BF16X3) {
+          RSVD_TRY(tc_apass_from_f32(Ac, 0, pr, r, Xin, ldr, Yc, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes,
+                                     P->status, st, false, nullptr, 0, nullptr, kps));
+          continue;
+        }
+      }
+      RSVD_TRY(apass_dense(Ac, 0, pr, r, Xin, ldr, Yc, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes,
+                           P->status, st));
+    }
+    if (write_copy) P->a16_ready = true;
+    P->h2d_pending = false;  // every chunk has been waited for
+    done = true;
+    return RSVD_OK;
+  };
   auto apass = [&](int trans, int pr, const T* Xin, T* Yout) -> rsvd_status {
     Span sp(pf, trans ? RSVD_STAGE_APASS_TRANS : RSVD_STAGE_APASS_FWD, st);
     ++pf.apass_calls;
+    if (!trans && P->h2d_pending) {
+      bool done = false;
+      RSVD_TRY(chunked_forward(pr, Xin, Yout, done));
+      if (done) return RSVD_OK;
+    }
+    RSVD_TRY(await_copy());
     if constexpr (std::is_same<T, float>::value) {
       if (a16_in) {
         Bf16Source b;
@@ -481,6 +551,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   if (ckpt_on) {
     hdr.m = m; hdr.n = n; hdr.k = k; hdr.p = P->p; hdr.q = P->q; hdr.r = r; hdr.ldr = ldr;
     hdr.prec = prec; hdr.dtype = P->dtype; hdr.kind = A.kind; hdr.seed = P->seed;
+    RSVD_TRY(await_copy());
     RSVD_TRY(matrix_fingerprint(A, &hdr.fingerprint, st));
     const int done = ckpt_try_load(P->ckpt_path, hdr, Q, X, st);
     if (done >= 0) {
@@ -511,6 +582,7 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     if constexpr (std::is_same<T, float>::value) {
       if (prec == RSVD_PREC_FP8) {  // E4M3 codes of A with tile scales, once per run
         Span sp(pf, RSVD_STAGE_QUANTIZE, st);
+        RSVD_TRY(await_copy());
         RSVD_TRY(fp8_quantize(static_cast<const float*>(A.data), m, n, A.ld, P->f8.qm, P->f8.qn,
                               const_cast<uint8_t*>(P->f8.codes), P->f8.ldc, const_cast<float*>(P->f8.scales),
                               P->f8_amax, st));
@@ -639,8 +711,12 @@ rsvd_status prepare_csr(rsvd_plan_s* P, const rsvd_matrix& A, rsvd_matrix* out, 
   const size_t sws = spmm_ws_bytes(nnz, P->r);
   const size_t need = a_bytes + t_bytes + sws + 1024;
   // Section 3.5: a host CSR whose copies do not fit under the cap is processed
-  // out of core, its tiles (and those of its transpose) streamed per pass
-  const bool stream_it = host && P->mem_cap && P->ws_bytes + need > P->mem_cap;
+  // out of core, its tiles (and those of its transpose) streamed per pass; so
+  // is a host CSR for which the options set tile edges (Section 3.1: the
+  // blocks of the block-cyclic map, resident after the first pass when they
+  // all fit)
+  const bool stream_it =
+      host && ((P->mem_cap && P->ws_bytes + need > P->mem_cap) || P->mb_req > 0 || P->nb_req > 0);
   // host views of the transpose's source, and of the transpose
   const int32_t *hrp = nullptr, *hci = nullptr;
   const float* hv = nullptr;
@@ -690,14 +766,22 @@ rsvd_status prepare_csr(rsvd_plan_s* P, const rsvd_matrix& A, rsvd_matrix* out, 
     return fail(RSVD_ERR_INVALID_ARG, "rsvd_run: rowptr[m] != nnz");
   }
   if (stream_it) {
-    if (P->ws_bytes >= P->mem_cap) return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: no room left for streaming");
+    size_t budget = 0;
+    if (P->mem_cap) {
+      if (P->ws_bytes >= P->mem_cap) return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: no room left for streaming");
+      budget = P->mem_cap - P->ws_bytes;
+    } else {  // no cap: the device memory free now, less a margin for the caller
+      size_t free_b = 0, total_b = 0;
+      RSVD_CUDA(cudaMemGetInfo(&free_b, &total_b));
+      budget = free_b > ((size_t)1 << 30) ? free_b - ((size_t)1 << 30) : free_b / 2;
+    }
     rsvd_matrix H = A;
     if (!have_t) {  // the transpose built above, in pinned host memory
       H.t_rowptr = P->h_tpinned;
       H.t_colidx = P->h_tpinned + n + 1;
       H.t_val = P->h_tval_pinned;
     }
-    RSVD_TRY(csr_stream_prepare(&P->cs, H, P->mb_req, P->nb_req, P->n_slots, P->mem_cap - P->ws_bytes, P->r));
+    RSVD_TRY(csr_stream_prepare(&P->cs, H, P->mb_req, P->nb_req, P->n_slots, budget, P->r));
     csr_stream_begin_run(P->cs);
     P->csr_streaming = true;
     *out = H;
@@ -1106,16 +1190,48 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
       P->a_copy_bytes = bytes;
     }
     const size_t row = (size_t)A->n * elem_size(A->dtype);
-    Span sp(P->prof, RSVD_STAGE_H2D, st);
-    RSVD_CUDA(cudaMemcpy2DAsync(P->Adev, (size_t)ldd * elem_size(A->dtype), A->data,
-                                (size_t)A->ld * elem_size(A->dtype), row, A->m, cudaMemcpyHostToDevice, st));
+    const size_t dpitch = (size_t)ldd * elem_size(A->dtype), spitch = (size_t)A->ld * elem_size(A->dtype);
+    // row chunks of about 256 MB (whole 128-row tiles), copied on a side stream
+    int64_t crow = (int64_t)(((size_t)256 << 20) / std::max<size_t>(dpitch, 1));
+    crow = std::max<int64_t>(128, crow / 128 * 128);
+    const int nch = (int)cdiv(A->m, crow);
+    if (!P->h2d_stream) RSVD_CUDA(cudaStreamCreateWithFlags(&P->h2d_stream, cudaStreamNonBlocking));
+    while ((int)P->h2d_ev.size() < nch + 2) {
+      cudaEvent_t e;
+      RSVD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      P->h2d_ev.push_back(e);
+    }
+    {
+      Span sp(P->prof, RSVD_STAGE_H2D, st);
+      // the copies start after the work already queued on the caller's stream
+      RSVD_CUDA(cudaEventRecord(P->h2d_ev[nch + 1], st));
+      RSVD_CUDA(cudaStreamWaitEvent(P->h2d_stream, P->h2d_ev[nch + 1], 0));
+      for (int c = 0; c < nch; ++c) {
+        const int64_t r0 = (int64_t)c * crow, rows = std::min<int64_t>(crow, A->m - r0);
+        RSVD_CUDA(cudaMemcpy2DAsync(static_cast<char*>(P->Adev) + (size_t)r0 * dpitch, dpitch,
+                                    static_cast<const char*>(A->data) + (size_t)r0 * spitch, spitch, row, rows,
+                                    cudaMemcpyHostToDevice, P->h2d_stream));
+        RSVD_CUDA(cudaEventRecord(P->h2d_ev[c], P->h2d_stream));
+      }
+      RSVD_CUDA(cudaEventRecord(P->h2d_ev[nch], P->h2d_stream));
+      if (P->prof.on) RSVD_CUDA(cudaStreamWaitEvent(st, P->h2d_ev[nch], 0));  // the stage time covers the copy
+    }
+    P->h2d_chunk_rows = crow;
+    P->h2d_chunks = nch;
+    P->h2d_pending = true;
     Ad.data = P->Adev;
     Ad.ld = ldd;
     Ad.location = RSVD_ON_DEVICE;
   }
-  if (P->dtype == RSVD_F64)
-    return run_typed<double>(P, Ad, static_cast<double*>(U), static_cast<double*>(S), static_cast<double*>(V), st);
-  return run_typed<float>(P, Ad, static_cast<float*>(U), static_cast<float*>(S), static_cast<float*>(V), st);
+  const rsvd_status res =
+      P->dtype == RSVD_F64
+          ? run_typed<double>(P, Ad, static_cast<double*>(U), static_cast<double*>(S), static_cast<double*>(V), st)
+          : run_typed<float>(P, Ad, static_cast<float*>(U), static_cast<float*>(S), static_cast<float*>(V), st);
+  if (P->h2d_pending) {  // a run that stopped before using A: the copy still ends before the call returns
+    cudaStreamSynchronize(P->h2d_stream);
+    P->h2d_pending = false;
+  }
+  return res;
 }
 
 rsvd_status rsvd_csr_tile(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx, const float* val,
@@ -1184,6 +1300,8 @@ void rsvd_destroy(rsvd_plan_t P) {
   if (P->csr_dev) cudaFree(P->csr_dev);
   if (P->h_tpinned) cudaFreeHost(P->h_tpinned);
   if (P->h_tval_pinned) cudaFreeHost(P->h_tval_pinned);
+  for (auto e : P->h2d_ev) cudaEventDestroy(e);
+  if (P->h2d_stream) cudaStreamDestroy(P->h2d_stream);
   stream_state_free(P->ss);
   csr_stream_free(P->cs);
   delete P;

@@ -70,6 +70,7 @@ constexpr int kMaxSopConverted = 4;
 // plan's BF16 copy, or an A stored in BF16 / FP16)
 constexpr int kSrc32 = 0, kSrc8 = 1, kSrc16 = 2;
 constexpr int kSplitMaxNP = 192;   // widest split-mode panel one pass supports
+constexpr int64_t kSplitChainSteps = 8;   // split mode: K steps (of 64) per TMEM accumulation chain
 constexpr int THREADS = 320;
 constexpr uint64_t kWaitNs = 1000000000ull;
 
@@ -96,6 +97,8 @@ struct TcArgs {
   uint16_t* a16lo;      // FP32 forward pass in split mode: also store BF16(A - BF16(A)) here, or null
   int64_t ld16;
   int a_lo;             // 16-bit source in split mode: 1 when A has a lo part (A = hi + lo)
+  int64_t chunk_ks;     // K steps per TMEM accumulation chain (>= 1); chains are added in FP32 by the epilogue
+  int sum_col;          // TMEM column of the running sum of a unit's chains (-1: in the output itself)
   int gram;             // 1: C = A^T A with one row tile: the panel operand is the converted A tile
   uint32_t idesc;       // tcgen05 instruction descriptor (operand type BF16 or FP16, FP32 accumulator)
 };
@@ -310,21 +313,23 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     if (lane == 0) {
       const uint32_t idesc = a.idesc;
       RingPos rop;
-      int64_t ua = 0;
-      for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x, ++ua) {
+      int64_t ua = 0;  // accumulation chains issued
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < units && ok && !*vabort; u += gridDim.x) {
         const int64_t z = u / a.mtiles;
         const int64_t k0 = z * a.ksteps_per_split;
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
+       for (int64_t c0 = k0; c0 < k1 && ok; c0 += a.chunk_ks, ++ua) {
+        const int64_t c1 = min(k1, c0 + a.chunk_ks);
         const int acc = (int)(ua & 1);
         const uint32_t pha = (uint32_t)((ua >> 1) & 1);
         if (!ptx::mbar_wait(&accEmpty[acc], pha ^ 1, vstatus, kWaitNs)) {
-          flag_timeout(a.status, kWaitAccFree, acc, k0, u); s_abort = 1; break;
+          flag_timeout(a.status, kWaitAccFree, acc, c0, u); s_abort = 1; ok = false; break;
         }
         ptx::tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * a.acc_stride);
         uint32_t accumulate = 0;
-        bool ok = true;
-        for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
+        for (int64_t ks = c0; ks < c1; ++ks, rop.next(SOP)) {
           const int sop = rop.slot;
           const uint32_t phop = rop.phase;
           if (!ptx::mbar_wait(&fullA[sop], phop, vstatus, kWaitNs)) {
@@ -360,6 +365,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         }
         if (!ok) break;
         ptx::mma_commit(&accFull[acc]);
+       }
       }
       // every product issued has completed before TMEM is released
       ptx::mma_commit(drain);
@@ -493,24 +499,74 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   } else if (warp >= 6) {
     // ---------------- epilogue ----------------
     // (warps 6-9 only: with a 16-bit source the converter warps 2-5 stay idle)
+    // Chains after the first of a unit are added in FP32 (rounded to
+    // nearest) -- to a running sum in TMEM, or to the output -- so no TMEM
+    // accumulation runs longer than chunk_ks K steps.
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16);
     int64_t ua = 0;
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++ua) {
+    bool ok = true;
+    for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
       const int64_t z = u / a.mtiles, mt = u % a.mtiles;
+      const int64_t k0 = z * a.ksteps_per_split;
+      const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
+     for (int64_t ch = k0; ch < k1; ch += a.chunk_ks, ++ua) {
       const int acc = (int)(ua & 1);
       const uint32_t pha = (uint32_t)((ua >> 1) & 1);
       const bool w = ptx::mbar_wait(&accFull[acc], pha, vstatus, kWaitNs);
-      if (!__all_sync(0xffffffffu, w)) { if (lane == 0) flag_timeout(a.status, kWaitAccFull, acc, 0, u); break; }
+      if (!__all_sync(0xffffffffu, w)) { if (lane == 0) flag_timeout(a.status, kWaitAccFull, acc, ch, u); ok = false; break; }
       ptx::tc_fence_after();
       const int64_t row = mt * BM + q * 32 + lane;
       float* crow = a.C + z * a.c_split_stride + row * a.ldc;
+      const bool first = ch == k0, last = ch + a.chunk_ks >= k1;
+      const bool tsum = a.sum_col >= 0;
+      if (tsum && !last) {
+        // keep the running sum in TMEM: sum = chain (first) or sum + chain
+        for (int c0 = 0; c0 < NP; c0 += 32) {
+          uint32_t v[32];
+          ptx::tmem_ld_32x32b_x32(lane_base + (uint32_t)(acc * a.acc_stride + c0), v);
+          if (!first) {
+            uint32_t t[32];
+            ptx::tmem_ld_32x32b_x32(lane_base + (uint32_t)(a.sum_col + c0), t);
+            ptx::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(t[j]) + __uint_as_float(v[j]));
+          } else {
+            ptx::tmem_ld_wait();
+          }
+          ptx::tmem_st_32x32b_x32(lane_base + (uint32_t)(a.sum_col + c0), v);
+        }
+        ptx::tmem_st_wait();
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&accEmpty[acc]);
+        continue;
+      }
+      // the unit's last chain: its value (plus the running sum) goes out
+      const bool add = a.accumulate || (!tsum && !first);
       for (int c0 = 0; c0 < NP; c0 += 32) {
         uint32_t v[32];
-        ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * a.acc_stride + c0), v);
-        ptx::tmem_ld_wait();
+        ptx::tmem_ld_32x32b_x32(lane_base + (uint32_t)(acc * a.acc_stride + c0), v);
+        if (tsum && !first) {
+          uint32_t t[32];
+          ptx::tmem_ld_32x32b_x32(lane_base + (uint32_t)(a.sum_col + c0), t);
+          ptx::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(t[j]) + __uint_as_float(v[j]));
+        } else {
+          ptx::tmem_ld_wait();
+        }
         if (row < a.M) {
           const int nv = min(32, a.N - c0);
-          if (a.accumulate) {
+          if (add && nv == 32 && (a.ldc & 3) == 0) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              float4* p = reinterpret_cast<float4*>(crow + c0 + j);
+              const float4 o = *p;
+              *p = make_float4(o.x + __uint_as_float(v[j]), o.y + __uint_as_float(v[j + 1]),
+                               o.z + __uint_as_float(v[j + 2]), o.w + __uint_as_float(v[j + 3]));
+            }
+          } else if (add) {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
               if (j < nv) crow[c0 + j] += __uint_as_float(v[j]);
@@ -530,6 +586,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(&accEmpty[acc]);
+     }
     }
   }
 
@@ -674,6 +731,7 @@ struct TcSource {
   uint16_t* copy16 = nullptr;       // FP32 forward pass: write the BF16 copy here
   uint16_t* copy16lo = nullptr;     // FP32 forward pass in split mode: and its lo part here
   int64_t ld16 = 0;
+  int64_t kps = 0;                  // K steps per split to use (0: the balanced choice for this shape)
 };
 
 rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, int prec, int r, const float* X,
@@ -709,7 +767,11 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: a 16-bit A needs a 16-byte aligned base and ld % 8 == 0");
   if (src8 && (src.f8->ldc % 16 != 0 || (reinterpret_cast<uintptr_t>(src.f8->codes) & 15) != 0))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: FP8 codes need a 16-byte aligned base and ld % 16 == 0");
-  const TcShape s = tc_shape(m, n, r, trans);
+  TcShape s = tc_shape(m, n, r, trans);
+  if (src.kps > 0) {  // a row block of a larger pass: that pass's split of the K range
+    s.ksteps_per_split = src.kps;
+    s.nsplit = (int)cdiv(s.ksteps, s.ksteps_per_split);
+  }
   Carver c(ws, ws_bytes);
   auto* Xhi = c.take<uint16_t>((size_t)s.NP * s.ldb);
   uint16_t* Xlo = split ? c.take<uint16_t>((size_t)s.NP * s.ldb) : nullptr;
@@ -764,8 +826,11 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   ta.N = r;
   ta.NP = s.NP;
   ta.acc_stride = (int)round_up(s.NP, 32);
+  // two accumulators, and in split mode a running sum when it fits in the
+  // 512 columns of TMEM (else the chains are added to the output)
+  const bool tsum = split && 3 * ta.acc_stride <= 512;
   int cols = 32;
-  while (cols < 2 * ta.acc_stride) cols *= 2;
+  while (cols < (tsum ? 3 : 2) * ta.acc_stride) cols *= 2;
   ta.tmem_cols = cols;
   ta.mtiles = s.mtiles;
   ta.ksteps = s.ksteps;
@@ -784,6 +849,15 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   ta.a16lo = src.copy16lo;
   ta.ld16 = src.ld16;
   ta.a_lo = a_lo ? 1 : 0;
+  // The tensor cores' FP32 accumulation truncates: each MMA added to an
+  // accumulator shrinks it by about half a unit in 2^-24 on average, a bias
+  // that grows with the number of MMAs in the chain (at 700 MMAs per chain it
+  // lowered every singular value of the dense workload by 1.3e-5 to 1.9e-5).
+  // Split-mode passes, which aim at FP32 accuracy, restart the accumulation
+  // every kSplitChainSteps K steps (96 MMAs) and add the chains in FP32,
+  // rounded to nearest, on the CUDA cores.
+  ta.chunk_ks = split ? kSplitChainSteps : s.ksteps_per_split;
+  ta.sum_col = tsum ? 2 * ta.acc_stride : -1;
   ta.gram = gram ? 1 : 0;
   ta.idesc = f16 ? ptx::idesc_f16_f32(BM, (uint32_t)s.NP) : ptx::idesc_bf16_f32(BM, (uint32_t)s.NP);
   if (src16 && trans) ta.idesc |= ptx::kIdescAMajorMN;
@@ -838,15 +912,22 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
 
 }  // namespace
 
+int64_t tc_ksteps_per_split(int64_t m, int64_t n, int r, int trans, int prec) {
+  // a pass over column halves of the panel takes each half's own split
+  if (round_up(r, 16) > (prec == RSVD_PREC_BF16X3 ? kSplitMaxNP : 256)) return 0;
+  return tc_shape(m, n, r, trans).ksteps_per_split;
+}
+
 rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X, int64_t ldx,
                               float* Y, int64_t ldy, int64_t, int64_t, void* ws, size_t ws_bytes,
                               int* status, cudaStream_t stream, bool accumulate, uint16_t* copy16,
-                              int64_t ld16, uint16_t* copy16lo) {
+                              int64_t ld16, uint16_t* copy16lo, int64_t kps) {
   TcSource src;
   src.A = &A;
   src.copy16 = copy16;
   src.copy16lo = copy16lo;
   src.ld16 = ld16;
+  src.kps = kps;
   return tc_apass_run(src, A.m, A.n, trans, prec, r, X, ldx, Y, ldy, ws, ws_bytes, status, stream, accumulate);
 }
 
@@ -857,11 +938,12 @@ rsvd_status tc_apass_from_bf16(const Bf16Source& b16, int trans, int r, const fl
 
 rsvd_status tc_apass_from_16(const Bf16Source& a16, int trans, int prec, int r, const float* X, int64_t ldx,
                              float* Y, int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream,
-                             bool accumulate) {
+                             bool accumulate, int64_t kps) {
   if (prec != RSVD_PREC_BF16 && prec != RSVD_PREC_BF16X3)
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: a 16-bit A takes BF16 or BF16X3 precision");
   TcSource src;
   src.b16 = &a16;
+  src.kps = kps;
   return tc_apass_run(src, a16.m, a16.n, trans, prec, r, X, ldx, Y, ldy, ws, ws_bytes, status, stream,
                       accumulate);
 }

@@ -218,10 +218,16 @@ rsvd_status tc_apass_from_fp8(const Fp8Source& f8, int trans, int r, const float
 // as its operands are, row-major with stride ld16 (a multiple of 64 >= n),
 // for tc_apass_from_bf16; copy16lo (optional, split mode only) receives
 // BF16(A - BF16(A)) in the same layout, the lo part of the split operand.
+// kps (optional): K steps per split, to give a row block of a larger pass the
+// larger pass's split of the K range (tc_ksteps_per_split), hence its sums.
 rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, const float* X,
                               int64_t ldx, float* Y, int64_t ldy, int64_t mb, int64_t nb, void* ws,
                               size_t ws_bytes, int* status, cudaStream_t stream, bool accumulate = false,
-                              uint16_t* copy16 = nullptr, int64_t ld16 = 0, uint16_t* copy16lo = nullptr);
+                              uint16_t* copy16 = nullptr, int64_t ld16 = 0, uint16_t* copy16lo = nullptr,
+                              int64_t kps = 0);
+// The K steps per split a pass over an m x n A chooses (0 where the pass
+// runs over column halves of the panel).
+int64_t tc_ksteps_per_split(int64_t m, int64_t n, int r, int trans, int prec);
 // A BF16 copy of a dense m x n A (row-major, stride ld elements).
 struct Bf16Source {
   const uint16_t* data = nullptr;
@@ -241,6 +247,6 @@ rsvd_status tc_apass_from_bf16(const Bf16Source& b16, int trans, int r, const fl
 // copy of an FP32 A) the product of that part with the panel's hi part too.
 rsvd_status tc_apass_from_16(const Bf16Source& a16, int trans, int prec, int r, const float* X, int64_t ldx,
                              float* Y, int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream,
-                             bool accumulate = false);
+                             bool accumulate = false, int64_t kps = 0);
 
 }  // namespace rsvd

@@ -235,15 +235,24 @@ def test_csr_streamed_full_width_blocks_match_in_core_bits(g, zipf):
 @pytest.mark.parametrize("mb,nb", [(3000, 1500), (7001, 5000), (20000, 999)])
 def test_csr_streamed_block_cyclic_grid_matches_oracle(g, zipf, mb, nb):
     """Streamed on the block-cyclic grid mb x nb (blocks cut on the host,
-    partial products of a row block added in block order), against the oracle."""
+    partial products of a row block added in block order), against the oracle:
+    under a cap that holds the slots and some resident blocks, and with no cap
+    (the block-cyclic map in core: every block resident after the first pass)."""
     m, n, rp, ci, v = zipf
     k, p, q, seed = 20, 10, 2, 2004
     A_bytes = (m + 1) * 4 + len(v) * 8
-    cap = _csr_min_cap(g, m, n, k, p) + A_bytes // 2
+    cap = _csr_min_cap(g, m, n, k, p) + A_bytes * 3
     plan = g.Plan(m, n, k, p, q, seed, mem_cap=cap, kind="csr", mb=mb, nb=nb)
     U, S, V = (t.cpu().numpy().astype(np.float64) for t in plan.run(_torch_csr(m, n, rp, ci, v, "cpu")))
-    assert plan.stream_stats()["tiles_streamed_per_pass"] > 0
+    st = plan.stream_stats()
+    assert st["h2d_bytes"] > 0 and st["tiles_resident"] > 0
     plan.close()
+    free = g.Plan(m, n, k, p, q, seed, kind="csr", mb=mb, nb=nb)
+    Uf, Sf, Vf = (t.cpu().numpy().astype(np.float64) for t in free.run(_torch_csr(m, n, rp, ci, v, "cpu")))
+    stf = free.stream_stats()
+    assert stf["tiles_streamed_per_pass"] == 0 and stf["h2d_bytes"] < 3 * A_bytes  # each block copied once
+    free.close()
+    assert np.array_equal(Sf, S)
     Uo, So, Vo = OR.rsvd(OL.CSR(m, n, rp, ci, v), k, p, q, seed, "f32")
     assert sigma_rel_err(S, So) <= 1e-5
     assert cluster_safe_angles(U, Uo, So, k) <= 1e-4 and cluster_safe_angles(V, Vo, So, k) <= 1e-4
