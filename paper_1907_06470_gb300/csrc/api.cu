@@ -536,10 +536,14 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     return apass_dense(A, trans, pr, r, Xin, ldr, Yout, ldr, P->mb, P->nb, P->apass_ws, P->apass_ws_bytes,
                        P->status, st);
   };
+  // Range-finder bases only carry the sketch's span to the next product: one
+  // CholeskyQR sweep for them; the final Q, whose orthonormality enters
+  // B = Q^T A, takes both sweeps
   auto orth = [&](int64_t M, const T* Yin, T* Qout, bool final_q) -> rsvd_status {
     Span sp(pf, RSVD_STAGE_ORTH, st);
     const bool tc = P->tc_orth_all || (P->tc_orth_inner && !final_q);
-    return orth_panel<T>(M, r, Yin, ldr, Qout, ldr, nullptr, P->orth, st, tc);
+    const bool one = !final_q;
+    return orth_panel<T>(M, r, Yin, ldr, Qout, ldr, nullptr, P->orth, st, tc, one);
   };
   // Section 3.8 persistence: the header of each checkpoint places its basis in
   // the execution plan; a matching checkpoint lets the run skip its steps.

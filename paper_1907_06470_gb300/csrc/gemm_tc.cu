@@ -71,6 +71,7 @@ constexpr int kMaxSopConverted = 4;
 constexpr int kSrc32 = 0, kSrc8 = 1, kSrc16 = 2;
 constexpr int kSplitMaxNP = 192;   // widest split-mode panel one pass supports
 constexpr int64_t kSplitChainSteps = 8;   // split mode: K steps (of 64) per TMEM accumulation chain
+constexpr int64_t kPlainChainSteps = 32;  // other modes, when a TMEM running sum fits
 constexpr int THREADS = 320;
 constexpr uint64_t kWaitNs = 1000000000ull;
 
@@ -826,9 +827,10 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   ta.N = r;
   ta.NP = s.NP;
   ta.acc_stride = (int)round_up(s.NP, 32);
-  // two accumulators, and in split mode a running sum when it fits in the
-  // 512 columns of TMEM (else the chains are added to the output)
-  const bool tsum = split && 3 * ta.acc_stride <= 512;
+  // two accumulators and a running sum when it fits in the 512 columns of TMEM
+  // (else split mode adds its chains to the output, other modes take one chain
+  // per output tile)
+  const bool tsum = 3 * ta.acc_stride <= 512;
   int cols = 32;
   while (cols < (tsum ? 3 : 2) * ta.acc_stride) cols *= 2;
   ta.tmem_cols = cols;
@@ -855,8 +857,9 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   // lowered every singular value of the dense workload by 1.3e-5 to 1.9e-5).
   // Split-mode passes, which aim at FP32 accuracy, restart the accumulation
   // every kSplitChainSteps K steps (96 MMAs) and add the chains in FP32,
-  // rounded to nearest, on the CUDA cores.
-  ta.chunk_ks = split ? kSplitChainSteps : s.ksteps_per_split;
+  // rounded to nearest, on the CUDA cores; other passes every
+  // kPlainChainSteps K steps (128 MMAs) where the running sum fits TMEM.
+  ta.chunk_ks = split ? kSplitChainSteps : (tsum ? kPlainChainSteps : s.ksteps_per_split);
   ta.sum_col = tsum ? 2 * ta.acc_stride : -1;
   ta.gram = gram ? 1 : 0;
   ta.idesc = f16 ? ptx::idesc_f16_f32(BM, (uint32_t)s.NP) : ptx::idesc_bf16_f32(BM, (uint32_t)s.NP);

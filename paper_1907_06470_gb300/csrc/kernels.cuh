@@ -64,9 +64,13 @@ struct OrthWs {
 size_t orth_ws_bytes(int64_t M, int r, int dtype, bool tc = false);
 OrthWs orth_ws_carve(Carver& c, int64_t M, int r, int dtype, bool tc = false);
 
+// one_sweep (R == NULL only): a single CholeskyQR sweep, for bases whose only
+// job is to span the sketch for the next product: Q spans Y as accurately as
+// after two sweeps (the second changes orthonormality, not the span) but is
+// orthonormal only to about eps cond(Y)^2.
 template <typename T>
 rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t ldq, double* R,
-                       const OrthWs& ws, cudaStream_t stream, bool tc = false);
+                       const OrthWs& ws, cudaStream_t stream, bool tc = false, bool one_sweep = false);
 
 // jacobi.cu -- Section 2.1 step 6 core.
 struct JacobiWs {

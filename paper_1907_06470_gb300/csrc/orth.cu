@@ -655,8 +655,13 @@ rsvd_status panel_times_tc(int64_t M, int r, const float* Y, int64_t ldy, const 
 
 template <typename T>
 rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t ldq, double* R,
-                       const OrthWs& ws, cudaStream_t stream, bool tc) {
-  T* Q1 = static_cast<T*>(ws.tmp);
+                       const OrthWs& ws, cudaStream_t stream, bool tc, bool one_sweep) {
+  // one sweep: Q = Y R1^-1 spans the columns of Y (dead pivots refilled) but is
+  // orthonormal only to about eps cond(Y)^2 -- enough where only the span is
+  // used; the second sweep restores orthonormality to rounding
+  if (R) one_sweep = false;
+  T* Q1 = one_sweep ? Q : static_cast<T*>(ws.tmp);
+  const int64_t ld1 = one_sweep ? ldq : ws.ld_tmp;
   const T* Rt = static_cast<const T*>(ws.Rinv_t);
   if constexpr (std::is_same<T, float>::value) {
     if (tc && ws.tc_ws && ldy % 4 == 0 && ldq % 4 == 0 && aligned16(Y) && aligned16(Q)) {
@@ -664,8 +669,9 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
       RSVD_TRY(gram_tc(M, r, Y, ldy, ws, stream));
       float* L1 = reinterpret_cast<float*>(ws.L1);
       RSVD_TRY(chol_inv<float>(r, ws, L1, ws.dead1, pivot_tau<float>(), stream));
-      RSVD_TRY(panel_times_tc(M, r, Y, ldy, Rt, Q1, ws.ld_tmp, ws, stream));
-      RSVD_TRY(fill_dead_columns(M, r, ws.dead1, Q1, ws.ld_tmp, RSVD_F32, kDeadFillSeed, stream));
+      RSVD_TRY(panel_times_tc(M, r, Y, ldy, Rt, Q1, ld1, ws, stream));
+      RSVD_TRY(fill_dead_columns(M, r, ws.dead1, Q1, ld1, RSVD_F32, kDeadFillSeed, stream));
+      if (one_sweep) return RSVD_OK;
       RSVD_TRY(gram_tc(M, r, Q1, ws.ld_tmp, ws, stream));
       float* L2 = reinterpret_cast<float*>(ws.L2);
       RSVD_TRY(chol_inv<float>(r, ws, L2, ws.dead2, pivot_tau<float>(), stream));
@@ -684,9 +690,9 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
   RSVD_TRY(gram<T>(M, r, Y, ldy, ws, stream));
   T* L1 = reinterpret_cast<T*>(ws.L1);
   RSVD_TRY(chol_inv<T>(r, ws, L1, ws.dead1, pivot_tau<T>(), stream));
-  RSVD_TRY(simt_gemm<T>(M, r, r, Y, ldy, false, Rt, ws.ld_rt, Q1, ws.ld_tmp, false, 1, r, nullptr, stream));
-  RSVD_TRY(fill_dead_columns(M, r, ws.dead1, Q1, ws.ld_tmp, sizeof(T) == 8 ? RSVD_F64 : RSVD_F32,
-                             kDeadFillSeed, stream));
+  RSVD_TRY(simt_gemm<T>(M, r, r, Y, ldy, false, Rt, ws.ld_rt, Q1, ld1, false, 1, r, nullptr, stream));
+  RSVD_TRY(fill_dead_columns(M, r, ws.dead1, Q1, ld1, sizeof(T) == 8 ? RSVD_F64 : RSVD_F32, kDeadFillSeed, stream));
+  if (one_sweep) return RSVD_OK;
   // sweep 2
   RSVD_TRY(gram<T>(M, r, Q1, ws.ld_tmp, ws, stream));
   T* L2 = reinterpret_cast<T*>(ws.L2);
@@ -702,8 +708,8 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
 }
 
 template rsvd_status orth_panel<float>(int64_t, int, const float*, int64_t, float*, int64_t, double*,
-                                       const OrthWs&, cudaStream_t, bool);
+                                       const OrthWs&, cudaStream_t, bool, bool);
 template rsvd_status orth_panel<double>(int64_t, int, const double*, int64_t, double*, int64_t,
-                                        double*, const OrthWs&, cudaStream_t, bool);
+                                        double*, const OrthWs&, cudaStream_t, bool, bool);
 
 }  // namespace rsvd
