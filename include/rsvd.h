@@ -277,8 +277,12 @@ rsvd_status rsvd_full(const rsvd_matrix* A, void* U, void* S, void* V, void* str
  * approximation otherwise.  The range finder is not differentiated.
  * Inputs (device, plan dtype): U m x k, S k, V n x k, and the cotangents
  * dU m x k, dS k, dV n x k, any of which may be NULL (zero).  Output dA: m x n
- * row-major (leading dimension n), overwritten.  Uses the plan's workspace;
- * enqueues only.  Errors: INVALID_ARG. */
+ * row-major (leading dimension n), overwritten.  FP32 plans form the final
+ * rank-2k product dA = [U M + P | U S^-1] [V | Q]^T on the tensor cores in
+ * split BF16 (about 16 significant bits per operand, FP32 accumulation over
+ * the 2k terms) and synchronise `stream` to read its status (TIMEOUT if a
+ * pipeline wait expired); FP64 plans compute in FP64 and enqueue only.  Uses
+ * the plan's workspace.  Errors: INVALID_ARG, TIMEOUT. */
 rsvd_status rsvd_backward(rsvd_plan_t plan, const void* U, const void* S, const void* V,
                           const void* dU, const void* dS, const void* dV, void* dA, void* stream);
 

@@ -9,6 +9,8 @@
 //   dA = [U | P] [V M^T + Q | V]^T        (one rank-2k product).
 // The k x k pieces are formed in FP64 (the U^T dU and V^T dV reductions add
 // FP64 chunk sums); the panels and the final product run in the data type.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -125,12 +127,13 @@ size_t backward_ws_bytes(int64_t m, int64_t n, int k, int dtype) {
   s.take<char>((size_t)cdiv(mx, kChunk) * k * k * esz);  // partials
   s.take<double>((size_t)2 * k * k);               // U^T dU, V^T dV
   s.take<char>((size_t)(3 * k * k + k) * esz);     // M^T, U^T dU, V^T dV, 1/S in the data type
+  if (dtype == RSVD_F32) s.take<char>(tc_gemm_wide_ws_bytes(m, 2 * k, n, RSVD_PREC_BF16X3));  // dA on the tensor cores
   return s.used + 256;
 }
 
 template <typename T>
 rsvd_status backward_typed(int64_t m, int64_t n, int k, const T* U, const T* S, const T* V, const T* dU,
-                           const T* dS, const T* dV, T* dA, void* ws, size_t ws_bytes, cudaStream_t st) {
+                           const T* dS, const T* dV, T* dA, void* ws, size_t ws_bytes, int* status, cudaStream_t st) {
   const int64_t mx = m > n ? m : n;
   Carver c(ws, ws_bytes);
   T* L = c.take<T>((size_t)m * 2 * k);
@@ -141,6 +144,8 @@ rsvd_status backward_typed(int64_t m, int64_t n, int k, const T* U, const T* S, 
   double* UtdU = c.take<double>((size_t)2 * k * k);
   double* VtdV = UtdU ? UtdU + (size_t)k * k : nullptr;
   T* small = c.take<T>((size_t)3 * k * k + k);
+  const size_t tcb = std::is_same<T, float>::value ? tc_gemm_wide_ws_bytes(m, 2 * k, n, RSVD_PREC_BF16X3) : 0;
+  void* tcws = tcb ? c.take<char>(tcb) : nullptr;
   if (c.overflow) return fail(RSVD_ERR_INVALID_ARG, "rsvd_backward: workspace too small");
   T* Mt = small;
   T* UtdU_t = small + (size_t)k * k;
@@ -163,16 +168,26 @@ rsvd_status backward_typed(int64_t m, int64_t n, int k, const T* U, const T* S, 
   right_panel_kernel<T><<<dim3((unsigned)cdiv(n, 32), (unsigned)cdiv(k, 32)), dim3(32, 8), 0, st>>>(
       n, k, V, dV, VM, XY, Sinv, Bt);
   RSVD_CUDA(after_launch());
-  // dA = L Bt  (m x n, K = 2k)
+  // dA = L Bt  (m x n, K = 2k): FP32 data on the tensor cores in split BF16
+  // (three products, about 16 significant bits per operand; the sums are
+  // 2k = 128 terms long), FP64 data on the FP64 units
+  if constexpr (std::is_same<T, float>::value) {
+    if ((2 * k) % 4 == 0) {
+      rsvd_matrix Lm = {};
+      Lm.kind = RSVD_DENSE; Lm.dtype = RSVD_F32; Lm.location = RSVD_ON_DEVICE;
+      Lm.m = m; Lm.n = 2 * k; Lm.data = L; Lm.ld = 2 * k;
+      return tc_gemm_wide(Lm, RSVD_PREC_BF16X3, n, Bt, n, dA, n, tcws, tcb, status, st);
+    }
+  }
   RSVD_TRY(simt_gemm<T>(m, n, 2 * k, L, 2 * k, false, Bt, n, dA, n, false, 1, 2 * k, nullptr, st));
   return RSVD_OK;
 }
 
 template rsvd_status backward_typed<float>(int64_t, int64_t, int, const float*, const float*, const float*,
-                                           const float*, const float*, const float*, float*, void*, size_t,
+                                           const float*, const float*, const float*, float*, void*, size_t, int*,
                                            cudaStream_t);
 template rsvd_status backward_typed<double>(int64_t, int64_t, int, const double*, const double*, const double*,
                                             const double*, const double*, const double*, double*, void*, size_t,
-                                            cudaStream_t);
+                                            int*, cudaStream_t);
 
 }  // namespace rsvd

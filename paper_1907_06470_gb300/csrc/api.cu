@@ -1289,11 +1289,14 @@ rsvd_status rsvd_backward(rsvd_plan_t P, const void* U, const void* S, const voi
     return backward_typed<double>(P->m, P->n, P->k, static_cast<const double*>(U), static_cast<const double*>(S),
                                   static_cast<const double*>(V), static_cast<const double*>(dU),
                                   static_cast<const double*>(dS), static_cast<const double*>(dV),
-                                  static_cast<double*>(dA), P->bwd_ws, P->bwd_ws_bytes, st);
-  return backward_typed<float>(P->m, P->n, P->k, static_cast<const float*>(U), static_cast<const float*>(S),
-                               static_cast<const float*>(V), static_cast<const float*>(dU),
-                               static_cast<const float*>(dS), static_cast<const float*>(dV),
-                               static_cast<float*>(dA), P->bwd_ws, P->bwd_ws_bytes, st);
+                                  static_cast<double*>(dA), P->bwd_ws, P->bwd_ws_bytes, nullptr, st);
+  // FP32: the rank-2k product runs on the tensor cores; its status word is read
+  RSVD_CUDA(cudaMemsetAsync(P->status, 0, 4 * sizeof(int), st));
+  RSVD_TRY(backward_typed<float>(P->m, P->n, P->k, static_cast<const float*>(U), static_cast<const float*>(S),
+                                 static_cast<const float*>(V), static_cast<const float*>(dU),
+                                 static_cast<const float*>(dS), static_cast<const float*>(dV),
+                                 static_cast<float*>(dA), P->bwd_ws, P->bwd_ws_bytes, P->status, st));
+  return read_device_status(P->status, st);
 }
 
 void rsvd_destroy(rsvd_plan_t P) {

@@ -82,6 +82,7 @@ struct TcArgs {
   int acc_stride;       // TMEM column offset of the second accumulator
   int tmem_cols;        // TMEM columns allocated
   int64_t mtiles;
+  int ntiles;           // column tiles of NP output columns (wide products; 1 for A-passes)
   int64_t ksteps;       // total K steps
   int64_t ksteps_per_split;
   int nsplit;
@@ -221,7 +222,11 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const int64_t units = a.mtiles * a.nsplit;
+  // a unit is one output tile (128 rows x NP columns) over one K split;
+  // unit u: row tile u % mtiles, column tile (u / mtiles) % ntiles, split
+  // u / (mtiles ntiles)
+  const int64_t mn_tiles = a.mtiles * a.ntiles;
+  const int64_t units = mn_tiles * a.nsplit;
   const uint32_t b_bytes = (uint32_t)NP * 128u;
 
   if (warp == 0) {
@@ -239,7 +244,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       RingPos rop;
       uint32_t issued = 0, parity = 0;  // per slot: loaded at least once, phase of the last load
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
-        const int64_t z = u / a.mtiles, mt = u % a.mtiles;
+        const int64_t z = u / mn_tiles, mt = u % a.mtiles;
         const int64_t k0 = z * a.ksteps_per_split;
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
         for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
@@ -269,7 +274,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       RingPos r32;
       uint32_t issued = 0, parity = 0;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
-        const int64_t z = u / a.mtiles, mt = u % a.mtiles;
+        const int64_t z = u / mn_tiles, mt = u % a.mtiles;
         const int64_t k0 = z * a.ksteps_per_split;
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
         for (int64_t ks = k0; ks < k1; ++ks, r32.next(S32)) {
@@ -291,7 +296,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       RingPos rop;
       uint32_t issued = 0, parity = 0;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
-        const int64_t z = u / a.mtiles;
+        const int64_t z = u / mn_tiles;
         const int64_t k0 = z * a.ksteps_per_split;
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
         for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
@@ -302,8 +307,9 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           ptx::mbar_arrive_expect_tx(&fullB[sop], b_bytes * L::PARTS);
           issued |= 1u << sop;
           parity = (parity & ~(1u << sop)) | (rop.phase << sop);
-          ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 0), &mapB, &fullB[sop], (int32_t)(ks * BK), 0);
-          if (SPLIT) ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 1), &mapBlo, &fullB[sop], (int32_t)(ks * BK), 0);
+          const int32_t ny = (int32_t)(((u / a.mtiles) % a.ntiles) * NP);  // first panel column of the tile
+          ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 0), &mapB, &fullB[sop], (int32_t)(ks * BK), ny);
+          if (SPLIT) ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 1), &mapBlo, &fullB[sop], (int32_t)(ks * BK), ny);
         }
       }
       for (int i = 0; i < SOP; ++i)
@@ -317,7 +323,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       int64_t ua = 0;  // accumulation chains issued
       bool ok = true;
       for (int64_t u = blockIdx.x; u < units && ok && !*vabort; u += gridDim.x) {
-        const int64_t z = u / a.mtiles;
+        const int64_t z = u / mn_tiles;
         const int64_t k0 = z * a.ksteps_per_split;
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
        for (int64_t c0 = k0; c0 < k1 && ok; c0 += a.chunk_ks, ++ua) {
@@ -377,7 +383,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     const int cw = warp - 2;
     RingPos r32, rop;
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-      const int64_t z = u / a.mtiles, mt = u % a.mtiles;
+      const int64_t z = u / mn_tiles, mt = u % a.mtiles;
       const int64_t k0 = z * a.ksteps_per_split;
       const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
       bool ok = true;
@@ -508,7 +514,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     int64_t ua = 0;
     bool ok = true;
     for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
-      const int64_t z = u / a.mtiles, mt = u % a.mtiles;
+      const int64_t z = u / mn_tiles, mt = u % a.mtiles;
       const int64_t k0 = z * a.ksteps_per_split;
       const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
      for (int64_t ch = k0; ch < k1; ch += a.chunk_ks, ++ua) {
@@ -518,7 +524,9 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       if (!__all_sync(0xffffffffu, w)) { if (lane == 0) flag_timeout(a.status, kWaitAccFull, acc, ch, u); ok = false; break; }
       ptx::tc_fence_after();
       const int64_t row = mt * BM + q * 32 + lane;
-      float* crow = a.C + z * a.c_split_stride + row * a.ldc;
+      const int col0 = (int)((u / a.mtiles) % a.ntiles) * NP;  // first output column of the tile
+      float* crow = a.C + z * a.c_split_stride + row * a.ldc + col0;
+      const int ncols = a.N - col0;  // output columns left from col0
       const bool first = ch == k0, last = ch + a.chunk_ks >= k1;
       const bool tsum = a.sum_col >= 0;
       if (tsum && !last) {
@@ -557,9 +565,9 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         } else {
           ptx::tmem_ld_wait();
         }
-        if (row < a.M) {
-          const int nv = min(32, a.N - c0);
-          if (add && nv == 32 && (a.ldc & 3) == 0) {
+        if (row < a.M && c0 < ncols) {
+          const int nv = min(32, ncols - c0);
+          if (add && nv == 32 && (a.ldc & 3) == 0 && (col0 & 3) == 0) {
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
               float4* p = reinterpret_cast<float4*>(crow + c0 + j);
@@ -571,7 +579,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 #pragma unroll
             for (int j = 0; j < 32; ++j)
               if (j < nv) crow[c0 + j] += __uint_as_float(v[j]);
-          } else if (nv == 32 && (a.ldc & 3) == 0) {
+          } else if (nv == 32 && (a.ldc & 3) == 0 && (col0 & 3) == 0) {
 #pragma unroll
             for (int j = 0; j < 32; j += 4)
               *reinterpret_cast<float4*>(crow + c0 + j) =
@@ -733,6 +741,7 @@ struct TcSource {
   uint16_t* copy16lo = nullptr;     // FP32 forward pass in split mode: and its lo part here
   int64_t ld16 = 0;
   int64_t kps = 0;                  // K steps per split to use (0: the balanced choice for this shape)
+  bool wide = false;                // forward product with any number of output columns, in column tiles
 };
 
 rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, int prec, int r, const float* X,
@@ -745,7 +754,9 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   // 16-bit source in split mode: A X_hi + A X_lo, plus A_lo X_hi when A has a
   // lo part (the split copy of an FP32 A)
   const bool a_lo = split && src16 && src.b16->lo != nullptr;
-  if (r < 1 || r > 512) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: r must be in [1, 512]");
+  if (r < 1 || (r > 512 && !src.wide)) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: r must be in [1, 512]");
+  if (src.wide && (trans || !src.A || src.copy16))
+    return fail(RSVD_ERR_INVALID_ARG, "tensor-core product: column tiles take a forward product over FP32 A");
   if (split && src8) return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: the FP8 source has no split mode");
   if (src16 && src.b16->lo && f16)
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: a split 16-bit source is BF16");
@@ -753,7 +764,7 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
                      src.ld16 < round_up(n, BK) || src.ld16 % BK != 0 || (src.copy16lo && !split)))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: the BF16 copy is written by one forward pass "
                                       "over FP32 A (ld16 a multiple of 64 covering n; its lo part in split mode)");
-  if (round_up(r, 16) > (split ? kSplitMaxNP : 256)) {
+  if (!src.wide && round_up(r, 16) > (split ? kSplitMaxNP : 256)) {
     // wider than one accumulator (256 columns) or than the split-mode operand
     // ring fits: passes over column halves of the panel (A is read per half)
     const int h = (int)round_up(cdiv(r, 2), 16);
@@ -768,14 +779,22 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: a 16-bit A needs a 16-byte aligned base and ld % 8 == 0");
   if (src8 && (src.f8->ldc % 16 != 0 || (reinterpret_cast<uintptr_t>(src.f8->codes) & 15) != 0))
     return fail(RSVD_ERR_INVALID_ARG, "tensor-core A-pass: FP8 codes need a 16-byte aligned base and ld % 16 == 0");
-  TcShape s = tc_shape(m, n, r, trans);
+  // column tiles of a wide product: NP columns each, the K range whole
+  const int np_wide = (int)std::min<int64_t>(round_up(r, 16), split ? kSplitMaxNP : 256);
+  TcShape s = tc_shape(m, n, src.wide ? np_wide : r, trans);
+  const int ntiles = src.wide ? (int)cdiv(r, s.NP) : 1;
+  const int64_t np_all = (int64_t)ntiles * s.NP;  // panel rows converted (all column tiles)
+  if (src.wide) {
+    s.ksteps_per_split = s.ksteps;
+    s.nsplit = 1;
+  }
   if (src.kps > 0) {  // a row block of a larger pass: that pass's split of the K range
     s.ksteps_per_split = src.kps;
     s.nsplit = (int)cdiv(s.ksteps, s.ksteps_per_split);
   }
   Carver c(ws, ws_bytes);
-  auto* Xhi = c.take<uint16_t>((size_t)s.NP * s.ldb);
-  uint16_t* Xlo = split ? c.take<uint16_t>((size_t)s.NP * s.ldb) : nullptr;
+  auto* Xhi = c.take<uint16_t>((size_t)np_all * s.ldb);
+  uint16_t* Xlo = split ? c.take<uint16_t>((size_t)np_all * s.ldb) : nullptr;
   const int64_t slab = round_up(s.M * r, 4);
   float* partial = s.nsplit > 1 ? c.take<float>((size_t)s.nsplit * slab) : nullptr;
   int* own_status = c.take<int>(4);
@@ -790,9 +809,9 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   const bool gram = trans && !src8 && !src16 && !src.copy16 && X == static_cast<const float*>(src.A->data) &&
                     ldx == src.A->ld && (int64_t)r == n && s.mtiles == 1;
   if (!gram) {  // panel -> BF16 or FP16 (hi, lo), K-major
-    dim3 grid((unsigned)cdiv(s.K, 32), (unsigned)cdiv(s.NP, 32));
-    if (f16) panel_to_16_kernel<__half><<<grid, dim3(32, 8), 0, stream>>>(s.K, r, s.NP, X, ldx, Xhi, Xlo, s.ldb);
-    else panel_to_16_kernel<__nv_bfloat16><<<grid, dim3(32, 8), 0, stream>>>(s.K, r, s.NP, X, ldx, Xhi, Xlo, s.ldb);
+    dim3 grid((unsigned)cdiv(s.K, 32), (unsigned)cdiv(np_all, 32));
+    if (f16) panel_to_16_kernel<__half><<<grid, dim3(32, 8), 0, stream>>>(s.K, r, (int)np_all, X, ldx, Xhi, Xlo, s.ldb);
+    else panel_to_16_kernel<__nv_bfloat16><<<grid, dim3(32, 8), 0, stream>>>(s.K, r, (int)np_all, X, ldx, Xhi, Xlo, s.ldb);
     RSVD_CUDA(after_launch());
   }
   const CUtensorMapDataType t16 = f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
@@ -814,10 +833,10 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
     RSVD_TRY(encode_2d(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, src.A->data, (uint64_t)n, (uint64_t)m,
                        (uint64_t)src.A->ld * 4, box_in, box_out, CU_TENSOR_MAP_SWIZZLE_NONE));
   if (!a_lo) mapAlo = mapA;
-  RSVD_TRY(encode_2d(&mapB, t16, Xhi, (uint64_t)s.K, (uint64_t)s.NP, (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP,
+  RSVD_TRY(encode_2d(&mapB, t16, Xhi, (uint64_t)s.K, (uint64_t)np_all, (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP,
                      CU_TENSOR_MAP_SWIZZLE_128B));
   if (split)
-    RSVD_TRY(encode_2d(&mapBlo, t16, Xlo, (uint64_t)s.K, (uint64_t)s.NP, (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP,
+    RSVD_TRY(encode_2d(&mapBlo, t16, Xlo, (uint64_t)s.K, (uint64_t)np_all, (uint64_t)s.ldb * 2, BK, (uint32_t)s.NP,
                        CU_TENSOR_MAP_SWIZZLE_128B));
   else
     mapBlo = mapB;
@@ -835,6 +854,7 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   while (cols < (tsum ? 3 : 2) * ta.acc_stride) cols *= 2;
   ta.tmem_cols = cols;
   ta.mtiles = s.mtiles;
+  ta.ntiles = ntiles;
   ta.ksteps = s.ksteps;
   ta.ksteps_per_split = s.ksteps_per_split;
   ta.nsplit = s.nsplit;
@@ -865,7 +885,7 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
   ta.idesc = f16 ? ptx::idesc_f16_f32(BM, (uint32_t)s.NP) : ptx::idesc_bf16_f32(BM, (uint32_t)s.NP);
   if (src16 && trans) ta.idesc |= ptx::kIdescAMajorMN;
 
-  const int64_t units = s.mtiles * s.nsplit;
+  const int64_t units = s.mtiles * ntiles * s.nsplit;
   const int grid = (int)(units < num_sms() ? units : num_sms());
   constexpr size_t kSmemMax = 232448;
   auto need = [&](int sop, int depth) {
@@ -914,6 +934,27 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
 }
 
 }  // namespace
+
+size_t tc_gemm_wide_ws_bytes(int64_t M, int64_t K, int64_t N, int prec) {
+  const int np = (int)std::min<int64_t>(round_up(N, 16), prec == RSVD_PREC_BF16X3 ? kSplitMaxNP : 256);
+  const int64_t np_all = cdiv(N, np) * np;
+  Sizer z;
+  z.take<uint16_t>((size_t)np_all * round_up(K, 8));
+  if (prec == RSVD_PREC_BF16X3) z.take<uint16_t>((size_t)np_all * round_up(K, 8));
+  z.take<int>(4);
+  (void)M;
+  return z.used + 256;
+}
+
+rsvd_status tc_gemm_wide(const rsvd_matrix& A, int prec, int64_t N, const float* X, int64_t ldx, float* Y,
+                         int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream) {
+  if (N < 1 || N > 0x7fffffffLL || (prec != RSVD_PREC_BF16 && prec != RSVD_PREC_BF16X3) || A.dtype != RSVD_F32)
+    return fail(RSVD_ERR_INVALID_ARG, "tensor-core product: FP32 A, BF16 or BF16X3, N >= 1");
+  TcSource src;
+  src.A = &A;
+  src.wide = true;
+  return tc_apass_run(src, A.m, A.n, 0, prec, (int)N, X, ldx, Y, ldy, ws, ws_bytes, status, stream, false);
+}
 
 int64_t tc_ksteps_per_split(int64_t m, int64_t n, int r, int trans, int prec) {
   // a pass over column halves of the panel takes each half's own split

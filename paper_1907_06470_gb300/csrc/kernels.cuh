@@ -120,8 +120,9 @@ rsvd_status gather_colmajor_f64(int64_t rows, int64_t cols, const T* A, int64_t 
 // adjoint.cu -- backward pass of the truncated SVD.
 size_t backward_ws_bytes(int64_t m, int64_t n, int k, int dtype);
 template <typename T>
+// status: device word (4 ints) that an expired tensor-core wait is recorded in
 rsvd_status backward_typed(int64_t m, int64_t n, int k, const T* U, const T* S, const T* V, const T* dU,
-                           const T* dS, const T* dV, T* dA, void* ws, size_t ws_bytes, cudaStream_t st);
+                           const T* dS, const T* dV, T* dA, void* ws, size_t ws_bytes, int* status, cudaStream_t st);
 
 // spmm.cu -- A-passes for a CSR matrix (FP32 values, int32 indices).
 constexpr int kSpmmMaxR = 512;
@@ -229,6 +230,13 @@ rsvd_status tc_apass_from_f32(const rsvd_matrix& A, int trans, int prec, int r, 
                               size_t ws_bytes, int* status, cudaStream_t stream, bool accumulate = false,
                               uint16_t* copy16 = nullptr, int64_t ld16 = 0, uint16_t* copy16lo = nullptr,
                               int64_t kps = 0);
+// Y (M x N, ldy) = A X for an FP32 A (M x K, A.ld % 4 == 0, 16-byte aligned)
+// and X (K x N, ldx) with any N, in output tiles of up to 192 (split) or 256
+// columns: the tensor-core product of a short K and a wide output (the
+// adjoint's rank-2k product).  prec BF16 or BF16X3.
+size_t tc_gemm_wide_ws_bytes(int64_t M, int64_t K, int64_t N, int prec);
+rsvd_status tc_gemm_wide(const rsvd_matrix& A, int prec, int64_t N, const float* X, int64_t ldx, float* Y,
+                         int64_t ldy, void* ws, size_t ws_bytes, int* status, cudaStream_t stream);
 // The K steps per split a pass over an m x n A chooses (0 where the pass
 // runs over column halves of the panel).
 int64_t tc_ksteps_per_split(int64_t m, int64_t n, int r, int trans, int prec);
