@@ -452,6 +452,15 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
   for (; sweep < kJacobiMaxSweeps; ++sweep) {
     __syncthreads();
     if (tid == 0) { s_rot = 0; s_maxrel = 0; }
+    // squared column norms, exact at the start of each sweep and then carried
+    // through the rotations (||c m_p - s m_q||^2 = c^2 a - 2 c s g + s^2 b), so
+    // that each pair reduces only its inner product
+    for (int c = warp; c < r; c += warps) {
+      float s2 = 0.f;
+      for (int i = lane; i < r; i += 32) s2 = fmaf(M[c * ldm + i], M[c * ldm + i], s2);
+      s2 = warp_sum(s2);
+      if (lane == 0) nrm[c] = s2;
+    }
     __syncthreads();
     // whether this thread's pairs rotated in the sweep, and the largest relative
     // off-diagonal they rotated: kept in registers, reduced once per sweep
@@ -472,18 +481,17 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
         const float4* mp4 = reinterpret_cast<const float4*>(M + p * ldm);
         const float4* mq4 = reinterpret_cast<const float4*>(M + q * ldm);
         float4 xv[V], yv[V];
-        float a = 0.f, b = 0.f, g = 0.f;
+        const float a = active ? nrm[p] : 0.f, b = active ? nrm[q] : 0.f;
+        float g = 0.f;
 #pragma unroll
         for (int t = 0; t < V; ++t) {
           const int i4 = hl + 16 * t;
           const bool ok = active && i4 < ld4;
           xv[t] = ok ? mp4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
           yv[t] = ok ? mq4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
-          a = fmaf(xv[t].x, xv[t].x, fmaf(xv[t].y, xv[t].y, fmaf(xv[t].z, xv[t].z, fmaf(xv[t].w, xv[t].w, a))));
-          b = fmaf(yv[t].x, yv[t].x, fmaf(yv[t].y, yv[t].y, fmaf(yv[t].z, yv[t].z, fmaf(yv[t].w, yv[t].w, b))));
           g = fmaf(xv[t].x, yv[t].x, fmaf(xv[t].y, yv[t].y, fmaf(xv[t].z, yv[t].z, fmaf(xv[t].w, yv[t].w, g))));
         }
-        a = half_warp_sum(a); b = half_warp_sum(b); g = half_warp_sum(g);
+        g = half_warp_sum(g);
         if (active && fabsf(g) > tol * sqrtf(a * b) && a > zero2 && b > zero2) {
           my_rot = true;
           my_mrel = fmaxf(my_mrel, fabsf(g) * rsqrtf(a * b));
@@ -499,6 +507,11 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
           float c = rsqrtf(x);
           c = c * fmaf(-0.5f * x, c * c, 1.5f);
           const float sn = c * t;
+          if (hl == 0) {
+            const float cc = c * c, ss = sn * sn, cs2 = 2.f * c * sn * g;
+            nrm[p] = fmaxf(fmaf(cc, a, fmaf(ss, b, -cs2)), 0.f);
+            nrm[q] = fmaxf(fmaf(ss, a, fmaf(cc, b, cs2)), 0.f);
+          }
           float4* mp = reinterpret_cast<float4*>(M + p * ldm);
           float4* mq = reinterpret_cast<float4*>(M + q * ldm);
           float4* wp = reinterpret_cast<float4*>(W + p * ldm);
