@@ -667,7 +667,7 @@ def run_sparse(args):
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
     nnz = int(rp[-1].item())
-    streamed = args.csr_cap_gb > 0
+    streamed = args.csr_cap_gb > 0 or args.csr_resident_gb >= 0
     pin = (lambda t: t.pin_memory()) if streamed else (lambda t: t)
     A_host = torch.sparse_csr_tensor(pin(rp.cpu()), pin(ci.cpu()), pin(v.cpu()), size=(m, n))
     t0 = time.perf_counter()
@@ -686,7 +686,16 @@ def run_sparse(args):
         del A_host
     torch.cuda.empty_cache()
     cap = int(args.csr_cap_gb * (1 << 30))
-    plan = g.Plan(m, n, k, p, q, w.seed, prec="fp32", kind="csr", mem_cap=cap)
+    if args.csr_resident_gb >= 0:
+        # the plan's own workspace plus this many GB for CSR blocks
+        import ctypes as C
+        from paper_1907_06470_gb300 import _lib
+        o = _lib.RsvdOpts(prec=_lib.PREC[args.csr_prec], refine=1, mb=0, nb=0, n_slots=2,
+                          dtype=_lib.DTYPE["f32"], kind=_lib.CSR)
+        out = C.c_size_t()
+        _lib.check(g.load().rsvd_plan_min_cap(m, n, k, p, C.byref(o), C.byref(out)))
+        cap = out.value + int(args.csr_resident_gb * (1 << 30))
+    plan = g.Plan(m, n, k, p, q, w.seed, prec=args.csr_prec, kind="csr", mem_cap=cap)
     plan.set_profiling(True)
     U, S, V = plan.run(A, At=At)
     torch.cuda.synchronize()
@@ -722,6 +731,9 @@ def run_sparse(args):
         return nnz * 8 + (M + 1) * 4 + K * ldr * 4 + M * ldr * 4
 
     peaks, peak_kind = _peaks()
+    # bytes per gathered panel value of the forward passes (all range-finder
+    # passes: compact for BF16 / BF16X3 plans)
+    bpv = {"fp32": 4, "bf16x3": 3, "bf16": 2}[args.csr_prec]
     fb = algo_bytes(m, n)
     tb = algo_bytes(n, m)
     roof = {"bound": "hbm", "kernel": "spmm_csr_vec_kernel (forward A-pass)",
@@ -730,8 +742,8 @@ def run_sparse(args):
             # the gathers hit L2 at a rate that depends on the size: a smaller
             # capture does not scale, so no traffic figure for this kernel
             "avg_launch_ms": fwd_ms, "traffic": None,
-            "gathered_panel_bytes_per_launch": nnz * ldr * 4,
-            "gather_GBps": nnz * ldr * 4 / (fwd_ms / 1e3) / 1e9}
+            "gathered_panel_bytes_per_launch": nnz * ldr * bpv,
+            "gather_GBps": nnz * ldr * bpv / (fwd_ms / 1e3) / 1e9}
     roof["frac"] = roof["achieved"] / roof["peak"]
     # The pass is bound by the gathers of panel rows (one ldr-float row per
     # entry), not by A's bytes: measure what the same kernel gathers per second
@@ -766,6 +778,41 @@ def run_sparse(args):
         "all_miss_TBps": ceil["dram"], "frac_of_l2_resident": roof["gather_GBps"] / 1e3 / ceil["l2_resident"],
         "how": "the same SpMM kernel on synthetic CSRs, 1e8 entries, rows of 128, uniform columns over 40000 "
                "(panel in L2) or over n (panel far larger than L2)"}
+    # the other panel precisions on the same matrix (in core): time per rSVD
+    # and per pass, and the top-k singular values against the FP32 plan's
+    paths = {}
+    if not args.no_compare and not streamed:
+        ref_S = None
+        for pp in ("fp32", "bf16x3", "bf16"):
+            if pp == args.csr_prec:
+                Sp, ms_p, f_p, t_p = S, ms, fwd_ms, tr_ms
+            else:
+                pl = g.Plan(m, n, k, p, q, w.seed, prec=pp, kind="csr")
+                pl.set_profiling(True)
+                Up, Sp, Vp = pl.run(A, At=At)
+                torch.cuda.synchronize()
+                q0 = torch.cuda.Event(enable_timing=True)
+                q1 = torch.cuda.Event(enable_timing=True)
+                q0.record(stream)
+                pl.run(A, Up, Sp, Vp, At=At)
+                q1.record(stream)
+                torch.cuda.synchronize()
+                sm = pl.stage_ms()
+                ms_p = q0.elapsed_time(q1)
+                f_p, t_p = sm["apass_fwd"] / fwd_calls, sm["apass_trans"] / tr_calls
+                pl.close()
+                del Up, Vp
+                torch.cuda.empty_cache()
+            Sv = Sp[:k].double().cpu()
+            if pp == "fp32":
+                ref_S = Sv
+            paths[pp] = {"ms_per_rsvd": ms_p, "forward_pass_ms": f_p, "transposed_pass_ms_mean": t_p,
+                         "panel_bytes_per_value": {"fp32": 4, "bf16x3": 3, "bf16": 2}[pp],
+                         "sigma_rel_diff_vs_fp32_plan": None if ref_S is None else
+                         float(((Sv - ref_S).abs() / ref_S).max())}
+        paths["note"] = ("range-finder passes gather the panel at 4 / 3 / 2 bytes per value; the final "
+                         "B^T = A^T Q gathers FP32 in every plan; the BF16X3 plan meets the FP32 bars against "
+                         "the FP64 oracle at the scaled size (tests/test_gpu_sparse.py)")
     link = None
     if streamed:
         st = plan.stream_stats()
@@ -778,12 +825,12 @@ def run_sparse(args):
     print(json.dumps({
         "mode": "csr", "workload": w.name if (m, n) == (w.m, w.n) else f"{w.name} scaled to {m}x{n}",
         "out_of_core": link,
-        "m": m, "n": n, "nnz": nnz, "k": k, "p": p, "q": q, "prec": "fp32", "steps": args.steps,
+        "m": m, "n": n, "nnz": nnz, "k": k, "p": p, "q": q, "prec": args.csr_prec, "steps": args.steps,
         "ms_per_rsvd": ms, "rsvd_per_s": 1e3 / ms, "apass_calls_per_rsvd": calls,
         "forward_pass_ms": fwd_ms, "transposed_pass_ms": tr_ms,
         "transposed_GBps_algorithmic": tb / (tr_ms / 1e3) / 1e9,
         "stages_ms_per_rsvd": {kk: vv / args.steps for kk, vv in stage_sum.items() if kk != "apass_calls"},
-        "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+        "roofline": roof, "clocks": clocks, "gpu_launches": launches, "paths": paths or None,
         "setup_s": {"generate_on_gpu": t_gen, "host_transpose": t_tr},
         "S_head": [float(x) for x in S[:4].cpu()],
     }))
@@ -807,6 +854,10 @@ def main():
     ap.add_argument("--csr-nnz", type=int, default=500_000_000)
     ap.add_argument("--csr-cap-gb", type=float, default=0.0,
                     help="device cap for the sparse workload: > 0 streams the host CSR out of core")
+    ap.add_argument("--csr-prec", default="fp32", choices=["fp32", "bf16x3", "bf16"],
+                    help="sparse workload: panel precision of the range-finder passes")
+    ap.add_argument("--csr-resident-gb", type=float, default=-1.0,
+                    help=">= 0: stream the host CSR under a cap of the plan's minimum plus this many GB")
     ap.add_argument("--ooc-rows", type=int, default=150000)
     ap.add_argument("--ooc-cap-gb", type=float, default=16.0)
     ap.add_argument("--ooc-tile", type=int, default=0, help="square tile edge (0: planner default)")

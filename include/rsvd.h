@@ -74,7 +74,11 @@ typedef struct {
   int32_t n_slots;   /* block-cyclic slots = copy/compute buffer pairs (default 2) */
   int32_t dtype;     /* rsvd_dtype of A and of the outputs: F64 or F32 (default F32) */
   int32_t kind;      /* rsvd_kind of the matrices this plan runs on (default DENSE);
-                        CSR plans take dtype F32 and prec FP32 */
+                        CSR plans take dtype F32 and prec FP32, BF16 or
+                        BF16X3: the range-finder passes of BF16 / BF16X3 CSR
+                        plans gather the panel rounded to BF16 / to 24 bits
+                        (see rsvd_apass), their final B^T = A^T Q an FP32
+                        panel */
   int32_t auto_q;    /* 1: choose the number of power iterations automatically,
                         with q (rsvd_plan) as the maximum (Section 2.2): after i
                         iterations the singular values sigma^(i) of B_i = Q_i^T A
@@ -169,7 +173,7 @@ typedef struct {
  * (0 = no cap: run in core when A fits, the paper's default in Section 3.5).
  * Rules: 1 <= k, 0 <= p, k + p <= min(m, n), 0 <= q <= 64, and k + p <= 256
  * for dense plans, k + p <= 512 for CSR plans (opts.kind = CSR: dtype F32,
- * prec FP32; they hold no backward workspace).
+ * prec FP32, BF16 or BF16X3; they hold no backward workspace).
  * Errors: INVALID_ARG, CAP_TOO_SMALL (see rsvd_plan_min_cap), OOM, CUDA.
  * On success *out receives a plan that must be released with rsvd_destroy. */
 rsvd_status rsvd_plan(int64_t m, int64_t n, int k, int p, int q, uint64_t seed,
@@ -397,15 +401,32 @@ rsvd_status rsvd_small_svd(int32_t r, const double* Mc, double* sigma, double* U
 
 /* Section 3.3 (sparse x dense product): Y = A X (trans = 0, CSR of A) or
  * Y = A^T X (trans = 1, using A.t_rowptr/t_colidx/t_val, which must be set)
- * for a CSR device matrix with FP32 values, FP32 panels, FP32 accumulation in
- * entry order (deterministic).  X: K x r row-major (ldx), Y: M x r row-major
- * (ldy), overwritten; r <= 512.  Goes through rsvd_apass with prec FP32 (mb,
- * nb ignored).  The workspace is optional: ws may be NULL, and then every row
- * is summed by one warp; with ws_bytes >= rsvd_spmm_workspace(A.nnz, r), rows
- * of more than 4096 entries are split into 4096-entry segments summed by
- * separate warps and added in segment order (same result for any timing).
- * A.nnz must equal rowptr[M] of the CSR used.  Enqueues only. */
+ * for a CSR device matrix with FP32 values and FP32 accumulation in entry
+ * order (deterministic).  X: K x r row-major FP32 (ldx), Y: M x r row-major
+ * (ldy), overwritten; r <= 512.  Goes through rsvd_apass (mb, nb ignored)
+ * with prec
+ *   FP32    the panel X as given;
+ *   BF16    X rounded to BF16 (round to nearest even) before the gathers;
+ *   BF16X3  X rounded to 24-bit floats (sign, 8-bit exponent, 15 stored
+ *           mantissa bits; round to nearest even on the FP32 bits), stored as
+ *           a BF16 high part and a low byte: 3 bytes per gathered value,
+ *           relative rounding error below 2^-16.
+ * The gathers of panel rows (r values per stored entry) bound the pass, so
+ * the compact panels move 1/2 and 3/4 of the FP32 bytes.  BF16 / BF16X3
+ * passes need ws (16-byte aligned) of rsvd_csr_apass_workspace(A.nnz, K, r,
+ * prec) bytes and ldy % 4 == 0 with Y 16-byte aligned.  For FP32 the
+ * workspace is optional: ws may be NULL, and then every row is summed by one
+ * warp; with ws_bytes >= rsvd_spmm_workspace(A.nnz, r), rows of more than
+ * 1024 entries are split into 1024-entry segments summed by separate warps and
+ * added in segment order (same result for any timing; the compact passes
+ * always split).  A.nnz must equal rowptr[M] of the CSR used.  Enqueues only. */
 size_t rsvd_spmm_workspace(int64_t nnz, int32_t r);
+
+/* Workspace bytes of rsvd_apass on a CSR matrix with nnz entries whose panel X
+ * has K rows (K = n for trans = 0, m for trans = 1), r columns, precision
+ * prec (FP32: rsvd_spmm_workspace(nnz, r); BF16, BF16X3: that plus the
+ * compact panel).  0 for r < 1 or K < 0. */
+size_t rsvd_csr_apass_workspace(int64_t nnz, int64_t K, int32_t r, int32_t prec);
 
 /* Host (CPU) transpose of a CSR matrix: from the CSR of the m x n matrix A
  * (rowptr m+1, colidx and val nnz = rowptr[m]) writes the CSR of A^T into

@@ -21,6 +21,9 @@ tiles     Block-cyclic tile map (Section 1, Section 3.1) and CSR tiles.
 rsvd      The randomized SVD with power iterations (Section 2.1 steps 1-7,
           Section 2.2 Eq. (2)/(3)) and the exact full SVD.
 adjoint   Truncated-SVD adjoint (not in the paper; Townsend 2016).
+panel     FP32 panels rounded to BF16 or to 24-bit floats (Section 3.2's
+          choice of number precision, applied to the gathered panel of the
+          sparse products of Section 3.3).
 
 Parity pins: every function above is pinned by a test in ``tests/`` except
 where its docstring says "parity unpinned".

@@ -324,18 +324,23 @@ def apass(A, X, trans=False, prec=None, mb=0, nb=0, out=None, At=None, split_lon
     """One A-pass: A @ X (trans=False) or A.T @ X (trans=True), on the library's kernels.
 
     A sparse CSR A (CUDA, float32) needs `At`, the CSR of A^T, for trans=True;
-    `split_long_rows` gives the call the workspace that splits long rows."""
+    `split_long_rows` gives the call the workspace that splits long rows (the
+    compact panels of prec "bf16" / "bf16x3" always have it)."""
     torch = _torch()
     if _is_csr(A):
         m, n = A.shape
         r = X.shape[1]
+        prec = prec or "fp32"
         if out is None:
-            out = torch.empty(n if trans else m, r, dtype=torch.float32, device=A.device)
+            out = torch.empty(n if trans else m, (r + 3) // 4 * 4, dtype=torch.float32, device=A.device)[:, :r]
         d, keep = _csr_desc(A, At)
         lib = load()
-        wsb = lib.rsvd_spmm_workspace(d.nnz, r) if split_long_rows else 0
+        if prec == "fp32":
+            wsb = lib.rsvd_spmm_workspace(d.nnz, r) if split_long_rows else 0
+        else:
+            wsb = lib.rsvd_csr_apass_workspace(d.nnz, m if trans else n, r, _lib.PREC[prec])
         ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=A.device)
-        _check(lib.rsvd_apass(C.byref(d), int(trans), _lib.PREC["fp32"], r, C.c_void_p(X.data_ptr()),
+        _check(lib.rsvd_apass(C.byref(d), int(trans), _lib.PREC[prec], r, C.c_void_p(X.data_ptr()),
                               X.stride(0), C.c_void_p(out.data_ptr()), out.stride(0), 0, 0,
                               C.c_void_p(ws.data_ptr() if wsb else None), wsb, _stream_ptr()))
         del keep

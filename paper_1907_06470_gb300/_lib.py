@@ -85,6 +85,7 @@ SIGNATURES = {
                               C.POINTER(c_i64)]),
     "rsvd_coo_to_csr": (c_i32, [c_i64, c_i64, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "rsvd_spmm_workspace": (c_size, [c_i64, c_i32]),
+    "rsvd_csr_apass_workspace": (c_size, [c_i64, c_i64, c_i32, c_i32]),
     "rsvd_plan_set_checkpoint": (c_i32, [c_vp, C.c_char_p, c_i32]),
     "rsvd_checkpoint_info": (c_i32, [C.c_char_p, C.POINTER(RsvdCheckpointInfo)]),
     "rsvd_fp8_quantize": (c_i32, [C.POINTER(RsvdMatrix), c_i64, c_i64, c_vp, c_i64, c_vp, c_vp]),

@@ -215,6 +215,8 @@ struct rsvd_plan_s {
   void* Qb = nullptr;   // n x ldr
   void* apass_ws = nullptr;
   size_t apass_ws_bytes = 0;
+  uint16_t* pk_h = nullptr;  // CSR plans of BF16 / BF16X3 precision: the panel in 16 bits
+  uint8_t* pk_l = nullptr;   // and, for BF16X3, its next 8 bits (24-bit panel)
   OrthWs orth;
   JacobiWs jac;
   double* R = nullptr;      // r x r
@@ -284,8 +286,9 @@ rsvd_status check_args(int64_t m, int64_t n, int k, int p, int q, const rsvd_opt
   if (o && o->kind != RSVD_DENSE && o->kind != RSVD_CSR) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: unknown kind");
   if (!csr && r > 256) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: k + p must not exceed 256 (dense)");
   if (csr && r > kSpmmMaxR) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: k + p must not exceed 512 (CSR)");
-  if (csr && (o->dtype != RSVD_F32 || o->prec != RSVD_PREC_FP32))
-    return fail(RSVD_ERR_UNSUPPORTED, "rsvd_plan: CSR plans take F32 values and FP32 precision");
+  if (csr && (o->dtype != RSVD_F32 ||
+              (o->prec != RSVD_PREC_FP32 && o->prec != RSVD_PREC_BF16 && o->prec != RSVD_PREC_BF16X3)))
+    return fail(RSVD_ERR_UNSUPPORTED, "rsvd_plan: CSR plans take F32 values and FP32, BF16 or BF16X3 precision");
   if (o) {
     if (o->dtype != RSVD_F32 && o->dtype != RSVD_F64)
       return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan: dtype must be F32 or F64");
@@ -337,7 +340,11 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   P->Qm = c.take<char>((size_t)P->m * P->ldr * esz);
   P->Bt = c.take<char>((size_t)P->n * P->ldr * esz);
   P->Qb = c.take<char>((size_t)P->n * P->ldr * esz);
-  const bool dense = P->kind == RSVD_DENSE;  // CSR passes need no workspace
+  const bool dense = P->kind == RSVD_DENSE;  // CSR passes need no workspace here
+  if (!dense && (P->prec == RSVD_PREC_BF16 || P->prec == RSVD_PREC_BF16X3)) {
+    P->pk_h = c.take<uint16_t>((size_t)mx * P->ldr);
+    P->pk_l = P->prec == RSVD_PREC_BF16X3 ? c.take<uint8_t>((size_t)mx * P->ldr) : nullptr;
+  }
   const size_t a0 = dense ? apass_ws_bytes(P->m, P->n, P->r, 0, P->prec, P->mb, P->nb) : 0;
   const size_t a1 = dense ? apass_ws_bytes(P->m, P->n, P->r, 1, P->prec, P->mb, P->nb) : 0;
   size_t a2 = 0;
@@ -399,8 +406,12 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
   T* Bt = static_cast<T*>(P->Bt);
   T* Qb = static_cast<T*>(P->Qb);
   const int prec = P->prec;
-  const int final_prec =
-      ((prec == RSVD_PREC_BF16 || prec == RSVD_PREC_FP8) && P->refine) ? RSVD_PREC_BF16X3 : prec;
+  // the final B^T = A^T Q: split BF16 for dense BF16 / FP8 plans (refine);
+  // an FP32 panel for CSR plans whose range finder gathers compact panels
+  const bool csr_compact = P->kind == RSVD_CSR && (prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3);
+  const int final_prec = csr_compact ? RSVD_PREC_FP32
+                         : ((prec == RSVD_PREC_BF16 || prec == RSVD_PREC_FP8) && P->refine) ? RSVD_PREC_BF16X3
+                                                                                             : prec;
   Profiler& pf = P->prof;
   // BF16 plans in core stream a BF16 copy of A after the first plain forward
   // pass has written it: half the bytes per pass, the same operands.  BF16X3
@@ -520,13 +531,26 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
       }
     }
     if constexpr (std::is_same<T, float>::value) {
-      if (A.kind == RSVD_CSR && P->csr_streaming)  // Sections 3.5, 3.7: CSR tiles streamed from the host
-        return csr_apass_streamed(P->cs, trans, r, Xin, ldr, Yout, ldr, st);
-      if (A.kind == RSVD_CSR)  // Section 3.3: sparse x dense; A^T through the CSR of A^T
-        return trans ? spmm_csr(n, r, A.t_rowptr, A.t_colidx, A.t_val, A.nnz, Xin, ldr, Yout, ldr, false,
-                                P->spmm_ws, P->spmm_ws_bytes, st)
-                     : spmm_csr(m, r, A.rowptr, A.colidx, A.val, A.nnz, Xin, ldr, Yout, ldr, false, P->spmm_ws,
-                                P->spmm_ws_bytes, st);
+      if (A.kind == RSVD_CSR) {
+        // Section 3.3: sparse x dense; A^T through the CSR of A^T.  BF16 and
+        // BF16X3 passes gather the panel rounded to 16 or 24 bits.
+        SpmmPanel px;
+        px.f = Xin;
+        px.ld = ldr;
+        if (pr == RSVD_PREC_BF16 || pr == RSVD_PREC_BF16X3) {
+          px.fmt = pr == RSVD_PREC_BF16 ? 1 : 2;
+          RSVD_TRY(spmm_pack(px.fmt, trans ? m : n, r, Xin, ldr, P->pk_h, P->pk_l, ldr, st));
+          px.f = nullptr;
+          px.h = P->pk_h;
+          px.l = px.fmt == 2 ? P->pk_l : nullptr;
+        }
+        if (P->csr_streaming)  // Sections 3.5, 3.7: CSR tiles streamed from the host
+          return csr_apass_streamed(P->cs, trans, r, px, Yout, ldr, st);
+        return trans ? spmm_csr_panel(n, r, A.t_rowptr, A.t_colidx, A.t_val, A.nnz, px, Yout, ldr, false,
+                                      P->spmm_ws, P->spmm_ws_bytes, st)
+                     : spmm_csr_panel(m, r, A.rowptr, A.colidx, A.val, A.nnz, px, Yout, ldr, false, P->spmm_ws,
+                                      P->spmm_ws_bytes, st);
+      }
     }
     if (P->streaming) return apass_streamed(P->ss, A, trans, pr, r, Xin, Yout, ldr, P->status, st);
     if constexpr (std::is_same<T, float>::value) {
@@ -580,7 +604,11 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
     RSVD_CUDA(cudaMemsetAsync(P->status, 0, 4 * sizeof(int), st));
     if (first_step == 0) {  // step 1: Gaussian test matrix (n x r); X may hold a resumed Z otherwise
       Span sp(pf, RSVD_STAGE_GAUSSIAN, st);
-      const bool bf16_panel = prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3 || prec == RSVD_PREC_FP8;
+      // BF16-valued test matrices for the tensor-core and BF16-panel paths; the
+      // 24-bit panels of CSR BF16X3 plans round an FP32 test matrix
+      const bool bf16_panel = A.kind == RSVD_CSR ? prec == RSVD_PREC_BF16
+                                                 : (prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3 ||
+                                                    prec == RSVD_PREC_FP8);
       RSVD_TRY(launch_gaussian(P->seed, n, r, bf16_panel ? kF32HoldingBf16 : P->dtype, 0, X, ldr, st));
     }
     if constexpr (std::is_same<T, float>::value) {
@@ -957,6 +985,18 @@ rsvd_status rsvd_tile_map(int64_t m, int64_t n, int64_t mb, int64_t nb, int32_t 
 
 size_t rsvd_spmm_workspace(int64_t nnz, int32_t r) { return spmm_ws_bytes(nnz < 0 ? 0 : nnz, r); }
 
+size_t rsvd_csr_apass_workspace(int64_t nnz, int64_t K, int32_t r, int32_t prec) {
+  if (r < 1 || K < 0) return 0;
+  const size_t sws = spmm_ws_bytes(nnz < 0 ? 0 : nnz, r);
+  if (prec != RSVD_PREC_BF16 && prec != RSVD_PREC_BF16X3) return sws;
+  const int64_t ld = round_up(r, 4);
+  Sizer z;
+  z.take<char>(sws);
+  z.take<uint16_t>((size_t)K * ld);
+  if (prec == RSVD_PREC_BF16X3) z.take<uint8_t>((size_t)K * ld);
+  return z.used + 256;
+}
+
 size_t rsvd_apass_workspace(int64_t m, int64_t n, int32_t r, int32_t trans, int32_t prec, int64_t mb,
                             int64_t nb) {
   if (prec == RSVD_PREC_FP8) {
@@ -998,15 +1038,42 @@ rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_
   if (!A || !X || !Y || r < 1 || (trans != 0 && trans != 1) || ldx < r || ldy < r)
     return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: bad arguments");
   if (A->kind == RSVD_CSR) {
-    if (r > kSpmmMaxR || prec != RSVD_PREC_FP32 || A->dtype != RSVD_F32 || A->location != RSVD_ON_DEVICE)
-      return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: CSR needs a device F32 matrix, prec FP32, r <= 512");
+    if (r > kSpmmMaxR || A->dtype != RSVD_F32 || A->location != RSVD_ON_DEVICE ||
+        (prec != RSVD_PREC_FP32 && prec != RSVD_PREC_BF16 && prec != RSVD_PREC_BF16X3))
+      return fail(RSVD_ERR_INVALID_ARG,
+                  "rsvd_apass: CSR needs a device F32 matrix, prec FP32, BF16 or BF16X3, r <= 512");
     const int32_t* rp = trans ? A->t_rowptr : A->rowptr;
     const int32_t* ci = trans ? A->t_colidx : A->colidx;
     const float* v = trans ? A->t_val : A->val;
     if (!rp || (A->nnz > 0 && (!ci || !v)))
       return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: CSR arrays missing (trans = 1 needs t_rowptr/t_colidx/t_val)");
-    return spmm_csr(trans ? A->n : A->m, r, rp, ci, v, A->nnz, static_cast<const float*>(X), ldx,
-                    static_cast<float*>(Y), ldy, false, ws, ws_bytes, as_stream(stream));
+    const int64_t M = trans ? A->n : A->m, K = trans ? A->m : A->n;
+    SpmmPanel px;
+    px.f = static_cast<const float*>(X);
+    px.ld = ldx;
+    void* sws = ws;
+    size_t sws_bytes = ws_bytes;
+    if (prec != RSVD_PREC_FP32) {
+      // the workspace holds the split-row tasks, then the compact panel
+      const size_t need = rsvd_csr_apass_workspace(A->nnz, K, r, prec);
+      if (!ws || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 16 != 0)
+        return fail(RSVD_ERR_INVALID_ARG,
+                    "rsvd_apass: CSR BF16 / BF16X3 passes need rsvd_csr_apass_workspace bytes, 16-byte aligned");
+      const int64_t ld = round_up(r, 4);
+      Carver c(ws, ws_bytes);
+      sws_bytes = spmm_ws_bytes(A->nnz, r);
+      sws = c.take<char>(sws_bytes);
+      uint16_t* h = c.take<uint16_t>((size_t)K * ld);
+      uint8_t* l = prec == RSVD_PREC_BF16X3 ? c.take<uint8_t>((size_t)K * ld) : nullptr;
+      px.fmt = prec == RSVD_PREC_BF16 ? 1 : 2;
+      RSVD_TRY(spmm_pack(px.fmt, K, r, static_cast<const float*>(X), ldx, h, l, ld, as_stream(stream)));
+      px.f = nullptr;
+      px.h = h;
+      px.l = l;
+      px.ld = ld;
+    }
+    return spmm_csr_panel(M, r, rp, ci, v, A->nnz, px, static_cast<float*>(Y), ldy, false, sws, sws_bytes,
+                          as_stream(stream));
   }
   if (r > 256) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: r must not exceed 256 (dense)");
   if (A->kind == RSVD_DENSE && A->ld < A->n) return fail(RSVD_ERR_INVALID_ARG, "rsvd_apass: ld < n");

@@ -335,7 +335,7 @@ void csr_stream_begin_run(CsrStream* s) {
   for (auto& o : s->o) std::fill(o.cache_valid.begin(), o.cache_valid.end(), 0);
 }
 
-rsvd_status csr_apass_streamed(CsrStream* s, int trans, int r, const float* X, int64_t ldx, float* Y, int64_t ldy,
+rsvd_status csr_apass_streamed(CsrStream* s, int trans, int r, const SpmmPanel& X, float* Y, int64_t ldy,
                                cudaStream_t st) {
   CsrOrient& o = s->o[trans ? 1 : 0];
   if (o.col_tiled) RSVD_CUDA(cudaMemsetAsync(Y, 0, (size_t)o.M * ldy * sizeof(float), st));
@@ -365,8 +365,12 @@ rsvd_status csr_apass_streamed(CsrStream* s, int trans, int r, const float* X, i
       s->h2d_bytes += T.bytes();
       if (cached) o.cache_valid[t] = 1;
     }
-    RSVD_TRY(spmm_csr(T.rows, r, d_rp, d_ci, d_v, T.nnz, X + T.col0 * ldx, ldx, Y + T.row0 * ldy, ldy,
-                      o.col_tiled, s->sws, s->sws_bytes, st));
+    SpmmPanel xt = X;  // the panel rows of the tile's columns
+    if (xt.f) xt.f += T.col0 * xt.ld;
+    if (xt.h) xt.h += T.col0 * xt.ld;
+    if (xt.l) xt.l += T.col0 * xt.ld;
+    RSVD_TRY(spmm_csr_panel(T.rows, r, d_rp, d_ci, d_v, T.nnz, xt, Y + T.row0 * ldy, ldy, o.col_tiled, s->sws,
+                            s->sws_bytes, st));
     if (!cached) RSVD_CUDA(cudaEventRecord(s->freed[slot], st));
   }
   return RSVD_OK;

@@ -128,11 +128,27 @@ rsvd_status backward_typed(int64_t m, int64_t n, int k, const T* U, const T* S, 
 constexpr int kSpmmMaxR = 512;
 // Rows with more entries than this are split into segments of this many
 // entries, one warp each, when the workspace allows.
-constexpr int kSpmmSeg = 4096;
+constexpr int kSpmmSeg = 1024;
 // Upper bound on the segment tasks of a matrix with nnz entries: each long
 // row of len entries takes ceil(len/kSpmmSeg) < 2 len/kSpmmSeg tasks.
 inline int64_t spmm_max_tasks(int64_t nnz) { return 2 * (nnz / kSpmmSeg) + 1; }
 size_t spmm_ws_bytes(int64_t nnz, int r);
+// The dense panel of a CSR A-pass: fmt 0 FP32 rows (f); fmt 1 BF16 rows (h);
+// fmt 2 24-bit rows, high 16 bits in h and the next 8 bits in l.  ld values
+// per row in every array (a multiple of 4 for fmt 1 and 2).
+struct SpmmPanel {
+  int fmt = 0;
+  const float* f = nullptr;
+  const uint16_t* h = nullptr;
+  const uint8_t* l = nullptr;
+  int64_t ld = 0;
+};
+// Rows of X (K x r, ldx) rounded into the compact formats (fmt 1 or 2).
+rsvd_status spmm_pack(int fmt, int64_t K, int r, const float* X, int64_t ldx, uint16_t* h, uint8_t* l, int64_t ld,
+                      cudaStream_t stream);
+rsvd_status spmm_csr_panel(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
+                           int64_t nnz, const SpmmPanel& X, float* Y, int64_t ldy, bool accumulate, void* ws,
+                           size_t ws_bytes, cudaStream_t stream);
 // Y (M x r, ldy) = (or +=) A X for the M-row CSR (rowptr, colidx, val; nnz
 // entries), X row-major (ldx).  ws (may be NULL) enables the long-row split.
 rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
@@ -189,7 +205,7 @@ struct CsrStream;
 rsvd_status csr_stream_prepare(CsrStream** ps, const rsvd_matrix& A, int64_t mb_req, int64_t nb_req, int slots,
                                size_t budget, int r);
 void csr_stream_begin_run(CsrStream* s);
-rsvd_status csr_apass_streamed(CsrStream* s, int trans, int r, const float* X, int64_t ldx, float* Y, int64_t ldy,
+rsvd_status csr_apass_streamed(CsrStream* s, int trans, int r, const SpmmPanel& X, float* Y, int64_t ldy,
                                cudaStream_t st);
 void csr_stream_free(CsrStream* s);
 void csr_stream_stats(const CsrStream* s, uint64_t* h2d, int64_t* per_pass, int64_t* cached);

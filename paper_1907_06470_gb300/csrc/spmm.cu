@@ -4,19 +4,27 @@
 //   forward     Y = A X      one warp per row of A
 //   transposed  Z = A^T Y    the same kernel on the CSR of A^T (the CSC of A)
 //
-// Each warp owns one output row.  The row's entries are read 32 at a time
-// (one (column, value) pair per lane, coalesced), then broadcast lane by lane;
-// for each entry the warp gathers one row of the dense panel (r values, 16-byte
-// vector loads, lane l holding columns 4l..4l+3 + 128t) and accumulates in
-// FP32 registers in entry order, so every output row is a fixed sequence of
-// FMAs and the result does not depend on scheduling.  The gathers dominate: a
-// pass reads nnz * r * 4 bytes of panel rows, which the Zipf-skewed column
-// popularity of the sparse workloads serves largely from L2.
+// Each output row is computed by one warp.  The row's entries are read 32 at
+// a time (one (column, value) pair per lane, coalesced), then broadcast lane
+// by lane; for each entry the warp gathers one row of the dense panel (r
+// values, 16-byte vector loads, lane l holding columns 4l..4l+3 + 128t) and
+// accumulates in FP32 registers in entry order, so every output row is a fixed
+// sequence of FMAs and the result does not depend on scheduling.  The gathers
+// dominate: a pass reads nnz * r * 4 bytes of panel rows, which the
+// Zipf-skewed column popularity of the sparse workloads serves largely from L2.
+//
+// The grid is persistent (the resident blocks of every SM) and its warps draw
+// rows kSpmmGrab at a time from a counter, so a warp that drew short rows
+// draws again instead of idling beside a long row of its block.  The CSR
+// arrays and the output are touched once per pass and move with streaming
+// (evict-first) loads and stores, leaving L2 to the gathered panel rows.
 //
 // The CSR of A^T is built on the host once (csr_transpose_host): a stable
 // counting sort over columns, split over threads by row ranges, so its entry
 // order (increasing row of A within each column) and hence the transposed
 // pass are deterministic.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <thread>
 #include <vector>
@@ -28,6 +36,7 @@ namespace rsvd {
 namespace {
 
 constexpr int kSpmmThreads = 256;
+constexpr int kSpmmGrab = 2;  // rows a warp takes per draw
 
 __device__ __forceinline__ void fma4(float4& a, float v, const float4& x) {
   a.x = fmaf(v, x.x, a.x);
@@ -36,21 +45,76 @@ __device__ __forceinline__ void fma4(float4& a, float v, const float4& x) {
   a.w = fmaf(v, x.w, a.w);
 }
 
-// V4 float4 slots per lane: panel rows of at most 128*V4 floats.  X rows start
-// 16-byte aligned (X aligned, ldx % 4 == 0); columns r..4*ceil(r/4)-1 are read
-// (inside ldx) but never written to Y.
+// The gathered panel, in one of three formats (SpmmPanel::fmt):
+//   0  FP32 rows (f, ld floats per row)
+//   1  BF16 rows (h, ld 16-bit values per row): X rounded to BF16
+//   2  24-bit rows split in two arrays (h: the high 16 bits, l: the next 8
+//      bits, ld values per row each): X rounded to 16 significant bits, the
+//      value's bits being h << 16 | l << 8
+// Lane l of a warp holds the values 4l..4l+3 + 128t of a row, so a lane loads
+// one float4 (FP32), one uint2 (the 16-bit parts) and one uint32 (the low
+// bytes) per slot t.
+template <int FMT>
+struct PanelSlot;
+
+template <>
+struct PanelSlot<0> {
+  float4 v;
+  __device__ __forceinline__ void load(const SpmmPanel& P, int64_t row, int q) {
+    v = __ldg(reinterpret_cast<const float4*>(P.f + row * P.ld) + q);
+  }
+  __device__ __forceinline__ void zero() { v = make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ __forceinline__ float4 get() const { return v; }
+};
+
+template <>
+struct PanelSlot<1> {
+  uint2 h;
+  __device__ __forceinline__ void load(const SpmmPanel& P, int64_t row, int q) {
+    h = __ldg(reinterpret_cast<const uint2*>(P.h + row * P.ld) + q);
+  }
+  __device__ __forceinline__ void zero() { h = make_uint2(0u, 0u); }
+  __device__ __forceinline__ float4 get() const {
+    return make_float4(__uint_as_float(h.x << 16), __uint_as_float(h.x & 0xffff0000u), __uint_as_float(h.y << 16),
+                       __uint_as_float(h.y & 0xffff0000u));
+  }
+};
+
+template <>
+struct PanelSlot<2> {
+  uint2 h;
+  uint32_t l;
+  __device__ __forceinline__ void load(const SpmmPanel& P, int64_t row, int q) {
+    h = __ldg(reinterpret_cast<const uint2*>(P.h + row * P.ld) + q);
+    l = __ldg(reinterpret_cast<const uint32_t*>(P.l + row * P.ld) + q);
+  }
+  __device__ __forceinline__ void zero() {
+    h = make_uint2(0u, 0u);
+    l = 0u;
+  }
+  __device__ __forceinline__ float4 get() const {
+    return make_float4(__uint_as_float((h.x << 16) | ((l & 0xffu) << 8)),
+                       __uint_as_float((h.x & 0xffff0000u) | (l & 0xff00u)),
+                       __uint_as_float((h.y << 16) | ((l >> 8) & 0xff00u)),
+                       __uint_as_float((h.y & 0xffff0000u) | ((l >> 16) & 0xff00u)));
+  }
+};
+
+// V4 slots per lane: panel rows of at most 128*V4 values.  Rows start 16-byte
+// (FP32), 8-byte (16-bit parts) and 4-byte (low bytes) aligned; values
+// r..4*ceil(r/4)-1 are read (inside ld) but never written to Y.
 // Sum over entries [e0, e1) of one row into acc (lane l: columns 4l..4l+3 + 128t).
-template <int V4>
+template <int V4, int FMT>
 __device__ __forceinline__ void row_segment_vec(int64_t e0, int64_t e1, int lane, int nv,
                                                 const int32_t* __restrict__ colidx, const float* __restrict__ val,
-                                                const float* __restrict__ X, int64_t ldx, float4 (&acc)[V4]) {
+                                                const SpmmPanel& P, float4 (&acc)[V4]) {
   for (int64_t b = e0; b < e1; b += 32) {
     const int64_t e = b + lane;
     int c = 0;
     float v = 0.f;
     if (e < e1) {
-      c = __ldg(colidx + e);
-      v = __ldg(val + e);
+      c = __ldcs(colidx + e);
+      v = __ldcs(val + e);
     }
     const int cnt = (int)(e1 - b < 32 ? e1 - b : 32);
     int j = 0;
@@ -63,29 +127,31 @@ __device__ __forceinline__ void row_segment_vec(int64_t e0, int64_t e1, int lane
         cj[u] = __shfl_sync(0xffffffffu, c, j + u);
         vj[u] = __shfl_sync(0xffffffffu, v, j + u);
       }
-      float4 x[4][V4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float4* xr = reinterpret_cast<const float4*>(X + (int64_t)cj[u] * ldx);
-#pragma unroll
-        for (int t = 0; t < V4; ++t) {
-          const int q = lane + 32 * t;
-          x[u][t] = q < nv ? __ldg(xr + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      }
+      PanelSlot<FMT> x[4][V4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int t = 0; t < V4; ++t) fma4(acc[t], vj[u], x[u][t]);
+        for (int t = 0; t < V4; ++t) {
+          const int q = lane + 32 * t;
+          if (q < nv) x[u][t].load(P, cj[u], q);
+          else x[u][t].zero();
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int t = 0; t < V4; ++t) fma4(acc[t], vj[u], x[u][t].get());
     }
     for (; j < cnt; ++j) {
       const int cj = __shfl_sync(0xffffffffu, c, j);
       const float vj = __shfl_sync(0xffffffffu, v, j);
-      const float4* xr = reinterpret_cast<const float4*>(X + (int64_t)cj * ldx);
 #pragma unroll
       for (int t = 0; t < V4; ++t) {
         const int q = lane + 32 * t;
-        if (q < nv) fma4(acc[t], vj, __ldg(xr + q));
+        if (q < nv) {
+          PanelSlot<FMT> x;
+          x.load(P, cj, q);
+          fma4(acc[t], vj, x.get());
+        }
       }
     }
   }
@@ -104,10 +170,10 @@ __device__ __forceinline__ void store_row_vec(float* yr, int r, int lane, int nv
     if (c0 + 4 <= r) {
       float4* p = reinterpret_cast<float4*>(yr + c0);
       if (accumulate) {
-        const float4 y = *p;
+        const float4 y = __ldcs(p);
         o.x += y.x; o.y += y.y; o.z += y.z; o.w += y.w;
       }
-      *p = o;
+      __stcs(p, o);
     } else {  // the panel's last, partial group of four columns
       yr[c0] = accumulate ? yr[c0] + o.x : o.x;
       if (c0 + 1 < r) yr[c0 + 1] = accumulate ? yr[c0 + 1] + o.y : o.y;
@@ -116,24 +182,40 @@ __device__ __forceinline__ void store_row_vec(float* yr, int r, int lane, int nv
   }
 }
 
-// One warp per row.  With split != 0, rows of more than kSpmmSeg entries are
-// left to the segment tasks (spmm_segment_kernel + spmm_combine_kernel).
-template <int V4>
-__global__ void __launch_bounds__(kSpmmThreads)
+// Persistent grid: warps draw kSpmmGrab rows at a time, from *next when it is
+// given (zeroed before the launch), else by a fixed stride.  With split != 0,
+// rows of more than kSpmmSeg entries are left to the segment tasks
+// (spmm_segment_kernel + spmm_combine_kernel).
+template <int V4, int FMT>
+__global__ void __launch_bounds__(kSpmmThreads, V4 >= 4 ? 2 : 3)
 spmm_csr_vec_kernel(int64_t M, int r, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                    const float* __restrict__ val, const float* __restrict__ X, int64_t ldx, float* __restrict__ Y,
-                    int64_t ldy, int accumulate, int split) {
+                    const float* __restrict__ val, const SpmmPanel P, float* __restrict__ Y, int64_t ldy,
+                    int accumulate, int split, unsigned long long* next) {
   const int lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (kSpmmThreads / 32) + (threadIdx.x >> 5);
-  if (row >= M) return;
-  const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
-  if (split && e1 - e0 > kSpmmSeg) return;
+  const int64_t gwarp = ((int64_t)blockIdx.x * kSpmmThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kSpmmThreads) >> 5;
   const int nv = (r + 3) >> 2;
-  float4 acc[V4];
+  for (int64_t it = 0;; ++it) {
+    int64_t base;
+    if (next) {
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(next, (unsigned long long)kSpmmGrab);
+      base = (int64_t)__shfl_sync(0xffffffffu, b, 0);
+    } else {
+      base = (gwarp + it * nwarps) * kSpmmGrab;
+    }
+    if (base >= M) break;
+    const int64_t end = base + kSpmmGrab < M ? base + kSpmmGrab : M;
+    for (int64_t row = base; row < end; ++row) {
+      const int64_t e0 = rowptr[row], e1 = rowptr[row + 1];
+      if (split && e1 - e0 > kSpmmSeg) continue;
+      float4 acc[V4];
 #pragma unroll
-  for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-  row_segment_vec<V4>(e0, e1, lane, nv, colidx, val, X, ldx, acc);
-  store_row_vec<V4>(Y + row * ldy, r, lane, nv, accumulate, acc);
+      for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      row_segment_vec<V4, FMT>(e0, e1, lane, nv, colidx, val, P, acc);
+      store_row_vec<V4>(Y + row * ldy, r, lane, nv, accumulate, acc);
+    }
+  }
 }
 
 // Task list of the long rows: a row of len > kSpmmSeg entries takes
@@ -154,35 +236,40 @@ __global__ void spmm_tasks_kernel(int64_t M, const int32_t* __restrict__ rowptr,
   }
 }
 
-// One warp per task: the partial product of one segment of a long row, written
-// to partial[task * ldp ...] (ldp = 4 ceil(r/4)).
-template <int V4>
-__global__ void __launch_bounds__(kSpmmThreads)
+// Persistent grid, one warp per task at a time (tasks gw, gw + warps, ...):
+// the partial product of one segment of a long row, written to
+// partial[task * ldp ...] (ldp = 4 ceil(r/4)).
+template <int V4, int FMT>
+__global__ void __launch_bounds__(kSpmmThreads, V4 >= 4 ? 2 : 3)
 spmm_segment_kernel(int r, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                    const float* __restrict__ val, const float* __restrict__ X, int64_t ldx,
-                    const int* __restrict__ counter, const int* __restrict__ task_row,
-                    const int* __restrict__ task_seg, float* __restrict__ partial, int64_t ldp) {
+                    const float* __restrict__ val, const SpmmPanel P, const int* __restrict__ counter,
+                    const int* __restrict__ task_row, const int* __restrict__ task_seg, int64_t max_tasks,
+                    float* __restrict__ partial, int64_t ldp) {
   const int lane = threadIdx.x & 31;
-  const int64_t task = (int64_t)blockIdx.x * (kSpmmThreads / 32) + (threadIdx.x >> 5);
-  if (task >= *counter) return;  // the grid covers max_tasks tasks
-  const int row = task_row[task], seg = task_seg[task];
-  const int64_t e0 = (int64_t)rowptr[row] + (int64_t)seg * kSpmmSeg;
-  const int64_t e1 = min((int64_t)rowptr[row + 1], e0 + kSpmmSeg);
+  const int64_t nwarps = ((int64_t)gridDim.x * kSpmmThreads) >> 5;
   const int nv = (r + 3) >> 2;
-  float4 acc[V4];
+  int64_t ntask = *counter;
+  if (ntask > max_tasks) ntask = max_tasks;
+  for (int64_t task = ((int64_t)blockIdx.x * kSpmmThreads + threadIdx.x) >> 5; task < ntask; task += nwarps) {
+    const int row = task_row[task], seg = task_seg[task];
+    const int64_t e0 = (int64_t)rowptr[row] + (int64_t)seg * kSpmmSeg;
+    const int64_t e1 = min((int64_t)rowptr[row + 1], e0 + kSpmmSeg);
+    float4 acc[V4];
 #pragma unroll
-  for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-  row_segment_vec<V4>(e0, e1, lane, nv, colidx, val, X, ldx, acc);
-  float4* p = reinterpret_cast<float4*>(partial + task * ldp);
+    for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    row_segment_vec<V4, FMT>(e0, e1, lane, nv, colidx, val, P, acc);
+    float4* p = reinterpret_cast<float4*>(partial + task * ldp);
 #pragma unroll
-  for (int t = 0; t < V4; ++t) {
-    const int q = lane + 32 * t;
-    if (q < nv) p[q] = acc[t];
+    for (int t = 0; t < V4; ++t) {
+      const int q = lane + 32 * t;
+      if (q < nv) p[q] = acc[t];
+    }
   }
 }
 
-// One warp per long row (its segment-0 task): the row's partials added in
-// segment order, then stored like a short row.
+// Persistent grid, one warp per long row at a time (found at its segment-0
+// task): the row's partials added in segment order, then stored like a short
+// row.
 template <int V4>
 __global__ void __launch_bounds__(kSpmmThreads)
 spmm_combine_kernel(int r, const int32_t* __restrict__ rowptr, const int* __restrict__ counter,
@@ -190,28 +277,55 @@ spmm_combine_kernel(int r, const int32_t* __restrict__ rowptr, const int* __rest
                     const float* __restrict__ partial, int64_t ldp, float* __restrict__ Y, int64_t ldy,
                     int accumulate) {
   const int lane = threadIdx.x & 31;
-  const int64_t task = (int64_t)blockIdx.x * (kSpmmThreads / 32) + (threadIdx.x >> 5);
-  if (task >= *counter || task_seg[task] != 0) return;
-  const int row = task_row[task];
-  const int64_t len = (int64_t)rowptr[row + 1] - rowptr[row];
-  const int nseg = (int)((len + kSpmmSeg - 1) / kSpmmSeg);
-  if (task + nseg > max_tasks) return;  // only if rowptr holds more than nnz entries
+  const int64_t nwarps = ((int64_t)gridDim.x * kSpmmThreads) >> 5;
   const int nv = (r + 3) >> 2;
-  float4 acc[V4];
+  int64_t ntask = *counter;
+  if (ntask > max_tasks) ntask = max_tasks;
+  for (int64_t task = ((int64_t)blockIdx.x * kSpmmThreads + threadIdx.x) >> 5; task < ntask; task += nwarps) {
+    if (task_seg[task] != 0) continue;
+    const int row = task_row[task];
+    const int64_t len = (int64_t)rowptr[row + 1] - rowptr[row];
+    const int nseg = (int)((len + kSpmmSeg - 1) / kSpmmSeg);
+    if (task + nseg > max_tasks) continue;  // only if rowptr holds more than nnz entries
+    float4 acc[V4];
 #pragma unroll
-  for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int s = 0; s < nseg; ++s) {
-    const float4* p = reinterpret_cast<const float4*>(partial + (task + s) * ldp);
+    for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < nseg; ++s) {
+      const float4* p = reinterpret_cast<const float4*>(partial + (task + s) * ldp);
 #pragma unroll
-    for (int t = 0; t < V4; ++t) {
-      const int q = lane + 32 * t;
-      if (q < nv) {
-        const float4 x = p[q];
-        acc[t].x += x.x; acc[t].y += x.y; acc[t].z += x.z; acc[t].w += x.w;
+      for (int t = 0; t < V4; ++t) {
+        const int q = lane + 32 * t;
+        if (q < nv) {
+          const float4 x = p[q];
+          acc[t].x += x.x; acc[t].y += x.y; acc[t].z += x.z; acc[t].w += x.w;
+        }
       }
     }
+    store_row_vec<V4>(Y + (int64_t)row * ldy, r, lane, nv, accumulate, acc);
   }
-  store_row_vec<V4>(Y + (int64_t)row * ldy, r, lane, nv, accumulate, acc);
+}
+
+// Panel conversion for the compact formats: rows of X (K x r, ldx) rounded to
+// BF16 (fmt 1, into h) or to 16 significant bits (fmt 2, high 16 bits into h,
+// the next 8 into l), both round-to-nearest-even; values r..ld-1 are zero.
+// One thread per value.
+__global__ void spmm_pack_kernel(int fmt, int64_t K, int r, const float* __restrict__ X, int64_t ldx,
+                                 uint16_t* __restrict__ h, uint8_t* __restrict__ l, int64_t ld) {
+  const int64_t total = K * ld;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i / ld;
+    const int c = (int)(i - row * ld);
+    const float x = c < r ? X[row * ldx + c] : 0.f;
+    if (fmt == 1) {
+      h[i] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    } else {
+      uint32_t b = __float_as_uint(x);
+      if ((b & 0x7fffffffu) > 0x7f800000u) b |= 0x00400000u;  // NaN stays NaN in 24 bits
+      else if ((b & 0x7f800000u) != 0x7f800000u) b += 0x7fu + ((b >> 8) & 1u);
+      h[i] = (uint16_t)(b >> 16);
+      l[i] = (uint8_t)((b >> 8) & 0xffu);
+    }
+  }
 }
 
 // Scalar variant for panels that are not 16-byte aligned: lane l holds columns
@@ -256,6 +370,44 @@ spmm_csr_scalar_kernel(int64_t M, int r, const int32_t* __restrict__ rowptr, con
   }
 }
 
+// Blocks of a kSpmmThreads-thread kernel resident on the whole device at once
+// (cached per kernel).
+template <typename K>
+int64_t resident_blocks(K kernel) {
+  static int64_t blocks = 0;
+  if (!blocks) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kSpmmThreads, 0);
+    blocks = (int64_t)(sms > 0 ? sms : 152) * (occ > 0 ? occ : 1);
+  }
+  return blocks;
+}
+
+template <int V4, int FMT>
+rsvd_status launch_vec(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
+                       const SpmmPanel& X, float* Y, int64_t ldy, int acc, bool split, unsigned long long* next,
+                       const int* counter, const int* task_row, const int* task_seg, int64_t max_tasks,
+                       float* partial, int64_t ldp, cudaStream_t stream) {
+  const int64_t row_blocks = cdiv(cdiv(M, kSpmmGrab), kSpmmThreads / 32);
+  const int64_t res = resident_blocks(spmm_csr_vec_kernel<V4, FMT>);
+  spmm_csr_vec_kernel<V4, FMT><<<(unsigned)(row_blocks < res ? row_blocks : res), kSpmmThreads, 0, stream>>>(
+      M, r, rowptr, colidx, val, X, Y, ldy, acc, split ? 1 : 0, next);
+  RSVD_CUDA(after_launch());
+  if (!split) return RSVD_OK;
+  const int64_t task_blocks = cdiv(max_tasks, kSpmmThreads / 32);
+  const int64_t sres = resident_blocks(spmm_segment_kernel<V4, FMT>);
+  spmm_segment_kernel<V4, FMT><<<(unsigned)(task_blocks < sres ? task_blocks : sres), kSpmmThreads, 0, stream>>>(
+      r, rowptr, colidx, val, X, counter, task_row, task_seg, max_tasks, partial, ldp);
+  RSVD_CUDA(after_launch());
+  const int64_t cres = resident_blocks(spmm_combine_kernel<V4>);
+  spmm_combine_kernel<V4><<<(unsigned)(task_blocks < cres ? task_blocks : cres), kSpmmThreads, 0, stream>>>(
+      r, rowptr, counter, task_row, task_seg, max_tasks, partial, ldp, Y, ldy, acc);
+  RSVD_CUDA(after_launch());
+  return RSVD_OK;
+}
+
 }  // namespace
 
 size_t spmm_ws_bytes(int64_t nnz, int r) {
@@ -268,71 +420,97 @@ size_t spmm_ws_bytes(int64_t nnz, int r) {
   return s.used + 256;
 }
 
-rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
-                     int64_t nnz, const float* X, int64_t ldx, float* Y, int64_t ldy, bool accumulate, void* ws,
-                     size_t ws_bytes, cudaStream_t stream) {
+rsvd_status spmm_pack(int fmt, int64_t K, int r, const float* X, int64_t ldx, uint16_t* h, uint8_t* l, int64_t ld,
+                      cudaStream_t stream) {
+  if (K <= 0) return RSVD_OK;
+  if ((fmt != 1 && fmt != 2) || r < 1 || ldx < r || ld < round_up(r, 4) || ld % 4 || !X || !h || (fmt == 2 && !l))
+    return fail(RSVD_ERR_INVALID_ARG, "spmm_pack: bad arguments");
+  const int64_t blocks = std::min<int64_t>(cdiv(K * ld, 256), 152 * 32);
+  spmm_pack_kernel<<<(unsigned)blocks, 256, 0, stream>>>(fmt, K, r, X, ldx, h, l, ld);
+  RSVD_CUDA(after_launch());
+  return RSVD_OK;
+}
+
+rsvd_status spmm_csr_panel(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
+                           int64_t nnz, const SpmmPanel& X, float* Y, int64_t ldy, bool accumulate, void* ws,
+                           size_t ws_bytes, cudaStream_t stream) {
   if (M <= 0) return RSVD_OK;
-  if (r < 1 || r > kSpmmMaxR || ldx < r || ldy < r || !rowptr || !X || !Y)
+  const bool fp32 = X.fmt == 0;
+  if (r < 1 || r > kSpmmMaxR || X.ld < r || ldy < r || !rowptr || !Y || X.fmt < 0 || X.fmt > 2 ||
+      (fp32 && !X.f) || (!fp32 && (!X.h || X.ld % 4 || (X.fmt == 2 && !X.l))))
     return fail(RSVD_ERR_INVALID_ARG, "spmm_csr: bad arguments");
   const int64_t blocks = cdiv(M, kSpmmThreads / 32);
   if (blocks > 0x7fffffffLL) return fail(RSVD_ERR_INVALID_ARG, "spmm_csr: too many rows");
   const int acc = accumulate ? 1 : 0;
-  const bool vec = ldx % 4 == 0 && ldy % 4 == 0 && aligned16(X) && aligned16(Y);
-  const dim3 grid((unsigned)blocks);
-  if (vec) {
-    const int v4 = (int)cdiv(cdiv(r, 4), 32);
-    // rows of more than kSpmmSeg entries are split into segment tasks when the
-    // workspace allows
-    const int64_t max_tasks = spmm_max_tasks(nnz);
-    const bool split = ws && ws_bytes >= spmm_ws_bytes(nnz, r) && nnz > kSpmmSeg;
-    int *counter = nullptr, *task_row = nullptr, *task_seg = nullptr;
-    float* partial = nullptr;
-    const int64_t ldp = round_up(r, 4);
-    if (split) {
-      Carver c(ws, ws_bytes);
-      counter = c.take<int>(4);
-      task_row = c.take<int>((size_t)max_tasks);
-      task_seg = c.take<int>((size_t)max_tasks);
-      partial = c.take<float>((size_t)max_tasks * ldp);
-      RSVD_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), stream));
-      int tb = (int)cdiv(M, 256);
-      if (tb > 152 * 16) tb = 152 * 16;
-      spmm_tasks_kernel<<<tb, 256, 0, stream>>>(M, rowptr, counter, (int)max_tasks, task_row, task_seg);
-      RSVD_CUDA(after_launch());
-    }
-    const dim3 tgrid((unsigned)cdiv(max_tasks, kSpmmThreads / 32));
-    const int sp = split ? 1 : 0;
-#define RSVD_VEC(V)                                                                                            \
-  do {                                                                                                         \
-    spmm_csr_vec_kernel<V><<<grid, kSpmmThreads, 0, stream>>>(M, r, rowptr, colidx, val, X, ldx, Y, ldy, acc, sp); \
-    RSVD_CUDA(after_launch());                                                                                 \
-    if (split) {                                                                                               \
-      spmm_segment_kernel<V><<<tgrid, kSpmmThreads, 0, stream>>>(r, rowptr, colidx, val, X, ldx, counter,      \
-                                                                 task_row, task_seg, partial, ldp);            \
-      RSVD_CUDA(after_launch());                                                                               \
-      spmm_combine_kernel<V><<<tgrid, kSpmmThreads, 0, stream>>>(r, rowptr, counter, task_row, task_seg,       \
-                                                                 max_tasks, partial, ldp, Y, ldy, acc);        \
-      RSVD_CUDA(after_launch());                                                                               \
-    }                                                                                                          \
-  } while (0)
-    switch (v4) {
-      case 1: RSVD_VEC(1); break;
-      case 2: RSVD_VEC(2); break;
-      case 3: RSVD_VEC(3); break;
-      default: RSVD_VEC(4); break;
-    }
-#undef RSVD_VEC
-    return RSVD_OK;
-  } else {
+  const bool vec = !fp32 || (X.ld % 4 == 0 && ldy % 4 == 0 && aligned16(X.f) && aligned16(Y));
+  if (!vec) {
+    const dim3 grid((unsigned)blocks);
     const int vs = (int)cdiv(r, 32);
-#define RSVD_SCA(V) spmm_csr_scalar_kernel<V><<<grid, kSpmmThreads, 0, stream>>>(M, r, rowptr, colidx, val, X, ldx, Y, ldy, acc)
+#define RSVD_SCA(V) \
+  spmm_csr_scalar_kernel<V><<<grid, kSpmmThreads, 0, stream>>>(M, r, rowptr, colidx, val, X.f, X.ld, Y, ldy, acc)
     if (vs <= 4) RSVD_SCA(4);
     else if (vs <= 8) RSVD_SCA(8);
     else RSVD_SCA(16);
 #undef RSVD_SCA
+    RSVD_CUDA(after_launch());
+    return RSVD_OK;
   }
-  RSVD_CUDA(after_launch());
-  return RSVD_OK;
+  if (ldy % 4 || !aligned16(Y)) return fail(RSVD_ERR_INVALID_ARG, "spmm_csr: compact panels need 16-byte output rows");
+  const int v4 = (int)cdiv(cdiv(r, 4), 32);
+  // rows of more than kSpmmSeg entries are split into segment tasks when the
+  // workspace allows; the row counter of the persistent grid sits beside the
+  // task counter
+  const bool ws_ok = ws && reinterpret_cast<uintptr_t>(ws) % 16 == 0;
+  const int64_t max_tasks = spmm_max_tasks(nnz);
+  const bool split = ws_ok && ws_bytes >= spmm_ws_bytes(nnz, r) && nnz > kSpmmSeg;
+  int *counter = nullptr, *task_row = nullptr, *task_seg = nullptr;
+  unsigned long long* next = nullptr;
+  float* partial = nullptr;
+  const int64_t ldp = round_up(r, 4);
+  if (ws_ok && ws_bytes >= 256) {
+    Carver c(ws, ws_bytes);
+    counter = c.take<int>(4);
+    next = reinterpret_cast<unsigned long long*>(counter + 2);
+    if (split) {
+      task_row = c.take<int>((size_t)max_tasks);
+      task_seg = c.take<int>((size_t)max_tasks);
+      partial = c.take<float>((size_t)max_tasks * ldp);
+    }
+    RSVD_CUDA(cudaMemsetAsync(counter, 0, 4 * sizeof(int), stream));
+  }
+  if (split) {
+    int tb = (int)cdiv(M, 256);
+    if (tb > 152 * 16) tb = 152 * 16;
+    spmm_tasks_kernel<<<tb, 256, 0, stream>>>(M, rowptr, counter, (int)max_tasks, task_row, task_seg);
+    RSVD_CUDA(after_launch());
+  }
+#define RSVD_VEC(V, F)                                                                                           \
+  return launch_vec<V, F>(M, r, rowptr, colidx, val, X, Y, ldy, acc, split, next, counter, task_row, task_seg, \
+                          max_tasks, partial, ldp, stream)
+#define RSVD_VEC_F(V)                  \
+  do {                                 \
+    if (X.fmt == 0) RSVD_VEC(V, 0);    \
+    else if (X.fmt == 1) RSVD_VEC(V, 1); \
+    else RSVD_VEC(V, 2);               \
+  } while (0)
+  switch (v4) {
+    case 1: RSVD_VEC_F(1);
+    case 2: RSVD_VEC_F(2);
+    case 3: RSVD_VEC_F(3);
+    default: RSVD_VEC_F(4);
+  }
+#undef RSVD_VEC_F
+#undef RSVD_VEC
+}
+
+rsvd_status spmm_csr(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
+                     int64_t nnz, const float* X, int64_t ldx, float* Y, int64_t ldy, bool accumulate, void* ws,
+                     size_t ws_bytes, cudaStream_t stream) {
+  SpmmPanel P;
+  P.fmt = 0;
+  P.f = X;
+  P.ld = ldx;
+  return spmm_csr_panel(M, r, rowptr, colidx, val, nnz, P, Y, ldy, accumulate, ws, ws_bytes, stream);
 }
 
 // Stable counting-sort transpose on the host.  Rows are split into T ranges of

@@ -251,15 +251,34 @@ def test_binding_maps_16bit_dtypes():
 def test_csr_plan_rules(lib):
     from paper_1907_06470_gb300 import _lib
     h = C.c_void_p()
-    # CSR plans take r up to 512, FP32 values and precision only
+    # CSR plans take r up to 512, FP32 values, and FP32, BF16 or BF16X3 precision
     o = _lib.RsvdOpts(prec=1, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
     out = C.c_size_t()
     assert lib.rsvd_plan_min_cap(100000, 50000, 300, 50, C.byref(o), C.byref(out)) == 0
+    fp32_cap = out.value
     o513 = _lib.RsvdOpts(prec=1, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
     assert lib.rsvd_plan_min_cap(100000, 50000, 500, 13, C.byref(o513), C.byref(out)) == 1
-    ob = _lib.RsvdOpts(prec=2, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
-    assert lib.rsvd_plan(1000, 500, 10, 5, 1, 1, 0, C.byref(ob), C.byref(h)) == 8
-    assert h.value is None
+    # the compact panels (16 / 24 bits per value of the larger side, ldr 352) on top
+    for prec, per in ((2, 2), (3, 3)):
+        oc = _lib.RsvdOpts(prec=prec, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
+        assert lib.rsvd_plan_min_cap(100000, 50000, 300, 50, C.byref(oc), C.byref(out)) == 0
+        assert 0 <= out.value - fp32_cap - 100000 * 352 * per <= 2048
+    for prec, dtype in ((4, 1), (0, 0), (1, 0)):  # FP8, FP64
+        ob = _lib.RsvdOpts(prec=prec, refine=1, mb=0, nb=0, n_slots=2, dtype=dtype, kind=1)
+        assert lib.rsvd_plan(1000, 500, 10, 5, 1, 1, 0, C.byref(ob), C.byref(h)) in (1, 8)
+        assert h.value is None
+
+
+def test_csr_apass_workspace_sizes(lib):
+    """FP32 passes need the split-row workspace only; BF16 / BF16X3 passes add
+    the compact panel (K rows of round_up(r, 4) values, 2 and 3 bytes each)."""
+    nnz, K, r = 10_000_000, 40000, 350
+    base = lib.rsvd_spmm_workspace(nnz, r)
+    assert lib.rsvd_csr_apass_workspace(nnz, K, r, 1) == base
+    for prec, per in ((2, 2), (3, 3)):
+        extra = lib.rsvd_csr_apass_workspace(nnz, K, r, prec) - base
+        assert K * 352 * per <= extra <= K * 352 * per + 1024
+    assert lib.rsvd_csr_apass_workspace(nnz, K, 0, 2) == 0
 
 
 def _ckpt_header(step=3, corrupt=False, **kw):

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import linalg as OL
+from oracle import panel as OP
 from oracle import rsvd as OR
 from oracle import tiles as OT
 from synth import zipf_csr
@@ -80,6 +81,34 @@ def test_csr_apass_matches_oracle(g, zipf, zipf_abs, r, aligned):
     assert np.all(np.abs(Z - Zo) <= _fp32_product_bound(Atabs, Yt) + 1e-30)
 
 
+@pytest.mark.parametrize("prec,bits", [("bf16", 8), ("bf16x3", 16)])
+@pytest.mark.parametrize("r", [7, 120, 350])
+def test_csr_compact_panel_pass_matches_oracle(g, zipf, zipf_abs, prec, bits, r):
+    """BF16 and 24-bit panels: the pass equals the FP64 product of A with the
+    panel rounded by the oracle (8 / 16 significant bits, ties to even),
+    within the FP32 accumulation bound -- forward, and transposed over the
+    long rows of A^T (split into segments)."""
+    m, n, rp, ci, v = zipf
+    A = OL.CSR(m, n, rp, ci, v)
+    Aabs, Atabs = zipf_abs
+    rng = np.random.default_rng(100 + r)
+    X = rng.standard_normal((n, r)).astype(np.float32)
+    Yt = (rng.standard_normal((m, r)) * 1e-3).astype(np.float32)
+    Ad = _torch_csr(m, n, rp, ci, v, "cuda")
+    Atd = g.csr_transpose(_torch_csr(m, n, rp, ci, v, "cpu")).to("cuda")
+    Y = g.apass(Ad, torch.as_tensor(X, device="cuda"), prec=prec).cpu().numpy().astype(np.float64)
+    Z = g.apass(Ad, torch.as_tensor(Yt, device="cuda"), trans=True, At=Atd, prec=prec).cpu().numpy()
+    Xr = OP.round_significant(X, bits).astype(np.float64)
+    Ytr = OP.round_significant(Yt, bits).astype(np.float64)
+    assert np.all(np.abs(Y - OL.csr_apply(A, Xr)) <= _fp32_product_bound(Aabs, Xr) + 1e-30)
+    Zo = OL.csr_apply(A, Ytr, trans=True)
+    assert np.all(np.abs(Z.astype(np.float64) - Zo) <= _fp32_product_bound(Atabs, Ytr) + 1e-30)
+    # the rounding is what moved the result: the FP32 panel's product differs
+    Yf = OL.csr_apply(A, X.astype(np.float64))
+    rel = np.abs(Y - Yf).max() / np.abs(Yf).max()
+    assert rel <= 2.0 ** -bits
+
+
 def test_csr_apass_is_deterministic(g, zipf):
     m, n, rp, ci, v = zipf
     Ad = _torch_csr(m, n, rp, ci, v, "cuda")
@@ -99,6 +128,26 @@ def test_csr_rsvd_scaled_sparse_workload_matches_oracle(g, zipf):
     assert sigma_rel_err(S, So) <= 1e-5
     assert cluster_safe_angles(U, Uo, So, 8, rel_gap=1e-2) <= 1e-4
     assert cluster_safe_angles(V, Vo, So, 8, rel_gap=1e-2) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_csr_rsvd_compact_panels_against_oracle(g, zipf, prec):
+    """CSR plans whose range finder gathers compact panels, the final
+    B^T = A^T Q an FP32 panel: 24-bit panels (BF16X3) meet the FP32 bars;
+    BF16 panels are reported against looser ones."""
+    m, n, rp, ci, v = zipf
+    k, p, q, seed = 64, 16, 3, 2004
+    U, S, V = g.rsvd(_torch_csr(m, n, rp, ci, v, "cuda"), k, p, q, seed, prec=prec)
+    U, S, V = (t.cpu().numpy().astype(np.float64) for t in (U, S, V))
+    Uo, So, Vo = OR.rsvd(OL.CSR(m, n, rp, ci, v), k, p, q, seed, "f32" if prec == "bf16x3" else "bf16")
+    es = sigma_rel_err(S, So)
+    eu = cluster_safe_angles(U, Uo, So, 8, rel_gap=1e-2)
+    ev = cluster_safe_angles(V, Vo, So, 8, rel_gap=1e-2)
+    print(f"CSR {prec} panels: sigma {es:.2e} U {eu:.2e} V {ev:.2e}")
+    if prec == "bf16x3":
+        assert es <= 1e-5 and eu <= 1e-4 and ev <= 1e-4
+    else:
+        assert es <= 1e-3 and eu <= 1e-1 and ev <= 1e-1
 
 
 def test_csr_input_locations_agree_bitwise(g, zipf):
@@ -201,31 +250,33 @@ def test_csr_cap_too_small_for_the_copies(g, zipf):
     plan.close()
 
 
-def _csr_min_cap(g, m, n, k, p):
+def _csr_min_cap(g, m, n, k, p, prec="fp32"):
     from paper_1907_06470_gb300 import _lib
     import ctypes as C
-    o = _lib.RsvdOpts(prec=1, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
+    o = _lib.RsvdOpts(prec=_lib.PREC[prec], refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
     out = C.c_size_t()
     assert g.load().rsvd_plan_min_cap(m, n, k, p, C.byref(o), C.byref(out)) == 0
     return out.value
 
 
-def test_csr_streamed_full_width_blocks_match_in_core_bits(g, zipf):
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_csr_streamed_full_width_blocks_match_in_core_bits(g, zipf, prec):
     """A host CSR over the cap is streamed in full-width row blocks (of A for
     the forward products, of A^T for the transposed ones): every output row is
     summed by the same kernel over the same entries as in core, so the result
-    is the same bits; and it meets the oracle at the FP32 bars."""
+    is the same bits (FP32 and 24-bit panels); and it meets the oracle at the
+    FP32 bars."""
     m, n, rp, ci, v = zipf
     k, p, q, seed = 20, 10, 2, 2004
     A_bytes = (m + 1) * 4 + len(v) * 8
-    cap = _csr_min_cap(g, m, n, k, p) + A_bytes // 2
+    cap = _csr_min_cap(g, m, n, k, p, prec) + A_bytes // 2
     Ah = _torch_csr(m, n, rp, ci, v, "cpu")
-    plan = g.Plan(m, n, k, p, q, seed, mem_cap=cap, kind="csr")
+    plan = g.Plan(m, n, k, p, q, seed, mem_cap=cap, kind="csr", prec=prec)
     Us, Ss, Vs = plan.run(Ah)
     st = plan.stream_stats()
     assert st["tiles_streamed_per_pass"] > 0 and st["h2d_bytes"] > A_bytes
     plan.close()
-    Ui, Si, Vi = g.rsvd(_torch_csr(m, n, rp, ci, v, "cuda"), k, p, q, seed)
+    Ui, Si, Vi = g.rsvd(_torch_csr(m, n, rp, ci, v, "cuda"), k, p, q, seed, prec=prec)
     assert torch.equal(Ss, Si) and torch.equal(Us, Ui) and torch.equal(Vs, Vi)
     Uo, So, Vo = OR.rsvd(OL.CSR(m, n, rp, ci, v), k, p, q, seed, "f32")
     assert sigma_rel_err(Ss.cpu().numpy(), So) <= 1e-5
@@ -258,14 +309,14 @@ def test_csr_streamed_block_cyclic_grid_matches_oracle(g, zipf, mb, nb):
     assert cluster_safe_angles(U, Uo, So, k) <= 1e-4 and cluster_safe_angles(V, Vo, So, k) <= 1e-4
 
 
-@pytest.mark.parametrize("split", [True, False])
-def test_csr_long_rows_at_segment_boundaries(g, split):
-    """Rows of 0, 1, 4095, 4096, 4097, 8192, 8193 and 30000 entries: the
-    segment split (4096 entries per warp, partials added in order) against the
-    oracle, with and without the split workspace."""
+@pytest.mark.parametrize("split,prec", [(True, "fp32"), (False, "fp32"), (True, "bf16x3")])
+def test_csr_long_rows_at_segment_boundaries(g, split, prec):
+    """Rows of 0, 1, 1023, 1024, 1025, 2048, 2049, 4097 and 30000 entries: the
+    segment split (1024 entries per warp, partials added in order) against the
+    oracle, with and without the split workspace, FP32 and 24-bit panels."""
     rng = np.random.default_rng(17)
     n, r = 40000, 130
-    lens = [0, 1, 4095, 4096, 4097, 8192, 8193, 30000, 5, 12000]
+    lens = [0, 1, 1023, 1024, 1025, 2048, 2049, 4097, 30000, 5, 12000]
     rows_c, rows_v = [], []
     for L in lens:
         c = np.sort(rng.choice(n, size=L, replace=False))
@@ -276,17 +327,19 @@ def test_csr_long_rows_at_segment_boundaries(g, split):
     v = np.concatenate(rows_v).astype(np.float32)
     m = len(lens)
     X = rng.standard_normal((n, r)).astype(np.float32)
+    rnd = (lambda x: x) if prec == "fp32" else OP.round_p24  # the panel both sides multiply
     Ad = _torch_csr(m, n, rp, ci, v, "cuda")
-    Y = g.apass(Ad, torch.as_tensor(X, device="cuda"), split_long_rows=split).cpu().numpy().astype(np.float64)
+    Y = g.apass(Ad, torch.as_tensor(X, device="cuda"), prec=prec,
+                split_long_rows=split).cpu().numpy().astype(np.float64)
     A = OL.CSR(m, n, rp, ci, v)
-    Yo = OL.csr_apply(A, X.astype(np.float64))
-    bound = _fp32_product_bound(OL.CSR(m, n, rp, ci, np.abs(v)), X)
+    Yo = OL.csr_apply(A, rnd(X).astype(np.float64))
+    bound = _fp32_product_bound(OL.CSR(m, n, rp, ci, np.abs(v)), rnd(X))
     assert np.all(np.abs(Y - Yo) <= bound + 1e-30)
     assert np.all(Y[0] == 0.0)
     # the transposed pass over the same long rows (columns of A^T)
     At = g.csr_transpose(_torch_csr(m, n, rp, ci, v, "cpu")).to("cuda")
     Yt = rng.standard_normal((n, r)).astype(np.float32)
-    Z = g.apass(At, torch.as_tensor(Yt, device="cuda"), trans=True, At=Ad,
+    Z = g.apass(At, torch.as_tensor(Yt, device="cuda"), trans=True, At=Ad, prec=prec,
                 split_long_rows=split).cpu().numpy().astype(np.float64)
-    Zo = OL.csr_apply(A, Yt.astype(np.float64))
-    assert np.all(np.abs(Z - Zo) <= _fp32_product_bound(OL.CSR(m, n, rp, ci, np.abs(v)), Yt) + 1e-30)
+    Zo = OL.csr_apply(A, rnd(Yt).astype(np.float64))
+    assert np.all(np.abs(Z - Zo) <= _fp32_product_bound(OL.CSR(m, n, rp, ci, np.abs(v)), rnd(Yt)) + 1e-30)
