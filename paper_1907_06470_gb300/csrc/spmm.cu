@@ -370,19 +370,30 @@ spmm_csr_scalar_kernel(int64_t M, int r, const int32_t* __restrict__ rowptr, con
   }
 }
 
-// Blocks of a kSpmmThreads-thread kernel resident on the whole device at once
-// (cached per kernel).
-template <typename K>
-int64_t resident_blocks(K kernel) {
-  static int64_t blocks = 0;
-  if (!blocks) {
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kSpmmThreads, 0);
-    blocks = (int64_t)(sms > 0 ? sms : 152) * (occ > 0 ? occ : 1);
-  }
-  return blocks;
+// Blocks of a kSpmmThreads-thread kernel resident on the whole device at once.
+int64_t resident_blocks_of(const void* kernel) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kSpmmThreads, 0);
+  return (int64_t)(sms > 0 ? sms : 152) * (occ > 0 ? occ : 1);
+}
+
+// The same, cached per kernel instance.
+template <int V4, int FMT>
+int64_t resident_vec() {
+  static const int64_t b = resident_blocks_of(reinterpret_cast<const void*>(spmm_csr_vec_kernel<V4, FMT>));
+  return b;
+}
+template <int V4, int FMT>
+int64_t resident_seg() {
+  static const int64_t b = resident_blocks_of(reinterpret_cast<const void*>(spmm_segment_kernel<V4, FMT>));
+  return b;
+}
+template <int V4>
+int64_t resident_comb() {
+  static const int64_t b = resident_blocks_of(reinterpret_cast<const void*>(spmm_combine_kernel<V4>));
+  return b;
 }
 
 template <int V4, int FMT>
@@ -391,17 +402,17 @@ rsvd_status launch_vec(int64_t M, int r, const int32_t* rowptr, const int32_t* c
                        const int* counter, const int* task_row, const int* task_seg, int64_t max_tasks,
                        float* partial, int64_t ldp, cudaStream_t stream) {
   const int64_t row_blocks = cdiv(cdiv(M, kSpmmGrab), kSpmmThreads / 32);
-  const int64_t res = resident_blocks(spmm_csr_vec_kernel<V4, FMT>);
+  const int64_t res = resident_vec<V4, FMT>();
   spmm_csr_vec_kernel<V4, FMT><<<(unsigned)(row_blocks < res ? row_blocks : res), kSpmmThreads, 0, stream>>>(
       M, r, rowptr, colidx, val, X, Y, ldy, acc, split ? 1 : 0, next);
   RSVD_CUDA(after_launch());
   if (!split) return RSVD_OK;
   const int64_t task_blocks = cdiv(max_tasks, kSpmmThreads / 32);
-  const int64_t sres = resident_blocks(spmm_segment_kernel<V4, FMT>);
+  const int64_t sres = resident_seg<V4, FMT>();
   spmm_segment_kernel<V4, FMT><<<(unsigned)(task_blocks < sres ? task_blocks : sres), kSpmmThreads, 0, stream>>>(
       r, rowptr, colidx, val, X, counter, task_row, task_seg, max_tasks, partial, ldp);
   RSVD_CUDA(after_launch());
-  const int64_t cres = resident_blocks(spmm_combine_kernel<V4>);
+  const int64_t cres = resident_comb<V4>();
   spmm_combine_kernel<V4><<<(unsigned)(task_blocks < cres ? task_blocks : cres), kSpmmThreads, 0, stream>>>(
       r, rowptr, counter, task_row, task_seg, max_tasks, partial, ldp, Y, ldy, acc);
   RSVD_CUDA(after_launch());
