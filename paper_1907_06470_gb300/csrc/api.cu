@@ -215,8 +215,8 @@ struct rsvd_plan_s {
   void* Qb = nullptr;   // n x ldr
   void* apass_ws = nullptr;
   size_t apass_ws_bytes = 0;
-  uint16_t* pk_h = nullptr;  // CSR plans of BF16 / BF16X3 precision: the panel in 16 bits
-  uint8_t* pk_l = nullptr;   // and, for BF16X3, its next 8 bits (24-bit panel)
+  uint16_t* pk_h = nullptr;   // CSR plans of BF16 precision: the panel in BF16
+  uint8_t* pk_24 = nullptr;   // CSR plans of BF16X3 precision: the panel in 24 bits
   OrthWs orth;
   JacobiWs jac;
   double* R = nullptr;      // r x r
@@ -342,8 +342,8 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   P->Qb = c.take<char>((size_t)P->n * P->ldr * esz);
   const bool dense = P->kind == RSVD_DENSE;  // CSR passes need no workspace here
   if (!dense && (P->prec == RSVD_PREC_BF16 || P->prec == RSVD_PREC_BF16X3)) {
-    P->pk_h = c.take<uint16_t>((size_t)mx * P->ldr);
-    P->pk_l = P->prec == RSVD_PREC_BF16X3 ? c.take<uint8_t>((size_t)mx * P->ldr) : nullptr;
+    if (P->prec == RSVD_PREC_BF16) P->pk_h = c.take<uint16_t>((size_t)mx * P->ldr);
+    else P->pk_24 = c.take<uint8_t>((size_t)mx * spmm_p24_row_bytes(P->ldr));
   }
   const size_t a0 = dense ? apass_ws_bytes(P->m, P->n, P->r, 0, P->prec, P->mb, P->nb) : 0;
   const size_t a1 = dense ? apass_ws_bytes(P->m, P->n, P->r, 1, P->prec, P->mb, P->nb) : 0;
@@ -539,10 +539,11 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
         px.ld = ldr;
         if (pr == RSVD_PREC_BF16 || pr == RSVD_PREC_BF16X3) {
           px.fmt = pr == RSVD_PREC_BF16 ? 1 : 2;
-          RSVD_TRY(spmm_pack(px.fmt, trans ? m : n, r, Xin, ldr, P->pk_h, P->pk_l, ldr, st));
+          RSVD_TRY(spmm_pack(px.fmt, trans ? m : n, r, Xin, ldr, P->pk_h, P->pk_24, ldr, st));
           px.f = nullptr;
           px.h = P->pk_h;
-          px.l = px.fmt == 2 ? P->pk_l : nullptr;
+          px.p24 = P->pk_24;
+          px.rb = spmm_p24_row_bytes(ldr);
         }
         if (P->csr_streaming)  // Sections 3.5, 3.7: CSR tiles streamed from the host
           return csr_apass_streamed(P->cs, trans, r, px, Yout, ldr, st);
@@ -992,8 +993,8 @@ size_t rsvd_csr_apass_workspace(int64_t nnz, int64_t K, int32_t r, int32_t prec)
   const int64_t ld = round_up(r, 4);
   Sizer z;
   z.take<char>(sws);
-  z.take<uint16_t>((size_t)K * ld);
-  if (prec == RSVD_PREC_BF16X3) z.take<uint8_t>((size_t)K * ld);
+  if (prec == RSVD_PREC_BF16) z.take<uint16_t>((size_t)K * ld);
+  else z.take<uint8_t>((size_t)K * spmm_p24_row_bytes(ld));
   return z.used + 256;
 }
 
@@ -1063,13 +1064,14 @@ rsvd_status rsvd_apass(const rsvd_matrix* A, int32_t trans, int32_t prec, int32_
       Carver c(ws, ws_bytes);
       sws_bytes = spmm_ws_bytes(A->nnz, r);
       sws = c.take<char>(sws_bytes);
-      uint16_t* h = c.take<uint16_t>((size_t)K * ld);
-      uint8_t* l = prec == RSVD_PREC_BF16X3 ? c.take<uint8_t>((size_t)K * ld) : nullptr;
+      uint16_t* h = prec == RSVD_PREC_BF16 ? c.take<uint16_t>((size_t)K * ld) : nullptr;
+      uint8_t* p24 = prec == RSVD_PREC_BF16X3 ? c.take<uint8_t>((size_t)K * spmm_p24_row_bytes(ld)) : nullptr;
       px.fmt = prec == RSVD_PREC_BF16 ? 1 : 2;
-      RSVD_TRY(spmm_pack(px.fmt, K, r, static_cast<const float*>(X), ldx, h, l, ld, as_stream(stream)));
+      RSVD_TRY(spmm_pack(px.fmt, K, r, static_cast<const float*>(X), ldx, h, p24, ld, as_stream(stream)));
       px.f = nullptr;
       px.h = h;
-      px.l = l;
+      px.p24 = p24;
+      px.rb = spmm_p24_row_bytes(ld);
       px.ld = ld;
     }
     return spmm_csr_panel(M, r, rp, ci, v, A->nnz, px, static_cast<float*>(Y), ldy, false, sws, sws_bytes,

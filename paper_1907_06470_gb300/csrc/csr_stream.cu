@@ -368,7 +368,7 @@ rsvd_status csr_apass_streamed(CsrStream* s, int trans, int r, const SpmmPanel& 
     SpmmPanel xt = X;  // the panel rows of the tile's columns
     if (xt.f) xt.f += T.col0 * xt.ld;
     if (xt.h) xt.h += T.col0 * xt.ld;
-    if (xt.l) xt.l += T.col0 * xt.ld;
+    if (xt.p24) xt.p24 += T.col0 * xt.rb;
     RSVD_TRY(spmm_csr_panel(T.rows, r, d_rp, d_ci, d_v, T.nnz, xt, Y + T.row0 * ldy, ldy, o.col_tiled, s->sws,
                             s->sws_bytes, st));
     if (!cached) RSVD_CUDA(cudaEventRecord(s->freed[slot], st));

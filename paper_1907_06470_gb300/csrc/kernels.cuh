@@ -133,18 +133,22 @@ constexpr int kSpmmSeg = 1024;
 // row of len entries takes ceil(len/kSpmmSeg) < 2 len/kSpmmSeg tasks.
 inline int64_t spmm_max_tasks(int64_t nnz) { return 2 * (nnz / kSpmmSeg) + 1; }
 size_t spmm_ws_bytes(int64_t nnz, int r);
-// The dense panel of a CSR A-pass: fmt 0 FP32 rows (f); fmt 1 BF16 rows (h);
-// fmt 2 24-bit rows, high 16 bits in h and the next 8 bits in l.  ld values
-// per row in every array (a multiple of 4 for fmt 1 and 2).
+// The dense panel of a CSR A-pass: fmt 0 FP32 rows (f, ld floats per row);
+// fmt 1 BF16 rows (h, ld values per row, ld a multiple of 4); fmt 2 24-bit
+// rows (p24, rb = spmm_p24_row_bytes(ld) bytes per row: groups of 128 values
+// as 256 bytes of high 16-bit parts then 128 bytes of low bytes).
 struct SpmmPanel {
   int fmt = 0;
   const float* f = nullptr;
   const uint16_t* h = nullptr;
-  const uint8_t* l = nullptr;
+  const uint8_t* p24 = nullptr;
   int64_t ld = 0;
+  int64_t rb = 0;
 };
-// Rows of X (K x r, ldx) rounded into the compact formats (fmt 1 or 2).
-rsvd_status spmm_pack(int fmt, int64_t K, int r, const float* X, int64_t ldx, uint16_t* h, uint8_t* l, int64_t ld,
+int64_t spmm_p24_row_bytes(int64_t ld);
+// Rows of X (K x r, ldx) rounded into the compact formats (fmt 1 into h, fmt 2
+// into p24).
+rsvd_status spmm_pack(int fmt, int64_t K, int r, const float* X, int64_t ldx, uint16_t* h, uint8_t* p24, int64_t ld,
                       cudaStream_t stream);
 rsvd_status spmm_csr_panel(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
                            int64_t nnz, const SpmmPanel& X, float* Y, int64_t ldy, bool accumulate, void* ws,

@@ -37,6 +37,8 @@ namespace {
 
 constexpr int kSpmmThreads = 256;
 constexpr int kSpmmGrab = 2;  // rows a warp takes per draw
+constexpr int kSpmmBuckets = 4096;             // panel row blocks the segment tasks are grouped by
+constexpr int64_t kSpmmBlockBytes = 32 << 20;  // bytes of panel rows per block
 
 __device__ __forceinline__ void fma4(float4& a, float v, const float4& x) {
   a.x = fmaf(v, x.x, a.x);
@@ -48,12 +50,14 @@ __device__ __forceinline__ void fma4(float4& a, float v, const float4& x) {
 // The gathered panel, in one of three formats (SpmmPanel::fmt):
 //   0  FP32 rows (f, ld floats per row)
 //   1  BF16 rows (h, ld 16-bit values per row): X rounded to BF16
-//   2  24-bit rows split in two arrays (h: the high 16 bits, l: the next 8
-//      bits, ld values per row each): X rounded to 16 significant bits, the
-//      value's bits being h << 16 | l << 8
+//   2  24-bit rows (p24, rb bytes per row): X rounded to 16 significant bits;
+//      each group of 128 values takes 384 bytes, the high 16 bits of the 128
+//      values (256 bytes) followed by their next 8 bits (128 bytes), so a
+//      value's bits are hi << 16 | lo << 8 and a gathered row is one
+//      contiguous 3-bytes-per-value run
 // Lane l of a warp holds the values 4l..4l+3 + 128t of a row, so a lane loads
-// one float4 (FP32), one uint2 (the 16-bit parts) and one uint32 (the low
-// bytes) per slot t.
+// one float4 (FP32), one uint2 (BF16), or one uint2 and one uint32 from the
+// same 384-byte group (24-bit) per slot t.
 template <int FMT>
 struct PanelSlot;
 
@@ -85,8 +89,9 @@ struct PanelSlot<2> {
   uint2 h;
   uint32_t l;
   __device__ __forceinline__ void load(const SpmmPanel& P, int64_t row, int q) {
-    h = __ldg(reinterpret_cast<const uint2*>(P.h + row * P.ld) + q);
-    l = __ldg(reinterpret_cast<const uint32_t*>(P.l + row * P.ld) + q);
+    const uint8_t* g = P.p24 + row * P.rb + (q >> 5) * 384;
+    h = __ldg(reinterpret_cast<const uint2*>(g) + (q & 31));
+    l = __ldg(reinterpret_cast<const uint32_t*>(g + 256) + (q & 31));
   }
   __device__ __forceinline__ void zero() {
     h = make_uint2(0u, 0u);
@@ -101,8 +106,8 @@ struct PanelSlot<2> {
 };
 
 // V4 slots per lane: panel rows of at most 128*V4 values.  Rows start 16-byte
-// (FP32), 8-byte (16-bit parts) and 4-byte (low bytes) aligned; values
-// r..4*ceil(r/4)-1 are read (inside ld) but never written to Y.
+// (FP32, 24-bit) or 8-byte (BF16) aligned; values r..4*ceil(r/4)-1 are read
+// (inside ld) but never written to Y.
 // Sum over entries [e0, e1) of one row into acc (lane l: columns 4l..4l+3 + 128t).
 template <int V4, int FMT>
 __device__ __forceinline__ void row_segment_vec(int64_t e0, int64_t e1, int lane, int nv,
@@ -236,21 +241,92 @@ __global__ void spmm_tasks_kernel(int64_t M, const int32_t* __restrict__ rowptr,
   }
 }
 
-// Persistent grid, one warp per task at a time (tasks gw, gw + warps, ...):
-// the partial product of one segment of a long row, written to
+// The segment tasks are run grouped by the panel row block (kSpmmBlockBytes
+// of panel rows) that holds the panel row of their first entry, so that the
+// warps running at any one time gather from a window of the panel that L2
+// keeps: the long rows' head segments share their panel rows, and so do the
+// segments of the dense columns of A (rows of the CSR of A^T).
+// Bucket of each task; counts per bucket.
+__global__ void spmm_task_bucket_kernel(const int* __restrict__ counter, int64_t max_tasks,
+                                        const int* __restrict__ task_row, const int* __restrict__ task_seg,
+                                        const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                        int64_t width, int* __restrict__ bucket_of, int* __restrict__ bucket_cnt) {
+  int64_t ntask = *counter;
+  if (ntask > max_tasks) ntask = max_tasks;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntask; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e0 = (int64_t)rowptr[task_row[t]] + (int64_t)task_seg[t] * kSpmmSeg;
+    int64_t b = (int64_t)colidx[e0] / width;
+    if (b >= kSpmmBuckets) b = kSpmmBuckets - 1;
+    bucket_of[t] = (int)b;
+    atomicAdd(&bucket_cnt[b], 1);
+  }
+}
+
+// Exclusive prefix sum of the kSpmmBuckets counts, in place (one block of 1024).
+__global__ void __launch_bounds__(1024) spmm_bucket_scan_kernel(int* __restrict__ bucket_cnt) {
+  constexpr int per = kSpmmBuckets / 1024;
+  __shared__ int wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int v[per];
+  int s = 0;
+#pragma unroll
+  for (int i = 0; i < per; ++i) {
+    v[i] = bucket_cnt[tid * per + i];
+    s += v[i];
+  }
+  int incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  int run = incl - s + (warp > 0 ? wsum[warp - 1] : 0);
+#pragma unroll
+  for (int i = 0; i < per; ++i) {
+    bucket_cnt[tid * per + i] = run;
+    run += v[i];
+  }
+}
+
+// order[]: the tasks grouped by bucket (their order inside a bucket does not
+// matter: each task writes its own partial slot).
+__global__ void spmm_bucket_scatter_kernel(const int* __restrict__ counter, int64_t max_tasks,
+                                           const int* __restrict__ bucket_of, int* __restrict__ bucket_cur,
+                                           int* __restrict__ order) {
+  int64_t ntask = *counter;
+  if (ntask > max_tasks) ntask = max_tasks;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntask; t += (int64_t)gridDim.x * blockDim.x)
+    order[atomicAdd(&bucket_cur[bucket_of[t]], 1)] = (int)t;
+}
+
+// Persistent grid, one warp per task at a time (positions gw, gw + warps, ...
+// of order[]): the partial product of one segment of a long row, written to
 // partial[task * ldp ...] (ldp = 4 ceil(r/4)).
 template <int V4, int FMT>
 __global__ void __launch_bounds__(kSpmmThreads, V4 >= 4 ? 2 : 3)
 spmm_segment_kernel(int r, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                     const float* __restrict__ val, const SpmmPanel P, const int* __restrict__ counter,
-                    const int* __restrict__ task_row, const int* __restrict__ task_seg, int64_t max_tasks,
-                    float* __restrict__ partial, int64_t ldp) {
+                    const int* __restrict__ task_row, const int* __restrict__ task_seg,
+                    const int* __restrict__ order, int64_t max_tasks, float* __restrict__ partial, int64_t ldp) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * kSpmmThreads) >> 5;
   const int nv = (r + 3) >> 2;
   int64_t ntask = *counter;
   if (ntask > max_tasks) ntask = max_tasks;
-  for (int64_t task = ((int64_t)blockIdx.x * kSpmmThreads + threadIdx.x) >> 5; task < ntask; task += nwarps) {
+  for (int64_t i = ((int64_t)blockIdx.x * kSpmmThreads + threadIdx.x) >> 5; i < ntask; i += nwarps) {
+    const int64_t task = order[i];
     const int row = task_row[task], seg = task_seg[task];
     const int64_t e0 = (int64_t)rowptr[row] + (int64_t)seg * kSpmmSeg;
     const int64_t e1 = min((int64_t)rowptr[row + 1], e0 + kSpmmSeg);
@@ -306,11 +382,11 @@ spmm_combine_kernel(int r, const int32_t* __restrict__ rowptr, const int* __rest
 }
 
 // Panel conversion for the compact formats: rows of X (K x r, ldx) rounded to
-// BF16 (fmt 1, into h) or to 16 significant bits (fmt 2, high 16 bits into h,
-// the next 8 into l), both round-to-nearest-even; values r..ld-1 are zero.
-// One thread per value.
+// BF16 (fmt 1, into h, ld values per row) or to 16 significant bits (fmt 2,
+// into p24, rb bytes per row in 384-byte groups of 128 values), both
+// round-to-nearest-even; values r..ld-1 are zero.  One thread per value.
 __global__ void spmm_pack_kernel(int fmt, int64_t K, int r, const float* __restrict__ X, int64_t ldx,
-                                 uint16_t* __restrict__ h, uint8_t* __restrict__ l, int64_t ld) {
+                                 uint16_t* __restrict__ h, uint8_t* __restrict__ p24, int64_t ld, int64_t rb) {
   const int64_t total = K * ld;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = i / ld;
@@ -322,8 +398,10 @@ __global__ void spmm_pack_kernel(int fmt, int64_t K, int r, const float* __restr
       uint32_t b = __float_as_uint(x);
       if ((b & 0x7fffffffu) > 0x7f800000u) b |= 0x00400000u;  // NaN stays NaN in 24 bits
       else if ((b & 0x7f800000u) != 0x7f800000u) b += 0x7fu + ((b >> 8) & 1u);
-      h[i] = (uint16_t)(b >> 16);
-      l[i] = (uint8_t)((b >> 8) & 0xffu);
+      uint8_t* g = p24 + row * rb + (c >> 7) * 384;
+      const int w = c & 127;
+      reinterpret_cast<uint16_t*>(g)[w] = (uint16_t)(b >> 16);
+      g[256 + w] = (uint8_t)((b >> 8) & 0xffu);
     }
   }
 }
@@ -399,8 +477,8 @@ int64_t resident_comb() {
 template <int V4, int FMT>
 rsvd_status launch_vec(int64_t M, int r, const int32_t* rowptr, const int32_t* colidx, const float* val,
                        const SpmmPanel& X, float* Y, int64_t ldy, int acc, bool split, unsigned long long* next,
-                       const int* counter, const int* task_row, const int* task_seg, int64_t max_tasks,
-                       float* partial, int64_t ldp, cudaStream_t stream) {
+                       const int* counter, const int* task_row, const int* task_seg, const int* order,
+                       int64_t max_tasks, float* partial, int64_t ldp, cudaStream_t stream) {
   const int64_t row_blocks = cdiv(cdiv(M, kSpmmGrab), kSpmmThreads / 32);
   const int64_t res = resident_vec<V4, FMT>();
   spmm_csr_vec_kernel<V4, FMT><<<(unsigned)(row_blocks < res ? row_blocks : res), kSpmmThreads, 0, stream>>>(
@@ -410,7 +488,7 @@ rsvd_status launch_vec(int64_t M, int r, const int32_t* rowptr, const int32_t* c
   const int64_t task_blocks = cdiv(max_tasks, kSpmmThreads / 32);
   const int64_t sres = resident_seg<V4, FMT>();
   spmm_segment_kernel<V4, FMT><<<(unsigned)(task_blocks < sres ? task_blocks : sres), kSpmmThreads, 0, stream>>>(
-      r, rowptr, colidx, val, X, counter, task_row, task_seg, max_tasks, partial, ldp);
+      r, rowptr, colidx, val, X, counter, task_row, task_seg, order, max_tasks, partial, ldp);
   RSVD_CUDA(after_launch());
   const int64_t cres = resident_comb<V4>();
   spmm_combine_kernel<V4><<<(unsigned)(task_blocks < cres ? task_blocks : cres), kSpmmThreads, 0, stream>>>(
@@ -425,19 +503,25 @@ size_t spmm_ws_bytes(int64_t nnz, int r) {
   const int64_t tasks = spmm_max_tasks(nnz);
   Sizer s;
   s.take<int>(4);
-  s.take<int>((size_t)tasks);
-  s.take<int>((size_t)tasks);
+  s.take<int>(kSpmmBuckets);
+  s.take<int>((size_t)tasks);  // task_row
+  s.take<int>((size_t)tasks);  // task_seg
+  s.take<int>((size_t)tasks);  // bucket_of
+  s.take<int>((size_t)tasks);  // order
   s.take<float>((size_t)tasks * round_up(r, 4));
   return s.used + 256;
 }
 
-rsvd_status spmm_pack(int fmt, int64_t K, int r, const float* X, int64_t ldx, uint16_t* h, uint8_t* l, int64_t ld,
+int64_t spmm_p24_row_bytes(int64_t ld) { return cdiv(ld, 128) * 384; }
+
+rsvd_status spmm_pack(int fmt, int64_t K, int r, const float* X, int64_t ldx, uint16_t* h, uint8_t* p24, int64_t ld,
                       cudaStream_t stream) {
   if (K <= 0) return RSVD_OK;
-  if ((fmt != 1 && fmt != 2) || r < 1 || ldx < r || ld < round_up(r, 4) || ld % 4 || !X || !h || (fmt == 2 && !l))
+  if ((fmt != 1 && fmt != 2) || r < 1 || ldx < r || ld < round_up(r, 4) || ld % 4 || !X || (fmt == 1 && !h) ||
+      (fmt == 2 && !p24))
     return fail(RSVD_ERR_INVALID_ARG, "spmm_pack: bad arguments");
   const int64_t blocks = std::min<int64_t>(cdiv(K * ld, 256), 152 * 32);
-  spmm_pack_kernel<<<(unsigned)blocks, 256, 0, stream>>>(fmt, K, r, X, ldx, h, l, ld);
+  spmm_pack_kernel<<<(unsigned)blocks, 256, 0, stream>>>(fmt, K, r, X, ldx, h, p24, ld, spmm_p24_row_bytes(ld));
   RSVD_CUDA(after_launch());
   return RSVD_OK;
 }
@@ -448,7 +532,8 @@ rsvd_status spmm_csr_panel(int64_t M, int r, const int32_t* rowptr, const int32_
   if (M <= 0) return RSVD_OK;
   const bool fp32 = X.fmt == 0;
   if (r < 1 || r > kSpmmMaxR || X.ld < r || ldy < r || !rowptr || !Y || X.fmt < 0 || X.fmt > 2 ||
-      (fp32 && !X.f) || (!fp32 && (!X.h || X.ld % 4 || (X.fmt == 2 && !X.l))))
+      (fp32 && !X.f) || (X.fmt == 1 && (!X.h || X.ld % 4)) ||
+      (X.fmt == 2 && (!X.p24 || X.ld % 4 || X.rb != spmm_p24_row_bytes(X.ld))))
     return fail(RSVD_ERR_INVALID_ARG, "spmm_csr: bad arguments");
   const int64_t blocks = cdiv(M, kSpmmThreads / 32);
   if (blocks > 0x7fffffffLL) return fail(RSVD_ERR_INVALID_ARG, "spmm_csr: too many rows");
@@ -474,7 +559,8 @@ rsvd_status spmm_csr_panel(int64_t M, int r, const int32_t* rowptr, const int32_
   const bool ws_ok = ws && reinterpret_cast<uintptr_t>(ws) % 16 == 0;
   const int64_t max_tasks = spmm_max_tasks(nnz);
   const bool split = ws_ok && ws_bytes >= spmm_ws_bytes(nnz, r) && nnz > kSpmmSeg;
-  int *counter = nullptr, *task_row = nullptr, *task_seg = nullptr;
+  int *counter = nullptr, *task_row = nullptr, *task_seg = nullptr, *bucket_cnt = nullptr, *bucket_of = nullptr,
+      *order = nullptr;
   unsigned long long* next = nullptr;
   float* partial = nullptr;
   const int64_t ldp = round_up(r, 4);
@@ -483,21 +569,39 @@ rsvd_status spmm_csr_panel(int64_t M, int r, const int32_t* rowptr, const int32_
     counter = c.take<int>(4);
     next = reinterpret_cast<unsigned long long*>(counter + 2);
     if (split) {
+      bucket_cnt = c.take<int>(kSpmmBuckets);
       task_row = c.take<int>((size_t)max_tasks);
       task_seg = c.take<int>((size_t)max_tasks);
+      bucket_of = c.take<int>((size_t)max_tasks);
+      order = c.take<int>((size_t)max_tasks);
       partial = c.take<float>((size_t)max_tasks * ldp);
     }
-    RSVD_CUDA(cudaMemsetAsync(counter, 0, 4 * sizeof(int), stream));
+    // the counters, and the bucket counts carved right after them
+    const size_t zero = split ? (size_t)(reinterpret_cast<char*>(bucket_cnt + kSpmmBuckets) -
+                                         reinterpret_cast<char*>(counter))
+                              : 4 * sizeof(int);
+    RSVD_CUDA(cudaMemsetAsync(counter, 0, zero, stream));
   }
   if (split) {
     int tb = (int)cdiv(M, 256);
     if (tb > 152 * 16) tb = 152 * 16;
     spmm_tasks_kernel<<<tb, 256, 0, stream>>>(M, rowptr, counter, (int)max_tasks, task_row, task_seg);
     RSVD_CUDA(after_launch());
+    // group the tasks by the block of panel rows of their first entry
+    const int64_t row_bytes = X.fmt == 0 ? X.ld * 4 : (X.fmt == 1 ? X.ld * 2 : X.rb);
+    const int64_t width = std::max<int64_t>(1, kSpmmBlockBytes / row_bytes);
+    const int gb = (int)std::min<int64_t>(cdiv(max_tasks, 256), 152 * 8);
+    spmm_task_bucket_kernel<<<gb, 256, 0, stream>>>(counter, max_tasks, task_row, task_seg, rowptr, colidx, width,
+                                                    bucket_of, bucket_cnt);
+    RSVD_CUDA(after_launch());
+    spmm_bucket_scan_kernel<<<1, 1024, 0, stream>>>(bucket_cnt);
+    RSVD_CUDA(after_launch());
+    spmm_bucket_scatter_kernel<<<gb, 256, 0, stream>>>(counter, max_tasks, bucket_of, bucket_cnt, order);
+    RSVD_CUDA(after_launch());
   }
 #define RSVD_VEC(V, F)                                                                                           \
   return launch_vec<V, F>(M, r, rowptr, colidx, val, X, Y, ldy, acc, split, next, counter, task_row, task_seg, \
-                          max_tasks, partial, ldp, stream)
+                          order, max_tasks, partial, ldp, stream)
 #define RSVD_VEC_F(V)                  \
   do {                                 \
     if (X.fmt == 0) RSVD_VEC(V, 0);    \

@@ -258,11 +258,12 @@ def test_csr_plan_rules(lib):
     fp32_cap = out.value
     o513 = _lib.RsvdOpts(prec=1, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
     assert lib.rsvd_plan_min_cap(100000, 50000, 500, 13, C.byref(o513), C.byref(out)) == 1
-    # the compact panels (16 / 24 bits per value of the larger side, ldr 352) on top
-    for prec, per in ((2, 2), (3, 3)):
+    # the compact panels on top, for the larger side (ldr 352): BF16 2 bytes per
+    # value; 24 bits in 384-byte groups of 128 values (3 groups per row)
+    for prec, row_bytes in ((2, 352 * 2), (3, 3 * 384)):
         oc = _lib.RsvdOpts(prec=prec, refine=1, mb=0, nb=0, n_slots=2, dtype=1, kind=1)
         assert lib.rsvd_plan_min_cap(100000, 50000, 300, 50, C.byref(oc), C.byref(out)) == 0
-        assert 0 <= out.value - fp32_cap - 100000 * 352 * per <= 2048
+        assert 0 <= out.value - fp32_cap - 100000 * row_bytes <= 2048
     for prec, dtype in ((4, 1), (0, 0), (1, 0)):  # FP8, FP64
         ob = _lib.RsvdOpts(prec=prec, refine=1, mb=0, nb=0, n_slots=2, dtype=dtype, kind=1)
         assert lib.rsvd_plan(1000, 500, 10, 5, 1, 1, 0, C.byref(ob), C.byref(h)) in (1, 8)
@@ -271,13 +272,14 @@ def test_csr_plan_rules(lib):
 
 def test_csr_apass_workspace_sizes(lib):
     """FP32 passes need the split-row workspace only; BF16 / BF16X3 passes add
-    the compact panel (K rows of round_up(r, 4) values, 2 and 3 bytes each)."""
+    the compact panel (K rows: round_up(r, 4) BF16 values, or 384 bytes per
+    group of 128 values at 24 bits)."""
     nnz, K, r = 10_000_000, 40000, 350
     base = lib.rsvd_spmm_workspace(nnz, r)
     assert lib.rsvd_csr_apass_workspace(nnz, K, r, 1) == base
-    for prec, per in ((2, 2), (3, 3)):
+    for prec, row_bytes in ((2, 352 * 2), (3, 3 * 384)):
         extra = lib.rsvd_csr_apass_workspace(nnz, K, r, prec) - base
-        assert K * 352 * per <= extra <= K * 352 * per + 1024
+        assert K * row_bytes <= extra <= K * row_bytes + 1024
     assert lib.rsvd_csr_apass_workspace(nnz, K, 0, 2) == 0
 
 
