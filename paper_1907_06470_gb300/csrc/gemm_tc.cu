@@ -238,7 +238,9 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     if (lane == 0 && DIRECT) {
       // A tiles straight into the operand slots: forward, one 64 x 128 box
       // (K-major rows of 128 bytes); transposed, two 64 x 64 boxes (the two
-      // 64-row halves of the MN-major tile, 8 KB apart)
+      // 64-row halves of the MN-major tile, 8 KB apart).  A and the panel
+      // share the slot, so this one thread loads both for each K step (two
+      // producer lanes of one warp would take turns at their waits).
       const int nA = (SPLIT && a.a_lo) ? 2 : 1;
       const uint32_t a_bytes = (uint32_t)(A16_BYTES * nA);
       RingPos rop;
@@ -247,14 +249,19 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         const int64_t z = u / mn_tiles, mt = u % a.mtiles;
         const int64_t k0 = z * a.ksteps_per_split;
         const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
+        const int32_t ny = (int32_t)(((u / a.mtiles) % a.ntiles) * NP);  // first panel column of the tile
         for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
           const int sop = rop.slot;
           if (!ptx::mbar_wait(&emptyOp[sop], rop.phase ^ 1, vstatus, kWaitNs)) {
             flag_timeout(a.status, kWaitAFree, sop, ks, u); s_abort = 1; break;
           }
           ptx::mbar_arrive_expect_tx(&fullA[sop], a_bytes);
+          ptx::mbar_arrive_expect_tx(&fullB[sop], b_bytes * L::PARTS);
           issued |= 1u << sop;
           parity = (parity & ~(1u << sop)) | (rop.phase << sop);
+          ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 0), &mapB, &fullB[sop], (int32_t)(ks * BK), ny);
+          if (SPLIT)
+            ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 1), &mapBlo, &fullB[sop], (int32_t)(ks * BK), ny);
           for (int part = 0; part < nA; ++part) {
             const CUtensorMap* map = part ? &mapAlo : &mapA;
             uint8_t* dst = smem + L::a16_off(sop, part);
@@ -269,7 +276,10 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       }
       // every load issued has landed before the CTA may exit (immediate unless stopped early)
       for (int i = 0; i < SOP; ++i)
-        if (issued >> i & 1) ptx::mbar_wait_drain(&fullA[i], parity >> i & 1, kWaitNs);
+        if (issued >> i & 1) {
+          ptx::mbar_wait_drain(&fullA[i], parity >> i & 1, kWaitNs);
+          ptx::mbar_wait_drain(&fullB[i], parity >> i & 1, kWaitNs);
+        }
     } else if (lane == 0) {
       RingPos r32;
       uint32_t issued = 0, parity = 0;
@@ -292,7 +302,7 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       }
       for (int i = 0; i < S32; ++i)
         if (issued >> i & 1) ptx::mbar_wait_drain(&full32[i], parity >> i & 1, kWaitNs);
-    } else if (lane == 1 && !a.gram) {
+    } else if (lane == 1 && !a.gram && !DIRECT) {
       RingPos rop;
       uint32_t issued = 0, parity = 0;
       for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
