@@ -9,6 +9,7 @@
 //   dA = [U | P] [V M^T + Q | V]^T        (one rank-2k product).
 // The k x k pieces are formed in FP64 (the U^T dU and V^T dV reductions add
 // FP64 chunk sums); the panels and the final product run in the data type.
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -19,18 +20,24 @@ namespace {
 
 constexpr int64_t kChunk = 256;
 
+// One warp per entry: lane l adds the chunks l, l + 32, ... in FP64, then the
+// 32 lane sums are added by a fixed shuffle tree (the same order every call).
 template <typename T>
 __global__ void sum_partials_f64_kernel(int k, int64_t nchunks, const T* __restrict__ P, double* __restrict__ out) {
   const int64_t kk = (int64_t)k * k;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < kk; e += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < kk; e += warps) {
     double s = 0.0;
-    for (int64_t c = 0; c < nchunks; ++c) s += (double)P[c * kk + e];
-    out[e] = s;
+    for (int64_t c = lane; c < nchunks; c += 32) s += (double)P[c * kk + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[e] = s;
   }
 }
 
-// One CTA: the k x k matrices M^T (to multiply V), U^T dU and V^T dV in the data
-// type, and 1/S.  A pair with S_i^2 = S_j^2 to within 1e-12 S_max^2 gets F = 0.
+// The k x k matrices M^T (to multiply V), U^T dU and V^T dV in the data type,
+// one entry per thread over the grid, and 1/S (block 0).  A pair with S_i^2 = S_j^2 to within 1e-12 S_max^2 gets F = 0.
 template <typename T>
 __global__ void small_adjoint_kernel(int k, const T* __restrict__ S, const T* __restrict__ dS,
                                      const double* __restrict__ UtdU, const double* __restrict__ VtdV,
@@ -39,7 +46,7 @@ __global__ void small_adjoint_kernel(int k, const T* __restrict__ S, const T* __
   double smax = 0.0;
   for (int i = 0; i < k; ++i) smax = fmax(smax, fabs((double)S[i]));
   const double guard = 1e-12 * smax * smax;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
     const int i = e / k, j = e % k;
     const double si = (double)S[i], sj = (double)S[j];
     double Fij = 0.0;
@@ -53,7 +60,8 @@ __global__ void small_adjoint_kernel(int k, const T* __restrict__ S, const T* __
     UtdU_t[e] = UtdU ? (T)UtdU[e] : T(0);
     VtdV_t[e] = VtdV ? (T)VtdV[e] : T(0);
   }
-  for (int i = threadIdx.x; i < k; i += blockDim.x) Sinv[i] = (T)(1.0 / (double)S[i]);
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) Sinv[i] = (T)(1.0 / (double)S[i]);
 }
 
 // L = [U | (dU - UX) diag(Sinv)]   (rows x 2k), UX = U (U^T dU) precomputed.
@@ -109,7 +117,8 @@ template <typename T>
 rsvd_status proj_gram(int64_t rows, int k, const T* X, const T* Y, T* partial, double* out, cudaStream_t st) {
   const int64_t nchunks = cdiv(rows, kChunk);
   RSVD_TRY(simt_gemm_partials<T>(k, k, rows, X, k, true, Y, k, (int)nchunks, kChunk, partial, st));
-  sum_partials_f64_kernel<T><<<(int)cdiv((int64_t)k * k, 256), 256, 0, st>>>(k, nchunks, partial, out);
+  sum_partials_f64_kernel<T><<<(int)std::min<int64_t>(cdiv((int64_t)k * k * 32, 256), 152 * 8), 256, 0, st>>>(
+      k, nchunks, partial, out);
   RSVD_CUDA(after_launch());
   return RSVD_OK;
 }
@@ -153,8 +162,9 @@ rsvd_status backward_typed(int64_t m, int64_t n, int k, const T* U, const T* S, 
   T* Sinv = small + 3 * (size_t)k * k;
   if (dU) RSVD_TRY(proj_gram<T>(m, k, U, dU, partial, UtdU, st));
   if (dV) RSVD_TRY(proj_gram<T>(n, k, V, dV, partial, VtdV, st));
-  small_adjoint_kernel<T><<<1, 256, 0, st>>>(k, S, dS, dU ? UtdU : nullptr, dV ? VtdV : nullptr, Mt, UtdU_t,
-                                             VtdV_t, Sinv);
+  small_adjoint_kernel<T><<<(int)cdiv((int64_t)k * k, 256), 256, 0, st>>>(k, S, dS, dU ? UtdU : nullptr,
+                                                                          dV ? VtdV : nullptr, Mt, UtdU_t, VtdV_t,
+                                                                          Sinv);
   RSVD_CUDA(after_launch());
   // left panel [U | P]
   if (dU) RSVD_TRY(simt_gemm<T>(m, k, k, U, k, false, UtdU_t, k, XY, k, false, 1, k, nullptr, st));

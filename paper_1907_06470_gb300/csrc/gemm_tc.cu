@@ -5,13 +5,18 @@
 //
 // A stays FP32 in HBM and is read exactly once per pass.  Each CTA is a
 // persistent, warp-specialised pipeline:
-//   warp 0     TMA producer: FP32 tile of A (64 x 128 or 128 x 64) and the
-//              BF16 panel tile (64 x N, 128-byte swizzle) per K step of 64
+//   warp 0     TMA producer: FP32 tile of A (64 x 128 or 128 x 64) per K
+//              step of 64 (a 16-bit A: the A tile and the panel tile, one
+//              thread, straight into the operand slot)
 //   warp 1     TMEM allocator and single-thread tcgen05.mma issuer
 //   warps 2-5  converters: round the FP32 tile to BF16 (and the residual to a
 //              second BF16 "lo" tile in split mode), transposing it for A^T,
 //              into the K-major 128-byte-swizzled operand layout
 //   warps 6-9  epilogue: tcgen05.ld of the FP32 accumulator, stores to C
+//   warp 10    TMA producer of the BF16 panel tile (64 x N, 128-byte
+//              swizzle) per K step, for the converted sources
+// Every producer loop runs in a warp of its own: two lanes of one warp that
+// each spin on their own barriers take turns and starve each other.
 // Two TMEM accumulators let the epilogue of one 128-row tile overlap the MMAs
 // of the next.  The reduction dimension may be split across CTAs for load
 // balance; the partial products are then added in a fixed order by a second
@@ -72,7 +77,11 @@ constexpr int kSrc32 = 0, kSrc8 = 1, kSrc16 = 2;
 constexpr int kSplitMaxNP = 192;   // widest split-mode panel one pass supports
 constexpr int64_t kSplitChainSteps = 8;   // split mode: K steps (of 64) per TMEM accumulation chain
 constexpr int64_t kPlainChainSteps = 32;  // other modes, when a TMEM running sum fits
-constexpr int THREADS = 320;
+constexpr int THREADS = 352;
+// epilogue staging: one 32 x 33 float block per epilogue warp (row stride 33:
+// no bank conflicts in either direction)
+constexpr int kStageFloatsPerWarp = 32 * 33;
+constexpr size_t kStageBytes = 4 * kStageFloatsPerWarp * sizeof(float);
 constexpr uint64_t kWaitNs = 1000000000ull;
 
 struct TcArgs {
@@ -103,6 +112,7 @@ struct TcArgs {
   int sum_col;          // TMEM column of the running sum of a unit's chains (-1: in the output itself)
   int gram;             // 1: C = A^T A with one row tile: the panel operand is the converted A tile
   uint32_t idesc;       // tcgen05 instruction descriptor (operand type BF16 or FP16, FP32 accumulator)
+  int c_stage;          // shared-memory offset of the epilogue's staging tiles (kStageBytes), or -1
 };
 
 #ifndef RSVD_TC_MAX_S32
@@ -302,28 +312,6 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       }
       for (int i = 0; i < S32; ++i)
         if (issued >> i & 1) ptx::mbar_wait_drain(&full32[i], parity >> i & 1, kWaitNs);
-    } else if (lane == 1 && !a.gram && !DIRECT) {
-      RingPos rop;
-      uint32_t issued = 0, parity = 0;
-      for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
-        const int64_t z = u / mn_tiles;
-        const int64_t k0 = z * a.ksteps_per_split;
-        const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
-        for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
-          const int sop = rop.slot;
-          if (!ptx::mbar_wait(&emptyOp[sop], rop.phase ^ 1, vstatus, kWaitNs)) {
-            flag_timeout(a.status, kWaitPanelFree, sop, ks, u); s_abort = 1; break;
-          }
-          ptx::mbar_arrive_expect_tx(&fullB[sop], b_bytes * L::PARTS);
-          issued |= 1u << sop;
-          parity = (parity & ~(1u << sop)) | (rop.phase << sop);
-          const int32_t ny = (int32_t)(((u / a.mtiles) % a.ntiles) * NP);  // first panel column of the tile
-          ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 0), &mapB, &fullB[sop], (int32_t)(ks * BK), ny);
-          if (SPLIT) ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 1), &mapBlo, &fullB[sop], (int32_t)(ks * BK), ny);
-        }
-      }
-      for (int i = 0; i < SOP; ++i)
-        if (issued >> i & 1) ptx::mbar_wait_drain(&fullB[i], parity >> i & 1, kWaitNs);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -513,6 +501,34 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       }
       if (!ok) break;
     }
+  } else if (warp == 10) {
+    // ---------------- panel producer ----------------
+    // With a converted source (FP32, FP8) the panel tiles load into the
+    // operand slots as the MMAs free them, from a warp of their own so that
+    // they never wait behind the A prefetch (and the other way round).
+    if (lane == 0 && !a.gram && !DIRECT) {
+      RingPos rop;
+      uint32_t issued = 0, parity = 0;
+      for (int64_t u = blockIdx.x; u < units && !*vabort; u += gridDim.x) {
+        const int64_t z = u / mn_tiles;
+        const int64_t k0 = z * a.ksteps_per_split;
+        const int64_t k1 = min(a.ksteps, k0 + a.ksteps_per_split);
+        for (int64_t ks = k0; ks < k1; ++ks, rop.next(SOP)) {
+          const int sop = rop.slot;
+          if (!ptx::mbar_wait(&emptyOp[sop], rop.phase ^ 1, vstatus, kWaitNs)) {
+            flag_timeout(a.status, kWaitPanelFree, sop, ks, u); s_abort = 1; break;
+          }
+          ptx::mbar_arrive_expect_tx(&fullB[sop], b_bytes * L::PARTS);
+          issued |= 1u << sop;
+          parity = (parity & ~(1u << sop)) | (rop.phase << sop);
+          const int32_t ny = (int32_t)(((u / a.mtiles) % a.ntiles) * NP);  // first panel column of the tile
+          ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 0), &mapB, &fullB[sop], (int32_t)(ks * BK), ny);
+          if (SPLIT) ptx::tma_load_2d(smem + L::b16_off(NP, SOP, sop, 1), &mapBlo, &fullB[sop], (int32_t)(ks * BK), ny);
+        }
+      }
+      for (int i = 0; i < SOP; ++i)
+        if (issued >> i & 1) ptx::mbar_wait_drain(&fullB[i], parity >> i & 1, kWaitNs);
+    }
   } else if (warp >= 6) {
     // ---------------- epilogue ----------------
     // (warps 6-9 only: with a 16-bit source the converter warps 2-5 stay idle)
@@ -575,7 +591,27 @@ tc_apass_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         } else {
           ptx::tmem_ld_wait();
         }
-        if (row < a.M && c0 < ncols) {
+        if (a.c_stage >= 0) {
+          // through shared memory: the warp's 32 x 32 block goes out one row
+          // per store, 32 consecutive columns (128 bytes) per instruction,
+          // instead of 32 rows x 16 bytes (large outputs are write bound)
+          float* stg = reinterpret_cast<float*>(smem + a.c_stage) + q * kStageFloatsPerWarp;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = __uint_as_float(v[j]);
+          __syncwarp();
+          const int64_t row0 = mt * BM + q * 32;
+          const bool col_ok = c0 + lane < ncols;
+          float* cbase = a.C + z * a.c_split_stride + col0 + c0 + lane;
+#pragma unroll 4
+          for (int rr = 0; rr < 32; ++rr) {
+            if (row0 + rr < a.M && col_ok) {
+              float* p = cbase + (row0 + rr) * a.ldc;
+              const float x = stg[rr * 33 + lane];
+              *p = add ? *p + x : x;
+            }
+          }
+          __syncwarp();
+        } else if (row < a.M && c0 < ncols) {
           const int nv = min(32, ncols - c0);
           if (add && nv == 32 && (a.ldc & 3) == 0 && (col0 & 3) == 0) {
 #pragma unroll
@@ -916,8 +952,22 @@ rsvd_status tc_apass_run(const TcSource& src, int64_t m, int64_t n, int trans, i
     s32 = kMaxS32;
     while (s32 > 2 && need(sop, s32) > kSmemMax) --s32;
   }
-  const size_t smem = need(sop, s32);
+  size_t smem = need(sop, s32);
   if (smem > kSmemMax) return fail(RSVD_ERR_UNSUPPORTED, "tensor-core A-pass: shared memory plan too large");
+  // products with a large output (the column tiles of a wide product) stage
+  // the epilogue's stores through shared memory, after the barriers; a
+  // staging ring one stage shorter if that is what it takes
+  ta.c_stage = -1;
+  if (src.wide) {
+    auto staged = [&](int sp, int d) { return round_up(need(sp, d) - 1024, 128) + kStageBytes + 1024; };
+    if (staged(sop, s32) > kSmemMax && s32 > 2) --s32;
+    if (staged(sop, s32) <= kSmemMax) {
+      ta.c_stage = (int)round_up(need(sop, s32) - 1024, 128);
+      smem = staged(sop, s32);
+    } else {
+      smem = need(sop, s32);
+    }
+  }
   ta.s32 = s32;
   ta.sop = sop;
   auto launch = [&](auto kern) -> rsvd_status {
