@@ -390,17 +390,21 @@ __global__ void jacobi_cluster_f32_kernel(int rows, int r, const double* __restr
 
 // FP32 one-sided Jacobi in one CTA with M and W in shared memory: the cheap
 // first phase.  Columns are stored with stride ldm = r rounded up to 4; each
-// half-warp rotates one column pair, lane l holding the float4s l, l + 16, ...
-// (V of them, V = ceil(r / 64)) of both columns, so a half-warp reads 256
-// contiguous bytes per access (no bank conflicts).  The 64 half-warps of the
-// CTA cover every pair of a round for r <= 128 at once.  The rotations are
-// accumulated in W32 (column-major r x r), which the FP64 phase then
-// orthonormalises and applies to M before finishing in FP64.
+// group of kF32PairLanes (8) lanes rotates one column pair, lane l of the
+// group holding the float4s l, l + 8, ... (V of them, V = ceil(r / 32)) of
+// both columns, so a group reads 128 contiguous bytes per access (no bank
+// conflicts).  The CTA has a group per pair of a round (480 threads at
+// r = 120).  A round is bound by instruction issue: every group computes the
+// rotation's scalars, so eight lanes per pair (rather than a half-warp) issue
+// half the warp-instructions per round.  The rotations are accumulated in W32
+// (column-major r x r), which the FP64 phase then orthonormalises and applies
+// to M before finishing in FP64.
 constexpr int kF32MaxR = 160;
+constexpr int kF32PairLanes = 8;
 
-__device__ __forceinline__ float half_warp_sum(float v) {
+__device__ __forceinline__ float pair_group_sum(float v) {
 #pragma unroll
-  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = kF32PairLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
@@ -418,7 +422,7 @@ size_t f32_jacobi_smem(int r) {
 }
 
 template <int V>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kF32PairLanes * kF32MaxR / 2)
 jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32, int* sweeps_out) {
   extern __shared__ __align__(16) float smf[];
   const int ldm = (r + 3) & ~3;
@@ -430,7 +434,7 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
   __shared__ int s_rot;
   __shared__ int s_maxrel;  // bits of the largest relative off-diagonal rotated in the sweep
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, warps = nt >> 5;
-  const int hw = tid >> 4, hl = tid & 15, nhw = nt >> 4;  // half-warp index, lane in it
+  const int hw = tid / kF32PairLanes, hl = tid % kF32PairLanes, nhw = nt / kF32PairLanes;  // group, lane in it
   const int rp = r + (r & 1), npairs = rp / 2;
   float f = 0.f;
   for (int c = warp; c < r; c += warps)
@@ -467,7 +471,7 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
     bool my_rot = false;
     float my_mrel = 0.f;
     for (int round = 0; round < rp - 1; ++round) {
-      // every half-warp takes the same number of iterations (shuffles need the full warp)
+      // every group takes the same number of iterations (shuffles need the full warp)
       for (int s0 = 0; s0 < npairs; s0 += nhw) {
         const int sl = s0 + hw;
         int p = 0, q = 0;
@@ -485,13 +489,13 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
         float g = 0.f;
 #pragma unroll
         for (int t = 0; t < V; ++t) {
-          const int i4 = hl + 16 * t;
+          const int i4 = hl + kF32PairLanes * t;
           const bool ok = active && i4 < ld4;
           xv[t] = ok ? mp4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
           yv[t] = ok ? mq4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
           g = fmaf(xv[t].x, yv[t].x, fmaf(xv[t].y, yv[t].y, fmaf(xv[t].z, yv[t].z, fmaf(xv[t].w, yv[t].w, g))));
         }
-        g = half_warp_sum(g);
+        g = pair_group_sum(g);
         if (active && fabsf(g) > tol * sqrtf(a * b) && a > zero2 && b > zero2) {
           my_rot = true;
           my_mrel = fmaxf(my_mrel, fabsf(g) * rsqrtf(a * b));
@@ -518,7 +522,7 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
           float4* wq = reinterpret_cast<float4*>(W + q * ldm);
 #pragma unroll
           for (int u = 0; u < V; ++u) {
-            const int i4 = hl + 16 * u;
+            const int i4 = hl + kF32PairLanes * u;
             if (i4 < ld4) {
               const float4 xx = xv[u], yy = yv[u];
               const float4 wu = wp[i4], wv = wq[i4];
@@ -753,13 +757,21 @@ rsvd_status jacobi_svd(int rows, int r, const double* Mc, double* sigma, double*
       RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
       RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
       RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      RSVD_CUDA(cudaFuncSetAttribute(jacobi_f32_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
       attr = true;
     }
-    // float4s per lane and column: ceil(ceil(r / 4) / 16)
-    const int V = (int)cdiv(cdiv(r, 4), 16);
-    if (V <= 1) jacobi_f32_kernel<1><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
-    else if (V == 2) jacobi_f32_kernel<2><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
-    else jacobi_f32_kernel<3><<<1, 1024, f32_jacobi_smem(r), stream>>>(r, Mc, ws.W32, ws.sweeps);
+    // float4s per lane and column: ceil(ceil(r / 4) / 8); a group of lanes per
+    // column pair of a round (a multiple of 32 threads, at most 1024)
+    const int V = (int)cdiv(cdiv(r, 4), kF32PairLanes);
+    const int npairs = (r + (r & 1)) / 2;
+    const int nt = (int)round_up((int64_t)npairs * kF32PairLanes, 32);  // at most 640 (r <= 160)
+    const size_t sm = f32_jacobi_smem(r);
+    if (V <= 1) jacobi_f32_kernel<1><<<1, nt, sm, stream>>>(r, Mc, ws.W32, ws.sweeps);
+    else if (V == 2) jacobi_f32_kernel<2><<<1, nt, sm, stream>>>(r, Mc, ws.W32, ws.sweeps);
+    else if (V == 3) jacobi_f32_kernel<3><<<1, nt, sm, stream>>>(r, Mc, ws.W32, ws.sweeps);
+    else if (V == 4) jacobi_f32_kernel<4><<<1, nt, sm, stream>>>(r, Mc, ws.W32, ws.sweeps);
+    else jacobi_f32_kernel<5><<<1, nt, sm, stream>>>(r, Mc, ws.W32, ws.sweeps);
     RSVD_CUDA(after_launch());
   }
   // Phase 2: Newton-Schulz steps make W orthogonal to FP64 accuracy:
