@@ -61,6 +61,46 @@ def test_interrupted_run_resumes_to_the_same_result(g, tmp_path, prec, dtype, st
         assert es <= 1e-3
 
 
+def test_a_new_process_resumes_after_the_first_one_ended(g, tmp_path):
+    """The interrupted run happens in a child process that ends abruptly after
+    the checkpoint of step 3 (os._exit, no teardown; none of its work is left
+    on the GPU); this process then resumes from the file and gets the
+    uninterrupted result, bit for bit, and the oracle's at the FP32 bars."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    path = str(tmp_path / "rsvd.ckpt")
+    k, p, q, seed = 20, 10, 2, 11
+    child = (
+        "import os, sys, numpy as np, torch\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "import paper_1907_06470_gb300 as g\n"
+        "from synth import prescribed_dense, spectrum_geometric\n"
+        "A, _, _ = prescribed_dense(3000, 1500, spectrum_geometric(1500, 0.98), 5, dtype=np.float32)\n"
+        f"plan = g.Plan(3000, 1500, {k}, {p}, {q}, {seed})\n"
+        f"plan.set_checkpoint({path!r}, stop_after_step=3)\n"
+        "try:\n"
+        "    plan.run(torch.as_tensor(A, device='cuda'))\n"
+        "except g.RsvdError as e:\n"
+        "    torch.cuda.synchronize()\n"
+        "    os._exit(17 if 'INTERRUPTED' in str(e) else 2)\n"
+        "os._exit(1)\n")
+    r = subprocess.run([sys.executable, "-c", child], cwd=root, timeout=900)
+    assert r.returncode == 17 and os.path.exists(path)
+    assert g.checkpoint_info(path)["step"] == 3
+    A = _A(5)
+    ref = [t.cpu() for t in g.Plan(3000, 1500, k, p, q, seed).run(A)]
+    plan = g.Plan(3000, 1500, k, p, q, seed)
+    plan.set_checkpoint(path)
+    out = [t.cpu() for t in plan.run(A)]
+    assert plan.info()["resumed_from"] == 3
+    for a, b in zip(ref, out):
+        assert torch.equal(a, b)
+    Uo, So, Vo = OR.rsvd(A.cpu().numpy(), k, p, q, seed, "f32")
+    U, S, V = (t.numpy().astype(np.float64) for t in out)
+    assert sigma_rel_err(S, So) <= 1e-5 and max_principal_angle(U, Uo) <= 1e-4
+
+
 def test_host_csr_resumes_from_its_checkpoint(g, tmp_path):
     """A CSR matrix held in host memory: the checkpoint's fingerprint is taken
     from the host arrays, so a restarted plan given the same host CSR resumes."""
