@@ -1247,8 +1247,11 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
       // fused sweeps stream full-width row panels (the default tile shape)
       if (P->fused && P->nb_req > 0 && P->nb_req < A->n)
         return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: fused sweeps stream full-width row panels (nb = 0 or n)");
+      // BF16 plans keep their resident tiles as BF16 copies (twice as many fit)
+      const bool bf16_cache = P->prec == RSVD_PREC_BF16 && P->dtype == RSVD_F32 && !P->fused &&
+                              round_up(P->r, 16) <= 256;
       RSVD_TRY(stream_prepare(&P->ss, A->m, A->n, elem_size(A->dtype), P->mb_req, P->nb_req, P->n_slots,
-                              P->mem_cap - P->ws_bytes, P->r, P->prec, final_prec));
+                              P->mem_cap - P->ws_bytes, P->r, P->prec, final_prec, bf16_cache));
       stream_begin_run(P->ss);
       P->streaming = true;
       if (P->dtype == RSVD_F64)

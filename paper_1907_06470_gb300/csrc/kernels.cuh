@@ -186,7 +186,7 @@ int ckpt_try_load(const std::string& path, const CkptHeader& expect, void* dev_q
 // stream.cu -- out-of-core A-passes over tiles of a pinned host matrix.
 struct StreamState;
 rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, int64_t mb_req, int64_t nb_req,
-                           int slots, size_t budget, int r, int prec, int final_prec);
+                           int slots, size_t budget, int r, int prec, int final_prec, bool bf16_cache);
 void stream_begin_run(StreamState* s);
 rsvd_status apass_streamed(StreamState* s, const rsvd_matrix& Ah, int trans, int prec, int r, const void* X,
                            void* Y, int64_t ldr, int* status, cudaStream_t st);

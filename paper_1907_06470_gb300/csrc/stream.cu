@@ -10,7 +10,12 @@
 // event that the next copy into the slot waits for.  Tiles that fit in the
 // device memory left under the cap after the workspace and the slots stay
 // resident after their first copy of a run (the resident cache), so later
-// passes of the same run stream only the rest.
+// passes of the same run stream only the rest.  BF16 plans keep the cached
+// tiles as their BF16 copy instead (half the bytes, so twice the tiles under
+// the same cap): the first forward pass of a run streams each such tile in
+// FP32 and writes its BF16 copy while multiplying it (the same operands, so the
+// same products), the later BF16 passes read the copy, and a pass in another
+// precision (the split-BF16 B^T, which needs FP32 A) streams the tile again.
 #include <vector>
 
 #include "common.cuh"
@@ -24,6 +29,8 @@ struct StreamState {
   size_t tile_bytes = 0;
   std::vector<void*> slot;
   std::vector<void*> cache;          // resident copies of tiles 0 .. ncache-1
+  bool cache16 = false;              // the cache holds BF16 copies (row stride ld16)
+  int64_t ld16 = 0;
   std::vector<char> cache_valid;     // filled during the current run
   std::vector<cudaEvent_t> copied;   // per slot
   std::vector<cudaEvent_t> freed;    // per slot
@@ -62,7 +69,7 @@ void stream_stats(const StreamState* s, uint64_t* h2d, int64_t* per_pass, int64_
 // Build (or reuse) the streaming state for an m x n host matrix of element
 // size esz within `budget` device bytes (the cap minus the plan workspace).
 rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, int64_t mb_req, int64_t nb_req,
-                           int slots, size_t budget, int r, int prec, int final_prec) {
+                           int slots, size_t budget, int r, int prec, int final_prec, bool bf16_cache) {
   if (slots < 1) slots = 2;
   // Default tile: a full-width row panel of about 512 MB (or less, to leave room
   // for the resident cache).  Rows of a panel are contiguous in host memory, and
@@ -103,7 +110,8 @@ rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, i
   if ((size_t)slots * tile_bytes + tws + ytile_bytes > budget)
     return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: mem_cap leaves no room for the streaming slots");
   StreamState* s = *ps;
-  if (s && s->mb == mb && s->nb == nb && s->S == slots && s->tile_bytes == tile_bytes) return RSVD_OK;
+  if (s && s->mb == mb && s->nb == nb && s->S == slots && s->tile_bytes == tile_bytes && s->cache16 == bf16_cache)
+    return RSVD_OK;
   delete s;
   s = new StreamState();
   *ps = s;
@@ -112,6 +120,8 @@ rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, i
   s->nb = nb;
   s->ld_tile = ld_tile;
   s->tile_bytes = tile_bytes;
+  s->cache16 = bf16_cache;
+  s->ld16 = round_up(nb, 64);
   RSVD_CUDA(cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking));
   RSVD_CUDA(cudaMalloc(&s->ws, tws));
   s->ws_bytes = tws;
@@ -128,11 +138,12 @@ rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, i
     s->freed.push_back(b);
   }
   const int64_t ntiles = cdiv(m, mb) * cdiv(n, nb);
-  int64_t ncache = (int64_t)((budget - (size_t)slots * tile_bytes - tws - ytile_bytes) / tile_bytes);
+  const size_t cache_tile_bytes = bf16_cache ? (size_t)mb * s->ld16 * 2 : tile_bytes;
+  int64_t ncache = (int64_t)((budget - (size_t)slots * tile_bytes - tws - ytile_bytes) / cache_tile_bytes);
   if (ncache > ntiles) ncache = ntiles;
   for (int64_t t = 0; t < ncache; ++t) {
     void* p = nullptr;
-    if (cudaMalloc(&p, tile_bytes) != cudaSuccess) {
+    if (cudaMalloc(&p, cache_tile_bytes) != cudaSuccess) {
       (void)cudaGetLastError();
       break;
     }
@@ -144,7 +155,7 @@ rsvd_status stream_prepare(StreamState** ps, int64_t m, int64_t n, size_t esz, i
   s->cache_valid.assign(s->cache.size(), 0);
   s->tiles_cached = (int64_t)s->cache.size();
   s->tiles_per_pass = ntiles - s->tiles_cached;
-  s->device_bytes = (size_t)(slots + s->cache.size()) * tile_bytes + tws + ytile_bytes;
+  s->device_bytes = (size_t)slots * tile_bytes + s->cache.size() * cache_tile_bytes + tws + ytile_bytes;
   return RSVD_OK;
 }
 
@@ -161,7 +172,8 @@ namespace {
 // tile (row stride ld_tile) and whether it is resident.
 rsvd_status fetch_tile(StreamState* s, const rsvd_matrix& Ah, int64_t t, int64_t row0, int64_t col0, int64_t rows,
                        int64_t cols, size_t esz, cudaStream_t st, rsvd_matrix* T, bool* cached_out) {
-  const bool cached = t < (int64_t)s->cache.size();
+  // a BF16 cache holds no FP32 tiles: the FP32 tile goes through a slot
+  const bool cached = !s->cache16 && t < (int64_t)s->cache.size();
   const int slot = (int)(t % s->S);
   void* tile = cached ? s->cache[t] : s->slot[slot];
   if (!cached || !s->cache_valid[t]) {
@@ -206,12 +218,30 @@ rsvd_status apass_streamed(StreamState* s, const rsvd_matrix& Ah, int trans, int
       const int64_t row0 = I * s->mb, col0 = J * s->nb;
       const int64_t rows = (row0 + s->mb < m ? s->mb : m - row0);
       const int64_t cols = (col0 + s->nb < n ? s->nb : n - col0);
+      const char* Xc = static_cast<const char*>(X);
+      char* Yc = static_cast<char*>(Y);
+      const bool c16 = s->cache16 && t < (int64_t)s->cache.size();
+      const float* Xt = reinterpret_cast<const float*>(Xc + (size_t)(trans ? row0 : col0) * ldr * esz);
+      float* Yt = reinterpret_cast<float*>(Yc + (size_t)(trans ? col0 : row0) * ldr * esz);
+      if (c16 && s->cache_valid[t] && prec == RSVD_PREC_BF16) {  // the resident BF16 copy
+        Bf16Source b;
+        b.data = static_cast<const uint16_t*>(s->cache[t]);
+        b.m = rows;
+        b.n = cols;
+        b.ld = s->ld16;
+        RSVD_TRY(tc_apass_from_16(b, trans, prec, r, Xt, ldr, Yt, ldr, s->ws, s->ws_bytes, status, st, true));
+        continue;
+      }
       rsvd_matrix T;
       bool cached;
       RSVD_TRY(fetch_tile(s, Ah, t, row0, col0, rows, cols, esz, st, &T, &cached));
-      const char* Xc = static_cast<const char*>(X);
-      char* Yc = static_cast<char*>(Y);
-      if (!trans)
+      if (c16 && !trans && prec == RSVD_PREC_BF16 && !s->cache_valid[t]) {
+        // the first BF16 forward pass over the tile this run: multiply it and
+        // keep its BF16 copy
+        RSVD_TRY(tc_apass_from_f32(T, 0, prec, r, Xt, ldr, Yt, ldr, 0, 0, s->ws, s->ws_bytes, status, st, true,
+                                   static_cast<uint16_t*>(s->cache[t]), s->ld16));
+        s->cache_valid[t] = 1;
+      } else if (!trans)
         RSVD_TRY(apass_dense(T, 0, prec, r, Xc + (size_t)col0 * ldr * esz, ldr, Yc + (size_t)row0 * ldr * esz, ldr,
                              0, 0, s->ws, s->ws_bytes, status, st, true));
       else

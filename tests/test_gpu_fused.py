@@ -75,10 +75,16 @@ def test_fused_streamed_matches_oracle_and_reads_a_q_plus_2_times(g, ooc_case, p
     st2 = plain.stream_stats()
     plain.close()
     # resident tiles cross the link once per run, the others once per pass:
-    # h2d = resident + passes x streamed, with q + 2 passes fused, 2q + 2 not
-    streamed = (st2["h2d_bytes"] - st["h2d_bytes"]) // q
-    resident = st["h2d_bytes"] - (q + 2) * streamed
-    assert streamed > 0 and resident > 0 and resident + streamed == A.nbytes
+    # h2d = resident + passes x streamed, with q + 2 passes fused, 2q + 2 not.
+    # (A plain BF16 plan keeps BF16 copies resident, twice as many tiles, and
+    # streams them again for its split-BF16 B^T: there only the total is
+    # compared.)
+    if prec == "bf16":
+        assert st["h2d_bytes"] < st2["h2d_bytes"]
+    else:
+        streamed = (st2["h2d_bytes"] - st["h2d_bytes"]) // q
+        resident = st["h2d_bytes"] - (q + 2) * streamed
+        assert streamed > 0 and resident > 0 and resident + streamed == A.nbytes
     Uo, So, Vo = OR.rsvd_fused_sweeps(A, k, p, q, seed, "f32" if prec == "fp32" else "bf16")
     es = sigma_rel_err(S, So)
     eu, ev = cluster_safe_angles(U, Uo, So, k), cluster_safe_angles(V, Vo, So, k)

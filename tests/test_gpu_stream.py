@@ -63,6 +63,29 @@ def test_streamed_matches_in_core(g, prec):
     assert max_principal_angle(Us, Ui) <= (1e-4 if prec == "fp32" else 1e-2)
 
 
+def test_bf16_plan_keeps_bf16_copies_resident(g):
+    """A streamed BF16 plan keeps its resident tiles as BF16 copies: 12 MB
+    more of cap hold six more 1024 x 1024 tiles (2 MB each, not 4 MB), the
+    link carries fewer bytes, and the result is the same bits as with fewer
+    resident tiles (the copy holds the very operands the FP32 tile is
+    converted to)."""
+    m, n, k, p, q, seed = 8192, 3072, 40, 12, 2, 77
+    A, _, _ = prescribed_dense(m, n, spectrum_geometric(n, 0.97), 5, dtype=np.float32)
+    Ah = torch.as_tensor(A).pin_memory()
+    base = _min_cap(g, m, n, k, p, "bf16", "f32", 1024, 1024) + 24 * 2**20
+    runs = []
+    for cap in (base, base + 12 * 2**20):
+        plan = g.Plan(m, n, k, p, q, seed, mem_cap=cap, prec="bf16", mb=1024, nb=1024)
+        out = [t.cpu() for t in plan.run(Ah)]
+        runs.append((out, plan.stream_stats()))
+        plan.close()
+    (a, sa), (b, sb) = runs
+    assert 5 <= sb["tiles_resident"] - sa["tiles_resident"] <= 7
+    assert sb["h2d_bytes"] < sa["h2d_bytes"]
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
 def test_tiles_smaller_than_a_row(g):
     """A cap so small that a tile is 16 x 16, less than one row of A."""
     m, n, k, p, q, seed = 100, 80, 6, 4, 1, 3
