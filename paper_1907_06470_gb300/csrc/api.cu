@@ -236,6 +236,8 @@ struct rsvd_plan_s {
   void* WRk = nullptr;      // r x k in dtype
   void* sign_scratch = nullptr;
   size_t sign_scratch_bytes = 0;
+  void* lift_ws = nullptr;  // the lift's tensor-core products (BF16-family plans)
+  size_t lift_ws_bytes = 0;
   void* bwd_ws = nullptr;   // backward pass (rsvd_backward)
   size_t bwd_ws_bytes = 0;
   int* status = nullptr;
@@ -374,6 +376,8 @@ size_t layout(rsvd_plan_s* P, void* base, size_t cap) {
   P->sign_scratch = c.take<char>(P->sign_scratch_bytes);
   P->bwd_ws_bytes = dense ? backward_ws_bytes(P->m, P->n, P->k, P->dtype) : 0;
   P->bwd_ws = c.take<char>(P->bwd_ws_bytes);
+  P->lift_ws_bytes = P->dtype == RSVD_F32 ? tc_gemm_wide_ws_bytes(mx, P->r, P->k, RSVD_PREC_BF16X3) : 0;
+  P->lift_ws = c.take<char>(P->lift_ws_bytes);
   if (P->prec == RSVD_PREC_FP8) {
     // quantisation tiles: the plan's tiles rounded up to multiples of 128
     Fp8Source& f = P->f8;
@@ -711,8 +715,29 @@ rsvd_status run_typed(rsvd_plan_s* P, const rsvd_matrix& A, T* U, T* S, T* V, cu
       T* WRk = static_cast<T*>(P->WRk);
       RSVD_TRY((convert_matrix<double, T>(r, k, P->UR, r, URk, k, st)));
       RSVD_TRY((convert_matrix<double, T>(r, k, P->WR, r, WRk, k, st)));
-      RSVD_TRY(simt_gemm<T>(m, k, r, Q, ldr, false, URk, k, U, k, false, 1, r, nullptr, st));
-      RSVD_TRY(simt_gemm<T>(n, k, r, Qb, ldr, false, WRk, k, V, k, false, 1, r, nullptr, st));
+      bool tc_lift = false;
+      if constexpr (std::is_same<T, float>::value) {
+        // BF16-family plans lift on the tensor cores in split BF16 (about 16
+        // significant bits per operand, far below their products' errors);
+        // FP32 plans keep the FP32 SIMT product
+        tc_lift = (prec == RSVD_PREC_BF16 || prec == RSVD_PREC_BF16X3 || prec == RSVD_PREC_FP8) &&
+                  P->lift_ws_bytes >= tc_gemm_wide_ws_bytes(m > n ? m : n, r, k, RSVD_PREC_BF16X3);
+        if (tc_lift) {
+          rsvd_matrix Qm{}, Qbm{};
+          Qm.kind = Qbm.kind = RSVD_DENSE;
+          Qm.dtype = Qbm.dtype = RSVD_F32;
+          Qm.location = Qbm.location = RSVD_ON_DEVICE;
+          Qm.m = m; Qm.n = r; Qm.data = Q; Qm.ld = ldr;
+          Qbm.m = n; Qbm.n = r; Qbm.data = Qb; Qbm.ld = ldr;
+          RSVD_TRY(tc_gemm_wide(Qm, RSVD_PREC_BF16X3, k, URk, k, U, k, P->lift_ws, P->lift_ws_bytes, P->status, st));
+          RSVD_TRY(tc_gemm_wide(Qbm, RSVD_PREC_BF16X3, k, WRk, k, V, k, P->lift_ws, P->lift_ws_bytes, P->status,
+                                st));
+        }
+      }
+      if (!tc_lift) {
+        RSVD_TRY(simt_gemm<T>(m, k, r, Q, ldr, false, URk, k, U, k, false, 1, r, nullptr, st));
+        RSVD_TRY(simt_gemm<T>(n, k, r, Qb, ldr, false, WRk, k, V, k, false, 1, r, nullptr, st));
+      }
       RSVD_TRY((convert_matrix<double, T>(1, k, P->sigma, k, S, k, st)));
       RSVD_TRY(normalise_signs<T>(m, n, k, U, k, V, k, P->sign_scratch, P->sign_scratch_bytes, st));
     }
