@@ -366,16 +366,27 @@ spmm_combine_kernel(int r, const int32_t* __restrict__ rowptr, const int* __rest
     float4 acc[V4];
 #pragma unroll
     for (int t = 0; t < V4; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int s = 0; s < nseg; ++s) {
-      const float4* p = reinterpret_cast<const float4*>(partial + (task + s) * ldp);
+    // eight segments' partials loaded together, then added in segment order
+    for (int s0 = 0; s0 < nseg; s0 += 8) {
+      float4 x[8][V4];
 #pragma unroll
-      for (int t = 0; t < V4; ++t) {
-        const int q = lane + 32 * t;
-        if (q < nv) {
-          const float4 x = p[q];
-          acc[t].x += x.x; acc[t].y += x.y; acc[t].z += x.z; acc[t].w += x.w;
+      for (int u = 0; u < 8; ++u) {
+        // past the last segment: the last one again (in cache, not added)
+        const float4* p = reinterpret_cast<const float4*>(partial + (task + min(s0 + u, nseg - 1)) * ldp);
+#pragma unroll
+        for (int t = 0; t < V4; ++t) {
+          const int q = lane + 32 * t;
+          x[u][t] = q < nv ? p[q] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (s0 + u < nseg) {
+#pragma unroll
+          for (int t = 0; t < V4; ++t) {
+            acc[t].x += x[u][t].x; acc[t].y += x[u][t].y; acc[t].z += x[u][t].z; acc[t].w += x[u][t].w;
+          }
+        }
     }
     store_row_vec<V4>(Y + (int64_t)row * ldy, r, lane, nv, accumulate, acc);
   }
