@@ -153,8 +153,8 @@ reduce_partials_kernel(int64_t M, int64_t N, int nsplit, const T* __restrict__ P
 }
 
 // The same sum with 4 consecutive columns per thread (16-byte loads) and the
-// split loop unrolled so the partial loads are in flight together; the order
-// of the additions (split 0, 1, 2, ...) is the same as above.
+// partials of up to 16 splits loaded together; the order of the additions
+// (split 0, 1, 2, ...) is the same as above.
 // One warp per output float4: lane l adds the partials of a contiguous block
 // of splits in order, then the 32 lane sums are combined by a fixed butterfly,
 // so the result does not depend on scheduling.
@@ -190,6 +190,7 @@ __global__ void reduce_partials_warp_vec4_kernel(int64_t M, int64_t N4, int nspl
   }
 }
 
+template <int U>
 __global__ void reduce_partials_vec4_kernel(int64_t M, int64_t N4, int nsplit, const float4* __restrict__ P,
                                             int64_t ldp4, int64_t pstride4, float4* __restrict__ out, int64_t ldo4,
                                             int accumulate) {
@@ -199,17 +200,15 @@ __global__ void reduce_partials_vec4_kernel(int64_t M, int64_t N4, int nsplit, c
     const int64_t i = e / N4, j = e - i * N4;
     const float4* src = P + i * ldp4 + j;
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    int z = 0;
-    for (; z + 4 <= nsplit; z += 4) {
-      float4 v[4];
+    // U partials loaded together (one wait per U), then added in order
+    for (int z0 = 0; z0 < nsplit; z0 += U) {
+      float4 v[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = src[(int64_t)(z + u) * pstride4];
+      for (int u = 0; u < U; ++u)  // past the last split: the last one again (in cache, not added)
+        v[u] = src[(int64_t)min(z0 + u, nsplit - 1) * pstride4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) { s.x += v[u].x; s.y += v[u].y; s.z += v[u].z; s.w += v[u].w; }
-    }
-    for (; z < nsplit; ++z) {
-      const float4 v = src[(int64_t)z * pstride4];
-      s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+      for (int u = 0; u < U; ++u)
+        if (z0 + u < nsplit) { s.x += v[u].x; s.y += v[u].y; s.z += v[u].z; s.w += v[u].w; }
     }
     float4* dst = out + i * ldo4 + j;
     if (accumulate) {
@@ -302,11 +301,22 @@ rsvd_status reduce_partials(int64_t M, int64_t N, int nsplit, const T* P, int64_
       return RSVD_OK;
     }
     if (vec) {
+      // a thread per output float4 where the grid allows (one round of loads)
       int64_t blocks = cdiv(M * (N / 4), 256);
-      if (blocks > 152 * 8) blocks = 152 * 8;
-      reduce_partials_vec4_kernel<<<(int)blocks, 256, 0, stream>>>(
-          M, N / 4, nsplit, reinterpret_cast<const float4*>(P), ldp / 4, pstride / 4, reinterpret_cast<float4*>(out),
-          ldo / 4, accumulate ? 1 : 0);
+      if (blocks > 152 * 64) blocks = 152 * 64;
+      // as many partials in flight as there are splits (up to 16)
+      const float4* P4 = reinterpret_cast<const float4*>(P);
+      float4* o4 = reinterpret_cast<float4*>(out);
+      const int acc = accumulate ? 1 : 0;
+      if (nsplit <= 4)
+        reduce_partials_vec4_kernel<4><<<(int)blocks, 256, 0, stream>>>(M, N / 4, nsplit, P4, ldp / 4, pstride / 4, o4,
+                                                                       ldo / 4, acc);
+      else if (nsplit <= 8)
+        reduce_partials_vec4_kernel<8><<<(int)blocks, 256, 0, stream>>>(M, N / 4, nsplit, P4, ldp / 4, pstride / 4, o4,
+                                                                       ldo / 4, acc);
+      else
+        reduce_partials_vec4_kernel<16><<<(int)blocks, 256, 0, stream>>>(M, N / 4, nsplit, P4, ldp / 4, pstride / 4,
+                                                                        o4, ldo / 4, acc);
       RSVD_CUDA(after_launch());
       return RSVD_OK;
     }
