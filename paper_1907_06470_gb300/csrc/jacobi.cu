@@ -62,6 +62,96 @@ __device__ __forceinline__ void jacobi_rotation(double a, double b, double g, do
   s = y * t;
 }
 
+// Outputs of a finished one-sided Jacobi: column norms sigma_c = ||M_c||, a
+// stable descending order, U_c = M_c / sigma_c and W_c.  Signs: each pair of
+// columns (U_c, W_c) is turned so that the entry of W_c largest in magnitude
+// (the first such) is positive, so that the output does not depend on the
+// path the sweeps took.  M (rows x r) and W (r x r) are column-major and read
+// through L2.
+
+// Warp-collective: the norm of column c and its sign (valid in every lane).
+__device__ __forceinline__ void column_norm_sign(int rows, int r, int c, const double* __restrict__ M,
+                                                 const double* __restrict__ W, int lane, double& nrm, double& sgn) {
+  double s2 = 0.0;
+  for (int i = lane; i < rows; i += 32) { const double x = __ldcg(&M[(int64_t)c * rows + i]); s2 = fma(x, x, s2); }
+  s2 = warp_sum_d(s2);
+  double wm = -1.0;
+  int wi = r;
+  for (int i = lane; i < r; i += 32) {
+    const double x = fabs(__ldcg(&W[(int64_t)c * r + i]));
+    if (x > wm) { wm = x; wi = i; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double om = __shfl_xor_sync(0xffffffffu, wm, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, wi, o);
+    if (om > wm || (om == wm && oi < wi)) { wm = om; wi = oi; }
+  }
+  nrm = sqrt(s2);
+  sgn = wi < r && __ldcg(&W[(int64_t)c * r + wi]) < 0.0 ? -1.0 : 1.0;
+}
+
+// Warp-collective: the rank of column c among the norms nrms[0..r) (ties by
+// index) and its normalised outputs.
+__device__ __forceinline__ void write_column(int rows, int r, int c, const double* __restrict__ M,
+                                             const double* __restrict__ W, const double* nrms, double sgn, int lane,
+                                             double* __restrict__ sigma, double* __restrict__ Uout,
+                                             double* __restrict__ Wout) {
+  const double sc = nrms[c];
+  int cnt = 0;
+  for (int d = lane; d < r; d += 32) cnt += (nrms[d] > sc) || (nrms[d] == sc && d < c);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  const int rank = cnt;
+  if (lane == 0) sigma[rank] = sc;
+  const double inv = sc > 0.0 ? sgn / sc : 0.0;
+  for (int i = lane; i < rows; i += 32) Uout[(int64_t)i * r + rank] = __ldcg(&M[(int64_t)c * rows + i]) * inv;
+  for (int i = lane; i < r; i += 32) Wout[(int64_t)i * r + rank] = sgn * __ldcg(&W[(int64_t)c * r + i]);
+}
+
+// All warps of one CTA (sh: 2 r doubles of shared memory).
+__device__ void form_outputs(int rows, int r, const double* __restrict__ M, const double* __restrict__ W,
+                             double* sh, double* __restrict__ sigma, double* __restrict__ Uout,
+                             double* __restrict__ Wout) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  double* sgn = sh + r;
+  for (int c = warp; c < r; c += warps) {
+    double nv, sg;
+    column_norm_sign(rows, r, c, M, W, lane, nv, sg);
+    if (lane == 0) { sh[c] = nv; sgn[c] = sg; }
+  }
+  __syncthreads();
+  for (int c = warp; c < r; c += warps) write_column(rows, r, c, M, W, sh, sgn[c], lane, sigma, Uout, Wout);
+}
+
+// Finish only: the columns of M W were orthogonalised before (the FP32
+// phase), so no sweeps run and the outputs are formed straight from M and W,
+// one warp per column over many SMs (FP64 arithmetic is slow on one SM): the
+// norms and signs (into nrm_sgn, 2 r doubles), then, after the launch
+// boundary, the ranks and the outputs.
+constexpr int kFinishWarps = 8;
+
+__global__ void __launch_bounds__(32 * kFinishWarps)
+jacobi_finish_norms_kernel(int rows, int r, const double* __restrict__ M, const double* __restrict__ W,
+                           double* __restrict__ nrm_sgn, int* sweeps_out) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kFinishWarps + (threadIdx.x >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = 0;
+  if (c >= r) return;
+  double nv, sg;
+  column_norm_sign(rows, r, c, M, W, lane, nv, sg);
+  if (lane == 0) { nrm_sgn[c] = nv; nrm_sgn[r + c] = sg; }
+}
+
+__global__ void __launch_bounds__(32 * kFinishWarps)
+jacobi_finish_out_kernel(int rows, int r, const double* __restrict__ M, const double* __restrict__ W,
+                         const double* __restrict__ nrm_sgn, double* sigma, double* Uout, double* Wout) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kFinishWarps + (threadIdx.x >> 5);
+  if (c >= r) return;
+  write_column(rows, r, c, M, W, nrm_sgn, nrm_sgn[r + c], lane, sigma, Uout, Wout);
+}
+
 // One cluster of up to 16 CTAs; warp w of CTA b owns pair slot b*warps + w of
 // every round.  Rounds are separated by the hardware cluster barrier; the
 // columns live in global memory and are accessed through L2 (.cg).
@@ -86,10 +176,9 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
   for (int64_t e = gtid; e < mm; e += gstride) __stcg(&M[e], Min[e]);
   for (int64_t e = gtid; e < ww; e += gstride) __stcg(&W[e], W0 ? W0[e] : ((e / r) == (e % r) ? 1.0 : 0.0));
   // Frobenius norm of the input (every CTA computes it), for the rounding-level
-  // column test of the sweeps (none in the finish-only mode)
+  // column test of the sweeps
   double f = 0.0;
-  if (max_sweeps > 0)
-    for (int64_t e = tid; e < mm; e += nthr) f += Min[e] * Min[e];
+  for (int64_t e = tid; e < mm; e += nthr) f += Min[e] * Min[e];
   f = warp_sum_d(f);
   if (lane == 0) red[warp] = f;
   __syncthreads();
@@ -245,52 +334,9 @@ __global__ void jacobi_cluster_kernel(int rows, int r, const double* __restrict_
     }
   }
   if (blockIdx.x != 0) return;
-  if (max_sweeps == 0) {
-    converged = true;  // finish only: the columns were orthogonalised before (FP32 phase)
-    sweep = -1;
-  }
   if (!converged) dev_set_status(status, DEV_NO_CONVERGE);
   if (tid == 0) *sweeps_out = sweep + (converged ? 1 : 0);
-  // column norms, stable descending order, normalised outputs.  Signs: each
-  // pair of columns (U_c, W_c) is turned so that the entry of W_c largest in
-  // magnitude (the first such) is positive, so that the output does not depend
-  // on the path the sweeps took.  One warp per column (sh: sigma_c, then the
-  // signs at sh + r).
-  double* sgn = sh + r;
-  for (int c = warp; c < r; c += warps) {
-    double s2 = 0.0;
-    for (int i = lane; i < rows; i += 32) { const double x = __ldcg(&M[(int64_t)c * rows + i]); s2 = fma(x, x, s2); }
-    s2 = warp_sum_d(s2);
-    double wm = -1.0;
-    int wi = r;
-    for (int i = lane; i < r; i += 32) {
-      const double x = fabs(__ldcg(&W[(int64_t)c * r + i]));
-      if (x > wm) { wm = x; wi = i; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double om = __shfl_xor_sync(0xffffffffu, wm, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, wi, o);
-      if (om > wm || (om == wm && oi < wi)) { wm = om; wi = oi; }
-    }
-    if (lane == 0) {
-      sh[c] = sqrt(s2);
-      sgn[c] = wi < r && __ldcg(&W[(int64_t)c * r + wi]) < 0.0 ? -1.0 : 1.0;
-    }
-  }
-  __syncthreads();
-  for (int c = warp; c < r; c += warps) {
-    const double sc = sh[c];
-    int cnt = 0;
-    for (int d = lane; d < r; d += 32) cnt += (sh[d] > sc) || (sh[d] == sc && d < c);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    const int rank = cnt;
-    if (lane == 0) sigma[rank] = sc;
-    const double inv = sc > 0.0 ? sgn[c] / sc : 0.0;
-    for (int i = lane; i < rows; i += 32) Uout[(int64_t)i * r + rank] = __ldcg(&M[(int64_t)c * rows + i]) * inv;
-    for (int i = lane; i < r; i += 32) Wout[(int64_t)i * r + rank] = sgn[c] * __ldcg(&W[(int64_t)c * r + i]);
-  }
+  form_outputs(rows, r, M, W, sh, sigma, Uout, Wout);
 }
 
 // FP32 first phase for r too large for one CTA's shared memory: the same
@@ -408,6 +454,31 @@ __device__ __forceinline__ float pair_group_sum(float v) {
   return v;
 }
 
+// Packed FP32 pairs (two floats in 64 bits) on the SM's two-wide FP32 path:
+// each half is one IEEE round-to-nearest multiply or fused multiply-add, as
+// the scalar instruction would give, at half the instructions.
+__device__ __forceinline__ unsigned long long f2_splat(float a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ float f2_hsum(unsigned long long a) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+  return lo + hi;
+}
+
 // column of round-robin position pos in round `round` (positions 1 .. rp-1 rotate)
 __device__ __forceinline__ int rr_col_fast(int pos, int round, int rp) {
   if (pos == 0) return 0;
@@ -422,7 +493,7 @@ size_t f32_jacobi_smem(int r) {
 }
 
 template <int V>
-__global__ void __launch_bounds__(kF32PairLanes * kF32MaxR / 2)
+__global__ void __launch_bounds__(kF32PairLanes * kF32MaxR / 2, 1)
 jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32, int* sweeps_out) {
   extern __shared__ __align__(16) float smf[];
   const int ldm = (r + 3) & ~3;
@@ -482,20 +553,21 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
           if (p >= r || q >= r) active = false;
           if (p > q) { const int t = p; p = q; q = t; }
         }
-        const float4* mp4 = reinterpret_cast<const float4*>(M + p * ldm);
-        const float4* mq4 = reinterpret_cast<const float4*>(M + q * ldm);
-        float4 xv[V], yv[V];
+        // 16 bytes per access as two packed pairs
+        const ulonglong2* mp4 = reinterpret_cast<const ulonglong2*>(M + p * ldm);
+        const ulonglong2* mq4 = reinterpret_cast<const ulonglong2*>(M + q * ldm);
+        ulonglong2 xv[V], yv[V];
         const float a = active ? nrm[p] : 0.f, b = active ? nrm[q] : 0.f;
-        float g = 0.f;
+        unsigned long long g2 = 0ull;  // (+0, +0)
 #pragma unroll
         for (int t = 0; t < V; ++t) {
           const int i4 = hl + kF32PairLanes * t;
           const bool ok = active && i4 < ld4;
-          xv[t] = ok ? mp4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
-          yv[t] = ok ? mq4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
-          g = fmaf(xv[t].x, yv[t].x, fmaf(xv[t].y, yv[t].y, fmaf(xv[t].z, yv[t].z, fmaf(xv[t].w, yv[t].w, g))));
+          xv[t] = ok ? mp4[i4] : make_ulonglong2(0ull, 0ull);
+          yv[t] = ok ? mq4[i4] : make_ulonglong2(0ull, 0ull);
+          g2 = f2_fma(xv[t].x, yv[t].x, f2_fma(xv[t].y, yv[t].y, g2));
         }
-        g = pair_group_sum(g);
+        float g = pair_group_sum(f2_hsum(g2));
         if (active && fabsf(g) > tol * sqrtf(a * b) && a > zero2 && b > zero2) {
           my_rot = true;
           my_mrel = fmaxf(my_mrel, fabsf(g) * rsqrtf(a * b));
@@ -516,20 +588,23 @@ jacobi_f32_kernel(int r, const double* __restrict__ Mc, float* __restrict__ W32,
             nrm[p] = fmaxf(fmaf(cc, a, fmaf(ss, b, -cs2)), 0.f);
             nrm[q] = fmaxf(fmaf(ss, a, fmaf(cc, b, cs2)), 0.f);
           }
-          float4* mp = reinterpret_cast<float4*>(M + p * ldm);
-          float4* mq = reinterpret_cast<float4*>(M + q * ldm);
-          float4* wp = reinterpret_cast<float4*>(W + p * ldm);
-          float4* wq = reinterpret_cast<float4*>(W + q * ldm);
+          // x' = c x - s y, y' = s x + c y on packed pairs: the product with s
+          // rounded, then one fused multiply-add
+          ulonglong2* mp = reinterpret_cast<ulonglong2*>(M + p * ldm);
+          ulonglong2* mq = reinterpret_cast<ulonglong2*>(M + q * ldm);
+          ulonglong2* wp = reinterpret_cast<ulonglong2*>(W + p * ldm);
+          ulonglong2* wq = reinterpret_cast<ulonglong2*>(W + q * ldm);
+          const unsigned long long c2 = f2_splat(c), s2 = f2_splat(sn), ns2 = f2_splat(-sn);
 #pragma unroll
           for (int u = 0; u < V; ++u) {
             const int i4 = hl + kF32PairLanes * u;
             if (i4 < ld4) {
-              const float4 xx = xv[u], yy = yv[u];
-              const float4 wu = wp[i4], wv = wq[i4];
-              mp[i4] = make_float4(c * xx.x - sn * yy.x, c * xx.y - sn * yy.y, c * xx.z - sn * yy.z, c * xx.w - sn * yy.w);
-              mq[i4] = make_float4(sn * xx.x + c * yy.x, sn * xx.y + c * yy.y, sn * xx.z + c * yy.z, sn * xx.w + c * yy.w);
-              wp[i4] = make_float4(c * wu.x - sn * wv.x, c * wu.y - sn * wv.y, c * wu.z - sn * wv.z, c * wu.w - sn * wv.w);
-              wq[i4] = make_float4(sn * wu.x + c * wv.x, sn * wu.y + c * wv.y, sn * wu.z + c * wv.z, sn * wu.w + c * wv.w);
+              const ulonglong2 xx = xv[u], yy = yv[u];
+              const ulonglong2 wu = wp[i4], wv = wq[i4];
+              mp[i4] = make_ulonglong2(f2_fma(c2, xx.x, f2_mul(ns2, yy.x)), f2_fma(c2, xx.y, f2_mul(ns2, yy.y)));
+              mq[i4] = make_ulonglong2(f2_fma(c2, yy.x, f2_mul(s2, xx.x)), f2_fma(c2, yy.y, f2_mul(s2, xx.y)));
+              wp[i4] = make_ulonglong2(f2_fma(c2, wu.x, f2_mul(ns2, wv.x)), f2_fma(c2, wu.y, f2_mul(ns2, wv.y)));
+              wq[i4] = make_ulonglong2(f2_fma(c2, wv.x, f2_mul(s2, wu.x)), f2_fma(c2, wv.y, f2_mul(s2, wu.y)));
             }
           }
         }
@@ -648,6 +723,17 @@ rsvd_status small_gemm64(int r, const double* A, bool transA, const double* B, d
 rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const double* W0, double* sigma, double* U,
                                   double* W, const JacobiWs& ws, cudaStream_t stream, double tol,
                                   int max_sweeps = kJacobiMaxSweeps) {
+  if (max_sweeps == 0) {
+    // finish only: a warp per column forms the outputs from M and the
+    // rotation W0; the norms and signs go through ws.M (rows x r >= 2 r doubles)
+    if (!W0 || rows < 2) return RSVD_ERR_INVALID_ARG;
+    const int grid = (int)cdiv(r, kFinishWarps);
+    jacobi_finish_norms_kernel<<<grid, 32 * kFinishWarps, 0, stream>>>(rows, r, Min, W0, ws.M, ws.sweeps);
+    RSVD_CUDA(after_launch());
+    jacobi_finish_out_kernel<<<grid, 32 * kFinishWarps, 0, stream>>>(rows, r, Min, W0, ws.M, sigma, U, W);
+    RSVD_CUDA(after_launch());
+    return RSVD_OK;
+  }
   RSVD_CUDA(cudaMemsetAsync(ws.rotated, 0, 3 * kJacobiMaxSweeps * sizeof(int), stream));
   const int rp = r + (r & 1);
   const int npairs = rp / 2;
@@ -660,9 +746,6 @@ rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const doub
   const size_t check_bytes = ((size_t)rows * r + r) * sizeof(double);
   const int check = max_sweeps > 0 && check_bytes <= (size_t)kClusterCheckSmem ? 1 : 0;
   const size_t smem = check ? check_bytes : 2 * (size_t)r * sizeof(double);
-  // finish only (no sweeps): one CTA of 16 warps forms the outputs (the
-  // kernel's register use allows 512 threads)
-  if (max_sweeps == 0) ncta = 1;
   static bool attr_set = false;
   if (!attr_set) {
     RSVD_CUDA(cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -671,7 +754,7 @@ rsvd_status launch_cluster_jacobi(int rows, int r, const double* Min, const doub
     attr_set = true;
   }
   for (;;) {
-    const int warps = max_sweeps == 0 ? 16 : (int)cdiv(npairs, ncta);
+    const int warps = (int)cdiv(npairs, ncta);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ncta);
     cfg.blockDim = dim3(32 * warps);
