@@ -9,6 +9,13 @@
 // into FMAs), and the angle is reduced to [-pi/4, pi/4] exactly in integer
 // arithmetic, so the values are reproducible bit for bit by any IEEE FP64
 // implementation that follows the same operation order.
+//
+// bfloat16 outputs need each deviate only to its nearest bfloat16 (8
+// significant bits), and FP64 arithmetic is slow on this GPU, so they are first
+// evaluated in FP32 from the same random bits (bf16_pair_fp32); the FP64
+// evaluation decides only the deviates whose FP32 value lies too close to a
+// bfloat16 rounding boundary (about one in 1500).  The result is the rounding
+// of the FP64 value either way.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -132,10 +139,8 @@ __device__ __forceinline__ void store_value(void* out, int64_t idx, double v) {
   }
 }
 
-// FP64 values of stream elements 2g and 2g+1.
-__device__ __forceinline__ void gaussian_pair(uint64_t seed, uint64_t g, double* even, double* odd) {
-  uint32_t c[4] = {(uint32_t)g, (uint32_t)(g >> 32), 0u, 0u};
-  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+// FP64 Box-Muller values of the 128 Philox bits c.
+__device__ __forceinline__ void box_muller_f64(const uint32_t c[4], double* even, double* odd) {
   const uint64_t n1 = (((uint64_t)c[0] << 32) | c[1]) >> 11;
   const uint64_t n2 = (((uint64_t)c[2] << 32) | c[3]) >> 11;
   const double u1 = (double)(n1 + 1) * 0x1.0p-53;  // exact, in (0, 1]
@@ -159,6 +164,73 @@ __device__ __forceinline__ void gaussian_pair(uint64_t seed, uint64_t g, double*
   *odd = __dmul_rn(rho, sin_t);
 }
 
+// FP64 values of stream elements 2g and 2g+1.
+__device__ __forceinline__ void gaussian_pair(uint64_t seed, uint64_t g, double* even, double* odd) {
+  uint32_t c[4] = {(uint32_t)g, (uint32_t)(g >> 32), 0u, 0u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  box_muller_f64(c, even, odd);
+}
+
+// bfloat16 bits of the nearest-even rounding shared by every real within a
+// relative 2^-19 of v (v a nonzero normal FP32 value), or -1 when the band
+// straddles a rounding boundary.  The band's ends are widened by 2^-22 for
+// their own rounding, so they enclose the band; rounding is monotone, so equal
+// roundings of the ends decide every value in it.
+__device__ __forceinline__ int bf16_if_determined(float v) {
+  const float a = fabsf(v);
+  const uint32_t bl = __float_as_uint(a * (1.f - 0x1.2p-19f));
+  const uint32_t bh = __float_as_uint(a * (1.f + 0x1.2p-19f));
+  const uint32_t rl = (bl + 0x7FFFu + ((bl >> 16) & 1u)) >> 16;
+  const uint32_t rh = (bh + 0x7FFFu + ((bh >> 16) & 1u)) >> 16;
+  if (rl != rh) return -1;
+  return (int)(rl | (v < 0.f ? 0x8000u : 0u));
+}
+
+// The bfloat16 roundings of the two FP64 deviates of the Philox bits c, from an
+// FP32 evaluation of the same Box-Muller formula, when the error bound decides
+// them; false otherwise.  Error of the FP32 values relative to the exact
+// deviates (CUDA's documented bounds: logf, log1pf, sinpif, cospif 1 ulp,
+// sqrtf correctly rounded; conversions of the integers 2^-24):
+//   ln u1: u1 <= 1/2 from logf of u1 rounded (|ln u1| >= ln 2), u1 > 1/2 from
+//          log1pf of 1 - u1 = m 2^-53 (m exact) rounded: at most 2^-22;
+//   rho = sqrt(-2 ln u1): half that plus 2^-24; sin and cos of pi y with
+//   y = d 2^-53 in [-1/4, 1/4] (the quadrant reduction is exact): 1.56 2^-23;
+//   the final product 2^-24 --
+// about 3.6 2^-23 = 2^-21.2 in all, within the 2^-19 band (the FP64 deviates
+// differ from the exact ones by a few 2^-53).  t = 2 n2 + 1 is odd and q 2^52
+// even, so d != 0: no deviate is zero, all are normal FP32 values.
+__device__ __forceinline__ bool bf16_pair_fp32(const uint32_t c[4], uint16_t* even, uint16_t* odd) {
+  const uint64_t n1 = (((uint64_t)c[0] << 32) | c[1]) >> 11;
+  const uint64_t n2 = (((uint64_t)c[2] << 32) | c[3]) >> 11;
+  float L;
+  if (n1 + 1 <= (1ULL << 52)) {
+    L = logf(__ull2float_rn(n1 + 1) * 0x1.0p-53f);
+  } else {
+    const uint64_t mm = (1ULL << 53) - (n1 + 1);  // 1 - u1 = mm 2^-53
+    if (mm == 0) return false;                    // u1 = 1: deviates of zero, left to FP64
+    L = log1pf(-(__ull2float_rn(mm) * 0x1.0p-53f));
+  }
+  const float rho = sqrtf(-2.f * L);
+  const uint64_t t = 2 * n2 + 1;
+  const uint64_t q = (t + (1ULL << 51)) >> 52;
+  const int64_t d = (int64_t)t - (int64_t)(q << 52);
+  const float y = __ll2float_rn(d) * 0x1.0p-53f;
+  const float s = sinpif(y), co = cospif(y);
+  float sin_t, cos_t;
+  switch (q & 3) {
+    case 0: sin_t = s; cos_t = co; break;
+    case 1: sin_t = co; cos_t = -s; break;
+    case 2: sin_t = -s; cos_t = -co; break;
+    default: sin_t = -co; cos_t = s; break;
+  }
+  const int be = bf16_if_determined(rho * cos_t);
+  const int bo = bf16_if_determined(rho * sin_t);
+  if (be < 0 || bo < 0) return false;
+  *even = (uint16_t)be;
+  *odd = (uint16_t)bo;
+  return true;
+}
+
 template <int kDtype>
 __global__ void __launch_bounds__(256) gaussian_kernel(uint64_t seed, int64_t n, int64_t r,
                                                        int layout, void* out, int64_t ld) {
@@ -166,16 +238,38 @@ __global__ void __launch_bounds__(256) gaussian_kernel(uint64_t seed, int64_t n,
   const int64_t pairs = (total + 1) / 2;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < pairs;
        g += (int64_t)gridDim.x * blockDim.x) {
-    double v2[2];
-    gaussian_pair(seed, (uint64_t)g, &v2[0], &v2[1]);
+    uint32_t c[4] = {(uint32_t)g, (uint32_t)((uint64_t)g >> 32), 0u, 0u};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    if constexpr (kDtype == RSVD_BF16 || kDtype == kF32HoldingBf16) {
+      uint16_t b2[2];
+      if (!bf16_pair_fp32(c, &b2[0], &b2[1])) {
+        double v2[2];
+        box_muller_f64(c, &v2[0], &v2[1]);
+        b2[0] = f64_to_bf16_bits(v2[0]);
+        b2[1] = f64_to_bf16_bits(v2[1]);
+      }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t e = 2 * g + h;
-      if (e >= total) break;
-      const double v = v2[h];
-      const int64_t i = e / r, j = e - i * r;
-      const int64_t idx = layout == 0 ? i * ld + j : j * ld + i;
-      store_value<kDtype>(out, idx, v);
+      for (int h = 0; h < 2; ++h) {
+        const int64_t e = 2 * g + h;
+        if (e >= total) break;
+        const int64_t i = e / r, j = e - i * r;
+        const int64_t idx = layout == 0 ? i * ld + j : j * ld + i;
+        if constexpr (kDtype == kF32HoldingBf16)
+          static_cast<uint32_t*>(out)[idx] = (uint32_t)b2[h] << 16;
+        else
+          static_cast<uint16_t*>(out)[idx] = b2[h];
+      }
+    } else {
+      double v2[2];
+      box_muller_f64(c, &v2[0], &v2[1]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t e = 2 * g + h;
+        if (e >= total) break;
+        const int64_t i = e / r, j = e - i * r;
+        const int64_t idx = layout == 0 ? i * ld + j : j * ld + i;
+        store_value<kDtype>(out, idx, v2[h]);
+      }
     }
   }
 }

@@ -45,6 +45,27 @@ def test_gaussian_bf16_bit_exact(g, n, r, seed):
     assert np.array_equal(got.T, ref)
 
 
+@pytest.mark.parametrize("n,r,seed", [(20000, 120, 2002), (1_000_000, 8, 11), (4_000_000, 1, 0xDEADBEEF)])
+def test_gaussian_bf16_fp32_first_equals_fp64_rounding(g, n, r, seed):
+    """bfloat16 entries are evaluated in FP32 first and go to FP64 only within
+    a relative 2^-19 of a rounding boundary: over millions of entries, the near-
+    boundary ones included, they are the FP64 entries (bit-exact with the
+    oracle above) rounded once by the oracle's to_bf16_bits."""
+    f64 = g.gaussian(n, r, seed, "f64").cpu().numpy()
+    ref = OG.to_bf16_bits(f64)
+    for layout in (0, 1):
+        got = g.gaussian(n, r, seed, "bf16", layout=layout).cpu().view(torch.int16).numpy().view(np.uint16)
+        assert np.array_equal(got if layout == 0 else got.T, ref)
+    # the FP64 decisions are exercised: entries within 2^-19 (relative) of the
+    # midpoint between two bfloat16 neighbours
+    a = np.abs(f64).ravel()
+    e = np.floor(np.log2(a))
+    spacing = np.exp2(e - 7)
+    frac = a / spacing - np.floor(a / spacing)
+    near = np.abs(frac - 0.5) * spacing <= 2.0 ** -19 * a
+    assert near.sum() >= 100
+
+
 def test_gaussian_sample_at_full_size(g):
     """1e6 x 350 stream (the sparse workload's width): sampled entries match the oracle."""
     n, r, seed = 1_000_000, 350, 2004
