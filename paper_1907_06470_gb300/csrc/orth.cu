@@ -459,18 +459,28 @@ chol_inv_fused_kernel(int r, const double* __restrict__ G, T* __restrict__ Lout,
 // R = R2 R1 with R1 = L1^T, R2 = L2^T (both upper triangular).  A dead pivot l
 // of the first sweep carries no part of Y (its column was a negligible
 // residual), so row l of R1 counts as zero.
+// One warp per entry (i, j): lanes over l in [i, j], their partial sums added
+// by a fixed shuffle tree (FP64, every SM busy: the sum is short, the FP64
+// latency long); entries below the diagonal are zero.
 template <typename T1, typename T2>
 __global__ void rprod_kernel(int r, const T1* __restrict__ L1, const int* __restrict__ dead1,
                              const T2* __restrict__ L2, double* __restrict__ R) {
+  const int lane = threadIdx.x & 31;
   const int64_t total = (int64_t)r * r;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total; e += nw) {
     const int i = (int)(e / r), j = (int)(e % r);
     double s = 0.0;
-    for (int l = i; l <= j; ++l)
+    for (int l = i + lane; l <= j; l += 32)
       if (!dead1[l]) s += (double)L2[(int64_t)l * r + i] * (double)L1[(int64_t)j * r + l];
-    R[e] = j >= i ? s : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) R[e] = j >= i ? s : 0.0;
   }
+}
+
+int rprod_blocks(int r) {
+  const int64_t b = cdiv((int64_t)r * r * 32, 256);
+  return (int)(b < 152 * 8 ? b : 152 * 8);
 }
 
 // Rows per partial Gram: each partial is a sum of gram_chunk(M) products in
@@ -679,7 +689,7 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
       RSVD_CUDA(after_launch());
       RSVD_TRY(panel_times_tc(M, r, Q1, ws.ld_tmp, Rt, Q, ldq, ws, stream));
       if (R) {
-        rprod_kernel<float, float><<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r, L1, ws.dead1, L2, R);
+        rprod_kernel<float, float><<<rprod_blocks(r), 256, 0, stream>>>(r, L1, ws.dead1, L2, R);
         RSVD_CUDA(after_launch());
       }
       return RSVD_OK;
@@ -701,7 +711,7 @@ rsvd_status orth_panel(int64_t M, int r, const T* Y, int64_t ldy, T* Q, int64_t 
   RSVD_CUDA(after_launch());
   RSVD_TRY(simt_gemm<T>(M, r, r, Q1, ws.ld_tmp, false, Rt, ws.ld_rt, Q, ldq, false, 1, r, nullptr, stream));
   if (R) {
-    rprod_kernel<T, T><<<(int)cdiv((int64_t)r * r, 256), 256, 0, stream>>>(r, L1, ws.dead1, L2, R);
+    rprod_kernel<T, T><<<rprod_blocks(r), 256, 0, stream>>>(r, L1, ws.dead1, L2, R);
     RSVD_CUDA(after_launch());
   }
   return RSVD_OK;
