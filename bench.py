@@ -400,16 +400,41 @@ def run_ours(args):
             torch.cuda.synchronize()
             host_split.append([round((tb - ta) * 1e3, 2), round((time.perf_counter() - tb) * 1e3, 2)])
         t_e2e = (time.perf_counter() - t0) / steps_e2e
+        # the same K steps with the inputs pipelined (Plan.prefetch): each step's
+        # 8 GB copy is issued before the previous step runs, so the link works
+        # while the previous matrix is factored; every step still copies its A
+        # (the first copy inside the timed region too) and reads back U, S, V
+        host_pipe = []
+        t0 = time.perf_counter()
+        plan_h.prefetch(A_host)
+        for i in range(steps_e2e):
+            ta = time.perf_counter()
+            if i + 1 < steps_e2e:
+                plan_h.prefetch(A_host)
+            plan_h.run(A_host, Ud, Sd, Vd)
+            tb = time.perf_counter()
+            Uh.copy_(Ud, non_blocking=True)
+            Sh.copy_(Sd, non_blocking=True)
+            Vh.copy_(Vd, non_blocking=True)
+            torch.cuda.synchronize()
+            host_pipe.append([round((tb - ta) * 1e3, 2), round((time.perf_counter() - tb) * 1e3, 2)])
+        t_pipe = (time.perf_counter() - t0) / steps_e2e
         gc.enable()
-        plan_h.set_profiling(True)  # one more call with stage events, outside the timed loop
+        plan_h.set_profiling(True)  # one more call with stage events, outside the timed loops
         plan_h.run(A_host, Ud, Sd, Vd)
         torch.cuda.synchronize()
-        e2e = {"value": ws / t_e2e, "unit": UNIT, "h2d_bytes_per_step": m * n * 4,
-               "d2h_bytes_per_step": (m * k + k + n * k) * 4, "ms_per_step": t_e2e * 1e3,
+        e2e = {"value": ws / t_pipe, "unit": UNIT, "h2d_bytes_per_step": m * n * 4,
+               "d2h_bytes_per_step": (m * k + k + n * k) * 4, "ms_per_step": t_pipe * 1e3,
+               "pipelined": "Plan.prefetch(A) of step i+1 issued before Plan.run of step i "
+                            "(rsvd_plan_prefetch); one H2D copy of A and one read-back of U, S, V per step",
+               "median_step_ms": statistics.median(a + b for a, b in host_pipe),
+               "host_ms_run_and_readback": host_pipe,
+               "serial": {"value": ws / t_e2e, "ms_per_step": t_e2e * 1e3,
+                          "median_step_ms": statistics.median(a + b for a, b in host_split),
+                          "host_ms_run_and_readback": host_split,
+                          "note": "each step's copy issued by its own Plan.run"},
                "stages_ms_untimed_call": {kk: round(vv, 3) for kk, vv in plan_h.stage_ms().items()
-                                          if kk in ("h2d", "total")},
-               "median_step_ms": statistics.median(a + b for a, b in host_split),
-               "host_ms_run_and_readback": host_split}
+                                          if kk in ("h2d", "total")}}
         plan_h.close()
         del A_host
 

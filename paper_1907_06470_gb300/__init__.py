@@ -174,6 +174,17 @@ class Plan:
         del keep
         return U, S, V
 
+    def prefetch(self, A):
+        """Start copying the pinned host tensor A to the device for a later
+        run(A) of this plan and return at once (rsvd_plan_prefetch): a stream
+        of host matrices keeps the link busy while the previous one is being
+        factored.  A must stay unchanged until that run has returned."""
+        if A.is_cuda:
+            raise ValueError("prefetch takes a host tensor")
+        d = _dense_desc(A)
+        self._prefetched = getattr(self, "_prefetched", [])[-1:] + [A]  # alive until the run
+        _check(load().rsvd_plan_prefetch(self._h, C.byref(d)))
+
     def backward(self, U, S, V, dU=None, dS=None, dV=None):
         """dA of the truncated SVD (see rsvd_backward) for cotangents dU, dS, dV (None = zero)."""
         torch = _torch()

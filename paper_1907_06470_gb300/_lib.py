@@ -61,6 +61,7 @@ SIGNATURES = {
     "rsvd_plan_min_cap": (c_i32, [c_i64, c_i64, C.c_int, C.c_int, C.POINTER(RsvdOpts), C.POINTER(c_size)]),
     "rsvd_plan_info": (c_i32, [c_vp, C.POINTER(RsvdPlanInfo)]),
     "rsvd_run": (c_i32, [c_vp, C.POINTER(RsvdMatrix), c_vp, c_vp, c_vp, c_vp]),
+    "rsvd_plan_prefetch": (c_i32, [c_vp, C.POINTER(RsvdMatrix)]),
     "rsvd_full": (c_i32, [C.POINTER(RsvdMatrix), c_vp, c_vp, c_vp, c_vp]),
     "rsvd_destroy": (None, [c_vp]),
     "rsvd_backward": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),

@@ -41,7 +41,7 @@ def _sources():
 def _digest() -> str:
     h = hashlib.sha256()
     files = _sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
-    files.append(os.path.join(INCLUDE, "rsvd.h"))
+    files += sorted(os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h"))
     for f in files:
         h.update(f.encode())
         with open(f, "rb") as fh:

@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "rsvd_pipeline.h"
 
 namespace rsvd {
 
@@ -250,6 +251,21 @@ struct rsvd_plan_s {
   int64_t h2d_chunk_rows = 0;
   int h2d_chunks = 0;
   bool h2d_pending = false;          // the current run's copy is in flight
+  // Host matrices prefetched for later runs (rsvd_plan_prefetch): up to two
+  // copies pending on h2d_stream, each into its own device buffer; rsvd_run
+  // takes the oldest when its descriptor is the run's A.
+  struct Prefetch {
+    void* dev = nullptr;
+    size_t bytes = 0;
+    bool pending = false;
+    uint64_t seq = 0;
+    rsvd_matrix desc{};
+    int64_t ldd = 0, chunk_rows = 0;
+    int chunks = 0;
+    std::vector<cudaEvent_t> ev;  // as h2d_ev
+  };
+  Prefetch pre[2];
+  uint64_t pre_seq = 0;
   uint16_t* a16 = nullptr;  // BF16 plans in core: BF16 copy of A, written by the first forward pass
   size_t a16_bytes = 0;
   int64_t a16_ld = 0;
@@ -970,6 +986,59 @@ rsvd_status full_svd_tall(const rsvd_matrix& A, void* U, void* S, void* V, cudaS
 
 }  // namespace
 
+namespace rsvd {
+namespace {
+
+// Row chunks of about 256 MB (whole 128-row tiles) of a dense host A copied to
+// dst (rows of ldd elements) on the plan's copy stream, one event after each
+// chunk (ev[c]) and one after the last (ev[chunks]); ev[chunks + 1] orders the
+// copies after the work queued on `after` when that is given.
+rsvd_status copy_host_chunks(rsvd_plan_t P, const rsvd_matrix& A, void* dst, int64_t ldd,
+                             std::vector<cudaEvent_t>& ev, cudaStream_t after, bool wait_after,
+                             int64_t* chunk_rows, int* chunks) {
+  const size_t esz = elem_size(A.dtype);
+  const size_t row = (size_t)A.n * esz;
+  const size_t dpitch = (size_t)ldd * esz, spitch = (size_t)A.ld * esz;
+  int64_t crow = (int64_t)(((size_t)256 << 20) / std::max<size_t>(dpitch, 1));
+  crow = std::max<int64_t>(128, crow / 128 * 128);
+  const int nch = (int)cdiv(A.m, crow);
+  if (!P->h2d_stream) RSVD_CUDA(cudaStreamCreateWithFlags(&P->h2d_stream, cudaStreamNonBlocking));
+  while ((int)ev.size() < nch + 2) {
+    cudaEvent_t e;
+    RSVD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ev.push_back(e);
+  }
+  if (wait_after) {
+    RSVD_CUDA(cudaEventRecord(ev[nch + 1], after));
+    RSVD_CUDA(cudaStreamWaitEvent(P->h2d_stream, ev[nch + 1], 0));
+  }
+  for (int c = 0; c < nch; ++c) {
+    const int64_t r0 = (int64_t)c * crow, rows = std::min<int64_t>(crow, A.m - r0);
+    RSVD_CUDA(cudaMemcpy2DAsync(static_cast<char*>(dst) + (size_t)r0 * dpitch, dpitch,
+                                static_cast<const char*>(A.data) + (size_t)r0 * spitch, spitch, row, rows,
+                                cudaMemcpyHostToDevice, P->h2d_stream));
+    RSVD_CUDA(cudaEventRecord(ev[c], P->h2d_stream));
+  }
+  RSVD_CUDA(cudaEventRecord(ev[nch], P->h2d_stream));
+  *chunk_rows = crow;
+  *chunks = nch;
+  return RSVD_OK;
+}
+
+bool same_host_matrix(const rsvd_matrix& a, const rsvd_matrix& b) {
+  return a.kind == b.kind && a.dtype == b.dtype && a.location == b.location && a.m == b.m && a.n == b.n &&
+         a.ld == b.ld && a.data == b.data;
+}
+
+// Pending prefetches dropped: their copies complete in order on h2d_stream
+// and their buffers are reused by later prefetches only.
+void drop_prefetches(rsvd_plan_t P) {
+  for (auto& e : P->pre) e.pending = false;
+}
+
+}  // namespace
+}  // namespace rsvd
+
 extern "C" {
 
 const char* rsvd_status_str(rsvd_status s) {
@@ -1264,6 +1333,7 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
     if (P->mem_cap && P->ws_bytes + bytes > P->mem_cap) {
       if (a16) return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: a BF16 or FP16 A is not streamed (it must fit the cap)");
       if (P->Adev) { cudaFree(P->Adev); P->Adev = nullptr; P->a_copy_bytes = 0; }
+      drop_prefetches(P);
       if (P->ws_bytes >= P->mem_cap) return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: no room left for streaming");
       if (P->prec == RSVD_PREC_FP8)
         return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: FP8 precision needs A in device memory (no streaming)");
@@ -1283,44 +1353,40 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
         return run_typed<double>(P, Ad, static_cast<double*>(U), static_cast<double*>(S), static_cast<double*>(V), st);
       return run_typed<float>(P, Ad, static_cast<float*>(U), static_cast<float*>(S), static_cast<float*>(V), st);
     }
-    if (P->a_copy_bytes < bytes) {
-      if (P->Adev) cudaFree(P->Adev);
-      P->Adev = nullptr;
-      P->a_copy_bytes = 0;
-      RSVD_CUDA(cudaMalloc(&P->Adev, bytes));
-      P->a_copy_bytes = bytes;
+    // the oldest pending prefetch, when it is this A, replaces the copy
+    rsvd_plan_s::Prefetch* pre = nullptr;
+    for (auto& e : P->pre)
+      if (e.pending && (!pre || e.seq < pre->seq)) pre = &e;
+    if (pre && !same_host_matrix(pre->desc, *A)) {
+      drop_prefetches(P);
+      pre = nullptr;
     }
-    const size_t row = (size_t)A->n * elem_size(A->dtype);
-    const size_t dpitch = (size_t)ldd * elem_size(A->dtype), spitch = (size_t)A->ld * elem_size(A->dtype);
-    // row chunks of about 256 MB (whole 128-row tiles), copied on a side stream
-    int64_t crow = (int64_t)(((size_t)256 << 20) / std::max<size_t>(dpitch, 1));
-    crow = std::max<int64_t>(128, crow / 128 * 128);
-    const int nch = (int)cdiv(A->m, crow);
-    if (!P->h2d_stream) RSVD_CUDA(cudaStreamCreateWithFlags(&P->h2d_stream, cudaStreamNonBlocking));
-    while ((int)P->h2d_ev.size() < nch + 2) {
-      cudaEvent_t e;
-      RSVD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-      P->h2d_ev.push_back(e);
-    }
-    {
+    if (pre) {
+      pre->pending = false;
+      std::swap(P->h2d_ev, pre->ev);  // the first pass waits on the prefetch's chunk events
+      P->h2d_chunk_rows = pre->chunk_rows;
+      P->h2d_chunks = pre->chunks;
+      Ad.data = pre->dev;
+      Ad.ld = pre->ldd;
+      if (P->prof.on) {
+        Span sp(P->prof, RSVD_STAGE_H2D, st);
+        RSVD_CUDA(cudaStreamWaitEvent(st, P->h2d_ev[P->h2d_chunks], 0));
+      }
+    } else {
+      if (P->a_copy_bytes < bytes) {
+        if (P->Adev) cudaFree(P->Adev);
+        P->Adev = nullptr;
+        P->a_copy_bytes = 0;
+        RSVD_CUDA(cudaMalloc(&P->Adev, bytes));
+        P->a_copy_bytes = bytes;
+      }
       Span sp(P->prof, RSVD_STAGE_H2D, st);
       // the copies start after the work already queued on the caller's stream
-      RSVD_CUDA(cudaEventRecord(P->h2d_ev[nch + 1], st));
-      RSVD_CUDA(cudaStreamWaitEvent(P->h2d_stream, P->h2d_ev[nch + 1], 0));
-      for (int c = 0; c < nch; ++c) {
-        const int64_t r0 = (int64_t)c * crow, rows = std::min<int64_t>(crow, A->m - r0);
-        RSVD_CUDA(cudaMemcpy2DAsync(static_cast<char*>(P->Adev) + (size_t)r0 * dpitch, dpitch,
-                                    static_cast<const char*>(A->data) + (size_t)r0 * spitch, spitch, row, rows,
-                                    cudaMemcpyHostToDevice, P->h2d_stream));
-        RSVD_CUDA(cudaEventRecord(P->h2d_ev[c], P->h2d_stream));
-      }
-      RSVD_CUDA(cudaEventRecord(P->h2d_ev[nch], P->h2d_stream));
-      if (P->prof.on) RSVD_CUDA(cudaStreamWaitEvent(st, P->h2d_ev[nch], 0));  // the stage time covers the copy
+      RSVD_TRY(copy_host_chunks(P, *A, P->Adev, ldd, P->h2d_ev, st, true, &P->h2d_chunk_rows, &P->h2d_chunks));
+      if (P->prof.on) RSVD_CUDA(cudaStreamWaitEvent(st, P->h2d_ev[P->h2d_chunks], 0));  // the stage time covers the copy
+      Ad.data = P->Adev;
     }
-    P->h2d_chunk_rows = crow;
-    P->h2d_chunks = nch;
     P->h2d_pending = true;
-    Ad.data = P->Adev;
     Ad.ld = ldd;
     Ad.location = RSVD_ON_DEVICE;
   }
@@ -1333,6 +1399,48 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
     P->h2d_pending = false;
   }
   return res;
+}
+
+rsvd_status rsvd_plan_prefetch(rsvd_plan_t P, const rsvd_matrix* A) {
+  if (!P || !A) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_prefetch: NULL argument");
+  const bool a16 = A->dtype == RSVD_BF16 || A->dtype == RSVD_F16;
+  if (P->kind != RSVD_DENSE || A->kind != RSVD_DENSE || A->location != RSVD_ON_HOST || !A->data)
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_prefetch: a dense host A of a dense plan");
+  if (A->m != P->m || A->n != P->n || A->ld < A->n || (A->dtype != P->dtype && !a16))
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_prefetch: A does not match the plan (shape or dtype)");
+  if (a16 && (P->dtype != RSVD_F32 || P->prec != RSVD_PREC_BF16))
+    return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_prefetch: a BF16 or FP16 A needs an F32 plan with BF16 precision");
+  const int64_t ldd = a16 ? round_up(A->n, 8) : A->n;
+  const size_t bytes = (size_t)A->m * ldd * elem_size(A->dtype);
+  if (P->mem_cap && P->ws_bytes + bytes > P->mem_cap)
+    return fail(RSVD_ERR_UNSUPPORTED, "rsvd_plan_prefetch: A does not fit the cap in core (rsvd_run streams it)");
+  rsvd_plan_s::Prefetch* e = nullptr;
+  for (auto& x : P->pre)
+    if (!x.pending) { e = &x; break; }
+  if (!e) return fail(RSVD_ERR_INVALID_ARG, "rsvd_plan_prefetch: two prefetches are already pending");
+  if (P->mem_cap) {
+    size_t held = P->ws_bytes + P->a_copy_bytes + P->a16_bytes;
+    for (auto& x : P->pre) held += &x == e ? std::max(x.bytes, bytes) : x.bytes;
+    if (held > P->mem_cap) return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_plan_prefetch: no room for the prefetch buffers");
+  }
+  if (e->bytes < bytes) {
+    if (e->dev) cudaFree(e->dev);
+    e->dev = nullptr;
+    e->bytes = 0;
+    if (cudaMalloc(&e->dev, bytes) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(RSVD_ERR_OOM, "rsvd_plan_prefetch: no device memory for the buffer");
+    }
+    e->bytes = bytes;
+  }
+  // the buffer is free: every run returns after its work has completed, and
+  // an earlier copy into it precedes this one on the same stream
+  RSVD_TRY(copy_host_chunks(P, *A, e->dev, ldd, e->ev, nullptr, false, &e->chunk_rows, &e->chunks));
+  e->ldd = ldd;
+  e->desc = *A;
+  e->seq = ++P->pre_seq;
+  e->pending = true;
+  return RSVD_OK;
 }
 
 rsvd_status rsvd_csr_tile(int64_t m, int64_t n, const int32_t* rowptr, const int32_t* colidx, const float* val,
@@ -1398,6 +1506,11 @@ rsvd_status rsvd_backward(rsvd_plan_t P, const void* U, const void* S, const voi
 
 void rsvd_destroy(rsvd_plan_t P) {
   if (!P) return;
+  if (P->h2d_stream) cudaStreamSynchronize(P->h2d_stream);  // no copy in flight into a freed buffer
+  for (auto& e : P->pre) {
+    if (e.dev) cudaFree(e.dev);
+    for (auto ev : e.ev) cudaEventDestroy(ev);
+  }
   if (P->ws) cudaFree(P->ws);
   if (P->Adev) cudaFree(P->Adev);
   if (P->a16) cudaFree(P->a16);

@@ -14,8 +14,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared_functions():
-    with open(os.path.join(ROOT, "include", "rsvd.h")) as fh:
-        text = fh.read()
+    text = ""
+    for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if name.endswith(".h"):
+            with open(os.path.join(ROOT, "include", name)) as fh:
+                text += fh.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"^\s*(?:rsvd_status|size_t|void|const char\*|unsigned long long)\s+(rsvd_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
