@@ -1036,6 +1036,21 @@ void drop_prefetches(rsvd_plan_t P) {
   for (auto& e : P->pre) e.pending = false;
 }
 
+// Under a memory cap, a run that does not take a prefetch gives the room of
+// the idle prefetch buffers back (their copies finish first).
+void release_idle_prefetch_buffers(rsvd_plan_t P) {
+  bool any = false;
+  for (auto& e : P->pre) any |= !e.pending && e.dev;
+  if (!any) return;
+  if (P->h2d_stream) cudaStreamSynchronize(P->h2d_stream);
+  for (auto& e : P->pre)
+    if (!e.pending && e.dev) {
+      cudaFree(e.dev);
+      e.dev = nullptr;
+      e.bytes = 0;
+    }
+}
+
 }  // namespace
 }  // namespace rsvd
 
@@ -1334,6 +1349,7 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
       if (a16) return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: a BF16 or FP16 A is not streamed (it must fit the cap)");
       if (P->Adev) { cudaFree(P->Adev); P->Adev = nullptr; P->a_copy_bytes = 0; }
       drop_prefetches(P);
+      release_idle_prefetch_buffers(P);
       if (P->ws_bytes >= P->mem_cap) return fail(RSVD_ERR_CAP_TOO_SMALL, "rsvd_run: no room left for streaming");
       if (P->prec == RSVD_PREC_FP8)
         return fail(RSVD_ERR_UNSUPPORTED, "rsvd_run: FP8 precision needs A in device memory (no streaming)");
@@ -1373,6 +1389,7 @@ rsvd_status rsvd_run(rsvd_plan_t P, const rsvd_matrix* A, void* U, void* S, void
         RSVD_CUDA(cudaStreamWaitEvent(st, P->h2d_ev[P->h2d_chunks], 0));
       }
     } else {
+      if (P->mem_cap) release_idle_prefetch_buffers(P);
       if (P->a_copy_bytes < bytes) {
         if (P->Adev) cudaFree(P->Adev);
         P->Adev = nullptr;
