@@ -42,7 +42,8 @@ extern "C" {
  * consumes the rows as they land, exactly as for a copy rsvd_run makes itself
  * (the results are the same bits).  A run given any other matrix drops the
  * pending prefetches (their copies still complete in order) and copies its A
- * itself.
+ * itself; under a memory cap, such a run (and a streamed run) first frees the
+ * idle prefetch buffers, so that the plan stays within the cap.
  * Errors: INVALID_ARG (NULL, a matrix that is not the plan's shape and dtype,
  * not dense on the host, or two prefetches already pending), UNSUPPORTED (A
  * would be streamed: it does not fit the plan's cap in core), CAP_TOO_SMALL
