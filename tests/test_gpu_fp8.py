@@ -76,7 +76,7 @@ def test_fp8_apass_is_the_product_of_the_decoded_matrix(g, trans, tile):
 
 def test_fp8_rsvd_reported_accuracy(g):
     """The randomized SVD on the FP8 path with the split-BF16 refinement of B^T
-    (c2 recipe scaled to 8000 x 4000): reported against the FP64 oracle; the
+    (the 100000 x 20000 dense recipe scaled to 8000 x 4000): reported against the FP64 oracle; the
     bound only guards against a broken path."""
     m, n, k, p, q, seed = 8000, 4000, 100, 20, 2, 2002
     A, _, _ = prescribed_dense(m, n, spectrum_harmonic_noisy(n, 1e-4, 3002), 1002, dtype=np.float32)
