@@ -344,3 +344,11 @@ def test_opts_layout_matches_the_header():
     assert [f for f, _ in _lib.RsvdOpts._fields_] == ["prec", "refine", "mb", "nb", "n_slots", "dtype", "kind",
                                                       "auto_q", "auto_q_tol", "fused", "reserved"]
     assert C.sizeof(_lib.RsvdOpts) == 56
+
+
+def test_prefetch_rejects_null_arguments_on_the_host(lib):
+    """rsvd_plan_prefetch checks its arguments before touching a plan or a GPU."""
+    from paper_1907_06470_gb300 import _lib
+    d = _lib.RsvdMatrix()
+    assert lib.rsvd_plan_prefetch(None, None) == 1
+    assert lib.rsvd_plan_prefetch(None, C.byref(d)) == 1
